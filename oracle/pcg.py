@@ -1,0 +1,62 @@
+"""Oracle preconditioned conjugate gradient, Alg. 1 (Sec. 2.2) (TEST INFRASTRUCTURE).
+
+x0 = 0, r0 = b; under pure Neumann walls the residual is shifted to zero mean after it
+is formed (Sec. 2.2, the null-space remark); the loop runs while ||r||_2 > tol ||b||_2
+(relative residual, b after the mean shift), the preconditioner is one FAS-style
+mu-cycle (oracle.mg.vcycle).  Returns (x, iterations, history of ||r||/||b||).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import mg
+
+
+def pcg(H, b, tol=1e-6, max_iter=200, prm=None, precond=True, transpose=False):
+    A = H.A.T.tocsr() if transpose else H.A
+    b = np.asarray(b, np.float64).copy()
+    ns = H.nullspace
+    if ns:
+        b = b - b.mean()
+    x = np.zeros_like(b)
+    r = b.copy()
+    bn = np.linalg.norm(b)
+    hist = [1.0]
+    if bn == 0.0:
+        return x, 0, hist
+    M = (lambda v: mg.vcycle(H, v, prm)) if precond else (lambda v: v.copy())
+    z = M(r)
+    p = z.copy()
+    rz = r @ z
+    k = 0
+    while np.linalg.norm(r) > tol * bn and k < max_iter:
+        Ap = A @ p
+        alpha = rz / (Ap @ p)
+        x = x + alpha * p
+        r = r - alpha * Ap
+        if ns:
+            r = r - r.mean()
+        k += 1
+        hist.append(np.linalg.norm(r) / bn)
+        if np.linalg.norm(r) <= tol * bn:
+            break
+        z = M(r)
+        rz_new = r @ z
+        beta = rz_new / rz
+        p = z + beta * p
+        rz = rz_new
+    return x, k, hist
+
+
+def direct_solve(H, b, transpose=False):
+    """Dense reference solution (tiny problems): numpy solve, or least squares with the
+    zero-mean normalisation when the operator has the constant null space."""
+    A = H.A.toarray()
+    if transpose:
+        A = A.T
+    b = np.asarray(b, np.float64)
+    if H.nullspace:
+        b = b - b.mean()
+        x = np.linalg.lstsq(A, b, rcond=None)[0]
+        return x - x.mean()
+    return np.linalg.solve(A, b)

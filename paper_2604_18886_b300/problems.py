@@ -1,0 +1,326 @@
+"""Seeded synthetic problem generators for the octree Poisson solve.
+
+This module produces INPUTS only: octree descriptions (root size, depth, refinement
+predicate parameters), per-face beta (fluid area fractions of cut faces), and
+right-hand sides (manufactured solutions, random divergence fields). It holds none
+of the solver's arithmetic (no operator, no coarsening, no cycle, no Krylov step);
+both the CUDA library and the CPU oracle consume its arrays unchanged.
+
+Geometry conventions shared by every consumer:
+  * Domain is the unit cube; the root grid has n0^3 cells; depth d has cell size
+    h_d = 1/(n0*2^d) and integer coordinates 0 <= i,j,k < n0*2^d.
+  * A face is named by (axis, depth, i, j, k): the depth of its finer side and the
+    integer coordinates, at that depth, of the cell on its + side (for a T-face whose
+    fine cell sits on the - side, that + cell is the virtual fine cell inside the
+    coarse leaf).  The face lies in the plane x_axis = i_axis * h_depth.
+  * Wall order for boundary conditions: x-, x+, y-, y+, z-, z+; 1 = Dirichlet (value
+    prescribed at the wall face), 0 = Neumann.
+
+The configurations mirror the paper's test grids (Sec. 4.1): a ball refined around the
+centre, narrow-band refinement around solid surfaces, and a band around the zero set
+of a random smooth field.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+NEUMANN = 0
+DIRICHLET = 1
+
+REFINE_NONE = 0
+REFINE_BALL_CENTRE = 1
+REFINE_SDF_BAND = 2
+REFINE_SINE_BAND = 3
+
+MAX_SPHERES = 4
+MAX_BOXES = 4
+MAX_SINES = 8
+
+
+@dataclass
+class OctreeDesc:
+    """Refinement description of an adaptive octree (Sec. 3, Sec. 4.1).
+
+    refine == REFINE_BALL_CENTRE: a depth-d cell (d < max_depth) is refined iff its
+        centre lies strictly inside the first sphere (squared distance < r^2).
+    refine == REFINE_SDF_BAND: refined iff |phi(centre)| < band + (sqrt(3)/2) h_d, with
+        phi the minimum of the sphere and box signed distances.
+    refine == REFINE_SINE_BAND: refined iff |phi(centre)| < band + |grad phi(centre)|
+        (sqrt(3)/2) h_d, phi = (1/n) sum_m sin(2 pi kappa_m (d_m . x) + theta_m).
+    """
+
+    n0: int
+    max_depth: int
+    refine: int = REFINE_NONE
+    band: float = 0.0
+    spheres: list = field(default_factory=list)   # (cx, cy, cz, r)
+    boxes: list = field(default_factory=list)     # (lox, loy, loz, hix, hiy, hiz)
+    sines: list = field(default_factory=list)     # (kappa, dx, dy, dz, theta)
+
+
+@dataclass
+class Problem:
+    name: str
+    desc: OctreeDesc
+    bc: tuple                 # 6 wall codes
+    beta: str = "one"         # "one" or "cut" (fluid fraction of the solid geometry)
+    rhs: str = "zero"         # "sin_dirichlet", "exp_sin_cos", "divergence", "normal"
+    seed: int = 0
+    mode: str = "mixed"       # suggested precision mode
+    tol: float = 1e-6
+    mu: int = 1
+    solid_spheres: list = field(default_factory=list)
+    solid_boxes: list = field(default_factory=list)
+    solid_sines: list = field(default_factory=list)
+    sine_offset: float = 0.0
+
+    @property
+    def neumann(self) -> bool:
+        return all(c == NEUMANN for c in self.bc)
+
+
+# ----------------------------------------------------------------------------------
+# configurations
+
+C3_SPHERE = (0.5, 0.5, 0.5, 0.2)
+C3_BOX = (0.65, 0.2, 0.3, 0.85, 0.8, 0.7)
+
+
+def c1(n0: int = 32) -> Problem:
+    """Uniform n0^3 grid, beta = 1, homogeneous Dirichlet walls, p = sin(pi x)sin(pi y)sin(pi z)."""
+    return Problem("c1_uniform%d" % n0, OctreeDesc(n0, 0), (DIRICHLET,) * 6,
+                   beta="one", rhs="sin_dirichlet", mode="fp64", tol=1e-10)
+
+
+def c2(n0: int = 64, radius: float = 0.25) -> Problem:
+    """n0^3 base, cells with centre within `radius` of the cube centre refined once;
+    beta = 1, Dirichlet walls with the manufactured p = exp(x) sin(2 pi y) cos(2 pi z)."""
+    d = OctreeDesc(n0, 1, REFINE_BALL_CENTRE, spheres=[(0.5, 0.5, 0.5, radius)])
+    return Problem("c2_ball%d" % n0, d, (DIRICHLET,) * 6, beta="one", rhs="exp_sin_cos",
+                   mode="mixed", tol=1e-6)
+
+
+def c3(n0: int = 64, depth: int = 2, band: float = 0.05, seed: int = 4) -> Problem:
+    """Cut-cell projection: band refinement around a solid sphere and box; fluid-fraction
+    beta clamped to [1e-3, 1]; Neumann everywhere; rhs = divergence of N(0,1) face
+    velocities, mean removed."""
+    d = OctreeDesc(n0, depth, REFINE_SDF_BAND, band=band, spheres=[C3_SPHERE], boxes=[C3_BOX])
+    return Problem("c3_cut%d_d%d" % (n0, depth), d, (NEUMANN,) * 6, beta="cut", rhs="divergence",
+                   seed=seed, mode="mixed_bf16", tol=1e-6,
+                   solid_spheres=[C3_SPHERE], solid_boxes=[C3_BOX])
+
+
+def c4_tree(k: int) -> Problem:
+    """Tree k of the batched set: effective resolution from {64, 96, 128}, 2-3 levels,
+    band refinement within 0.05 of a random sphere; even k Dirichlet beta=1, odd k cut-cell
+    Neumann."""
+    rng = np.random.default_rng(5 + k)
+    eff = int(rng.choice([64, 96, 128]))
+    levels = int(rng.choice([2, 3]))
+    depth = levels - 1
+    n0 = eff // (2 ** depth)
+    r = float(rng.uniform(0.1, 0.3))
+    c = rng.uniform(0.3, 0.7, size=3)
+    sph = (float(c[0]), float(c[1]), float(c[2]), r)
+    d = OctreeDesc(n0, depth, REFINE_SDF_BAND, band=0.05, spheres=[sph])
+    if k % 2 == 0:
+        return Problem("c4_t%d" % k, d, (DIRICHLET,) * 6, beta="one", rhs="normal",
+                       seed=100 + k, mode="mixed", tol=1e-6)
+    return Problem("c4_t%d" % k, d, (NEUMANN,) * 6, beta="cut", rhs="normal", seed=100 + k,
+                   mode="mixed", tol=1e-6, solid_spheres=[sph])
+
+
+def c5_sines(seed: int = 6, n: int = 8):
+    """Random smooth field (1/n) sum sin(2 pi kappa (d.x) + theta), kappa in {1..4}."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        kappa = float(rng.integers(1, 5))
+        v = rng.normal(size=3)
+        v = v / np.linalg.norm(v)
+        theta = float(rng.uniform(0.0, 2.0 * math.pi))
+        out.append((kappa, float(v[0]), float(v[1]), float(v[2]), theta))
+    return out
+
+
+def c5(n0: int = 128, depth: int = 3, band: float = 0.02, seed: int = 7) -> Problem:
+    sines = c5_sines()
+    d = OctreeDesc(n0, depth, REFINE_SINE_BAND, band=band, sines=sines)
+    return Problem("c5_sine%d_d%d" % (n0, depth), d, (NEUMANN,) * 6, beta="cut",
+                   rhs="divergence", seed=seed, mode="mixed", tol=1e-6, solid_sines=sines)
+
+
+def by_name(name: str) -> Problem:
+    table = {"c1": c1, "c2": c2, "c3": c3, "c5": c5}
+    return table[name]()
+
+
+# ----------------------------------------------------------------------------------
+# geometry helpers (vectorised numpy, float64)
+
+def solid_sdf(p: Problem, x, y, z):
+    """Signed distance of the fluid region (positive in fluid, negative in solids):
+    min over sphere and box distances, or the sine field."""
+    x = np.asarray(x, np.float64)
+    y = np.asarray(y, np.float64)
+    z = np.asarray(z, np.float64)
+    phi = np.full(np.broadcast(x, y, z).shape, np.inf)
+    for (cx, cy, cz, r) in p.solid_spheres:
+        phi = np.minimum(phi, np.sqrt((x - cx) ** 2 + (y - cy) ** 2 + (z - cz) ** 2) - r)
+    for (lx, ly, lz, hx, hy, hz) in p.solid_boxes:
+        qx = np.abs(x - 0.5 * (lx + hx)) - 0.5 * (hx - lx)
+        qy = np.abs(y - 0.5 * (ly + hy)) - 0.5 * (hy - ly)
+        qz = np.abs(z - 0.5 * (lz + hz)) - 0.5 * (hz - lz)
+        out = np.sqrt(np.maximum(qx, 0) ** 2 + np.maximum(qy, 0) ** 2 + np.maximum(qz, 0) ** 2)
+        ins = np.minimum(np.maximum(qx, np.maximum(qy, qz)), 0.0)
+        phi = np.minimum(phi, out + ins)
+    if p.solid_sines:
+        s = np.zeros_like(phi)
+        for (kap, dx, dy, dz, th) in p.solid_sines:
+            s = s + np.sin(2 * math.pi * kap * (dx * x + dy * y + dz * z) + th)
+        phi = np.minimum(phi, s / len(p.solid_sines) - p.sine_offset)
+    return phi
+
+
+def _tri_positive_fraction(a, b, c):
+    """Area fraction of {phi > 0} on a triangle where phi is linear with vertex values a,b,c."""
+    v = np.stack([a, b, c], axis=-1)
+    v = np.sort(v, axis=-1)
+    lo, mid, hi = v[..., 0], v[..., 1], v[..., 2]
+    out = np.zeros(lo.shape)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        # exactly one vertex positive: similar triangle at the positive corner
+        one = (hi > 0) & (mid <= 0)
+        f1 = hi * hi / ((hi - lo) * (hi - mid))
+        # two vertices positive: complement of the negative corner triangle
+        two = (mid > 0) & (lo <= 0)
+        f2 = 1.0 - lo * lo / ((mid - lo) * (hi - lo))
+    out = np.where(lo > 0, 1.0, out)
+    out = np.where(one, f1, out)
+    out = np.where(two, f2, out)
+    return out
+
+
+def face_fluid_fraction(p: Problem, faces) -> np.ndarray:
+    """Fluid area fraction of each face from the SDF at its four corners, splitting the
+    face into two triangles along its (0,0)-(1,1) diagonal (local axes = the two other
+    axes in increasing order) and integrating the linear interpolant exactly."""
+    axis = faces["axis"]
+    h = 1.0 / (p.desc.n0 * (2.0 ** faces["depth"]))
+    ijk = np.stack([faces["i"], faces["j"], faces["k"]], axis=1).astype(np.float64)
+    base = ijk * h[:, None]
+    frac = np.empty(len(axis))
+    for a in range(3):
+        sel = axis == a
+        if not np.any(sel):
+            continue
+        u, v = [b for b in range(3) if b != a]
+        b0 = base[sel]
+        hh = h[sel]
+
+        def corner(du, dv):
+            q = b0.copy()
+            q[:, u] += du * hh
+            q[:, v] += dv * hh
+            return solid_sdf(p, q[:, 0], q[:, 1], q[:, 2])
+
+        p00, p10, p11, p01 = corner(0, 0), corner(1, 0), corner(1, 1), corner(0, 1)
+        t1 = _tri_positive_fraction(p00, p10, p11)
+        t2 = _tri_positive_fraction(p00, p11, p01)
+        frac[sel] = 0.5 * (t1 + t2)
+    return frac
+
+
+def face_beta(p: Problem, faces) -> np.ndarray:
+    """Per-face beta in canonical face order (float32): 1 for beta="one"; the clamped
+    fluid fraction max(1e-3, min(1, f)) for beta="cut"."""
+    n = len(faces["axis"])
+    if p.beta == "one":
+        return np.ones(n, np.float32)
+    f = face_fluid_fraction(p, faces)
+    return np.clip(f, 1e-3, 1.0).astype(np.float32)
+
+
+# ----------------------------------------------------------------------------------
+# right-hand sides
+
+def _leaf_geometry(p: Problem, leaves):
+    d = leaves["depth"].astype(np.float64)
+    h = 1.0 / (p.desc.n0 * 2.0 ** d)
+    x = (leaves["i"] + 0.5) * h
+    y = (leaves["j"] + 0.5) * h
+    z = (leaves["k"] + 0.5) * h
+    return h, x, y, z
+
+
+def exact_solution(p: Problem, x, y, z):
+    if p.rhs == "sin_dirichlet":
+        return np.sin(math.pi * x) * np.sin(math.pi * y) * np.sin(math.pi * z)
+    if p.rhs == "exp_sin_cos":
+        return np.exp(x) * np.sin(2 * math.pi * y) * np.cos(2 * math.pi * z)
+    raise ValueError("no closed-form solution for rhs kind %r" % p.rhs)
+
+
+def _source(p: Problem, x, y, z):
+    """f = -lap(p_exact)."""
+    if p.rhs == "sin_dirichlet":
+        return 3 * math.pi ** 2 * exact_solution(p, x, y, z)
+    if p.rhs == "exp_sin_cos":
+        return (8 * math.pi ** 2 - 1.0) * exact_solution(p, x, y, z)
+    raise ValueError(p.rhs)
+
+
+def rhs(p: Problem, leaves, faces=None, beta=None) -> np.ndarray:
+    """Right-hand side in canonical leaf order (float64).
+
+    Manufactured kinds: b_i = V_i f(x_i) plus, for each Dirichlet wall face of leaf i,
+    the boundary lift 2 h_i g(face centre) (the wall value enters through a half-cell
+    distance, so the face weight is 2 beta h with beta = 1 on walls).
+    "divergence": b_i = sum over the faces of i of +-beta_f h_f^2 u_f with u_f ~ N(0,1)
+    (+ on the cell's + side, - on its - side), then the mean is removed.
+    "normal": N(0,1) per leaf, mean removed when every wall is Neumann.
+    """
+    n = len(leaves["depth"])
+    if p.rhs in ("sin_dirichlet", "exp_sin_cos"):
+        h, x, y, z = _leaf_geometry(p, leaves)
+        b = h ** 3 * _source(p, x, y, z)
+        nd = p.desc.n0 * 2 ** leaves["depth"].astype(np.int64)
+        coords = (leaves["i"], leaves["j"], leaves["k"])
+        centre = (x, y, z)
+        for a in range(3):
+            for side in (0, 1):
+                if p.bc[2 * a + side] != DIRICHLET:
+                    continue
+                on = coords[a] == 0 if side == 0 else coords[a] == nd - 1
+                if not np.any(on):
+                    continue
+                fc = [c[on].copy() for c in centre]
+                fc[a] = np.zeros(on.sum()) if side == 0 else np.ones(on.sum())
+                g = exact_solution(p, fc[0], fc[1], fc[2])
+                b[on] += 2.0 * h[on] * g
+        return b
+    rng = np.random.default_rng(p.seed)
+    if p.rhs == "divergence":
+        assert faces is not None and beta is not None
+        hf = 1.0 / (p.desc.n0 * 2.0 ** faces["depth"])
+        u = rng.standard_normal(len(faces["axis"]))
+        flux = beta.astype(np.float64) * hf * hf * u
+        b = np.zeros(n)
+        np.add.at(b, faces["minus"], flux)
+        np.add.at(b, faces["plus"], -flux)
+        return b - b.mean()
+    if p.rhs == "normal":
+        b = rng.standard_normal(n)
+        if p.neumann:
+            b = b - b.mean()
+        return b
+    if p.rhs == "zero":
+        return np.zeros(n)
+    raise ValueError(p.rhs)
+
+
+def random_vector(n: int, seed: int) -> np.ndarray:
+    return np.random.default_rng(seed).standard_normal(n)

@@ -1,0 +1,110 @@
+"""Pins for the oracle octree (Sec. 3): 2:1 balance, minimality, canonical order, counts."""
+import numpy as np
+import pytest
+
+from oracle import octree as O
+from paper_2604_18886_b300 import problems as P
+
+
+def _trees():
+    yield P.c2(8).desc
+    yield P.c2(16, radius=0.3).desc
+    yield P.OctreeDesc(4, 3, P.REFINE_SDF_BAND, band=0.02, spheres=[(0.3, 0.4, 0.55, 0.17)])
+    yield P.OctreeDesc(6, 3, P.REFINE_SDF_BAND, band=0.01, spheres=[(0.21, 0.8, 0.5, 0.11)],
+                       boxes=[(0.5, 0.1, 0.2, 0.9, 0.35, 0.6)])
+    yield P.c3(8, 2).desc
+
+
+@pytest.mark.parametrize("desc", list(_trees()))
+def test_face_neighbours_differ_by_at_most_one_depth(desc):
+    t = O.Octree(desc)
+    L = t.leaves
+    # brute force over all leaf pairs sharing a face: map every depth-D position to its
+    # leaf and compare the depths of face-adjacent positions
+    D, n = t.D, t.nd(t.D)
+    owner = np.full((n, n, n), -1, np.int64)
+    for r in range(t.n_leaves):
+        d = L["depth"][r]
+        s = 2 ** (D - d)
+        i, j, k = L["i"][r] * s, L["j"][r] * s, L["k"][r] * s
+        assert np.all(owner[i:i + s, j:j + s, k:k + s] == -1)
+        owner[i:i + s, j:j + s, k:k + s] = r
+    assert np.all(owner >= 0), "leaves must tile the domain"
+    dep = L["depth"][owner]
+    for a in range(3):
+        d1 = np.take(dep, np.arange(n - 1), axis=a)
+        d2 = np.take(dep, np.arange(1, n), axis=a)
+        assert np.abs(d1 - d2).max() <= 1
+
+
+@pytest.mark.parametrize("desc", list(_trees()))
+def test_balance_is_minimal_and_contains_predicate(desc):
+    t = O.Octree(desc)
+    for d in range(t.D + 1):
+        assert np.all(np.isin(t.pred_refined[d], t.refined[d]))
+    # every inner cell whose children are all leaves and that the predicate did not
+    # refine must be forced: some face neighbour at the same depth is itself inner
+    for d in range(t.D):
+        nd = t.nd(d)
+        extra = np.setdiff1d(t.refined[d], t.pred_refined[d])
+        for key in extra:
+            i, j, k = O._unkey(key, nd)
+            kids = t._children(d, np.array([key]))
+            if np.any(t.is_refined(d + 1, kids)):
+                continue
+            forced = False
+            for (a, s) in O.DIRS:
+                c = [int(i), int(j), int(k)]
+                c[a] += s
+                if 0 <= c[a] < nd and t.is_refined(d, np.array([O._key(*c, nd)]))[0]:
+                    forced = True
+            assert forced, "balance refinement at depth %d is not forced" % d
+
+
+@pytest.mark.parametrize("desc", list(_trees()))
+def test_counts_and_canonical_order(desc):
+    t = O.Octree(desc)
+    n_inner = sum(len(r) for r in t.refined)
+    assert t.n_leaves == desc.n0 ** 3 + 7 * n_inner
+    L = t.leaves
+    mk = O.morton(L["i"], L["j"], L["k"])
+    order = np.lexsort((mk, L["depth"]))
+    assert np.array_equal(order, np.arange(t.n_leaves))
+    vol = (1.0 / (desc.n0 * 2.0 ** L["depth"])) ** 3
+    assert abs(vol.sum() - 1.0) < 1e-12
+
+
+def test_neighbour_table_consistency():
+    t = O.Octree(P.c2(8).desc)
+    kind, rank = t.neighbour_table()
+    L = t.leaves
+    for r in range(t.n_leaves):
+        for q, (a, s) in enumerate(O.DIRS):
+            if kind[r, q] == O.SAME:
+                o = rank[r, q]
+                assert L["depth"][o] == L["depth"][r]
+                assert kind[o, q ^ 1] == O.SAME and rank[o, q ^ 1] == r
+            elif kind[r, q] == O.COARSER:
+                o = rank[r, q]
+                assert L["depth"][o] == L["depth"][r] - 1
+                assert kind[o, q ^ 1] == O.FINER
+    f = t.faces()
+    # every SAME pair appears once as a face, every COARSER relation once
+    n_same = (kind == O.SAME).sum() // 2
+    n_t = (kind == O.COARSER).sum()
+    assert len(f["axis"]) == n_same + n_t
+    mk = O.morton(f["i"], f["j"], f["k"])
+    order = np.lexsort((mk, f["depth"], f["axis"]))
+    assert np.array_equal(order, np.arange(len(order)))
+
+
+def test_ball_centre_predicate_exact():
+    # squared distance test is exact for these dyadic centres
+    d = P.OctreeDesc(4, 1, P.REFINE_BALL_CENTRE, spheres=[(0.5, 0.5, 0.5, 0.25)])
+    # depth-0 centres are (i+0.5)/4: distance^2 from 0.5 is 3*(0.125^2) = 0.046875 < 0.0625
+    # for the 8 central cells and >= 0.046875 + 0.25 - ... for the others
+    sel = O.refine_predicate(d, 0, np.array([1, 2, 0, 3]), np.array([1, 2, 1, 1]),
+                             np.array([1, 2, 1, 1]))
+    assert list(sel) == [True, True, False, False]
+    t = O.Octree(d)
+    assert len(t.refined[0]) == 8 and t.n_leaves == 64 + 7 * 8
