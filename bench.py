@@ -1,0 +1,328 @@
+"""Benchmark: full multigrid-preconditioned CG solve to relative residual 1e-6.
+
+One step = one ocg_pcg_solve (Alg. 1 with one FAS-style V-cycle per iteration) of the
+two-level octree workload: 64^3 root grid, cells whose centre lies within 0.25 of the
+cube centre refined once (382,936 leaves), beta = 1, Dirichlet walls, manufactured
+p = exp(x) sin(2 pi y) cos(2 pi z); FP32 cycle inside FP64 PCG ("mixed"), with the plain
+FP32 solve reported beside it.  Inputs are resident in HBM before the timed region; L2
+is flushed (256 MB write) before every timed step.  Under torchrun every rank solves
+its own replica (the path does not shard below one octree): weak scaling, no
+collective in the data path.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes as C
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "solve Mcells/s at rel-res 1e-6 (mixed/batched vs plain FP32), % HBM roof"
+UNIT = "Mcells/s"
+WORKLOAD = ("octree 64^3 root, ball r=0.25 at the centre refined once (382,936 leaves, "
+            "effective 128^3), beta=1, Dirichlet walls, p=exp(x)sin(2pi y)cos(2pi z)")
+# algorithmic bytes per cell of one red-black colour sweep: 16 B coefficients (c, c_x-,
+# c_y-, c_z- in FP32) + 4 B u read + 2 B u write (half the cells) + 2 B b (half)
+SWEEP_BYTES_PER_CELL = 24.0
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def _kernel_hash():
+    h = hashlib.sha256()
+    for f in ("kernels.cuh", "ocg_api.cu"):
+        with open(os.path.join(ROOT, "paper_2604_18886_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _profiled_traffic():
+    """DRAM bytes per launch of the probed sweep from the committed ncu summary, if it
+    was taken on the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", "sweep_c2_level0.txt")
+    try:
+        kv = {}
+        for line in open(p):
+            if ":" in line:
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+        if kv.get("kernel_hash") == _kernel_hash():
+            return float(kv["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class Clocks:
+    def __init__(self, index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _setup(dev):
+    import numpy as np
+    import torch
+    from paper_2604_18886_b300 import problems as P
+    from paper_2604_18886_b300 import solver as S
+    p = P.c2(64)
+    tree = S.Octree(p.desc)
+    faces = tree.faces()
+    beta = P.face_beta(p, faces)
+    hier = S.Hierarchy(tree, torch.from_numpy(beta).to(dev), p.bc, S.mg_params(coef="f32"))
+    b = P.rhs(p, tree.leaves(), faces, beta)
+    return p, tree, hier, torch.from_numpy(b).to(dev), np
+
+
+def _time_solves(hier, b, x, steps, precision, flush, stream):
+    import torch
+    times, iters = [], []
+    for s in range(steps):
+        flush.fill_(float(s))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, st = hier.solve(b, x, tol=1e-6, precision=precision, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        iters.append(st.iterations)
+        assert st.converged
+    return times, iters
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2604_18886_b300 import _lib as L
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    p, tree, hier, b, np = _setup(dev)
+    x = torch.empty_like(b)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+    for _ in range(args.warmup):
+        hier.solve(b, x, tol=1e-6, precision="mixed", stream=stream)
+        hier.solve(b, x, tol=1e-6, precision="fp32", stream=stream)
+    # ---- timed region: mixed solve
+    levels = [tree.level(m)[0].shape[0] for m in range(0, tree.D + 1)]
+    big = int(max(range(len(levels)), key=lambda q: levels[q]))
+    L.check(L.lib().ocg_probe_set(hier.handle, L.OCG_PROBE_SWEEP, big))
+    n0 = C.c_int64()
+    L.check(L.lib().ocg_launch_count(C.byref(n0)))
+    clocks = Clocks(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    times, iters = _time_solves(hier, b, x, args.steps, "mixed", flush, stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    if world > 1:
+        dist.barrier()
+    ck = clocks.stop()
+    n1 = C.c_int64()
+    L.check(L.lib().ocg_launch_count(C.byref(n1)))
+    nl, tot_ms, cells = C.c_int64(), C.c_double(), C.c_int64()
+    L.check(L.lib().ocg_probe_read(hier.handle, C.c_void_p(stream.cuda_stream), C.byref(nl),
+                                   C.byref(tot_ms), C.byref(cells)))
+    L.check(L.lib().ocg_probe_set(hier.handle, L.OCG_PROBE_OFF, 0))
+    ms = statistics.mean(times)
+    total_ms = sum(times)
+    if world > 1:
+        tt = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    value = world * tree.n_leaves * args.steps / (total_ms / 1e3) / 1e6
+    # ---- plain FP32 beside it
+    times32, iters32 = _time_solves(hier, b, x, args.steps, "fp32", flush, stream)
+    v32 = tree.n_leaves / (statistics.mean(times32) / 1e3) / 1e6
+    # ---- end to end through the C ABI with host buffers
+    bh = b.cpu().pin_memory()
+    xh = torch.empty_like(bh).pin_memory()
+    e2e_t = []
+    for s in range(args.steps):
+        flush.fill_(float(s))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.copy_(bh, non_blocking=True)
+        hier.solve(b, x, tol=1e-6, precision="mixed", stream=stream)
+        xh.copy_(x, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_t.append(e0.elapsed_time(e1))
+    e2e_total = sum(e2e_t)
+    if world > 1:
+        tt = torch.tensor([e2e_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_total = float(tt.item())
+    e2e = world * tree.n_leaves * args.steps / (e2e_total / 1e3) / 1e6
+    # ---- roofline of the dominant kernel (red-black sweep on the largest level)
+    peak, peak_kind = _peaks()
+    avg_launch_ms = tot_ms.value / max(nl.value, 1)
+    achieved = SWEEP_BYTES_PER_CELL * cells.value / (avg_launch_ms / 1e3) / 1e9
+    traffic = _profiled_traffic()
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 cycle + f64 pcg", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "precision": "mixed (FP32 V-cycle, FP64 PCG)", "tol": 1e-6,
+                   "leaves": tree.n_leaves, "iterations": iters, "cycle": "V (mu=1), nu=2/2, coarsest 10",
+                   "l2": "flushed before every timed step (256 MB write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "wall_s_timed": round(wall, 3)},
+        "plain_fp32": {"value": round(v32, 3), "unit": UNIT, "ms_per_step": round(statistics.mean(times32), 4),
+                       "iterations": iters32},
+        "value_mi_cells": round(value / 1.048576, 3),
+        "roofline": {"bound": "hbm", "kernel": "k_sweep (RBGS colour sweep) on level %d" % big,
+                     "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "peak_source": peak_kind,
+                     "bytes_per_cell": SWEEP_BYTES_PER_CELL, "cells_per_launch": cells.value,
+                     "launches": nl.value, "avg_launch_us": round(avg_launch_ms * 1e3, 3),
+                     "traffic": traffic},
+        "e2e": {"value": round(e2e, 3), "unit": UNIT, "h2d_bytes_per_step": tree.n_leaves * 8,
+                "d2h_bytes_per_step": tree.n_leaves * 8},
+        "clocks": ck,
+        "gpu_launches": int(n1.value - n0.value),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(budget_s=args.cpu_budget)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def _oracle_problem():
+    from oracle import octree as O
+    from oracle import operator as OP
+    from paper_2604_18886_b300 import problems as P
+    p = P.c2(64)
+    t = O.Octree(p.desc)
+    f = t.faces()
+    beta = P.face_beta(p, f)
+    H = OP.Hierarchy(t, beta, p.bc)
+    b = P.rhs(p, t.leaves, f, beta)
+    return t, H, b
+
+
+def cpu_baseline(budget_s=15.0):
+    """The FP64 oracle (explicit CSR, scipy) timed on the host on the same workload."""
+    from oracle import pcg
+    t, H, b = _oracle_problem()
+    times = []
+    t_end = time.perf_counter() + budget_s
+    while not times or (time.perf_counter() < t_end and len(times) < 20):
+        t0 = time.perf_counter()
+        pcg.pcg(H, b, tol=1e-6)
+        times.append(time.perf_counter() - t0)
+    v = t.n_leaves / statistics.mean(times) / 1e6
+    return {"value": round(v, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d full solves of the same workload (oracle set-up excluded), %.1f s" %
+                      (len(times), sum(times))}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return
+    from oracle import pcg
+    t, H, b = _oracle_problem()
+    for _ in range(args.warmup):
+        pcg.pcg(H, b, tol=1e-6)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        _, k, _ = pcg.pcg(H, b, tol=1e-6)
+        times.append(time.perf_counter() - t0)
+    ms = statistics.mean(times) * 1e3
+    v = t.n_leaves / (ms / 1e3) / 1e6
+    out = {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": WORKLOAD, "precision": "FP64 oracle (scipy CSR, Alg. 4 cycle, Alg. 1)",
+                      "tol": 1e-6, "leaves": t.n_leaves, "iterations": k},
+           "cpu_baseline": {"value": round(v, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": "one full solve per step (set-up excluded)"},
+           "e2e": {"value": round(v, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

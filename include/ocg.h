@@ -1,0 +1,194 @@
+/*
+ * ocg.h - C ABI of libocg: multigrid-preconditioned conjugate gradient for
+ * div(beta grad p) = b on a 2:1-balanced adaptive octree with cut cells, on one
+ * B300 GPU (sm_103a).
+ *
+ * Method: "Matrix-Free Multigrid with Algebraically Consistent Coarsening on Adaptive
+ * Octrees" (Wang, Sun, Zhu).  Operator: Sec. 2.1 (Eq. projection-poisson-system) with
+ * the T-junction ghost rule of Sec. 3.1 (Eq. t-junction-ghost-values); coarsening:
+ * Sec. 2.5, Alg. 3; preconditioner: the FAS-style mu-cycle of Sec. 3.2, Alg. 4, with
+ * red-black Gauss-Seidel smoothing (Sec. 2.3); Krylov loop: Alg. 1 (Sec. 2.2).
+ *
+ * Conventions
+ *  - Every function returns an int status: OCG_OK (0) or a negative OCG_E* code;
+ *    ocg_last_error() returns a message for the calling thread's last failure.
+ *  - Handles (ocg_octree, ocg_hier) are opaque and owned by the library; release them
+ *    with the matching *_destroy.  A hierarchy keeps a pointer to its octree: destroy
+ *    the hierarchy first.
+ *  - Vector arguments named *_dev are caller-owned device pointers; *_host are
+ *    caller-owned host pointers.  Leaf vectors are indexed in canonical leaf order:
+ *    sorted by (depth, Morton key of (i,j,k) with x in bit 0).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  A call
+ *    is asynchronous on that stream unless its comment says it synchronises.
+ *  - Boundary codes per wall in the order x-, x+, y-, y+, z-, z+: OCG_BC_NEUMANN (0) or
+ *    OCG_BC_DIRICHLET (1, value held at the wall face, weight 2*h, beta = 1 on walls;
+ *    a non-zero wall value enters through the right-hand side).
+ */
+#ifndef OCG_H
+#define OCG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OCG_OK 0
+#define OCG_EINVAL (-1)    /* malformed argument or unsupported size */
+#define OCG_ENOMEM (-2)    /* device or host allocation failed */
+#define OCG_ECUDA (-3)     /* a CUDA runtime call failed */
+#define OCG_ENOTCONV (-4)  /* max_iter reached before the tolerance; stats are filled */
+#define OCG_ENAN (-5)      /* a non-finite residual norm was detected */
+#define OCG_ESTATE (-6)    /* handle in the wrong state for this call */
+
+#define OCG_BC_NEUMANN 0
+#define OCG_BC_DIRICHLET 1
+
+#define OCG_REFINE_NONE 0        /* uniform root grid */
+#define OCG_REFINE_BALL_CENTRE 1 /* refine iff |centre - c|^2 < r^2 (first sphere) */
+#define OCG_REFINE_SDF_BAND 2    /* refine iff |phi(centre)| < band + (sqrt(3)/2) h */
+
+#define OCG_F64 0
+#define OCG_F32 1
+
+#define OCG_PREC_FP64 0        /* FP64 PCG and FP64 cycle; needs coef_dtype OCG_F64 */
+#define OCG_PREC_FP32 1        /* FP32 vectors throughout, FP64 dot products */
+#define OCG_PREC_MIXED 2       /* FP64 PCG vectors and dots, FP32 cycle */
+
+typedef struct ocg_octree ocg_octree;
+typedef struct ocg_hier ocg_hier;
+
+/* Refinement description (Sec. 3, Sec. 4.1 grids).  Root grid n0^3 cells on the unit
+ * cube (n0 even, 2 <= n0, n0 * 2^max_depth <= 2^20), leaves at depths 0..max_depth.
+ * A depth-d cell with d < max_depth is refined when the predicate holds at its centre
+ * x = (i + 0.5) / (n0 2^d); predicate arithmetic is IEEE float64 in a fixed order:
+ *   BALL_CENTRE: (dx*dx + dy*dy) + dz*dz < r*r with d = x - centre of spheres[0]
+ *   SDF_BAND:    |phi| < band + (0.5*sqrt(3)) * (1/(n0 2^d)), phi = min over
+ *                spheres sqrt(dx*dx+dy*dy+dz*dz) - r and boxes (lo, hi):
+ *                q = |x - 0.5*(lo+hi)| - 0.5*(hi-lo),
+ *                sqrt(mx*mx+my*my+mz*mz) + min(max(qx, max(qy, qz)), 0), m = max(q, 0)
+ * followed by the minimal refinement that makes face-neighbouring leaves differ by at
+ * most one depth (Sec. 3). */
+typedef struct {
+    int32_t n0;
+    int32_t max_depth;
+    int32_t refine;
+    int32_t n_spheres;      /* <= 4 */
+    int32_t n_boxes;        /* <= 4 */
+    int32_t reserved;
+    double band;
+    double spheres[4][4];   /* cx, cy, cz, r */
+    double boxes[4][6];     /* lox, loy, loz, hix, hiy, hiz */
+} ocg_octree_desc;
+
+/* Build the octree and its multigrid tables on the host (no device call; the tables are
+ * uploaded to the current device by the first ocg_setup_hierarchy on this octree).
+ * Errors: EINVAL (bad desc), ENOMEM. */
+int ocg_octree_build(const ocg_octree_desc* desc, ocg_octree** out);
+void ocg_octree_destroy(ocg_octree* t);
+
+/* counts[0] leaves, [1] canonical faces, [2] max depth D, [3] coarsest level mc (<= 0),
+ * [4] cells over all levels (padded), [5] T-junction octet records, [6] cells of the
+ * tree levels 0..D (leaves and inner), [7] octets over all levels. */
+int ocg_octree_counts(const ocg_octree* t, int64_t counts[8]);
+
+/* Canonical tables for bit-exact comparison (host buffers sized from counts).
+ * Leaves: depth, i, j, k (coordinates at the leaf's depth), n_leaves each. */
+int ocg_octree_export_leaves(const ocg_octree* t, int32_t* depth, int32_t* i, int32_t* j,
+                             int32_t* k);
+/* Per leaf and direction (x-,x+,y-,y+,z-,z+), 6 entries per leaf: kind 0 wall,
+ * 1 same-depth leaf, 2 coarser leaf (fine side of a T-junction), 3 refined neighbour
+ * (coarse side); rank = canonical rank of the neighbour leaf for kinds 1 and 2, else -1. */
+int ocg_octree_export_neighbours(const ocg_octree* t, int8_t* kind, int64_t* rank);
+/* Faces in canonical order (axis, depth of the finer side, Morton key of the cell on
+ * the + side at that depth); minus/plus = canonical leaf ranks of the two sides. */
+int ocg_octree_export_faces(const ocg_octree* t, int32_t* axis, int32_t* depth, int32_t* i,
+                            int32_t* j, int32_t* k, int64_t* minus, int64_t* plus);
+/* Cells of multigrid level m (mc <= m <= D) in Morton order of the level's grid: depth-m
+ * cells for m >= 0, the uniform root coarsening n0/2^-m for m < 0 (padding cells of an
+ * odd coarsest grid excluded).  Call with i == NULL to get *n only. leaf: 1 for leaves. */
+int ocg_octree_export_level(const ocg_octree* t, int32_t m, int64_t* n, int32_t* i,
+                            int32_t* j, int32_t* k, int8_t* leaf);
+
+/* Multigrid parameters (Sec. 2.3, 3.3). */
+typedef struct {
+    int32_t mu;            /* cycle index: 1 V-cycle, 2 W-cycle */
+    int32_t nu_pre;        /* RBGS iterations before the coarse correction (red->black) */
+    int32_t nu_post;       /* after it (black->red) */
+    int32_t nu_coarsest;   /* at the coarsest level: half red->black, half black->red */
+    double beta_restrict;  /* beta applied on the restriction (Alg. 4): 2 */
+    double alpha;          /* R = P^T / alpha (Sec. 3.3): 2 */
+    int32_t coef_dtype;    /* OCG_F64 or OCG_F32 storage of the matrix-free coefficients */
+    int32_t bf16_coarse;   /* 1: the cycle reads BF16 copies of levels below the finest */
+} ocg_mg_params;
+
+/* Fill leaf coefficients from face beta (canonical face order, float32, device) and the
+ * wall codes (Sec. 2.1; T sub-faces per Sec. 3.1), then coarsen every level with Alg. 3
+ * (FP64 arithmetic, stored in coef_dtype).  Synchronises.
+ * Errors: EINVAL (negative or non-finite beta, bad params), ENOMEM, ECUDA. */
+int ocg_setup_hierarchy(const ocg_octree* t, const float* face_beta_dev, const int32_t bc[6],
+                        const ocg_mg_params* prm, void* stream, ocg_hier** out);
+void ocg_hier_destroy(ocg_hier* h);
+
+/* Stored coefficients (c, c_x-, c_y-, c_z-) of level m, cells in the order of
+ * ocg_octree_export_level, as float64 host arrays.  Synchronises. */
+int ocg_hier_export_coefs(const ocg_hier* h, int32_t m, double* c, double* cx, double* cy,
+                          double* cz);
+
+/* y = A x for the composite leaf operator (Sec. 2.1 flux sums, Sec. 3.1 ghosts; inner
+ * values are the mean of their active children).  dtype OCG_F64 or OCG_F32 for both x
+ * and y (device, canonical leaf order, n_leaves).  transpose must be 0 in this version. */
+int ocg_apply_A(ocg_hier* h, int32_t dtype, const void* x_dev, void* y_dev, int32_t transpose,
+                void* stream);
+
+/* z = one FAS-style mu-cycle from zero applied to r (Alg. 4), dtype OCG_F64 or OCG_F32
+ * (F64 needs coef_dtype OCG_F64; F32 needs OCG_F32); device, canonical leaf order. */
+int ocg_vcycle(ocg_hier* h, int32_t dtype, const void* r_dev, void* z_dev, void* stream);
+
+typedef struct {
+    double tol;              /* stop when ||r||_2 <= tol ||b||_2 (recursive residual) */
+    int32_t max_iter;
+    int32_t precision;       /* OCG_PREC_* */
+    int32_t nullspace;       /* -1 auto (all walls Neumann), 0 off, 1 zero-mean residual */
+    int32_t reserved;
+} ocg_solve_params;
+
+#define OCG_HIST 128
+typedef struct {
+    int32_t iterations;      /* operator applications inside the loop */
+    int32_t converged;
+    double rel_res;          /* last recursive ||r|| / ||b|| */
+    double true_rel_res;     /* ||b - A x|| / ||b|| recomputed in FP64 at exit */
+    double hist[OCG_HIST];   /* rel_res after each iteration, hist[0] = 1 */
+} ocg_solve_stats;
+
+/* Solve A x = b (Alg. 1 preconditioned by one mu-cycle per iteration, x0 = 0).  b and x
+ * are float64 device vectors in canonical leaf order.  Synchronises once per iteration
+ * to test convergence.  Errors: ENOTCONV (stats filled), ENAN, EINVAL, ECUDA. */
+int ocg_pcg_solve(ocg_hier* h, const double* b_dev, double* x_dev, const ocg_solve_params* prm,
+                  ocg_solve_stats* stats, void* stream);
+
+/* Measurement hooks (no counterpart in the paper; used by the benchmark).
+ * ocg_probe_set: from now on, bracket every launch of kernel `kind` on level `level`
+ * with CUDA events recorded on the launching stream (kind 0 off, 1 red-black sweep,
+ * 2 residual+restriction, 3 prolongation, 4 composite operator (level = tree level)).
+ * ocg_probe_read: synchronises the stream, returns the number of bracketed launches,
+ * their summed duration in ms and the cells one launch processes, and resets. */
+#define OCG_PROBE_OFF 0
+#define OCG_PROBE_SWEEP 1
+#define OCG_PROBE_RESTRICT 2
+#define OCG_PROBE_PROLONG 3
+#define OCG_PROBE_APPLY 4
+int ocg_probe_set(ocg_hier* h, int32_t kind, int32_t level);
+int ocg_probe_read(ocg_hier* h, void* stream, int64_t* launches, double* total_ms,
+                   int64_t* cells_per_launch);
+/* Total kernel launches issued by this library in this process. */
+int ocg_launch_count(int64_t* n);
+
+const char* ocg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OCG_H */

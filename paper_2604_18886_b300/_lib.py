@@ -1,0 +1,109 @@
+"""ctypes binding of libocg.so (argument marshalling only; every step runs in the library).
+
+Names follow the C ABI in include/ocg.h.  Device vectors are passed as torch CUDA tensors
+(only their data pointers cross the boundary)."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libocg.so")
+
+OCG_OK, OCG_EINVAL, OCG_ENOMEM, OCG_ECUDA, OCG_ENOTCONV, OCG_ENAN, OCG_ESTATE = 0, -1, -2, -3, -4, -5, -6
+OCG_F64, OCG_F32 = 0, 1
+OCG_PREC_FP64, OCG_PREC_FP32, OCG_PREC_MIXED = 0, 1, 2
+OCG_HIST = 128
+
+
+class OctreeDesc(C.Structure):
+    _fields_ = [("n0", C.c_int32), ("max_depth", C.c_int32), ("refine", C.c_int32),
+                ("n_spheres", C.c_int32), ("n_boxes", C.c_int32), ("reserved", C.c_int32),
+                ("band", C.c_double), ("spheres", (C.c_double * 4) * 4),
+                ("boxes", (C.c_double * 6) * 4)]
+
+
+class MGParams(C.Structure):
+    _fields_ = [("mu", C.c_int32), ("nu_pre", C.c_int32), ("nu_post", C.c_int32),
+                ("nu_coarsest", C.c_int32), ("beta_restrict", C.c_double), ("alpha", C.c_double),
+                ("coef_dtype", C.c_int32), ("bf16_coarse", C.c_int32)]
+
+
+class SolveParams(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("precision", C.c_int32),
+                ("nullspace", C.c_int32), ("reserved", C.c_int32)]
+
+
+class SolveStats(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("converged", C.c_int32), ("rel_res", C.c_double),
+                ("true_rel_res", C.c_double), ("hist", C.c_double * OCG_HIST)]
+
+
+class OcgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("libocg error %d: %s" % (code, msg))
+        self.code = code
+
+
+_lib = None
+
+# (name, restype, argtypes)
+_SIGS = [
+    ("ocg_last_error", C.c_char_p, []),
+    ("ocg_octree_build", C.c_int, [C.POINTER(OctreeDesc), C.POINTER(C.c_void_p)]),
+    ("ocg_octree_destroy", None, [C.c_void_p]),
+    ("ocg_octree_counts", C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
+    ("ocg_octree_export_leaves", C.c_int, [C.c_void_p] + [C.c_void_p] * 4),
+    ("ocg_octree_export_neighbours", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("ocg_octree_export_faces", C.c_int, [C.c_void_p] + [C.c_void_p] * 7),
+    ("ocg_octree_export_level", C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int64)] + [C.c_void_p] * 4),
+    ("ocg_setup_hierarchy", C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int32), C.POINTER(MGParams),
+                                      C.c_void_p, C.POINTER(C.c_void_p)]),
+    ("ocg_hier_destroy", None, [C.c_void_p]),
+    ("ocg_hier_export_coefs", C.c_int, [C.c_void_p, C.c_int32] + [C.c_void_p] * 4),
+    ("ocg_apply_A", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
+    ("ocg_vcycle", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("ocg_pcg_solve", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(SolveParams),
+                                C.POINTER(SolveStats), C.c_void_p]),
+    ("ocg_probe_set", C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
+    ("ocg_probe_read", C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_double),
+                                 C.POINTER(C.c_int64)]),
+    ("ocg_launch_count", C.c_int, [C.POINTER(C.c_int64)]),
+]
+
+OCG_PROBE_OFF, OCG_PROBE_SWEEP, OCG_PROBE_RESTRICT, OCG_PROBE_PROLONG, OCG_PROBE_APPLY = 0, 1, 2, 3, 4
+
+EXPORTED = [n for n, _, _ in _SIGS]
+
+
+def lib():
+    """Load libocg.so (built in-tree); raises if it is missing — there is no fallback."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libocg.so is not built (run paper_2604_18886_b300/build.py)")
+        L = C.CDLL(LIB_PATH)
+        for name, res, args in _SIGS:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def check(code):
+    if code != OCG_OK:
+        msg = lib().ocg_last_error().decode(errors="replace")
+        raise OcgError(code, msg)
+    return code
+
+
+def ptr(a):
+    """Data pointer of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data_as(C.c_void_p)
+    return C.c_void_p(a.data_ptr())

@@ -1,0 +1,77 @@
+// Host-side octree construction and multigrid tables for libocg.
+//
+// Layout used by every kernel (see kernels.cuh):
+//  * Multigrid levels m = D (finest) .. mc (coarsest).  Level m >= 0 holds every cell
+//    of depth m (leaves and inner); level m < 0 is the uniform coarsening of the root
+//    grid by 2^-m.  The coarsest grid is padded to an even size with inactive cells.
+//  * Cells of a level are stored in octets: the 8 children of one cell of the next
+//    coarser grid, slot s = dx + 2 dy + 4 dz, octets sorted by the Morton key of that
+//    parent.  Inside a level the cell order is therefore the level's Morton order.
+//  * Levels are concatenated in the order 0, 1, ..., D, -1, -2, ..., mc; cells of the
+//    tree levels 0..D form the prefix [0, n_tree) that the Krylov vectors cover.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/ocg.h"
+
+namespace ocg {
+
+struct LevelMeta {
+    int m = 0;        // level index (depth for m >= 0)
+    int N = 0;        // cells per axis of the level grid
+    int Np = 0;       // padded size (N rounded up to even at the coarsest level)
+    int64_t off = 0;  // first global cell
+    int64_t ncell = 0;
+    int64_t oct_off = 0;  // first global octet (= off / 8)
+    int64_t noct = 0;
+    double h = 0.0;   // cell size for m >= 0
+};
+
+struct HostTree {
+    ocg_octree_desc desc{};
+    int n0 = 0, D = 0, mc = 0;
+    std::vector<LevelMeta> lv;          // indexed by m - mc
+    std::vector<int> order;             // storage order of levels (values m)
+    int64_t ncell = 0, noct = 0, ntree = 0, nleaf = 0, nt = 0, nface = 0;
+
+    // octet parent keys per level (sorted Morton keys of the parent coordinates)
+    std::vector<std::vector<uint64_t>> okeys;  // indexed by m - mc
+
+    // global tables
+    std::vector<int32_t> nbr;        // [6][noct]: level-local octet, -1 wall, -2-t T record
+    std::vector<int32_t> oct_parent; // [noct]: global parent cell, -1 at the coarsest level
+    std::vector<int32_t> child_oct;  // [ncell]: global octet of the children, -1 if none
+    std::vector<int32_t> tK;         // [6][nt]: global cell of the coarser leaf, -1
+    std::vector<int32_t> t_oct;      // [nt]: global octet owning the record
+    std::vector<int32_t> leaf_cell;  // [nleaf]: canonical rank -> global cell
+    std::vector<int32_t> cell_rank;  // [ncell]: global cell -> canonical rank or -1
+    std::vector<uint8_t> cell_flags; // [ncell]: bit0 leaf, bit1 active-able (not padding)
+    std::vector<int8_t> cell_level;  // [ncell]
+
+    // canonical leaves
+    std::vector<int32_t> leaf_depth, leaf_i, leaf_j, leaf_k;
+    // canonical faces
+    std::vector<int32_t> f_axis, f_depth, f_i, f_j, f_k;
+    std::vector<int64_t> f_minus, f_plus;
+    std::vector<int64_t> f_slot;     // destination of -beta*h (see setup kernel)
+    std::vector<uint8_t> f_kind;     // 0: c_{a-} of a cell, 1: T record + face weight
+    // neighbour export
+    std::vector<int8_t> nb_kind;
+    std::vector<int64_t> nb_rank;
+
+    const LevelMeta& L(int m) const { return lv[m - mc]; }
+    LevelMeta& L(int m) { return lv[m - mc]; }
+    int64_t cell_index(int m, int64_t i, int64_t j, int64_t k) const;  // -1 if absent
+    void cell_coords(int m, int64_t g, int64_t& i, int64_t& j, int64_t& k) const;
+};
+
+// Builds everything; throws std::runtime_error with a message on invalid input.
+void build_host_tree(const ocg_octree_desc& desc, HostTree& T);
+
+uint64_t morton3(uint64_t i, uint64_t j, uint64_t k);
+void demorton3(uint64_t key, uint64_t& i, uint64_t& j, uint64_t& k);
+
+}  // namespace ocg

@@ -1,0 +1,178 @@
+"""Python face of libocg: Octree / Hierarchy handles and the solve calls.
+
+Marshalling only: every arithmetic step runs inside libocg.so (host octree build, CUDA
+kernels for set-up, operator, cycle and Krylov loop).  Device vectors are torch CUDA
+tensors; the library fails loudly (ImportError / OcgError) when it is missing or a call
+fails — there is no CPU path here.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib as L
+from . import problems as P
+
+
+def _desc(d: P.OctreeDesc) -> L.OctreeDesc:
+    out = L.OctreeDesc()
+    out.n0 = d.n0
+    out.max_depth = d.max_depth
+    out.refine = d.refine
+    out.band = d.band
+    if len(d.spheres) > 4 or len(d.boxes) > 4:
+        raise ValueError("at most 4 spheres and 4 boxes")
+    if d.refine == P.REFINE_SINE_BAND:
+        raise ValueError("sine-band refinement is not available in the library")
+    out.n_spheres = len(d.spheres)
+    out.n_boxes = len(d.boxes)
+    for q, s in enumerate(d.spheres):
+        for c in range(4):
+            out.spheres[q][c] = float(s[c])
+    for q, b in enumerate(d.boxes):
+        for c in range(6):
+            out.boxes[q][c] = float(b[c])
+    return out
+
+
+class Octree:
+    """Host-built octree (libocg ocg_octree_build) with its canonical exports."""
+
+    def __init__(self, desc: P.OctreeDesc):
+        lib = L.lib()
+        self._h = C.c_void_p()
+        self.desc = desc
+        L.check(lib.ocg_octree_build(C.byref(_desc(desc)), C.byref(self._h)))
+        c = (C.c_int64 * 8)()
+        L.check(lib.ocg_octree_counts(self._h, c))
+        (self.n_leaves, self.n_faces, self.D, self.mc, self.n_cells, self.n_trec, self.n_tree,
+         self.n_oct) = [int(v) for v in c]
+
+    def __del__(self):
+        if getattr(self, "_h", None) and self._h.value:
+            L.lib().ocg_octree_destroy(self._h)
+            self._h = C.c_void_p()
+
+    @property
+    def handle(self):
+        return self._h
+
+    def leaves(self):
+        n = self.n_leaves
+        a = {k: np.empty(n, np.int32) for k in ("depth", "i", "j", "k")}
+        L.check(L.lib().ocg_octree_export_leaves(self._h, L.ptr(a["depth"]), L.ptr(a["i"]),
+                                                 L.ptr(a["j"]), L.ptr(a["k"])))
+        return {k: v.astype(np.int64) for k, v in a.items()}
+
+    def neighbours(self):
+        kind = np.empty((self.n_leaves, 6), np.int8)
+        rank = np.empty((self.n_leaves, 6), np.int64)
+        L.check(L.lib().ocg_octree_export_neighbours(self._h, L.ptr(kind), L.ptr(rank)))
+        return kind, rank
+
+    def faces(self):
+        n = self.n_faces
+        a = {k: np.empty(n, np.int32) for k in ("axis", "depth", "i", "j", "k")}
+        mi = np.empty(n, np.int64)
+        pl = np.empty(n, np.int64)
+        L.check(L.lib().ocg_octree_export_faces(self._h, L.ptr(a["axis"]), L.ptr(a["depth"]),
+                                                L.ptr(a["i"]), L.ptr(a["j"]), L.ptr(a["k"]),
+                                                L.ptr(mi), L.ptr(pl)))
+        out = {k: v.astype(np.int64) for k, v in a.items()}
+        out["minus"] = mi
+        out["plus"] = pl
+        return out
+
+    def level(self, m):
+        n = C.c_int64()
+        L.check(L.lib().ocg_octree_export_level(self._h, m, C.byref(n), None, None, None, None))
+        n = n.value
+        i, j, k = (np.empty(n, np.int32) for _ in range(3))
+        leaf = np.empty(n, np.int8)
+        L.check(L.lib().ocg_octree_export_level(self._h, m, C.byref(C.c_int64(n)), L.ptr(i), L.ptr(j),
+                                                L.ptr(k), L.ptr(leaf)))
+        return i.astype(np.int64), j.astype(np.int64), k.astype(np.int64), leaf.astype(bool)
+
+
+def mg_params(mu=1, nu_pre=2, nu_post=2, nu_coarsest=10, beta=2.0, alpha=2.0, coef="f32",
+              bf16_coarse=False) -> L.MGParams:
+    p = L.MGParams()
+    p.mu, p.nu_pre, p.nu_post, p.nu_coarsest = mu, nu_pre, nu_post, nu_coarsest
+    p.beta_restrict, p.alpha = beta, alpha
+    p.coef_dtype = L.OCG_F64 if coef == "f64" else L.OCG_F32
+    p.bf16_coarse = 1 if bf16_coarse else 0
+    return p
+
+
+PRECISIONS = {"fp64": L.OCG_PREC_FP64, "fp32": L.OCG_PREC_FP32, "mixed": L.OCG_PREC_MIXED}
+
+
+class Hierarchy:
+    """Multigrid hierarchy on the current CUDA device (ocg_setup_hierarchy)."""
+
+    def __init__(self, tree: Octree, beta, bc, prm: L.MGParams = None, stream=None):
+        import torch
+        lib = L.lib()
+        self.tree = tree
+        self.prm = prm or mg_params()
+        if isinstance(beta, np.ndarray):
+            beta = torch.from_numpy(np.ascontiguousarray(beta, np.float32)).cuda()
+        assert beta.dtype == torch.float32 and beta.is_cuda and beta.numel() == tree.n_faces
+        self._beta = beta
+        bcv = (C.c_int32 * 6)(*[int(v) for v in bc])
+        self._h = C.c_void_p()
+        st = C.c_void_p(stream.cuda_stream if stream is not None else torch.cuda.current_stream().cuda_stream)
+        L.check(lib.ocg_setup_hierarchy(tree.handle, L.ptr(beta), bcv, C.byref(self.prm), st,
+                                        C.byref(self._h)))
+
+    def __del__(self):
+        if getattr(self, "_h", None) and self._h.value:
+            L.lib().ocg_hier_destroy(self._h)
+            self._h = C.c_void_p()
+
+    @property
+    def handle(self):
+        return self._h
+
+    def coefs(self, m):
+        i, _, _, _ = self.tree.level(m)
+        n = len(i)
+        out = [np.empty(n) for _ in range(4)]
+        L.check(L.lib().ocg_hier_export_coefs(self._h, m, *[L.ptr(a) for a in out]))
+        return out
+
+    @staticmethod
+    def _stream(stream):
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream()
+        return C.c_void_p(s.cuda_stream)
+
+    def apply_A(self, x, stream=None):
+        import torch
+        y = torch.empty_like(x)
+        dt = L.OCG_F64 if x.dtype == torch.float64 else L.OCG_F32
+        L.check(L.lib().ocg_apply_A(self._h, dt, L.ptr(x), L.ptr(y), 0, self._stream(stream)))
+        return y
+
+    def vcycle(self, r, stream=None):
+        import torch
+        z = torch.empty_like(r)
+        dt = L.OCG_F64 if r.dtype == torch.float64 else L.OCG_F32
+        L.check(L.lib().ocg_vcycle(self._h, dt, L.ptr(r), L.ptr(z), self._stream(stream)))
+        return z
+
+    def solve(self, b, x=None, tol=1e-6, max_iter=100, precision="mixed", nullspace=-1,
+              stream=None, raise_on_notconv=True):
+        import torch
+        assert b.dtype == torch.float64 and b.is_cuda
+        if x is None:
+            x = torch.empty_like(b)
+        sp = L.SolveParams()
+        sp.tol, sp.max_iter, sp.precision, sp.nullspace = tol, max_iter, PRECISIONS[precision], nullspace
+        st = L.SolveStats()
+        code = L.lib().ocg_pcg_solve(self._h, L.ptr(b), L.ptr(x), C.byref(sp), C.byref(st),
+                                     self._stream(stream))
+        if code not in (L.OCG_OK, L.OCG_ENOTCONV) or (code == L.OCG_ENOTCONV and raise_on_notconv):
+            L.check(code)
+        return x, st

@@ -1,0 +1,75 @@
+"""CPU tests of libocg: the library loads and exports every declared symbol, and its host
+octree build reproduces the oracle's canonical tables bit for bit (leaves, neighbour
+codes, faces, multigrid level cell sets)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import octree as O
+from paper_2604_18886_b300 import _lib
+from paper_2604_18886_b300 import problems as P
+from paper_2604_18886_b300 import solver as S
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_library_exports_every_declared_symbol():
+    hdr = open(os.path.join(ROOT, "include", "ocg.h")).read()
+    declared = set(re.findall(r"^\s*(?:int|void|const char\*)\s+(ocg_\w+)\s*\(", hdr, re.M))
+    assert declared == set(_lib.EXPORTED)
+    L = _lib.lib()
+    for name in declared:
+        assert hasattr(L, name), name
+
+
+def _descs():
+    yield P.c1(8).desc
+    yield P.c2(8).desc
+    yield P.c2(16, radius=0.3).desc
+    yield P.c3(8, 2).desc
+    yield P.OctreeDesc(4, 3, P.REFINE_SDF_BAND, band=0.02, spheres=[(0.3, 0.4, 0.55, 0.17)])
+    yield P.OctreeDesc(6, 3, P.REFINE_SDF_BAND, band=0.01, spheres=[(0.21, 0.8, 0.5, 0.11)],
+                       boxes=[(0.5, 0.1, 0.2, 0.9, 0.35, 0.6)])
+    yield P.OctreeDesc(12, 2, P.REFINE_SDF_BAND, band=0.05, spheres=[(0.45, 0.55, 0.5, 0.23)])
+    yield P.c4_tree(1).desc
+
+
+@pytest.mark.parametrize("desc", list(_descs()))
+def test_octree_tables_bit_exact(desc):
+    t = O.Octree(desc)
+    g = S.Octree(desc)
+    assert g.n_leaves == t.n_leaves
+    lo, lg = t.leaves, g.leaves()
+    for k in ("depth", "i", "j", "k"):
+        assert np.array_equal(lo[k], lg[k]), k
+    ko, ro = t.neighbour_table()
+    kg, rg = g.neighbours()
+    assert np.array_equal(ko, kg)
+    assert np.array_equal(ro, rg)
+    fo, fg = t.faces(), g.faces()
+    assert g.n_faces == len(fo["axis"])
+    for k in ("axis", "depth", "i", "j", "k", "minus", "plus"):
+        assert np.array_equal(fo[k], fg[k]), k
+    assert g.mc == t.min_level() and g.D == t.D
+    for m in range(g.mc, g.D + 1):
+        io, jo, ko_, leafo = t.level_cells(m)
+        ig, jg, kg_, leafg = g.level(m)
+        assert np.array_equal(io, ig) and np.array_equal(jo, jg) and np.array_equal(ko_, kg_)
+        assert np.array_equal(leafo, leafg)
+
+
+def test_config_leaf_counts():
+    # c2: 64^3 base with the central ball refined once
+    g = S.Octree(P.c2(64).desc)
+    assert g.n_leaves == 382936
+    assert g.mc == -4 and g.D == 1
+
+
+def test_invalid_descriptions_are_rejected():
+    with pytest.raises(_lib.OcgError) as e:
+        S.Octree(P.OctreeDesc(7, 1))
+    assert e.value.code == _lib.OCG_EINVAL
+    with pytest.raises(_lib.OcgError):
+        S.Octree(P.OctreeDesc(8, 1, P.REFINE_BALL_CENTRE))   # no sphere given
