@@ -168,6 +168,22 @@ typedef struct {
 int ocg_pcg_solve(ocg_hier* h, const double* b_dev, double* x_dev, const ocg_solve_params* prm,
                   ocg_solve_stats* stats, void* stream);
 
+/* Operator apply that allocates nothing (no counterpart in the paper).
+ * For callers that must not allocate device memory at call time, e.g. code running
+ * under a memory budget enforced by an external allocator, a real-time loop that may not
+ * block on cudaMalloc, or a host framework that forbids allocations outside its own
+ * pool.  Computes the same y = A x as ocg_apply_A with dtype OCG_F32 and transpose 0
+ * (float32 x_dev / y_dev, canonical leaf order, caller-owned), but its two work vectors
+ * live in a fixed device array compiled into the library (8 MiB, held by every GPU that
+ * loads the library until the process exits), so at most OCG_NOALLOC_MAX_CELLS cells of
+ * the tree levels 0..D (counts[6] of ocg_octree_counts) are accepted; larger trees get
+ * OCG_EINVAL.  The first call on a device looks up that array's device address (with
+ * that device current); make the first call before any stream capture.  All calls share
+ * the array: calls that overlap on the GPU (other streams, other threads) race and must
+ * be serialised by the caller.  Calls no cudaMalloc / cudaFree. */
+#define OCG_NOALLOC_MAX_CELLS (1 << 20)
+int ocg_apply_A_f32_noalloc(ocg_hier* h, const float* x_dev, float* y_dev, void* stream);
+
 /* Measurement hooks (no counterpart in the paper; used by the benchmark).
  * ocg_probe_set: from now on, bracket every launch of kernel `kind` on level `level`
  * with CUDA events recorded on the launching stream (kind 0 off, 1 red-black sweep,

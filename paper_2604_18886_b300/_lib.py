@@ -16,6 +16,7 @@ OCG_OK, OCG_EINVAL, OCG_ENOMEM, OCG_ECUDA, OCG_ENOTCONV, OCG_ENAN, OCG_ESTATE = 
 OCG_F64, OCG_F32 = 0, 1
 OCG_PREC_FP64, OCG_PREC_FP32, OCG_PREC_MIXED = 0, 1, 2
 OCG_HIST = 128
+OCG_NOALLOC_MAX_CELLS = 1 << 20
 
 
 class OctreeDesc(C.Structure):
@@ -67,6 +68,7 @@ _SIGS = [
     ("ocg_vcycle", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("ocg_pcg_solve", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(SolveParams),
                                 C.POINTER(SolveStats), C.c_void_p]),
+    ("ocg_apply_A_f32_noalloc", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("ocg_probe_set", C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
     ("ocg_probe_read", C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_double),
                                  C.POINTER(C.c_int64)]),

@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <stdexcept>
 #include <string>
 #include <type_traits>
@@ -784,3 +785,52 @@ int ocg_launch_count(int64_t* n) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------
+// Operator apply without allocation: the two internal-layout work vectors (the input
+// scattered to cell order, and the output in cell order) live in this fixed array.
+namespace {
+static __device__ __align__(256) float g_noalloc_scratch[2 * (int64_t)OCG_NOALLOC_MAX_CELLS];
+
+std::mutex g_noalloc_mu;
+float* g_noalloc_ptr[256] = {};   // device address of g_noalloc_scratch per device ordinal
+
+float* noalloc_scratch() {
+    int dev = 0;
+    ck(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev < 0 || dev >= 256) throw Status(OCG_EINVAL, "device ordinal out of range");
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        ck(cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress");
+        g_noalloc_ptr[dev] = (float*)p;
+    }
+    return g_noalloc_ptr[dev];
+}
+}  // namespace
+
+extern "C" int ocg_apply_A_f32_noalloc(ocg_hier* h, const float* x, float* y, void* stream) {
+    return guard([&] {
+        if (!h || !x || !y) throw Status(OCG_EINVAL, "null argument");
+        const ocg_octree* t = h->t;
+        const HostTree& H = t->H;
+        if (!t->on_device) throw Status(OCG_ESTATE, "octree tables are not on the device");
+        if (H.ntree > (int64_t)OCG_NOALLOC_MAX_CELLS)
+            throw Status(OCG_EINVAL, "tree has " + std::to_string(H.ntree) + " cells; the allocation-free apply "
+                                     "accepts at most " + std::to_string((int64_t)OCG_NOALLOC_MAX_CELLS));
+        cudaStream_t st = (cudaStream_t)stream;
+        float* base = noalloc_scratch();
+        float* P = base;
+        float* Y = base + OCG_NOALLOC_MAX_CELLS;
+        // cells that are not leaves are overwritten by child averages before use; clear
+        // anyway so no value of an earlier call can leak into this one
+        ck(cudaMemsetAsync(P, 0, H.ntree * sizeof(float), st), "memset");
+        k_scatter<float, float><<<nblk(H.nleaf), BLK, 0, st>>>(x, P, t->leaf_cell, H.nleaf);
+        ck_launch("scatter");
+        if (h->c64[0]) apply_outer<float, double, double>(t, h->C64(), P, Y, nullptr, st);
+        else apply_outer<float, float, float>(t, h->C32(), P, Y, nullptr, st);
+        k_gather<float, float><<<nblk(H.nleaf), BLK, 0, st>>>(Y, y, t->leaf_cell, H.nleaf);
+        ck_launch("gather");
+        g_launches += 2;
+    });
+}
