@@ -122,7 +122,7 @@ def _setup(dev):
     return p, tree, hier, torch.from_numpy(b).to(dev), np
 
 
-def _time_solves(hier, b, x, steps, precision, flush, stream):
+def _time_solves(hier, b, x, steps, precision, flush, stream, nvtx=False):
     import torch
     times, iters = [], []
     for s in range(steps):
@@ -130,7 +130,11 @@ def _time_solves(hier, b, x, steps, precision, flush, stream):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
+        if nvtx:
+            torch.cuda.nvtx.range_push("timed")
         _, st = hier.solve(b, x, tol=1e-6, precision=precision, stream=stream)
+        if nvtx:
+            torch.cuda.nvtx.range_pop()
         e1.record(stream)
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
@@ -169,7 +173,7 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    times, iters = _time_solves(hier, b, x, args.steps, "mixed", flush, stream)
+    times, iters = _time_solves(hier, b, x, args.steps, "mixed", flush, stream, nvtx=args.nvtx)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     if world > 1:
@@ -315,6 +319,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--nvtx", action="store_true", help="NVTX range 'timed' around the timed mixed solves")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
