@@ -145,12 +145,14 @@ int ocg_apply_A(ocg_hier* h, int32_t dtype, const void* x_dev, void* y_dev, int3
  * (F64 needs coef_dtype OCG_F64; F32 needs OCG_F32); device, canonical leaf order. */
 int ocg_vcycle(ocg_hier* h, int32_t dtype, const void* r_dev, void* z_dev, void* stream);
 
+#define OCG_SOLVE_EAGER 1    /* flags: launch kernel by kernel, test convergence on the host */
+
 typedef struct {
     double tol;              /* stop when ||r||_2 <= tol ||b||_2 (recursive residual) */
-    int32_t max_iter;
+    int32_t max_iter;        /* >= 1 */
     int32_t precision;       /* OCG_PREC_* */
     int32_t nullspace;       /* -1 auto (all walls Neumann), 0 off, 1 zero-mean residual */
-    int32_t reserved;
+    int32_t flags;           /* OCG_SOLVE_* */
 } ocg_solve_params;
 
 #define OCG_HIST 128
@@ -159,12 +161,19 @@ typedef struct {
     int32_t converged;
     double rel_res;          /* last recursive ||r|| / ||b|| */
     double true_rel_res;     /* ||b - A x|| / ||b|| recomputed in FP64 at exit */
+    int64_t kernels;         /* kernel launches this solve executed */
     double hist[OCG_HIST];   /* rel_res after each iteration, hist[0] = 1 */
 } ocg_solve_stats;
 
 /* Solve A x = b (Alg. 1 preconditioned by one mu-cycle per iteration, x0 = 0).  b and x
- * are float64 device vectors in canonical leaf order.  Synchronises once per iteration
- * to test convergence.  Errors: ENOTCONV (stats filled), ENAN, EINVAL, ECUDA. */
+ * are float64 device vectors in canonical leaf order.  By default the loop runs as a
+ * CUDA graph (captured on the first solve of each precision / null-space mode and kept
+ * with the hierarchy) whose iterations sit under a conditional WHILE node: the test
+ * ||r|| <= tol ||b|| is made on the device and the call synchronises once, at the end.
+ * With OCG_SOLVE_EAGER, or while a probe is set, kernels are launched one by one and the
+ * host tests convergence after every iteration.  The true residual is recomputed in FP64
+ * at exit.  A hierarchy serves one solve at a time (its work vectors are shared).
+ * Errors: ENOTCONV (stats filled), ENAN, EINVAL, ECUDA. */
 int ocg_pcg_solve(ocg_hier* h, const double* b_dev, double* x_dev, const ocg_solve_params* prm,
                   ocg_solve_stats* stats, void* stream);
 

@@ -32,14 +32,17 @@ class MGParams(C.Structure):
                 ("coef_dtype", C.c_int32), ("bf16_coarse", C.c_int32)]
 
 
+OCG_SOLVE_EAGER = 1
+
+
 class SolveParams(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("precision", C.c_int32),
-                ("nullspace", C.c_int32), ("reserved", C.c_int32)]
+                ("nullspace", C.c_int32), ("flags", C.c_int32)]
 
 
 class SolveStats(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("converged", C.c_int32), ("rel_res", C.c_double),
-                ("true_rel_res", C.c_double), ("hist", C.c_double * OCG_HIST)]
+                ("true_rel_res", C.c_double), ("kernels", C.c_int64), ("hist", C.c_double * OCG_HIST)]
 
 
 class OcgError(RuntimeError):

@@ -1,9 +1,13 @@
 // libocg: C ABI, hierarchy set-up, the mu-cycle driver and the PCG loop.
 // Every arithmetic step of the solve runs in the kernels of kernels.cuh; this file only
-// allocates device memory, uploads the octree tables and sequences launches on the
-// caller's stream.
+// allocates device memory, uploads the octree tables and sequences launches.  The PCG
+// loop is captured once per (hierarchy, precision, null-space mode) into a CUDA graph
+// whose iterations run under a conditional WHILE node: the convergence test of Alg. 1
+// is evaluated by the reduction kernel that forms ||r||, so a solve needs no host round
+// trip per iteration.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -17,6 +21,7 @@
 
 #include "../../include/ocg.h"
 #include "kernels.cuh"
+#include "octet.cuh"
 #include "octree_host.h"
 
 using namespace ocg;
@@ -105,17 +110,24 @@ struct Probe {
     }
 };
 
-// Launch wrapper: counts launches and brackets the probed kernel with events.
+// Launch context: stream, probe (eager launches only; null while capturing) and a
+// counter of the kernels issued through it.
+struct Ctx {
+    cudaStream_t st;
+    Probe* probe;
+    int64_t count;
+};
+
 template <class F>
-void launch(Probe* pr, int kind, int m, int64_t cells, cudaStream_t st, F&& f) {
-    const bool p = pr && pr->on(kind, m);
+void launch(Ctx& c, int kind, int m, int64_t cells, F&& f) {
+    const bool p = c.probe && c.probe->on(kind, m);
     if (p) {
-        pr->cells = cells;
-        pr->begin(st);
+        c.probe->cells = cells;
+        c.probe->begin(c.st);
     }
     f();
-    ++g_launches;
-    if (p) pr->end(st);
+    ++c.count;
+    if (p) c.probe->end(c.st);
 }
 
 }  // namespace
@@ -146,13 +158,21 @@ struct ocg_octree {
         fdepth = dupload(H.f_depth);
         on_device = true;
     }
-
-    Tables tables() const { return Tables{nbr, oct_parent, child_oct, tK, H.noct, H.nt}; }
-    LevelArgs largs(int m) const { return LevelArgs{H.L(m).off, H.L(m).ncell}; }
+    Tables tables() const { return Tables{nbr, oct_parent, child_oct, tK, (int)H.noct, (int)H.nt}; }
+    LevelArgs largs(int m) const { return LevelArgs{(int)H.L(m).off, (int)H.L(m).ncell}; }
     ~ocg_octree() {
         dfree(nbr); dfree(oct_parent); dfree(child_oct); dfree(tK); dfree(leaf_cell);
         dfree(flags); dfree(level); dfree(fslot); dfree(fkind); dfree(fdepth);
     }
+};
+
+constexpr int NO_TAIL = 1 << 20;   // no level has this index
+
+struct GraphSolve {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int64_t outer_kernels = 0;   // kernels outside the WHILE body
+    int64_t body_kernels = 0;    // kernels per WHILE iteration
 };
 
 struct ocg_hier {
@@ -165,48 +185,98 @@ struct ocg_hier {
     float* c32[4] = {nullptr, nullptr, nullptr, nullptr};
     float* tw32 = nullptr;
     __nv_bfloat16* c16[4] = {nullptr, nullptr, nullptr, nullptr};
-    // work space
+    // work space, allocated once at set-up at the widest type so a captured graph keeps
+    // valid pointers: x, r, p, Ap, bt (b in cell order), xt, yt over the tree cells;
+    // U, B over all cells
+    double *x = nullptr, *r = nullptr, *p = nullptr, *Ap = nullptr, *bt = nullptr, *xt = nullptr, *yt = nullptr;
+    double *U = nullptr, *B = nullptr;
     double* S = nullptr;       // device scalars
     double* hS = nullptr;      // pinned host mirror
     double* part = nullptr;    // block partials
-    int64_t npart = 0;
-    void* vec[8] = {};         // x, r, p, Ap (outer type), U, B (cycle type), xt, yt
-    size_t vec_bytes[8] = {};
+    unsigned* cnt = nullptr;   // reduction arrival counter
     Probe probe;
+    // coarse tail (levels run in one shared-memory CTA), per cycle value type
+    int tail_top[2] = {NO_TAIL, NO_TAIL};  // [float, double]
+    size_t tail_smem[2] = {0, 0};
+    TailArgs tail_args[2];
+    cudaStream_t cap = nullptr;   // private stream for graph capture
+    GraphSolve graphs[3][2];      // [precision][null space]
 
     Coefs<double, double> C64() const { return {c64[0], c64[1], c64[2], c64[3], tw64}; }
     Coefs<float, float> C32() const { return {c32[0], c32[1], c32[2], c32[3], tw32}; }
     Coefs<__nv_bfloat16, float> C16() const { return {c16[0], c16[1], c16[2], c16[3], tw32}; }
 
-    void* vec_of(int i, size_t bytes) {
-        if (vec_bytes[i] < bytes) {
-            dfree(vec[i]);
-            vec[i] = nullptr;
-            vec_bytes[i] = 0;
-            ck(cudaMalloc(&vec[i], bytes), "cudaMalloc work vector");
-            vec_bytes[i] = bytes;
-        }
-        return vec[i];
-    }
     ~ocg_hier() {
+        for (auto& row : graphs)
+            for (auto& gs : row) {
+                if (gs.exec) cudaGraphExecDestroy(gs.exec);
+                if (gs.graph) cudaGraphDestroy(gs.graph);
+            }
+        if (cap) cudaStreamDestroy(cap);
         for (int i = 0; i < 4; ++i) { dfree(c64[i]); dfree(c32[i]); dfree(c16[i]); }
-        dfree(tw64); dfree(tw32); dfree(S); dfree(part);
+        dfree(tw64); dfree(tw32); dfree(S); dfree(part); dfree(cnt);
         if (hS) cudaFreeHost(hS);
-        for (auto& v : vec) dfree(v);
+        for (double* v : {x, r, p, Ap, bt, xt, yt, U, B}) dfree(v);
     }
 };
 
 namespace {
 
+// ------------------------------------------------------------------ coarse tail choice
+// The tail is the longest run of the coarsest levels with m <= 0 (no T faces there)
+// whose shared-memory image (6 values + 1 flag byte per cell, 7 ints per octet) fits.
+size_t tail_bytes(int64_t cells, size_t vbytes) {
+    return (size_t)cells * (6 * vbytes + 1) + (size_t)(cells / 8) * 7 * sizeof(int) + 64;
+}
+
+void choose_tail(ocg_hier* h, int which, size_t vbytes) {
+    const HostTree& H = h->t->H;
+    const size_t budget = 200 * 1024;
+    int top = NO_TAIL;
+    int64_t cells = 0;
+    for (int m = H.mc; m <= std::min(0, H.D); ++m) {
+        const int64_t c = cells + H.L(m).ncell;
+        if (tail_bytes(c, vbytes) > budget || m - H.mc + 1 > MAXLEV) break;
+        cells = c;
+        top = m;
+    }
+    h->tail_top[which] = top;
+    if (top == NO_TAIL) return;
+    TailArgs& A = h->tail_args[which];
+    std::memset(&A, 0, sizeof(A));
+    A.nlev = top - H.mc + 1;
+    int sb = 0;
+    for (int li = 0; li < A.nlev; ++li) {
+        const int m = top - li;
+        A.L[li].off = (int)H.L(m).off;
+        A.L[li].ncell = (int)H.L(m).ncell;
+        A.L[li].sbase = sb;
+        sb += (int)H.L(m).ncell;
+    }
+    A.ncell = sb;
+    A.mu = h->prm.mu;
+    A.nu_pre = h->prm.nu_pre;
+    A.nu_post = h->prm.nu_post;
+    A.nu_coarsest = h->prm.nu_coarsest;
+    h->tail_smem[which] = tail_bytes(sb, vbytes);
+}
+
 // ------------------------------------------------------------------ mu-cycle driver
+template <class CC>
+struct CoefTypes {
+    using TC = std::remove_const_t<std::remove_pointer_t<decltype(CC::d)>>;
+    using TW = std::remove_const_t<std::remove_pointer_t<decltype(CC::tw)>>;
+};
+
 template <class TV>
 struct Cycle {
     ocg_hier* h;
     TV* U;
     TV* B;
-    cudaStream_t st;
+    Ctx& c;
 
     const HostTree& H() const { return h->t->H; }
+    static constexpr int W = std::is_same<TV, double>::value ? 1 : 0;
 
     template <class F>
     void with_coefs(int m, F&& f) {
@@ -219,24 +289,23 @@ struct Cycle {
     }
     void fixb(int m) {
         with_coefs(m, [&](auto C) {
-            using CC = decltype(C);
-            using TC = std::remove_const_t<std::remove_pointer_t<decltype(CC::d)>>;
-            using TW = std::remove_const_t<std::remove_pointer_t<decltype(CC::tw)>>;
+            using TC = typename CoefTypes<decltype(C)>::TC;
+            using TW = typename CoefTypes<decltype(C)>::TW;
             const LevelArgs A = h->t->largs(m);
-            launch(&h->probe, -1, m, A.ncell, st, [&] {
-                k_sweep<TV, TC, TW, MODE_FIXB><<<nblk(A.ncell), BLK, 0, st>>>(A, h->t->tables(), C, U, B, 0);
+            launch(c, -1, m, A.ncell, [&] {
+                k_osweep<TV, TC, TW><<<nblk(A.ncell / 8, OBLK), OBLK, 0, c.st>>>(A, h->t->tables(), C, U, B, 0, 0, 1);
             });
         });
         ck_launch("fixb");
     }
-    void sweep(int m, int colour) {
+    void sweep(int m, int colour, int prolong) {
         with_coefs(m, [&](auto C) {
-            using CC = decltype(C);
-            using TC = std::remove_const_t<std::remove_pointer_t<decltype(CC::d)>>;
-            using TW = std::remove_const_t<std::remove_pointer_t<decltype(CC::tw)>>;
+            using TC = typename CoefTypes<decltype(C)>::TC;
+            using TW = typename CoefTypes<decltype(C)>::TW;
             const LevelArgs A = h->t->largs(m);
-            launch(&h->probe, OCG_PROBE_SWEEP, m, A.ncell, st, [&] {
-                k_sweep<TV, TC, TW, MODE_SWEEP><<<nblk(A.ncell), BLK, 0, st>>>(A, h->t->tables(), C, U, B, colour);
+            launch(c, OCG_PROBE_SWEEP, m, A.ncell, [&] {
+                k_osweep<TV, TC, TW>
+                    <<<nblk(A.ncell / 8, OBLK), OBLK, 0, c.st>>>(A, h->t->tables(), C, U, B, colour, prolong, 0);
             });
         });
         ck_launch("sweep");
@@ -244,215 +313,337 @@ struct Cycle {
     void restrict_(int m) {
         const TV scale = TV(h->prm.beta_restrict / h->prm.alpha);
         with_coefs(m, [&](auto C) {
-            using CC = decltype(C);
-            using TC = std::remove_const_t<std::remove_pointer_t<decltype(CC::d)>>;
-            using TW = std::remove_const_t<std::remove_pointer_t<decltype(CC::tw)>>;
+            using TC = typename CoefTypes<decltype(C)>::TC;
+            using TW = typename CoefTypes<decltype(C)>::TW;
             const LevelArgs A = h->t->largs(m);
-            launch(&h->probe, OCG_PROBE_RESTRICT, m, A.ncell, st, [&] {
-                k_restrict<TV, TC, TW><<<nblk(A.ncell), BLK, 0, st>>>(A, h->t->tables(), C, U, B, scale);
+            launch(c, OCG_PROBE_RESTRICT, m, A.ncell, [&] {
+                k_orestrict<TV, TC, TW><<<nblk(A.ncell / 8, OBLK), OBLK, 0, c.st>>>(A, h->t->tables(), C, U, B, scale);
             });
         });
         ck_launch("restrict");
     }
     void prolong(int m) {
         with_coefs(m, [&](auto C) {
-            using CC = decltype(C);
-            using TC = std::remove_const_t<std::remove_pointer_t<decltype(CC::d)>>;
+            using TC = typename CoefTypes<decltype(C)>::TC;
             const LevelArgs A = h->t->largs(m);
-            launch(&h->probe, OCG_PROBE_PROLONG, m, A.ncell, st, [&] {
-                k_prolong<TV, TC><<<nblk(A.ncell), BLK, 0, st>>>(A, h->t->tables(), C.d, U);
+            launch(c, OCG_PROBE_PROLONG, m, A.ncell, [&] {
+                k_oprolong<TV, TC><<<nblk(A.ncell / 8, OBLK), OBLK, 0, c.st>>>(A, h->t->tables(), C.d, U);
             });
         });
         ck_launch("prolong");
     }
-    void coarsest(int m, bool fas) {
+    void coarsest(int m, bool fas, bool prolong_up) {
         with_coefs(m, [&](auto C) {
-            using CC = decltype(C);
-            using TC = std::remove_const_t<std::remove_pointer_t<decltype(CC::d)>>;
-            using TW = std::remove_const_t<std::remove_pointer_t<decltype(CC::tw)>>;
+            using TC = typename CoefTypes<decltype(C)>::TC;
+            using TW = typename CoefTypes<decltype(C)>::TW;
             const LevelArgs A = h->t->largs(m);
-            int nt = (int)std::min<int64_t>(1024, (A.ncell + 31) / 32 * 32);
-            launch(&h->probe, -1, m, A.ncell, st, [&] {
-                k_coarsest<TV, TC, TW><<<1, nt, 0, st>>>(A, h->t->tables(), C, U, B, h->prm.nu_coarsest, fas ? 1 : 0);
+            const int nt = (int)std::min<int64_t>(1024, (A.ncell + 31) / 32 * 32);
+            launch(c, -1, m, A.ncell, [&] {
+                k_coarsest<TV, TC, TW><<<1, nt, 0, c.st>>>(A, h->t->tables(), C, U, B, h->prm.nu_coarsest,
+                                                          fas ? 1 : 0, prolong_up ? 1 : 0);
             });
         });
         ck_launch("coarsest");
     }
-    // Alg. 4 at level m; `fas` marks the first visit after a restriction from m+1
-    void cycle(int m, bool fas) {
-        if (m == H().mc) {
-            coarsest(m, fas);
-            return;
-        }
-        if (fas) fixb(m);
-        for (int it = 0; it < h->prm.nu_pre; ++it) { sweep(m, 0); sweep(m, 1); }
-        restrict_(m);
-        for (int k = 0; k < h->prm.mu; ++k) cycle(m - 1, k == 0);
-        prolong(m);
-        for (int it = 0; it < h->prm.nu_post; ++it) { sweep(m, 1); sweep(m, 0); }
+    void tail(bool fas, bool prolong_up) {
+        const int m = h->tail_top[W];
+        TailArgs A = h->tail_args[W];
+        A.fas = fas ? 1 : 0;
+        A.prolong = prolong_up ? 1 : 0;
+        const TV scale = TV(h->prm.beta_restrict / h->prm.alpha);
+        const size_t sm = h->tail_smem[W];
+        with_coefs(m, [&](auto C) {
+            using TC = typename CoefTypes<decltype(C)>::TC;
+            using TW = typename CoefTypes<decltype(C)>::TW;
+            ck(cudaFuncSetAttribute(k_tail<TV, TC, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
+               "cudaFuncSetAttribute");
+            const int nt = (int)std::min<int64_t>(1024, (A.L[0].ncell + 31) / 32 * 32);
+            launch(c, -1, m, A.ncell, [&] {
+                k_tail<TV, TC, TW><<<1, nt, sm, c.st>>>(A, h->t->tables(), C, U, B, scale);
+            });
+        });
+        ck_launch("tail");
     }
-    void run() { cycle(H().D, false); }
+    // Alg. 4 at level m.  fas: first visit after a restriction from m+1 (complete the
+    // FAS right-hand side); prolong_up: the last visit, whose final operation prolongs
+    // onto level m+1.
+    void cycle(int m, bool fas, bool prolong_up) {
+        if (m == h->tail_top[W]) { tail(fas, prolong_up); return; }
+        if (m == H().mc) { coarsest(m, fas, prolong_up); return; }
+        if (fas) fixb(m);
+        for (int it = 0; it < h->prm.nu_pre; ++it) { sweep(m, 0, 0); sweep(m, 1, 0); }
+        restrict_(m);
+        for (int k = 0; k < h->prm.mu; ++k) cycle(m - 1, k == 0, k == h->prm.mu - 1);
+        const int np = h->prm.nu_post;
+        for (int it = 0; it < np; ++it) {
+            sweep(m, 1, 0);
+            sweep(m, 0, (it == np - 1 && prolong_up) ? 1 : 0);
+        }
+        if (np == 0 && prolong_up) prolong(m + 1);
+    }
+    void run() { cycle(H().D, false, false); }
 };
 
 // ------------------------------------------------------------------ composite operator
+OMultiLevel tree_levels(const HostTree& H) {
+    OMultiLevel ML{};
+    ML.n = H.D + 1;
+    int b = 0;
+    for (int m = 0; m <= H.D; ++m) {
+        ML.off[m] = (int)H.L(m).off;
+        ML.noct[m] = (int)(H.L(m).ncell / 8);
+        ML.boff[m] = b;
+        b += (int)nblk(H.L(m).ncell / 8, OBLK);
+    }
+    ML.boff[H.D + 1] = b;
+    return ML;
+}
+
+Red make_red(ocg_hier* h, int nb, int op, cudaGraphConditionalHandle cond = 0, int set_cond = 0) {
+    Red R;
+    R.part = h->part;
+    R.cnt = h->cnt;
+    R.S = h->S;
+    R.nb = nb;
+    R.op = op;
+    R.nleaf = (double)h->t->H.nleaf;
+    R.cond = cond;
+    R.set_cond = set_cond;
+    return R;
+}
+
 // Y = A P on the tree cells (P's inner entries are overwritten with child averages);
-// block partials of (p, Ap) go to part (if non-null); returns the number of partials.
+// op = OP_ALPHA also reduces (p, Ap) and forms alpha on the device.
 template <class TO, class TC, class TW>
-int64_t apply_outer(const ocg_octree* t, Coefs<TC, TW> C, TO* P, TO* Y, double* part, cudaStream_t st,
-                    Probe* pr = nullptr) {
+void apply_outer(ocg_hier* h, Coefs<TC, TW> C, TO* P, TO* Y, int op, Ctx& c) {
+    const ocg_octree* t = h->t;
     const HostTree& H = t->H;
     for (int m = H.D; m >= 1; --m) {
         const LevelArgs A = t->largs(m);
-        launch(pr, -1, m, A.ncell, st, [&] { k_avg<TO, TC><<<nblk(A.ncell), BLK, 0, st>>>(A, t->tables(), C.d, P); });
+        launch(c, -1, m, A.ncell, [&] {
+            k_oavg<TO, TC><<<nblk(A.ncell / 8, OBLK), OBLK, 0, c.st>>>(A, t->tables(), C.d, P);
+        });
     }
     ck_launch("avg");
-    int64_t nb = 0;
-    for (int m = 0; m <= H.D; ++m) {
-        const LevelArgs A = t->largs(m);
-        launch(pr, OCG_PROBE_APPLY, m, A.ncell, st, [&] {
-            k_apply<TO, TC, TW><<<nblk(A.ncell), BLK, 0, st>>>(A, t->tables(), C, P, Y, part ? part + nb : nullptr);
-        });
-        nb += nblk(A.ncell);
-    }
+    const OMultiLevel ML = tree_levels(H);
+    const Red R = make_red(h, ML.boff[ML.n], op);
+    launch(c, OCG_PROBE_APPLY, 0, H.ntree, [&] {
+        k_oapply<TO, TC, TW><<<ML.boff[ML.n], OBLK, 0, c.st>>>(ML, t->tables(), C, P, Y, R);
+    });
     ck_launch("apply");
-    return nb;
 }
 
-void finalize(ocg_hier* h, int64_t nb, int op, cudaStream_t st) {
-    k_finalize<<<1, 256, 0, st>>>(h->part, nb, op, h->S, (double)h->t->H.nleaf);
-    ++g_launches;
-    ck_launch("finalize");
+// ------------------------------------------------------------------ PCG (Alg. 1)
+// The loop is split so that a WHILE body holds exactly one iteration:
+//   begin:  r = b; ||b|| (null-space shift); z = M r; rho = (r, z); p = z; half_a
+//   body:   half_b; half_a                    (repeated while not converged)
+//   half_a: Ap = A p, alpha; x += alpha p, r -= alpha Ap; ||r|| test (sets the condition)
+//   half_b: z = M r; beta; p = z + beta p
+//   finish: true residual ||b - A x|| in FP64
+template <class TO, class TV, class TC, class TW>
+struct Pcg {
+    ocg_hier* h;
+    Coefs<TC, TW> Co;
+    bool ns;
+    Ctx& c;
+    cudaGraphConditionalHandle cond;
+    int set_cond;
+
+    const HostTree& H() const { return h->t->H; }
+    TO* x() { return (TO*)h->x; }
+    TO* r() { return (TO*)h->r; }
+    TO* p() { return (TO*)h->p; }
+    TO* Ap() { return (TO*)h->Ap; }
+    TV* U() { return (TV*)h->U; }
+    TV* B() { return (TV*)h->B; }
+    int n() const { return (int)H().ntree; }
+    unsigned gb() const { return nblk(H().ntree); }
+    void zero(void* ptr, size_t bytes) { ck(cudaMemsetAsync(ptr, 0, bytes, c.st), "memset"); }
+
+    void begin() {
+        zero(h->x, n() * sizeof(TO));
+        zero(h->p, n() * sizeof(TO));
+        zero(h->B, H().ncell * sizeof(TV));
+        launch(c, -1, 0, n(), [&] { k_cast<double, TO><<<gb(), BLK, 0, c.st>>>(h->bt, r(), n()); });
+        launch(c, -1, 0, n(), [&] { k_dot<TO, TO><<<gb(), BLK, 0, c.st>>>(r(), r(), n(), make_red(h, gb(), OP_BB)); });
+        launch(c, -1, 0, n(), [&] { k_project<TO, TV><<<gb(), BLK, 0, c.st>>>(r(), h->t->flags, h->S, B(), n()); });
+        ck_launch("begin");
+        precondition();
+        launch(c, -1, 0, n(), [&] { k_dot<TO, TV><<<gb(), BLK, 0, c.st>>>(r(), U(), n(), make_red(h, gb(), OP_RZ0)); });
+        launch(c, -1, 0, n(), [&] { k_pupdate<TO, TV><<<gb(), BLK, 0, c.st>>>(p(), U(), h->S, n(), 1); });
+        ck_launch("begin");
+        half_a();
+    }
+    void precondition() {
+        zero(h->U, H().ntree * sizeof(TV));
+        Cycle<TV>{h, U(), B(), c}.run();
+    }
+    void half_a() {
+        apply_outer<TO, TC, TW>(h, Co, p(), Ap(), OP_ALPHA, c);
+        launch(c, -1, 0, n(), [&] {
+            k_update<TO, TV><<<gb(), BLK, 0, c.st>>>(x(), r(), p(), Ap(), ns ? nullptr : B(), n(),
+                                                     make_red(h, gb(), OP_RR, cond, set_cond));
+        });
+        if (ns)
+            launch(c, -1, 0, n(), [&] { k_project<TO, TV><<<gb(), BLK, 0, c.st>>>(r(), h->t->flags, h->S, B(), n()); });
+        ck_launch("half_a");
+    }
+    void half_b() {
+        precondition();
+        launch(c, -1, 0, n(), [&] { k_dot<TO, TV><<<gb(), BLK, 0, c.st>>>(r(), U(), n(), make_red(h, gb(), OP_BETA)); });
+        launch(c, -1, 0, n(), [&] { k_pupdate<TO, TV><<<gb(), BLK, 0, c.st>>>(p(), U(), h->S, n(), 0); });
+        ck_launch("half_b");
+    }
+    void finish() {
+        launch(c, -1, 0, n(), [&] { k_cast<TO, double><<<gb(), BLK, 0, c.st>>>(x(), h->xt, n()); });
+        apply_outer<double, TC, TW>(h, Co, h->xt, h->yt, OP_NONE, c);
+        launch(c, -1, 0, n(), [&] {
+            k_resid<double><<<gb(), BLK, 0, c.st>>>(h->bt, h->yt, h->t->flags, n(), make_red(h, gb(), OP_TRUE));
+        });
+        ck_launch("finish");
+    }
+};
+
+// Capture begin; WHILE(not converged) { half_b; half_a }; finish into one graph.
+template <class TO, class TV, class TC, class TW>
+void build_graph(ocg_hier* h, Coefs<TC, TW> Co, bool ns, GraphSolve& gs) {
+    if (!h->cap) ck(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking), "cudaStreamCreate");
+    cudaStream_t cs = h->cap;
+    Ctx c{cs, nullptr, 0};
+    ck(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "begin capture");
+    cudaGraph_t g = nullptr;
+    cudaStreamCaptureStatus stt;
+    try {
+        ck(cudaStreamGetCaptureInfo(cs, &stt, nullptr, &g, nullptr, nullptr, nullptr), "capture info");
+        cudaGraphConditionalHandle cond;
+        ck(cudaGraphConditionalHandleCreate(&cond, g, 0, 0), "conditional handle");
+        Pcg<TO, TV, TC, TW> pc{h, Co, ns, c, cond, 1};
+        pc.begin();
+        const cudaGraphNode_t* deps = nullptr;
+        size_t ndeps = 0;
+        ck(cudaStreamGetCaptureInfo(cs, &stt, nullptr, &g, &deps, nullptr, &ndeps), "capture info");
+        cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = cond;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t wnode;
+        ck(cudaGraphAddNode(&wnode, g, deps, nullptr, ndeps, &np), "add WHILE node");
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        ck(cudaStreamUpdateCaptureDependencies(cs, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies),
+           "update capture dependencies");
+        const int64_t before_finish = c.count;
+        pc.finish();
+        gs.outer_kernels = c.count;
+        (void)before_finish;
+        ck(cudaStreamEndCapture(cs, &g), "end capture");
+        // the body: one iteration, captured into the WHILE node's child graph
+        Ctx cb{cs, nullptr, 0};
+        ck(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal),
+           "begin body capture");
+        Pcg<TO, TV, TC, TW> pb{h, Co, ns, cb, cond, 1};
+        pb.half_b();
+        pb.half_a();
+        cudaGraph_t bg = nullptr;
+        ck(cudaStreamEndCapture(cs, &bg), "end body capture");
+        gs.body_kernels = cb.count;
+        ck(cudaGraphInstantiate(&gs.exec, g, 0), "graph instantiate");
+        gs.graph = g;
+    } catch (...) {
+        cudaGraph_t junk = nullptr;
+        cudaStreamEndCapture(cs, &junk);
+        if (junk) cudaGraphDestroy(junk);
+        cudaGetLastError();
+        throw;
+    }
 }
 
 void ensure_work(ocg_hier* h) {
+    if (h->S) return;
     const HostTree& H = h->t->H;
-    if (!h->S) {
-        h->S = dalloc<double>(S_COUNT);
-        ck(cudaMallocHost((void**)&h->hS, S_COUNT * sizeof(double)), "cudaMallocHost");
-    }
-    int64_t need = 2 * (nblk(H.ntree) + (int64_t)(H.D + 1) + 8);
-    if (h->npart < need) {
-        dfree(h->part);
-        h->part = nullptr;
-        h->part = dalloc<double>(need);
-        h->npart = need;
-    }
+    const int64_t n = H.ntree;
+    for (double** v : {&h->x, &h->r, &h->p, &h->Ap, &h->bt, &h->xt, &h->yt}) *v = dalloc<double>(n);
+    h->U = dalloc<double>(H.ncell);
+    h->B = dalloc<double>(H.ncell);
+    h->S = dalloc<double>(S_COUNT);
+    ck(cudaMallocHost((void**)&h->hS, S_COUNT * sizeof(double)), "cudaMallocHost");
+    h->part = dalloc<double>(2 * ((int64_t)nblk(n) + H.D + 8));
+    h->cnt = dalloc<unsigned>(1);
+    ck(cudaMemset(h->cnt, 0, sizeof(unsigned)), "memset");
+    ck(cudaMemset(h->S, 0, S_COUNT * sizeof(double)), "memset");
 }
 
-void fetch_S(ocg_hier* h, cudaStream_t st) {
-    ck(cudaMemcpyAsync(h->hS, h->S, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, st), "copy scalars");
-    ck(cudaStreamSynchronize(st), "stream sync");
-}
-
-// Alg. 1 with x0 = 0, preconditioned by one mu-cycle; TO = Krylov vector type, TV =
-// cycle type, outer operator on coefficients of type TC.
 template <class TO, class TV, class TC, class TW>
-int pcg_run(ocg_hier* h, Coefs<TC, TW> Co, const double* b_user, double* x_user, const ocg_solve_params* sp,
-            ocg_solve_stats* stats, cudaStream_t st) {
+int pcg_solve(ocg_hier* h, Coefs<TC, TW> Co, int prec, const double* b_user, double* x_user,
+              const ocg_solve_params* sp, ocg_solve_stats* stats, cudaStream_t st) {
     const ocg_octree* t = h->t;
     const HostTree& H = t->H;
-    const int64_t n = H.ntree;
-    ensure_work(h);
-    TO* x = (TO*)h->vec_of(0, n * sizeof(TO));
-    TO* r = (TO*)h->vec_of(1, n * sizeof(TO));
-    TO* p = (TO*)h->vec_of(2, n * sizeof(TO));
-    TO* Ap = (TO*)h->vec_of(3, n * sizeof(TO));
-    TV* U = (TV*)h->vec_of(4, H.ncell * sizeof(TV));
-    TV* B = (TV*)h->vec_of(5, H.ncell * sizeof(TV));
     const bool ns = sp->nullspace < 0 ? h->ns_auto : sp->nullspace != 0;
-    ck(cudaMemsetAsync(x, 0, n * sizeof(TO), st), "memset");
-    ck(cudaMemsetAsync(r, 0, n * sizeof(TO), st), "memset");
-    ck(cudaMemsetAsync(p, 0, n * sizeof(TO), st), "memset");
-    ck(cudaMemsetAsync(B, 0, H.ncell * sizeof(TV), st), "memset");
-    ck(cudaMemsetAsync(h->S, 0, S_COUNT * sizeof(double), st), "memset");
-    const double nsv = ns ? 1.0 : 0.0;
-    ck(cudaMemcpyAsync(h->S + S_NS, &nsv, sizeof(double), cudaMemcpyHostToDevice, st), "copy");
-    ++g_launches;
-    k_scatter<double, TO><<<nblk(H.nleaf), BLK, 0, st>>>(b_user, r, t->leaf_cell, H.nleaf);
+    const bool eager = (sp->flags & OCG_SOLVE_EAGER) || h->probe.kind != OCG_PROBE_OFF;
+    // scalars: tolerance, iteration cap, null-space flag, counters
+    std::memset(h->hS, 0, S_COUNT * sizeof(double));
+    h->hS[S_NS] = ns ? 1.0 : 0.0;
+    h->hS[S_TOL] = sp->tol;
+    h->hS[S_MAXIT] = sp->max_iter;
+    Ctx c{st, &h->probe, 0};
+    ck(cudaMemcpyAsync(h->S, h->hS, S_COUNT * sizeof(double), cudaMemcpyHostToDevice, st), "copy scalars");
+    ck(cudaMemsetAsync(h->bt, 0, H.ntree * sizeof(double), st), "memset");
+    launch(c, -1, 0, H.nleaf, [&] {
+        k_scatter<double, double><<<nblk(H.nleaf), BLK, 0, st>>>(b_user, h->bt, t->leaf_cell, (int)H.nleaf);
+    });
     ck_launch("scatter");
-    const unsigned gb = nblk(n);
-    ++g_launches;
-    k_dot<TO, TO><<<gb, BLK, 0, st>>>(r, r, n, h->part);
-    finalize(h, gb, OP_BB, st);
-    TV* bcast = (TV*)B;
-    ++g_launches;
-    k_project<TO, TV><<<gb, BLK, 0, st>>>(r, t->flags, h->S, bcast, n);
-    ck_launch("project");
-    fetch_S(h, st);
-    const double bb = h->hS[S_BB];
-    std::memset(stats, 0, sizeof(*stats));
-    stats->hist[0] = 1.0;
-    if (!(bb > 0.0)) {
-        ck(cudaMemsetAsync(x_user, 0, H.nleaf * sizeof(double), st), "memset");
-        stats->converged = 1;
-        ck(cudaStreamSynchronize(st), "sync");
-        return OCG_OK;
-    }
-    Cycle<TV> cyc{h, U, B, st};
-    ck(cudaMemsetAsync(U, 0, H.ncell * sizeof(TV), st), "memset");
-    cyc.run();
-    ++g_launches;
-    k_dot<TO, TV><<<gb, BLK, 0, st>>>(r, U, n, h->part);
-    finalize(h, gb, OP_RZ0, st);
-    ++g_launches;
-    k_pupdate<TO, TV><<<gb, BLK, 0, st>>>(p, U, h->S, n, 1);
-    ck_launch("pupdate");
-    int k = 0;
-    double rel = 1.0;
-    int status = OCG_ENOTCONV;
-    while (k < sp->max_iter) {
-        const int64_t nb = apply_outer<TO, TC, TW>(t, Co, p, Ap, h->part, st, &h->probe);
-        finalize(h, nb, OP_ALPHA, st);
-        ++g_launches;
-        k_update<TO, TV><<<gb, BLK, 0, st>>>(x, r, p, Ap, h->S, ns ? nullptr : B, n, h->part);
-        ck_launch("update");
-        finalize(h, gb, OP_RR, st);
-        if (ns) {
-            ++g_launches;
-            k_project<TO, TV><<<gb, BLK, 0, st>>>(r, t->flags, h->S, B, n);
-            ck_launch("project");
+    int64_t kernels = c.count;
+    if (eager) {
+        Pcg<TO, TV, TC, TW> pc{h, Co, ns, c, 0, 0};
+        pc.begin();
+        while (true) {
+            ck(cudaMemcpyAsync(h->hS, h->S, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, st), "copy scalars");
+            ck(cudaStreamSynchronize(st), "stream sync");
+            if (h->hS[S_DONE] != 0.0) break;
+            pc.half_b();
+            pc.half_a();
         }
-        fetch_S(h, st);
-        ++k;
-        const double rr = h->hS[S_RR];
-        rel = std::sqrt(std::max(rr, 0.0) / bb);
-        if (k < OCG_HIST) stats->hist[k] = rel;
-        if (!std::isfinite(rel)) { status = OCG_ENAN; break; }
-        if (rel <= sp->tol) { status = OCG_OK; break; }
-        ck(cudaMemsetAsync(U, 0, H.ncell * sizeof(TV), st), "memset");
-        cyc.run();
-        ++g_launches;
-        k_dot<TO, TV><<<gb, BLK, 0, st>>>(r, U, n, h->part);
-        finalize(h, gb, OP_BETA, st);
-        ++g_launches;
-        k_pupdate<TO, TV><<<gb, BLK, 0, st>>>(p, U, h->S, n, 0);
-        ck_launch("pupdate");
+        pc.finish();
+        kernels = c.count;
+    } else {
+        GraphSolve& gs = h->graphs[prec][ns ? 1 : 0];
+        if (!gs.exec) build_graph<TO, TV, TC, TW>(h, Co, ns, gs);
+        ck(cudaGraphLaunch(gs.exec, st), "graph launch");
     }
-    ++g_launches;
-    k_gather<TO, double><<<nblk(H.nleaf), BLK, 0, st>>>(x, x_user, t->leaf_cell, H.nleaf);
+    launch(c, -1, 0, H.nleaf, [&] {
+        k_gather<TO, double><<<nblk(H.nleaf), BLK, 0, st>>>((const TO*)h->x, x_user, t->leaf_cell, (int)H.nleaf);
+    });
     ck_launch("gather");
-    // true residual ||b - A x|| in FP64 (null-space shifted like the recursive one)
-    double* xt = (double*)h->vec_of(6, n * sizeof(double));
-    double* yt = (double*)h->vec_of(7, n * sizeof(double));
-    ck(cudaMemsetAsync(xt, 0, n * sizeof(double), st), "memset");
-    ck(cudaMemsetAsync(yt, 0, n * sizeof(double), st), "memset");
-    ++g_launches;
-    k_scatter<double, double><<<nblk(H.nleaf), BLK, 0, st>>>(x_user, xt, t->leaf_cell, H.nleaf);
-    apply_outer<double, TC, TW>(t, Co, xt, yt, nullptr, st);
-    ck(cudaMemsetAsync(xt, 0, n * sizeof(double), st), "memset");
-    ++g_launches;
-    k_scatter<double, double><<<nblk(H.nleaf), BLK, 0, st>>>(b_user, xt, t->leaf_cell, H.nleaf);
-    ++g_launches;
-    k_resid<double><<<gb, BLK, 0, st>>>(xt, yt, t->flags, n, h->part);
-    finalize(h, gb, OP_RR, st);
-    fetch_S(h, st);
+    ck(cudaMemcpyAsync(h->hS, h->S, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, st), "copy scalars");
+    ck(cudaStreamSynchronize(st), "stream sync");
+    const double* S = h->hS;
+    const int k = (int)S[S_K];
+    if (!eager) {
+        const GraphSolve& gs = h->graphs[prec][ns ? 1 : 0];
+        kernels = c.count + gs.outer_kernels + (int64_t)std::max(k - 1, 0) * gs.body_kernels;
+    } else {
+        kernels = c.count;
+    }
+    g_launches += kernels;
+    std::memset(stats, 0, sizeof(*stats));
+    const double bb = S[S_BB];
     stats->iterations = k;
-    stats->rel_res = rel;
-    stats->converged = status == OCG_OK;
-    stats->true_rel_res = std::sqrt(std::max(h->hS[S_RR], 0.0) / bb);
-    if (status == OCG_ENOTCONV) g_err = "PCG reached max_iter before the tolerance";
-    if (status == OCG_ENAN) g_err = "non-finite residual norm";
-    return status;
+    stats->hist[0] = 1.0;
+    for (int q = 1; q <= k && q < OCG_HIST; ++q) stats->hist[q] = S[S_HIST + q];
+    stats->rel_res = bb > 0.0 ? std::sqrt(std::max(S[S_RR], 0.0) / bb) : 0.0;
+    stats->true_rel_res = bb > 0.0 ? std::sqrt(std::max(S[S_TRUE], 0.0) / bb) : 0.0;
+    stats->kernels = kernels;
+    const bool conv = !(stats->rel_res > sp->tol);
+    stats->converged = conv ? 1 : 0;
+    if (!std::isfinite(stats->rel_res) || !std::isfinite(stats->true_rel_res)) {
+        g_err = "non-finite residual norm";
+        return OCG_ENAN;
+    }
+    if (!conv) {
+        g_err = "PCG reached max_iter before the tolerance";
+        return OCG_ENOTCONV;
+    }
+    return OCG_OK;
 }
 
 }  // namespace
@@ -570,41 +761,43 @@ int ocg_setup_hierarchy(const ocg_octree* t, const float* beta, const int32_t bc
             if (bc[q] == OCG_BC_DIRICHLET) ns = false;
         }
         h->ns_auto = ns;
-        for (int q = 0; q < 4; ++q) h->c64[q] = dalloc<double>(H.ncell);
         const int64_t ntw = 24 * std::max<int64_t>(H.nt, 1);
+        h->c64[0] = dalloc<double>(H.ncell);
         h->tw64 = dalloc<double>(ntw);
-        for (int q = 0; q < 4; ++q) ck(cudaMemsetAsync(h->c64[q], 0, H.ncell * sizeof(double), st), "memset");
-        ck(cudaMemsetAsync(h->tw64, 0, ntw * sizeof(double), st), "memset");
-        // c64[1..3] are contiguous views for the kernels' [3][ncell] indexing: allocate
-        // one block instead
-        double* cm = dalloc<double>(3 * H.ncell);
+        double* cm = dalloc<double>(3 * H.ncell);   // c_x-, c_y-, c_z- as one [3][ncell] block
+        ck(cudaMemsetAsync(h->c64[0], 0, H.ncell * sizeof(double), st), "memset");
         ck(cudaMemsetAsync(cm, 0, 3 * H.ncell * sizeof(double), st), "memset");
+        ck(cudaMemsetAsync(h->tw64, 0, ntw * sizeof(double), st), "memset");
         std::vector<double> hd(H.D + 1);
         for (int d = 0; d <= H.D; ++d) hd[d] = 1.0 / (double)((int64_t)H.n0 << d);
         double* dh = dupload(hd);
         int* derr = dalloc<int>(1);
         ck(cudaMemsetAsync(derr, 0, sizeof(int), st), "memset");
-        k_face_scatter<<<nblk(H.nface), BLK, 0, st>>>(beta, t->fslot, t->fkind, t->fdepth, dh, H.nface, cm,
-                                                     h->tw64, derr);
-        ck_launch("face scatter");
+        if (H.nface > 0) {
+            k_face_scatter<<<nblk(H.nface), BLK, 0, st>>>(beta, t->fslot, t->fkind, t->fdepth, dh, (int)H.nface, cm,
+                                                         h->tw64, derr);
+            ck_launch("face scatter");
+        }
         LevelTab LT{};
         LT.mc = H.mc;
         for (int m = H.mc; m <= H.D; ++m) {
-            LT.off[m - H.mc] = H.L(m).off;
+            LT.off[m - H.mc] = (int)H.L(m).off;
             LT.h[m - H.mc] = H.L(m).h;
         }
         k_leaf_gather<<<nblk(H.nleaf), BLK, 0, st>>>(t->leaf_cell, t->level, t->tables(), LT,
                                                     make_int4(bc[0], bc[1], bc[2], bc[3]), make_int2(bc[4], bc[5]),
-                                                    H.nleaf, H.ncell, h->c64[0], cm, h->tw64);
+                                                    (int)H.nleaf, (int)H.ncell, h->c64[0], cm, h->tw64);
         ck_launch("leaf gather");
         for (int m = H.D; m > H.mc; --m) {
             const LevelArgs A = t->largs(m);
-            k_coarsen<<<nblk(A.ncell / 8), BLK, 0, st>>>(A, t->tables(), prm->alpha, h->c64[0], cm, H.ncell);
+            k_coarsen<<<nblk(A.ncell / 8), BLK, 0, st>>>(A, t->tables(), prm->alpha, h->c64[0], cm, (int)H.ncell);
             ck_launch("coarsen");
         }
-        for (int q = 0; q < 3; ++q)
+        for (int q = 0; q < 3; ++q) {
+            h->c64[q + 1] = dalloc<double>(H.ncell);
             ck(cudaMemcpyAsync(h->c64[q + 1], cm + q * H.ncell, H.ncell * sizeof(double), cudaMemcpyDeviceToDevice, st),
                "copy");
+        }
         int herr = 0;
         ck(cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, st), "copy");
         ck(cudaStreamSynchronize(st), "setup sync");
@@ -627,6 +820,9 @@ int ocg_setup_hierarchy(const ocg_octree* t, const float* beta, const int32_t bc
             dfree(h->tw64);
             h->tw64 = nullptr;
         }
+        ensure_work(h.get());
+        choose_tail(h.get(), 0, sizeof(float));
+        choose_tail(h.get(), 1, sizeof(double));
         *out = h.release();
     });
 }
@@ -664,17 +860,21 @@ int ocg_apply_A(ocg_hier* h, int32_t dtype, const void* x, void* y, int32_t tran
         cudaStream_t st = (cudaStream_t)stream;
         const ocg_octree* t = h->t;
         const HostTree& H = t->H;
+        Ctx c{st, &h->probe, 0};
         auto run = [&](auto* tag, auto C) {
             using TO = std::remove_pointer_t<decltype(tag)>;
-            using CC = decltype(C);
-            using TC = std::remove_const_t<std::remove_pointer_t<decltype(CC::d)>>;
-            using TW = std::remove_const_t<std::remove_pointer_t<decltype(CC::tw)>>;
-            TO* P = (TO*)h->vec_of(6, H.ntree * sizeof(TO));
-            TO* Y = (TO*)h->vec_of(7, H.ntree * sizeof(TO));
+            using TC = typename CoefTypes<decltype(C)>::TC;
+            using TW = typename CoefTypes<decltype(C)>::TW;
+            TO* P = (TO*)h->xt;
+            TO* Y = (TO*)h->yt;
             ck(cudaMemsetAsync(P, 0, H.ntree * sizeof(TO), st), "memset");
-            k_scatter<TO, TO><<<nblk(H.nleaf), BLK, 0, st>>>((const TO*)x, P, t->leaf_cell, H.nleaf);
-            apply_outer<TO, TC, TW>(t, C, P, Y, nullptr, st);
-            k_gather<TO, TO><<<nblk(H.nleaf), BLK, 0, st>>>(Y, (TO*)y, t->leaf_cell, H.nleaf);
+            launch(c, -1, 0, H.nleaf, [&] {
+                k_scatter<TO, TO><<<nblk(H.nleaf), BLK, 0, st>>>((const TO*)x, P, t->leaf_cell, (int)H.nleaf);
+            });
+            apply_outer<TO, TC, TW>(h, C, P, Y, OP_NONE, c);
+            launch(c, -1, 0, H.nleaf, [&] {
+                k_gather<TO, TO><<<nblk(H.nleaf), BLK, 0, st>>>(Y, (TO*)y, t->leaf_cell, (int)H.nleaf);
+            });
             ck_launch("apply_A");
         };
         if (dtype == OCG_F64) {
@@ -686,6 +886,7 @@ int ocg_apply_A(ocg_hier* h, int32_t dtype, const void* x, void* y, int32_t tran
         } else {
             throw Status(OCG_EINVAL, "dtype");
         }
+        g_launches += c.count;
     });
 }
 
@@ -695,16 +896,20 @@ int ocg_vcycle(ocg_hier* h, int32_t dtype, const void* r, void* z, void* stream)
         cudaStream_t st = (cudaStream_t)stream;
         const ocg_octree* t = h->t;
         const HostTree& H = t->H;
+        Ctx c{st, &h->probe, 0};
         auto run = [&](auto* tag) {
             using TV = std::remove_pointer_t<decltype(tag)>;
-            TV* U = (TV*)h->vec_of(4, H.ncell * sizeof(TV));
-            TV* B = (TV*)h->vec_of(5, H.ncell * sizeof(TV));
+            TV* U = (TV*)h->U;
+            TV* B = (TV*)h->B;
             ck(cudaMemsetAsync(U, 0, H.ncell * sizeof(TV), st), "memset");
             ck(cudaMemsetAsync(B, 0, H.ncell * sizeof(TV), st), "memset");
-            k_scatter<TV, TV><<<nblk(H.nleaf), BLK, 0, st>>>((const TV*)r, B, t->leaf_cell, H.nleaf);
-            Cycle<TV> cyc{h, U, B, st};
-            cyc.run();
-            k_gather<TV, TV><<<nblk(H.nleaf), BLK, 0, st>>>(U, (TV*)z, t->leaf_cell, H.nleaf);
+            launch(c, -1, 0, H.nleaf, [&] {
+                k_scatter<TV, TV><<<nblk(H.nleaf), BLK, 0, st>>>((const TV*)r, B, t->leaf_cell, (int)H.nleaf);
+            });
+            Cycle<TV>{h, U, B, c}.run();
+            launch(c, -1, 0, H.nleaf, [&] {
+                k_gather<TV, TV><<<nblk(H.nleaf), BLK, 0, st>>>(U, (TV*)z, t->leaf_cell, (int)H.nleaf);
+            });
             ck_launch("vcycle");
         };
         if (dtype == OCG_F64) {
@@ -716,6 +921,7 @@ int ocg_vcycle(ocg_hier* h, int32_t dtype, const void* r, void* z, void* stream)
         } else {
             throw Status(OCG_EINVAL, "dtype");
         }
+        g_launches += c.count;
     });
 }
 
@@ -724,20 +930,20 @@ int ocg_pcg_solve(ocg_hier* h, const double* b, double* x, const ocg_solve_param
     int status = OCG_OK;
     int g = guard([&] {
         if (!h || !b || !x || !sp || !stats) throw Status(OCG_EINVAL, "null argument");
-        if (!(sp->tol > 0) || sp->max_iter < 0) throw Status(OCG_EINVAL, "tol / max_iter");
+        if (!(sp->tol > 0) || sp->max_iter < 1) throw Status(OCG_EINVAL, "tol must be > 0 and max_iter >= 1");
         cudaStream_t st = (cudaStream_t)stream;
         switch (sp->precision) {
             case OCG_PREC_FP64:
                 if (!h->c64[0]) throw Status(OCG_EINVAL, "FP64 solve needs coef_dtype F64");
-                status = pcg_run<double, double>(h, h->C64(), b, x, sp, stats, st);
+                status = pcg_solve<double, double>(h, h->C64(), 0, b, x, sp, stats, st);
                 break;
             case OCG_PREC_FP32:
                 if (!h->c32[0]) throw Status(OCG_EINVAL, "FP32 solve needs coef_dtype F32");
-                status = pcg_run<float, float>(h, h->C32(), b, x, sp, stats, st);
+                status = pcg_solve<float, float>(h, h->C32(), 1, b, x, sp, stats, st);
                 break;
             case OCG_PREC_MIXED:
                 if (!h->c32[0]) throw Status(OCG_EINVAL, "mixed solve needs coef_dtype F32");
-                status = pcg_run<double, float>(h, h->C32(), b, x, sp, stats, st);
+                status = pcg_solve<double, float>(h, h->C32(), 2, b, x, sp, stats, st);
                 break;
             default:
                 throw Status(OCG_EINVAL, "precision");
@@ -745,10 +951,6 @@ int ocg_pcg_solve(ocg_hier* h, const double* b, double* x, const ocg_solve_param
     });
     return g != OCG_OK ? g : status;
 }
-
-}  // extern "C"
-
-extern "C" {
 
 int ocg_probe_set(ocg_hier* h, int32_t kind, int32_t level) {
     return guard([&] {
@@ -825,12 +1027,17 @@ extern "C" int ocg_apply_A_f32_noalloc(ocg_hier* h, const float* x, float* y, vo
         // cells that are not leaves are overwritten by child averages before use; clear
         // anyway so no value of an earlier call can leak into this one
         ck(cudaMemsetAsync(P, 0, H.ntree * sizeof(float), st), "memset");
-        k_scatter<float, float><<<nblk(H.nleaf), BLK, 0, st>>>(x, P, t->leaf_cell, H.nleaf);
+        Ctx c{st, nullptr, 0};
+        launch(c, -1, 0, H.nleaf, [&] {
+            k_scatter<float, float><<<nblk(H.nleaf), BLK, 0, st>>>(x, P, t->leaf_cell, (int)H.nleaf);
+        });
         ck_launch("scatter");
-        if (h->c64[0]) apply_outer<float, double, double>(t, h->C64(), P, Y, nullptr, st);
-        else apply_outer<float, float, float>(t, h->C32(), P, Y, nullptr, st);
-        k_gather<float, float><<<nblk(H.nleaf), BLK, 0, st>>>(Y, y, t->leaf_cell, H.nleaf);
+        if (h->c64[0]) apply_outer<float, double, double>(h, h->C64(), P, Y, OP_NONE, c);
+        else apply_outer<float, float, float>(h, h->C32(), P, Y, OP_NONE, c);
+        launch(c, -1, 0, H.nleaf, [&] {
+            k_gather<float, float><<<nblk(H.nleaf), BLK, 0, st>>>(Y, y, t->leaf_cell, (int)H.nleaf);
+        });
         ck_launch("gather");
-        g_launches += 2;
+        g_launches += c.count;
     });
 }

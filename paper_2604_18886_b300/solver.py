@@ -163,13 +163,14 @@ class Hierarchy:
         return z
 
     def solve(self, b, x=None, tol=1e-6, max_iter=100, precision="mixed", nullspace=-1,
-              stream=None, raise_on_notconv=True):
+              stream=None, raise_on_notconv=True, eager=False):
         import torch
         assert b.dtype == torch.float64 and b.is_cuda
         if x is None:
             x = torch.empty_like(b)
         sp = L.SolveParams()
         sp.tol, sp.max_iter, sp.precision, sp.nullspace = tol, max_iter, PRECISIONS[precision], nullspace
+        sp.flags = L.OCG_SOLVE_EAGER if eager else 0
         st = L.SolveStats()
         code = L.lib().ocg_pcg_solve(self._h, L.ptr(b), L.ptr(x), C.byref(sp), C.byref(st),
                                      self._stream(stream))

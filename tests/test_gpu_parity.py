@@ -245,3 +245,30 @@ def test_errors_are_reported():
     b = cuda(np.random.default_rng(0).standard_normal(g.n_leaves))
     x, st = gh.solve(b, tol=1e-14, max_iter=2, raise_on_notconv=False)
     assert st.iterations == 2 and not st.converged
+
+
+@pytest.mark.parametrize("mu", [1, 2])
+@pytest.mark.parametrize("precision", ["mixed", "fp32"])
+def test_graph_and_eager_solves_agree(precision, mu):
+    # the CUDA-graph solve (device-side convergence test under a conditional WHILE node)
+    # runs the same kernels in the same order as the kernel-by-kernel solve
+    p = P.c3(16, 2)
+    t, H, g, gh, f, beta = build(p, "f32", mu=mu)
+    b = cuda(P.rhs(p, t.leaves, f, beta))
+    xg, sg = gh.solve(b, tol=1e-7, precision=precision)
+    xe, se = gh.solve(b, tol=1e-7, precision=precision, eager=True)
+    assert sg.iterations == se.iterations and sg.converged and se.converged
+    assert torch.equal(xg, xe)
+    assert [sg.hist[i] for i in range(sg.iterations + 1)] == [se.hist[i] for i in range(se.iterations + 1)]
+    xg2, sg2 = gh.solve(b, tol=1e-7, precision=precision)       # graph replay
+    assert torch.equal(xg, xg2) and sg2.kernels == sg.kernels
+
+
+def test_wcycle_solve_matches_oracle():
+    p = P.c3(16, 2)
+    t, H, g, gh, f, beta = build(p, "f64", mu=2)
+    b = P.rhs(p, t.leaves, f, beta)
+    xo, ko, ho = pcg.pcg(H, b, tol=1e-8, prm=mg.CycleParams(mu=2))
+    x, st = gh.solve(cuda(b), tol=1e-8, precision="fp64")
+    assert st.iterations == ko
+    assert rel(x.cpu().numpy(), xo) <= 1e-9
