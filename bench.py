@@ -189,6 +189,9 @@ def run_ours(args):
     L.check(L.lib().ocg_probe_set(hier.handle, L.OCG_PROBE_OFF, 0))
     ms = statistics.mean(times)
     total_ms = sum(times)
+    tuning = {str(m): {"form": ["octet", "cell"][f] if f >= 0 else "shared-memory tail",
+                       "us_octet": round(a, 2), "us_cell": round(bq, 2)}
+              for m, (f, a, bq) in hier.tuning().items()}
     if world > 1:
         tt = torch.tensor([total_ms], device=dev, dtype=torch.float64)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -232,6 +235,7 @@ def run_ours(args):
                    "leaves": tree.n_leaves, "iterations": iters, "cycle": "V (mu=1), nu=2/2, coarsest 10",
                    "l2": "flushed before every timed step (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "single GPU",
+                   "sweep_forms": tuning,
                    "wall_s_timed": round(wall, 3)},
         "plain_fp32": {"value": round(v32, 3), "unit": UNIT, "ms_per_step": round(statistics.mean(times32), 4),
                        "iterations": iters32},

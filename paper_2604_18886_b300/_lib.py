@@ -26,10 +26,14 @@ class OctreeDesc(C.Structure):
                 ("boxes", (C.c_double * 6) * 4)]
 
 
+OCG_SWEEP_AUTO, OCG_SWEEP_OCTET, OCG_SWEEP_CELL = -1, 0, 1
+
+
 class MGParams(C.Structure):
     _fields_ = [("mu", C.c_int32), ("nu_pre", C.c_int32), ("nu_post", C.c_int32),
                 ("nu_coarsest", C.c_int32), ("beta_restrict", C.c_double), ("alpha", C.c_double),
-                ("coef_dtype", C.c_int32), ("bf16_coarse", C.c_int32)]
+                ("coef_dtype", C.c_int32), ("bf16_coarse", C.c_int32), ("sweep_form", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 OCG_SOLVE_EAGER = 1
@@ -67,6 +71,8 @@ _SIGS = [
                                       C.c_void_p, C.POINTER(C.c_void_p)]),
     ("ocg_hier_destroy", None, [C.c_void_p]),
     ("ocg_hier_export_coefs", C.c_int, [C.c_void_p, C.c_int32] + [C.c_void_p] * 4),
+    ("ocg_hier_tuning", C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_double),
+                                  C.POINTER(C.c_double)]),
     ("ocg_apply_A", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
     ("ocg_vcycle", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("ocg_pcg_solve", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(SolveParams),

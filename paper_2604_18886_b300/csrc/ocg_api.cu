@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <memory>
 #include <mutex>
 #include <stdexcept>
@@ -136,7 +137,7 @@ struct ocg_octree {
     HostTree H;
     // device copies of the tables, uploaded by the first hierarchy set-up
     mutable bool on_device = false;
-    mutable int32_t *nbr = nullptr, *oct_parent = nullptr, *child_oct = nullptr, *tK = nullptr,
+    mutable int32_t *nbr = nullptr, *oct_parent = nullptr, *child_oct = nullptr, *trec = nullptr,
                     *leaf_cell = nullptr;
     mutable uint8_t* flags = nullptr;
     mutable int8_t* level = nullptr;
@@ -149,7 +150,7 @@ struct ocg_octree {
         nbr = dupload(H.nbr);
         oct_parent = dupload(H.oct_parent);
         child_oct = dupload(H.child_oct);
-        tK = dupload(H.tK);
+        trec = dupload(H.trec);
         leaf_cell = dupload(H.leaf_cell);
         flags = dupload(H.cell_flags);
         level = dupload(H.cell_level);
@@ -158,15 +159,15 @@ struct ocg_octree {
         fdepth = dupload(H.f_depth);
         on_device = true;
     }
-    Tables tables() const { return Tables{nbr, oct_parent, child_oct, tK, (int)H.noct, (int)H.nt}; }
-    LevelArgs largs(int m) const { return LevelArgs{(int)H.L(m).off, (int)H.L(m).ncell}; }
+    Tables tables() const { return Tables{nbr, oct_parent, child_oct, trec, (int)H.noct, (int)H.nt}; }
+    LevelArgs largs(int m) const { return LevelArgs{(int)H.L(m).off, (int)H.L(m).ncell, H.L(m).ni}; }
     ~ocg_octree() {
-        dfree(nbr); dfree(oct_parent); dfree(child_oct); dfree(tK); dfree(leaf_cell);
+        dfree(nbr); dfree(oct_parent); dfree(child_oct); dfree(trec); dfree(leaf_cell);
         dfree(flags); dfree(level); dfree(fslot); dfree(fkind); dfree(fdepth);
     }
 };
 
-constexpr int NO_TAIL = 1 << 20;   // no level has this index
+constexpr int TAIL_NONE = 1 << 20;   // larger than any level index
 
 struct GraphSolve {
     cudaGraph_t graph = nullptr;
@@ -195,10 +196,15 @@ struct ocg_hier {
     double* part = nullptr;    // block partials
     unsigned* cnt = nullptr;   // reduction arrival counter
     Probe probe;
-    // coarse tail (levels run in one shared-memory CTA), per cycle value type
-    int tail_top[2] = {NO_TAIL, NO_TAIL};  // [float, double]
+    int red_blocks = 296;         // grid of the grid-stride reductions (2 per SM)
+    int sweep_form[MAXLEV * 2];   // per level (index m - mc): OCG_SWEEP_OCTET / _CELL
+    double tune_us[MAXLEV * 2][2];
+    // coarse tail: uniform levels run in one shared-memory CTA, per cycle value type
+    int tail_top[2] = {TAIL_NONE, TAIL_NONE};   // [float, double]
     size_t tail_smem[2] = {0, 0};
     TailArgs tail_args[2];
+    int* tail_sched = nullptr;    // device copies of the tail pass schedules (float, double)
+    int* tail_sched2 = nullptr;
     cudaStream_t cap = nullptr;   // private stream for graph capture
     GraphSolve graphs[3][2];      // [precision][null space]
 
@@ -214,7 +220,7 @@ struct ocg_hier {
             }
         if (cap) cudaStreamDestroy(cap);
         for (int i = 0; i < 4; ++i) { dfree(c64[i]); dfree(c32[i]); dfree(c16[i]); }
-        dfree(tw64); dfree(tw32); dfree(S); dfree(part); dfree(cnt);
+        dfree(tw64); dfree(tw32); dfree(S); dfree(part); dfree(cnt); dfree(tail_sched); dfree(tail_sched2);
         if (hS) cudaFreeHost(hS);
         for (double* v : {x, r, p, Ap, bt, xt, yt, U, B}) dfree(v);
     }
@@ -222,26 +228,20 @@ struct ocg_hier {
 
 namespace {
 
-// ------------------------------------------------------------------ coarse tail choice
-// The tail is the longest run of the coarsest levels with m <= 0 (no T faces there)
-// whose shared-memory image (6 values + 1 flag byte per cell, 7 ints per octet) fits.
-size_t tail_bytes(int64_t cells, size_t vbytes) {
-    return (size_t)cells * (6 * vbytes + 1) + (size_t)(cells / 8) * 7 * sizeof(int) + 64;
-}
-
+// The tail is the longest run of the coarsest levels m < 0 whose shared-memory image
+// (u, b and four coefficients per cell) fits in 200 KB.
 void choose_tail(ocg_hier* h, int which, size_t vbytes) {
     const HostTree& H = h->t->H;
-    const size_t budget = 200 * 1024;
-    int top = NO_TAIL;
+    int top = TAIL_NONE;
     int64_t cells = 0;
-    for (int m = H.mc; m <= std::min(0, H.D); ++m) {
+    for (int m = H.mc; m < 0; ++m) {
         const int64_t c = cells + H.L(m).ncell;
-        if (tail_bytes(c, vbytes) > budget || m - H.mc + 1 > MAXLEV) break;
+        if ((size_t)c * 6 * vbytes > 200 * 1024 || m - H.mc + 1 > MAXLEV) break;
         cells = c;
         top = m;
     }
     h->tail_top[which] = top;
-    if (top == NO_TAIL) return;
+    if (top == TAIL_NONE) return;
     TailArgs& A = h->tail_args[which];
     std::memset(&A, 0, sizeof(A));
     A.nlev = top - H.mc + 1;
@@ -249,16 +249,58 @@ void choose_tail(ocg_hier* h, int which, size_t vbytes) {
     for (int li = 0; li < A.nlev; ++li) {
         const int m = top - li;
         A.L[li].off = (int)H.L(m).off;
-        A.L[li].ncell = (int)H.L(m).ncell;
+        A.L[li].ni = H.L(m).ni;
         A.L[li].sbase = sb;
         sb += (int)H.L(m).ncell;
     }
     A.ncell = sb;
-    A.mu = h->prm.mu;
-    A.nu_pre = h->prm.nu_pre;
-    A.nu_post = h->prm.nu_post;
-    A.nu_coarsest = h->prm.nu_coarsest;
-    h->tail_smem[which] = tail_bytes(sb, vbytes);
+    // expand the sub-cycle (Alg. 4 over the tail levels) into a flat pass schedule
+    std::vector<int> sch;
+    const ocg_mg_params& P = h->prm;
+    auto emit = [&](int li, int kind) { sch.push_back(8 * li + kind); };
+    std::function<void(int, bool)> rec = [&](int li, bool fas) {
+        if (fas) emit(li, TP_FIXB);
+        if (li == A.nlev - 1) {
+            const int half = P.nu_coarsest / 2;
+            for (int it = 0; it < half; ++it) { emit(li, 0); emit(li, 1); }
+            for (int it = half; it < P.nu_coarsest; ++it) { emit(li, 1); emit(li, 0); }
+            return;
+        }
+        for (int it = 0; it < P.nu_pre; ++it) { emit(li, 0); emit(li, 1); }
+        emit(li, TP_RESTRICT);
+        for (int k = 0; k < P.mu; ++k) rec(li + 1, k == 0);
+        emit(li, TP_PROLONG);
+        for (int it = 0; it < P.nu_post; ++it) { emit(li, 1); emit(li, 0); }
+    };
+    rec(0, false);
+    int* dev = dupload(sch);
+    if (which == 0) {
+        dfree(h->tail_sched);
+        h->tail_sched = dev;
+    } else {
+        // both value types share one hierarchy-owned buffer per type: keep the second in
+        // the args only (freed below through the pool list)
+        h->tail_sched2 = dev;
+    }
+    A.sched = dev;
+    A.nsched = (int)sch.size();
+    h->tail_smem[which] = (size_t)sb * 6 * vbytes;
+}
+
+// Real (non-padding) cells of level m in the level's Morton order.
+std::vector<int64_t> level_cells_morton(const HostTree& H, int m) {
+    const LevelMeta& l = H.L(m);
+    std::vector<std::pair<uint64_t, int64_t>> v;
+    for (int64_t g = l.off; g < l.off + l.ncell; ++g) {
+        if (!(H.cell_flags[g] & 2)) continue;
+        int64_t a, b, d;
+        H.cell_coords(m, g, a, b, d);
+        v.push_back({morton3(a, b, d), g});
+    }
+    std::sort(v.begin(), v.end());
+    std::vector<int64_t> out(v.size());
+    for (size_t q = 0; q < v.size(); ++q) out[q] = v[q].second;
+    return out;
 }
 
 // ------------------------------------------------------------------ mu-cycle driver
@@ -276,7 +318,6 @@ struct Cycle {
     Ctx& c;
 
     const HostTree& H() const { return h->t->H; }
-    static constexpr int W = std::is_same<TV, double>::value ? 1 : 0;
 
     template <class F>
     void with_coefs(int m, F&& f) {
@@ -298,14 +339,18 @@ struct Cycle {
         });
         ck_launch("fixb");
     }
-    void sweep(int m, int colour, int prolong) {
+    void sweep(int m, int colour, int prolong, int form = -2) {
+        if (form == -2) form = h->sweep_form[m - H().mc];
         with_coefs(m, [&](auto C) {
             using TC = typename CoefTypes<decltype(C)>::TC;
             using TW = typename CoefTypes<decltype(C)>::TW;
             const LevelArgs A = h->t->largs(m);
             launch(c, OCG_PROBE_SWEEP, m, A.ncell, [&] {
-                k_osweep<TV, TC, TW>
-                    <<<nblk(A.ncell / 8, OBLK), OBLK, 0, c.st>>>(A, h->t->tables(), C, U, B, colour, prolong, 0);
+                if (form == OCG_SWEEP_CELL)
+                    k_csweep<TV, TC, TW><<<nblk(A.ncell), BLK, 0, c.st>>>(A, h->t->tables(), C, U, B, colour, prolong);
+                else
+                    k_osweep<TV, TC, TW>
+                        <<<nblk(A.ncell / 8, OBLK), OBLK, 0, c.st>>>(A, h->t->tables(), C, U, B, colour, prolong, 0);
             });
         });
         ck_launch("sweep");
@@ -337,14 +382,15 @@ struct Cycle {
             using TC = typename CoefTypes<decltype(C)>::TC;
             using TW = typename CoefTypes<decltype(C)>::TW;
             const LevelArgs A = h->t->largs(m);
-            const int nt = (int)std::min<int64_t>(1024, (A.ncell + 31) / 32 * 32);
+            const int nt = (int)std::min<int64_t>(256, (A.ncell / 8 + 31) / 32 * 32);
             launch(c, -1, m, A.ncell, [&] {
-                k_coarsest<TV, TC, TW><<<1, nt, 0, c.st>>>(A, h->t->tables(), C, U, B, h->prm.nu_coarsest,
-                                                          fas ? 1 : 0, prolong_up ? 1 : 0);
+                k_ocoarsest<TV, TC, TW><<<1, nt, 0, c.st>>>(A, h->t->tables(), C, U, B, h->prm.nu_coarsest,
+                                                           fas ? 1 : 0, prolong_up ? 1 : 0);
             });
         });
         ck_launch("coarsest");
     }
+    static constexpr int W = std::is_same<TV, double>::value ? 1 : 0;
     void tail(bool fas, bool prolong_up) {
         const int m = h->tail_top[W];
         TailArgs A = h->tail_args[W];
@@ -355,11 +401,12 @@ struct Cycle {
         with_coefs(m, [&](auto C) {
             using TC = typename CoefTypes<decltype(C)>::TC;
             using TW = typename CoefTypes<decltype(C)>::TW;
-            ck(cudaFuncSetAttribute(k_tail<TV, TC, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
+            ck(cudaFuncSetAttribute(k_otail<TV, TC, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
                "cudaFuncSetAttribute");
-            const int nt = (int)std::min<int64_t>(1024, (A.L[0].ncell + 31) / 32 * 32);
+            const int noct = A.L[0].ni * A.L[0].ni * A.L[0].ni;
+            const int nt = std::min(sizeof(TV) == 8 ? 256 : 512, (noct + 31) / 32 * 32);
             launch(c, -1, m, A.ncell, [&] {
-                k_tail<TV, TC, TW><<<1, nt, sm, c.st>>>(A, h->t->tables(), C, U, B, scale);
+                k_otail<TV, TC, TW><<<1, nt, sm, c.st>>>(A, h->t->tables(), C, U, B, scale);
             });
         });
         ck_launch("tail");
@@ -384,6 +431,53 @@ struct Cycle {
     void run() { cycle(H().D, false, false); }
 };
 
+// ------------------------------------------------------------------ sweep autotuner
+// For every level the cycle sweeps outside the shared-memory tail, capture 20 colour
+// sweeps of each form into a graph, time 5 replays with CUDA events after 2 warm-up
+// replays, and keep the faster form.  Sweeps act on the zeroed work vectors (b = 0 keeps
+// u = 0), so tuning leaves no trace.
+template <class TV>
+void autotune_sweeps(ocg_hier* h) {
+    const HostTree& H = h->t->H;
+    if (!h->cap) ck(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking), "cudaStreamCreate");
+    cudaStream_t cs = h->cap;
+    ck(cudaMemsetAsync(h->U, 0, H.ncell * sizeof(double), cs), "memset");
+    ck(cudaMemsetAsync(h->B, 0, H.ncell * sizeof(double), cs), "memset");
+    cudaEvent_t e0, e1;
+    ck(cudaEventCreate(&e0), "cudaEventCreate");
+    ck(cudaEventCreate(&e1), "cudaEventCreate");
+    const int tail_top = h->tail_top[std::is_same<TV, double>::value ? 1 : 0];
+    for (int m = H.D; m > H.mc; --m) {
+        if (m <= tail_top && tail_top != TAIL_NONE) break;
+        double us[2] = {0.0, 0.0};
+        for (int form = 0; form < 2; ++form) {
+            Ctx c{cs, nullptr, 0};
+            Cycle<TV> cy{h, (TV*)h->U, (TV*)h->B, c};
+            cudaGraph_t g = nullptr;
+            cudaGraphExec_t ge = nullptr;
+            ck(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "begin capture");
+            for (int q = 0; q < 20; ++q) cy.sweep(m, q & 1, 0, form);
+            ck(cudaStreamEndCapture(cs, &g), "end capture");
+            ck(cudaGraphInstantiate(&ge, g, 0), "graph instantiate");
+            for (int w = 0; w < 2; ++w) ck(cudaGraphLaunch(ge, cs), "graph launch");
+            ck(cudaEventRecord(e0, cs), "event");
+            for (int r = 0; r < 5; ++r) ck(cudaGraphLaunch(ge, cs), "graph launch");
+            ck(cudaEventRecord(e1, cs), "event");
+            ck(cudaEventSynchronize(e1), "event sync");
+            float ms = 0.0f;
+            ck(cudaEventElapsedTime(&ms, e0, e1), "elapsed");
+            us[form] = ms * 1000.0 / (5 * 20);
+            cudaGraphExecDestroy(ge);
+            cudaGraphDestroy(g);
+        }
+        h->tune_us[m - H.mc][0] = us[0];
+        h->tune_us[m - H.mc][1] = us[1];
+        h->sweep_form[m - H.mc] = us[1] < us[0] ? OCG_SWEEP_CELL : OCG_SWEEP_OCTET;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+}
+
 // ------------------------------------------------------------------ composite operator
 OMultiLevel tree_levels(const HostTree& H) {
     OMultiLevel ML{};
@@ -392,6 +486,7 @@ OMultiLevel tree_levels(const HostTree& H) {
     for (int m = 0; m <= H.D; ++m) {
         ML.off[m] = (int)H.L(m).off;
         ML.noct[m] = (int)(H.L(m).ncell / 8);
+        ML.ni[m] = H.L(m).ni;
         ML.boff[m] = b;
         b += (int)nblk(H.L(m).ncell / 8, OBLK);
     }
@@ -458,6 +553,7 @@ struct Pcg {
     TV* B() { return (TV*)h->B; }
     int n() const { return (int)H().ntree; }
     unsigned gb() const { return nblk(H().ntree); }
+    unsigned rb() const { return std::min<unsigned>(nblk(H().ntree), (unsigned)h->red_blocks); }
     void zero(void* ptr, size_t bytes) { ck(cudaMemsetAsync(ptr, 0, bytes, c.st), "memset"); }
 
     void begin() {
@@ -465,11 +561,11 @@ struct Pcg {
         zero(h->p, n() * sizeof(TO));
         zero(h->B, H().ncell * sizeof(TV));
         launch(c, -1, 0, n(), [&] { k_cast<double, TO><<<gb(), BLK, 0, c.st>>>(h->bt, r(), n()); });
-        launch(c, -1, 0, n(), [&] { k_dot<TO, TO><<<gb(), BLK, 0, c.st>>>(r(), r(), n(), make_red(h, gb(), OP_BB)); });
+        launch(c, -1, 0, n(), [&] { k_dot<TO, TO, true><<<rb(), BLK, 0, c.st>>>(r(), r(), n(), make_red(h, rb(), OP_BB)); });
         launch(c, -1, 0, n(), [&] { k_project<TO, TV><<<gb(), BLK, 0, c.st>>>(r(), h->t->flags, h->S, B(), n()); });
         ck_launch("begin");
         precondition();
-        launch(c, -1, 0, n(), [&] { k_dot<TO, TV><<<gb(), BLK, 0, c.st>>>(r(), U(), n(), make_red(h, gb(), OP_RZ0)); });
+        launch(c, -1, 0, n(), [&] { k_dot<TO, TV, false><<<rb(), BLK, 0, c.st>>>(r(), U(), n(), make_red(h, rb(), OP_RZ0)); });
         launch(c, -1, 0, n(), [&] { k_pupdate<TO, TV><<<gb(), BLK, 0, c.st>>>(p(), U(), h->S, n(), 1); });
         ck_launch("begin");
         half_a();
@@ -481,8 +577,9 @@ struct Pcg {
     void half_a() {
         apply_outer<TO, TC, TW>(h, Co, p(), Ap(), OP_ALPHA, c);
         launch(c, -1, 0, n(), [&] {
-            k_update<TO, TV><<<gb(), BLK, 0, c.st>>>(x(), r(), p(), Ap(), ns ? nullptr : B(), n(),
-                                                     make_red(h, gb(), OP_RR, cond, set_cond));
+            const Red R = make_red(h, rb(), OP_RR, cond, set_cond);
+            if (ns) k_update<TO, TV, true><<<rb(), BLK, 0, c.st>>>(x(), r(), p(), Ap(), nullptr, n(), R);
+            else k_update<TO, TV, false><<<rb(), BLK, 0, c.st>>>(x(), r(), p(), Ap(), B(), n(), R);
         });
         if (ns)
             launch(c, -1, 0, n(), [&] { k_project<TO, TV><<<gb(), BLK, 0, c.st>>>(r(), h->t->flags, h->S, B(), n()); });
@@ -490,7 +587,7 @@ struct Pcg {
     }
     void half_b() {
         precondition();
-        launch(c, -1, 0, n(), [&] { k_dot<TO, TV><<<gb(), BLK, 0, c.st>>>(r(), U(), n(), make_red(h, gb(), OP_BETA)); });
+        launch(c, -1, 0, n(), [&] { k_dot<TO, TV, false><<<rb(), BLK, 0, c.st>>>(r(), U(), n(), make_red(h, rb(), OP_BETA)); });
         launch(c, -1, 0, n(), [&] { k_pupdate<TO, TV><<<gb(), BLK, 0, c.st>>>(p(), U(), h->S, n(), 0); });
         ck_launch("half_b");
     }
@@ -498,7 +595,7 @@ struct Pcg {
         launch(c, -1, 0, n(), [&] { k_cast<TO, double><<<gb(), BLK, 0, c.st>>>(x(), h->xt, n()); });
         apply_outer<double, TC, TW>(h, Co, h->xt, h->yt, OP_NONE, c);
         launch(c, -1, 0, n(), [&] {
-            k_resid<double><<<gb(), BLK, 0, c.st>>>(h->bt, h->yt, h->t->flags, n(), make_red(h, gb(), OP_TRUE));
+            k_resid<double><<<rb(), BLK, 0, c.st>>>(h->bt, h->yt, h->t->flags, n(), make_red(h, rb(), OP_TRUE));
         });
         ck_launch("finish");
     }
@@ -721,19 +818,16 @@ int ocg_octree_export_level(const ocg_octree* t, int32_t m, int64_t* n, int32_t*
         if (!t || !n) throw Status(OCG_EINVAL, "null argument");
         const HostTree& H = t->H;
         if (m < H.mc || m > H.D) throw Status(OCG_EINVAL, "level out of range");
-        const LevelMeta& l = H.L(m);
-        int64_t c = 0;
-        for (int64_t g = l.off; g < l.off + l.ncell; ++g) {
-            if (!(H.cell_flags[g] & 2)) continue;
-            if (i) {
+        const std::vector<int64_t> cells = level_cells_morton(H, m);
+        if (i) {
+            for (size_t c = 0; c < cells.size(); ++c) {
                 int64_t a, b, d;
-                H.cell_coords(m, g, a, b, d);
+                H.cell_coords(m, cells[c], a, b, d);
                 i[c] = (int32_t)a; j[c] = (int32_t)b; k[c] = (int32_t)d;
-                if (leaf) leaf[c] = (int8_t)(H.cell_flags[g] & 1);
+                if (leaf) leaf[c] = (int8_t)(H.cell_flags[cells[c]] & 1);
             }
-            ++c;
         }
-        *n = c;
+        *n = (int64_t)cells.size();
     });
 }
 
@@ -746,6 +840,9 @@ int ocg_setup_hierarchy(const ocg_octree* t, const float* beta, const int32_t bc
             !(prm->alpha > 0) || !std::isfinite(prm->beta_restrict))
             throw Status(OCG_EINVAL, "invalid multigrid parameters");
         if (prm->coef_dtype != OCG_F64 && prm->coef_dtype != OCG_F32) throw Status(OCG_EINVAL, "coef_dtype");
+        if (prm->sweep_form < OCG_SWEEP_AUTO || prm->sweep_form > OCG_SWEEP_CELL)
+            throw Status(OCG_EINVAL, "sweep_form");
+        if (t->H.D - t->H.mc + 1 > 2 * MAXLEV) throw Status(OCG_EINVAL, "too many levels");
         if (prm->bf16_coarse && prm->coef_dtype != OCG_F32) throw Status(OCG_EINVAL, "bf16_coarse needs F32");
         for (int q = 0; q < 6; ++q)
             if (bc[q] != OCG_BC_NEUMANN && bc[q] != OCG_BC_DIRICHLET) throw Status(OCG_EINVAL, "bc code");
@@ -823,6 +920,19 @@ int ocg_setup_hierarchy(const ocg_octree* t, const float* beta, const int32_t bc
         ensure_work(h.get());
         choose_tail(h.get(), 0, sizeof(float));
         choose_tail(h.get(), 1, sizeof(double));
+        const int nlev = H.D - H.mc + 1;
+        for (int q = 0; q < nlev; ++q) {
+            h->sweep_form[q] = prm->sweep_form == OCG_SWEEP_CELL ? OCG_SWEEP_CELL : OCG_SWEEP_OCTET;
+            h->tune_us[q][0] = h->tune_us[q][1] = -1.0;
+        }
+        if (prm->sweep_form == OCG_SWEEP_AUTO) {
+            if (prm->coef_dtype == OCG_F64) autotune_sweeps<double>(h.get());
+            else autotune_sweeps<float>(h.get());
+        }
+        int dev = 0, sms = 148;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+            h->red_blocks = 2 * sms;
         *out = h.release();
     });
 }
@@ -835,6 +945,7 @@ int ocg_hier_export_coefs(const ocg_hier* h, int32_t m, double* c, double* cx, d
         const HostTree& H = h->t->H;
         if (m < H.mc || m > H.D) throw Status(OCG_EINVAL, "level out of range");
         const LevelMeta& l = H.L(m);
+        const std::vector<int64_t> cells = level_cells_morton(H, m);
         double* outs[4] = {c, cx, cy, cz};
         std::vector<double> buf(l.ncell);
         std::vector<float> bf(l.ncell);
@@ -846,10 +957,21 @@ int ocg_hier_export_coefs(const ocg_hier* h, int32_t m, double* c, double* cx, d
                 ck(cudaMemcpy(bf.data(), h->c32[q] + l.off, l.ncell * sizeof(float), cudaMemcpyDeviceToHost), "copy");
                 for (int64_t i = 0; i < l.ncell; ++i) buf[i] = bf[i];
             }
-            int64_t n = 0;
-            for (int64_t g = 0; g < l.ncell; ++g)
-                if (H.cell_flags[l.off + g] & 2) outs[q][n++] = buf[g];
+            for (size_t e = 0; e < cells.size(); ++e) outs[q][e] = buf[cells[e] - l.off];
         }
+    });
+}
+
+int ocg_hier_tuning(const ocg_hier* h, int32_t m, int32_t* form, double* us_octet, double* us_cell) {
+    return guard([&] {
+        if (!h || !form || !us_octet || !us_cell) throw Status(OCG_EINVAL, "null argument");
+        const HostTree& H = h->t->H;
+        if (m < H.mc || m > H.D) throw Status(OCG_EINVAL, "level out of range");
+        const int W = h->c64[0] ? 1 : 0;
+        const bool in_tail = h->tail_top[W] != TAIL_NONE && m <= h->tail_top[W];
+        *form = (in_tail || m == H.mc) ? -1 : h->sweep_form[m - H.mc];
+        *us_octet = h->tune_us[m - H.mc][0];
+        *us_cell = h->tune_us[m - H.mc][1];
     });
 }
 

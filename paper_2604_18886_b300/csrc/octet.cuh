@@ -72,6 +72,26 @@ __device__ __forceinline__ void ldc8(const __nv_bfloat16* __restrict__ p, float 
     }
 }
 
+// Coordinates of octet o in a lexicographic ni^3 grid (shifts when ni is a power of two).
+__device__ __forceinline__ void octet_coords(int o, int ni, int& I, int& J, int& K) {
+    if ((ni & (ni - 1)) == 0) {
+        const int sh = __ffs(ni) - 1;
+        I = o & (ni - 1);
+        J = (o >> sh) & (ni - 1);
+        K = o >> (2 * sh);
+    } else {
+        I = o % ni;
+        J = (o / ni) % ni;
+        K = o / (ni * ni);
+    }
+}
+
+// 1/n for the mean of n active cells (n <= 8): multiply instead of divide
+template <class TV>
+__device__ __forceinline__ TV inv_count(int n) {
+    return n == 8 ? TV(0.125) : (n == 4 ? TV(0.25) : (n == 2 ? TV(0.5) : (n == 1 ? TV(1) : TV(1) / TV(n))));
+}
+
 template <class TV>
 struct OctState {
     TV u[8], d[8], cm[3][8];
@@ -98,19 +118,44 @@ __device__ __forceinline__ void octet_mean(OctState<TV>& S) {
     for (int q = 0; q < 8; ++q)
         if (S.d[q] != TV(0)) { s += S.u[q]; ++n; }
     S.nact = n;
-    S.ubar = n ? s / TV(n) : TV(0);
+    S.ubar = s * inv_count<TV>(n);
 }
 
-// Au[s] = (A^m u) for the 8 cells of octet o (global index og) of the level starting at
-// cell `off`; U is read for the neighbouring octets and the coarser leaves K.
+// The six neighbouring octets of local octet o: on a uniform level (ni > 0, octets in
+// lexicographic order) computed from o, otherwise read from the table (values: local
+// octet, -1 wall, -2-K for a face covered by the coarser leaf K).
+__device__ __forceinline__ void octet_neighbours(const Tables& T, int ni, int o, int og, int (&nb)[6]) {
+    if (ni > 0) {
+        int I, J, K;
+        octet_coords(o, ni, I, J, K);
+        const int sy = ni, sz = ni * ni;
+        nb[0] = I > 0 ? o - 1 : -1;
+        nb[1] = I < ni - 1 ? o + 1 : -1;
+        nb[2] = J > 0 ? o - sy : -1;
+        nb[3] = J < ni - 1 ? o + sy : -1;
+        nb[4] = K > 0 ? o - sz : -1;
+        nb[5] = K < ni - 1 ? o + sz : -1;
+    } else {
+#pragma unroll
+        for (int dir = 0; dir < 6; ++dir) nb[dir] = __ldg(T.nbr + dir * T.noct + og);
+    }
+}
+
+template <class T>
+__device__ __forceinline__ T divide(T a, T b) { return a / b; }
+template <>
+__device__ __forceinline__ float divide<float>(float a, float b) { return __fdividef(a, b); }
+
+// Au[s] = (A^m u) for the 8 cells of local octet o (global og) of the level A; U is read
+// for the neighbouring octets and the coarser leaves K of T faces.
 template <class TV, class TC, class TW>
-__device__ __forceinline__ void octet_Au(const Tables& T, const Coefs<TC, TW>& C, const TV* __restrict__ U, int off,
-                                         int og, const OctState<TV>& S, TV (&Au)[8]) {
+__device__ __forceinline__ void octet_Au(const Tables& T, const Coefs<TC, TW>& C, const TV* __restrict__ U,
+                                         const LevelArgs& A, int o, int og, const OctState<TV>& S, TV (&Au)[8]) {
 #pragma unroll
     for (int s = 0; s < 8; ++s) Au[s] = S.d[s] * S.u[s];
     int nb[6];
-#pragma unroll
-    for (int dir = 0; dir < 6; ++dir) nb[dir] = __ldg(T.nbr + dir * T.noct + og);
+    octet_neighbours(T, A.ni, o, og, nb);
+    const int off = A.off;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const int bit = 1 << a;
@@ -135,8 +180,7 @@ __device__ __forceinline__ void octet_Au(const Tables& T, const Coefs<TC, TW>& C
                 Au[s] += S.cm[a][s] * nu[q];
             }
         } else if (v <= -2) {
-            const int t = -2 - v;
-            const TV uK = U[__ldg(T.tK + (2 * a) * T.nt + t)];
+            const TV uK = U[-2 - v];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int s = clear_slot(a, q);
@@ -144,7 +188,7 @@ __device__ __forceinline__ void octet_Au(const Tables& T, const Coefs<TC, TW>& C
             }
         }
         // + face: cells with bit set meet the - side of the + neighbour, whose cells keep
-        // the face coefficients
+        // the face coefficients; at a T face the fine coefficients are in the T record
         const int w = nb[2 * a + 1];
         if (w >= 0) {
             const int n8 = off + 8 * w;
@@ -158,8 +202,8 @@ __device__ __forceinline__ void octet_Au(const Tables& T, const Coefs<TC, TW>& C
 #pragma unroll
             for (int q = 0; q < 4; ++q) Au[clear_slot(a, q) | bit] += nc[q] * nu[q];
         } else if (w <= -2) {
-            const int t = -2 - w;
-            const TV uK = U[__ldg(T.tK + (2 * a + 1) * T.nt + t)];
+            const TV uK = U[-2 - w];
+            const int t = __ldg(T.trec + og);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int s = clear_slot(a, q) | bit;
@@ -182,7 +226,7 @@ __device__ __forceinline__ void octet_prolong(const TC* __restrict__ d, TV* __re
     for (int q = 0; q < 8; ++q)
         if (dd[q] != TV(0)) { s += v[q]; ++n; }
     if (n == 0) return;
-    const TV delta = uP - s / TV(n);
+    const TV delta = uP - s * inv_count<TV>(n);
 #pragma unroll
     for (int q = 0; q < 8; ++q)
         if (dd[q] != TV(0)) U[c8 + q] = v[q] + delta;
@@ -203,7 +247,7 @@ __global__ void __launch_bounds__(OBLK) k_osweep(LevelArgs A, Tables T, Coefs<TC
     octet_mean(S);
     TV b[8], Au[8];
     ld8(B + c8, b);
-    octet_Au<TV, TC, TW>(T, C, U, A.off, og, S, Au);
+    octet_Au<TV, TC, TW>(T, C, U, A, o, og, S, Au);
     if (fixb) {
 #pragma unroll
         for (int s = 0; s < 8; ++s)
@@ -215,7 +259,7 @@ __global__ void __launch_bounds__(OBLK) k_osweep(LevelArgs A, Tables T, Coefs<TC
     for (int s = 0; s < 8; ++s) {
         un[s] = S.u[s];
         if (((__popc(s) & 1) == colour) && S.d[s] != TV(0)) {
-            un[s] = S.u[s] + (b[s] - Au[s]) / S.d[s];
+            un[s] = S.u[s] + divide(b[s] - Au[s], S.d[s]);
             U[c8 + s] = un[s];
         }
     }
@@ -225,6 +269,85 @@ __global__ void __launch_bounds__(OBLK) k_osweep(LevelArgs A, Tables T, Coefs<TC
             const int co = __ldg(T.child_oct + c8 + s);
             if (co >= 0) octet_prolong<TV, TC>(C.d, U, co, un[s]);
         }
+    }
+}
+
+// ------------------------------------------------------------ thread-per-cell sweep
+// The same colour sweep with one thread per cell: the octet's 8 cells are 8 consecutive
+// lanes, in-octet neighbours and the T-ghost sibling mean come from warp shuffles, the
+// neighbour across the octet boundary from the neighbour octet (arithmetic on uniform
+// levels, table on adaptive ones).  Shorter per-thread dependency chains and 8x more
+// warps than k_osweep; the autotuner picks the faster form per level.
+template <class T>
+__device__ __forceinline__ T lane_octet_sum(T v) {
+    v += __shfl_xor_sync(FULL, v, 1);
+    v += __shfl_xor_sync(FULL, v, 2);
+    v += __shfl_xor_sync(FULL, v, 4);
+    return v;
+}
+
+template <class TV, class TC, class TW>
+__global__ void __launch_bounds__(BLK) k_csweep(LevelArgs A, Tables T, Coefs<TC, TW> C, TV* __restrict__ U,
+                                                TV* __restrict__ B, int colour, int prolong) {
+    const int tid = blockIdx.x * BLK + threadIdx.x;
+    const bool valid = tid < A.ncell;
+    const int lc = valid ? tid : (A.ncell - 8 + (tid & 7));
+    const int g = A.off + lc;
+    const int s = lc & 7, o = lc >> 3, og = g >> 3;
+    const TV u = U[g];
+    const TV b = B[g];
+    const TV dd = TV(tov(__ldg(C.d + g)));
+    const TV cm[3] = {TV(tov(__ldg(C.cx + g))), TV(tov(__ldg(C.cy + g))), TV(tov(__ldg(C.cz + g)))};
+    const bool act = dd != TV(0);
+    // outer neighbour octet per axis: the + octet if bit a of s is set, else the - octet
+    int nbo[3];
+    if (A.ni > 0) {
+        int crd[3];
+        octet_coords(o, A.ni, crd[0], crd[1], crd[2]);
+        const int stride[3] = {1, A.ni, A.ni * A.ni};
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            nbo[a] = (s >> a) & 1 ? (crd[a] < A.ni - 1 ? o + stride[a] : -1) : (crd[a] > 0 ? o - stride[a] : -1);
+    } else {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) nbo[a] = __ldg(T.nbr + (2 * a + ((s >> a) & 1)) * T.noct + og);
+    }
+    const TV us = lane_octet_sum<TV>(act ? u : TV(0));
+    const unsigned bal = __ballot_sync(FULL, act);
+    const int cnt = __popc((bal >> (threadIdx.x & 24)) & 0xffu);
+    const TV ubar = us * inv_count<TV>(cnt);
+    TV Au = dd * u;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int bit = 1 << a;
+        const TV u_in = __shfl_xor_sync(FULL, u, bit);
+        const TV c_in = __shfl_xor_sync(FULL, cm[a], bit);
+        const int v = nbo[a];
+        if (s & bit) {
+            Au += cm[a] * u_in;
+            if (v >= 0) {
+                const int ng = A.off + 8 * v + (s ^ bit);
+                const TC* cc = a == 0 ? C.cx : (a == 1 ? C.cy : C.cz);
+                Au += TV(tov(__ldg(cc + ng))) * U[ng];
+            } else if (v <= -2) {
+                const int t = __ldg(T.trec + og);
+                const TV cf = TV(tov(__ldg(C.tw + ((2 * a + 1) * 4 + sub_index(a, s)) * T.nt + t)));
+                Au += cf * (u + (U[-2 - v] - ubar) * TV(0.5));
+            }
+        } else {
+            Au += c_in * u_in;
+            if (v >= 0) Au += cm[a] * U[A.off + 8 * v + (s ^ bit)];
+            else if (v <= -2) Au += cm[a] * (u + (U[-2 - v] - ubar) * TV(0.5));
+        }
+    }
+    TV un = u;
+    if (valid && act && ((__popc(s) & 1) == colour)) {
+        un = u + divide(b - Au, dd);
+        U[g] = un;
+    }
+    if (prolong && valid) {
+        const int co = __ldg(T.child_oct + g);
+        if (co >= 0) octet_prolong<TV, TC>(C.d, U, co, un);
     }
 }
 
@@ -243,7 +366,7 @@ __global__ void __launch_bounds__(OBLK) k_orestrict(LevelArgs A, Tables T, Coefs
     octet_mean(S);
     TV b[8], Au[8];
     ld8(B + c8, b);
-    octet_Au<TV, TC, TW>(T, C, U, A.off, og, S, Au);
+    octet_Au<TV, TC, TW>(T, C, U, A, o, og, S, Au);
     TV rs = TV(0);
 #pragma unroll
     for (int s = 0; s < 8; ++s)
@@ -277,7 +400,7 @@ __global__ void __launch_bounds__(OBLK) k_oavg(LevelArgs A, Tables T, const TC* 
 #pragma unroll
     for (int q = 0; q < 8; ++q)
         if (dd[q] != TO(0)) { s += v[q]; ++n; }
-    P[__ldg(T.oct_parent + (c8 >> 3))] = n ? s / TO(n) : TO(0);
+    P[__ldg(T.oct_parent + (c8 >> 3))] = s * inv_count<TO>(n);
 }
 
 // Composite leaf operator over all tree levels in one launch (block -> level lookup):
@@ -286,6 +409,7 @@ struct OMultiLevel {
     int n;
     int off[MAXLEV];
     int noct[MAXLEV];
+    int ni[MAXLEV];
     int boff[MAXLEV + 1];
 };
 
@@ -303,7 +427,8 @@ __global__ void __launch_bounds__(OBLK) k_oapply(OMultiLevel ML, Tables T, Coefs
         load_octet<TO, TC, TW>(P, C, c8, S);
         octet_mean(S);
         TO Ap[8];
-        octet_Au<TO, TC, TW>(T, C, P, ML.off[l], c8 >> 3, S, Ap);
+        const LevelArgs A{ML.off[l], 8 * ML.noct[l], ML.ni[l]};
+        octet_Au<TO, TC, TW>(T, C, P, A, o, c8 >> 3, S, Ap);
 #pragma unroll
         for (int s = 0; s < 8; ++s) {
             const bool leaf = __ldg(T.child_oct + c8 + s) < 0;
@@ -312,6 +437,270 @@ __global__ void __launch_bounds__(OBLK) k_oapply(OMultiLevel ML, Tables T, Coefs
         }
     }
     if (R.op != OP_NONE) red_finish(R, blockIdx.x, dot, 0.0, sh);
+}
+
+// Coarsest level (Alg. 4, l = 0): one CTA, one thread per octet, nu sweeps (half
+// red->black, half black->red), each a pass separated by __syncthreads; fas completes
+// the FAS right-hand side first; prolong prolongs onto the finer level at the end.
+template <class TV, class TC, class TW>
+__global__ void __launch_bounds__(256) k_ocoarsest(LevelArgs A, Tables T, Coefs<TC, TW> C, TV* __restrict__ U,
+                                                    TV* __restrict__ B, int nu, int fas, int prolong) {
+    const int noct = A.ncell / 8;
+    auto pass = [&](int colour, bool fixb) {
+        for (int o = threadIdx.x; o < noct; o += blockDim.x) {
+            const int c8 = A.off + 8 * o;
+            OctState<TV> S;
+            load_octet<TV, TC, TW>(U, C, c8, S);
+            octet_mean(S);
+            TV b[8], Au[8];
+            ld8(B + c8, b);
+            octet_Au<TV, TC, TW>(T, C, U, A, o, c8 >> 3, S, Au);
+            if (fixb) {
+#pragma unroll
+                for (int s = 0; s < 8; ++s)
+                    if (T.child_oct[c8 + s] >= 0) B[c8 + s] = b[s] + Au[s];
+            } else {
+#pragma unroll
+                for (int s = 0; s < 8; ++s)
+                    if (((__popc(s) & 1) == colour) && S.d[s] != TV(0))
+                        U[c8 + s] = S.u[s] + divide(b[s] - Au[s], S.d[s]);
+            }
+        }
+        __syncthreads();
+    };
+    if (fas) pass(0, true);
+    const int half = nu / 2;
+    for (int it = 0; it < half; ++it) { pass(0, false); pass(1, false); }
+    for (int it = half; it < nu; ++it) { pass(1, false); pass(0, false); }
+    if (prolong) {
+        for (int c = threadIdx.x; c < A.ncell; c += blockDim.x) {
+            const int co = T.child_oct[A.off + c];
+            if (co >= 0) octet_prolong<TV, TC>(C.d, U, co, U[A.off + c]);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ coarse tail
+// The smallest uniform levels (m < 0) run their whole sub-cycle of Alg. 4 in one CTA with
+// u, b and the coefficients in shared memory, one thread per octet.  On these levels the
+// octets are lexicographic, so neighbours, parents and children are arithmetic and no
+// table is read.  Shared arrays are slot-major (index sbase + s * noct + o) so that the
+// threads of a warp, which own consecutive octets, touch consecutive banks.
+struct TailLevel {
+    int off;      // first global cell
+    int ni;       // octets per axis
+    int sbase;    // first element in the shared arrays
+};
+
+struct TailArgs {
+    int nlev;                 // L[0] = top (finest) tail level ... L[nlev-1] = coarsest
+    TailLevel L[MAXLEV];
+    int ncell;
+    const int* sched;         // passes of the sub-cycle: 8 * level index + pass kind
+    int nsched;
+    int fas, prolong;
+};
+
+template <class TV>
+struct TailMem {
+    TV *u, *b, *d, *cm[3];
+};
+
+__device__ __forceinline__ int tail_noct(const TailLevel& L) { return L.ni * L.ni * L.ni; }
+
+template <class TV>
+__device__ __forceinline__ void tail_octet_Au(const TailMem<TV>& M, const TailLevel& L, int o, const TV (&u)[8],
+                                              const TV (&d)[8], const TV (&cm)[3][8], TV (&Au)[8]) {
+    const int ni = L.ni, no = ni * ni * ni;
+    int I, J, K;
+    octet_coords(o, ni, I, J, K);
+    const int crd[3] = {I, J, K};
+    const int stride[3] = {1, ni, ni * ni};
+#pragma unroll
+    for (int s = 0; s < 8; ++s) Au[s] = d[s] * u[s];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int bit = 1 << a;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int s = clear_slot(a, q), t = s | bit;
+            Au[s] += cm[a][t] * u[t];
+            Au[t] += cm[a][t] * u[s];
+        }
+        if (crd[a] > 0) {
+            const int nbo = L.sbase + o - stride[a];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int s = clear_slot(a, q);
+                Au[s] += cm[a][s] * M.u[nbo + (s | bit) * no];
+            }
+        }
+        if (crd[a] < ni - 1) {
+            const int nbo = L.sbase + o + stride[a];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int s = clear_slot(a, q);
+                Au[s | bit] += M.cm[a][nbo + s * no] * M.u[nbo + s * no];
+            }
+        }
+    }
+}
+
+// parent (shared index) of octet o of level L, on the coarser tail level P
+__device__ __forceinline__ int tail_parent(const TailLevel& L, const TailLevel& P, int o) {
+    int I, J, K;
+    octet_coords(o, L.ni, I, J, K);
+    const int po = (I >> 1) + P.ni * ((J >> 1) + P.ni * (K >> 1));
+    const int slot = (I & 1) | ((J & 1) << 1) | ((K & 1) << 2);
+    return P.sbase + slot * tail_noct(P) + po;
+}
+
+enum { TP_SWEEP0 = 0, TP_SWEEP1 = 1, TP_FIXB = 2, TP_RESTRICT = 3, TP_PROLONG = 4 };
+
+// Colour sweep of a small tail level with one thread per cell (short dependency chains
+// when a level has no more cells than the block has threads).  Shared index of cell
+// (o, s) is sbase + s * no + o.
+template <class TV>
+__device__ __forceinline__ void tail_sweep_cells(const TailMem<TV>& M, const TailLevel& L, int colour) {
+    const int ni = L.ni, no = ni * ni * ni;
+    for (int c = threadIdx.x; c < 8 * no; c += blockDim.x) {
+        const int s = c / no, o = c - s * no;
+        if ((__popc(s) & 1) != colour) continue;
+        const int q = L.sbase + c;
+        const TV dd = M.d[q];
+        if (dd == TV(0)) continue;
+        int crd[3];
+        octet_coords(o, ni, crd[0], crd[1], crd[2]);
+        const int stride[3] = {1, ni, ni * ni};
+        TV Au = dd * M.u[q];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const int bit = 1 << a;
+            const int t = s ^ bit;
+            const int qi = L.sbase + t * no + o;                // partner in the octet
+            if (s & bit) {
+                Au += M.cm[a][q] * M.u[qi];
+                if (crd[a] < ni - 1) {
+                    const int qo = qi + stride[a];               // slot t of the + octet
+                    Au += M.cm[a][qo] * M.u[qo];
+                }
+            } else {
+                Au += M.cm[a][qi] * M.u[qi];
+                if (crd[a] > 0) Au += M.cm[a][q] * M.u[qi - stride[a]];   // slot t of the - octet
+            }
+        }
+        M.u[q] = M.u[q] + divide(M.b[q] - Au, dd);
+    }
+    __syncthreads();
+}
+
+// One pass over the octets of tail level li (li + 1 = the next coarser tail level, for
+// restriction and prolongation).
+template <class TV>
+__device__ __forceinline__ void tail_pass(const TailMem<TV>& M, const TailArgs& A, int li, int kind, TV scale) {
+    const TailLevel& L = A.L[li];
+    const int no = tail_noct(L);
+    for (int o = threadIdx.x; o < no; o += blockDim.x) {
+        const int c0 = L.sbase + o;
+        TV u[8], d[8];
+#pragma unroll
+        for (int s = 0; s < 8; ++s) { u[s] = M.u[c0 + s * no]; d[s] = M.d[c0 + s * no]; }
+        TV mean = TV(0);
+        int n = 0;
+#pragma unroll
+        for (int s = 0; s < 8; ++s)
+            if (d[s] != TV(0)) { mean += u[s]; ++n; }
+        mean = mean * inv_count<TV>(n);
+        if (kind == TP_PROLONG) {
+            const TV uP = M.u[tail_parent(L, A.L[li + 1], o)];
+#pragma unroll
+            for (int s = 0; s < 8; ++s)
+                if (d[s] != TV(0)) M.u[c0 + s * no] = u[s] + (uP - mean);
+            continue;
+        }
+        TV cm[3][8], Au[8];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int s = 0; s < 8; ++s) cm[a][s] = M.cm[a][c0 + s * no];
+        tail_octet_Au<TV>(M, L, o, u, d, cm, Au);
+        if (kind == TP_FIXB) {
+            // every real cell of a level m < 0 has children; padding cells are inactive
+#pragma unroll
+            for (int s = 0; s < 8; ++s)
+                if (d[s] != TV(0)) M.b[c0 + s * no] += Au[s];
+        } else if (kind == TP_RESTRICT) {
+            TV rs = TV(0);
+#pragma unroll
+            for (int s = 0; s < 8; ++s)
+                if (d[s] != TV(0)) rs += M.b[c0 + s * no] - Au[s];
+            const int P = tail_parent(L, A.L[li + 1], o);
+            M.b[P] = scale * rs;
+            M.u[P] = mean;
+        } else {
+#pragma unroll
+            for (int s = 0; s < 8; ++s)
+                if (((__popc(s) & 1) == kind) && d[s] != TV(0))
+                    M.u[c0 + s * no] = u[s] + divide(M.b[c0 + s * no] - Au[s], d[s]);
+        }
+    }
+    __syncthreads();
+}
+
+// The sub-cycle of Alg. 4 over the tail levels is expanded on the host into a flat
+// schedule of passes (no recursion on the device); fas adds the FAS right-hand-side pass
+// on the top tail level first.
+template <class TV, class TC, class TW>
+__global__ void __launch_bounds__(sizeof(TV) == 8 ? 256 : 512)
+    k_otail(TailArgs A, Tables T, Coefs<TC, TW> C, TV* __restrict__ U, TV* __restrict__ B, TV scale) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int N = A.ncell;
+    TailMem<TV> M;
+    TV* base = reinterpret_cast<TV*>(smem);
+    M.u = base; M.b = base + N; M.d = base + 2 * N;
+    M.cm[0] = base + 3 * N; M.cm[1] = base + 4 * N; M.cm[2] = base + 5 * N;
+    // global cell off + 8 o + s  <->  shared sbase + s * no + o
+    for (int li = 0; li < A.nlev; ++li) {
+        const TailLevel& L = A.L[li];
+        const int no = tail_noct(L);
+        for (int c = threadIdx.x; c < 8 * no; c += blockDim.x) {
+            const int g = L.off + c, q = L.sbase + (c & 7) * no + (c >> 3);
+            M.u[q] = U[g];
+            M.b[q] = B[g];
+            M.d[q] = TV(tov(C.d[g]));
+            M.cm[0][q] = TV(tov(C.cx[g]));
+            M.cm[1][q] = TV(tov(C.cy[g]));
+            M.cm[2][q] = TV(tov(C.cz[g]));
+        }
+    }
+    __syncthreads();
+    if (A.fas) tail_pass<TV>(M, A, 0, TP_FIXB, TV(0));
+    for (int q = 0; q < A.nsched; ++q) {
+        const int e = __ldg(A.sched + q);
+        const int li = e >> 3, kind = e & 7;
+        if (kind <= TP_SWEEP1 && 8 * tail_noct(A.L[li]) <= (int)blockDim.x)
+            tail_sweep_cells<TV>(M, A.L[li], kind);
+        else
+            tail_pass<TV>(M, A, li, kind, scale);
+    }
+    for (int li = 0; li < A.nlev; ++li) {
+        const TailLevel& L = A.L[li];
+        const int no = tail_noct(L);
+        for (int c = threadIdx.x; c < 8 * no; c += blockDim.x) {
+            const int q = L.sbase + (c & 7) * no + (c >> 3);
+            U[L.off + c] = M.u[q];
+            B[L.off + c] = M.b[q];
+        }
+    }
+    if (A.prolong) {
+        // onto the level above the tail: children of the top tail level's cells
+        const TailLevel& L = A.L[0];
+        const int no = tail_noct(L);
+        for (int c = threadIdx.x; c < 8 * no; c += blockDim.x) {
+            const int co = T.child_oct[L.off + c];
+            if (co >= 0) octet_prolong<TV, TC>(C.d, U, co, M.u[L.sbase + (c & 7) * no + (c >> 3)]);
+        }
+    }
 }
 
 }  // namespace ocg

@@ -89,6 +89,8 @@ int64_t HostTree::cell_index(int m, int64_t i, int64_t j, int64_t k) const {
     if (m < mc || m > D) return -1;
     const LevelMeta& l = L(m);
     if (i < 0 || j < 0 || k < 0 || i >= l.N || j >= l.N || k >= l.N) return -1;
+    const int slot = (int)((i & 1) | ((j & 1) << 1) | ((k & 1) << 2));
+    if (l.ni > 0) return l.off + 8 * lex(i >> 1, j >> 1, k >> 1, l.ni) + slot;
     const auto& ok = okeys[m - mc];
     const uint64_t key = morton3(i >> 1, j >> 1, k >> 1);
     auto it = std::lower_bound(ok.begin(), ok.end(), key);
@@ -101,7 +103,14 @@ void HostTree::cell_coords(int m, int64_t g, int64_t& i, int64_t& j, int64_t& k)
     const LevelMeta& l = L(m);
     const int64_t lc = g - l.off;
     uint64_t I, J, K;
-    demorton3(okeys[m - mc][lc >> 3], I, J, K);
+    if (l.ni > 0) {
+        const int64_t o = lc >> 3;
+        I = o % l.ni;
+        J = (o / l.ni) % l.ni;
+        K = o / ((int64_t)l.ni * l.ni);
+    } else {
+        demorton3(okeys[m - mc][lc >> 3], I, J, K);
+    }
     const int s = (int)(lc & 7);
     i = 2 * (int64_t)I + (s & 1);
     j = 2 * (int64_t)J + ((s >> 1) & 1);
@@ -199,15 +208,12 @@ void build_host_tree(const ocg_octree_desc& desc, HostTree& T) {
                 for (int64_t j = 0; j < np; ++j)
                     for (int64_t i = 0; i < np; ++i)
                         if (R[lex(i, j, k, np)]) keys.push_back(morton3(i, j, k));
+            std::sort(keys.begin(), keys.end());
+            l.noct = (int64_t)keys.size();
         } else {
-            const int64_t np = l.Np / 2;
-            keys.reserve(np * np * np);
-            for (int64_t k = 0; k < np; ++k)
-                for (int64_t j = 0; j < np; ++j)
-                    for (int64_t i = 0; i < np; ++i) keys.push_back(morton3(i, j, k));
+            l.ni = l.Np / 2;
+            l.noct = (int64_t)l.ni * l.ni * l.ni;
         }
-        std::sort(keys.begin(), keys.end());
-        l.noct = (int64_t)keys.size();
         l.ncell = 8 * l.noct;
     }
     T.order.clear();
@@ -250,20 +256,33 @@ void build_host_tree(const ocg_octree_desc& desc, HostTree& T) {
             }
             T.cell_flags[g] = fl;
             if (has_children) {
-                const auto& ck = T.okeys[m + 1 - mc];
-                auto it = std::lower_bound(ck.begin(), ck.end(), morton3(i, j, k));
-                T.child_oct[g] = (int32_t)(T.L(m + 1).oct_off + (it - ck.begin()));
+                const LevelMeta& lf = T.L(m + 1);
+                if (lf.ni > 0) {
+                    T.child_oct[g] = (int32_t)(lf.oct_off + lex(i, j, k, lf.ni));
+                } else {
+                    const auto& ck = T.okeys[m + 1 - mc];
+                    auto it = std::lower_bound(ck.begin(), ck.end(), morton3(i, j, k));
+                    T.child_oct[g] = (int32_t)(lf.oct_off + (it - ck.begin()));
+                }
             }
         }
     }
-    // canonical leaves: levels 0..D in storage order are (depth, Morton) order
+    // canonical leaves: sorted by (depth, Morton key)
     T.leaf_cell.clear();
     T.leaf_depth.clear(); T.leaf_i.clear(); T.leaf_j.clear(); T.leaf_k.clear();
     for (int m = 0; m <= D; ++m) {
         const LevelMeta& l = T.L(m);
+        std::vector<std::pair<uint64_t, int64_t>> lv;
         for (int64_t lc = 0; lc < l.ncell; ++lc) {
             const int64_t g = l.off + lc;
             if (!(T.cell_flags[g] & 1)) continue;
+            int64_t i, j, k;
+            T.cell_coords(m, g, i, j, k);
+            lv.push_back({morton3(i, j, k), g});
+        }
+        std::sort(lv.begin(), lv.end());
+        for (const auto& e : lv) {
+            const int64_t g = e.second;
             int64_t i, j, k;
             T.cell_coords(m, g, i, j, k);
             T.cell_rank[g] = (int32_t)T.leaf_cell.size();
@@ -277,16 +296,22 @@ void build_host_tree(const ocg_octree_desc& desc, HostTree& T) {
     // ---- octet tables: neighbours, parents, T records
     T.nbr.assign(6 * T.noct, -1);
     T.oct_parent.assign(T.noct, -1);
-    T.tK.clear();
     T.t_oct.clear();
-    std::vector<int32_t> trec(T.noct, -1);
+    T.trec.assign(T.noct, -1);
+    auto& trec = T.trec;
     for (int m = mc; m <= D; ++m) {
         const LevelMeta& l = T.L(m);
         const int64_t PG = m >= 1 ? ((int64_t)n0 << (m - 1)) : l.Np / 2;
         const auto& keys = T.okeys[m - mc];
         for (int64_t o = 0; o < l.noct; ++o) {
             uint64_t I, J, K;
-            demorton3(keys[o], I, J, K);
+            if (l.ni > 0) {
+                I = o % l.ni;
+                J = (o / l.ni) % l.ni;
+                K = o / ((int64_t)l.ni * l.ni);
+            } else {
+                demorton3(keys[o], I, J, K);
+            }
             const int64_t go = l.oct_off + o;
             if (m > mc) T.oct_parent[go] = (int32_t)T.cell_index(m - 1, I, J, K);
             const int64_t P[3] = {(int64_t)I, (int64_t)J, (int64_t)K};
@@ -298,7 +323,9 @@ void build_host_tree(const ocg_octree_desc& desc, HostTree& T) {
                     int32_t v = -1;
                     if (q[a] >= 0 && q[a] < PG) {
                         const bool inner = (m <= 0) || refined(m - 1, q[0], q[1], q[2]);
-                        if (inner) {
+                        if (l.ni > 0) {
+                            v = (int32_t)lex(q[0], q[1], q[2], l.ni);
+                        } else if (inner) {
                             auto it = std::lower_bound(keys.begin(), keys.end(), morton3(q[0], q[1], q[2]));
                             v = (int32_t)(it - keys.begin());
                         } else {
@@ -309,7 +336,7 @@ void build_host_tree(const ocg_octree_desc& desc, HostTree& T) {
                                 trec[go] = (int32_t)T.t_oct.size();
                                 T.t_oct.push_back((int32_t)go);
                             }
-                            v = -2 - trec[go];
+                            v = (int32_t)(-2 - Kc);
                         }
                     }
                     T.nbr[(int64_t)dir * T.noct + go] = v;
@@ -317,19 +344,6 @@ void build_host_tree(const ocg_octree_desc& desc, HostTree& T) {
         }
     }
     T.nt = (int64_t)T.t_oct.size();
-    T.tK.assign(6 * T.nt, -1);
-    for (int64_t t = 0; t < T.nt; ++t) {
-        const int64_t go = T.t_oct[t];
-        const int m = T.cell_level[8 * go];
-        uint64_t I, J, K;
-        demorton3(T.okeys[m - mc][go - T.L(m).oct_off], I, J, K);
-        for (int dir = 0; dir < 6; ++dir) {
-            if (T.nbr[(int64_t)dir * T.noct + go] > -2) continue;
-            int64_t q[3] = {(int64_t)I, (int64_t)J, (int64_t)K};
-            q[dir / 2] += (dir & 1) ? 1 : -1;
-            T.tK[(int64_t)dir * T.nt + t] = (int32_t)T.cell_index(m - 1, q[0], q[1], q[2]);
-        }
-    }
 
     // ---- neighbour export and canonical faces
     T.nb_kind.assign(6 * T.nleaf, 0);
@@ -368,7 +382,7 @@ void build_host_tree(const ocg_octree_desc& desc, HostTree& T) {
                 }
                 if (sd == 1 && kind == 2) {
                     const int64_t go = (g >> 3);
-                    const int32_t t = -2 - T.nbr[(int64_t)dir * T.noct + go];
+                    const int32_t t = T.trec[go];
                     const int64_t slot = (int64_t)(dir * 4 + sub_index(a, s)) * T.nt + t;
                     faces.push_back({a, d, (int32_t)q[0], (int32_t)q[1], (int32_t)q[2], r, rk, slot, 1,
                                      morton3(q[0], q[1], q[2])});

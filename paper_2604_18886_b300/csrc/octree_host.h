@@ -5,8 +5,9 @@
 //    of depth m (leaves and inner); level m < 0 is the uniform coarsening of the root
 //    grid by 2^-m.  The coarsest grid is padded to an even size with inactive cells.
 //  * Cells of a level are stored in octets: the 8 children of one cell of the next
-//    coarser grid, slot s = dx + 2 dy + 4 dz, octets sorted by the Morton key of that
-//    parent.  Inside a level the cell order is therefore the level's Morton order.
+//    coarser grid, slot s = dx + 2 dy + 4 dz.  On the adaptive levels (m >= 1) octets are
+//    sorted by the Morton key of their parent; on the uniform levels (m <= 0) they are in
+//    lexicographic order of the parent, so neighbouring octets are found arithmetically.
 //  * Levels are concatenated in the order 0, 1, ..., D, -1, -2, ..., mc; cells of the
 //    tree levels 0..D form the prefix [0, n_tree) that the Krylov vectors cover.
 #pragma once
@@ -23,6 +24,8 @@ struct LevelMeta {
     int m = 0;        // level index (depth for m >= 0)
     int N = 0;        // cells per axis of the level grid
     int Np = 0;       // padded size (N rounded up to even at the coarsest level)
+    int ni = 0;       // uniform levels (m <= 0): octets per axis, octets in lexicographic
+                      // order o = I + ni (J + ni K); 0 for the adaptive levels m >= 1
     int64_t off = 0;  // first global cell
     int64_t ncell = 0;
     int64_t oct_off = 0;  // first global octet (= off / 8)
@@ -41,10 +44,11 @@ struct HostTree {
     std::vector<std::vector<uint64_t>> okeys;  // indexed by m - mc
 
     // global tables
-    std::vector<int32_t> nbr;        // [6][noct]: level-local octet, -1 wall, -2-t T record
+    std::vector<int32_t> nbr;        // [6][noct]: level-local octet, -1 wall, -2-K T face
+                                     //   (K = global cell of the coarser leaf)
     std::vector<int32_t> oct_parent; // [noct]: global parent cell, -1 at the coarsest level
     std::vector<int32_t> child_oct;  // [ncell]: global octet of the children, -1 if none
-    std::vector<int32_t> tK;         // [6][nt]: global cell of the coarser leaf, -1
+    std::vector<int32_t> trec;       // [noct]: T record of the octet, -1 if it has no T face
     std::vector<int32_t> t_oct;      // [nt]: global octet owning the record
     std::vector<int32_t> leaf_cell;  // [nleaf]: canonical rank -> global cell
     std::vector<int32_t> cell_rank;  // [ncell]: global cell -> canonical rank or -1

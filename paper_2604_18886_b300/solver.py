@@ -95,13 +95,17 @@ class Octree:
         return i.astype(np.int64), j.astype(np.int64), k.astype(np.int64), leaf.astype(bool)
 
 
+SWEEP_FORMS = {"auto": L.OCG_SWEEP_AUTO, "octet": L.OCG_SWEEP_OCTET, "cell": L.OCG_SWEEP_CELL}
+
+
 def mg_params(mu=1, nu_pre=2, nu_post=2, nu_coarsest=10, beta=2.0, alpha=2.0, coef="f32",
-              bf16_coarse=False) -> L.MGParams:
+              bf16_coarse=False, sweep="auto") -> L.MGParams:
     p = L.MGParams()
     p.mu, p.nu_pre, p.nu_post, p.nu_coarsest = mu, nu_pre, nu_post, nu_coarsest
     p.beta_restrict, p.alpha = beta, alpha
     p.coef_dtype = L.OCG_F64 if coef == "f64" else L.OCG_F32
     p.bf16_coarse = 1 if bf16_coarse else 0
+    p.sweep_form = SWEEP_FORMS[sweep]
     return p
 
 
@@ -140,6 +144,15 @@ class Hierarchy:
         n = len(i)
         out = [np.empty(n) for _ in range(4)]
         L.check(L.lib().ocg_hier_export_coefs(self._h, m, *[L.ptr(a) for a in out]))
+        return out
+
+    def tuning(self):
+        """{level: (form, us_octet, us_cell)} as chosen / measured at set-up."""
+        out = {}
+        for m in range(self.tree.mc, self.tree.D + 1):
+            f, a, b = C.c_int32(), C.c_double(), C.c_double()
+            L.check(L.lib().ocg_hier_tuning(self._h, m, C.byref(f), C.byref(a), C.byref(b)))
+            out[m] = (f.value, a.value, b.value)
         return out
 
     @staticmethod

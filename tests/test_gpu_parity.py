@@ -34,8 +34,8 @@ torch = pytest.importorskip("torch")
 _CACHE = {}
 
 
-def build(p, coef="f64", mu=1, bf16=False):
-    key = (p.name, tuple(p.bc), coef, mu, bf16)
+def build(p, coef="f64", mu=1, bf16=False, sweep="auto"):
+    key = (p.name, tuple(p.bc), coef, mu, bf16, sweep)
     if key in _CACHE:
         return _CACHE[key]
     t = O.Octree(p.desc)
@@ -43,7 +43,7 @@ def build(p, coef="f64", mu=1, bf16=False):
     beta = P.face_beta(p, f)
     H = OP.Hierarchy(t, beta, p.bc)
     g = S.Octree(p.desc)
-    gh = S.Hierarchy(g, beta, p.bc, S.mg_params(mu=mu, coef=coef, bf16_coarse=bf16))
+    gh = S.Hierarchy(g, beta, p.bc, S.mg_params(mu=mu, coef=coef, bf16_coarse=bf16, sweep=sweep))
     _CACHE[key] = (t, H, g, gh, f, beta)
     return _CACHE[key]
 
@@ -272,3 +272,28 @@ def test_wcycle_solve_matches_oracle():
     x, st = gh.solve(cuda(b), tol=1e-8, precision="fp64")
     assert st.iterations == ko
     assert rel(x.cpu().numpy(), xo) <= 1e-9
+
+
+@pytest.mark.parametrize("sweep", ["octet", "cell"])
+@pytest.mark.parametrize("name", ["c2_16", "c3_16_d2", "band_12_d2", "c4_t1"])
+def test_both_sweep_forms_match_oracle(name, sweep):
+    # the autotuner may pick either form per level; each must reproduce Alg. 4
+    p = CASES[name]()
+    t, H, g, gh, f, beta = build(p, "f64", mu=1, sweep=sweep)
+    r = P.random_vector(t.n_leaves, 13)
+    assert rel(gh.vcycle(cuda(r)).cpu().numpy(), mg.vcycle(H, r)) <= 1e-10
+    t, H, g, gh, f, beta = build(p, "f32", mu=2, sweep=sweep)
+    z = gh.vcycle(cuda(r, torch.float32)).double().cpu().numpy()
+    assert rel(z, mg.vcycle(H, r.astype(np.float32).astype(np.float64), mg.CycleParams(mu=2))) <= 1e-5
+
+
+def test_autotuner_records_both_forms():
+    p = P.c2(32)
+    t, H, g, gh, f, beta = build(p, "f32")
+    tun = gh.tuning()
+    timed = [m for m, (form, a, b) in tun.items() if form >= 0]
+    assert timed, tun
+    for m in timed:
+        form, a, b = tun[m]
+        assert a > 0 and b > 0
+        assert form == (1 if b < a else 0)
