@@ -47,7 +47,7 @@ def _peaks():
 
 def _kernel_hash():
     h = hashlib.sha256()
-    for f in ("kernels.cuh", "ocg_api.cu"):
+    for f in ("kernels.cuh", "octet.cuh", "ocg_api.cu"):
         with open(os.path.join(ROOT, "paper_2604_18886_b300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -14,7 +14,8 @@ Modules:
   operator - leaf coefficients (Sec. 2.1, Eq. projection-poisson-system; Sec. 3.1
              T-junction ghosts), Alg. 3 coarsening, level matrices, composite A
   mg      - FAS-style mu-cycle (Alg. 4) and the plain mu-cycle (Alg. 2)
-  pcg     - preconditioned CG (Alg. 1)
+  pcg     - preconditioned CG (Alg. 1); preconditioned BiCGStab for the adjoint system
+  adjoint - gradients of a loss through the solve: transpose solve and per-face dL/dbeta
 
 Every function is pinned by tests in tests/test_oracle_*.py against closed forms,
 worked values printed in the paper, invariants, brute force and dense solves.
