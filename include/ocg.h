@@ -149,7 +149,11 @@ int ocg_hier_export_coefs(const ocg_hier* h, int32_t m, double* c, double* cx, d
 
 /* y = A x for the composite leaf operator (Sec. 2.1 flux sums, Sec. 3.1 ghosts; inner
  * values are the mean of their active children).  dtype OCG_F64 or OCG_F32 for both x
- * and y (device, canonical leaf order, n_leaves).  transpose must be 0 in this version. */
+ * and y (device, canonical leaf order, n_leaves).  transpose = 1 gives y = A^T x (the
+ * operator of the adjoint solve; no counterpart in the paper): A x plus the rows of
+ * A^T - A, which only T-junctions make non-zero (every tree cell is taken as active
+ * there).  Other transpose values: EINVAL.  The first transposed call builds and
+ * uploads the octree's adjoint tables (host work, synchronous). */
 int ocg_apply_A(ocg_hier* h, int32_t dtype, const void* x_dev, void* y_dev, int32_t transpose,
                 void* stream);
 
@@ -157,7 +161,8 @@ int ocg_apply_A(ocg_hier* h, int32_t dtype, const void* x_dev, void* y_dev, int3
  * (F64 needs coef_dtype OCG_F64; F32 needs OCG_F32); device, canonical leaf order. */
 int ocg_vcycle(ocg_hier* h, int32_t dtype, const void* r_dev, void* z_dev, void* stream);
 
-#define OCG_SOLVE_EAGER 1    /* flags: launch kernel by kernel, test convergence on the host */
+#define OCG_SOLVE_EAGER 1      /* flags: launch kernel by kernel, test convergence on the host */
+#define OCG_SOLVE_TRANSPOSE 2  /* flags: solve A^T x = b (adjoint system) by BiCGStab */
 
 typedef struct {
     double tol;              /* stop when ||r||_2 <= tol ||b||_2 (recursive residual) */
@@ -184,10 +189,28 @@ typedef struct {
  * ||r|| <= tol ||b|| is made on the device and the call synchronises once, at the end.
  * With OCG_SOLVE_EAGER, or while a probe is set, kernels are launched one by one and the
  * host tests convergence after every iteration.  The true residual is recomputed in FP64
- * at exit.  A hierarchy serves one solve at a time (its work vectors are shared).
- * Errors: ENOTCONV (stats filled), ENAN, EINVAL, ECUDA. */
+ * at exit.  With the null space on, b is shifted to zero mean and x is returned with
+ * zero mean over the leaves.
+ * With OCG_SOLVE_TRANSPOSE the call solves A^T x = b (adjoint system; no counterpart in
+ * the paper) by right-preconditioned BiCGStab (van der Vorst 1992) with the same
+ * mu-cycle: Alg. 1 with that cycle stagnates on A^T, which T-junctions make differ from
+ * A.  One iteration there applies the cycle and A^T twice; `iterations` counts
+ * iterations.  A hierarchy serves one solve at a time (its work vectors are shared).
+ * Errors: ENOTCONV (stats filled), ENAN, EINVAL (also unknown flags), ECUDA. */
 int ocg_pcg_solve(ocg_hier* h, const double* b_dev, double* x_dev, const ocg_solve_params* prm,
                   ocg_solve_stats* stats, void* stream);
+
+/* Face gradient of a loss through the solve (adjoint; no counterpart in the paper).
+ * With p the solution of A p = b and lambda that of A^T lambda = dL/dp, writes
+ * dbeta[f] = dL/dbeta_f = -lambda^T (dA/dbeta_f) p for every canonical face f (the order
+ * of ocg_octree_export_faces): -h_f (lambda_i - lambda_j)(p_i - p_j) for the face between
+ * equal-depth leaves i (- side) and j, and -(h_f/2)(lambda_i - lambda_K)(pbar_P - p_K) for
+ * a T sub-face of the fine leaf i against the coarser leaf K, pbar_P the mean of the
+ * leaves under i's parent (Sec. 3.1 ghost).  p, lambda: float64 device vectors in
+ * canonical leaf order; dbeta: float64 device vector of n_faces.  Uses the hierarchy's
+ * work vectors (one call at a time per hierarchy). */
+int ocg_face_grad(ocg_hier* h, const double* p_dev, const double* lambda_dev, double* dbeta_dev,
+                  void* stream);
 
 /* Operator apply that allocates nothing (no counterpart in the paper).
  * For callers that must not allocate device memory at call time, e.g. code running

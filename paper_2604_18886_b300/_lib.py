@@ -37,6 +37,7 @@ class MGParams(C.Structure):
 
 
 OCG_SOLVE_EAGER = 1
+OCG_SOLVE_TRANSPOSE = 2
 
 
 class SolveParams(C.Structure):
@@ -74,6 +75,7 @@ _SIGS = [
     ("ocg_hier_tuning", C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_double),
                                   C.POINTER(C.c_double)]),
     ("ocg_apply_A", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
+    ("ocg_face_grad", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("ocg_vcycle", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("ocg_pcg_solve", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(SolveParams),
                                 C.POINTER(SolveStats), C.c_void_p]),

@@ -55,9 +55,14 @@ __device__ __forceinline__ int sub_index(int a, int s) {
 // Device scalars of the Krylov loop.
 enum {
     S_PAP = 0, S_ALPHA, S_RZ, S_BETA, S_RR, S_RS, S_MEAN, S_BB, S_NS, S_TOL, S_MAXIT, S_K, S_DONE, S_TRUE,
-    S_HIST = 16, S_COUNT = 16 + 128
+    S_RHO, S_RHON, S_OMEGA, S_XMEAN,
+    S_HIST = 24, S_COUNT = 24 + 128
 };
-enum { OP_NONE = -1, OP_ALPHA = 0, OP_RR = 1, OP_BETA = 2, OP_RZ0 = 3, OP_BB = 4, OP_TRUE = 5 };
+enum {
+    OP_NONE = -1, OP_ALPHA = 0, OP_RR = 1, OP_BETA = 2, OP_RZ0 = 3, OP_BB = 4, OP_TRUE = 5,
+    // BiCGStab (adjoint system) and the zero-mean shift of the returned solution
+    OP_BI_INIT = 6, OP_BI_ALPHA = 7, OP_BI_OMEGA = 8, OP_BI_RR = 9, OP_XMEAN = 10
+};
 
 // A reduction spread over nb blocks: each block stores its FP64 partial(s) in part[blk]
 // (and part[nb + blk]); the last block to arrive sums them in a fixed order and applies
@@ -89,7 +94,22 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     return t;  // valid in thread 0
 }
 
-__device__ void red_apply(const Red& R, double sa, double sb) {
+// Convergence bookkeeping shared by both Krylov loops: iteration count, history, stop
+// flag and the WHILE-node condition.
+__device__ __forceinline__ void red_converged(const Red& R, double rr) {
+    double* S = R.S;
+    S[S_RR] = rr;
+    const int k = (int)S[S_K] + 1;
+    S[S_K] = k;
+    const double bb = S[S_BB];
+    const double rel = bb > 0.0 ? sqrt(fmax(rr, 0.0) / bb) : 0.0;
+    if (k < 128) S[S_HIST + k] = rel;
+    const bool done = !(rel > S[S_TOL]) || k >= (int)S[S_MAXIT];
+    S[S_DONE] = done ? 1.0 : 0.0;
+    if (R.set_cond) cudaGraphSetConditional(R.cond, done ? 0u : 1u);
+}
+
+__device__ void red_apply(const Red& R, double sa, double sb, double sc) {
     double* S = R.S;
     const bool ns = S[S_NS] != 0.0;
     switch (R.op) {
@@ -104,17 +124,8 @@ __device__ void red_apply(const Red& R, double sa, double sb) {
         }
         case OP_RR: {
             const double mean = ns ? sb / R.nleaf : 0.0;
-            const double rr = ns ? sa - sb * mean : sa;
             S[S_MEAN] = mean;
-            S[S_RR] = rr;
-            const int k = (int)S[S_K] + 1;
-            S[S_K] = k;
-            const double bb = S[S_BB];
-            const double rel = bb > 0.0 ? sqrt(fmax(rr, 0.0) / bb) : 0.0;
-            if (k < 128) S[S_HIST + k] = rel;
-            const bool done = !(rel > S[S_TOL]) || k >= (int)S[S_MAXIT];
-            S[S_DONE] = done ? 1.0 : 0.0;
-            if (R.set_cond) cudaGraphSetConditional(R.cond, done ? 0u : 1u);
+            red_converged(R, ns ? sa - sb * mean : sa);
             break;
         }
         case OP_TRUE: {
@@ -122,18 +133,49 @@ __device__ void red_apply(const Red& R, double sa, double sb) {
             S[S_TRUE] = ns ? sa - sb * mean : sa;
             break;
         }
+        // BiCGStab: sa = (rhat, r) with rhat = r = b after the null-space shift
+        case OP_BI_INIT: {
+            S[S_RHON] = sa;
+            S[S_RHO] = S[S_ALPHA] = S[S_OMEGA] = 1.0;
+            S[S_BETA] = sa;
+            S[S_K] = 0.0;
+            const double bb = S[S_BB];
+            const bool done = !(bb > 0.0) || !(sqrt(fmax(sa, 0.0) / bb) > S[S_TOL]) || (int)S[S_MAXIT] <= 0;
+            S[S_DONE] = done ? 1.0 : 0.0;
+            if (R.set_cond) cudaGraphSetConditional(R.cond, done ? 0u : 1u);
+            break;
+        }
+        case OP_BI_ALPHA: S[S_ALPHA] = sa != 0.0 ? S[S_RHON] / sa : 0.0; break;   // sa = (rhat, v)
+        case OP_BI_OMEGA: S[S_OMEGA] = sb != 0.0 ? sa / sb : 0.0; break;          // (t, s) / (t, t)
+        case OP_BI_RR: {
+            // sa = ||r||^2, sb = sum(r), sc = (rhat, r); rhat has zero mean under the
+            // null space, so the shift r -= mean leaves (rhat, r) unchanged
+            const double mean = ns ? sb / R.nleaf : 0.0;
+            S[S_MEAN] = mean;
+            red_converged(R, ns ? sa - sb * mean : sa);
+            S[S_RHO] = S[S_RHON];
+            S[S_RHON] = sc;
+            const double den = S[S_RHO] * S[S_OMEGA];
+            S[S_BETA] = den != 0.0 ? (sc * S[S_ALPHA]) / den : 0.0;
+            break;
+        }
+        case OP_XMEAN: S[S_XMEAN] = ns ? sb / R.nleaf : 0.0; break;
         default: break;
     }
 }
 
-// Called by every block of a reduction; blk = index of this block within it.
-__device__ void red_finish(const Red& R, int blk, double va, double vb, double* sh) {
+// Called by every block of a reduction; blk = index of this block within it.  NV = 2 or
+// 3 partial sums per block (part holds NV * nb doubles).
+template <int NV = 2>
+__device__ void red_finish(const Red& R, int blk, double va, double vb, double vc, double* sh) {
     __shared__ int last;
     const double ta = block_sum(va, sh);
     const double tb = block_sum(vb, sh);
+    const double tc = NV > 2 ? block_sum(vc, sh) : 0.0;
     if (threadIdx.x == 0) {
         R.part[blk] = ta;
         R.part[R.nb + blk] = tb;
+        if (NV > 2) R.part[2 * R.nb + blk] = tc;
         __threadfence();
         const unsigned prev = atomicAdd(R.cnt, 1u);
         last = prev == (unsigned)(R.nb - 1) ? 1 : 0;
@@ -141,17 +183,22 @@ __device__ void red_finish(const Red& R, int blk, double va, double vb, double* 
     __syncthreads();
     if (!last) return;
     __threadfence();
-    double a = 0.0, b = 0.0;
+    double a = 0.0, b = 0.0, c = 0.0;
     for (int i = threadIdx.x; i < R.nb; i += blockDim.x) {
         a += __ldcg(R.part + i);
         b += __ldcg(R.part + R.nb + i);
+        if (NV > 2) c += __ldcg(R.part + 2 * R.nb + i);
     }
     const double sa = block_sum(a, sh);
     const double sb = block_sum(b, sh);
+    const double sc = NV > 2 ? block_sum(c, sh) : 0.0;
     if (threadIdx.x == 0) {
-        red_apply(R, sa, sb);
+        red_apply(R, sa, sb, sc);
         *R.cnt = 0u;
     }
+}
+__device__ __forceinline__ void red_finish(const Red& R, int blk, double va, double vb, double* sh) {
+    red_finish<2>(R, blk, va, vb, 0.0, sh);
 }
 
 // ----------------------------------------------------------------- PCG vector kernels
@@ -234,6 +281,111 @@ __global__ void __launch_bounds__(BLK) k_resid(const TO* __restrict__ b, const T
         s += d;
     }
     red_finish(R, blockIdx.x, v, s, sh);
+}
+
+// Solution read-out: out[rank] = in[cell] - S[S_XMEAN] (zero mean under the null space).
+template <class TI, class TO>
+__global__ void k_gather_shift(const TI* __restrict__ in, TO* __restrict__ out, const int32_t* __restrict__ leaf_cell,
+                               const double* __restrict__ S, int n) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n) out[r] = TO((double)in[leaf_cell[r]] - S[S_XMEAN]);
+}
+
+// ------------------------------------------------------- BiCGStab (adjoint system)
+// Right-preconditioned BiCGStab (van der Vorst 1992) over the tree cells; the scalars
+// alpha, beta, omega, rho live in S and are formed by the reductions (OP_BI_*).
+// p = r + beta (p - omega v); b32 = p (the cycle's right-hand side)
+template <class TO, class TB>
+__global__ void k_bi_p(TO* __restrict__ p, const TO* __restrict__ r, const TO* __restrict__ v,
+                       TB* __restrict__ b32, const double* __restrict__ S, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const TO pn = r[i] + TO(S[S_BETA]) * (p[i] - TO(S[S_OMEGA]) * v[i]);
+    p[i] = pn;
+    b32[i] = TB(pn);
+}
+
+// s = r - alpha v; b32 = s
+template <class TO, class TB>
+__global__ void k_bi_s(TO* __restrict__ s, const TO* __restrict__ r, const TO* __restrict__ v,
+                       TB* __restrict__ b32, const double* __restrict__ S, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const TO sn = r[i] - TO(S[S_ALPHA]) * v[i];
+    s[i] = sn;
+    b32[i] = TB(sn);
+}
+
+// (t, s) and (t, t)
+template <class TO>
+__global__ void __launch_bounds__(BLK) k_dot2(const TO* __restrict__ t, const TO* __restrict__ s, int n, Red R) {
+    __shared__ double sh[32];
+    double ts = 0.0, tt = 0.0;
+    for (int i = blockIdx.x * BLK + threadIdx.x; i < n; i += gridDim.x * BLK) {
+        const double ti = (double)t[i];
+        ts += ti * (double)s[i];
+        tt += ti * ti;
+    }
+    red_finish(R, blockIdx.x, ts, tt, sh);
+}
+
+// x += alpha ph + omega sh; r = s - omega t; reduces ||r||^2, sum(r), (rhat, r)
+template <class TO>
+__global__ void __launch_bounds__(BLK) k_bi_x(TO* __restrict__ x, TO* __restrict__ r, const TO* __restrict__ s,
+                                              const TO* __restrict__ t, const TO* __restrict__ ph,
+                                              const TO* __restrict__ shv, const TO* __restrict__ rhat, int n, Red R) {
+    __shared__ double sh[32];
+    const TO alpha = TO(R.S[S_ALPHA]), omega = TO(R.S[S_OMEGA]);
+    double rr = 0.0, rs = 0.0, rh = 0.0;
+    for (int i = blockIdx.x * BLK + threadIdx.x; i < n; i += gridDim.x * BLK) {
+        x[i] = x[i] + alpha * ph[i] + omega * shv[i];
+        const TO rn = s[i] - omega * t[i];
+        r[i] = rn;
+        const double rd = (double)rn;
+        rr += rd * rd;
+        rs += rd;
+        rh += (double)rhat[i] * rd;
+    }
+    red_finish<3>(R, blockIdx.x, rr, rs, rh, sh);
+}
+
+// ------------------------------------------------------------------ adjoint kernels
+// Y[row] += sum_e mult[e] beta[face[e]] X[col[e]] over the listed rows: the A^T - A part of
+// the transposed composite operator (non-zero only around T-junctions).
+template <class TO>
+__global__ void k_tcorr(int nrow, const int32_t* __restrict__ row, const int32_t* __restrict__ ptr,
+                        const int32_t* __restrict__ col, const int32_t* __restrict__ face,
+                        const double* __restrict__ mult, const float* __restrict__ beta, const TO* __restrict__ X,
+                        TO* __restrict__ Y) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nrow) return;
+    double acc = 0.0;
+    for (int e = ptr[q]; e < ptr[q + 1]; ++e) acc += mult[e] * (double)beta[face[e]] * (double)X[col[e]];
+    const int g = row[q];
+    Y[g] = TO((double)Y[g] + acc);
+}
+
+// dL/dbeta_f = -lambda^T (dA/dbeta_f) p per canonical face: -h (l_a - l_b)(p_a - p_b) for a
+// face between equal-depth leaves, -(h/2)(l_i - l_K)(pbar_P - p_K) for a T sub-face (fine
+// leaf i = a, coarser leaf K = b, P = parent of i whose P entry holds the child mean).
+__global__ void k_face_grad(int nface, const int32_t* __restrict__ fa, const int32_t* __restrict__ fb,
+                            const int32_t* __restrict__ fp, const double* __restrict__ fh,
+                            const double* __restrict__ P, const double* __restrict__ Lm, double* __restrict__ out) {
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nface) return;
+    const int a = fa[f], b = fb[f], par = fp[f];
+    const double dl = Lm[a] - Lm[b];
+    out[f] = par < 0 ? -fh[f] * dl * (P[a] - P[b]) : -0.5 * fh[f] * dl * (P[par] - P[b]);
+}
+
+// sum of x over the leaves (flags bit 0), into the second slot of R
+__global__ void __launch_bounds__(BLK) k_leafsum(const double* __restrict__ x, const uint8_t* __restrict__ flags,
+                                                 int n, Red R) {
+    __shared__ double sh[32];
+    double v = 0.0;
+    for (int i = blockIdx.x * BLK + threadIdx.x; i < n; i += gridDim.x * BLK)
+        if (flags[i] & 1) v += x[i];
+    red_finish(R, blockIdx.x, 0.0, v, sh);
 }
 
 template <class TO, class TZ>

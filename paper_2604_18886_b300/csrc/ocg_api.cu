@@ -161,9 +161,40 @@ struct ocg_octree {
     }
     Tables tables() const { return Tables{nbr, oct_parent, child_oct, trec, (int)H.noct, (int)H.nt}; }
     LevelArgs largs(int m) const { return LevelArgs{(int)H.L(m).off, (int)H.L(m).ncell, H.L(m).ni}; }
+
+    // adjoint tables (topology only), built on first use
+    mutable std::mutex adj_mu;
+    mutable bool adj_ready = false;
+    mutable int tc_nrow = 0;
+    mutable int32_t *tc_row = nullptr, *tc_ptr = nullptr, *tc_col = nullptr, *tc_face = nullptr;
+    mutable double* tc_mult = nullptr;
+    mutable int32_t *fg_a = nullptr, *fg_b = nullptr, *fg_p = nullptr;
+    mutable double* fg_h = nullptr;
+    void upload_adjoint() const {
+        std::lock_guard<std::mutex> lk(adj_mu);
+        if (adj_ready) return;
+        TransposeCorrection tc;
+        build_transpose_correction(H, tc);
+        tc_nrow = (int)tc.row.size();
+        tc_row = dupload(tc.row);
+        tc_ptr = dupload(tc.ptr);
+        tc_col = dupload(tc.col);
+        tc_face = dupload(tc.face);
+        tc_mult = dupload(tc.mult);
+        std::vector<int32_t> a, b, pp;
+        std::vector<double> hh;
+        build_face_grad_tables(H, a, b, pp, hh);
+        fg_a = dupload(a);
+        fg_b = dupload(b);
+        fg_p = dupload(pp);
+        fg_h = dupload(hh);
+        adj_ready = true;
+    }
     ~ocg_octree() {
         dfree(nbr); dfree(oct_parent); dfree(child_oct); dfree(trec); dfree(leaf_cell);
         dfree(flags); dfree(level); dfree(fslot); dfree(fkind); dfree(fdepth);
+        dfree(tc_row); dfree(tc_ptr); dfree(tc_col); dfree(tc_face); dfree(tc_mult);
+        dfree(fg_a); dfree(fg_b); dfree(fg_p); dfree(fg_h);
     }
 };
 
@@ -206,18 +237,24 @@ struct ocg_hier {
     int* tail_sched = nullptr;    // device copies of the tail pass schedules (float, double)
     int* tail_sched2 = nullptr;
     cudaStream_t cap = nullptr;   // private stream for graph capture
-    GraphSolve graphs[3][2];      // [precision][null space]
+    GraphSolve graphs[2][3][2];   // [transpose][precision][null space]
+    float* beta = nullptr;        // copy of the face fractions (transposed operator)
+    // BiCGStab vectors over the tree cells (adjoint solves), allocated on first use
+    double *rhat = nullptr, *s = nullptr, *tv = nullptr, *ph = nullptr, *sh = nullptr;
 
     Coefs<double, double> C64() const { return {c64[0], c64[1], c64[2], c64[3], tw64}; }
     Coefs<float, float> C32() const { return {c32[0], c32[1], c32[2], c32[3], tw32}; }
     Coefs<__nv_bfloat16, float> C16() const { return {c16[0], c16[1], c16[2], c16[3], tw32}; }
 
     ~ocg_hier() {
-        for (auto& row : graphs)
-            for (auto& gs : row) {
-                if (gs.exec) cudaGraphExecDestroy(gs.exec);
-                if (gs.graph) cudaGraphDestroy(gs.graph);
-            }
+        for (auto& tr : graphs)
+            for (auto& row : tr)
+                for (auto& gs : row) {
+                    if (gs.exec) cudaGraphExecDestroy(gs.exec);
+                    if (gs.graph) cudaGraphDestroy(gs.graph);
+                }
+        for (double* v : {rhat, s, tv, ph, sh}) dfree(v);
+        dfree(beta);
         if (cap) cudaStreamDestroy(cap);
         for (int i = 0; i < 4; ++i) { dfree(c64[i]); dfree(c32[i]); dfree(c16[i]); }
         dfree(tw64); dfree(tw32); dfree(S); dfree(part); dfree(cnt); dfree(tail_sched); dfree(tail_sched2);
@@ -528,6 +565,20 @@ void apply_outer(ocg_hier* h, Coefs<TC, TW> C, TO* P, TO* Y, int op, Ctx& c) {
     ck_launch("apply");
 }
 
+// Y = A^T P on the leaves: A P, then the A^T - A rows around the T-junctions.
+template <class TO, class TC, class TW>
+void apply_outer_T(ocg_hier* h, Coefs<TC, TW> C, TO* P, TO* Y, Ctx& c) {
+    const ocg_octree* t = h->t;
+    apply_outer<TO, TC, TW>(h, C, P, Y, OP_NONE, c);
+    if (t->tc_nrow > 0) {
+        launch(c, -1, 0, t->tc_nrow, [&] {
+            k_tcorr<TO><<<nblk(t->tc_nrow), BLK, 0, c.st>>>(t->tc_nrow, t->tc_row, t->tc_ptr, t->tc_col, t->tc_face,
+                                                           t->tc_mult, h->beta, P, Y);
+        });
+        ck_launch("apply_T correction");
+    }
+}
+
 // ------------------------------------------------------------------ PCG (Alg. 1)
 // The loop is split so that a WHILE body holds exactly one iteration:
 //   begin:  r = b; ||b|| (null-space shift); z = M r; rho = (r, z); p = z; half_a
@@ -535,6 +586,17 @@ void apply_outer(ocg_hier* h, Coefs<TC, TW> C, TO* P, TO* Y, int op, Ctx& c) {
 //   half_a: Ap = A p, alpha; x += alpha p, r -= alpha Ap; ||r|| test (sets the condition)
 //   half_b: z = M r; beta; p = z + beta p
 //   finish: true residual ||b - A x|| in FP64
+// S[S_XMEAN] = mean of the solution over the leaves (xt holds it in FP64; inner cells 0).
+// The averaging pass of the true-residual apply wrote child means into xt's inner cells,
+// so the sum runs over leaves through the flags.
+void solution_mean(ocg_hier* h, Ctx& c, const double* xt) {
+    const int n = (int)h->t->H.ntree;
+    const unsigned rb = std::min<unsigned>(nblk(n), (unsigned)h->red_blocks);
+    launch(c, -1, 0, n, [&] {
+        k_leafsum<<<rb, BLK, 0, c.st>>>(xt, h->t->flags, n, make_red(h, rb, OP_XMEAN));
+    });
+}
+
 template <class TO, class TV, class TC, class TW>
 struct Pcg {
     ocg_hier* h;
@@ -591,18 +653,107 @@ struct Pcg {
         launch(c, -1, 0, n(), [&] { k_pupdate<TO, TV><<<gb(), BLK, 0, c.st>>>(p(), U(), h->S, n(), 0); });
         ck_launch("half_b");
     }
+    void body() {
+        half_b();
+        half_a();
+    }
     void finish() {
         launch(c, -1, 0, n(), [&] { k_cast<TO, double><<<gb(), BLK, 0, c.st>>>(x(), h->xt, n()); });
         apply_outer<double, TC, TW>(h, Co, h->xt, h->yt, OP_NONE, c);
         launch(c, -1, 0, n(), [&] {
             k_resid<double><<<rb(), BLK, 0, c.st>>>(h->bt, h->yt, h->t->flags, n(), make_red(h, rb(), OP_TRUE));
         });
+        if (ns) solution_mean(h, c, h->xt);
         ck_launch("finish");
     }
 };
 
-// Capture begin; WHILE(not converged) { half_b; half_a }; finish into one graph.
+// ------------------------------------------------------- BiCGStab (adjoint system)
+// Solves A^T x = b, right-preconditioned by the same mu-cycle (the cycle approximates
+// A^{-1}; Alg. 1 with it stagnates on A^T because A is not symmetric at T-junctions).
+//   begin: r = rhat = b (null-space shift), rho = (rhat, r), condition
+//   body:  p = r + beta (p - omega v); ph = M p; v = A^T ph; alpha = rho / (rhat, v);
+//          s = r - alpha v; sh = M s; t = A^T sh; omega = (t, s) / (t, t);
+//          x += alpha ph + omega sh; r = s - omega t; ||r|| test, rho, beta
+//   finish: true residual ||b - A^T x|| in FP64
 template <class TO, class TV, class TC, class TW>
+struct BiCG {
+    ocg_hier* h;
+    Coefs<TC, TW> Co;
+    bool ns;
+    Ctx& c;
+    cudaGraphConditionalHandle cond;
+    int set_cond;
+
+    const HostTree& H() const { return h->t->H; }
+    TO* V(double* p) { return (TO*)p; }
+    TV* U() { return (TV*)h->U; }
+    TV* B() { return (TV*)h->B; }
+    int n() const { return (int)H().ntree; }
+    unsigned gb() const { return nblk(H().ntree); }
+    unsigned rb() const { return std::min<unsigned>(nblk(H().ntree), (unsigned)h->red_blocks); }
+    void zero(void* ptr, size_t bytes) { ck(cudaMemsetAsync(ptr, 0, bytes, c.st), "memset"); }
+
+    void begin() {
+        zero(h->x, n() * sizeof(TO));
+        zero(h->p, n() * sizeof(TO));
+        zero(h->Ap, n() * sizeof(TO));
+        zero(h->B, H().ncell * sizeof(TV));
+        TO* r = V(h->r);
+        launch(c, -1, 0, n(), [&] { k_cast<double, TO><<<gb(), BLK, 0, c.st>>>(h->bt, r, n()); });
+        launch(c, -1, 0, n(), [&] { k_dot<TO, TO, true><<<rb(), BLK, 0, c.st>>>(r, r, n(), make_red(h, rb(), OP_BB)); });
+        if (ns)
+            launch(c, -1, 0, n(), [&] {
+                k_project<TO, TV><<<gb(), BLK, 0, c.st>>>(r, h->t->flags, h->S, (TV*)nullptr, n());
+            });
+        launch(c, -1, 0, n(), [&] { k_cast<TO, TO><<<gb(), BLK, 0, c.st>>>(r, V(h->rhat), n()); });
+        launch(c, -1, 0, n(), [&] {
+            k_dot<TO, TO, false><<<rb(), BLK, 0, c.st>>>(V(h->rhat), r, n(), make_red(h, rb(), OP_BI_INIT, cond, set_cond));
+        });
+        ck_launch("bicg begin");
+    }
+    void precondition(TO* out) {
+        zero(h->U, H().ntree * sizeof(TV));
+        Cycle<TV>{h, U(), B(), c}.run();
+        launch(c, -1, 0, n(), [&] { k_cast<TV, TO><<<gb(), BLK, 0, c.st>>>(U(), out, n()); });
+    }
+    void body() {
+        TO *r = V(h->r), *p = V(h->p), *v = V(h->Ap), *s = V(h->s), *t = V(h->tv), *ph = V(h->ph), *sh = V(h->sh);
+        launch(c, -1, 0, n(), [&] { k_bi_p<TO, TV><<<gb(), BLK, 0, c.st>>>(p, r, v, B(), h->S, n()); });
+        precondition(ph);
+        apply_outer_T<TO, TC, TW>(h, Co, ph, v, c);
+        launch(c, -1, 0, n(), [&] {
+            k_dot<TO, TO, false><<<rb(), BLK, 0, c.st>>>(V(h->rhat), v, n(), make_red(h, rb(), OP_BI_ALPHA));
+        });
+        launch(c, -1, 0, n(), [&] { k_bi_s<TO, TV><<<gb(), BLK, 0, c.st>>>(s, r, v, B(), h->S, n()); });
+        precondition(sh);
+        apply_outer_T<TO, TC, TW>(h, Co, sh, t, c);
+        launch(c, -1, 0, n(), [&] { k_dot2<TO><<<rb(), BLK, 0, c.st>>>(t, s, n(), make_red(h, rb(), OP_BI_OMEGA)); });
+        launch(c, -1, 0, n(), [&] {
+            k_bi_x<TO><<<rb(), BLK, 0, c.st>>>(V(h->x), r, s, t, ph, sh, V(h->rhat), n(),
+                                               make_red(h, rb(), OP_BI_RR, cond, set_cond));
+        });
+        if (ns)
+            launch(c, -1, 0, n(), [&] {
+                k_project<TO, TV><<<gb(), BLK, 0, c.st>>>(r, h->t->flags, h->S, (TV*)nullptr, n());
+            });
+        ck_launch("bicg body");
+    }
+    void finish() {
+        launch(c, -1, 0, n(), [&] { k_cast<TO, double><<<gb(), BLK, 0, c.st>>>(V(h->x), h->xt, n()); });
+        apply_outer_T<double, TC, TW>(h, Co, h->xt, h->yt, c);
+        launch(c, -1, 0, n(), [&] {
+            k_resid<double><<<rb(), BLK, 0, c.st>>>(h->bt, h->yt, h->t->flags, n(), make_red(h, rb(), OP_TRUE));
+        });
+        if (ns) solution_mean(h, c, h->xt);
+        ck_launch("bicg finish");
+    }
+};
+
+// Capture begin; WHILE(not converged) { body }; finish into one graph.  Solver is Pcg or
+// BiCG (both: begin / body / finish, the reduction that ends each of begin and body sets
+// the WHILE condition).
+template <template <class, class, class, class> class Solver, class TO, class TV, class TC, class TW>
 void build_graph(ocg_hier* h, Coefs<TC, TW> Co, bool ns, GraphSolve& gs) {
     if (!h->cap) ck(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking), "cudaStreamCreate");
     cudaStream_t cs = h->cap;
@@ -614,7 +765,7 @@ void build_graph(ocg_hier* h, Coefs<TC, TW> Co, bool ns, GraphSolve& gs) {
         ck(cudaStreamGetCaptureInfo(cs, &stt, nullptr, &g, nullptr, nullptr, nullptr), "capture info");
         cudaGraphConditionalHandle cond;
         ck(cudaGraphConditionalHandleCreate(&cond, g, 0, 0), "conditional handle");
-        Pcg<TO, TV, TC, TW> pc{h, Co, ns, c, cond, 1};
+        Solver<TO, TV, TC, TW> pc{h, Co, ns, c, cond, 1};
         pc.begin();
         const cudaGraphNode_t* deps = nullptr;
         size_t ndeps = 0;
@@ -638,9 +789,8 @@ void build_graph(ocg_hier* h, Coefs<TC, TW> Co, bool ns, GraphSolve& gs) {
         Ctx cb{cs, nullptr, 0};
         ck(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal),
            "begin body capture");
-        Pcg<TO, TV, TC, TW> pb{h, Co, ns, cb, cond, 1};
-        pb.half_b();
-        pb.half_a();
+        Solver<TO, TV, TC, TW> pb{h, Co, ns, cb, cond, 1};
+        pb.body();
         cudaGraph_t bg = nullptr;
         ck(cudaStreamEndCapture(cs, &bg), "end body capture");
         gs.body_kernels = cb.count;
@@ -664,17 +814,25 @@ void ensure_work(ocg_hier* h) {
     h->B = dalloc<double>(H.ncell);
     h->S = dalloc<double>(S_COUNT);
     ck(cudaMallocHost((void**)&h->hS, S_COUNT * sizeof(double)), "cudaMallocHost");
-    h->part = dalloc<double>(2 * ((int64_t)nblk(n) + H.D + 8));
+    h->part = dalloc<double>(3 * ((int64_t)nblk(n) + H.D + 8));
     h->cnt = dalloc<unsigned>(1);
     ck(cudaMemset(h->cnt, 0, sizeof(unsigned)), "memset");
     ck(cudaMemset(h->S, 0, S_COUNT * sizeof(double)), "memset");
 }
 
-template <class TO, class TV, class TC, class TW>
-int pcg_solve(ocg_hier* h, Coefs<TC, TW> Co, int prec, const double* b_user, double* x_user,
-              const ocg_solve_params* sp, ocg_solve_stats* stats, cudaStream_t st) {
+void ensure_bicg(ocg_hier* h) {
+    h->t->upload_adjoint();
+    if (h->rhat) return;
+    const int64_t n = h->t->H.ntree;
+    for (double** v : {&h->rhat, &h->s, &h->tv, &h->ph, &h->sh}) *v = dalloc<double>(n);
+}
+
+template <template <class, class, class, class> class Solver, class TO, class TV, class TC, class TW>
+int krylov_solve(ocg_hier* h, Coefs<TC, TW> Co, int prec, const double* b_user, double* x_user,
+                 const ocg_solve_params* sp, ocg_solve_stats* stats, cudaStream_t st) {
     const ocg_octree* t = h->t;
     const HostTree& H = t->H;
+    const bool transpose = (sp->flags & OCG_SOLVE_TRANSPOSE) != 0;
     const bool ns = sp->nullspace < 0 ? h->ns_auto : sp->nullspace != 0;
     const bool eager = (sp->flags & OCG_SOLVE_EAGER) || h->probe.kind != OCG_PROBE_OFF;
     // scalars: tolerance, iteration cap, null-space flag, counters
@@ -690,25 +848,30 @@ int pcg_solve(ocg_hier* h, Coefs<TC, TW> Co, int prec, const double* b_user, dou
     });
     ck_launch("scatter");
     int64_t kernels = c.count;
+    GraphSolve& gs = h->graphs[transpose ? 1 : 0][prec][ns ? 1 : 0];
     if (eager) {
-        Pcg<TO, TV, TC, TW> pc{h, Co, ns, c, 0, 0};
+        Solver<TO, TV, TC, TW> pc{h, Co, ns, c, 0, 0};
         pc.begin();
         while (true) {
             ck(cudaMemcpyAsync(h->hS, h->S, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, st), "copy scalars");
             ck(cudaStreamSynchronize(st), "stream sync");
             if (h->hS[S_DONE] != 0.0) break;
-            pc.half_b();
-            pc.half_a();
+            pc.body();
         }
         pc.finish();
         kernels = c.count;
     } else {
-        GraphSolve& gs = h->graphs[prec][ns ? 1 : 0];
-        if (!gs.exec) build_graph<TO, TV, TC, TW>(h, Co, ns, gs);
+        if (!gs.exec) build_graph<Solver, TO, TV, TC, TW>(h, Co, ns, gs);
         ck(cudaGraphLaunch(gs.exec, st), "graph launch");
     }
+    // the solution is read from xt (FP64 copy of x made by finish), shifted to zero mean
+    // under the null space
     launch(c, -1, 0, H.nleaf, [&] {
-        k_gather<TO, double><<<nblk(H.nleaf), BLK, 0, st>>>((const TO*)h->x, x_user, t->leaf_cell, (int)H.nleaf);
+        if (ns)
+            k_gather_shift<double, double><<<nblk(H.nleaf), BLK, 0, st>>>(h->xt, x_user, t->leaf_cell, h->S,
+                                                                         (int)H.nleaf);
+        else
+            k_gather<double, double><<<nblk(H.nleaf), BLK, 0, st>>>(h->xt, x_user, t->leaf_cell, (int)H.nleaf);
     });
     ck_launch("gather");
     ck(cudaMemcpyAsync(h->hS, h->S, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, st), "copy scalars");
@@ -716,8 +879,10 @@ int pcg_solve(ocg_hier* h, Coefs<TC, TW> Co, int prec, const double* b_user, dou
     const double* S = h->hS;
     const int k = (int)S[S_K];
     if (!eager) {
-        const GraphSolve& gs = h->graphs[prec][ns ? 1 : 0];
-        kernels = c.count + gs.outer_kernels + (int64_t)std::max(k - 1, 0) * gs.body_kernels;
+        // PCG's begin ends with the first half iteration, so its WHILE body runs k - 1
+        // times; BiCGStab's body runs k times
+        const int64_t body_runs = transpose ? k : std::max(k - 1, 0);
+        kernels = c.count + gs.outer_kernels + body_runs * gs.body_kernels;
     } else {
         kernels = c.count;
     }
@@ -737,7 +902,7 @@ int pcg_solve(ocg_hier* h, Coefs<TC, TW> Co, int prec, const double* b_user, dou
         return OCG_ENAN;
     }
     if (!conv) {
-        g_err = "PCG reached max_iter before the tolerance";
+        g_err = "Krylov loop reached max_iter before the tolerance";
         return OCG_ENOTCONV;
     }
     return OCG_OK;
@@ -918,6 +1083,9 @@ int ocg_setup_hierarchy(const ocg_octree* t, const float* beta, const int32_t bc
             h->tw64 = nullptr;
         }
         ensure_work(h.get());
+        h->beta = dalloc<float>(H.nface);
+        if (H.nface > 0)
+            ck(cudaMemcpyAsync(h->beta, beta, H.nface * sizeof(float), cudaMemcpyDeviceToDevice, st), "copy beta");
         choose_tail(h.get(), 0, sizeof(float));
         choose_tail(h.get(), 1, sizeof(double));
         const int nlev = H.D - H.mc + 1;
@@ -978,7 +1146,8 @@ int ocg_hier_tuning(const ocg_hier* h, int32_t m, int32_t* form, double* us_octe
 int ocg_apply_A(ocg_hier* h, int32_t dtype, const void* x, void* y, int32_t transpose, void* stream) {
     return guard([&] {
         if (!h || !x || !y) throw Status(OCG_EINVAL, "null argument");
-        if (transpose) throw Status(OCG_EINVAL, "transpose is not available in this version");
+        if (transpose != 0 && transpose != 1) throw Status(OCG_EINVAL, "transpose must be 0 or 1");
+        if (transpose) h->t->upload_adjoint();
         cudaStream_t st = (cudaStream_t)stream;
         const ocg_octree* t = h->t;
         const HostTree& H = t->H;
@@ -993,7 +1162,8 @@ int ocg_apply_A(ocg_hier* h, int32_t dtype, const void* x, void* y, int32_t tran
             launch(c, -1, 0, H.nleaf, [&] {
                 k_scatter<TO, TO><<<nblk(H.nleaf), BLK, 0, st>>>((const TO*)x, P, t->leaf_cell, (int)H.nleaf);
             });
-            apply_outer<TO, TC, TW>(h, C, P, Y, OP_NONE, c);
+            if (transpose) apply_outer_T<TO, TC, TW>(h, C, P, Y, c);
+            else apply_outer<TO, TC, TW>(h, C, P, Y, OP_NONE, c);
             launch(c, -1, 0, H.nleaf, [&] {
                 k_gather<TO, TO><<<nblk(H.nleaf), BLK, 0, st>>>(Y, (TO*)y, t->leaf_cell, (int)H.nleaf);
             });
@@ -1047,25 +1217,68 @@ int ocg_vcycle(ocg_hier* h, int32_t dtype, const void* r, void* z, void* stream)
     });
 }
 
+int ocg_face_grad(ocg_hier* h, const double* p, const double* lambda, double* dbeta, void* stream) {
+    return guard([&] {
+        if (!h || !p || !lambda || !dbeta) throw Status(OCG_EINVAL, "null argument");
+        const ocg_octree* t = h->t;
+        const HostTree& H = t->H;
+        if (H.nface == 0) return;
+        t->upload_adjoint();
+        cudaStream_t st = (cudaStream_t)stream;
+        Ctx c{st, nullptr, 0};
+        // p into the tree cells with child means on inner cells (the pbar of Sec. 3.1),
+        // lambda into the tree cells
+        ck(cudaMemsetAsync(h->xt, 0, H.ntree * sizeof(double), st), "memset");
+        ck(cudaMemsetAsync(h->yt, 0, H.ntree * sizeof(double), st), "memset");
+        launch(c, -1, 0, H.nleaf, [&] {
+            k_scatter<double, double><<<nblk(H.nleaf), BLK, 0, st>>>(p, h->xt, t->leaf_cell, (int)H.nleaf);
+        });
+        launch(c, -1, 0, H.nleaf, [&] {
+            k_scatter<double, double><<<nblk(H.nleaf), BLK, 0, st>>>(lambda, h->yt, t->leaf_cell, (int)H.nleaf);
+        });
+        for (int m = H.D; m >= 1; --m) {
+            const LevelArgs A = t->largs(m);
+            launch(c, -1, m, A.ncell, [&] {
+                if (h->c64[0])
+                    k_oavg<double, double><<<nblk(A.ncell / 8, OBLK), OBLK, 0, st>>>(A, t->tables(), h->c64[0], h->xt);
+                else
+                    k_oavg<double, float><<<nblk(A.ncell / 8, OBLK), OBLK, 0, st>>>(A, t->tables(), h->c32[0], h->xt);
+            });
+        }
+        launch(c, -1, 0, H.nface, [&] {
+            k_face_grad<<<nblk(H.nface), BLK, 0, st>>>((int)H.nface, t->fg_a, t->fg_b, t->fg_p, t->fg_h, h->xt, h->yt,
+                                                      dbeta);
+        });
+        ck_launch("face_grad");
+        g_launches += c.count;
+    });
+}
+
 int ocg_pcg_solve(ocg_hier* h, const double* b, double* x, const ocg_solve_params* sp, ocg_solve_stats* stats,
                   void* stream) {
     int status = OCG_OK;
     int g = guard([&] {
         if (!h || !b || !x || !sp || !stats) throw Status(OCG_EINVAL, "null argument");
         if (!(sp->tol > 0) || sp->max_iter < 1) throw Status(OCG_EINVAL, "tol must be > 0 and max_iter >= 1");
+        if (sp->flags & ~(OCG_SOLVE_EAGER | OCG_SOLVE_TRANSPOSE)) throw Status(OCG_EINVAL, "unknown solve flags");
         cudaStream_t st = (cudaStream_t)stream;
+        const bool tr = (sp->flags & OCG_SOLVE_TRANSPOSE) != 0;
+        if (tr) ensure_bicg(h);
         switch (sp->precision) {
             case OCG_PREC_FP64:
                 if (!h->c64[0]) throw Status(OCG_EINVAL, "FP64 solve needs coef_dtype F64");
-                status = pcg_solve<double, double>(h, h->C64(), 0, b, x, sp, stats, st);
+                status = tr ? krylov_solve<BiCG, double, double>(h, h->C64(), 0, b, x, sp, stats, st)
+                            : krylov_solve<Pcg, double, double>(h, h->C64(), 0, b, x, sp, stats, st);
                 break;
             case OCG_PREC_FP32:
                 if (!h->c32[0]) throw Status(OCG_EINVAL, "FP32 solve needs coef_dtype F32");
-                status = pcg_solve<float, float>(h, h->C32(), 1, b, x, sp, stats, st);
+                status = tr ? krylov_solve<BiCG, float, float>(h, h->C32(), 1, b, x, sp, stats, st)
+                            : krylov_solve<Pcg, float, float>(h, h->C32(), 1, b, x, sp, stats, st);
                 break;
             case OCG_PREC_MIXED:
                 if (!h->c32[0]) throw Status(OCG_EINVAL, "mixed solve needs coef_dtype F32");
-                status = pcg_solve<double, float>(h, h->C32(), 2, b, x, sp, stats, st);
+                status = tr ? krylov_solve<BiCG, double, float>(h, h->C32(), 2, b, x, sp, stats, st)
+                            : krylov_solve<Pcg, double, float>(h, h->C32(), 2, b, x, sp, stats, st);
                 break;
             default:
                 throw Status(OCG_EINVAL, "precision");

@@ -124,7 +124,8 @@ class Hierarchy:
             beta = torch.from_numpy(np.ascontiguousarray(beta, np.float32)).cuda()
         assert beta.dtype == torch.float32 and beta.is_cuda and beta.numel() == tree.n_faces
         self._beta = beta
-        bcv = (C.c_int32 * 6)(*[int(v) for v in bc])
+        self._bc = tuple(int(v) for v in bc)
+        bcv = (C.c_int32 * 6)(*self._bc)
         self._h = C.c_void_p()
         st = C.c_void_p(stream.cuda_stream if stream is not None else torch.cuda.current_stream().cuda_stream)
         L.check(lib.ocg_setup_hierarchy(tree.handle, L.ptr(beta), bcv, C.byref(self.prm), st,
@@ -161,12 +162,27 @@ class Hierarchy:
         s = stream if stream is not None else torch.cuda.current_stream()
         return C.c_void_p(s.cuda_stream)
 
-    def apply_A(self, x, stream=None):
+    def apply_A(self, x, stream=None, transpose=False):
+        """y = A x (or A^T x) of the composite leaf operator."""
         import torch
         y = torch.empty_like(x)
         dt = L.OCG_F64 if x.dtype == torch.float64 else L.OCG_F32
-        L.check(L.lib().ocg_apply_A(self._h, dt, L.ptr(x), L.ptr(y), 0, self._stream(stream)))
+        L.check(L.lib().ocg_apply_A(self._h, dt, L.ptr(x), L.ptr(y), 1 if transpose else 0,
+                                    self._stream(stream)))
         return y
+
+    @property
+    def nullspace(self):
+        """True when every wall is Neumann (constant null space, zero-mean solutions)."""
+        return all(int(v) == 0 for v in self._bc)
+
+    def face_grad(self, p, lam, stream=None):
+        """dL/dbeta per canonical face from the solution p and the adjoint solution lam."""
+        import torch
+        assert p.dtype == torch.float64 and lam.dtype == torch.float64
+        out = torch.empty(self.tree.n_faces, dtype=torch.float64, device=p.device)
+        L.check(L.lib().ocg_face_grad(self._h, L.ptr(p), L.ptr(lam), L.ptr(out), self._stream(stream)))
+        return out
 
     def vcycle(self, r, stream=None):
         import torch
@@ -176,14 +192,16 @@ class Hierarchy:
         return z
 
     def solve(self, b, x=None, tol=1e-6, max_iter=100, precision="mixed", nullspace=-1,
-              stream=None, raise_on_notconv=True, eager=False):
+              stream=None, raise_on_notconv=True, eager=False, transpose=False):
+        """x with A x = b (PCG, Alg. 1), or A^T x = b with transpose=True (BiCGStab, the
+        adjoint system).  Returns (x, stats)."""
         import torch
         assert b.dtype == torch.float64 and b.is_cuda
         if x is None:
             x = torch.empty_like(b)
         sp = L.SolveParams()
         sp.tol, sp.max_iter, sp.precision, sp.nullspace = tol, max_iter, PRECISIONS[precision], nullspace
-        sp.flags = L.OCG_SOLVE_EAGER if eager else 0
+        sp.flags = (L.OCG_SOLVE_EAGER if eager else 0) | (L.OCG_SOLVE_TRANSPOSE if transpose else 0)
         st = L.SolveStats()
         code = L.lib().ocg_pcg_solve(self._h, L.ptr(b), L.ptr(x), C.byref(sp), C.byref(st),
                                      self._stream(stream))

@@ -1,0 +1,162 @@
+"""GPU parity of the adjoint path (transposed operator, BiCGStab transpose solve, face
+gradient, autograd wrapper) against the FP64 oracle, and the gradient against central
+finite differences at the full two-level workload size.
+
+Tolerances as in test_gpu_parity: FP64 applies 1e-12, FP32 applies 1e-6 relative to the
+vector's max norm; FP64 Krylov iterates 1e-8 (BiCGStab's two-sided recurrences amplify
+rounding-order differences more than CG's).  Finite differences: 1e-4 relative to the
+largest sampled gradient (spec bar).
+"""
+import numpy as np
+import pytest
+
+from oracle import adjoint as ADJ
+from oracle import pcg
+from paper_2604_18886_b300 import problems as P
+from paper_2604_18886_b300 import solver as S
+
+from test_gpu_parity import CASES, build, cuda, rel
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+NAMES = ["c2_16", "c2_16_neumann", "c3_16_d2", "c4_t1", "band_12_d2"]
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_transposed_apply_matches_oracle(name):
+    t, H, g, gh, f, beta = build(CASES[name](), "f64")
+    x = P.random_vector(t.n_leaves, 21)
+    AT = H.A.T.tocsr()
+    y = gh.apply_A(cuda(x), transpose=True).cpu().numpy()
+    assert rel(y, AT @ x) <= 1e-12
+    # A^T differs from A exactly where T-junctions are
+    yf = gh.apply_A(cuda(x)).cpu().numpy()
+    assert rel(yf, H.A @ x) <= 1e-12
+    t, H, g, gh, f, beta = build(CASES[name](), "f32")
+    x32 = x.astype(np.float32)
+    y32 = gh.apply_A(cuda(x32, torch.float32), transpose=True).double().cpu().numpy()
+    assert rel(y32, AT @ x32.astype(np.float64)) <= 1e-6
+
+
+@pytest.mark.parametrize("name", ["c2_16", "c2_16_neumann", "c3_16_d2", "c4_t1"])
+def test_bicgstab_fp64_follows_oracle_iterates(name):
+    t, H, g, gh, f, beta = build(CASES[name](), "f64")
+    rhs = P.random_vector(t.n_leaves, 22)
+    xo, ko, ho = pcg.bicgstab(H, rhs, tol=1e-8, transpose=True)
+    x, st = gh.solve(cuda(rhs), tol=1e-8, precision="fp64", transpose=True)
+    assert st.converged and st.iterations == ko
+    hist = [st.hist[i] for i in range(st.iterations + 1)]
+    assert np.allclose(hist, ho, rtol=1e-6, atol=0)
+    if H.nullspace:
+        xo = xo - xo.mean()
+    assert rel(x.cpu().numpy(), xo) <= 1e-8
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp32"])
+@pytest.mark.parametrize("name", ["c2_16", "c2_16_neumann", "c3_16_d2", "c4_t1"])
+def test_transpose_solution_within_1e5(name, precision):
+    t, H, g, gh, f, beta = build(CASES[name](), "f32")
+    rhs = P.random_vector(t.n_leaves, 23)
+    ref = ADJ.solve(H, rhs, transpose=True, tol=1e-12)
+    xo, ko, _ = pcg.bicgstab(H, rhs, tol=1e-6, transpose=True)
+    if H.nullspace:
+        xo = xo - xo.mean()
+    x, st = gh.solve(cuda(rhs), tol=1e-6, precision=precision, transpose=True)
+    x = x.cpu().numpy()
+    assert st.converged and st.rel_res <= 1e-6 and abs(st.iterations - ko) <= 1
+    if H.nullspace:
+        assert abs(x.mean()) <= 1e-12 * np.abs(x).max()
+    assert rel(x, ref) <= 1.5 * rel(xo, ref) + 1e-5, (rel(x, ref), rel(xo, ref))
+    if precision == "mixed":
+        assert st.true_rel_res <= 1.5e-6
+        x9, st9 = gh.solve(cuda(rhs), tol=1e-9, precision="mixed", transpose=True)
+        assert st9.converged and st9.true_rel_res <= 2e-9
+        assert rel(x9.cpu().numpy(), ref) <= 1e-5
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_face_grad_matches_oracle(name):
+    t, H, g, gh, f, beta = build(CASES[name](), "f32")
+    p = P.random_vector(t.n_leaves, 24)
+    lam = P.random_vector(t.n_leaves, 25)
+    ref = ADJ.face_grad(H, p, lam)
+    out = gh.face_grad(cuda(p), cuda(lam)).cpu().numpy()
+    assert out.shape == ref.shape
+    assert rel(out, ref) <= 1e-12
+
+
+def test_graph_and_eager_transpose_solves_agree():
+    t, H, g, gh, f, beta = build(CASES["c3_16_d2"](), "f32")
+    rhs = cuda(P.random_vector(t.n_leaves, 26))
+    xg, sg = gh.solve(rhs, tol=1e-6, precision="mixed", transpose=True)
+    xe, se = gh.solve(rhs, tol=1e-6, precision="mixed", transpose=True, eager=True)
+    assert torch.equal(xg, xe) and sg.iterations == se.iterations and sg.kernels == se.kernels
+
+
+@pytest.mark.parametrize("name", ["c2_16", "c3_16_d2"])
+def test_autograd_matches_oracle_gradients(name):
+    from paper_2604_18886_b300.autograd import poisson_solve
+    p = CASES[name]()
+    t, H, g, gh, f, beta = build(p, "f32")
+    b = P.rhs(p, t.leaves, f, beta)
+    pt = P.random_vector(t.n_leaves, 2)
+    x_o, lam_o, gb_o, gbeta_o = ADJ.gradients(H, b, pt)
+    bt = cuda(b).requires_grad_(True)
+    betat = cuda(beta, torch.float32).requires_grad_(True)
+    x = poisson_solve(bt, betat, g, p.bc, tol=1e-10, precision="mixed")
+    loss = 0.5 * ((x - cuda(pt)) ** 2).sum()
+    loss.backward()
+    assert rel(x.detach().cpu().numpy(), x_o) <= 1e-5
+    assert rel(bt.grad.cpu().numpy(), gb_o) <= 1e-5
+    assert rel(betat.grad.double().cpu().numpy(), gbeta_o) <= 1e-5
+
+
+def test_gradient_matches_central_differences_full_size():
+    # the two-level workload (64^3 root, ball r = 0.25 refined once): L = 1/2 ||p - p_t||^2,
+    # p_t ~ N(0,1) (seed 2); 64 interior faces drawn with seed 3, both regular and T
+    # sub-faces; FP64 solves to 1e-12; L+ - L- = 1/2 <p+ - p-, p+ + p- - 2 p_t>
+    p = P.c2(64)
+    g = S.Octree(p.desc)
+    fc = g.faces()
+    beta = P.face_beta(p, fc)
+    lv = g.leaves()
+    b = cuda(P.rhs(p, lv, fc, beta))
+    pt = cuda(P.random_vector(g.n_leaves, 2))
+    prm = S.mg_params(coef="f64", sweep="octet")
+
+    def solve(bv):
+        h = S.Hierarchy(g, bv, p.bc, prm)
+        x, st = h.solve(b, tol=1e-12, precision="fp64", max_iter=200)
+        assert st.converged
+        return h, x
+
+    h0, x0 = solve(beta)
+    lam, st = h0.solve(x0 - pt, tol=1e-12, precision="fp64", max_iter=200, transpose=True)
+    assert st.converged
+    grad = h0.face_grad(x0, lam).cpu().numpy()
+    dm = lv["depth"][fc["minus"]]
+    dp = lv["depth"][fc["plus"]]
+    rng = np.random.default_rng(3)
+    reg = np.nonzero(dm == dp)[0]
+    tf = np.nonzero(dm != dp)[0]
+    faces = np.concatenate([rng.choice(reg, 48, replace=False), rng.choice(tf, 16, replace=False)])
+    fd = np.empty(len(faces))
+    for q, fi in enumerate(faces):
+        eps = 1e-3 * float(beta[fi])
+        sols = []
+        for sgn in (1.0, -1.0):
+            bb = beta.copy()
+            bb[fi] = np.float32(beta[fi] + sgn * eps)
+            sols.append(solve(bb)[1])
+            e_act = float(bb[fi]) - float(beta[fi])
+            if sgn > 0:
+                ep = e_act
+            else:
+                em = -e_act
+        dl = 0.5 * torch.dot(sols[0] - sols[1], sols[0] + sols[1] - 2.0 * pt).item()
+        fd[q] = dl / (ep + em)
+    scale = np.abs(grad[faces]).max()
+    err = np.abs(fd - grad[faces])
+    assert err.max() <= 1e-4 * scale, (err.max(), scale)
