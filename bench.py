@@ -56,7 +56,7 @@ def _kernel_hash():
 def _profiled_traffic():
     """DRAM bytes per launch of the probed sweep from the committed ncu summary, if it
     was taken on the current kernel sources."""
-    p = os.path.join(ROOT, "profiles", "sweep_c2_level0.txt")
+    p = os.path.join(ROOT, "profiles", "sweep_c2_level0_octet.txt")
     try:
         kv = {}
         for line in open(p):
@@ -71,41 +71,69 @@ def _profiled_traffic():
 
 
 class Clocks:
+    """nvidia-smi samples (every 20 ms) of SM clock, power and throttle reasons; started
+    before the timed region, which is bracketed by line marks."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
     def __init__(self, index):
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
-        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
-            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + q,
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + self.Q,
                                        "--format=csv,noheader,nounits", "-lms", "20"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
 
-    def stop(self):
+    def _rows(self):
+        rows = []
+        try:
+            for line in open(self.f.name):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9 and line.endswith("\n"):
+                    rows.append(parts)
+        except Exception:
+            pass
+        return rows
+
+    def wait_first(self, timeout=15.0):
+        t_end = time.time() + timeout
+        while self.p is not None and time.time() < t_end and not self._rows():
+            time.sleep(0.05)
+
+    def mark(self):
+        return len(self._rows())
+
+    def stop(self, lo, hi):
         if self.p is None:
             return None
+        time.sleep(0.05)
         self.p.terminate()
         try:
             self.p.wait(timeout=5)
         except Exception:
             self.p.kill()
-        self.f.flush()
-        rows = []
-        for line in open(self.f.name):
-            parts = [x.strip() for x in line.split(",")]
-            if len(parts) >= 9:
-                rows.append(parts)
+        rows = self._rows()
         os.unlink(self.f.name)
-        if not rows:
-            return None
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        inside = rows[lo:hi + 1]
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0,
+                    "note": "no nvidia-smi sample fell inside the timed region"}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in inside if num(r[1]) is not None]
+        mx = [num(r[2]) for r in inside if num(r[2]) is not None]
+        pw = [num(r[3]) for r in inside if num(r[3]) is not None]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        reasons = sorted({names[i] for r in inside for i in range(4) if r[5 + i].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+                "power_w": statistics.median(pw) if pw else None, "reasons": reasons, "samples": len(inside)}
 
 
 def _setup(dev):
@@ -120,6 +148,14 @@ def _setup(dev):
     hier = S.Hierarchy(tree, torch.from_numpy(beta).to(dev), p.bc, S.mg_params(coef="f32"))
     b = P.rhs(p, tree.leaves(), faces, beta)
     return p, tree, hier, torch.from_numpy(b).to(dev), np
+
+
+def _hier_bf16(p, tree, dev):
+    import torch
+    from paper_2604_18886_b300 import problems as P
+    from paper_2604_18886_b300 import solver as S
+    beta = P.face_beta(p, tree.faces())
+    return S.Hierarchy(tree, torch.from_numpy(beta).to(dev), p.bc, S.mg_params(coef="f32", bf16_coarse=True))
 
 
 def _time_solves(hier, b, x, steps, precision, flush, stream, nvtx=False, eager=False):
@@ -167,26 +203,20 @@ def run_ours(args):
     levels = [tree.level(m)[0].shape[0] for m in range(0, tree.D + 1)]
     big = int(max(range(len(levels)), key=lambda q: levels[q]))
     clocks = Clocks(local)
+    clocks.wait_first()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    mark0 = clocks.mark()
     t0 = time.perf_counter()
     times, iters, kernels = _time_solves(hier, b, x, args.steps, "mixed", flush, stream, nvtx=args.nvtx,
                                          eager=args.eager)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
+    mark1 = clocks.mark()
     if world > 1:
         dist.barrier()
-    ck = clocks.stop()
-    # ---- dominant kernel: the same steps launched kernel by kernel, with the library's
-    # probe bracketing every red-black sweep of the largest level by CUDA events on the
-    # launching stream (event records cannot sit inside the graph's WHILE body)
-    L.check(L.lib().ocg_probe_set(hier.handle, L.OCG_PROBE_SWEEP, big))
-    times_e, _, _ = _time_solves(hier, b, x, args.steps, "mixed", flush, stream, eager=True)
-    nl, tot_ms, cells = C.c_int64(), C.c_double(), C.c_int64()
-    L.check(L.lib().ocg_probe_read(hier.handle, C.c_void_p(stream.cuda_stream), C.byref(nl),
-                                   C.byref(tot_ms), C.byref(cells)))
-    L.check(L.lib().ocg_probe_set(hier.handle, L.OCG_PROBE_OFF, 0))
+    ck = clocks.stop(mark0, mark1)
     ms = statistics.mean(times)
     total_ms = sum(times)
     tuning = {str(m): {"form": ["octet", "cell"][f] if f >= 0 else "shared-memory tail",
@@ -197,15 +227,65 @@ def run_ours(args):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         total_ms = float(tt.item())
     value = world * tree.n_leaves * args.steps / (total_ms / 1e3) / 1e6
+    if args.only_timed:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": round(value, 3), "unit": UNIT, "steps": args.steps,
+                              "ms_per_step": round(ms, 4), "note": "--only-timed (profiling aid)"}), flush=True)
+        return
+    # ---- per-kernel durations inside a graph: the same solve (same iteration count) as
+    # one flat graph whose probe events are event-record nodes around the probed launches
+    def probe(kind, level, reps=5):
+        L.check(L.lib().ocg_probe_set(hier.handle, kind, level))
+        nl_t, ms_t, cells = 0, 0.0, 0
+        for r in range(reps):
+            flush.fill_(float(r))
+            hier.solve(b, x, tol=1e-6, precision="mixed", stream=stream, max_iter=iters[0], unrolled=True,
+                       raise_on_notconv=False)
+            nl, tot, ce = C.c_int64(), C.c_double(), C.c_int64()
+            L.check(L.lib().ocg_probe_read(hier.handle, C.c_void_p(stream.cuda_stream), C.byref(nl),
+                                           C.byref(tot), C.byref(ce)))
+            nl_t += nl.value
+            ms_t += tot.value
+            cells = ce.value
+        L.check(L.lib().ocg_probe_set(hier.handle, L.OCG_PROBE_OFF, 0))
+        return nl_t, ms_t, cells
+    sw_n, sw_ms, sw_cells = probe(L.OCG_PROBE_SWEEP, big)
+    tail_top = max([m for m, (f, a, bq) in hier.tuning().items() if f < 0 and m < 0] or [tree.mc])
+    tl_n, tl_ms, tl_cells = probe(L.OCG_PROBE_TAIL, tail_top)
+    ap_n, ap_ms, ap_cells = probe(L.OCG_PROBE_APPLY, 0)
     # ---- plain FP32 beside it
     times32, iters32, _ = _time_solves(hier, b, x, args.steps, "fp32", flush, stream)
     v32 = tree.n_leaves / (statistics.mean(times32) / 1e3) / 1e6
+    # ---- mixed with BF16 coarse-level coefficients
+    hb = _hier_bf16(p, tree, dev)
+    for _ in range(args.warmup):
+        hb.solve(b, x, tol=1e-6, precision="mixed", stream=stream)
+    times_b, iters_b, _ = _time_solves(hb, b, x, args.steps, "mixed", flush, stream)
+    vb16 = tree.n_leaves / (statistics.mean(times_b) / 1e3) / 1e6
+    del hb
+    # ---- adjoint: transpose solve (BiCGStab, same cycle) + face gradient
+    ptgt = torch.from_numpy(np.random.default_rng(2).standard_normal(tree.n_leaves)).to(dev)
+    xs, _ = hier.solve(b, tol=1e-6, precision="mixed", stream=stream)
+    gp = xs - ptgt
+    adj_t, adj_it = [], []
+    for r in range(max(3, min(args.steps, 20))):
+        flush.fill_(float(r))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lam, sa = hier.solve(gp, tol=1e-6, precision="mixed", stream=stream, transpose=True)
+        hier.face_grad(xs, lam, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        if r > 0:
+            adj_t.append(e0.elapsed_time(e1))
+            adj_it.append(sa.iterations)
     # ---- end to end through the C ABI with host buffers
     bh = b.cpu().pin_memory()
     xh = torch.empty_like(bh).pin_memory()
     e2e_t = []
-    for s in range(args.steps):
-        flush.fill_(float(s))
+    for s_ in range(args.steps):
+        flush.fill_(float(s_))
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -221,33 +301,41 @@ def run_ours(args):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         e2e_total = float(tt.item())
     e2e = world * tree.n_leaves * args.steps / (e2e_total / 1e3) / 1e6
-    # ---- roofline of the dominant kernel (red-black sweep on the largest level)
+    # ---- roofline of the dominant kernel family: the red-black sweep on the largest level
     peak, peak_kind = _peaks()
-    avg_launch_ms = tot_ms.value / max(nl.value, 1)
-    achieved = SWEEP_BYTES_PER_CELL * cells.value / (avg_launch_ms / 1e3) / 1e9
+    sweep_us = sw_ms * 1e3 / max(sw_n, 1)
+    achieved = SWEEP_BYTES_PER_CELL * sw_cells / (sweep_us / 1e6) / 1e9
     traffic = _profiled_traffic()
+    fwd = tuning.get(str(big), {}).get("form", "octet")
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 cycle + f64 pcg", "data": "synthetic",
         "config": {"workload": WORKLOAD, "precision": "mixed (FP32 V-cycle, FP64 PCG)", "tol": 1e-6,
-                   "leaves": tree.n_leaves, "iterations": iters, "cycle": "V (mu=1), nu=2/2, coarsest 10",
+                   "leaves": tree.n_leaves, "iterations": sorted(set(iters)),
+                   "cycle": "V (mu=1), nu=2/2, coarsest 10",
                    "l2": "flushed before every timed step (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "sweep_forms": tuning,
                    "wall_s_timed": round(wall, 3)},
         "plain_fp32": {"value": round(v32, 3), "unit": UNIT, "ms_per_step": round(statistics.mean(times32), 4),
-                       "iterations": iters32},
+                       "iterations": sorted(set(iters32))},
+        "mixed_bf16_coarse": {"value": round(vb16, 3), "unit": UNIT,
+                              "ms_per_step": round(statistics.mean(times_b), 4),
+                              "iterations": sorted(set(iters_b))},
+        "adjoint": {"ms": round(statistics.mean(adj_t), 4), "iterations": sorted(set(adj_it)),
+                    "what": "A^T lambda = p - p_t by BiCGStab (mixed, tol 1e-6) + face gradient"},
         "value_mi_cells": round(value / 1.048576, 3),
-        "roofline": {"bound": "hbm", "kernel": "k_sweep (RBGS colour sweep) on level %d" % big,
+        "roofline": {"bound": "hbm", "kernel": "red-black colour sweep (%s form) on level %d" % (fwd, big),
                      "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "peak_source": peak_kind,
-                     "bytes_per_cell": SWEEP_BYTES_PER_CELL, "cells_per_launch": cells.value,
-                     "launches": nl.value, "avg_launch_us": round(avg_launch_ms * 1e3, 3),
-                     "timing": "CUDA events around each launch, eager repetition of the timed steps",
+                     "bytes_per_cell": SWEEP_BYTES_PER_CELL, "cells_per_launch": sw_cells,
+                     "launches": sw_n, "avg_launch_us": round(sweep_us, 3),
+                     "timing": "CUDA event-record nodes around each launch inside one graph of the solve",
                      "traffic": traffic},
-        "eager_ms_per_step": round(statistics.mean(times_e), 4),
+        "kernels_us": {"coarse_tail": round(tl_ms * 1e3 / max(tl_n, 1), 3), "coarse_tail_launches": tl_n,
+                       "operator_apply": round(ap_ms * 1e3 / max(ap_n, 1), 3), "operator_launches": ap_n},
         "e2e": {"value": round(e2e, 3), "unit": UNIT, "h2d_bytes_per_step": tree.n_leaves * 8,
                 "d2h_bytes_per_step": tree.n_leaves * 8},
         "clocks": ck,
@@ -322,12 +410,14 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--nvtx", action="store_true", help="NVTX range 'timed' around the timed mixed solves")
+    ap.add_argument("--only-timed", action="store_true",
+                    help="run the warm-up and the timed mixed solves only (profiling aid)")
     ap.add_argument("--eager", action="store_true",
                     help="launch the timed solves kernel by kernel (profiling aid; not the benchmark path)")
     args = ap.parse_args()

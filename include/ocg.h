@@ -163,6 +163,9 @@ int ocg_vcycle(ocg_hier* h, int32_t dtype, const void* r_dev, void* z_dev, void*
 
 #define OCG_SOLVE_EAGER 1      /* flags: launch kernel by kernel, test convergence on the host */
 #define OCG_SOLVE_TRANSPOSE 2  /* flags: solve A^T x = b (adjoint system) by BiCGStab */
+#define OCG_SOLVE_UNROLLED 4   /* flags (measurement): run exactly max_iter iterations as one
+                                  flat CUDA graph without the WHILE node, so that a probe's
+                                  events become graph nodes around the probed kernels */
 
 typedef struct {
     double tol;              /* stop when ||r||_2 <= tol ||b||_2 (recursive residual) */
@@ -231,7 +234,8 @@ int ocg_apply_A_f32_noalloc(ocg_hier* h, const float* x_dev, float* y_dev, void*
 /* Measurement hooks (no counterpart in the paper; used by the benchmark).
  * ocg_probe_set: from now on, bracket every launch of kernel `kind` on level `level`
  * with CUDA events recorded on the launching stream (kind 0 off, 1 red-black sweep,
- * 2 residual+restriction, 3 prolongation, 4 composite operator (level = tree level)).
+ * 2 residual+restriction, 3 prolongation, 4 composite operator (level 0), 5 the
+ * shared-memory coarse kernel (level = its finest level)).
  * ocg_probe_read: synchronises the stream, returns the number of bracketed launches,
  * their summed duration in ms and the cells one launch processes, and resets. */
 #define OCG_PROBE_OFF 0
@@ -239,6 +243,7 @@ int ocg_apply_A_f32_noalloc(ocg_hier* h, const float* x_dev, float* y_dev, void*
 #define OCG_PROBE_RESTRICT 2
 #define OCG_PROBE_PROLONG 3
 #define OCG_PROBE_APPLY 4
+#define OCG_PROBE_TAIL 5
 int ocg_probe_set(ocg_hier* h, int32_t kind, int32_t level);
 int ocg_probe_read(ocg_hier* h, void* stream, int64_t* launches, double* total_ms,
                    int64_t* cells_per_launch);

@@ -38,6 +38,7 @@ class MGParams(C.Structure):
 
 OCG_SOLVE_EAGER = 1
 OCG_SOLVE_TRANSPOSE = 2
+OCG_SOLVE_UNROLLED = 4
 
 
 class SolveParams(C.Structure):
@@ -87,6 +88,7 @@ _SIGS = [
 ]
 
 OCG_PROBE_OFF, OCG_PROBE_SWEEP, OCG_PROBE_RESTRICT, OCG_PROBE_PROLONG, OCG_PROBE_APPLY = 0, 1, 2, 3, 4
+OCG_PROBE_TAIL = 5
 
 EXPORTED = [n for n, _, _ in _SIGS]
 

@@ -38,6 +38,7 @@ struct Status : std::runtime_error {
 
 void ck(cudaError_t e, const char* what) {
     if (e != cudaSuccess) {
+        cudaGetLastError();   // clear a non-sticky error so later launch checks do not see it
         if (e == cudaErrorMemoryAllocation) throw Status(OCG_ENOMEM, std::string(what) + ": out of device memory");
         throw Status(OCG_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
     }
@@ -103,11 +104,21 @@ struct Probe {
                 ev.push_back(e);
             }
         }
-        ck(cudaEventRecord(ev[used], st), "cudaEventRecord");
+        record(ev[used], st);
     }
     void end(cudaStream_t st) {
-        ck(cudaEventRecord(ev[used + 1], st), "cudaEventRecord");
+        record(ev[used + 1], st);
         used += 2;
+    }
+    // under stream capture a plain record only joins streams; an external record becomes
+    // an event-record node that timestamps like a stream record
+    static void record(cudaEvent_t e, cudaStream_t st) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        ck(cudaStreamIsCapturing(st, &cs), "cudaStreamIsCapturing");
+        if (cs == cudaStreamCaptureStatusActive)
+            ck(cudaEventRecordWithFlags(e, st, cudaEventRecordExternal), "cudaEventRecordWithFlags");
+        else
+            ck(cudaEventRecord(e, st), "cudaEventRecord");
     }
 };
 
@@ -442,7 +453,7 @@ struct Cycle {
                "cudaFuncSetAttribute");
             const int noct = A.L[0].ni * A.L[0].ni * A.L[0].ni;
             const int nt = std::min(sizeof(TV) == 8 ? 256 : 512, (noct + 31) / 32 * 32);
-            launch(c, -1, m, A.ncell, [&] {
+            launch(c, OCG_PROBE_TAIL, m, A.ncell, [&] {
                 k_otail<TV, TC, TW><<<1, nt, sm, c.st>>>(A, h->t->tables(), C, U, B, scale);
             });
         });
@@ -849,7 +860,36 @@ int krylov_solve(ocg_hier* h, Coefs<TC, TW> Co, int prec, const double* b_user, 
     ck_launch("scatter");
     int64_t kernels = c.count;
     GraphSolve& gs = h->graphs[transpose ? 1 : 0][prec][ns ? 1 : 0];
-    if (eager) {
+    const bool unrolled = (sp->flags & OCG_SOLVE_UNROLLED) != 0;
+    if (unrolled) {
+        // measurement form: exactly max_iter iterations captured into one flat graph (no
+        // WHILE node), so probe events become event-record nodes between the kernels
+        if (!h->cap) ck(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking), "cudaStreamCreate");
+        Ctx cc{h->cap, &h->probe, 0};
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t ge = nullptr;
+        ck(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+        try {
+            Solver<TO, TV, TC, TW> pc{h, Co, ns, cc, 0, 0};
+            pc.begin();
+            const int nbody = transpose ? sp->max_iter : sp->max_iter - 1;
+            for (int q = 0; q < nbody; ++q) pc.body();
+            pc.finish();
+        } catch (...) {
+            cudaGraph_t junk = nullptr;
+            cudaStreamEndCapture(h->cap, &junk);
+            if (junk) cudaGraphDestroy(junk);
+            cudaGetLastError();
+            throw;
+        }
+        ck(cudaStreamEndCapture(h->cap, &g), "end capture");
+        ck(cudaGraphInstantiate(&ge, g, 0), "graph instantiate");
+        ck(cudaGraphLaunch(ge, st), "graph launch");
+        ck(cudaStreamSynchronize(st), "stream sync");
+        cudaGraphExecDestroy(ge);
+        cudaGraphDestroy(g);
+        kernels = cc.count;
+    } else if (eager) {
         Solver<TO, TV, TC, TW> pc{h, Co, ns, c, 0, 0};
         pc.begin();
         while (true) {
@@ -878,7 +918,9 @@ int krylov_solve(ocg_hier* h, Coefs<TC, TW> Co, int prec, const double* b_user, 
     ck(cudaStreamSynchronize(st), "stream sync");
     const double* S = h->hS;
     const int k = (int)S[S_K];
-    if (!eager) {
+    if (unrolled) {
+        kernels += c.count;   // captured kernels + scatter and gather
+    } else if (!eager) {
         // PCG's begin ends with the first half iteration, so its WHILE body runs k - 1
         // times; BiCGStab's body runs k times
         const int64_t body_runs = transpose ? k : std::max(k - 1, 0);
@@ -1260,7 +1302,8 @@ int ocg_pcg_solve(ocg_hier* h, const double* b, double* x, const ocg_solve_param
     int g = guard([&] {
         if (!h || !b || !x || !sp || !stats) throw Status(OCG_EINVAL, "null argument");
         if (!(sp->tol > 0) || sp->max_iter < 1) throw Status(OCG_EINVAL, "tol must be > 0 and max_iter >= 1");
-        if (sp->flags & ~(OCG_SOLVE_EAGER | OCG_SOLVE_TRANSPOSE)) throw Status(OCG_EINVAL, "unknown solve flags");
+        if (sp->flags & ~(OCG_SOLVE_EAGER | OCG_SOLVE_TRANSPOSE | OCG_SOLVE_UNROLLED))
+            throw Status(OCG_EINVAL, "unknown solve flags");
         cudaStream_t st = (cudaStream_t)stream;
         const bool tr = (sp->flags & OCG_SOLVE_TRANSPOSE) != 0;
         if (tr) ensure_bicg(h);
@@ -1290,7 +1333,7 @@ int ocg_pcg_solve(ocg_hier* h, const double* b, double* x, const ocg_solve_param
 int ocg_probe_set(ocg_hier* h, int32_t kind, int32_t level) {
     return guard([&] {
         if (!h) throw Status(OCG_EINVAL, "null hierarchy");
-        if (kind < OCG_PROBE_OFF || kind > OCG_PROBE_APPLY) throw Status(OCG_EINVAL, "probe kind");
+        if (kind < OCG_PROBE_OFF || kind > OCG_PROBE_TAIL) throw Status(OCG_EINVAL, "probe kind");
         h->probe.kind = kind;
         h->probe.level = level;
         h->probe.used = 0;

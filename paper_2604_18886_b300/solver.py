@@ -192,7 +192,7 @@ class Hierarchy:
         return z
 
     def solve(self, b, x=None, tol=1e-6, max_iter=100, precision="mixed", nullspace=-1,
-              stream=None, raise_on_notconv=True, eager=False, transpose=False):
+              stream=None, raise_on_notconv=True, eager=False, transpose=False, unrolled=False):
         """x with A x = b (PCG, Alg. 1), or A^T x = b with transpose=True (BiCGStab, the
         adjoint system).  Returns (x, stats)."""
         import torch
@@ -201,7 +201,8 @@ class Hierarchy:
             x = torch.empty_like(b)
         sp = L.SolveParams()
         sp.tol, sp.max_iter, sp.precision, sp.nullspace = tol, max_iter, PRECISIONS[precision], nullspace
-        sp.flags = (L.OCG_SOLVE_EAGER if eager else 0) | (L.OCG_SOLVE_TRANSPOSE if transpose else 0)
+        sp.flags = ((L.OCG_SOLVE_EAGER if eager else 0) | (L.OCG_SOLVE_TRANSPOSE if transpose else 0) |
+                    (L.OCG_SOLVE_UNROLLED if unrolled else 0))
         st = L.SolveStats()
         code = L.lib().ocg_pcg_solve(self._h, L.ptr(b), L.ptr(x), C.byref(sp), C.byref(st),
                                      self._stream(stream))

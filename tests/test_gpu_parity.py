@@ -301,3 +301,24 @@ def test_autotuner_records_both_forms():
         form, a, b = tun[m]
         assert a > 0 and b > 0
         assert form == (1 if b < a else 0)
+
+
+def test_unrolled_measurement_solve_repeats_the_graph_solve():
+    # the measurement form (fixed iteration count, flat graph, probe events as graph
+    # nodes) runs the same kernels as the WHILE-node graph and gives the same result
+    from paper_2604_18886_b300 import _lib as L
+    import ctypes as C
+    p = P.c3(16, 2)
+    t, H, g, gh, f, beta = build(p, "f32")
+    b = cuda(P.rhs(p, t.leaves, f, beta))
+    xg, sg = gh.solve(b, tol=1e-7, precision="mixed")
+    L.check(L.lib().ocg_probe_set(gh.handle, L.OCG_PROBE_SWEEP, g.D))
+    xu, su = gh.solve(b, tol=1e-7, precision="mixed", max_iter=sg.iterations, unrolled=True)
+    nl, tot, ce = C.c_int64(), C.c_double(), C.c_int64()
+    L.check(L.lib().ocg_probe_read(gh.handle, C.c_void_p(torch.cuda.current_stream().cuda_stream),
+                                   C.byref(nl), C.byref(tot), C.byref(ce)))
+    L.check(L.lib().ocg_probe_set(gh.handle, L.OCG_PROBE_OFF, 0))
+    assert torch.equal(xg, xu) and su.iterations == sg.iterations and su.kernels == sg.kernels
+    # 8 sweeps per visit of the finest level; one preconditioner application per
+    # iteration (the first in begin, the others in the k - 1 loop bodies)
+    assert nl.value == 8 * sg.iterations and tot.value > 0 and ce.value > 0
