@@ -203,6 +203,37 @@ typedef struct {
 int ocg_pcg_solve(ocg_hier* h, const double* b_dev, double* x_dev, const ocg_solve_params* prm,
                   ocg_solve_stats* stats, void* stream);
 
+/* Batched solves: many independent problems advanced together (no counterpart in the
+ * paper).  A batch groups n hierarchies (each set up by ocg_setup_hierarchy with FP32
+ * coefficients, no BF16, mu = 1, nu_post >= 1, equal nu / alpha / beta_restrict, and a
+ * shared-memory coarse tail, i.e. an even root grid of at least 8 cells per axis).  One
+ * launch per phase serves all problems: the V-cycle phases are aligned at the problems'
+ * coarse tails (one CTA per problem in a single tail launch); the sweep form of each
+ * height above the tails is timed at creation when the first hierarchy's sweep_form is
+ * OCG_SWEEP_AUTO.  The batch uses the hierarchies' work vectors: while it exists, do not
+ * run other solves on those hierarchies concurrently with it, and destroy it before them.
+ * Synchronises the stream.  Errors: EINVAL (incompatible hierarchies), ENOMEM, ECUDA. */
+typedef struct ocg_batch ocg_batch;
+int ocg_batch_create(ocg_hier* const* hs, int32_t n, void* stream, ocg_batch** out);
+void ocg_batch_destroy(ocg_batch* b);
+
+/* Heights of the batch's V-cycle above the coarse tails (*heights) and, for height h
+ * (1..*heights), the chosen sweep form and the timed microseconds of one colour sweep
+ * of all problems in each form (-1 if not timed). */
+int ocg_batch_info(const ocg_batch* b, int32_t h, int32_t* heights, int32_t* form, double* us_octet,
+                   double* us_cell);
+
+/* Solve A_p x_p = b_p for every problem p of the batch by Alg. 1 preconditioned by one
+ * V-cycle (mixed precision: FP32 cycle, FP64 Krylov vectors; prm->precision must be
+ * OCG_PREC_MIXED, prm->flags 0).  b_dev[p] / x_dev[p]: float64 device vectors of problem
+ * p in canonical leaf order (host arrays of n device pointers).  Per-problem alpha, beta,
+ * residual and stop test; a problem that has converged is frozen while the others go on;
+ * the loop is one CUDA graph whose WHILE node runs while any problem is open.  stats: n
+ * entries, filled per problem (kernels = launches of the whole batch).  Synchronises
+ * once.  Errors: ENOTCONV (some problem hit max_iter; stats filled), ENAN, EINVAL. */
+int ocg_pcg_solve_batched(ocg_batch* b, const double* const* b_dev, double* const* x_dev,
+                          const ocg_solve_params* prm, ocg_solve_stats* stats, void* stream);
+
 /* Face gradient of a loss through the solve (adjoint; no counterpart in the paper).
  * With p the solution of A p = b and lambda that of A^T lambda = dL/dp, writes
  * dbeta[f] = dL/dbeta_f = -lambda^T (dA/dbeta_f) p for every canonical face f (the order

@@ -85,6 +85,12 @@ _SIGS = [
     ("ocg_probe_read", C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_double),
                                  C.POINTER(C.c_int64)]),
     ("ocg_launch_count", C.c_int, [C.POINTER(C.c_int64)]),
+    ("ocg_batch_create", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.POINTER(C.c_void_p)]),
+    ("ocg_batch_destroy", None, [C.c_void_p]),
+    ("ocg_batch_info", C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                 C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    ("ocg_pcg_solve_batched", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(SolveParams),
+                                        C.c_void_p, C.c_void_p]),
 ]
 
 OCG_PROBE_OFF, OCG_PROBE_SWEEP, OCG_PROBE_RESTRICT, OCG_PROBE_PROLONG, OCG_PROBE_APPLY = 0, 1, 2, 3, 4

@@ -7,7 +7,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libocg.so")
 SOURCES = ["ocg_api.cu", "octree_host.cpp"]
-DEPS = SOURCES + ["kernels.cuh", "octet.cuh", "octree_host.h"]
+DEPS = SOURCES + ["kernels.cuh", "octet.cuh", "batch.cuh", "batch_host.cuh", "octree_host.h"]
 
 
 def _nvcc():

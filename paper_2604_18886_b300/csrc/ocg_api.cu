@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -21,6 +22,7 @@
 #include <vector>
 
 #include "../../include/ocg.h"
+#include "batch.cuh"
 #include "kernels.cuh"
 #include "octet.cuh"
 #include "octree_host.h"
@@ -1369,6 +1371,8 @@ int ocg_launch_count(int64_t* n) {
 // ---------------------------------------------------------------------------------
 // Operator apply without allocation: the two internal-layout work vectors (the input
 // scattered to cell order, and the output in cell order) live in this fixed array.
+#include "batch_host.cuh"
+
 namespace {
 static __device__ __align__(256) float g_noalloc_scratch[2 * (int64_t)OCG_NOALLOC_MAX_CELLS];
 

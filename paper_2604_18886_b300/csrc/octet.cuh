@@ -236,10 +236,9 @@ __device__ __forceinline__ void octet_prolong(const TC* __restrict__ d, TV* __re
 // right-hand side b += A^m u* on cells with children (Alg. 4).  prolong: after the
 // update, every cell with children prolongs its final value onto them.
 template <class TV, class TC, class TW>
-__global__ void __launch_bounds__(OBLK) k_osweep(LevelArgs A, Tables T, Coefs<TC, TW> C, TV* __restrict__ U,
-                                                 TV* __restrict__ B, int colour, int prolong, int fixb) {
-    const int o = blockIdx.x * OBLK + threadIdx.x;
-    if (o >= A.ncell / 8) return;
+__device__ __forceinline__ void osweep_octet(const LevelArgs& A, const Tables& T, const Coefs<TC, TW>& C,
+                                             TV* __restrict__ U, TV* __restrict__ B, int o, int colour,
+                                             int prolong, int fixb) {
     const int c8 = A.off + 8 * o;
     const int og = c8 >> 3;
     OctState<TV> S;
@@ -272,6 +271,14 @@ __global__ void __launch_bounds__(OBLK) k_osweep(LevelArgs A, Tables T, Coefs<TC
     }
 }
 
+template <class TV, class TC, class TW>
+__global__ void __launch_bounds__(OBLK) k_osweep(LevelArgs A, Tables T, Coefs<TC, TW> C, TV* __restrict__ U,
+                                                 TV* __restrict__ B, int colour, int prolong, int fixb) {
+    const int o = blockIdx.x * OBLK + threadIdx.x;
+    if (o >= A.ncell / 8) return;
+    osweep_octet<TV, TC, TW>(A, T, C, U, B, o, colour, prolong, fixb);
+}
+
 // ------------------------------------------------------------ thread-per-cell sweep
 // The same colour sweep with one thread per cell: the octet's 8 cells are 8 consecutive
 // lanes, in-octet neighbours and the T-ghost sibling mean come from warp shuffles, the
@@ -286,10 +293,13 @@ __device__ __forceinline__ T lane_octet_sum(T v) {
     return v;
 }
 
+// tid: thread index within the level (the 8 lanes of an octet are consecutive and
+// aligned to 8 inside the warp); threads past the level's end work on a copy of the last
+// octet so that the warp shuffles stay full, and write nothing.
 template <class TV, class TC, class TW>
-__global__ void __launch_bounds__(BLK) k_csweep(LevelArgs A, Tables T, Coefs<TC, TW> C, TV* __restrict__ U,
-                                                TV* __restrict__ B, int colour, int prolong) {
-    const int tid = blockIdx.x * BLK + threadIdx.x;
+__device__ __forceinline__ void csweep_cell(const LevelArgs& A, const Tables& T, const Coefs<TC, TW>& C,
+                                            TV* __restrict__ U, TV* __restrict__ B, int tid, int colour,
+                                            int prolong) {
     const bool valid = tid < A.ncell;
     const int lc = valid ? tid : (A.ncell - 8 + (tid & 7));
     const int g = A.off + lc;
@@ -351,14 +361,18 @@ __global__ void __launch_bounds__(BLK) k_csweep(LevelArgs A, Tables T, Coefs<TC,
     }
 }
 
+template <class TV, class TC, class TW>
+__global__ void __launch_bounds__(BLK) k_csweep(LevelArgs A, Tables T, Coefs<TC, TW> C, TV* __restrict__ U,
+                                                TV* __restrict__ B, int colour, int prolong) {
+    csweep_cell<TV, TC, TW>(A, T, C, U, B, blockIdx.x * BLK + threadIdx.x, colour, prolong);
+}
+
 // Residual and FAS restriction (Alg. 4): r = b - A^m u; the parent gets
 // b_P = (beta/alpha) sum r (A^{m-1} u* is added on the coarse level by the fixb pass) and
 // u_P = u* = mean of the active children.
 template <class TV, class TC, class TW>
-__global__ void __launch_bounds__(OBLK) k_orestrict(LevelArgs A, Tables T, Coefs<TC, TW> C, TV* __restrict__ U,
-                                                    TV* __restrict__ B, TV scale) {
-    const int o = blockIdx.x * OBLK + threadIdx.x;
-    if (o >= A.ncell / 8) return;
+__device__ __forceinline__ void orestrict_octet(const LevelArgs& A, const Tables& T, const Coefs<TC, TW>& C,
+                                                TV* __restrict__ U, TV* __restrict__ B, TV scale, int o) {
     const int c8 = A.off + 8 * o;
     const int og = c8 >> 3;
     OctState<TV> S;
@@ -374,6 +388,14 @@ __global__ void __launch_bounds__(OBLK) k_orestrict(LevelArgs A, Tables T, Coefs
     const int P = __ldg(T.oct_parent + og);
     B[P] = scale * rs;
     U[P] = S.ubar;
+}
+
+template <class TV, class TC, class TW>
+__global__ void __launch_bounds__(OBLK) k_orestrict(LevelArgs A, Tables T, Coefs<TC, TW> C, TV* __restrict__ U,
+                                                    TV* __restrict__ B, TV scale) {
+    const int o = blockIdx.x * OBLK + threadIdx.x;
+    if (o >= A.ncell / 8) return;
+    orestrict_octet<TV, TC, TW>(A, T, C, U, B, scale, o);
 }
 
 // Prolongation as its own launch (thread per child octet).
@@ -651,8 +673,9 @@ __device__ __forceinline__ void tail_pass(const TailMem<TV>& M, const TailArgs& 
 // schedule of passes (no recursion on the device); fas adds the FAS right-hand-side pass
 // on the top tail level first.
 template <class TV, class TC, class TW>
-__global__ void __launch_bounds__(sizeof(TV) == 8 ? 256 : 512)
-    k_otail(TailArgs A, Tables T, Coefs<TC, TW> C, TV* __restrict__ U, TV* __restrict__ B, TV scale) {
+__device__ __forceinline__ void tail_cycle(const TailArgs& A, int fas, int prolong, const Tables& T,
+                                           const Coefs<TC, TW>& C, TV* __restrict__ U, TV* __restrict__ B,
+                                           TV scale) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int N = A.ncell;
     TailMem<TV> M;
@@ -674,7 +697,7 @@ __global__ void __launch_bounds__(sizeof(TV) == 8 ? 256 : 512)
         }
     }
     __syncthreads();
-    if (A.fas) tail_pass<TV>(M, A, 0, TP_FIXB, TV(0));
+    if (fas) tail_pass<TV>(M, A, 0, TP_FIXB, TV(0));
     for (int q = 0; q < A.nsched; ++q) {
         const int e = __ldg(A.sched + q);
         const int li = e >> 3, kind = e & 7;
@@ -692,7 +715,7 @@ __global__ void __launch_bounds__(sizeof(TV) == 8 ? 256 : 512)
             B[L.off + c] = M.b[q];
         }
     }
-    if (A.prolong) {
+    if (prolong) {
         // onto the level above the tail: children of the top tail level's cells
         const TailLevel& L = A.L[0];
         const int no = tail_noct(L);
@@ -701,6 +724,12 @@ __global__ void __launch_bounds__(sizeof(TV) == 8 ? 256 : 512)
             if (co >= 0) octet_prolong<TV, TC>(C.d, U, co, M.u[L.sbase + (c & 7) * no + (c >> 3)]);
         }
     }
+}
+
+template <class TV, class TC, class TW>
+__global__ void __launch_bounds__(sizeof(TV) == 8 ? 256 : 512)
+    k_otail(TailArgs A, Tables T, Coefs<TC, TW> C, TV* __restrict__ U, TV* __restrict__ B, TV scale) {
+    tail_cycle<TV, TC, TW>(A, A.fas, A.prolong, T, C, U, B, scale);
 }
 
 }  // namespace ocg

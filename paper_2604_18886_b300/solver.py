@@ -209,3 +209,51 @@ class Hierarchy:
         if code not in (L.OCG_OK, L.OCG_ENOTCONV) or (code == L.OCG_ENOTCONV and raise_on_notconv):
             L.check(code)
         return x, st
+
+
+class Batch:
+    """Many independent hierarchies solved together (ocg_batch_create /
+    ocg_pcg_solve_batched): one launch per phase for all problems, per-problem scalars
+    and stop tests, one CUDA graph for the whole loop."""
+
+    def __init__(self, hiers, stream=None):
+        import torch
+        self.hiers = list(hiers)          # kept alive for the batch's lifetime
+        n = len(self.hiers)
+        arr = (C.c_void_p * n)(*[h.handle.value for h in self.hiers])
+        self._h = C.c_void_p()
+        st = C.c_void_p(stream.cuda_stream if stream is not None else torch.cuda.current_stream().cuda_stream)
+        L.check(L.lib().ocg_batch_create(C.cast(arr, C.c_void_p), n, st, C.byref(self._h)))
+
+    def __del__(self):
+        if getattr(self, "_h", None) and self._h.value:
+            L.lib().ocg_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def info(self):
+        """{height: (form, us_octet, us_cell)} of the batched sweeps."""
+        hts, f, a, b = C.c_int32(), C.c_int32(), C.c_double(), C.c_double()
+        L.check(L.lib().ocg_batch_info(self._h, 1, C.byref(hts), C.byref(f), C.byref(a), C.byref(b)))
+        out = {}
+        for h in range(1, hts.value + 1):
+            L.check(L.lib().ocg_batch_info(self._h, h, C.byref(hts), C.byref(f), C.byref(a), C.byref(b)))
+            out[h] = (f.value, a.value, b.value)
+        return out
+
+    def solve(self, bs, xs=None, tol=1e-6, max_iter=100, nullspace=-1, stream=None, raise_on_notconv=True):
+        import torch
+        n = len(self.hiers)
+        assert len(bs) == n and all(b.dtype == torch.float64 and b.is_cuda for b in bs)
+        if xs is None:
+            xs = [torch.empty_like(b) for b in bs]
+        bp = (C.c_void_p * n)(*[b.data_ptr() for b in bs])
+        xp = (C.c_void_p * n)(*[x.data_ptr() for x in xs])
+        sp = L.SolveParams()
+        sp.tol, sp.max_iter, sp.precision, sp.nullspace, sp.flags = tol, max_iter, L.OCG_PREC_MIXED, nullspace, 0
+        stats = (L.SolveStats * n)()
+        s = stream if stream is not None else torch.cuda.current_stream()
+        code = L.lib().ocg_pcg_solve_batched(self._h, C.cast(bp, C.c_void_p), C.cast(xp, C.c_void_p), C.byref(sp),
+                                             C.cast(stats, C.c_void_p), C.c_void_p(s.cuda_stream))
+        if code not in (L.OCG_OK, L.OCG_ENOTCONV) or (code == L.OCG_ENOTCONV and raise_on_notconv):
+            L.check(code)
+        return xs, list(stats)
