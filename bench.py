@@ -158,6 +158,43 @@ def _hier_bf16(p, tree, dev):
     return S.Hierarchy(tree, torch.from_numpy(beta).to(dev), p.bc, S.mg_params(coef="f32", bf16_coarse=True))
 
 
+def _cut_cell(dev, stream, flush, args):
+    """The cut-cell projection workload: 64^3 root, two levels of refinement within 0.05
+    of a solid sphere and box, fluid-fraction beta, Neumann walls, divergence rhs; mixed
+    solve with BF16 coarse coefficients to 1e-6."""
+    import torch
+    from paper_2604_18886_b300 import problems as P
+    from paper_2604_18886_b300 import solver as S
+    p = P.c3(64, 2)
+    g = S.Octree(p.desc)
+    f = g.faces()
+    beta = P.face_beta(p, f)
+    h = S.Hierarchy(g, torch.from_numpy(beta).to(dev), p.bc, S.mg_params(coef="f32", bf16_coarse=True))
+    b = torch.from_numpy(P.rhs(p, g.leaves(), f, beta)).to(dev)
+    x = torch.empty_like(b)
+    for _ in range(args.warmup):
+        h.solve(b, x, tol=1e-6, precision="mixed", stream=stream)
+    steps = max(3, min(args.steps, 20))
+    t, its = [], set()
+    for s_ in range(steps):
+        flush.fill_(float(s_))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, st = h.solve(b, x, tol=1e-6, precision="mixed", stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        t.append(e0.elapsed_time(e1))
+        its.add(st.iterations)
+        assert st.converged
+    ms = statistics.mean(t)
+    return {"workload": "cut-cell projection: 64^3 root, sphere r=0.2 and box, band 0.05, 2 levels "
+                        "(%d leaves), fluid-fraction beta, Neumann, divergence rhs" % g.n_leaves,
+            "precision": "mixed, BF16 coarse coefficients", "value": round(g.n_leaves / (ms / 1e3) / 1e6, 3),
+            "unit": UNIT, "ms_per_step": round(ms, 4), "steps": steps, "iterations": sorted(its),
+            "true_rel_res": st.true_rel_res}
+
+
 BATCH_WORKLOAD = ("64 independent octrees, effective 64/96/128 with 2-3 levels refined within 0.05 of a "
                   "seeded random sphere; even trees beta=1 Dirichlet, odd trees cut-cell beta Neumann; "
                   "rhs N(0,1)")
@@ -346,6 +383,8 @@ def run_ours(args):
         if r > 0:
             adj_t.append(e0.elapsed_time(e1))
             adj_it.append(sa.iterations)
+    # ---- cut-cell workload (mixed, BF16 coarse coefficients)
+    cut = None if args.no_batch else _cut_cell(dev, stream, flush, args)
     # ---- batched form: 64 independent trees, one graph, one launch per phase
     batched = None if args.no_batch else _batched(dev, stream, flush, args)
     # ---- end to end through the C ABI with host buffers
@@ -404,6 +443,7 @@ def run_ours(args):
                      "traffic": traffic},
         "kernels_us": {"coarse_tail": round(tl_ms * 1e3 / max(tl_n, 1), 3), "coarse_tail_launches": tl_n,
                        "operator_apply": round(ap_ms * 1e3 / max(ap_n, 1), 3), "operator_launches": ap_n},
+        "cut_cell": cut,
         "batched": batched,
         "e2e": {"value": round(e2e, 3), "unit": UNIT, "h2d_bytes_per_step": tree.n_leaves * 8,
                 "d2h_bytes_per_step": tree.n_leaves * 8},

@@ -322,3 +322,40 @@ def test_unrolled_measurement_solve_repeats_the_graph_solve():
     # 8 sweeps per visit of the finest level; one preconditioner application per
     # iteration (the first in begin, the others in the k - 1 loop bodies)
     assert nl.value == 8 * sg.iterations and tot.value > 0 and ce.value > 0
+
+
+def test_full_size_cut_cell_properties():
+    # the cut-cell workload at full size (64^3 root, 2 levels of band refinement around the
+    # solid sphere and box, 2,637,132 leaves, Neumann walls, fluid-fraction beta): the
+    # oracle cannot assemble this size in a test, so check what holds at any size
+    p = P.c3(64, 2)
+    g = S.Octree(p.desc)
+    f = g.faces()
+    beta = P.face_beta(p, f)
+    b = cuda(P.rhs(p, g.leaves(), f, beta))
+    h16 = S.Hierarchy(g, beta, p.bc, S.mg_params(coef="f32", bf16_coarse=True))
+    h32 = S.Hierarchy(g, beta, p.bc, S.mg_params(coef="f32"))
+    # constant null space of the composite operator (rounding of the FP32 coefficients)
+    one = torch.ones(g.n_leaves, dtype=torch.float64, device="cuda")
+    a1 = h32.apply_A(one).abs().max().item()
+    assert a1 <= 1e-6 * h32.apply_A(cuda(P.random_vector(g.n_leaves, 7))).abs().max().item()
+    # mixed solves with BF16 and FP32 coarse coefficients both reach the tolerance with
+    # the FP64 true residual
+    x16, s16 = h16.solve(b, tol=1e-6, precision="mixed")
+    x32, s32 = h32.solve(b, tol=1e-6, precision="mixed")
+    assert s16.converged and s16.true_rel_res <= 1.5e-6
+    assert s32.converged and s32.true_rel_res <= 1.5e-6
+    assert abs(x16.mean().item()) <= 1e-12 * x16.abs().max().item()
+    # the tol-1e-9 solution: both tol-1e-6 solves are close to it
+    x9, s9 = h32.solve(b, tol=1e-9, precision="mixed")
+    assert s9.converged and s9.true_rel_res <= 2e-9
+    for x in (x16, x32):
+        assert (x - x9).abs().max().item() <= 1e-3 * x9.abs().max().item()
+    # grid-independent iteration counts: the same geometry at half the root resolution
+    ph = P.c3(32, 2)
+    gh_ = S.Octree(ph.desc)
+    fh = gh_.faces()
+    bh = P.face_beta(ph, fh)
+    hh = S.Hierarchy(gh_, bh, ph.bc, S.mg_params(coef="f32", bf16_coarse=True))
+    _, sh = hh.solve(cuda(P.rhs(ph, gh_.leaves(), fh, bh)), tol=1e-6, precision="mixed")
+    assert abs(sh.iterations - s16.iterations) <= 2, (sh.iterations, s16.iterations)
