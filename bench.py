@@ -150,6 +150,24 @@ def _setup(dev):
     return p, tree, hier, torch.from_numpy(b).to(dev), np
 
 
+def max_over_ranks(v, dev):
+    """Largest value of v over the ranks of the default process group (v itself when
+    there is none): the timed region is as long as its slowest replica."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(v)
+    t = torch.tensor([float(v)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank, steps, world, total_ms):
+    """Whole-job throughput in millions of units per second: every rank solves its own
+    replica, total_ms is the slowest rank's timed region."""
+    return world * units_per_rank * steps / (total_ms / 1e3) / 1e6
+
+
 def _hier_bf16(p, tree, dev):
     import torch
     from paper_2604_18886_b300 import problems as P
@@ -325,11 +343,8 @@ def run_ours(args):
     tuning = {str(m): {"form": ["octet", "cell"][f] if f >= 0 else "shared-memory tail",
                        "us_octet": round(a, 2), "us_cell": round(bq, 2)}
               for m, (f, a, bq) in hier.tuning().items()}
-    if world > 1:
-        tt = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    value = world * tree.n_leaves * args.steps / (total_ms / 1e3) / 1e6
+    total_ms = max_over_ranks(total_ms, dev)
+    value = replica_throughput(tree.n_leaves, args.steps, world, total_ms)
     if args.only_timed:
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": round(value, 3), "unit": UNIT, "steps": args.steps,
@@ -402,12 +417,8 @@ def run_ours(args):
         e1.record(stream)
         e1.synchronize()
         e2e_t.append(e0.elapsed_time(e1))
-    e2e_total = sum(e2e_t)
-    if world > 1:
-        tt = torch.tensor([e2e_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_total = float(tt.item())
-    e2e = world * tree.n_leaves * args.steps / (e2e_total / 1e3) / 1e6
+    e2e_total = max_over_ranks(sum(e2e_t), dev)
+    e2e = replica_throughput(tree.n_leaves, args.steps, world, e2e_total)
     # ---- roofline of the dominant kernel family: the red-black sweep on the largest level
     peak, peak_kind = _peaks()
     sweep_us = sw_ms * 1e3 / max(sw_n, 1)
