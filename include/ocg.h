@@ -47,6 +47,8 @@ extern "C" {
 #define OCG_REFINE_NONE 0        /* uniform root grid */
 #define OCG_REFINE_BALL_CENTRE 1 /* refine iff |centre - c|^2 < r^2 (first sphere) */
 #define OCG_REFINE_SDF_BAND 2    /* refine iff |phi(centre)| < band + (sqrt(3)/2) h */
+#define OCG_REFINE_SINE_BAND 3   /* refine iff |phi(c)| < band + |grad phi(c)| (sqrt(3)/2) h,
+                                    phi a normalised sum of plane sine waves */
 
 #define OCG_F64 0
 #define OCG_F32 1
@@ -67,6 +69,21 @@ typedef struct ocg_hier ocg_hier;
  *                spheres sqrt(dx*dx+dy*dy+dz*dz) - r and boxes (lo, hi):
  *                q = |x - 0.5*(lo+hi)| - 0.5*(hi-lo),
  *                sqrt(mx*mx+my*my+mz*mz) + min(max(qx, max(qy, qz)), 0), m = max(q, 0)
+ *   SINE_BAND:   phi = s / n and |grad phi| = sqrt((gx*gx + gy*gy) + gz*gz) / n over the
+ *                n = n_sines waves (kappa, dx, dy, dz, theta) = sines[w], accumulated in
+ *                w order from 0: w2 = TWO_PI * kappa, a = w2 * ((dx*x + dy*y) + dz*z) + theta,
+ *                s += sin(a), g += (w2 * cos(a)) * (dx, dy, dz); refined iff
+ *                |phi| < band + (|grad phi| * (0.5*sqrt(3))) * (1/(n0 2^d)).
+ *                TWO_PI is 2 pi rounded to double.  sin and cos are the library's own
+ *                deterministic forms (so that any implementation can reproduce the tree
+ *                bit for bit): k = rint(a * (2/pi)), r = ((a - k P1) - k P2) - k P3 with
+ *                pi/2 = P1 + P2 + P3 (P1 = 0x1.921fb544p+0, P2 = 0x1.0b4611a6p-34,
+ *                P3 = 0x1.3198a2e037073p-69), Taylor polynomials in r2 = r*r evaluated by
+ *                Horner from the highest term, sin r = r + (r*r2) * sum_{j=0..7}
+ *                (-1)^(j+1)/(2j+3)! r2^j and cos r = 1 + r2 * sum_{j=0..8} (-1)^(j+1)/(2j+2)!
+ *                r2^j, coefficients formed as 1.0 / n! in double, and the quadrant
+ *                q = k mod 4 selecting (sin r, cos r, -sin r, -cos r) for sin(a) and
+ *                (cos r, -sin r, -cos r, sin r) for cos(a).  Valid for |a| < 2^20.
  * followed by the minimal refinement that makes face-neighbouring leaves differ by at
  * most one depth (Sec. 3). */
 typedef struct {
@@ -79,6 +96,9 @@ typedef struct {
     double band;
     double spheres[4][4];   /* cx, cy, cz, r */
     double boxes[4][6];     /* lox, loy, loz, hix, hiy, hiz */
+    int32_t n_sines;        /* 1..8 for SINE_BAND, else ignored */
+    int32_t reserved2;
+    double sines[8][5];     /* kappa, dx, dy, dz, theta per wave (|a| < 2^20 required) */
 } ocg_octree_desc;
 
 /* Build the octree and its multigrid tables on the host (no device call; the tables are
@@ -104,6 +124,12 @@ int ocg_octree_export_neighbours(const ocg_octree* t, int8_t* kind, int64_t* ran
  * the + side at that depth); minus/plus = canonical leaf ranks of the two sides. */
 int ocg_octree_export_faces(const ocg_octree* t, int32_t* axis, int32_t* depth, int32_t* i,
                             int32_t* j, int32_t* k, int64_t* minus, int64_t* plus);
+/* The same for canonical faces first .. first+count-1 only (buffers of count entries), so
+ * that trees with hundreds of millions of faces can be read in pieces.  NULL buffers are
+ * skipped.  Errors: EINVAL (range outside 0..n_faces). */
+int ocg_octree_export_faces_range(const ocg_octree* t, int64_t first, int64_t count, int32_t* axis,
+                                  int32_t* depth, int32_t* i, int32_t* j, int32_t* k,
+                                  int64_t* minus, int64_t* plus);
 /* Cells of multigrid level m (mc <= m <= D) in Morton order of the level's grid: depth-m
  * cells for m >= 0, the uniform root coarsening n0/2^-m for m < 0 (padding cells of an
  * odd coarsest grid excluded).  Call with i == NULL to get *n only. leaf: 1 for leaves. */

@@ -59,6 +59,11 @@ def refine_predicate(desc, d, i, j, k):
                     box     q = |x - 0.5*(lo+hi)| - 0.5*(hi-lo) per axis;
                             sqrt(mx*mx + my*my + mz*mz) + min(max(qx, max(qy, qz)), 0)
                             with m = max(q, 0)
+      sine band   : |phi| < band + (|grad phi| * (0.5*sqrt(3))) * (1/n_d) with
+                    phi = s/n, |grad phi| = sqrt(gx*gx + gy*gy + gz*gz)/n over the n waves
+                    (kappa, dx, dy, dz, theta), accumulated wave by wave from 0:
+                    w = 2pi*kappa, a = w*(dx*x + dy*y + dz*z) + theta, s += sin a,
+                    g += (w cos a) * (dx, dy, dz); sin and cos from oracle.trig
     Ties count as not refined.
     """
     from paper_2604_18886_b300 import problems as P
@@ -87,6 +92,21 @@ def refine_predicate(desc, d, i, j, k):
             inside = np.minimum(np.maximum(qx, np.maximum(qy, qz)), 0.0)
             phi = np.minimum(phi, outside + inside)
         slack = desc.band + (0.5 * math.sqrt(3.0)) * (1.0 / nd)
+        return np.abs(phi) < slack
+    if desc.refine == P.REFINE_SINE_BAND:
+        from . import trig
+        s = np.zeros(x.shape)
+        gx, gy, gz = np.zeros(x.shape), np.zeros(x.shape), np.zeros(x.shape)
+        for (kap, dx, dy, dz, th) in desc.sines:
+            w = trig.TWO_PI * kap
+            a = w * (dx * x + dy * y + dz * z) + th
+            s = s + trig.det_sin(a)
+            g = w * trig.det_cos(a)
+            gx, gy, gz = gx + g * dx, gy + g * dy, gz + g * dz
+        n = float(len(desc.sines))
+        phi = s / n
+        grad = np.sqrt(gx * gx + gy * gy + gz * gz) / n
+        slack = desc.band + (grad * (0.5 * math.sqrt(3.0))) * (1.0 / nd)
         return np.abs(phi) < slack
     raise NotImplementedError("refine kind %d" % desc.refine)
 

@@ -23,7 +23,8 @@ class OctreeDesc(C.Structure):
     _fields_ = [("n0", C.c_int32), ("max_depth", C.c_int32), ("refine", C.c_int32),
                 ("n_spheres", C.c_int32), ("n_boxes", C.c_int32), ("reserved", C.c_int32),
                 ("band", C.c_double), ("spheres", (C.c_double * 4) * 4),
-                ("boxes", (C.c_double * 6) * 4)]
+                ("boxes", (C.c_double * 6) * 4), ("n_sines", C.c_int32), ("reserved2", C.c_int32),
+                ("sines", (C.c_double * 5) * 8)]
 
 
 OCG_SWEEP_AUTO, OCG_SWEEP_OCTET, OCG_SWEEP_CELL = -1, 0, 1
@@ -68,6 +69,7 @@ _SIGS = [
     ("ocg_octree_export_leaves", C.c_int, [C.c_void_p] + [C.c_void_p] * 4),
     ("ocg_octree_export_neighbours", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("ocg_octree_export_faces", C.c_int, [C.c_void_p] + [C.c_void_p] * 7),
+    ("ocg_octree_export_faces_range", C.c_int, [C.c_void_p, C.c_int64, C.c_int64] + [C.c_void_p] * 7),
     ("ocg_octree_export_level", C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int64)] + [C.c_void_p] * 4),
     ("ocg_setup_hierarchy", C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int32), C.POINTER(MGParams),
                                       C.c_void_p, C.POINTER(C.c_void_p)]),

@@ -401,7 +401,7 @@ __global__ void k_pupdate(TO* __restrict__ p, const TZ* __restrict__ z, const do
 // -beta_f h_f into the face's destination: the - face coefficient of its + cell, or the
 // T record weight of a fine leaf's + face.  Flags a negative / non-finite beta.
 __global__ void k_face_scatter(const float* __restrict__ beta, const int64_t* __restrict__ slot,
-                               const uint8_t* __restrict__ kind, const int32_t* __restrict__ depth,
+                               const uint8_t* __restrict__ kind, const int8_t* __restrict__ depth,
                                const double* __restrict__ hdepth, int nface, double* __restrict__ cm,
                                double* __restrict__ tw, int* __restrict__ err) {
     const int f = blockIdx.x * blockDim.x + threadIdx.x;

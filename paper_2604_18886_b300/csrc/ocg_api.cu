@@ -156,7 +156,7 @@ struct ocg_octree {
     mutable int8_t* level = nullptr;
     mutable int64_t* fslot = nullptr;
     mutable uint8_t* fkind = nullptr;
-    mutable int32_t* fdepth = nullptr;
+    mutable int8_t* fdepth = nullptr;
 
     void upload() const {
         if (on_device) return;
@@ -338,6 +338,25 @@ void choose_tail(ocg_hier* h, int which, size_t vbytes) {
 }
 
 // Real (non-padding) cells of level m in the level's Morton order.
+void export_faces(const HostTree& H, int64_t first, int64_t count, int32_t* axis, int32_t* depth, int32_t* i,
+                  int32_t* j, int32_t* k, int64_t* minus, int64_t* plus) {
+#pragma omp parallel for schedule(static)
+    for (int64_t q = 0; q < count; ++q) {
+        const int64_t f = first + q;
+        if (axis) axis[q] = H.f_axis[f];
+        if (depth) depth[q] = H.f_depth[f];
+        if (i || j || k) {
+            int32_t a, b, c;
+            face_plus_cell(H, f, a, b, c);
+            if (i) i[q] = a;
+            if (j) j[q] = b;
+            if (k) k[q] = c;
+        }
+        if (minus) minus[q] = H.f_minus[f];
+        if (plus) plus[q] = H.f_plus[f];
+    }
+}
+
 std::vector<int64_t> level_cells_morton(const HostTree& H, int m) {
     const LevelMeta& l = H.L(m);
     std::vector<std::pair<uint64_t, int64_t>> v;
@@ -1000,8 +1019,15 @@ int ocg_octree_export_neighbours(const ocg_octree* t, int8_t* kind, int64_t* ran
     return guard([&] {
         if (!t) throw Status(OCG_EINVAL, "null octree");
         const HostTree& H = t->H;
-        if (kind) std::memcpy(kind, H.nb_kind.data(), H.nb_kind.size());
-        if (rank) std::memcpy(rank, H.nb_rank.data(), H.nb_rank.size() * sizeof(int64_t));
+#pragma omp parallel for schedule(static)
+        for (int64_t r = 0; r < H.nleaf; ++r)
+            for (int dir = 0; dir < 6; ++dir) {
+                int8_t kd;
+                int64_t rk;
+                leaf_neighbour(H, r, dir, kd, rk);
+                if (kind) kind[6 * r + dir] = kd;
+                if (rank) rank[6 * r + dir] = rk;
+            }
     });
 }
 
@@ -1010,14 +1036,18 @@ int ocg_octree_export_faces(const ocg_octree* t, int32_t* axis, int32_t* depth, 
     return guard([&] {
         if (!t) throw Status(OCG_EINVAL, "null octree");
         const HostTree& H = t->H;
-        const size_t n4 = H.nface * sizeof(int32_t), n8 = H.nface * sizeof(int64_t);
-        if (axis) std::memcpy(axis, H.f_axis.data(), n4);
-        if (depth) std::memcpy(depth, H.f_depth.data(), n4);
-        if (i) std::memcpy(i, H.f_i.data(), n4);
-        if (j) std::memcpy(j, H.f_j.data(), n4);
-        if (k) std::memcpy(k, H.f_k.data(), n4);
-        if (minus) std::memcpy(minus, H.f_minus.data(), n8);
-        if (plus) std::memcpy(plus, H.f_plus.data(), n8);
+        export_faces(H, 0, H.nface, axis, depth, i, j, k, minus, plus);
+    });
+}
+
+int ocg_octree_export_faces_range(const ocg_octree* t, int64_t first, int64_t count, int32_t* axis,
+                                  int32_t* depth, int32_t* i, int32_t* j, int32_t* k, int64_t* minus,
+                                  int64_t* plus) {
+    return guard([&] {
+        if (!t) throw Status(OCG_EINVAL, "null octree");
+        const HostTree& H = t->H;
+        if (first < 0 || count < 0 || first + count > H.nface) throw Status(OCG_EINVAL, "face range");
+        export_faces(H, first, count, axis, depth, i, j, k, minus, plus);
     });
 }
 

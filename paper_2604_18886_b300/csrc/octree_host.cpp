@@ -48,6 +48,56 @@ void demorton3(uint64_t key, uint64_t& i, uint64_t& j, uint64_t& k) {
 
 static inline int64_t lex(int64_t i, int64_t j, int64_t k, int64_t n) { return (k * n + j) * n + i; }
 
+// Deterministic sine and cosine of the sine-band predicate (the exact recipe is stated in
+// ocg.h): Cody-Waite reduction by pi/2 with a three-part constant whose first two parts
+// carry 33 significant bits (k * part is exact for |k| < 2^20), then Taylor polynomials of
+// the reduced argument r in [-pi/4, pi/4] evaluated by Horner's rule; the truncation error
+// there is below 1e-19.  Coefficients are (-1)^j / n!, formed by one IEEE division of the
+// exactly representable factorial.
+namespace {
+struct DetTrig {
+    double sc[8];   // r^(2j+3) coefficient of sin r, j = 0..7
+    double cc[9];   // r^(2j+2) coefficient of cos r, j = 0..8
+    DetTrig() {
+        double f = 1.0;
+        for (int n = 1; n <= 18; ++n) {
+            f = f * (double)n;   // exact: 18! < 2^53
+            if (n >= 3 && (n & 1)) sc[(n - 3) / 2] = (((n - 3) / 2) & 1 ? 1.0 : -1.0) / f;
+            if (n >= 2 && !(n & 1)) cc[(n - 2) / 2] = (((n - 2) / 2) & 1 ? 1.0 : -1.0) / f;
+        }
+    }
+};
+const DetTrig& det_trig() {
+    static const DetTrig t;
+    return t;
+}
+constexpr double DT_2_OVER_PI = 0x1.45f306dc9c883p-1;
+constexpr double DT_P1 = 0x1.921fb544p+0;
+constexpr double DT_P2 = 0x1.0b4611a6p-34;
+constexpr double DT_P3 = 0x1.3198a2e037073p-69;
+constexpr double DT_TWO_PI = 0x1.921fb54442d18p+2;
+
+// sin and cos of a together (the predicate needs both at the same argument)
+void det_sincos(double a, double& sa, double& ca) {
+    const DetTrig& T = det_trig();
+    const double k = std::rint(a * DT_2_OVER_PI);
+    const double r = ((a - k * DT_P1) - k * DT_P2) - k * DT_P3;
+    const double r2 = r * r;
+    double ps = T.sc[7];
+    for (int j = 6; j >= 0; --j) ps = ps * r2 + T.sc[j];
+    double pc = T.cc[8];
+    for (int j = 7; j >= 0; --j) pc = pc * r2 + T.cc[j];
+    const double s = r + (r * r2) * ps;
+    const double c = 1.0 + r2 * pc;
+    switch ((int)((int64_t)k & 3)) {
+        case 0: sa = s; ca = c; break;
+        case 1: sa = c; ca = -s; break;
+        case 2: sa = -s; ca = -c; break;
+        default: sa = -c; ca = s; break;
+    }
+}
+}  // namespace
+
 // Refinement predicate (documented in ocg.h); no FMA contraction in this file.
 static bool refine_pred(const ocg_octree_desc& d, int depth, int64_t i, int64_t j, int64_t k) {
     const double nd = (double)((int64_t)d.n0 << depth);
@@ -80,6 +130,26 @@ static bool refine_pred(const ocg_octree_desc& d, int depth, int64_t i, int64_t 
             phi = std::fmin(phi, outside + inside);
         }
         const double slack = d.band + (0.5 * std::sqrt(3.0)) * (1.0 / nd);
+        return std::fabs(phi) < slack;
+    }
+    if (d.refine == OCG_REFINE_SINE_BAND) {
+        double s = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
+        for (int w = 0; w < d.n_sines; ++w) {
+            const double* q = d.sines[w];
+            const double w2 = DT_TWO_PI * q[0];
+            const double a = w2 * ((q[1] * x + q[2] * y) + q[3] * z) + q[4];
+            double sa, ca;
+            det_sincos(a, sa, ca);
+            s = s + sa;
+            const double g = w2 * ca;
+            gx = gx + g * q[1];
+            gy = gy + g * q[2];
+            gz = gz + g * q[3];
+        }
+        const double n = (double)d.n_sines;
+        const double phi = s / n;
+        const double gn = std::sqrt((gx * gx + gy * gy) + gz * gz) / n;
+        const double slack = d.band + (gn * (0.5 * std::sqrt(3.0))) * (1.0 / nd);
         return std::fabs(phi) < slack;
     }
     return false;
@@ -117,6 +187,65 @@ void HostTree::cell_coords(int m, int64_t g, int64_t& i, int64_t& j, int64_t& k)
     k = 2 * (int64_t)K + ((s >> 2) & 1);
 }
 
+// Parallel stream compaction: out = [value(c) for c in 0..n-1 if keep(c)], in order.
+// pred(c, value&) returns keep and fills value.
+template <class V, class F>
+static std::vector<V> par_compact(int64_t n, F&& pred) {
+#ifdef _OPENMP
+    const int nch = std::max(1, omp_get_max_threads() * 8);
+#else
+    const int nch = 1;
+#endif
+    std::vector<int64_t> cnt(nch + 1, 0);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int c = 0; c < nch; ++c) {
+        const int64_t lo = n * c / nch, hi = n * (c + 1) / nch;
+        int64_t k = 0;
+        V v{};
+        for (int64_t q = lo; q < hi; ++q) k += pred(q, v) ? 1 : 0;
+        cnt[c + 1] = k;
+    }
+    for (int c = 0; c < nch; ++c) cnt[c + 1] += cnt[c];
+    std::vector<V> out(cnt[nch]);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int c = 0; c < nch; ++c) {
+        const int64_t lo = n * c / nch, hi = n * (c + 1) / nch;
+        int64_t k = cnt[c];
+        V v{};
+        for (int64_t q = lo; q < hi; ++q)
+            if (pred(q, v)) out[k++] = v;
+    }
+    return out;
+}
+
+// Parallel exclusive scan: visit(c, sum of weight(0..c-1)) for every c, in chunks.
+template <class W, class F>
+static void par_scan(int64_t n, W&& weight, F&& visit) {
+#ifdef _OPENMP
+    const int nch = std::max(1, omp_get_max_threads() * 8);
+#else
+    const int nch = 1;
+#endif
+    std::vector<int64_t> cnt(nch + 1, 0);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int c = 0; c < nch; ++c) {
+        const int64_t lo = n * c / nch, hi = n * (c + 1) / nch;
+        int64_t k = 0;
+        for (int64_t q = lo; q < hi; ++q) k += weight(q);
+        cnt[c + 1] = k;
+    }
+    for (int c = 0; c < nch; ++c) cnt[c + 1] += cnt[c];
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int c = 0; c < nch; ++c) {
+        const int64_t lo = n * c / nch, hi = n * (c + 1) / nch;
+        int64_t k = cnt[c];
+        for (int64_t q = lo; q < hi; ++q) {
+            visit(q, k);
+            k += weight(q);
+        }
+    }
+}
+
 static int sub_index(int a, int s) {
     // position of slot s among the 4 cells of an octet face normal to axis a
     if (a == 0) return ((s >> 1) & 1) | (((s >> 2) & 1) << 1);
@@ -130,8 +259,18 @@ void build_host_tree(const ocg_octree_desc& desc, HostTree& T) {
     if (n0 < 2 || (n0 & 1)) throw std::runtime_error("n0 must be even and >= 2");
     if (D < 0 || D > 12) throw std::runtime_error("max_depth out of range [0, 12]");
     if (((int64_t)n0 << D) > (1 << 20)) throw std::runtime_error("n0 * 2^max_depth exceeds 2^20");
-    if (desc.refine < OCG_REFINE_NONE || desc.refine > OCG_REFINE_SDF_BAND)
+    if (desc.refine < OCG_REFINE_NONE || desc.refine > OCG_REFINE_SINE_BAND)
         throw std::runtime_error("unknown refine kind");
+    if (desc.refine == OCG_REFINE_SINE_BAND) {
+        if (desc.n_sines < 1 || desc.n_sines > 8) throw std::runtime_error("n_sines must be in 1..8");
+        for (int w = 0; w < desc.n_sines; ++w) {
+            const double* q = desc.sines[w];
+            // |a| <= 2 pi |kappa| (|dx| + |dy| + |dz|) + |theta| on the unit cube
+            const double amax = 6.3 * std::fabs(q[0]) * (std::fabs(q[1]) + std::fabs(q[2]) + std::fabs(q[3])) +
+                                std::fabs(q[4]);
+            if (!(amax < 1048576.0)) throw std::runtime_error("sine wave argument out of range (|a| < 2^20)");
+        }
+    }
     if (desc.n_spheres < 0 || desc.n_spheres > 4 || desc.n_boxes < 0 || desc.n_boxes > 4)
         throw std::runtime_error("too many primitives");
     if (desc.refine == OCG_REFINE_BALL_CENTRE && desc.n_spheres < 1)
@@ -160,11 +299,13 @@ void build_host_tree(const ocg_octree_desc& desc, HostTree& T) {
                     if (refine_pred(desc, d, i, j, k)) R[lex(i, j, k, nd)] = 1;
                 }
     }
-    // ---- face 2:1 balance, deepest inner cells first
+    // ---- face 2:1 balance, deepest inner cells first (within one depth the order of the
+    // marks does not matter: depth e is read, depth e-1 written)
     for (int e = D - 1; e >= 1; --e) {
         const int64_t ne = (int64_t)n0 << e, np = ne / 2;
-        auto& R = ref[e];
-        auto& Rp = ref[e - 1];
+        const auto& R = ref[e];
+        uint8_t* Rp = ref[e - 1].data();
+#pragma omp parallel for schedule(static)
         for (int64_t k = 0; k < ne; ++k)
             for (int64_t j = 0; j < ne; ++j)
                 for (int64_t i = 0; i < ne; ++i) {
@@ -175,7 +316,8 @@ void build_host_tree(const ocg_octree_desc& desc, HostTree& T) {
                             int64_t q[3] = {c[0], c[1], c[2]};
                             q[a] += s;
                             if (q[a] < 0 || q[a] >= ne) continue;
-                            Rp[lex(q[0] >> 1, q[1] >> 1, q[2] >> 1, np)] = 1;
+                            __atomic_store_n(&Rp[lex(q[0] >> 1, q[1] >> 1, q[2] >> 1, np)], (uint8_t)1,
+                                             __ATOMIC_RELAXED);
                         }
                 }
     }
@@ -185,7 +327,9 @@ void build_host_tree(const ocg_octree_desc& desc, HostTree& T) {
         return ref[d][lex(i, j, k, nd)] != 0;
     };
 
-    // ---- levels and octet parent keys
+    // ---- levels and octet parent keys.  Level 1's octets are the refined root cells in
+    // Morton order; for m >= 2 the cells of level m-1 in storage order are already in
+    // Morton order (parent key << 3 | slot), so level m's keys are its refined cells.
     const int nlev = D - mc + 1;
     T.lv.assign(nlev, LevelMeta{});
     T.okeys.assign(nlev, {});
@@ -201,14 +345,30 @@ void build_host_tree(const ocg_octree_desc& desc, HostTree& T) {
             l.Np = (m == mc) ? Ncp : l.N;
         }
         auto& keys = T.okeys[m - mc];
-        if (m >= 1) {
-            const int64_t np = (int64_t)n0 << (m - 1);
-            const auto& R = ref[m - 1];
+        if (m == 1) {
+            const int64_t np = n0;
+            const auto& R = ref[0];
             for (int64_t k = 0; k < np; ++k)
                 for (int64_t j = 0; j < np; ++j)
                     for (int64_t i = 0; i < np; ++i)
                         if (R[lex(i, j, k, np)]) keys.push_back(morton3(i, j, k));
             std::sort(keys.begin(), keys.end());
+        } else if (m >= 2) {
+            const auto& pk = T.okeys[m - 1 - mc];
+            const auto& R = ref[m - 1];
+            const int64_t nd = (int64_t)n0 << (m - 1);
+            auto is_ref = [&](uint64_t key) {
+                uint64_t i, j, k;
+                demorton3(key, i, j, k);
+                return R[lex((int64_t)i, (int64_t)j, (int64_t)k, nd)] != 0;
+            };
+            keys = par_compact<uint64_t>((int64_t)pk.size() * 8, [&](int64_t c, uint64_t& out) {
+                const uint64_t key = (pk[c >> 3] << 3) | (uint64_t)(c & 7);
+                out = key;
+                return is_ref(key);
+            });
+        }
+        if (m >= 1) {
             l.noct = (int64_t)keys.size();
         } else {
             l.ni = l.Np / 2;
@@ -247,15 +407,10 @@ void build_host_tree(const ocg_octree_desc& desc, HostTree& T) {
             const bool real = i < l.N && j < l.N && k < l.N;
             if (!real) continue;
             uint8_t fl = 2;
-            bool has_children;
-            if (m >= 0) {
-                has_children = refined(m, i, j, k);
-                if (!has_children) fl |= 1;
-            } else {
-                has_children = true;
-            }
+            const bool has_children = m >= 0 ? refined(m, i, j, k) : true;
+            if (m >= 0 && !has_children) fl |= 1;
             T.cell_flags[g] = fl;
-            if (has_children) {
+            if (has_children && m <= 0) {
                 const LevelMeta& lf = T.L(m + 1);
                 if (lf.ni > 0) {
                     T.child_oct[g] = (int32_t)(lf.oct_off + lex(i, j, k, lf.ni));
@@ -266,144 +421,255 @@ void build_host_tree(const ocg_octree_desc& desc, HostTree& T) {
                 }
             }
         }
+        if (m >= 1 && m < D) {
+            // children octets of level m+1 follow the refined cells of level m in storage order
+            const int64_t base = T.L(m + 1).oct_off;
+            par_scan(l.ncell, [&](int64_t lc) { return (T.cell_flags[l.off + lc] & 1) ? 0 : 1; },
+                     [&](int64_t lc, int64_t rank) {
+                         if (!(T.cell_flags[l.off + lc] & 1)) T.child_oct[l.off + lc] = (int32_t)(base + rank);
+                     });
+        }
     }
-    // canonical leaves: sorted by (depth, Morton key)
+    // canonical leaves: sorted by (depth, Morton key); level 0 is sorted explicitly, levels
+    // m >= 1 are stored in Morton order already
     T.leaf_cell.clear();
-    T.leaf_depth.clear(); T.leaf_i.clear(); T.leaf_j.clear(); T.leaf_k.clear();
-    for (int m = 0; m <= D; ++m) {
-        const LevelMeta& l = T.L(m);
+    T.leaf_first.assign(D + 2, 0);
+    {
+        const LevelMeta& l = T.L(0);
         std::vector<std::pair<uint64_t, int64_t>> lv;
         for (int64_t lc = 0; lc < l.ncell; ++lc) {
             const int64_t g = l.off + lc;
             if (!(T.cell_flags[g] & 1)) continue;
             int64_t i, j, k;
-            T.cell_coords(m, g, i, j, k);
+            T.cell_coords(0, g, i, j, k);
             lv.push_back({morton3(i, j, k), g});
         }
         std::sort(lv.begin(), lv.end());
-        for (const auto& e : lv) {
-            const int64_t g = e.second;
-            int64_t i, j, k;
-            T.cell_coords(m, g, i, j, k);
-            T.cell_rank[g] = (int32_t)T.leaf_cell.size();
-            T.leaf_cell.push_back((int32_t)g);
-            T.leaf_depth.push_back(m);
-            T.leaf_i.push_back((int32_t)i); T.leaf_j.push_back((int32_t)j); T.leaf_k.push_back((int32_t)k);
-        }
+        for (const auto& e : lv) T.leaf_cell.push_back((int32_t)e.second);
+    }
+    for (int m = 1; m <= D; ++m) {
+        T.leaf_first[m] = (int64_t)T.leaf_cell.size();
+        const LevelMeta& l = T.L(m);
+        std::vector<int32_t> part = par_compact<int32_t>(l.ncell, [&](int64_t lc, int32_t& out) {
+            out = (int32_t)(l.off + lc);
+            return (T.cell_flags[l.off + lc] & 1) != 0;
+        });
+        T.leaf_cell.insert(T.leaf_cell.end(), part.begin(), part.end());
     }
     T.nleaf = (int64_t)T.leaf_cell.size();
+    T.leaf_first[D + 1] = T.nleaf;
+    T.leaf_depth.resize(T.nleaf);
+    T.leaf_i.resize(T.nleaf); T.leaf_j.resize(T.nleaf); T.leaf_k.resize(T.nleaf);
+#pragma omp parallel for schedule(static)
+    for (int64_t r = 0; r < T.nleaf; ++r) {
+        const int64_t g = T.leaf_cell[r];
+        const int m = T.cell_level[g];
+        int64_t i, j, k;
+        T.cell_coords(m, g, i, j, k);
+        T.cell_rank[g] = (int32_t)r;
+        T.leaf_depth[r] = m;
+        T.leaf_i[r] = (int32_t)i; T.leaf_j[r] = (int32_t)j; T.leaf_k[r] = (int32_t)k;
+    }
 
-    // ---- octet tables: neighbours, parents, T records
+    // ---- octet tables: parents, neighbours (coarse to fine: an adaptive level reads the
+    // neighbours of its parents' level), T records
     T.nbr.assign(6 * T.noct, -1);
     T.oct_parent.assign(T.noct, -1);
-    T.t_oct.clear();
-    T.trec.assign(T.noct, -1);
-    auto& trec = T.trec;
     for (int m = mc; m <= D; ++m) {
         const LevelMeta& l = T.L(m);
-        const int64_t PG = m >= 1 ? ((int64_t)n0 << (m - 1)) : l.Np / 2;
-        const auto& keys = T.okeys[m - mc];
-        for (int64_t o = 0; o < l.noct; ++o) {
-            uint64_t I, J, K;
-            if (l.ni > 0) {
-                I = o % l.ni;
-                J = (o / l.ni) % l.ni;
-                K = o / ((int64_t)l.ni * l.ni);
-            } else {
-                demorton3(keys[o], I, J, K);
-            }
-            const int64_t go = l.oct_off + o;
-            if (m > mc) T.oct_parent[go] = (int32_t)T.cell_index(m - 1, I, J, K);
-            const int64_t P[3] = {(int64_t)I, (int64_t)J, (int64_t)K};
-            for (int a = 0; a < 3; ++a)
-                for (int sd = 0; sd < 2; ++sd) {
-                    const int dir = 2 * a + sd;
+        if (m <= 0) {
+#pragma omp parallel for schedule(static)
+            for (int64_t o = 0; o < l.noct; ++o) {
+                const int64_t I = o % l.ni, J = (o / l.ni) % l.ni, K = o / ((int64_t)l.ni * l.ni);
+                const int64_t go = l.oct_off + o;
+                if (m > mc) T.oct_parent[go] = (int32_t)T.cell_index(m - 1, I, J, K);
+                const int64_t P[3] = {I, J, K};
+                for (int dir = 0; dir < 6; ++dir) {
+                    const int a = dir >> 1;
                     int64_t q[3] = {P[0], P[1], P[2]};
-                    q[a] += sd ? 1 : -1;
-                    int32_t v = -1;
-                    if (q[a] >= 0 && q[a] < PG) {
-                        const bool inner = (m <= 0) || refined(m - 1, q[0], q[1], q[2]);
-                        if (l.ni > 0) {
-                            v = (int32_t)lex(q[0], q[1], q[2], l.ni);
-                        } else if (inner) {
-                            auto it = std::lower_bound(keys.begin(), keys.end(), morton3(q[0], q[1], q[2]));
-                            v = (int32_t)(it - keys.begin());
-                        } else {
-                            const int64_t Kc = T.cell_index(m - 1, q[0], q[1], q[2]);
-                            if (Kc < 0 || !(T.cell_flags[Kc] & 1))
-                                throw std::runtime_error("internal: unbalanced T-junction");
-                            if (trec[go] < 0) {
-                                trec[go] = (int32_t)T.t_oct.size();
-                                T.t_oct.push_back((int32_t)go);
-                            }
-                            v = (int32_t)(-2 - Kc);
-                        }
-                    }
-                    T.nbr[(int64_t)dir * T.noct + go] = v;
+                    q[a] += (dir & 1) ? 1 : -1;
+                    const bool in = q[a] >= 0 && q[a] < l.ni;
+                    T.nbr[(int64_t)dir * T.noct + go] = in ? (int32_t)lex(q[0], q[1], q[2], l.ni) : -1;
                 }
+            }
+            continue;
+        }
+        const LevelMeta& lp = T.L(m - 1);
+#pragma omp parallel for schedule(static)
+        for (int64_t lc = 0; lc < lp.ncell; ++lc) {
+            const int32_t co = T.child_oct[lp.off + lc];
+            if (co >= 0) T.oct_parent[co] = (int32_t)(lp.off + lc);
+        }
+        int bad = 0;
+#pragma omp parallel for schedule(static) reduction(| : bad)
+        for (int64_t o = 0; o < l.noct; ++o) {
+            const int64_t go = l.oct_off + o;
+            const int64_t Pc = T.oct_parent[go];
+            const int sp = (int)(Pc & 7);
+            const int64_t pog = Pc >> 3;
+            for (int dir = 0; dir < 6; ++dir) {
+                const int a = dir >> 1, bit = 1 << a;
+                const bool plus = dir & 1;
+                int64_t Q = -1;
+                if (((sp & bit) != 0) != plus) {
+                    Q = plus ? Pc + bit : Pc - bit;   // sibling in the parent's octet
+                } else {
+                    const int32_t v = T.nbr[(int64_t)dir * T.noct + pog];
+                    if (v >= 0) Q = lp.off + 8 * (int64_t)v + (sp ^ bit);
+                    else if (v <= -2) bad = 1;        // a refined cell beside a coarser leaf
+                }
+                int32_t out = -1;
+                if (Q >= 0) {
+                    const int32_t cq = T.child_oct[Q];
+                    if (cq >= 0) out = (int32_t)(cq - l.oct_off);
+                    else if (T.cell_flags[Q] & 1) out = (int32_t)(-2 - Q);
+                    else bad = 1;
+                }
+                T.nbr[(int64_t)dir * T.noct + go] = out;
+            }
+        }
+        if (bad) throw std::runtime_error("internal: unbalanced T-junction");
+    }
+    T.t_oct.clear();
+    T.trec.assign(T.noct, -1);
+    for (int64_t go = 0; go < T.noct; ++go) {
+        bool has_t = false;
+        for (int dir = 0; dir < 6; ++dir) has_t |= T.nbr[(int64_t)dir * T.noct + go] <= -2;
+        if (has_t) {
+            T.trec[go] = (int32_t)T.t_oct.size();
+            T.t_oct.push_back((int32_t)go);
         }
     }
     T.nt = (int64_t)T.t_oct.size();
 
-    // ---- neighbour export and canonical faces
-    T.nb_kind.assign(6 * T.nleaf, 0);
-    T.nb_rank.assign(6 * T.nleaf, -1);
-    struct F { int32_t a, d, i, j, k; int64_t minus, plus, slot; uint8_t kind; uint64_t mk; };
-    std::vector<F> faces;
-    for (int64_t r = 0; r < T.nleaf; ++r) {
+    // ---- canonical faces, grouped by (axis, depth of the finer side) and sorted within a
+    // group by the Morton key of the + cell.  The - face of a leaf (same-depth or coarser
+    // leaf on its - side) is keyed by the leaf itself, so these come in leaf order; the +
+    // face of a fine leaf against a coarser leaf (T record) is keyed by the virtual cell
+    // beyond it and is merged in.
+    std::vector<int64_t> gcount(3 * (D + 1), 0), gbase(3 * (D + 1) + 1, 0);
+    struct Group {
+        std::vector<int32_t> mi, pl;
+        std::vector<int64_t> slot;
+        std::vector<uint64_t> tkey;
+        std::vector<int32_t> tmi, tpl;
+        std::vector<int64_t> tslot;
+    };
+    auto leaf_key = [&](int64_t r) -> uint64_t {
         const int d = T.leaf_depth[r];
-        const int64_t c[3] = {T.leaf_i[r], T.leaf_j[r], T.leaf_k[r]};
-        const int64_t nd = (int64_t)n0 << d;
-        const int64_t g = T.leaf_cell[r];
-        const int s = (int)((g - T.L(d).off) & 7);
-        for (int a = 0; a < 3; ++a)
-            for (int sd = 0; sd < 2; ++sd) {
-                const int dir = 2 * a + sd;
-                int64_t q[3] = {c[0], c[1], c[2]};
-                q[a] += sd ? 1 : -1;
-                int8_t kind = 0;
-                int64_t rk = -1;
-                if (q[a] >= 0 && q[a] < nd) {
-                    const int64_t gn = T.cell_index(d, q[0], q[1], q[2]);
-                    if (gn >= 0) {
-                        if (T.cell_flags[gn] & 1) { kind = 1; rk = T.cell_rank[gn]; }
-                        else kind = 3;
-                    } else {
-                        const int64_t gk = T.cell_index(d - 1, q[0] >> 1, q[1] >> 1, q[2] >> 1);
-                        kind = 2;
-                        rk = T.cell_rank[gk];
-                    }
+        if (d == 0) return morton3(T.leaf_i[r], T.leaf_j[r], T.leaf_k[r]);
+        const int64_t lc = T.leaf_cell[r] - T.L(d).off;
+        return (T.okeys[d - mc][lc >> 3] << 3) | (uint64_t)(lc & 7);
+    };
+    std::vector<Group> groups(3 * (D + 1));
+    for (int a = 0; a < 3; ++a)
+        for (int d = 0; d <= D; ++d) {
+            Group& G = groups[a * (D + 1) + d];
+            const int64_t r0 = T.leaf_first[d], r1 = T.leaf_first[d + 1];
+            const int64_t off = T.L(d).off;
+            const int bit = 1 << a;
+            // - faces
+            struct MF { int32_t mi, pl; int64_t slot; };
+            std::vector<MF> mf = par_compact<MF>(r1 - r0, [&](int64_t q, MF& out) {
+                const int64_t r = r0 + q, g = T.leaf_cell[r];
+                const int s = (int)(g & 7);
+                int64_t gn = -1;
+                if (s & bit) gn = g - bit;
+                else {
+                    const int32_t v = T.nbr[(int64_t)(2 * a) * T.noct + (g >> 3)];
+                    if (v >= 0) gn = off + 8 * (int64_t)v + (s | bit);
+                    else if (v <= -2) gn = -2 - (int64_t)v;
                 }
-                T.nb_kind[6 * r + dir] = kind;
-                T.nb_rank[6 * r + dir] = rk;
-                if (sd == 0 && (kind == 1 || kind == 2)) {
-                    faces.push_back({a, d, (int32_t)c[0], (int32_t)c[1], (int32_t)c[2], rk, r,
-                                     (int64_t)a * T.ncell + g, 0, morton3(c[0], c[1], c[2])});
-                }
-                if (sd == 1 && kind == 2) {
-                    const int64_t go = (g >> 3);
-                    const int32_t t = T.trec[go];
-                    const int64_t slot = (int64_t)(dir * 4 + sub_index(a, s)) * T.nt + t;
-                    faces.push_back({a, d, (int32_t)q[0], (int32_t)q[1], (int32_t)q[2], r, rk, slot, 1,
-                                     morton3(q[0], q[1], q[2])});
-                }
+                if (gn < 0 || !(T.cell_flags[gn] & 1)) return false;
+                out = MF{T.cell_rank[gn], (int32_t)r, (int64_t)a * T.ncell + g};
+                return true;
+            });
+            G.mi.resize(mf.size()); G.pl.resize(mf.size()); G.slot.resize(mf.size());
+            for (size_t q = 0; q < mf.size(); ++q) { G.mi[q] = mf[q].mi; G.pl[q] = mf[q].pl; G.slot[q] = mf[q].slot; }
+            // + faces at T-junctions
+            struct TF { uint64_t key; int32_t mi, pl; int64_t slot; };
+            std::vector<TF> tf = par_compact<TF>(r1 - r0, [&](int64_t q, TF& out) {
+                const int64_t r = r0 + q, g = T.leaf_cell[r];
+                const int s = (int)(g & 7);
+                if (!(s & bit)) return false;
+                const int32_t v = T.nbr[(int64_t)(2 * a + 1) * T.noct + (g >> 3)];
+                if (v > -2) return false;
+                int64_t c[3] = {T.leaf_i[r], T.leaf_j[r], T.leaf_k[r]};
+                c[a] += 1;
+                const int32_t t = T.trec[g >> 3];
+                out = TF{morton3(c[0], c[1], c[2]), (int32_t)r, T.cell_rank[-2 - (int64_t)v],
+                         (int64_t)((2 * a + 1) * 4 + sub_index(a, s)) * T.nt + t};
+                return true;
+            });
+            std::sort(tf.begin(), tf.end(), [](const TF& x, const TF& y) { return x.key < y.key; });
+            G.tkey.resize(tf.size()); G.tmi.resize(tf.size()); G.tpl.resize(tf.size()); G.tslot.resize(tf.size());
+            for (size_t q = 0; q < tf.size(); ++q) {
+                G.tkey[q] = tf[q].key; G.tmi[q] = tf[q].mi; G.tpl[q] = tf[q].pl; G.tslot[q] = tf[q].slot;
             }
-    }
-    std::sort(faces.begin(), faces.end(), [](const F& x, const F& y) {
-        if (x.a != y.a) return x.a < y.a;
-        if (x.d != y.d) return x.d < y.d;
-        return x.mk < y.mk;
-    });
-    T.nface = (int64_t)faces.size();
+            gcount[a * (D + 1) + d] = (int64_t)(mf.size() + tf.size());
+        }
+    for (size_t q = 0; q < gcount.size(); ++q) gbase[q + 1] = gbase[q] + gcount[q];
+    T.nface = gbase.back();
     T.f_axis.resize(T.nface); T.f_depth.resize(T.nface);
-    T.f_i.resize(T.nface); T.f_j.resize(T.nface); T.f_k.resize(T.nface);
     T.f_minus.resize(T.nface); T.f_plus.resize(T.nface);
     T.f_slot.resize(T.nface); T.f_kind.resize(T.nface);
-    for (int64_t f = 0; f < T.nface; ++f) {
-        const F& x = faces[f];
-        T.f_axis[f] = x.a; T.f_depth[f] = x.d; T.f_i[f] = x.i; T.f_j[f] = x.j; T.f_k[f] = x.k;
-        T.f_minus[f] = x.minus; T.f_plus[f] = x.plus; T.f_slot[f] = x.slot; T.f_kind[f] = x.kind;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int gi = 0; gi < (int)groups.size(); ++gi) {
+        Group& G = groups[gi];
+        const int a = gi / (D + 1), d = gi % (D + 1);
+        int64_t f = gbase[gi];
+        size_t x = 0, y = 0;
+        while (x < G.mi.size() || y < G.tkey.size()) {
+            const bool take_t = y < G.tkey.size() && (x >= G.mi.size() || G.tkey[y] < leaf_key(G.pl[x]));
+            if (take_t) {
+                T.f_minus[f] = G.tmi[y]; T.f_plus[f] = G.tpl[y]; T.f_slot[f] = G.tslot[y]; T.f_kind[f] = 1;
+                ++y;
+            } else {
+                T.f_minus[f] = G.mi[x]; T.f_plus[f] = G.pl[x]; T.f_slot[f] = G.slot[x]; T.f_kind[f] = 0;
+                ++x;
+            }
+            T.f_axis[f] = (int8_t)a;
+            T.f_depth[f] = (int8_t)d;
+            ++f;
+        }
+        G = Group();   // release the group's buffers
     }
+}
+
+void face_plus_cell(const HostTree& T, int64_t f, int32_t& i, int32_t& j, int32_t& k) {
+    if (T.f_kind[f] == 0) {
+        const int64_t r = T.f_plus[f];
+        i = T.leaf_i[r]; j = T.leaf_j[r]; k = T.leaf_k[r];
+    } else {
+        const int64_t r = T.f_minus[f];
+        i = T.leaf_i[r] + (T.f_axis[f] == 0);
+        j = T.leaf_j[r] + (T.f_axis[f] == 1);
+        k = T.leaf_k[r] + (T.f_axis[f] == 2);
+    }
+}
+
+void leaf_neighbour(const HostTree& T, int64_t r, int dir, int8_t& kind, int64_t& rank) {
+    const int d = T.leaf_depth[r];
+    const int64_t g = T.leaf_cell[r];
+    const int a = dir >> 1, bit = 1 << a, s = (int)(g & 7);
+    const bool plus = dir & 1;
+    int64_t gn = -1;
+    kind = 0;
+    rank = -1;
+    if (((s & bit) != 0) != plus) {
+        gn = plus ? g + bit : g - bit;
+    } else {
+        const int32_t v = T.nbr[(int64_t)dir * T.noct + (g >> 3)];
+        if (v >= 0) gn = T.L(d).off + 8 * (int64_t)v + (s ^ bit);
+        else if (v <= -2) {
+            kind = 2;
+            rank = T.cell_rank[-2 - (int64_t)v];
+            return;
+        }
+    }
+    if (gn < 0) return;
+    if (T.cell_flags[gn] & 1) { kind = 1; rank = T.cell_rank[gn]; }
+    else kind = 3;
 }
 
 // ---------------------------------------------------------------- adjoint tables

@@ -51,20 +51,18 @@ struct HostTree {
     std::vector<int32_t> trec;       // [noct]: T record of the octet, -1 if it has no T face
     std::vector<int32_t> t_oct;      // [nt]: global octet owning the record
     std::vector<int32_t> leaf_cell;  // [nleaf]: canonical rank -> global cell
+    std::vector<int64_t> leaf_first; // [D+2]: first canonical rank of each depth
     std::vector<int32_t> cell_rank;  // [ncell]: global cell -> canonical rank or -1
     std::vector<uint8_t> cell_flags; // [ncell]: bit0 leaf, bit1 active-able (not padding)
     std::vector<int8_t> cell_level;  // [ncell]
 
     // canonical leaves
     std::vector<int32_t> leaf_depth, leaf_i, leaf_j, leaf_k;
-    // canonical faces
-    std::vector<int32_t> f_axis, f_depth, f_i, f_j, f_k;
-    std::vector<int64_t> f_minus, f_plus;
+    // canonical faces (the + cell's coordinates follow from the leaves: face_plus_cell)
+    std::vector<int8_t> f_axis, f_depth;
+    std::vector<int32_t> f_minus, f_plus;  // canonical leaf ranks of the two sides
     std::vector<int64_t> f_slot;     // destination of -beta*h (see setup kernel)
     std::vector<uint8_t> f_kind;     // 0: c_{a-} of a cell, 1: T record + face weight
-    // neighbour export
-    std::vector<int8_t> nb_kind;
-    std::vector<int64_t> nb_rank;
 
     const LevelMeta& L(int m) const { return lv[m - mc]; }
     LevelMeta& L(int m) { return lv[m - mc]; }
@@ -74,6 +72,14 @@ struct HostTree {
 
 // Builds everything; throws std::runtime_error with a message on invalid input.
 void build_host_tree(const ocg_octree_desc& desc, HostTree& T);
+
+// Integer coordinates (at the face's depth) of the cell on the + side of canonical face f;
+// for a T sub-face whose fine leaf is on the - side that cell is virtual.
+void face_plus_cell(const HostTree& T, int64_t f, int32_t& i, int32_t& j, int32_t& k);
+
+// Neighbour code of leaf r in direction dir (x-, x+, y-, y+, z-, z+): kind 0 wall, 1 same-depth
+// leaf, 2 coarser leaf, 3 refined neighbour; rank = canonical rank for kinds 1 and 2, else -1.
+void leaf_neighbour(const HostTree& T, int64_t r, int dir, int8_t& kind, int64_t& rank);
 
 // A^T - A of the composite leaf operator by rows.  Only T-junctions make A non-symmetric:
 // a T sub-face f of the fine leaf i against the coarser leaf K contributes

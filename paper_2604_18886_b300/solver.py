@@ -21,10 +21,12 @@ def _desc(d: P.OctreeDesc) -> L.OctreeDesc:
     out.max_depth = d.max_depth
     out.refine = d.refine
     out.band = d.band
-    if len(d.spheres) > 4 or len(d.boxes) > 4:
-        raise ValueError("at most 4 spheres and 4 boxes")
-    if d.refine == P.REFINE_SINE_BAND:
-        raise ValueError("sine-band refinement is not available in the library")
+    if len(d.spheres) > 4 or len(d.boxes) > 4 or len(d.sines) > 8:
+        raise ValueError("at most 4 spheres, 4 boxes and 8 sine waves")
+    out.n_sines = len(d.sines)
+    for q, w in enumerate(d.sines):
+        for c in range(5):
+            out.sines[q][c] = float(w[c])
     out.n_spheres = len(d.spheres)
     out.n_boxes = len(d.boxes)
     for q, s in enumerate(d.spheres):

@@ -34,6 +34,9 @@ def _descs():
                        boxes=[(0.5, 0.1, 0.2, 0.9, 0.35, 0.6)])
     yield P.OctreeDesc(12, 2, P.REFINE_SDF_BAND, band=0.05, spheres=[(0.45, 0.55, 0.5, 0.23)])
     yield P.c4_tree(1).desc
+    yield P.c5(8, 2).desc           # sine band: deterministic sin/cos in both builders
+    yield P.c5(6, 3, band=0.01).desc
+    yield P.c5(16, 2).desc
 
 
 @pytest.mark.parametrize("desc", list(_descs()))
