@@ -350,32 +350,31 @@ __global__ void __launch_bounds__(BLK) k_bi_x(TO* __restrict__ x, TO* __restrict
 }
 
 // ------------------------------------------------------------------ adjoint kernels
-// Y[row] += sum_e mult[e] beta[face[e]] X[col[e]] over the listed rows: the A^T - A part of
-// the transposed composite operator (non-zero only around T-junctions).
-template <class TO>
-__global__ void k_tcorr(int nrow, const int32_t* __restrict__ row, const int32_t* __restrict__ ptr,
-                        const int32_t* __restrict__ col, const int32_t* __restrict__ face,
-                        const double* __restrict__ mult, const float* __restrict__ beta, const TO* __restrict__ X,
-                        TO* __restrict__ Y) {
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= nrow) return;
-    double acc = 0.0;
-    for (int e = ptr[q]; e < ptr[q + 1]; ++e) acc += mult[e] * (double)beta[face[e]] * (double)X[col[e]];
-    const int g = row[q];
-    Y[g] = TO((double)Y[g] + acc);
-}
-
 // dL/dbeta_f = -lambda^T (dA/dbeta_f) p per canonical face: -h (l_a - l_b)(p_a - p_b) for a
-// face between equal-depth leaves, -(h/2)(l_i - l_K)(pbar_P - p_K) for a T sub-face (fine
-// leaf i = a, coarser leaf K = b, P = parent of i whose P entry holds the child mean).
-__global__ void k_face_grad(int nface, const int32_t* __restrict__ fa, const int32_t* __restrict__ fb,
-                            const int32_t* __restrict__ fp, const double* __restrict__ fh,
-                            const double* __restrict__ P, const double* __restrict__ Lm, double* __restrict__ out) {
+// face between equal-depth leaves a (- side) and b, -(h/2)(l_i - l_K)(pbar_P - p_K) for a T
+// sub-face of the fine leaf i against the coarser leaf K, P = parent of i, whose entry of P
+// holds the mean of its children.  The fine side of a T face is the - leaf for kind 1
+// (T-record faces) and the + leaf when the - leaf is shallower than the face.
+struct FaceHs {
+    double h[32];   // face size per depth
+};
+__global__ void k_face_grad(int nface, const int32_t* __restrict__ fminus, const int32_t* __restrict__ fplus,
+                            const uint8_t* __restrict__ fkind, const int8_t* __restrict__ fdepth,
+                            const int32_t* __restrict__ leaf_cell, const int8_t* __restrict__ level,
+                            const int32_t* __restrict__ oct_parent, FaceHs H, const double* __restrict__ P,
+                            const double* __restrict__ Lm, double* __restrict__ out) {
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= nface) return;
-    const int a = fa[f], b = fb[f], par = fp[f];
-    const double dl = Lm[a] - Lm[b];
-    out[f] = par < 0 ? -fh[f] * dl * (P[a] - P[b]) : -0.5 * fh[f] * dl * (P[par] - P[b]);
+    const int ga = leaf_cell[fminus[f]], gb = leaf_cell[fplus[f]];
+    const int d = fdepth[f];
+    const double h = H.h[d];
+    if (fkind[f] == 0 && level[ga] == d) {
+        out[f] = -h * (Lm[ga] - Lm[gb]) * (P[ga] - P[gb]);
+        return;
+    }
+    const int gi = fkind[f] == 1 ? ga : gb, gK = fkind[f] == 1 ? gb : ga;
+    const int par = oct_parent[gi >> 3];
+    out[f] = -0.5 * h * (Lm[gi] - Lm[gK]) * (P[par] - P[gK]);
 }
 
 // sum of x over the leaves (flags bit 0), into the second slot of R

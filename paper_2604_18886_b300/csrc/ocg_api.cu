@@ -178,36 +178,26 @@ struct ocg_octree {
     // adjoint tables (topology only), built on first use
     mutable std::mutex adj_mu;
     mutable bool adj_ready = false;
-    mutable int tc_nrow = 0;
-    mutable int32_t *tc_row = nullptr, *tc_ptr = nullptr, *tc_col = nullptr, *tc_face = nullptr;
-    mutable double* tc_mult = nullptr;
-    mutable int32_t *fg_a = nullptr, *fg_b = nullptr, *fg_p = nullptr;
-    mutable double* fg_h = nullptr;
+    mutable int n_tcoarse = 0, n_tdesc = 0;
+    mutable int32_t *t_oct = nullptr, *tcoarse = nullptr, *tdesc = nullptr, *fminus = nullptr, *fplus = nullptr;
     void upload_adjoint() const {
         std::lock_guard<std::mutex> lk(adj_mu);
         if (adj_ready) return;
-        TransposeCorrection tc;
-        build_transpose_correction(H, tc);
-        tc_nrow = (int)tc.row.size();
-        tc_row = dupload(tc.row);
-        tc_ptr = dupload(tc.ptr);
-        tc_col = dupload(tc.col);
-        tc_face = dupload(tc.face);
-        tc_mult = dupload(tc.mult);
-        std::vector<int32_t> a, b, pp;
-        std::vector<double> hh;
-        build_face_grad_tables(H, a, b, pp, hh);
-        fg_a = dupload(a);
-        fg_b = dupload(b);
-        fg_p = dupload(pp);
-        fg_h = dupload(hh);
+        AdjointTopology at;
+        build_adjoint_topology(H, at);
+        n_tcoarse = (int)at.tcoarse.size();
+        n_tdesc = (int)at.tdesc.size();
+        t_oct = dupload(H.t_oct);
+        tcoarse = dupload(at.tcoarse);
+        tdesc = dupload(at.tdesc);
+        fminus = dupload(H.f_minus);
+        fplus = dupload(H.f_plus);
         adj_ready = true;
     }
     ~ocg_octree() {
         dfree(nbr); dfree(oct_parent); dfree(child_oct); dfree(trec); dfree(leaf_cell);
         dfree(flags); dfree(level); dfree(fslot); dfree(fkind); dfree(fdepth);
-        dfree(tc_row); dfree(tc_ptr); dfree(tc_col); dfree(tc_face); dfree(tc_mult);
-        dfree(fg_a); dfree(fg_b); dfree(fg_p); dfree(fg_h);
+        dfree(t_oct); dfree(tcoarse); dfree(tdesc); dfree(fminus); dfree(fplus);
     }
 };
 
@@ -227,6 +217,7 @@ struct ocg_hier {
     bool ns_auto = false;
     double* c64[4] = {nullptr, nullptr, nullptr, nullptr};
     double* tw64 = nullptr;
+    double* tseed = nullptr;   // adjoint: per tree cell, the a_P weight sums of the T faces
     float* c32[4] = {nullptr, nullptr, nullptr, nullptr};
     float* tw32 = nullptr;
     __nv_bfloat16* c16[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -268,6 +259,7 @@ struct ocg_hier {
                 }
         for (double* v : {rhat, s, tv, ph, sh}) dfree(v);
         dfree(beta);
+        dfree(tseed);
         if (cap) cudaStreamDestroy(cap);
         for (int i = 0; i < 4; ++i) { dfree(c64[i]); dfree(c32[i]); dfree(c16[i]); }
         dfree(tw64); dfree(tw32); dfree(S); dfree(part); dfree(cnt); dfree(tail_sched); dfree(tail_sched2);
@@ -602,13 +594,20 @@ template <class TO, class TC, class TW>
 void apply_outer_T(ocg_hier* h, Coefs<TC, TW> C, TO* P, TO* Y, Ctx& c) {
     const ocg_octree* t = h->t;
     apply_outer<TO, TC, TW>(h, C, P, Y, OP_NONE, c);
-    if (t->tc_nrow > 0) {
-        launch(c, -1, 0, t->tc_nrow, [&] {
-            k_tcorr<TO><<<nblk(t->tc_nrow), BLK, 0, c.st>>>(t->tc_nrow, t->tc_row, t->tc_ptr, t->tc_col, t->tc_face,
-                                                           t->tc_mult, h->beta, P, Y);
-        });
-        ck_launch("apply_T correction");
-    }
+    const HostTree& H = t->H;
+    if (H.nt == 0) return;
+    const Tables T = t->tables();
+    launch(c, -1, 0, H.nt, [&] {
+        k_tfine<TO, TC, TW><<<nblk(H.nt, OBLK), OBLK, 0, c.st>>>(T, C, t->t_oct, P, Y, h->tseed);
+    });
+    launch(c, -1, 0, t->n_tcoarse, [&] {
+        k_tcoarse<TO, TC, TW><<<nblk(t->n_tcoarse), BLK, 0, c.st>>>(T, C, tree_levels(H), t->level, t->tcoarse,
+                                                                    t->n_tcoarse, P, Y);
+    });
+    launch(c, -1, 0, t->n_tdesc, [&] {
+        k_tdesc<TO><<<nblk(t->n_tdesc), BLK, 0, c.st>>>(T, t->tdesc, t->n_tdesc, (int)H.ntree, t->flags, h->tseed, Y);
+    });
+    ck_launch("apply_T correction");
 }
 
 // ------------------------------------------------------------------ PCG (Alg. 1)
@@ -852,8 +851,15 @@ void ensure_work(ocg_hier* h) {
     ck(cudaMemset(h->S, 0, S_COUNT * sizeof(double)), "memset");
 }
 
-void ensure_bicg(ocg_hier* h) {
+void ensure_adjoint(ocg_hier* h) {
     h->t->upload_adjoint();
+    if (h->tseed) return;
+    h->tseed = dalloc<double>(h->t->H.ntree);
+    ck(cudaMemset(h->tseed, 0, h->t->H.ntree * sizeof(double)), "memset");
+}
+
+void ensure_bicg(ocg_hier* h) {
+    ensure_adjoint(h);
     if (h->rhat) return;
     const int64_t n = h->t->H.ntree;
     for (double** v : {&h->rhat, &h->s, &h->tv, &h->ph, &h->sh}) *v = dalloc<double>(n);
@@ -1221,7 +1227,7 @@ int ocg_apply_A(ocg_hier* h, int32_t dtype, const void* x, void* y, int32_t tran
     return guard([&] {
         if (!h || !x || !y) throw Status(OCG_EINVAL, "null argument");
         if (transpose != 0 && transpose != 1) throw Status(OCG_EINVAL, "transpose must be 0 or 1");
-        if (transpose) h->t->upload_adjoint();
+        if (transpose) ensure_adjoint(h);
         cudaStream_t st = (cudaStream_t)stream;
         const ocg_octree* t = h->t;
         const HostTree& H = t->H;
@@ -1297,7 +1303,7 @@ int ocg_face_grad(ocg_hier* h, const double* p, const double* lambda, double* db
         const ocg_octree* t = h->t;
         const HostTree& H = t->H;
         if (H.nface == 0) return;
-        t->upload_adjoint();
+        ensure_adjoint(h);
         cudaStream_t st = (cudaStream_t)stream;
         Ctx c{st, nullptr, 0};
         // p into the tree cells with child means on inner cells (the pbar of Sec. 3.1),
@@ -1320,8 +1326,10 @@ int ocg_face_grad(ocg_hier* h, const double* p, const double* lambda, double* db
             });
         }
         launch(c, -1, 0, H.nface, [&] {
-            k_face_grad<<<nblk(H.nface), BLK, 0, st>>>((int)H.nface, t->fg_a, t->fg_b, t->fg_p, t->fg_h, h->xt, h->yt,
-                                                      dbeta);
+            FaceHs fh{};
+            for (int d = 0; d <= H.D; ++d) fh.h[d] = 1.0 / (double)((int64_t)H.n0 << d);
+            k_face_grad<<<nblk(H.nface), BLK, 0, st>>>((int)H.nface, t->fminus, t->fplus, t->fkind, t->fdepth,
+                                                      t->leaf_cell, t->level, t->oct_parent, fh, h->xt, h->yt, dbeta);
         });
         ck_launch("face_grad");
         g_launches += c.count;

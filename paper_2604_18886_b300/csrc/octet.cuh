@@ -461,6 +461,108 @@ __global__ void __launch_bounds__(OBLK) k_oapply(OMultiLevel ML, Tables T, Coefs
     if (R.op != OP_NONE) red_finish(R, blockIdx.x, dot, 0.0, sh);
 }
 
+// ------------------------------------------------------------ transposed operator
+// A^T x = A x + (A^T - A) x, the correction summed over the T sub-faces f (fine leaf i,
+// coarser leaf K, P = parent of i, c_f = w_f / 2):
+//   c_f (x_i - x_K) a_P  -  c_f (xbar_P - x_K) (e_i - e_K),
+// xbar_P = a_P^T x the mean of P's children (written into x's inner cells by the
+// averaging pass of the forward apply).  Three gathers, each output written by one thread:
+//   k_tfine:   per T octet: y_i -= sum c_f (xbar_P - x_K); tseed[P] = sum c_f (x_i - x_K);
+//   k_tcoarse: per coarse leaf K: y_K += sum c_f ((xbar_P - x_K) - (x_i - x_K));
+//   k_tdesc:   per octet below a T parent: every leaf gets sum over its ancestors A of
+//              tseed[A] 8^-(depth difference)  (tseed is zero away from the T parents).
+// c_f comes from the same coefficients as the forward operator (the fine cell's c_{a-} for a
+// face on the octet's - side, the T record for the + side), so the result is the exact
+// transpose of the operator k_oapply applies.
+template <class TO, class TC, class TW>
+__global__ void __launch_bounds__(OBLK) k_tfine(Tables T, Coefs<TC, TW> C, const int32_t* __restrict__ t_oct,
+                                                 TO* __restrict__ X, TO* __restrict__ Y, double* __restrict__ tseed) {
+    const int q = blockIdx.x * OBLK + threadIdx.x;
+    if (q >= T.nt) return;
+    const int og = __ldg(t_oct + q);
+    const int c8 = 8 * og;
+    const int P = __ldg(T.oct_parent + og);
+    const double xbar = (double)X[P];
+    double yi[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    double tacc = 0.0;
+#pragma unroll
+    for (int dir = 0; dir < 6; ++dir) {
+        const int v = __ldg(T.nbr + dir * T.noct + og);
+        if (v > -2) continue;
+        const double xK = (double)X[-2 - v];
+        const int a = dir >> 1, bit = 1 << a;
+        const TC* cm = a == 0 ? C.cx : (a == 1 ? C.cy : C.cz);
+#pragma unroll
+        for (int qq = 0; qq < 4; ++qq) {
+            const int s = clear_slot(a, qq) | ((dir & 1) ? bit : 0);
+            const double cf = (dir & 1) ? (double)tov(__ldg(C.tw + ((2 * a + 1) * 4 + qq) * T.nt + q))
+                                        : (double)tov(__ldg(cm + c8 + s));
+            const double c = -0.5 * cf;
+            tacc += c * ((double)X[c8 + s] - xK);
+            yi[s] -= c * (xbar - xK);
+        }
+    }
+    tseed[P] = tacc;
+#pragma unroll
+    for (int s = 0; s < 8; ++s)
+        if (yi[s] != 0.0) Y[c8 + s] = TO((double)Y[c8 + s] + yi[s]);
+}
+
+template <class TO, class TC, class TW>
+__global__ void k_tcoarse(Tables T, Coefs<TC, TW> C, OMultiLevel ML, const int8_t* __restrict__ level,
+                          const int32_t* __restrict__ tcoarse, int n, const TO* __restrict__ X, TO* __restrict__ Y) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const int K = __ldg(tcoarse + q);
+    const int m = level[K];
+    const int off = ML.off[m], sK = K & 7, og = K >> 3, o = (K - off) >> 3;
+    int nb[6];
+    octet_neighbours(T, ML.ni[m], o, og, nb);
+    const double xK = (double)X[K];
+    double acc = 0.0;
+#pragma unroll
+    for (int dir = 0; dir < 6; ++dir) {
+        const int a = dir >> 1, bit = 1 << a;
+        const bool plus = dir & 1;
+        int Q = -1;
+        if (((sK & bit) != 0) != plus) Q = plus ? K + bit : K - bit;
+        else if (nb[dir] >= 0) Q = off + 8 * nb[dir] + (sK ^ bit);
+        if (Q < 0) continue;
+        const int co = __ldg(T.child_oct + Q);
+        if (co < 0) continue;
+        const double xbar = (double)X[Q];
+        const TC* cm = a == 0 ? C.cx : (a == 1 ? C.cy : C.cz);
+        const int t = plus ? 0 : __ldg(T.trec + co);
+#pragma unroll
+        for (int qq = 0; qq < 4; ++qq) {
+            const int s = clear_slot(a, qq) | (plus ? 0 : bit);
+            const int i = 8 * co + s;
+            const double cf = plus ? (double)tov(__ldg(cm + i))
+                                   : (double)tov(__ldg(C.tw + ((2 * a + 1) * 4 + qq) * T.nt + t));
+            acc += -0.5 * cf * ((xbar - xK) - ((double)X[i] - xK));
+        }
+    }
+    Y[K] = TO((double)Y[K] + acc);
+}
+
+template <class TO>
+__global__ void k_tdesc(Tables T, const int32_t* __restrict__ tdesc, int n, int ntree,
+                        const uint8_t* __restrict__ flags, const double* __restrict__ tseed, TO* __restrict__ Y) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const int og = __ldg(tdesc + q);
+    double acc = 0.0, w = 0.125;
+    int A = __ldg(T.oct_parent + og);
+    while (A >= 0 && A < ntree) {
+        acc += tseed[A] * w;
+        w *= 0.125;
+        A = __ldg(T.oct_parent + (A >> 3));
+    }
+#pragma unroll
+    for (int s = 0; s < 8; ++s)
+        if (flags[8 * og + s] & 1) Y[8 * og + s] = TO((double)Y[8 * og + s] + acc);
+}
+
 // Coarsest level (Alg. 4, l = 0): one CTA, one thread per octet, nu sweeps (half
 // red->black, half black->red), each a pass separated by __syncthreads; fas completes
 // the FAS right-hand side first; prolong prolongs onto the finer level at the end.

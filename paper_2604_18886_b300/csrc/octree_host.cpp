@@ -673,88 +673,27 @@ void leaf_neighbour(const HostTree& T, int64_t r, int dir, int8_t& kind, int64_t
 }
 
 // ---------------------------------------------------------------- adjoint tables
-namespace {
-
-// Leaves under cell g with their averaging weights (1/8 per level below g).
-void collect_support(const HostTree& T, int64_t g, double w, std::vector<std::pair<int32_t, double>>& out) {
-    const int32_t co = T.child_oct[g];
-    if (co < 0) {
-        out.push_back({(int32_t)g, w});
-        return;
-    }
-    for (int s = 0; s < 8; ++s) collect_support(T, 8 * (int64_t)co + s, w * 0.125, out);
-}
-
-bool fine_is_minus(const HostTree& T, int64_t f) {
-    return T.leaf_depth[T.f_minus[f]] == T.f_depth[f];
-}
-
-}  // namespace
-
-void build_transpose_correction(const HostTree& T, TransposeCorrection& out) {
-    struct E {
-        int32_t row, col, face;
-        double mult;
-    };
-    std::vector<E> e;
-    std::vector<std::pair<int32_t, double>> supp;
-    for (int64_t f = 0; f < T.nface; ++f) {
-        const int64_t rm = T.f_minus[f], rp = T.f_plus[f];
-        if (T.leaf_depth[rm] == T.leaf_depth[rp]) continue;
-        const bool fm = fine_is_minus(T, f);
-        const int32_t gi = T.leaf_cell[fm ? rm : rp];
-        const int32_t gK = T.leaf_cell[fm ? rp : rm];
-        const int64_t gP = T.oct_parent[gi >> 3];
-        const double hh = 0.5 / (double)((int64_t)T.n0 << T.f_depth[f]);
-        supp.clear();
-        collect_support(T, gP, 1.0, supp);
-        const int32_t fi = (int32_t)f;
-        e.push_back({gi, gK, fi, hh});
-        e.push_back({gK, gi, fi, -hh});
-        for (const auto& jw : supp) {
-            const double a = hh * jw.second;
-            e.push_back({gi, jw.first, fi, -a});
-            e.push_back({gK, jw.first, fi, a});
-            e.push_back({jw.first, gi, fi, a});
-            e.push_back({jw.first, gK, fi, -a});
-        }
-    }
-    std::stable_sort(e.begin(), e.end(), [](const E& x, const E& y) { return x.row < y.row; });
-    out = TransposeCorrection{};
-    out.col.resize(e.size());
-    out.face.resize(e.size());
-    out.mult.resize(e.size());
-    for (size_t q = 0; q < e.size(); ++q) {
-        if (q == 0 || e[q].row != e[q - 1].row) {
-            out.row.push_back(e[q].row);
-            out.ptr.push_back((int32_t)q);
-        }
-        out.col[q] = e[q].col;
-        out.face[q] = e[q].face;
-        out.mult[q] = e[q].mult;
-    }
-    out.ptr.push_back((int32_t)e.size());
-}
-
-void build_face_grad_tables(const HostTree& T, std::vector<int32_t>& fa, std::vector<int32_t>& fb,
-                            std::vector<int32_t>& fp, std::vector<double>& fh) {
-    fa.resize(T.nface);
-    fb.resize(T.nface);
-    fp.resize(T.nface);
-    fh.resize(T.nface);
-    for (int64_t f = 0; f < T.nface; ++f) {
-        const int64_t rm = T.f_minus[f], rp = T.f_plus[f];
-        fh[f] = 1.0 / (double)((int64_t)T.n0 << T.f_depth[f]);
-        if (T.leaf_depth[rm] == T.leaf_depth[rp]) {
-            fa[f] = T.leaf_cell[rm];
-            fb[f] = T.leaf_cell[rp];
-            fp[f] = -1;
-        } else {
-            const bool fm = fine_is_minus(T, f);
-            fa[f] = T.leaf_cell[fm ? rm : rp];
-            fb[f] = T.leaf_cell[fm ? rp : rm];
-            fp[f] = T.oct_parent[fa[f] >> 3];
-        }
+void build_adjoint_topology(const HostTree& T, AdjointTopology& out) {
+    out = AdjointTopology{};
+    // coarse leaves of the T-junctions: the K of every T face of every T octet
+    std::vector<int32_t> ks = par_compact<int32_t>(T.nt * 6, [&](int64_t q, int32_t& v) {
+        const int64_t go = T.t_oct[q / 6];
+        const int32_t n = T.nbr[(q % 6) * T.noct + go];
+        v = -2 - n;
+        return n <= -2;
+    });
+    std::sort(ks.begin(), ks.end());
+    ks.erase(std::unique(ks.begin(), ks.end()), ks.end());
+    out.tcoarse = std::move(ks);
+    // the T octets (children of the T parents) and every octet below them, level by level
+    std::vector<int32_t> front(T.t_oct.begin(), T.t_oct.end());
+    while (!front.empty()) {
+        out.tdesc.insert(out.tdesc.end(), front.begin(), front.end());
+        std::vector<int32_t> next = par_compact<int32_t>((int64_t)front.size() * 8, [&](int64_t q, int32_t& v) {
+            v = T.child_oct[8 * (int64_t)front[q >> 3] + (q & 7)];
+            return v >= 0;
+        });
+        front.swap(next);
     }
 }
 

@@ -81,22 +81,18 @@ void face_plus_cell(const HostTree& T, int64_t f, int32_t& i, int32_t& j, int32_
 // leaf, 2 coarser leaf, 3 refined neighbour; rank = canonical rank for kinds 1 and 2, else -1.
 void leaf_neighbour(const HostTree& T, int64_t r, int dir, int8_t& kind, int64_t& rank);
 
-// A^T - A of the composite leaf operator by rows.  Only T-junctions make A non-symmetric:
+// Topology of A^T - A of the composite leaf operator.  Only T-junctions make A non-symmetric:
 // a T sub-face f of the fine leaf i against the coarser leaf K contributes
-// (w_f/2) [(a_P - e_K)(e_i - e_K)^T - (e_i - e_K)(a_P - e_K)^T], a_P the averaging weights
-// of the leaves under i's parent P (1/8 per level; every tree cell is taken as active).
-// Entry e of row row[q] (q-th listed row, entries ptr[q]..ptr[q+1]) is
-// mult[e] * beta[face[e]] * x[col[e]]; rows and columns are global leaf cells.
-struct TransposeCorrection {
-    std::vector<int32_t> row, ptr, col, face;
-    std::vector<double> mult;
+// (w_f/2) [(a_P - e_K)(e_i - e_K)^T - (e_i - e_K)(a_P - e_K)^T], a_P the averaging weights of
+// the leaves under i's parent P (1/8 per level; every tree cell is taken as active).  The
+// correction is applied matrix-free (kernels k_tfine, k_tcoarse, k_tdesc) from
+//   tcoarse: the coarse leaves K (global cells, sorted, unique);
+//   tdesc:   the T octets followed by every octet below them (global octets), whose leaves
+//            receive the a_P terms.
+struct AdjointTopology {
+    std::vector<int32_t> tcoarse, tdesc;
 };
-void build_transpose_correction(const HostTree& T, TransposeCorrection& out);
-
-// Per canonical face: leaf cells a (the fine leaf at a T-junction, else the - leaf) and b,
-// the global cell of a's parent at a T-junction (-1 otherwise), and the face size h_f.
-void build_face_grad_tables(const HostTree& T, std::vector<int32_t>& fa, std::vector<int32_t>& fb,
-                            std::vector<int32_t>& fp, std::vector<double>& fh);
+void build_adjoint_topology(const HostTree& T, AdjointTopology& out);
 
 uint64_t morton3(uint64_t i, uint64_t j, uint64_t k);
 void demorton3(uint64_t key, uint64_t& i, uint64_t& j, uint64_t& k);

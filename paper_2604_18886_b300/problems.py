@@ -305,12 +305,11 @@ def rhs(p: Problem, leaves, faces=None, beta=None) -> np.ndarray:
     rng = np.random.default_rng(p.seed)
     if p.rhs == "divergence":
         assert faces is not None and beta is not None
-        hf = 1.0 / (p.desc.n0 * 2.0 ** faces["depth"])
-        u = rng.standard_normal(len(faces["axis"]))
-        flux = beta.astype(np.float64) * hf * hf * u
         b = np.zeros(n)
-        np.add.at(b, faces["minus"], flux)
-        np.add.at(b, faces["plus"], -flux)
+        nf = len(faces["axis"])
+        for first in range(0, nf, FACE_CHUNK):
+            sl = slice(first, min(nf, first + FACE_CHUNK))
+            divergence_accumulate(p, b, rng, {k: v[sl] for k, v in faces.items()}, beta[sl])
         return b - b.mean()
     if p.rhs == "normal":
         b = rng.standard_normal(n)
@@ -320,6 +319,111 @@ def rhs(p: Problem, leaves, faces=None, beta=None) -> np.ndarray:
     if p.rhs == "zero":
         return np.zeros(n)
     raise ValueError(p.rhs)
+
+
+# faces per piece when face arrays are processed in pieces (the divergence right-hand side
+# accumulates piece by piece in this order whatever the tree size)
+FACE_CHUNK = 1 << 25
+
+
+def divergence_accumulate(p: Problem, b, rng, faces, beta):
+    """Adds one piece of faces (in canonical order, continuing the draws of rng) to the
+    integrated divergence b: flux_f = beta_f h_f^2 u_f, u_f ~ N(0,1), added to the - leaf
+    and subtracted from the + leaf."""
+    n = len(b)
+    hf = 1.0 / (p.desc.n0 * 2.0 ** np.asarray(faces["depth"], np.float64))
+    u = rng.standard_normal(len(hf))
+    flux = np.asarray(beta, np.float64) * hf * hf * u
+    b += np.bincount(faces["minus"], weights=flux, minlength=n)
+    b -= np.bincount(faces["plus"], weights=flux, minlength=n)
+
+
+def _solid_sdf_torch(p: Problem, x, y, z):
+    import torch
+    phi = torch.full_like(x, float("inf"))
+    for (cx, cy, cz, r) in p.solid_spheres:
+        phi = torch.minimum(phi, torch.sqrt((x - cx) ** 2 + (y - cy) ** 2 + (z - cz) ** 2) - r)
+    for (lx, ly, lz, hx, hy, hz) in p.solid_boxes:
+        qx = torch.abs(x - 0.5 * (lx + hx)) - 0.5 * (hx - lx)
+        qy = torch.abs(y - 0.5 * (ly + hy)) - 0.5 * (hy - ly)
+        qz = torch.abs(z - 0.5 * (lz + hz)) - 0.5 * (hz - lz)
+        out = torch.sqrt(qx.clamp(min=0) ** 2 + qy.clamp(min=0) ** 2 + qz.clamp(min=0) ** 2)
+        ins = torch.clamp(torch.maximum(qx, torch.maximum(qy, qz)), max=0.0)
+        phi = torch.minimum(phi, out + ins)
+    if p.solid_sines:
+        sfield = torch.zeros_like(x)
+        for (kap, dx, dy, dz, th) in p.solid_sines:
+            sfield = sfield + torch.sin(2 * math.pi * kap * (dx * x + dy * y + dz * z) + th)
+        phi = torch.minimum(phi, sfield / len(p.solid_sines) - p.sine_offset)
+    return phi
+
+
+def _tri_positive_fraction_torch(a, b, c):
+    import torch
+    v, _ = torch.sort(torch.stack([a, b, c], dim=-1), dim=-1)
+    lo, mid, hi = v[..., 0], v[..., 1], v[..., 2]
+    one = (hi > 0) & (mid <= 0)
+    two = (mid > 0) & (lo <= 0)
+    f1 = hi * hi / torch.where(one, (hi - lo) * (hi - mid), torch.ones_like(hi))
+    f2 = 1.0 - lo * lo / torch.where(two, (mid - lo) * (hi - lo), torch.ones_like(hi))
+    out = torch.where(lo > 0, torch.ones_like(lo), torch.zeros_like(lo))
+    out = torch.where(one, f1, out)
+    return torch.where(two, f2, out)
+
+
+def face_beta_torch(p: Problem, axis, depth, i, j, k):
+    """face_beta for one piece of faces given as device tensors (the same formula as the
+    numpy version, evaluated in float64 with the device's sin): float32 tensor."""
+    import torch
+    if p.beta == "one":
+        return torch.ones(axis.shape, dtype=torch.float32, device=axis.device)
+    h = 1.0 / (p.desc.n0 * torch.pow(2.0, depth.double()))
+    base = torch.stack([i, j, k], dim=1).double() * h[:, None]
+    frac = torch.empty(axis.shape, dtype=torch.float64, device=axis.device)
+    for a in range(3):
+        sel = axis == a
+        if not bool(sel.any()):
+            continue
+        u, v = [q for q in range(3) if q != a]
+        b0, hh = base[sel], h[sel]
+
+        def corner(du, dv):
+            q = b0.clone()
+            q[:, u] += du * hh
+            q[:, v] += dv * hh
+            return _solid_sdf_torch(p, q[:, 0], q[:, 1], q[:, 2])
+
+        p00, p10, p11, p01 = corner(0, 0), corner(1, 0), corner(1, 1), corner(0, 1)
+        frac[sel] = 0.5 * (_tri_positive_fraction_torch(p00, p10, p11) + _tri_positive_fraction_torch(p00, p11, p01))
+    return torch.clamp(frac, 1e-3, 1.0).float()
+
+
+def large_inputs(p: Problem, n_leaves: int, n_faces: int, read_faces, device):
+    """Face beta (float32, on `device`) and right-hand side (float64 numpy, canonical leaf
+    order) of a problem too large to hold its face tables at once.  read_faces(first,
+    count) returns one piece of the canonical faces as numpy arrays (axis, depth, i, j, k,
+    minus, plus).  beta is evaluated on the device; the right-hand side follows rhs()."""
+    import torch
+    beta = torch.empty(n_faces, dtype=torch.float32, device=device)
+    rng = np.random.default_rng(p.seed)
+    b = np.zeros(n_leaves)
+    for first in range(0, n_faces, FACE_CHUNK):
+        cnt = min(FACE_CHUNK, n_faces - first)
+        f = read_faces(first, cnt)
+        t = {q: torch.from_numpy(f[q]).to(device) for q in ("axis", "depth", "i", "j", "k")}
+        bt = face_beta_torch(p, t["axis"], t["depth"], t["i"], t["j"], t["k"])
+        beta[first:first + cnt] = bt
+        if p.rhs == "divergence":
+            divergence_accumulate(p, b, rng, f, bt.cpu().numpy())
+    if p.rhs == "divergence":
+        b = b - b.mean()
+    elif p.rhs == "normal":
+        b = rng.standard_normal(n_leaves)
+        if p.neumann:
+            b = b - b.mean()
+    else:
+        raise ValueError("large_inputs supports the random right-hand sides only")
+    return beta, b
 
 
 def random_vector(n: int, seed: int) -> np.ndarray:

@@ -86,6 +86,18 @@ class Octree:
         out["plus"] = pl
         return out
 
+    def faces_range(self, first, count):
+        """Canonical faces first .. first+count-1 as int32 / int64 numpy arrays."""
+        a = {k: np.empty(count, np.int32) for k in ("axis", "depth", "i", "j", "k")}
+        mi = np.empty(count, np.int64)
+        pl = np.empty(count, np.int64)
+        L.check(L.lib().ocg_octree_export_faces_range(self._h, first, count, L.ptr(a["axis"]),
+                                                      L.ptr(a["depth"]), L.ptr(a["i"]), L.ptr(a["j"]),
+                                                      L.ptr(a["k"]), L.ptr(mi), L.ptr(pl)))
+        a["minus"] = mi
+        a["plus"] = pl
+        return a
+
     def level(self, m):
         n = C.c_int64()
         L.check(L.lib().ocg_octree_export_level(self._h, m, C.byref(n), None, None, None, None))

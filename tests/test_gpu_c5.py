@@ -1,0 +1,108 @@
+"""The large differentiable solve at full size: 128^3 root refined three times within 0.02
+(plus the cell's reach) of the zero set of a seeded sum of 8 plane sine waves
+(wavenumbers 1-4), effective 1024^3, fluid-fraction beta of the field's positive side,
+Neumann walls, divergence right-hand side (seed 7); loss L = 1/2 ||p - p_t||^2 with
+p_t ~ N(0,1) (seed 8).  Too large for the oracle: checked through properties that hold at
+any size (the FP64 residual of the returned solution, agreement of the mixed solve with
+the FP64 solve, grid-independent iteration counts against the same field at half the
+resolution) and the gradient against central finite differences on 32 faces (seed 9).
+
+Finite differences at 1e8 unknowns: the difference of two independently converged solves
+is dominated by their solver errors (each ~1e-12 relative to a solution whose loss is
+~1e7), not by the O(1e-9) change in L.  So p(beta +- eps) - p(beta) is obtained by solving
+the perturbed system for the difference itself,
+    A(beta +- eps) dp = -(A(beta +- eps) - A(beta)) p,
+which is the same quantity (an identity, not a linearisation), and
+    L+ - L- = <dp+ - dp-, p - p_t + (dp+ + dp-)/2>.
+"""
+import numpy as np
+import pytest
+
+from paper_2604_18886_b300 import problems as P
+from paper_2604_18886_b300 import solver as S
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+_STATE = {}
+
+
+def _setup(n0=128):
+    if n0 in _STATE:
+        return _STATE[n0]
+    p = P.c5(n0, 3)
+    g = S.Octree(p.desc)
+    beta, b = P.large_inputs(p, g.n_leaves, g.n_faces, g.faces_range, "cuda")
+    _STATE[n0] = (p, g, beta, torch.from_numpy(b).cuda())
+    return _STATE[n0]
+
+
+def test_full_size_c5_counts_and_mixed_solve():
+    p, g, beta, b = _setup(128)
+    assert 5e7 < g.n_leaves < 2e8, g.n_leaves
+    assert g.D == 3 and g.mc == -5
+    h = S.Hierarchy(g, beta, p.bc, S.mg_params(coef="f32"))
+    x, st = h.solve(b, tol=1e-6, precision="mixed")
+    assert st.converged and st.true_rel_res <= 1.5e-6, (st.iterations, st.true_rel_res)
+    assert abs(x.mean().item()) <= 1e-12 * x.abs().max().item()
+    # independent FP64 check of the returned solution through the FP64 operator apply
+    r = b - h.apply_A(x)
+    rr = (r - r.mean()).norm().item() / b.norm().item()
+    assert rr <= 1.5e-6, rr
+    # the same field at half the resolution (eff. 512) needs about as many iterations
+    p2, g2, beta2, b2 = _setup(64)
+    h2 = S.Hierarchy(g2, beta2, p2.bc, S.mg_params(coef="f32"))
+    x2, st2 = h2.solve(b2, tol=1e-6, precision="mixed")
+    assert st2.converged and abs(st.iterations - st2.iterations) <= 2, (st.iterations, st2.iterations)
+    _STATE["mixed"] = (x, st.iterations)
+
+
+def test_full_size_c5_gradient_matches_central_differences():
+    p, g, beta, b = _setup(128)
+    prm = S.mg_params(coef="f64", sweep="octet")
+    h0 = S.Hierarchy(g, beta, p.bc, prm)
+    x0, st = h0.solve(b, tol=1e-12, precision="fp64", max_iter=300)
+    assert st.converged
+    if "mixed" in _STATE:
+        xm = _STATE["mixed"][0]
+        assert ((xm - x0).norm() / x0.norm()).item() <= 1e-4
+    pt = torch.from_numpy(np.random.default_rng(8).standard_normal(g.n_leaves)).cuda()
+    lam, st = h0.solve(x0 - pt, tol=1e-12, precision="fp64", max_iter=300, transpose=True)
+    assert st.converged
+    grad = h0.face_grad(x0, lam)
+    rng = np.random.default_rng(9)
+    faces = np.sort(rng.choice(g.n_faces, 32, replace=False))
+    Ax0 = h0.apply_A(x0)
+    g0 = x0 - pt
+    fd = np.empty(len(faces))
+    for q, fi in enumerate(faces):
+        b0 = float(beta[fi])
+        eps = 1e-3 * b0
+        dps, epss = [], []
+        for sgn in (1.0, -1.0):
+            bb = beta.clone()
+            bb[fi] = float(np.float32(b0 + sgn * eps))
+            epss.append(abs(float(bb[fi]) - b0))
+            hs = S.Hierarchy(g, bb, p.bc, prm)
+            rhs = Ax0 - hs.apply_A(x0)
+            dp, s2 = hs.solve(rhs, tol=1e-12, precision="fp64", max_iter=300)
+            assert s2.converged
+            dps.append(dp)
+            del hs
+        dl = torch.dot(dps[0] - dps[1], g0 + 0.5 * (dps[0] + dps[1])).item()
+        fd[q] = dl / (epss[0] + epss[1])
+    got = grad[torch.from_numpy(faces).cuda()].cpu().numpy()
+    scale = np.abs(got).max()
+    assert scale > 0
+    err = np.abs(fd - got)
+    assert err.max() <= 1e-4 * scale, (err.max(), scale)
+    # dL/db = lambda: central differences in b_k (exact in b, the solve is linear)
+    lv = rng.choice(g.n_leaves, 4, replace=False)
+    for k in lv:
+        e = torch.zeros_like(b)
+        e[int(k)] = 1.0
+        d, s3 = h0.solve(e, tol=1e-12, precision="fp64", max_iter=300)
+        assert s3.converged
+        fdb = torch.dot(d, g0).item()
+        assert abs(fdb - lam[int(k)].item()) <= 1e-6 * lam.abs().max().item()

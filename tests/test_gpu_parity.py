@@ -67,6 +67,7 @@ CASES = {
     "c2_16_neumann": lambda: _neumann(P.c2(16)),
     "c3_16_d2": lambda: P.c3(16, 2),
     "c4_t1": lambda: P.c4_tree(1),
+    "c5_8_d2": lambda: P.c5(8, 2),
     "band_12_d2": lambda: P.Problem("band12", P.OctreeDesc(12, 2, P.REFINE_SDF_BAND, band=0.05,
                                                               spheres=[(0.45, 0.55, 0.5, 0.23)]),
                                     (1, 0, 1, 0, 0, 1), beta="one", rhs="normal", seed=3),
@@ -158,7 +159,7 @@ def test_pcg_fp64_follows_oracle_iterates(name):
 
 
 @pytest.mark.parametrize("precision", ["mixed", "fp32"])
-@pytest.mark.parametrize("name", ["c2_16", "c2_16_neumann", "c3_16_d2", "c4_t1"])
+@pytest.mark.parametrize("name", ["c2_16", "c2_16_neumann", "c3_16_d2", "c4_t1", "c5_8_d2"])
 def test_pcg_solution_within_1e5(name, precision):
     p = CASES[name]()
     t, H, g, gh, f, beta = build(p, "f32")
