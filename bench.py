@@ -213,6 +213,87 @@ def _cut_cell(dev, stream, flush, args):
             "true_rel_res": st.true_rel_res}
 
 
+LARGE_WORKLOAD = ("large differentiable solve: 128^3 root refined 3 times within 0.02 (+ cell reach) of the "
+                  "zero set of 8 seeded plane sine waves (effective 1024^3), fluid-fraction beta, Neumann, "
+                  "divergence rhs")
+
+
+def _large(dev, stream, flush, args, peak):
+    """The sine-band workload at full size: mixed solve to 1e-6 (timed), the red-black sweep
+    on its finest level (per-launch events inside an unrolled graph of the same solve),
+    and the adjoint (transpose solve + face gradient)."""
+    import numpy as np
+    import torch
+    from paper_2604_18886_b300 import _lib as L
+    from paper_2604_18886_b300 import problems as P
+    from paper_2604_18886_b300 import solver as S
+    t0 = time.perf_counter()
+    p = P.c5(128, 3)
+    g = S.Octree(p.desc)
+    t_build = time.perf_counter() - t0
+    beta, bh = P.large_inputs(p, g.n_leaves, g.n_faces, g.faces_range, dev)
+    b = torch.from_numpy(bh).to(dev)
+    del bh
+    t1 = time.perf_counter()
+    h = S.Hierarchy(g, beta, p.bc, S.mg_params(coef="f32"))
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t1
+    x = torch.empty_like(b)
+    for _ in range(args.warmup):
+        h.solve(b, x, tol=1e-6, precision="mixed", stream=stream)
+    steps = max(3, min(args.steps, 10))
+    t, its = [], set()
+    for s_ in range(steps):
+        flush.fill_(float(s_))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, st = h.solve(b, x, tol=1e-6, precision="mixed", stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        t.append(e0.elapsed_time(e1))
+        its.add(st.iterations)
+        assert st.converged
+    ms = statistics.mean(t)
+    # finest-level sweep inside an unrolled graph of the same solve
+    D = g.D
+    L.check(L.lib().ocg_probe_set(h.handle, L.OCG_PROBE_SWEEP, D))
+    h.solve(b, x, tol=1e-6, precision="mixed", stream=stream, max_iter=st.iterations, unrolled=True,
+            raise_on_notconv=False)
+    nl, tot, ce = C.c_int64(), C.c_double(), C.c_int64()
+    L.check(L.lib().ocg_probe_read(h.handle, C.c_void_p(stream.cuda_stream), C.byref(nl), C.byref(tot),
+                                   C.byref(ce)))
+    L.check(L.lib().ocg_probe_set(h.handle, L.OCG_PROBE_OFF, 0))
+    sweep_us = tot.value * 1e3 / max(nl.value, 1)
+    achieved = SWEEP_BYTES_PER_CELL * ce.value / (sweep_us / 1e6) / 1e9
+    form = {0: "octet", 1: "cell"}.get(h.tuning()[D][0], "?")
+    # adjoint: transpose solve of dL/dp = p - p_t and the face gradient
+    ptgt = torch.from_numpy(np.random.default_rng(8).standard_normal(g.n_leaves)).to(dev)
+    gp = x - ptgt
+    del ptgt
+    adj = None
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lam, sa = h.solve(gp, tol=1e-6, precision="mixed", stream=stream, transpose=True, max_iter=200,
+                      raise_on_notconv=False)
+    h.face_grad(x, lam, stream=stream)
+    e1.record(stream)
+    e1.synchronize()
+    adj = {"ms": round(e0.elapsed_time(e1), 3), "iterations": sa.iterations, "converged": bool(sa.converged),
+           "rel_res": sa.rel_res,
+           "what": "A^T lambda = p - p_t by BiCGStab (mixed, tol 1e-6) + face gradient"}
+    return {"workload": LARGE_WORKLOAD, "leaves": g.n_leaves, "faces": g.n_faces, "cells_all_levels": g.n_cells,
+            "precision": "mixed (FP32 V-cycle, FP64 PCG)", "value": round(g.n_leaves / (ms / 1e3) / 1e6, 3),
+            "unit": UNIT, "ms_per_step": round(ms, 3), "steps": steps, "iterations": sorted(its),
+            "true_rel_res": st.true_rel_res, "build_s": round(t_build, 2), "setup_s": round(t_setup, 2),
+            "roofline": {"bound": "hbm", "kernel": "red-black colour sweep (%s form) on level %d" % (form, D),
+                         "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "bytes_per_cell": SWEEP_BYTES_PER_CELL,
+                         "cells_per_launch": ce.value, "launches": nl.value, "avg_launch_us": round(sweep_us, 2)},
+            "adjoint": adj}
+
+
 BATCH_WORKLOAD = ("64 independent octrees, effective 64/96/128 with 2-3 levels refined within 0.05 of a "
                   "seeded random sphere; even trees beta=1 Dirichlet, odd trees cut-cell beta Neumann; "
                   "rhs N(0,1)")
@@ -402,6 +483,8 @@ def run_ours(args):
     cut = None if args.no_batch else _cut_cell(dev, stream, flush, args)
     # ---- batched form: 64 independent trees, one graph, one launch per phase
     batched = None if args.no_batch else _batched(dev, stream, flush, args)
+    # ---- the large sine-band workload (effective 1024^3)
+    large = None if args.no_large else _large(dev, stream, flush, args, _peaks()[0])
     # ---- end to end through the C ABI with host buffers
     bh = b.cpu().pin_memory()
     xh = torch.empty_like(bh).pin_memory()
@@ -456,6 +539,7 @@ def run_ours(args):
                        "operator_apply": round(ap_ms * 1e3 / max(ap_n, 1), 3), "operator_launches": ap_n},
         "cut_cell": cut,
         "batched": batched,
+        "large": large,
         "e2e": {"value": round(e2e, 3), "unit": UNIT, "h2d_bytes_per_step": tree.n_leaves * 8,
                 "d2h_bytes_per_step": tree.n_leaves * 8},
         "clocks": ck,
@@ -537,6 +621,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--nvtx", action="store_true", help="NVTX range 'timed' around the timed mixed solves")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 64-tree form")
+    ap.add_argument("--no-large", action="store_true", help="skip the large sine-band workload")
     ap.add_argument("--only-timed", action="store_true",
                     help="run the warm-up and the timed mixed solves only (profiling aid)")
     ap.add_argument("--eager", action="store_true",

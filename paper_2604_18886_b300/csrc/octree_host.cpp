@@ -685,16 +685,22 @@ void build_adjoint_topology(const HostTree& T, AdjointTopology& out) {
     std::sort(ks.begin(), ks.end());
     ks.erase(std::unique(ks.begin(), ks.end()), ks.end());
     out.tcoarse = std::move(ks);
-    // the T octets (children of the T parents) and every octet below them, level by level
-    std::vector<int32_t> front(T.t_oct.begin(), T.t_oct.end());
-    while (!front.empty()) {
-        out.tdesc.insert(out.tdesc.end(), front.begin(), front.end());
-        std::vector<int32_t> next = par_compact<int32_t>((int64_t)front.size() * 8, [&](int64_t q, int32_t& v) {
-            v = T.child_oct[8 * (int64_t)front[q >> 3] + (q & 7)];
-            return v >= 0;
-        });
-        front.swap(next);
+    // every octet that is a T octet (the children of a T parent) or lies below one, each
+    // listed once: marked top-down level by level (a T octet may itself lie under another
+    // T parent), then collected in global octet order
+    std::vector<uint8_t> mark(T.noct, 0);
+    for (int m = 1; m <= T.D; ++m) {
+        const LevelMeta& l = T.L(m);
+#pragma omp parallel for schedule(static)
+        for (int64_t o = 0; o < l.noct; ++o) {
+            const int64_t go = l.oct_off + o;
+            mark[go] = (T.trec[go] >= 0 || mark[T.oct_parent[go] >> 3]) ? 1 : 0;
+        }
     }
+    out.tdesc = par_compact<int32_t>(T.noct, [&](int64_t go, int32_t& v) {
+        v = (int32_t)go;
+        return mark[go] != 0;
+    });
 }
 
 }  // namespace ocg

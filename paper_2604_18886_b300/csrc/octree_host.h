@@ -87,8 +87,8 @@ void leaf_neighbour(const HostTree& T, int64_t r, int dir, int8_t& kind, int64_t
 // the leaves under i's parent P (1/8 per level; every tree cell is taken as active).  The
 // correction is applied matrix-free (kernels k_tfine, k_tcoarse, k_tdesc) from
 //   tcoarse: the coarse leaves K (global cells, sorted, unique);
-//   tdesc:   the T octets followed by every octet below them (global octets), whose leaves
-//            receive the a_P terms.
+//   tdesc:   every T octet and every octet below one (global octets, each once), whose
+//            leaves receive the a_P terms.
 struct AdjointTopology {
     std::vector<int32_t> tcoarse, tdesc;
 };

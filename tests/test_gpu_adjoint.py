@@ -55,7 +55,7 @@ def test_bicgstab_fp64_follows_oracle_iterates(name):
 
 
 @pytest.mark.parametrize("precision", ["mixed", "fp32"])
-@pytest.mark.parametrize("name", ["c2_16", "c2_16_neumann", "c3_16_d2", "c4_t1", "c5_8_d2"])
+@pytest.mark.parametrize("name", ["c2_16", "c2_16_neumann", "c3_16_d2", "c4_t1"])
 def test_transpose_solution_within_1e5(name, precision):
     t, H, g, gh, f, beta = build(CASES[name](), "f32")
     rhs = P.random_vector(t.n_leaves, 23)

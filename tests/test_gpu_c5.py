@@ -55,7 +55,9 @@ def test_full_size_c5_counts_and_mixed_solve():
     h2 = S.Hierarchy(g2, beta2, p2.bc, S.mg_params(coef="f32"))
     x2, st2 = h2.solve(b2, tol=1e-6, precision="mixed")
     assert st2.converged and abs(st.iterations - st2.iterations) <= 2, (st.iterations, st2.iterations)
-    _STATE["mixed"] = (x, st.iterations)
+    x9, st9 = h.solve(b, tol=1e-9, precision="mixed", max_iter=300)
+    assert st9.converged and st9.true_rel_res <= 2e-9
+    _STATE["mixed"] = (x, x9)
 
 
 def test_full_size_c5_gradient_matches_central_differences():
@@ -65,8 +67,17 @@ def test_full_size_c5_gradient_matches_central_differences():
     x0, st = h0.solve(b, tol=1e-12, precision="fp64", max_iter=300)
     assert st.converged
     if "mixed" in _STATE:
-        xm = _STATE["mixed"][0]
-        assert ((xm - x0).norm() / x0.norm()).item() <= 1e-4
+        # a relative residual of 1e-6 does not bound the cut-cell solution error by 1e-5:
+        # the mixed tol-1e-6 solution may be 1.5x as far from the tight FP64 solution as the
+        # FP64 solver's own tol-1e-6 iterate (+1e-5); the mixed solve to 1e-9 within 1e-5
+        xm, x9 = _STATE["mixed"]
+        x6, _ = h0.solve(b, tol=1e-6, precision="fp64", max_iter=300)
+
+        def rel(a):
+            return ((a - x0).abs().max() / x0.abs().max()).item()
+
+        assert rel(xm) <= 1.5 * rel(x6) + 1e-5, (rel(xm), rel(x6))
+        assert rel(x9) <= 1e-5, rel(x9)
     pt = torch.from_numpy(np.random.default_rng(8).standard_normal(g.n_leaves)).cuda()
     lam, st = h0.solve(x0 - pt, tol=1e-12, precision="fp64", max_iter=300, transpose=True)
     assert st.converged
