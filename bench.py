@@ -228,7 +228,7 @@ def _large(dev, stream, flush, args, peak):
     from paper_2604_18886_b300 import problems as P
     from paper_2604_18886_b300 import solver as S
     t0 = time.perf_counter()
-    p = P.c5(128, 3)
+    p = P.c5(args.large_n0, 3)
     g = S.Octree(p.desc)
     t_build = time.perf_counter() - t0
     beta, bh = P.large_inputs(p, g.n_leaves, g.n_faces, g.faces_range, dev)
@@ -241,20 +241,28 @@ def _large(dev, stream, flush, args, peak):
     x = torch.empty_like(b)
     for _ in range(args.warmup):
         h.solve(b, x, tol=1e-6, precision="mixed", stream=stream)
-    steps = max(3, min(args.steps, 10))
+    steps = max(1 if args.only_large else 3, min(args.steps, 10))
     t, its = [], set()
     for s_ in range(steps):
         flush.fill_(float(s_))
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        _, st = h.solve(b, x, tol=1e-6, precision="mixed", stream=stream)
+        if args.nvtx:
+            torch.cuda.nvtx.range_push("timed")
+        _, st = h.solve(b, x, tol=1e-6, precision="mixed", stream=stream, eager=args.eager)
+        if args.nvtx:
+            torch.cuda.nvtx.range_pop()
         e1.record(stream)
         e1.synchronize()
         t.append(e0.elapsed_time(e1))
         its.add(st.iterations)
         assert st.converged
     ms = statistics.mean(t)
+    if args.only_large:
+        return {"workload": LARGE_WORKLOAD, "n0": args.large_n0, "leaves": g.n_leaves,
+                "value": round(g.n_leaves / (ms / 1e3) / 1e6, 3), "unit": UNIT, "ms_per_step": round(ms, 3),
+                "steps": steps, "iterations": sorted(its), "note": "--only-large (profiling aid)"}
     # finest-level sweep inside an unrolled graph of the same solve
     D = g.D
     L.check(L.lib().ocg_probe_set(h.handle, L.OCG_PROBE_SWEEP, D))
@@ -266,7 +274,8 @@ def _large(dev, stream, flush, args, peak):
     L.check(L.lib().ocg_probe_set(h.handle, L.OCG_PROBE_OFF, 0))
     sweep_us = tot.value * 1e3 / max(nl.value, 1)
     achieved = SWEEP_BYTES_PER_CELL * ce.value / (sweep_us / 1e6) / 1e9
-    form = {0: "octet", 1: "cell"}.get(h.tuning()[D][0], "?")
+    tun = h.tuning()
+    form = S.SWEEP_FORM_NAMES.get(tun[D][0], "?")
     # adjoint: transpose solve of dL/dp = p - p_t and the face gradient
     ptgt = torch.from_numpy(np.random.default_rng(8).standard_normal(g.n_leaves)).to(dev)
     gp = x - ptgt
@@ -287,6 +296,9 @@ def _large(dev, stream, flush, args, peak):
             "precision": "mixed (FP32 V-cycle, FP64 PCG)", "value": round(g.n_leaves / (ms / 1e3) / 1e6, 3),
             "unit": UNIT, "ms_per_step": round(ms, 3), "steps": steps, "iterations": sorted(its),
             "true_rel_res": st.true_rel_res, "build_s": round(t_build, 2), "setup_s": round(t_setup, 2),
+            "sweep_forms": {str(m): {"form": S.SWEEP_FORM_NAMES.get(v[0], "shared-memory tail"),
+                                     "us_octet": round(v[1], 2), "us_cell": round(v[2], 2), "us_quad": round(v[3], 2)}
+                            for m, v in tun.items() if m >= 0},
             "roofline": {"bound": "hbm", "kernel": "red-black colour sweep (%s form) on level %d" % (form, D),
                          "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "bytes_per_cell": SWEEP_BYTES_PER_CELL,
@@ -395,6 +407,12 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
+    if args.only_large:
+        flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+        out = _large(dev, stream, flush, args, _peaks()[0])
+        if rank == 0:
+            print(json.dumps(out), flush=True)
+        return
     p, tree, hier, b, np = _setup(dev)
     x = torch.empty_like(b)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
@@ -421,9 +439,10 @@ def run_ours(args):
     ck = clocks.stop(mark0, mark1)
     ms = statistics.mean(times)
     total_ms = sum(times)
-    tuning = {str(m): {"form": ["octet", "cell"][f] if f >= 0 else "shared-memory tail",
-                       "us_octet": round(a, 2), "us_cell": round(bq, 2)}
-              for m, (f, a, bq) in hier.tuning().items()}
+    from paper_2604_18886_b300 import solver as S
+    tuning = {str(m): {"form": S.SWEEP_FORM_NAMES[f] if f >= 0 else "shared-memory tail",
+                       "us_octet": round(a, 2), "us_cell": round(bq, 2), "us_quad": round(qq, 2)}
+              for m, (f, a, bq, qq) in hier.tuning().items()}
     total_ms = max_over_ranks(total_ms, dev)
     value = replica_throughput(tree.n_leaves, args.steps, world, total_ms)
     if args.only_timed:
@@ -449,7 +468,7 @@ def run_ours(args):
         L.check(L.lib().ocg_probe_set(hier.handle, L.OCG_PROBE_OFF, 0))
         return nl_t, ms_t, cells
     sw_n, sw_ms, sw_cells = probe(L.OCG_PROBE_SWEEP, big)
-    tail_top = max([m for m, (f, a, bq) in hier.tuning().items() if f < 0 and m < 0] or [tree.mc])
+    tail_top = max([m for m, v in hier.tuning().items() if v[0] < 0 and m < 0] or [tree.mc])
     tl_n, tl_ms, tl_cells = probe(L.OCG_PROBE_TAIL, tail_top)
     ap_n, ap_ms, ap_cells = probe(L.OCG_PROBE_APPLY, 0)
     # ---- plain FP32 beside it
@@ -622,6 +641,10 @@ def main():
     ap.add_argument("--nvtx", action="store_true", help="NVTX range 'timed' around the timed mixed solves")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 64-tree form")
     ap.add_argument("--no-large", action="store_true", help="skip the large sine-band workload")
+    ap.add_argument("--only-large", action="store_true",
+                    help="run only the timed solves of the large sine-band workload (profiling aid)")
+    ap.add_argument("--large-n0", type=int, default=128,
+                    help="root grid of the sine-band workload (128: effective 1024^3; smaller for profiling)")
     ap.add_argument("--only-timed", action="store_true",
                     help="run the warm-up and the timed mixed solves only (profiling aid)")
     ap.add_argument("--eager", action="store_true",

@@ -230,7 +230,25 @@ __global__ void __launch_bounds__(BLK) k_update(TO* __restrict__ x, TO* __restri
     __shared__ double sh[32];
     const TO alpha = TO(R.S[S_ALPHA]);
     double rr = 0.0, rs = 0.0;
-    for (int i = blockIdx.x * BLK + threadIdx.x; i < n; i += gridDim.x * BLK) {
+    const int st = gridDim.x * BLK;
+    int i = blockIdx.x * BLK + threadIdx.x;
+    // four independent elements per thread and pass keep enough loads in flight
+    for (; i + 3 * st < n; i += 4 * st) {
+        TO xv[4], pv[4], rv[4], av[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) { xv[q] = x[i + q * st]; pv[q] = p[i + q * st]; rv[q] = r[i + q * st]; av[q] = Ap[i + q * st]; }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            x[i + q * st] = xv[q] + alpha * pv[q];
+            const TO rn = rv[q] - alpha * av[q];
+            r[i + q * st] = rn;
+            if (b32) b32[i + q * st] = TB(rn);
+            const double rd = (double)rn;
+            rr += rd * rd;
+            if (SUM) rs += rd;
+        }
+    }
+    for (; i < n; i += st) {
         x[i] = x[i] + alpha * p[i];
         const TO rn = r[i] - alpha * Ap[i];
         r[i] = rn;
@@ -260,7 +278,21 @@ template <class TA, class TB, bool SUM>
 __global__ void __launch_bounds__(BLK) k_dot(const TA* __restrict__ a, const TB* __restrict__ b, int n, Red R) {
     __shared__ double sh[32];
     double v = 0.0, s = 0.0;
-    for (int i = blockIdx.x * BLK + threadIdx.x; i < n; i += gridDim.x * BLK) {
+    const int st = gridDim.x * BLK;
+    int i = blockIdx.x * BLK + threadIdx.x;
+    for (; i + 3 * st < n; i += 4 * st) {
+        TA av[4];
+        TB bv[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) { av[q] = a[i + q * st]; bv[q] = b[i + q * st]; }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const double ai = (double)av[q];
+            v += ai * (double)bv[q];
+            if (SUM) s += ai;
+        }
+    }
+    for (; i < n; i += st) {
         const double ai = (double)a[i];
         v += ai * (double)b[i];
         if (SUM) s += ai;

@@ -232,8 +232,8 @@ struct ocg_hier {
     unsigned* cnt = nullptr;   // reduction arrival counter
     Probe probe;
     int red_blocks = 296;         // grid of the grid-stride reductions (2 per SM)
-    int sweep_form[MAXLEV * 2];   // per level (index m - mc): OCG_SWEEP_OCTET / _CELL
-    double tune_us[MAXLEV * 2][2];
+    int sweep_form[MAXLEV * 2];   // per level (index m - mc): OCG_SWEEP_OCTET / _CELL / _QUAD
+    double tune_us[MAXLEV * 2][3];
     // coarse tail: uniform levels run in one shared-memory CTA, per cycle value type
     int tail_top[2] = {TAIL_NONE, TAIL_NONE};   // [float, double]
     size_t tail_smem[2] = {0, 0};
@@ -409,6 +409,8 @@ struct Cycle {
             launch(c, OCG_PROBE_SWEEP, m, A.ncell, [&] {
                 if (form == OCG_SWEEP_CELL)
                     k_csweep<TV, TC, TW><<<nblk(A.ncell), BLK, 0, c.st>>>(A, h->t->tables(), C, U, B, colour, prolong);
+                else if (form == OCG_SWEEP_QUAD)
+                    k_qsweep<TV, TC, TW><<<nblk(A.ncell / 4), BLK, 0, c.st>>>(A, h->t->tables(), C, U, B, colour, prolong);
                 else
                     k_osweep<TV, TC, TW>
                         <<<nblk(A.ncell / 8, OBLK), OBLK, 0, c.st>>>(A, h->t->tables(), C, U, B, colour, prolong, 0);
@@ -510,8 +512,8 @@ void autotune_sweeps(ocg_hier* h) {
     const int tail_top = h->tail_top[std::is_same<TV, double>::value ? 1 : 0];
     for (int m = H.D; m > H.mc; --m) {
         if (m <= tail_top && tail_top != TAIL_NONE) break;
-        double us[2] = {0.0, 0.0};
-        for (int form = 0; form < 2; ++form) {
+        double us[3] = {0.0, 0.0, 0.0};
+        for (int form = 0; form < 3; ++form) {
             Ctx c{cs, nullptr, 0};
             Cycle<TV> cy{h, (TV*)h->U, (TV*)h->B, c};
             cudaGraph_t g = nullptr;
@@ -531,15 +533,29 @@ void autotune_sweeps(ocg_hier* h) {
             cudaGraphExecDestroy(ge);
             cudaGraphDestroy(g);
         }
-        h->tune_us[m - H.mc][0] = us[0];
-        h->tune_us[m - H.mc][1] = us[1];
-        h->sweep_form[m - H.mc] = us[1] < us[0] ? OCG_SWEEP_CELL : OCG_SWEEP_OCTET;
+        int best = OCG_SWEEP_OCTET;
+        for (int form = 0; form < 3; ++form) {
+            h->tune_us[m - H.mc][form] = us[form];
+            if (us[form] < us[best]) best = form;
+        }
+        h->sweep_form[m - H.mc] = best;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
 }
 
 // ------------------------------------------------------------------ composite operator
+int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            n <= 0)
+            n = 148;
+    }
+    return n;
+}
+
 OMultiLevel tree_levels(const HostTree& H) {
     OMultiLevel ML{};
     ML.n = H.D + 1;
@@ -582,9 +598,11 @@ void apply_outer(ocg_hier* h, Coefs<TC, TW> C, TO* P, TO* Y, int op, Ctx& c) {
     }
     ck_launch("avg");
     const OMultiLevel ML = tree_levels(H);
-    const Red R = make_red(h, ML.boff[ML.n], op);
+    // a bounded grid (blocks stride over the octet blocks): few partials to reduce
+    const int nb = std::min(ML.boff[ML.n], 16 * sm_count());
+    const Red R = make_red(h, nb, op);
     launch(c, OCG_PROBE_APPLY, 0, H.ntree, [&] {
-        k_oapply<TO, TC, TW><<<ML.boff[ML.n], OBLK, 0, c.st>>>(ML, t->tables(), C, P, Y, R);
+        k_oapply<TO, TC, TW><<<nb, OBLK, 0, c.st>>>(ML, t->tables(), C, P, Y, R);
     });
     ck_launch("apply");
 }
@@ -1085,7 +1103,7 @@ int ocg_setup_hierarchy(const ocg_octree* t, const float* beta, const int32_t bc
             !(prm->alpha > 0) || !std::isfinite(prm->beta_restrict))
             throw Status(OCG_EINVAL, "invalid multigrid parameters");
         if (prm->coef_dtype != OCG_F64 && prm->coef_dtype != OCG_F32) throw Status(OCG_EINVAL, "coef_dtype");
-        if (prm->sweep_form < OCG_SWEEP_AUTO || prm->sweep_form > OCG_SWEEP_CELL)
+        if (prm->sweep_form < OCG_SWEEP_AUTO || prm->sweep_form > OCG_SWEEP_QUAD)
             throw Status(OCG_EINVAL, "sweep_form");
         if (t->H.D - t->H.mc + 1 > 2 * MAXLEV) throw Status(OCG_EINVAL, "too many levels");
         if (prm->bf16_coarse && prm->coef_dtype != OCG_F32) throw Status(OCG_EINVAL, "bf16_coarse needs F32");
@@ -1170,17 +1188,18 @@ int ocg_setup_hierarchy(const ocg_octree* t, const float* beta, const int32_t bc
         choose_tail(h.get(), 1, sizeof(double));
         const int nlev = H.D - H.mc + 1;
         for (int q = 0; q < nlev; ++q) {
-            h->sweep_form[q] = prm->sweep_form == OCG_SWEEP_CELL ? OCG_SWEEP_CELL : OCG_SWEEP_OCTET;
-            h->tune_us[q][0] = h->tune_us[q][1] = -1.0;
+            h->sweep_form[q] = prm->sweep_form == OCG_SWEEP_AUTO ? OCG_SWEEP_OCTET : prm->sweep_form;
+            h->tune_us[q][0] = h->tune_us[q][1] = h->tune_us[q][2] = -1.0;
         }
         if (prm->sweep_form == OCG_SWEEP_AUTO) {
             if (prm->coef_dtype == OCG_F64) autotune_sweeps<double>(h.get());
             else autotune_sweeps<float>(h.get());
         }
-        int dev = 0, sms = 148;
-        if (cudaGetDevice(&dev) == cudaSuccess &&
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
-            h->red_blocks = 2 * sms;
+        // grid of the grid-stride reductions: 2 blocks per SM on small trees (few partials,
+        // short latency chain), up to 8 per SM (full occupancy) once every thread has at
+        // least 8 elements
+        const int sms = sm_count();
+        h->red_blocks = (int)std::max<int64_t>(2 * sms, std::min<int64_t>(8 * sms, H.ntree / (BLK * 8)));
         *out = h.release();
     });
 }
@@ -1210,9 +1229,10 @@ int ocg_hier_export_coefs(const ocg_hier* h, int32_t m, double* c, double* cx, d
     });
 }
 
-int ocg_hier_tuning(const ocg_hier* h, int32_t m, int32_t* form, double* us_octet, double* us_cell) {
+int ocg_hier_tuning(const ocg_hier* h, int32_t m, int32_t* form, double* us_octet, double* us_cell,
+                    double* us_quad) {
     return guard([&] {
-        if (!h || !form || !us_octet || !us_cell) throw Status(OCG_EINVAL, "null argument");
+        if (!h || !form || !us_octet || !us_cell || !us_quad) throw Status(OCG_EINVAL, "null argument");
         const HostTree& H = h->t->H;
         if (m < H.mc || m > H.D) throw Status(OCG_EINVAL, "level out of range");
         const int W = h->c64[0] ? 1 : 0;
@@ -1220,6 +1240,7 @@ int ocg_hier_tuning(const ocg_hier* h, int32_t m, int32_t* form, double* us_octe
         *form = (in_tail || m == H.mc) ? -1 : h->sweep_form[m - H.mc];
         *us_octet = h->tune_us[m - H.mc][0];
         *us_cell = h->tune_us[m - H.mc][1];
+        *us_quad = h->tune_us[m - H.mc][2];
     });
 }
 

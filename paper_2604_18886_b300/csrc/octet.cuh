@@ -367,6 +367,219 @@ __global__ void __launch_bounds__(BLK) k_csweep(LevelArgs A, Tables T, Coefs<TC,
     csweep_cell<TV, TC, TW>(A, T, C, U, B, blockIdx.x * BLK + threadIdx.x, colour, prolong);
 }
 
+// ------------------------------------------------------------ half-octet sweep
+// The same colour sweep with two threads per octet: thread hz = lane & 1 owns the z-layer
+// hz (slots 4 hz .. 4 hz + 3, contiguous), so its values and coefficients arrive in one
+// vector load per array (16 B in FP32); the partner lane (lane ^ 1) holds the other layer
+// and supplies the z-neighbours inside the octet and its half of the T-ghost mean by
+// shuffles; the face to a neighbouring octet reads that octet's matching layer with one
+// vector load (x and y faces: the same layer; z faces: the facing layer).  In-layer index
+// q = dx + 2 dy.
+__device__ __forceinline__ void ld4(const float* __restrict__ p, float (&r)[4]) {
+    const float4 a = *reinterpret_cast<const float4*>(p);
+    r[0] = a.x; r[1] = a.y; r[2] = a.z; r[3] = a.w;
+}
+__device__ __forceinline__ void ld4(const double* __restrict__ p, double (&r)[4]) {
+    const double2 a = reinterpret_cast<const double2*>(p)[0];
+    const double2 b = reinterpret_cast<const double2*>(p)[1];
+    r[0] = a.x; r[1] = a.y; r[2] = b.x; r[3] = b.y;
+}
+__device__ __forceinline__ void st4(float* __restrict__ p, const float (&r)[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(r[0], r[1], r[2], r[3]);
+}
+__device__ __forceinline__ void st4(double* __restrict__ p, const double (&r)[4]) {
+    reinterpret_cast<double2*>(p)[0] = make_double2(r[0], r[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(r[2], r[3]);
+}
+template <class TV>
+__device__ __forceinline__ void ldc4(const float* __restrict__ p, TV (&r)[4]) {
+    const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+    r[0] = TV(a.x); r[1] = TV(a.y); r[2] = TV(a.z); r[3] = TV(a.w);
+}
+template <class TV>
+__device__ __forceinline__ void ldc4(const double* __restrict__ p, TV (&r)[4]) {
+    const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+    const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+    r[0] = TV(a.x); r[1] = TV(a.y); r[2] = TV(b.x); r[3] = TV(b.y);
+}
+template <class TV>
+__device__ __forceinline__ void ldc4(const __nv_bfloat16* __restrict__ p, TV (&r)[4]) {
+    const uint2 raw = __ldg(reinterpret_cast<const uint2*>(p));
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&raw);
+    const float2 f0 = __bfloat1622float2(h[0]), f1 = __bfloat1622float2(h[1]);
+    r[0] = TV(f0.x); r[1] = TV(f0.y); r[2] = TV(f1.x); r[3] = TV(f1.y);
+}
+
+// neighbouring octet of local octet o in direction dir (arithmetic on uniform levels)
+__device__ __forceinline__ int octet_neighbour(const Tables& T, int ni, int o, int og, int dir) {
+    if (ni > 0) {
+        int c[3];
+        octet_coords(o, ni, c[0], c[1], c[2]);
+        const int a = dir >> 1;
+        const int stride = a == 0 ? 1 : (a == 1 ? ni : ni * ni);
+        if (dir & 1) return c[a] < ni - 1 ? o + stride : -1;
+        return c[a] > 0 ? o - stride : -1;
+    }
+    return __ldg(T.nbr + dir * T.noct + og);
+}
+
+template <class TV, class TC, class TW>
+__global__ void __launch_bounds__(BLK) k_qsweep(LevelArgs A, Tables T, Coefs<TC, TW> C, TV* __restrict__ U,
+                                                TV* __restrict__ B, int colour, int prolong) {
+    const int tid = blockIdx.x * BLK + threadIdx.x;
+    const int noct = A.ncell >> 3;
+    const bool valid = (tid >> 1) < noct;
+    const int o = valid ? (tid >> 1) : noct - 1;   // past the end: a copy of the last octet, no writes
+    const int hz = tid & 1;
+    const int c8 = A.off + 8 * o, og = c8 >> 3, base = c8 + 4 * hz;
+    TV u[4], b[4], d[4], cx[4], cy[4], cz[4];
+    ld4(U + base, u);
+    ld4(B + base, b);
+    ldc4<TV>(C.d + base, d);
+    ldc4<TV>(C.cx + base, cx);
+    ldc4<TV>(C.cy + base, cy);
+    ldc4<TV>(C.cz + base, cz);
+    // octet mean over the active cells (both layers)
+    TV ssum = TV(0);
+    int cnt = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if (d[q] != TV(0)) { ssum += u[q]; ++cnt; }
+    ssum += __shfl_xor_sync(FULL, ssum, 1);
+    cnt += __shfl_xor_sync(FULL, cnt, 1);
+    const TV ubar = ssum * inv_count<TV>(cnt);
+    TV up[4], czp[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        up[q] = __shfl_xor_sync(FULL, u[q], 1);
+        czp[q] = __shfl_xor_sync(FULL, cz[q], 1);
+    }
+    TV Au[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) Au[q] = d[q] * u[q];
+    // faces inside the layer (coefficient kept by the + cell) and between the layers
+    Au[0] += cx[1] * u[1]; Au[1] += cx[1] * u[0]; Au[2] += cx[3] * u[3]; Au[3] += cx[3] * u[2];
+    Au[0] += cy[2] * u[2]; Au[2] += cy[2] * u[0]; Au[1] += cy[3] * u[3]; Au[3] += cy[3] * u[1];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) Au[q] += (hz ? cz[q] : czp[q]) * up[q];
+    const int off = A.off;
+    const TV half = TV(0.5);
+    // x- : cells q = 0, 2 against the - octet's q = 1, 3 of this layer
+    {
+        const int v = octet_neighbour(T, A.ni, o, og, 0);
+        if (v >= 0) {
+            TV nu[4];
+            ld4(U + off + 8 * v + 4 * hz, nu);
+            Au[0] += cx[0] * nu[1];
+            Au[2] += cx[2] * nu[3];
+        } else if (v <= -2) {
+            const TV uK = U[-2 - v];
+            Au[0] += cx[0] * (u[0] + (uK - ubar) * half);
+            Au[2] += cx[2] * (u[2] + (uK - ubar) * half);
+        }
+    }
+    // y- : cells q = 0, 1 against the - octet's q = 2, 3
+    {
+        const int v = octet_neighbour(T, A.ni, o, og, 2);
+        if (v >= 0) {
+            TV nu[4];
+            ld4(U + off + 8 * v + 4 * hz, nu);
+            Au[0] += cy[0] * nu[2];
+            Au[1] += cy[1] * nu[3];
+        } else if (v <= -2) {
+            const TV uK = U[-2 - v];
+            Au[0] += cy[0] * (u[0] + (uK - ubar) * half);
+            Au[1] += cy[1] * (u[1] + (uK - ubar) * half);
+        }
+    }
+    // x+ : cells q = 1, 3 against the + octet's q = 0, 2 (their c_x- is the face's)
+    {
+        const int w = octet_neighbour(T, A.ni, o, og, 1);
+        if (w >= 0) {
+            TV nu[4], nc[4];
+            ld4(U + off + 8 * w + 4 * hz, nu);
+            ldc4<TV>(C.cx + off + 8 * w + 4 * hz, nc);
+            Au[1] += nc[0] * nu[0];
+            Au[3] += nc[2] * nu[2];
+        } else if (w <= -2) {
+            const TV uK = U[-2 - w];
+            const int t = __ldg(T.trec + og);
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const int q = 2 * k + 1;   // sub-face index of slot 4 hz + q on the x+ face
+                const TV cf = TV(tov(__ldg(C.tw + (1 * 4 + (k | (hz << 1))) * T.nt + t)));
+                Au[q] += cf * (u[q] + (uK - ubar) * half);
+            }
+        }
+    }
+    // y+ : cells q = 2, 3 against the + octet's q = 0, 1
+    {
+        const int w = octet_neighbour(T, A.ni, o, og, 3);
+        if (w >= 0) {
+            TV nu[4], nc[4];
+            ld4(U + off + 8 * w + 4 * hz, nu);
+            ldc4<TV>(C.cy + off + 8 * w + 4 * hz, nc);
+            Au[2] += nc[0] * nu[0];
+            Au[3] += nc[1] * nu[1];
+        } else if (w <= -2) {
+            const TV uK = U[-2 - w];
+            const int t = __ldg(T.trec + og);
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const int q = 2 + k;       // sub-face index (q & 1) | (hz << 1) on the y+ face
+                const TV cf = TV(tov(__ldg(C.tw + (3 * 4 + (k | (hz << 1))) * T.nt + t)));
+                Au[q] += cf * (u[q] + (uK - ubar) * half);
+            }
+        }
+    }
+    // z : layer 0 faces the - octet's layer 1, layer 1 faces the + octet's layer 0
+    if (hz == 0) {
+        const int v = octet_neighbour(T, A.ni, o, og, 4);
+        if (v >= 0) {
+            TV nu[4];
+            ld4(U + off + 8 * v + 4, nu);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) Au[q] += cz[q] * nu[q];
+        } else if (v <= -2) {
+            const TV uK = U[-2 - v];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) Au[q] += cz[q] * (u[q] + (uK - ubar) * half);
+        }
+    } else {
+        const int w = octet_neighbour(T, A.ni, o, og, 5);
+        if (w >= 0) {
+            TV nu[4], nc[4];
+            ld4(U + off + 8 * w, nu);
+            ldc4<TV>(C.cz + off + 8 * w, nc);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) Au[q] += nc[q] * nu[q];
+        } else if (w <= -2) {
+            const TV uK = U[-2 - w];
+            const int t = __ldg(T.trec + og);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const TV cf = TV(tov(__ldg(C.tw + (5 * 4 + q) * T.nt + t)));
+                Au[q] += cf * (u[q] + (uK - ubar) * half);
+            }
+        }
+    }
+    TV un[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int s = 4 * hz + q;
+        un[q] = ((__popc(s) & 1) == colour && d[q] != TV(0)) ? u[q] + divide(b[q] - Au[q], d[q]) : u[q];
+    }
+    if (!valid) return;
+    st4(U + base, un);   // the other colour's values are rewritten unchanged
+    if (prolong) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int co = __ldg(T.child_oct + base + q);
+            if (co >= 0) octet_prolong<TV, TC>(C.d, U, co, un[q]);
+        }
+    }
+}
+
 // Residual and FAS restriction (Alg. 4): r = b - A^m u; the parent gets
 // b_P = (beta/alpha) sum r (A^{m-1} u* is added on the coarse level by the fixb pass) and
 // u_P = u* = mean of the active children.
@@ -435,14 +648,18 @@ struct OMultiLevel {
     int boff[MAXLEV + 1];
 };
 
+// The grid is bounded (a few blocks per SM) and strides over the per-level octet blocks
+// boff[], so the dot product reduces over at most gridDim partials.
 template <class TO, class TC, class TW>
 __global__ void __launch_bounds__(OBLK) k_oapply(OMultiLevel ML, Tables T, Coefs<TC, TW> C, const TO* __restrict__ P,
                                                  TO* __restrict__ Y, Red R) {
     __shared__ double sh[32];
-    int l = 0;
-    while (l + 1 < ML.n && (int)blockIdx.x >= ML.boff[l + 1]) ++l;
-    const int o = ((int)blockIdx.x - ML.boff[l]) * OBLK + threadIdx.x;
     double dot = 0.0;
+    const int nvb = ML.boff[ML.n];
+    int l = 0;
+    for (int vb = blockIdx.x; vb < nvb; vb += gridDim.x) {
+    while (l + 1 < ML.n && vb >= ML.boff[l + 1]) ++l;
+    const int o = (vb - ML.boff[l]) * OBLK + threadIdx.x;
     if (o < ML.noct[l]) {
         const int c8 = ML.off[l] + 8 * o;
         OctState<TO> S;
@@ -457,6 +674,7 @@ __global__ void __launch_bounds__(OBLK) k_oapply(OMultiLevel ML, Tables T, Coefs
             Y[c8 + s] = leaf ? Ap[s] : TO(0);
             if (leaf) dot += (double)S.u[s] * (double)Ap[s];
         }
+    }
     }
     if (R.op != OP_NONE) red_finish(R, blockIdx.x, dot, 0.0, sh);
 }

@@ -109,7 +109,9 @@ class Octree:
         return i.astype(np.int64), j.astype(np.int64), k.astype(np.int64), leaf.astype(bool)
 
 
-SWEEP_FORMS = {"auto": L.OCG_SWEEP_AUTO, "octet": L.OCG_SWEEP_OCTET, "cell": L.OCG_SWEEP_CELL}
+SWEEP_FORMS = {"auto": L.OCG_SWEEP_AUTO, "octet": L.OCG_SWEEP_OCTET, "cell": L.OCG_SWEEP_CELL,
+               "quad": L.OCG_SWEEP_QUAD}
+SWEEP_FORM_NAMES = {L.OCG_SWEEP_OCTET: "octet", L.OCG_SWEEP_CELL: "cell", L.OCG_SWEEP_QUAD: "quad"}
 
 
 def mg_params(mu=1, nu_pre=2, nu_post=2, nu_coarsest=10, beta=2.0, alpha=2.0, coef="f32",
@@ -162,12 +164,12 @@ class Hierarchy:
         return out
 
     def tuning(self):
-        """{level: (form, us_octet, us_cell)} as chosen / measured at set-up."""
+        """{level: (form, us_octet, us_cell, us_quad)} as chosen / measured at set-up."""
         out = {}
         for m in range(self.tree.mc, self.tree.D + 1):
-            f, a, b = C.c_int32(), C.c_double(), C.c_double()
-            L.check(L.lib().ocg_hier_tuning(self._h, m, C.byref(f), C.byref(a), C.byref(b)))
-            out[m] = (f.value, a.value, b.value)
+            f, a, b, q = C.c_int32(), C.c_double(), C.c_double(), C.c_double()
+            L.check(L.lib().ocg_hier_tuning(self._h, m, C.byref(f), C.byref(a), C.byref(b), C.byref(q)))
+            out[m] = (f.value, a.value, b.value, q.value)
         return out
 
     @staticmethod
