@@ -235,7 +235,7 @@ def _large(dev, stream, flush, args, peak):
     b = torch.from_numpy(bh).to(dev)
     del bh
     t1 = time.perf_counter()
-    h = S.Hierarchy(g, beta, p.bc, S.mg_params(coef="f32"))
+    h = S.Hierarchy(g, beta, p.bc, S.mg_params(coef="f32", sweep=args.sweep))
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t1
     x = torch.empty_like(b)
@@ -259,10 +259,15 @@ def _large(dev, stream, flush, args, peak):
         its.add(st.iterations)
         assert st.converged
     ms = statistics.mean(t)
+    tun = h.tuning()
+    forms = {str(m): {"form": S.SWEEP_FORM_NAMES.get(v[0], "shared-memory tail"), "us_octet": round(v[1], 2),
+                      "us_cell": round(v[2], 2), "us_quad": round(v[3], 2), "us_tile": round(v[4], 2)}
+             for m, v in tun.items() if m >= 0}
     if args.only_large:
         return {"workload": LARGE_WORKLOAD, "n0": args.large_n0, "leaves": g.n_leaves,
                 "value": round(g.n_leaves / (ms / 1e3) / 1e6, 3), "unit": UNIT, "ms_per_step": round(ms, 3),
-                "steps": steps, "iterations": sorted(its), "note": "--only-large (profiling aid)"}
+                "steps": steps, "iterations": sorted(its), "sweep_forms": forms,
+                "note": "--only-large (profiling aid)"}
     # finest-level sweep inside an unrolled graph of the same solve
     D = g.D
     L.check(L.lib().ocg_probe_set(h.handle, L.OCG_PROBE_SWEEP, D))
@@ -274,7 +279,6 @@ def _large(dev, stream, flush, args, peak):
     L.check(L.lib().ocg_probe_set(h.handle, L.OCG_PROBE_OFF, 0))
     sweep_us = tot.value * 1e3 / max(nl.value, 1)
     achieved = SWEEP_BYTES_PER_CELL * ce.value / (sweep_us / 1e6) / 1e9
-    tun = h.tuning()
     form = S.SWEEP_FORM_NAMES.get(tun[D][0], "?")
     # adjoint: transpose solve of dL/dp = p - p_t and the face gradient
     ptgt = torch.from_numpy(np.random.default_rng(8).standard_normal(g.n_leaves)).to(dev)
@@ -296,9 +300,7 @@ def _large(dev, stream, flush, args, peak):
             "precision": "mixed (FP32 V-cycle, FP64 PCG)", "value": round(g.n_leaves / (ms / 1e3) / 1e6, 3),
             "unit": UNIT, "ms_per_step": round(ms, 3), "steps": steps, "iterations": sorted(its),
             "true_rel_res": st.true_rel_res, "build_s": round(t_build, 2), "setup_s": round(t_setup, 2),
-            "sweep_forms": {str(m): {"form": S.SWEEP_FORM_NAMES.get(v[0], "shared-memory tail"),
-                                     "us_octet": round(v[1], 2), "us_cell": round(v[2], 2), "us_quad": round(v[3], 2)}
-                            for m, v in tun.items() if m >= 0},
+            "sweep_forms": forms,
             "roofline": {"bound": "hbm", "kernel": "red-black colour sweep (%s form) on level %d" % (form, D),
                          "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "bytes_per_cell": SWEEP_BYTES_PER_CELL,
@@ -441,8 +443,9 @@ def run_ours(args):
     total_ms = sum(times)
     from paper_2604_18886_b300 import solver as S
     tuning = {str(m): {"form": S.SWEEP_FORM_NAMES[f] if f >= 0 else "shared-memory tail",
-                       "us_octet": round(a, 2), "us_cell": round(bq, 2), "us_quad": round(qq, 2)}
-              for m, (f, a, bq, qq) in hier.tuning().items()}
+                       "us_octet": round(a, 2), "us_cell": round(bq, 2), "us_quad": round(qq, 2),
+                       "us_tile": round(tt, 2)}
+              for m, (f, a, bq, qq, tt) in hier.tuning().items()}
     total_ms = max_over_ranks(total_ms, dev)
     value = replica_throughput(tree.n_leaves, args.steps, world, total_ms)
     if args.only_timed:
@@ -643,6 +646,8 @@ def main():
     ap.add_argument("--no-large", action="store_true", help="skip the large sine-band workload")
     ap.add_argument("--only-large", action="store_true",
                     help="run only the timed solves of the large sine-band workload (profiling aid)")
+    ap.add_argument("--sweep", default="auto", choices=["auto", "octet", "cell", "quad", "tile"],
+                    help="sweep form of the large workload's hierarchy (auto: timed at set-up; profiling aid)")
     ap.add_argument("--large-n0", type=int, default=128,
                     help="root grid of the sine-band workload (128: effective 1024^3; smaller for profiling)")
     ap.add_argument("--only-timed", action="store_true",

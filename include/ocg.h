@@ -147,7 +147,8 @@ typedef struct {
     int32_t coef_dtype;    /* OCG_F64 or OCG_F32 storage of the matrix-free coefficients */
     int32_t bf16_coarse;   /* 1: the cycle reads BF16 copies of levels below the finest */
     int32_t sweep_form;    /* OCG_SWEEP_AUTO (time every form per level at set-up and keep
-                              the fastest), OCG_SWEEP_OCTET, OCG_SWEEP_CELL or OCG_SWEEP_QUAD */
+                              the fastest), OCG_SWEEP_OCTET, OCG_SWEEP_CELL, OCG_SWEEP_QUAD or
+                              OCG_SWEEP_TILE */
     int32_t reserved;
 } ocg_mg_params;
 
@@ -155,6 +156,7 @@ typedef struct {
 #define OCG_SWEEP_OCTET 0      /* one thread per octet (8 cells in registers) */
 #define OCG_SWEEP_CELL 1       /* one thread per cell (octet in 8 lanes) */
 #define OCG_SWEEP_QUAD 2       /* two threads per octet (one z-layer of 4 cells each) */
+#define OCG_SWEEP_TILE 3       /* one thread per octet, the block's octets shared in shared memory */
 
 /* Fill leaf coefficients from face beta (canonical face order, float32, device) and the
  * wall codes (Sec. 2.1; T sub-faces per Sec. 3.1), then coarsen every level with Alg. 3
@@ -168,7 +170,7 @@ void ocg_hier_destroy(ocg_hier* h);
  * colour sweep in each form (microseconds, captured in a CUDA graph; -1 if not timed).
  * Levels run inside the shared-memory coarse kernel report form -1. */
 int ocg_hier_tuning(const ocg_hier* h, int32_t m, int32_t* form, double* us_octet, double* us_cell,
-                    double* us_quad);
+                    double* us_quad, double* us_tile);
 
 /* Stored coefficients (c, c_x-, c_y-, c_z-) of level m, cells in the order of
  * ocg_octree_export_level, as float64 host arrays.  Synchronises. */

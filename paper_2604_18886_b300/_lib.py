@@ -27,7 +27,7 @@ class OctreeDesc(C.Structure):
                 ("sines", (C.c_double * 5) * 8)]
 
 
-OCG_SWEEP_AUTO, OCG_SWEEP_OCTET, OCG_SWEEP_CELL, OCG_SWEEP_QUAD = -1, 0, 1, 2
+OCG_SWEEP_AUTO, OCG_SWEEP_OCTET, OCG_SWEEP_CELL, OCG_SWEEP_QUAD, OCG_SWEEP_TILE = -1, 0, 1, 2, 3
 
 
 class MGParams(C.Structure):
@@ -76,7 +76,7 @@ _SIGS = [
     ("ocg_hier_destroy", None, [C.c_void_p]),
     ("ocg_hier_export_coefs", C.c_int, [C.c_void_p, C.c_int32] + [C.c_void_p] * 4),
     ("ocg_hier_tuning", C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_double),
-                                  C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+                                  C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     ("ocg_apply_A", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
     ("ocg_face_grad", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("ocg_vcycle", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),

@@ -233,7 +233,7 @@ struct ocg_hier {
     Probe probe;
     int red_blocks = 296;         // grid of the grid-stride reductions (2 per SM)
     int sweep_form[MAXLEV * 2];   // per level (index m - mc): OCG_SWEEP_OCTET / _CELL / _QUAD
-    double tune_us[MAXLEV * 2][3];
+    double tune_us[MAXLEV * 2][4];
     // coarse tail: uniform levels run in one shared-memory CTA, per cycle value type
     int tail_top[2] = {TAIL_NONE, TAIL_NONE};   // [float, double]
     size_t tail_smem[2] = {0, 0};
@@ -411,6 +411,9 @@ struct Cycle {
                     k_csweep<TV, TC, TW><<<nblk(A.ncell), BLK, 0, c.st>>>(A, h->t->tables(), C, U, B, colour, prolong);
                 else if (form == OCG_SWEEP_QUAD)
                     k_qsweep<TV, TC, TW><<<nblk(A.ncell / 4), BLK, 0, c.st>>>(A, h->t->tables(), C, U, B, colour, prolong);
+                else if (form == OCG_SWEEP_TILE)
+                    k_tsweep<TV, TC, TW><<<nblk(A.ncell / 8, TBLK), TBLK, 0, c.st>>>(A, h->t->tables(), C, U, B, colour,
+                                                                                  prolong);
                 else
                     k_osweep<TV, TC, TW>
                         <<<nblk(A.ncell / 8, OBLK), OBLK, 0, c.st>>>(A, h->t->tables(), C, U, B, colour, prolong, 0);
@@ -512,8 +515,8 @@ void autotune_sweeps(ocg_hier* h) {
     const int tail_top = h->tail_top[std::is_same<TV, double>::value ? 1 : 0];
     for (int m = H.D; m > H.mc; --m) {
         if (m <= tail_top && tail_top != TAIL_NONE) break;
-        double us[3] = {0.0, 0.0, 0.0};
-        for (int form = 0; form < 3; ++form) {
+        double us[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int form = 0; form < 4; ++form) {
             Ctx c{cs, nullptr, 0};
             Cycle<TV> cy{h, (TV*)h->U, (TV*)h->B, c};
             cudaGraph_t g = nullptr;
@@ -534,7 +537,7 @@ void autotune_sweeps(ocg_hier* h) {
             cudaGraphDestroy(g);
         }
         int best = OCG_SWEEP_OCTET;
-        for (int form = 0; form < 3; ++form) {
+        for (int form = 0; form < 4; ++form) {
             h->tune_us[m - H.mc][form] = us[form];
             if (us[form] < us[best]) best = form;
         }
@@ -1103,7 +1106,7 @@ int ocg_setup_hierarchy(const ocg_octree* t, const float* beta, const int32_t bc
             !(prm->alpha > 0) || !std::isfinite(prm->beta_restrict))
             throw Status(OCG_EINVAL, "invalid multigrid parameters");
         if (prm->coef_dtype != OCG_F64 && prm->coef_dtype != OCG_F32) throw Status(OCG_EINVAL, "coef_dtype");
-        if (prm->sweep_form < OCG_SWEEP_AUTO || prm->sweep_form > OCG_SWEEP_QUAD)
+        if (prm->sweep_form < OCG_SWEEP_AUTO || prm->sweep_form > OCG_SWEEP_TILE)
             throw Status(OCG_EINVAL, "sweep_form");
         if (t->H.D - t->H.mc + 1 > 2 * MAXLEV) throw Status(OCG_EINVAL, "too many levels");
         if (prm->bf16_coarse && prm->coef_dtype != OCG_F32) throw Status(OCG_EINVAL, "bf16_coarse needs F32");
@@ -1189,7 +1192,7 @@ int ocg_setup_hierarchy(const ocg_octree* t, const float* beta, const int32_t bc
         const int nlev = H.D - H.mc + 1;
         for (int q = 0; q < nlev; ++q) {
             h->sweep_form[q] = prm->sweep_form == OCG_SWEEP_AUTO ? OCG_SWEEP_OCTET : prm->sweep_form;
-            h->tune_us[q][0] = h->tune_us[q][1] = h->tune_us[q][2] = -1.0;
+            h->tune_us[q][0] = h->tune_us[q][1] = h->tune_us[q][2] = h->tune_us[q][3] = -1.0;
         }
         if (prm->sweep_form == OCG_SWEEP_AUTO) {
             if (prm->coef_dtype == OCG_F64) autotune_sweeps<double>(h.get());
@@ -1230,9 +1233,9 @@ int ocg_hier_export_coefs(const ocg_hier* h, int32_t m, double* c, double* cx, d
 }
 
 int ocg_hier_tuning(const ocg_hier* h, int32_t m, int32_t* form, double* us_octet, double* us_cell,
-                    double* us_quad) {
+                    double* us_quad, double* us_tile) {
     return guard([&] {
-        if (!h || !form || !us_octet || !us_cell || !us_quad) throw Status(OCG_EINVAL, "null argument");
+        if (!h || !form || !us_octet || !us_cell || !us_quad || !us_tile) throw Status(OCG_EINVAL, "null argument");
         const HostTree& H = h->t->H;
         if (m < H.mc || m > H.D) throw Status(OCG_EINVAL, "level out of range");
         const int W = h->c64[0] ? 1 : 0;
@@ -1241,6 +1244,7 @@ int ocg_hier_tuning(const ocg_hier* h, int32_t m, int32_t* form, double* us_octe
         *us_octet = h->tune_us[m - H.mc][0];
         *us_cell = h->tune_us[m - H.mc][1];
         *us_quad = h->tune_us[m - H.mc][2];
+        *us_tile = h->tune_us[m - H.mc][3];
     });
 }
 

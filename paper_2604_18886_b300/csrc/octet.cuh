@@ -141,6 +141,19 @@ __device__ __forceinline__ void octet_neighbours(const Tables& T, int ni, int o,
     }
 }
 
+// neighbouring octet of local octet o in direction dir (arithmetic on uniform levels)
+__device__ __forceinline__ int octet_neighbour(const Tables& T, int ni, int o, int og, int dir) {
+    if (ni > 0) {
+        int c[3];
+        octet_coords(o, ni, c[0], c[1], c[2]);
+        const int a = dir >> 1;
+        const int stride = a == 0 ? 1 : (a == 1 ? ni : ni * ni);
+        if (dir & 1) return c[a] < ni - 1 ? o + stride : -1;
+        return c[a] > 0 ? o - stride : -1;
+    }
+    return __ldg(T.nbr + dir * T.noct + og);
+}
+
 template <class T>
 __device__ __forceinline__ T divide(T a, T b) { return a / b; }
 template <>
@@ -272,11 +285,134 @@ __device__ __forceinline__ void osweep_octet(const LevelArgs& A, const Tables& T
 }
 
 template <class TV, class TC, class TW>
-__global__ void __launch_bounds__(OBLK) k_osweep(LevelArgs A, Tables T, Coefs<TC, TW> C, TV* __restrict__ U,
+__global__ void __launch_bounds__(OBLK, sizeof(TV) == 4 ? 16 : 8) k_osweep(LevelArgs A, Tables T, Coefs<TC, TW> C, TV* __restrict__ U,
                                                  TV* __restrict__ B, int colour, int prolong, int fixb) {
     const int o = blockIdx.x * OBLK + threadIdx.x;
     if (o >= A.ncell / 8) return;
     osweep_octet<TV, TC, TW>(A, T, C, U, B, o, colour, prolong, fixb);
+}
+
+// ------------------------------------------------------------ shared-block sweep
+// The octet form with the block's u and face coefficients shared: each thread loads its
+// octet (as in k_osweep) and also places u, c_x-, c_y-, c_z- in shared memory, slot-major
+// (index s * TBLK + local octet, conflict-free across a warp); reads of a neighbouring
+// octet that lies in the same block (most of them on Morton-ordered levels) then come
+// from shared memory instead of a scattered global load.
+constexpr int TBLK = 128;
+
+template <class TV>
+struct TileSh {
+    TV u[8 * TBLK], cm[3][8 * TBLK];
+};
+
+template <class TV, class TC, class TW>
+__global__ void __launch_bounds__(TBLK) k_tsweep(LevelArgs A, Tables T, Coefs<TC, TW> C, TV* __restrict__ U,
+                                                 TV* __restrict__ B, int colour, int prolong) {
+    __shared__ TileSh<TV> sh;
+    const int noct = A.ncell >> 3;
+    const int o0 = blockIdx.x * TBLK, lo = threadIdx.x;
+    const int o = o0 + lo;
+    const bool valid = o < noct;
+    const int c8 = A.off + 8 * (valid ? o : noct - 1), og = c8 >> 3;
+    // the neighbour indices are loaded with the octet, before the barrier
+    int nb[6];
+    octet_neighbours(T, A.ni, valid ? o : noct - 1, og, nb);
+    OctState<TV> S;
+    load_octet<TV, TC, TW>(U, C, c8, S);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        sh.u[q * TBLK + lo] = S.u[q];
+        sh.cm[0][q * TBLK + lo] = S.cm[0][q];
+        sh.cm[1][q * TBLK + lo] = S.cm[1][q];
+        sh.cm[2][q * TBLK + lo] = S.cm[2][q];
+    }
+    __syncthreads();
+    if (!valid) return;
+    octet_mean(S);
+    TV b[8], Au[8];
+    ld8(B + c8, b);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) Au[q] = S.d[q] * S.u[q];
+    const int off = A.off;
+    const int nend = min(TBLK, noct - o0);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int bit = 1 << a;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int s = clear_slot(a, q), t = s | bit;
+            const TV c = S.cm[a][t];
+            Au[s] += c * S.u[t];
+            Au[t] += c * S.u[s];
+        }
+        const int v = nb[2 * a];
+        if (v >= 0) {
+            const int lv = v - o0;
+            TV nu[4];
+            if (lv >= 0 && lv < nend) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) nu[q] = sh.u[(clear_slot(a, q) | bit) * TBLK + lv];
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) nu[q] = U[off + 8 * v + (clear_slot(a, q) | bit)];
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) Au[clear_slot(a, q)] += S.cm[a][clear_slot(a, q)] * nu[q];
+        } else if (v <= -2) {
+            const TV uK = U[-2 - v];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int s = clear_slot(a, q);
+                Au[s] += S.cm[a][s] * (S.u[s] + (uK - S.ubar) * TV(0.5));
+            }
+        }
+        const int w = nb[2 * a + 1];
+        if (w >= 0) {
+            const int lw = w - o0;
+            TV nu[4], nc[4];
+            if (lw >= 0 && lw < nend) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    nu[q] = sh.u[clear_slot(a, q) * TBLK + lw];
+                    nc[q] = sh.cm[a][clear_slot(a, q) * TBLK + lw];
+                }
+            } else {
+                const TC* cc = a == 0 ? C.cx : (a == 1 ? C.cy : C.cz);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    nu[q] = U[off + 8 * w + clear_slot(a, q)];
+                    nc[q] = TV(tov(__ldg(cc + off + 8 * w + clear_slot(a, q))));
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) Au[clear_slot(a, q) | bit] += nc[q] * nu[q];
+        } else if (w <= -2) {
+            const TV uK = U[-2 - w];
+            const int t = __ldg(T.trec + og);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int s = clear_slot(a, q) | bit;
+                const TV cf = TV(tov(__ldg(C.tw + ((2 * a + 1) * 4 + q) * T.nt + t)));
+                Au[s] += cf * (S.u[s] + (uK - S.ubar) * TV(0.5));
+            }
+        }
+    }
+    TV un[8];
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+        un[s] = S.u[s];
+        if (((__popc(s) & 1) == colour) && S.d[s] != TV(0)) {
+            un[s] = S.u[s] + divide(b[s] - Au[s], S.d[s]);
+            U[c8 + s] = un[s];
+        }
+    }
+    if (prolong) {
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+            const int co = __ldg(T.child_oct + c8 + s);
+            if (co >= 0) octet_prolong<TV, TC>(C.d, U, co, un[s]);
+        }
+    }
 }
 
 // ------------------------------------------------------------ thread-per-cell sweep
@@ -408,19 +544,6 @@ __device__ __forceinline__ void ldc4(const __nv_bfloat16* __restrict__ p, TV (&r
     const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&raw);
     const float2 f0 = __bfloat1622float2(h[0]), f1 = __bfloat1622float2(h[1]);
     r[0] = TV(f0.x); r[1] = TV(f0.y); r[2] = TV(f1.x); r[3] = TV(f1.y);
-}
-
-// neighbouring octet of local octet o in direction dir (arithmetic on uniform levels)
-__device__ __forceinline__ int octet_neighbour(const Tables& T, int ni, int o, int og, int dir) {
-    if (ni > 0) {
-        int c[3];
-        octet_coords(o, ni, c[0], c[1], c[2]);
-        const int a = dir >> 1;
-        const int stride = a == 0 ? 1 : (a == 1 ? ni : ni * ni);
-        if (dir & 1) return c[a] < ni - 1 ? o + stride : -1;
-        return c[a] > 0 ? o - stride : -1;
-    }
-    return __ldg(T.nbr + dir * T.noct + og);
 }
 
 template <class TV, class TC, class TW>

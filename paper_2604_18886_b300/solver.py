@@ -110,8 +110,9 @@ class Octree:
 
 
 SWEEP_FORMS = {"auto": L.OCG_SWEEP_AUTO, "octet": L.OCG_SWEEP_OCTET, "cell": L.OCG_SWEEP_CELL,
-               "quad": L.OCG_SWEEP_QUAD}
-SWEEP_FORM_NAMES = {L.OCG_SWEEP_OCTET: "octet", L.OCG_SWEEP_CELL: "cell", L.OCG_SWEEP_QUAD: "quad"}
+               "quad": L.OCG_SWEEP_QUAD, "tile": L.OCG_SWEEP_TILE}
+SWEEP_FORM_NAMES = {L.OCG_SWEEP_OCTET: "octet", L.OCG_SWEEP_CELL: "cell", L.OCG_SWEEP_QUAD: "quad",
+                    L.OCG_SWEEP_TILE: "tile"}
 
 
 def mg_params(mu=1, nu_pre=2, nu_post=2, nu_coarsest=10, beta=2.0, alpha=2.0, coef="f32",
@@ -164,12 +165,13 @@ class Hierarchy:
         return out
 
     def tuning(self):
-        """{level: (form, us_octet, us_cell, us_quad)} as chosen / measured at set-up."""
+        """{level: (form, us_octet, us_cell, us_quad, us_tile)} as chosen / measured at set-up."""
         out = {}
         for m in range(self.tree.mc, self.tree.D + 1):
-            f, a, b, q = C.c_int32(), C.c_double(), C.c_double(), C.c_double()
-            L.check(L.lib().ocg_hier_tuning(self._h, m, C.byref(f), C.byref(a), C.byref(b), C.byref(q)))
-            out[m] = (f.value, a.value, b.value, q.value)
+            f = C.c_int32()
+            us = [C.c_double() for _ in range(4)]
+            L.check(L.lib().ocg_hier_tuning(self._h, m, C.byref(f), *[C.byref(v) for v in us]))
+            out[m] = (f.value,) + tuple(v.value for v in us)
         return out
 
     @staticmethod

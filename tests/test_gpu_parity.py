@@ -279,7 +279,7 @@ def test_wcycle_solve_matches_oracle():
     assert rel(x.cpu().numpy(), xo - xo.mean()) <= 1e-9      # all-Neumann: zero-mean output
 
 
-@pytest.mark.parametrize("sweep", ["octet", "cell", "quad"])
+@pytest.mark.parametrize("sweep", ["octet", "cell", "quad", "tile"])
 @pytest.mark.parametrize("name", ["c2_16", "c3_16_d2", "band_12_d2", "c4_t1", "c5_8_d2"])
 def test_every_sweep_form_matches_oracle(name, sweep):
     # the autotuner may pick any form per level; each must reproduce Alg. 4
