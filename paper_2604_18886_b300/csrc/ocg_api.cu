@@ -605,7 +605,10 @@ void apply_outer(ocg_hier* h, Coefs<TC, TW> C, TO* P, TO* Y, int op, Ctx& c) {
     const int nb = std::min(ML.boff[ML.n], 16 * sm_count());
     const Red R = make_red(h, nb, op);
     launch(c, OCG_PROBE_APPLY, 0, H.ntree, [&] {
-        k_oapply<TO, TC, TW><<<nb, OBLK, 0, c.st>>>(ML, t->tables(), C, P, Y, R);
+        if constexpr (std::is_same<TO, double>::value && std::is_same<TC, float>::value)
+            k_oapply_df<TC, TW><<<nb, OBLK, 0, c.st>>>(ML, t->tables(), C, P, Y, R);
+        else
+            k_oapply<TO, TC, TW><<<nb, OBLK, 0, c.st>>>(ML, t->tables(), C, P, Y, R);
     });
     ck_launch("apply");
 }

@@ -802,6 +802,189 @@ __global__ void __launch_bounds__(OBLK) k_oapply(OMultiLevel ML, Tables T, Coefs
     if (R.op != OP_NONE) red_finish(R, blockIdx.x, dot, 0.0, sh);
 }
 
+// ------------------------------------------------------------ double-float outer apply
+// The mixed-precision outer operator (FP64 vectors, FP32 coefficients) without the FP64
+// pipe, which runs at 1/64 of the FP32 rate on this GPU: every binary64 value is split
+// exactly into a pair of binary32 (hi, lo) with integer operations (48 significant bits
+// kept), the stencil is evaluated in pair arithmetic with error-free transformations
+// (TwoSum, TwoProd by FMA; T. J. Dekker, "A floating-point technique for extending the
+// available precision", Numer. Math. 18, 1971), and only the final hi + lo of each output
+// is one binary64 addition.  The flux form
+//   (A u)_s = (d_s - sum_f w_f) u_s + sum_f w_f (u_s - u_f)   (+ T ghosts (w_f/2)(ubar - u_K))
+// computes every face difference before scaling it, so the rounding error is relative to
+// the fluxes, not to d_s u_s; the remainder d_s - sum_f w_f (non-zero at walls and by the
+// FP32 rounding of the stored coefficients) is summed exactly.
+struct DF {
+    float hi, lo;
+};
+__device__ __forceinline__ DF df_two_sum(float a, float b) {
+    const float s = a + b, bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ DF df_norm(float hi, float lo) {
+    const float s = hi + lo;
+    return {s, lo - (s - hi)};
+}
+__device__ __forceinline__ DF df_add(DF x, DF y) {
+    const DF s = df_two_sum(x.hi, y.hi);
+    return df_norm(s.hi, s.lo + (x.lo + y.lo));
+}
+__device__ __forceinline__ DF df_sub(DF x, DF y) { return df_add(x, DF{-y.hi, -y.lo}); }
+__device__ __forceinline__ DF df_mul_f(DF x, float c) {
+    const float p = x.hi * c;
+    return df_norm(p, fmaf(x.hi, c, -p) + x.lo * c);
+}
+__device__ __forceinline__ DF df_mul(DF x, DF y) {
+    const float p = x.hi * y.hi;
+    return df_norm(p, fmaf(x.hi, y.hi, -p) + (x.hi * y.lo + x.lo * y.hi));
+}
+__device__ __forceinline__ DF df_add_f(DF x, float c) {   // exact accumulation of coefficients
+    const DF s = df_two_sum(x.hi, c);
+    return df_norm(s.hi, s.lo + x.lo);
+}
+// binary64 -> (hi, lo): hi = the leading 24 bits (truncated), lo = the next 24 (rounded);
+// |v| < 2^-126 is flushed to 0, infinities and NaN are kept in hi.
+__device__ __forceinline__ DF df_split(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+    const int e = (int)((b >> 52) & 0x7FF) - 1023;
+    if (e < -126) return {__uint_as_float(sign), 0.0f};
+    const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+    if (e > 127) return {__uint_as_float(sign | 0x7F800000u | (m ? 0x400000u : 0u)), 0.0f};
+    const float hi = __uint_as_float(sign | ((unsigned)(e + 127) << 23) | (unsigned)(m >> 29));
+    const unsigned mlo = (unsigned)(m & 0x1FFFFFFFull);
+    if (mlo == 0u || e < -74) return {hi, 0.0f};
+    const float lo = __uint2float_rn(mlo) * __uint_as_float((unsigned)(e - 52 + 127) << 23);
+    return {hi, sign ? -lo : lo};
+}
+// binary32 -> binary64 by bits (exact; subnormal floats are flushed to 0)
+__device__ __forceinline__ double f2d_bits(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned ex = (u >> 23) & 0xFFu;
+    const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+    if (ex == 0u) return __longlong_as_double((long long)sign);
+    const unsigned long long e64 = ex == 0xFFu ? 0x7FFull : (unsigned long long)(ex - 127u + 1023u);
+    return __longlong_as_double((long long)(sign | (e64 << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29)));
+}
+__device__ __forceinline__ double df_to_double(DF x) { return f2d_bits(x.hi) + f2d_bits(x.lo); }
+
+template <class TC, class TW>
+__global__ void __launch_bounds__(OBLK) k_oapply_df(OMultiLevel ML, Tables T, Coefs<TC, TW> C,
+                                                    const double* __restrict__ P, double* __restrict__ Y, Red R) {
+    __shared__ double sh[32];
+    DF dot{0.0f, 0.0f};
+    const int nvb = ML.boff[ML.n];
+    int l = 0;
+    for (int vb = blockIdx.x; vb < nvb; vb += gridDim.x) {
+        while (l + 1 < ML.n && vb >= ML.boff[l + 1]) ++l;
+        const int o = (vb - ML.boff[l]) * OBLK + threadIdx.x;
+        if (o >= ML.noct[l]) continue;
+        const int off = ML.off[l], ni = ML.ni[l];
+        const int c8 = off + 8 * o, og = c8 >> 3;
+        int leafbits = 0;
+#pragma unroll
+        for (int s = 0; s < 8; ++s) leafbits |= (__ldg(T.child_oct + c8 + s) < 0 ? 1 : 0) << s;
+        if (!leafbits) {
+            // no leaf in the octet: the composite operator has no row here
+            reinterpret_cast<double4*>(Y + c8)[0] = make_double4(0.0, 0.0, 0.0, 0.0);
+            reinterpret_cast<double4*>(Y + c8)[1] = make_double4(0.0, 0.0, 0.0, 0.0);
+            continue;
+        }
+        DF u[8];
+        float d[8], cm[3][8];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const double2 v = reinterpret_cast<const double2*>(P + c8)[q];
+            u[2 * q] = df_split(v.x);
+            u[2 * q + 1] = df_split(v.y);
+        }
+        ldc8(C.d + c8, d);
+        ldc8(C.cx + c8, cm[0]);
+        ldc8(C.cy + c8, cm[1]);
+        ldc8(C.cz + c8, cm[2]);
+        // mean of the active cells (the T ghost's ubar)
+        DF us{0.0f, 0.0f};
+        int n = 0;
+#pragma unroll
+        for (int s = 0; s < 8; ++s)
+            if (d[s] != 0.0f) { us = df_add(us, u[s]); ++n; }
+        const float ic = inv_count<float>(n);
+        const DF ubar{us.hi * ic, us.lo * ic};   // exact for n = 1, 2, 4, 8
+        DF acc[8], dr[8];
+#pragma unroll
+        for (int s = 0; s < 8; ++s) { acc[s] = DF{0.0f, 0.0f}; dr[s] = DF{d[s], 0.0f}; }
+        int nb[6];
+        octet_neighbours(T, ni, o, og, nb);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const int bit = 1 << a;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int s = clear_slot(a, q), t = s | bit;
+                const float c = cm[a][t];
+                const DF fl = df_mul_f(df_sub(u[s], u[t]), -c);
+                acc[s] = df_add(acc[s], fl);
+                acc[t] = df_sub(acc[t], fl);
+                dr[s] = df_add_f(dr[s], c);
+                dr[t] = df_add_f(dr[t], c);
+            }
+            const int v = nb[2 * a];
+            if (v >= 0) {
+                const double* pn = P + off + 8 * v;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int s = clear_slot(a, q);
+                    const DF un = df_split(pn[s | bit]);
+                    acc[s] = df_add(acc[s], df_mul_f(df_sub(u[s], un), -cm[a][s]));
+                    dr[s] = df_add_f(dr[s], cm[a][s]);
+                }
+            } else if (v <= -2) {
+                const DF gk = df_mul_f(df_sub(df_split(P[-2 - v]), ubar), 0.5f);   // (u_K - ubar)/2
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int s = clear_slot(a, q);
+                    acc[s] = df_add(acc[s], df_mul_f(gk, cm[a][s]));
+                    dr[s] = df_add_f(dr[s], cm[a][s]);
+                }
+            }
+            const int w = nb[2 * a + 1];
+            if (w >= 0) {
+                const double* pn = P + off + 8 * w;
+                const TC* cc = (a == 0 ? C.cx : (a == 1 ? C.cy : C.cz)) + off + 8 * w;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int s = clear_slot(a, q) | bit;
+                    const float c = (float)tov(__ldg(cc + clear_slot(a, q)));
+                    const DF un = df_split(pn[clear_slot(a, q)]);
+                    acc[s] = df_add(acc[s], df_mul_f(df_sub(u[s], un), -c));
+                    dr[s] = df_add_f(dr[s], c);
+                }
+            } else if (w <= -2) {
+                const DF gk = df_mul_f(df_sub(df_split(P[-2 - w]), ubar), 0.5f);
+                const int t = __ldg(T.trec + og);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int s = clear_slot(a, q) | bit;
+                    const float c = (float)tov(__ldg(C.tw + ((2 * a + 1) * 4 + q) * T.nt + t));
+                    acc[s] = df_add(acc[s], df_mul_f(gk, c));
+                    dr[s] = df_add_f(dr[s], c);
+                }
+            }
+        }
+        double y[8];
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+            const bool leaf = (leafbits >> s) & 1;
+            const DF au = df_add(acc[s], df_mul(dr[s], u[s]));
+            y[s] = leaf ? df_to_double(au) : 0.0;
+            if (leaf) dot = df_add(dot, df_mul(u[s], au));
+        }
+        reinterpret_cast<double4*>(Y + c8)[0] = make_double4(y[0], y[1], y[2], y[3]);
+        reinterpret_cast<double4*>(Y + c8)[1] = make_double4(y[4], y[5], y[6], y[7]);
+    }
+    if (R.op != OP_NONE) red_finish(R, blockIdx.x, df_to_double(dot), 0.0, sh);
+}
+
 // ------------------------------------------------------------ transposed operator
 // A^T x = A x + (A^T - A) x, the correction summed over the T sub-faces f (fine leaf i,
 // coarser leaf K, P = parent of i, c_f = w_f / 2):

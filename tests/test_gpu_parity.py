@@ -103,6 +103,24 @@ def test_apply_A_fp64(name):
     assert rel(y, H.A @ x) <= 1e-12
 
 
+@pytest.mark.parametrize("name", ["c2_16", "c2_16_neumann", "c1_16"])
+def test_mixed_outer_apply_is_fp64_accurate(name):
+    # FP64 vectors on an FP32-coefficient hierarchy (the mixed solve's outer operator, run
+    # in pair-of-FP32 arithmetic): with beta = 1 every stored leaf coefficient is a
+    # multiple of h and exact in FP32, so the result must match the FP64 oracle to FP64
+    # rounding (relative to the vector's max norm), smooth and rough inputs alike
+    t, H, g, gh, f, beta = build(CASES[name](), "f32")
+    n = t.n_leaves
+    lv = t.leaves
+    h = 1.0 / (t.n0 * 2.0 ** lv["depth"])
+    xs = np.sin(3.1 * (lv["i"] + 0.5) * h) * np.cos(2.3 * (lv["j"] + 0.5) * h) + 0.25
+    for x in (P.random_vector(n, 31), xs, 1e-7 * xs + 1e3):
+        y = gh.apply_A(cuda(x)).cpu().numpy()
+        ref = H.A @ x
+        assert np.abs(y - ref).max() <= 1e-12 * max(np.abs(ref).max(), 1e-300) + 1e-14 * np.abs(x).max() * np.abs(H.A).max(), \
+            np.abs(y - ref).max()
+
+
 @pytest.mark.parametrize("name", list(CASES))
 def test_apply_A_fp32(name):
     t, H, g, gh, f, beta = build(CASES[name](), "f32")
