@@ -268,6 +268,18 @@ def _large(dev, stream, flush, args, peak):
                 "value": round(g.n_leaves / (ms / 1e3) / 1e6, 3), "unit": UNIT, "ms_per_step": round(ms, 3),
                 "steps": steps, "iterations": sorted(its), "sweep_forms": forms,
                 "note": "--only-large (profiling aid)"}
+    # plain FP32 beside it (FP32 Krylov vectors, FP64 dot products)
+    t32 = []
+    for s_ in range(steps):
+        flush.fill_(float(s_))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, st32 = h.solve(b, x, tol=1e-6, precision="fp32", stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        t32.append(e0.elapsed_time(e1))
+    ms32 = statistics.mean(t32)
     # finest-level sweep inside an unrolled graph of the same solve
     D = g.D
     L.check(L.lib().ocg_probe_set(h.handle, L.OCG_PROBE_SWEEP, D))
@@ -300,6 +312,9 @@ def _large(dev, stream, flush, args, peak):
             "precision": "mixed (FP32 V-cycle, FP64 PCG)", "value": round(g.n_leaves / (ms / 1e3) / 1e6, 3),
             "unit": UNIT, "ms_per_step": round(ms, 3), "steps": steps, "iterations": sorted(its),
             "true_rel_res": st.true_rel_res, "build_s": round(t_build, 2), "setup_s": round(t_setup, 2),
+            "plain_fp32": {"value": round(g.n_leaves / (ms32 / 1e3) / 1e6, 3), "unit": UNIT,
+                           "ms_per_step": round(ms32, 3), "iterations": st32.iterations,
+                           "true_rel_res": st32.true_rel_res},
             "sweep_forms": forms,
             "roofline": {"bound": "hbm", "kernel": "red-black colour sweep (%s form) on level %d" % (form, D),
                          "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
