@@ -15,6 +15,15 @@ namespace ocg {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int BLK = 256;
+
+// Programmatic dependent launch (sm_90 and later): every kernel of this library first waits
+// until the grid it depends on has completed and its memory is visible, then lets the next
+// grid be scheduled.  Launched with the programmatic-serialization attribute (launch_k),
+// the next kernel's blocks are placed on the SMs while this one runs and the gap between
+// dependent kernels shrinks; launched without it, the wait returns at once.
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
 constexpr int MAXLEV = 16;
 
 struct Tables {
@@ -205,12 +214,14 @@ __device__ __forceinline__ void red_finish(const Red& R, int blk, double va, dou
 template <class TI, class TO>
 __global__ void k_scatter(const TI* __restrict__ in, TO* __restrict__ out, const int32_t* __restrict__ leaf_cell,
                           int n) {
+    pdl_enter();
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r < n) out[leaf_cell[r]] = TO(in[r]);
 }
 
 template <class TI, class TO>
 __global__ void k_cast(const TI* __restrict__ in, TO* __restrict__ out, int n) {
+    pdl_enter();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = TO(in[i]);
 }
@@ -218,6 +229,7 @@ __global__ void k_cast(const TI* __restrict__ in, TO* __restrict__ out, int n) {
 template <class TI, class TO>
 __global__ void k_gather(const TI* __restrict__ in, TO* __restrict__ out, const int32_t* __restrict__ leaf_cell,
                          int n) {
+    pdl_enter();
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r < n) out[r] = TO(in[leaf_cell[r]]);
 }
@@ -227,6 +239,7 @@ __global__ void k_gather(const TI* __restrict__ in, TO* __restrict__ out, const 
 template <class TO, class TB, bool SUM>
 __global__ void __launch_bounds__(BLK) k_update(TO* __restrict__ x, TO* __restrict__ r, const TO* __restrict__ p,
                                                 const TO* __restrict__ Ap, TB* __restrict__ b32, int n, Red R) {
+    pdl_enter();
     __shared__ double sh[32];
     const TO alpha = TO(R.S[S_ALPHA]);
     double rr = 0.0, rs = 0.0;
@@ -264,6 +277,7 @@ __global__ void __launch_bounds__(BLK) k_update(TO* __restrict__ x, TO* __restri
 template <class TO, class TB>
 __global__ void k_project(TO* __restrict__ r, const uint8_t* __restrict__ flags, const double* __restrict__ S,
                           TB* __restrict__ b32, int n) {
+    pdl_enter();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     TO v = r[i];
@@ -276,6 +290,7 @@ __global__ void k_project(TO* __restrict__ r, const uint8_t* __restrict__ flags,
 // (a, b) over the first n cells; with SUM also sum(a) (the null-space mean of Sec. 2.2)
 template <class TA, class TB, bool SUM>
 __global__ void __launch_bounds__(BLK) k_dot(const TA* __restrict__ a, const TB* __restrict__ b, int n, Red R) {
+    pdl_enter();
     __shared__ double sh[32];
     double v = 0.0, s = 0.0;
     const int st = gridDim.x * BLK;
@@ -304,6 +319,7 @@ __global__ void __launch_bounds__(BLK) k_dot(const TA* __restrict__ a, const TB*
 template <class TO>
 __global__ void __launch_bounds__(BLK) k_resid(const TO* __restrict__ b, const TO* __restrict__ y,
                                                const uint8_t* __restrict__ flags, int n, Red R) {
+    pdl_enter();
     __shared__ double sh[32];
     double v = 0.0, s = 0.0;
     for (int i = blockIdx.x * BLK + threadIdx.x; i < n; i += gridDim.x * BLK) {
@@ -319,6 +335,7 @@ __global__ void __launch_bounds__(BLK) k_resid(const TO* __restrict__ b, const T
 template <class TI, class TO>
 __global__ void k_gather_shift(const TI* __restrict__ in, TO* __restrict__ out, const int32_t* __restrict__ leaf_cell,
                                const double* __restrict__ S, int n) {
+    pdl_enter();
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r < n) out[r] = TO((double)in[leaf_cell[r]] - S[S_XMEAN]);
 }
@@ -330,6 +347,7 @@ __global__ void k_gather_shift(const TI* __restrict__ in, TO* __restrict__ out, 
 template <class TO, class TB>
 __global__ void k_bi_p(TO* __restrict__ p, const TO* __restrict__ r, const TO* __restrict__ v,
                        TB* __restrict__ b32, const double* __restrict__ S, int n) {
+    pdl_enter();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const TO pn = r[i] + TO(S[S_BETA]) * (p[i] - TO(S[S_OMEGA]) * v[i]);
@@ -341,6 +359,7 @@ __global__ void k_bi_p(TO* __restrict__ p, const TO* __restrict__ r, const TO* _
 template <class TO, class TB>
 __global__ void k_bi_s(TO* __restrict__ s, const TO* __restrict__ r, const TO* __restrict__ v,
                        TB* __restrict__ b32, const double* __restrict__ S, int n) {
+    pdl_enter();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const TO sn = r[i] - TO(S[S_ALPHA]) * v[i];
@@ -351,6 +370,7 @@ __global__ void k_bi_s(TO* __restrict__ s, const TO* __restrict__ r, const TO* _
 // (t, s) and (t, t)
 template <class TO>
 __global__ void __launch_bounds__(BLK) k_dot2(const TO* __restrict__ t, const TO* __restrict__ s, int n, Red R) {
+    pdl_enter();
     __shared__ double sh[32];
     double ts = 0.0, tt = 0.0;
     for (int i = blockIdx.x * BLK + threadIdx.x; i < n; i += gridDim.x * BLK) {
@@ -366,6 +386,7 @@ template <class TO>
 __global__ void __launch_bounds__(BLK) k_bi_x(TO* __restrict__ x, TO* __restrict__ r, const TO* __restrict__ s,
                                               const TO* __restrict__ t, const TO* __restrict__ ph,
                                               const TO* __restrict__ shv, const TO* __restrict__ rhat, int n, Red R) {
+    pdl_enter();
     __shared__ double sh[32];
     const TO alpha = TO(R.S[S_ALPHA]), omega = TO(R.S[S_OMEGA]);
     double rr = 0.0, rs = 0.0, rh = 0.0;
@@ -395,6 +416,7 @@ __global__ void k_face_grad(int nface, const int32_t* __restrict__ fminus, const
                             const int32_t* __restrict__ leaf_cell, const int8_t* __restrict__ level,
                             const int32_t* __restrict__ oct_parent, FaceHs H, const double* __restrict__ P,
                             const double* __restrict__ Lm, double* __restrict__ out) {
+    pdl_enter();
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= nface) return;
     const int ga = leaf_cell[fminus[f]], gb = leaf_cell[fplus[f]];
@@ -412,6 +434,7 @@ __global__ void k_face_grad(int nface, const int32_t* __restrict__ fminus, const
 // sum of x over the leaves (flags bit 0), into the second slot of R
 __global__ void __launch_bounds__(BLK) k_leafsum(const double* __restrict__ x, const uint8_t* __restrict__ flags,
                                                  int n, Red R) {
+    pdl_enter();
     __shared__ double sh[32];
     double v = 0.0;
     for (int i = blockIdx.x * BLK + threadIdx.x; i < n; i += gridDim.x * BLK)
@@ -422,6 +445,7 @@ __global__ void __launch_bounds__(BLK) k_leafsum(const double* __restrict__ x, c
 template <class TO, class TZ>
 __global__ void k_pupdate(TO* __restrict__ p, const TZ* __restrict__ z, const double* __restrict__ S, int n,
                           int first) {
+    pdl_enter();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     p[i] = first ? TO(z[i]) : TO(z[i]) + TO(S[S_BETA]) * p[i];
@@ -435,6 +459,7 @@ __global__ void k_face_scatter(const float* __restrict__ beta, const int64_t* __
                                const uint8_t* __restrict__ kind, const int8_t* __restrict__ depth,
                                const double* __restrict__ hdepth, int nface, double* __restrict__ cm,
                                double* __restrict__ tw, int* __restrict__ err) {
+    pdl_enter();
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= nface) return;
     const float b = beta[f];
@@ -456,6 +481,7 @@ struct LevelTab {
 __global__ void k_leaf_gather(const int32_t* __restrict__ leaf_cell, const int8_t* __restrict__ level,
                               Tables T, LevelTab LT, int4 bc_lo, int2 bc_hi, int nleaf, int ncell,
                               double* __restrict__ dg, double* __restrict__ cm, const double* __restrict__ tw) {
+    pdl_enter();
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= nleaf) return;
     const int bc[6] = {bc_lo.x, bc_lo.y, bc_lo.z, bc_lo.w, bc_hi.x, bc_hi.y};
@@ -530,6 +556,7 @@ __global__ void k_leaf_gather(const int32_t* __restrict__ leaf_cell, const int8_
 // children; - face coefficients from the children on the parent's - faces / alpha.
 __global__ void k_coarsen(LevelArgs A, Tables T, double alpha, double* __restrict__ dg, double* __restrict__ cm,
                           int ncell) {
+    pdl_enter();
     const int o = blockIdx.x * blockDim.x + threadIdx.x;
     if (o >= A.ncell / 8) return;
     const int c8 = A.off + 8 * o;
@@ -562,12 +589,14 @@ __global__ void k_convert(const double* __restrict__ in, TS* __restrict__ out, i
 
 template <>
 __global__ void k_convert<float>(const double* __restrict__ in, float* __restrict__ out, int64_t n) {
+    pdl_enter();
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n) out[i] = (float)in[i];
 }
 
 template <>
 __global__ void k_convert<__nv_bfloat16>(const double* __restrict__ in, __nv_bfloat16* __restrict__ out, int64_t n) {
+    pdl_enter();
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n) out[i] = __float2bfloat16_rn((float)in[i]);
 }

@@ -12,6 +12,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <functional>
 #include <memory>
@@ -82,6 +83,32 @@ int guard(F&& f) {
         g_err = e.what();
         return OCG_EINVAL;
     }
+}
+
+// Kernel launch with the programmatic-serialization attribute (see pdl_enter); OCG_PDL=0
+// in the environment launches without it.
+inline bool pdl_enabled() {
+    static int v = -1;
+    if (v < 0) {
+        const char* e = std::getenv("OCG_PDL");
+        v = (e && e[0] == '0') ? 0 : 1;
+    }
+    return v == 1;
+}
+template <typename... KArgs, typename... Args>
+inline void launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args&&... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+    if (e != cudaSuccess) throw Status(OCG_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
 }
 
 inline unsigned nblk(int64_t n, int b = BLK) { return (unsigned)((n + b - 1) / b); }
@@ -395,7 +422,7 @@ struct Cycle {
             using TW = typename CoefTypes<decltype(C)>::TW;
             const LevelArgs A = h->t->largs(m);
             launch(c, -1, m, A.ncell, [&] {
-                k_osweep<TV, TC, TW><<<nblk(A.ncell / 8, OBLK), OBLK, 0, c.st>>>(A, h->t->tables(), C, U, B, 0, 0, 1);
+                launch_k(k_osweep<TV, TC, TW>, nblk(A.ncell / 8, OBLK), OBLK, 0, c.st, A, h->t->tables(), C, U, B, 0, 0, 1);
             });
         });
         ck_launch("fixb");
@@ -408,15 +435,14 @@ struct Cycle {
             const LevelArgs A = h->t->largs(m);
             launch(c, OCG_PROBE_SWEEP, m, A.ncell, [&] {
                 if (form == OCG_SWEEP_CELL)
-                    k_csweep<TV, TC, TW><<<nblk(A.ncell), BLK, 0, c.st>>>(A, h->t->tables(), C, U, B, colour, prolong);
+                    launch_k(k_csweep<TV, TC, TW>, nblk(A.ncell), BLK, 0, c.st, A, h->t->tables(), C, U, B, colour, prolong);
                 else if (form == OCG_SWEEP_QUAD)
-                    k_qsweep<TV, TC, TW><<<nblk(A.ncell / 4), BLK, 0, c.st>>>(A, h->t->tables(), C, U, B, colour, prolong);
+                    launch_k(k_qsweep<TV, TC, TW>, nblk(A.ncell / 4), BLK, 0, c.st, A, h->t->tables(), C, U, B, colour, prolong);
                 else if (form == OCG_SWEEP_TILE)
-                    k_tsweep<TV, TC, TW><<<nblk(A.ncell / 8, TBLK), TBLK, 0, c.st>>>(A, h->t->tables(), C, U, B, colour,
+                    launch_k(k_tsweep<TV, TC, TW>, nblk(A.ncell / 8, TBLK), TBLK, 0, c.st, A, h->t->tables(), C, U, B, colour,
                                                                                   prolong);
                 else
-                    k_osweep<TV, TC, TW>
-                        <<<nblk(A.ncell / 8, OBLK), OBLK, 0, c.st>>>(A, h->t->tables(), C, U, B, colour, prolong, 0);
+                    launch_k(k_osweep<TV, TC, TW>, nblk(A.ncell / 8, OBLK), OBLK, 0, c.st, A, h->t->tables(), C, U, B, colour, prolong, 0);
             });
         });
         ck_launch("sweep");
@@ -428,7 +454,7 @@ struct Cycle {
             using TW = typename CoefTypes<decltype(C)>::TW;
             const LevelArgs A = h->t->largs(m);
             launch(c, OCG_PROBE_RESTRICT, m, A.ncell, [&] {
-                k_orestrict<TV, TC, TW><<<nblk(A.ncell / 8, OBLK), OBLK, 0, c.st>>>(A, h->t->tables(), C, U, B, scale);
+                launch_k(k_orestrict<TV, TC, TW>, nblk(A.ncell / 8, OBLK), OBLK, 0, c.st, A, h->t->tables(), C, U, B, scale);
             });
         });
         ck_launch("restrict");
@@ -438,7 +464,7 @@ struct Cycle {
             using TC = typename CoefTypes<decltype(C)>::TC;
             const LevelArgs A = h->t->largs(m);
             launch(c, OCG_PROBE_PROLONG, m, A.ncell, [&] {
-                k_oprolong<TV, TC><<<nblk(A.ncell / 8, OBLK), OBLK, 0, c.st>>>(A, h->t->tables(), C.d, U);
+                launch_k(k_oprolong<TV, TC>, nblk(A.ncell / 8, OBLK), OBLK, 0, c.st, A, h->t->tables(), C.d, U);
             });
         });
         ck_launch("prolong");
@@ -450,7 +476,7 @@ struct Cycle {
             const LevelArgs A = h->t->largs(m);
             const int nt = (int)std::min<int64_t>(256, (A.ncell / 8 + 31) / 32 * 32);
             launch(c, -1, m, A.ncell, [&] {
-                k_ocoarsest<TV, TC, TW><<<1, nt, 0, c.st>>>(A, h->t->tables(), C, U, B, h->prm.nu_coarsest,
+                launch_k(k_ocoarsest<TV, TC, TW>, 1, nt, 0, c.st, A, h->t->tables(), C, U, B, h->prm.nu_coarsest,
                                                            fas ? 1 : 0, prolong_up ? 1 : 0);
             });
         });
@@ -472,7 +498,7 @@ struct Cycle {
             const int noct = A.L[0].ni * A.L[0].ni * A.L[0].ni;
             const int nt = std::min(sizeof(TV) == 8 ? 256 : 512, (noct + 31) / 32 * 32);
             launch(c, OCG_PROBE_TAIL, m, A.ncell, [&] {
-                k_otail<TV, TC, TW><<<1, nt, sm, c.st>>>(A, h->t->tables(), C, U, B, scale);
+                launch_k(k_otail<TV, TC, TW>, 1, nt, sm, c.st, A, h->t->tables(), C, U, B, scale);
             });
         });
         ck_launch("tail");
@@ -596,7 +622,7 @@ void apply_outer(ocg_hier* h, Coefs<TC, TW> C, TO* P, TO* Y, int op, Ctx& c) {
     for (int m = H.D; m >= 1; --m) {
         const LevelArgs A = t->largs(m);
         launch(c, -1, m, A.ncell, [&] {
-            k_oavg<TO, TC><<<nblk(A.ncell / 8, OBLK), OBLK, 0, c.st>>>(A, t->tables(), C.d, P);
+            launch_k(k_oavg<TO, TC>, nblk(A.ncell / 8, OBLK), OBLK, 0, c.st, A, t->tables(), C.d, P);
         });
     }
     ck_launch("avg");
@@ -606,9 +632,9 @@ void apply_outer(ocg_hier* h, Coefs<TC, TW> C, TO* P, TO* Y, int op, Ctx& c) {
     const Red R = make_red(h, nb, op);
     launch(c, OCG_PROBE_APPLY, 0, H.ntree, [&] {
         if constexpr (std::is_same<TO, double>::value && std::is_same<TC, float>::value)
-            k_oapply_df<TC, TW><<<nb, OBLK, 0, c.st>>>(ML, t->tables(), C, P, Y, R);
+            launch_k(k_oapply_df<TC, TW>, nb, OBLK, 0, c.st, ML, t->tables(), C, P, Y, R);
         else
-            k_oapply<TO, TC, TW><<<nb, OBLK, 0, c.st>>>(ML, t->tables(), C, P, Y, R);
+            launch_k(k_oapply<TO, TC, TW>, nb, OBLK, 0, c.st, ML, t->tables(), C, P, Y, R);
     });
     ck_launch("apply");
 }
@@ -622,14 +648,14 @@ void apply_outer_T(ocg_hier* h, Coefs<TC, TW> C, TO* P, TO* Y, Ctx& c) {
     if (H.nt == 0) return;
     const Tables T = t->tables();
     launch(c, -1, 0, H.nt, [&] {
-        k_tfine<TO, TC, TW><<<nblk(H.nt, OBLK), OBLK, 0, c.st>>>(T, C, t->t_oct, P, Y, h->tseed);
+        launch_k(k_tfine<TO, TC, TW>, nblk(H.nt, OBLK), OBLK, 0, c.st, T, C, t->t_oct, P, Y, h->tseed);
     });
     launch(c, -1, 0, t->n_tcoarse, [&] {
-        k_tcoarse<TO, TC, TW><<<nblk(t->n_tcoarse), BLK, 0, c.st>>>(T, C, tree_levels(H), t->level, t->tcoarse,
+        launch_k(k_tcoarse<TO, TC, TW>, nblk(t->n_tcoarse), BLK, 0, c.st, T, C, tree_levels(H), t->level, t->tcoarse,
                                                                     t->n_tcoarse, P, Y);
     });
     launch(c, -1, 0, t->n_tdesc, [&] {
-        k_tdesc<TO><<<nblk(t->n_tdesc), BLK, 0, c.st>>>(T, t->tdesc, t->n_tdesc, (int)H.ntree, t->flags, h->tseed, Y);
+        launch_k(k_tdesc<TO>, nblk(t->n_tdesc), BLK, 0, c.st, T, t->tdesc, t->n_tdesc, (int)H.ntree, t->flags, h->tseed, Y);
     });
     ck_launch("apply_T correction");
 }
@@ -648,7 +674,7 @@ void solution_mean(ocg_hier* h, Ctx& c, const double* xt) {
     const int n = (int)h->t->H.ntree;
     const unsigned rb = std::min<unsigned>(nblk(n), (unsigned)h->red_blocks);
     launch(c, -1, 0, n, [&] {
-        k_leafsum<<<rb, BLK, 0, c.st>>>(xt, h->t->flags, n, make_red(h, rb, OP_XMEAN));
+        launch_k(k_leafsum, rb, BLK, 0, c.st, xt, h->t->flags, n, make_red(h, rb, OP_XMEAN));
     });
 }
 
@@ -677,13 +703,13 @@ struct Pcg {
         zero(h->x, n() * sizeof(TO));
         zero(h->p, n() * sizeof(TO));
         zero(h->B, H().ncell * sizeof(TV));
-        launch(c, -1, 0, n(), [&] { k_cast<double, TO><<<gb(), BLK, 0, c.st>>>(h->bt, r(), n()); });
-        launch(c, -1, 0, n(), [&] { k_dot<TO, TO, true><<<rb(), BLK, 0, c.st>>>(r(), r(), n(), make_red(h, rb(), OP_BB)); });
-        launch(c, -1, 0, n(), [&] { k_project<TO, TV><<<gb(), BLK, 0, c.st>>>(r(), h->t->flags, h->S, B(), n()); });
+        launch(c, -1, 0, n(), [&] { launch_k(k_cast<double, TO>, gb(), BLK, 0, c.st, h->bt, r(), n()); });
+        launch(c, -1, 0, n(), [&] { launch_k(k_dot<TO, TO, true>, rb(), BLK, 0, c.st, r(), r(), n(), make_red(h, rb(), OP_BB)); });
+        launch(c, -1, 0, n(), [&] { launch_k(k_project<TO, TV>, gb(), BLK, 0, c.st, r(), h->t->flags, h->S, B(), n()); });
         ck_launch("begin");
         precondition();
-        launch(c, -1, 0, n(), [&] { k_dot<TO, TV, false><<<rb(), BLK, 0, c.st>>>(r(), U(), n(), make_red(h, rb(), OP_RZ0)); });
-        launch(c, -1, 0, n(), [&] { k_pupdate<TO, TV><<<gb(), BLK, 0, c.st>>>(p(), U(), h->S, n(), 1); });
+        launch(c, -1, 0, n(), [&] { launch_k(k_dot<TO, TV, false>, rb(), BLK, 0, c.st, r(), U(), n(), make_red(h, rb(), OP_RZ0)); });
+        launch(c, -1, 0, n(), [&] { launch_k(k_pupdate<TO, TV>, gb(), BLK, 0, c.st, p(), U(), h->S, n(), 1); });
         ck_launch("begin");
         half_a();
     }
@@ -695,17 +721,17 @@ struct Pcg {
         apply_outer<TO, TC, TW>(h, Co, p(), Ap(), OP_ALPHA, c);
         launch(c, -1, 0, n(), [&] {
             const Red R = make_red(h, rb(), OP_RR, cond, set_cond);
-            if (ns) k_update<TO, TV, true><<<rb(), BLK, 0, c.st>>>(x(), r(), p(), Ap(), nullptr, n(), R);
-            else k_update<TO, TV, false><<<rb(), BLK, 0, c.st>>>(x(), r(), p(), Ap(), B(), n(), R);
+            if (ns) launch_k(k_update<TO, TV, true>, rb(), BLK, 0, c.st, x(), r(), p(), Ap(), nullptr, n(), R);
+            else launch_k(k_update<TO, TV, false>, rb(), BLK, 0, c.st, x(), r(), p(), Ap(), B(), n(), R);
         });
         if (ns)
-            launch(c, -1, 0, n(), [&] { k_project<TO, TV><<<gb(), BLK, 0, c.st>>>(r(), h->t->flags, h->S, B(), n()); });
+            launch(c, -1, 0, n(), [&] { launch_k(k_project<TO, TV>, gb(), BLK, 0, c.st, r(), h->t->flags, h->S, B(), n()); });
         ck_launch("half_a");
     }
     void half_b() {
         precondition();
-        launch(c, -1, 0, n(), [&] { k_dot<TO, TV, false><<<rb(), BLK, 0, c.st>>>(r(), U(), n(), make_red(h, rb(), OP_BETA)); });
-        launch(c, -1, 0, n(), [&] { k_pupdate<TO, TV><<<gb(), BLK, 0, c.st>>>(p(), U(), h->S, n(), 0); });
+        launch(c, -1, 0, n(), [&] { launch_k(k_dot<TO, TV, false>, rb(), BLK, 0, c.st, r(), U(), n(), make_red(h, rb(), OP_BETA)); });
+        launch(c, -1, 0, n(), [&] { launch_k(k_pupdate<TO, TV>, gb(), BLK, 0, c.st, p(), U(), h->S, n(), 0); });
         ck_launch("half_b");
     }
     void body() {
@@ -713,10 +739,10 @@ struct Pcg {
         half_a();
     }
     void finish() {
-        launch(c, -1, 0, n(), [&] { k_cast<TO, double><<<gb(), BLK, 0, c.st>>>(x(), h->xt, n()); });
+        launch(c, -1, 0, n(), [&] { launch_k(k_cast<TO, double>, gb(), BLK, 0, c.st, x(), h->xt, n()); });
         apply_outer<double, TC, TW>(h, Co, h->xt, h->yt, OP_NONE, c);
         launch(c, -1, 0, n(), [&] {
-            k_resid<double><<<rb(), BLK, 0, c.st>>>(h->bt, h->yt, h->t->flags, n(), make_red(h, rb(), OP_TRUE));
+            launch_k(k_resid<double>, rb(), BLK, 0, c.st, h->bt, h->yt, h->t->flags, n(), make_red(h, rb(), OP_TRUE));
         });
         if (ns) solution_mean(h, c, h->xt);
         ck_launch("finish");
@@ -755,50 +781,50 @@ struct BiCG {
         zero(h->Ap, n() * sizeof(TO));
         zero(h->B, H().ncell * sizeof(TV));
         TO* r = V(h->r);
-        launch(c, -1, 0, n(), [&] { k_cast<double, TO><<<gb(), BLK, 0, c.st>>>(h->bt, r, n()); });
-        launch(c, -1, 0, n(), [&] { k_dot<TO, TO, true><<<rb(), BLK, 0, c.st>>>(r, r, n(), make_red(h, rb(), OP_BB)); });
+        launch(c, -1, 0, n(), [&] { launch_k(k_cast<double, TO>, gb(), BLK, 0, c.st, h->bt, r, n()); });
+        launch(c, -1, 0, n(), [&] { launch_k(k_dot<TO, TO, true>, rb(), BLK, 0, c.st, r, r, n(), make_red(h, rb(), OP_BB)); });
         if (ns)
             launch(c, -1, 0, n(), [&] {
-                k_project<TO, TV><<<gb(), BLK, 0, c.st>>>(r, h->t->flags, h->S, (TV*)nullptr, n());
+                launch_k(k_project<TO, TV>, gb(), BLK, 0, c.st, r, h->t->flags, h->S, (TV*)nullptr, n());
             });
-        launch(c, -1, 0, n(), [&] { k_cast<TO, TO><<<gb(), BLK, 0, c.st>>>(r, V(h->rhat), n()); });
+        launch(c, -1, 0, n(), [&] { launch_k(k_cast<TO, TO>, gb(), BLK, 0, c.st, r, V(h->rhat), n()); });
         launch(c, -1, 0, n(), [&] {
-            k_dot<TO, TO, false><<<rb(), BLK, 0, c.st>>>(V(h->rhat), r, n(), make_red(h, rb(), OP_BI_INIT, cond, set_cond));
+            launch_k(k_dot<TO, TO, false>, rb(), BLK, 0, c.st, V(h->rhat), r, n(), make_red(h, rb(), OP_BI_INIT, cond, set_cond));
         });
         ck_launch("bicg begin");
     }
     void precondition(TO* out) {
         zero(h->U, H().ntree * sizeof(TV));
         Cycle<TV>{h, U(), B(), c}.run();
-        launch(c, -1, 0, n(), [&] { k_cast<TV, TO><<<gb(), BLK, 0, c.st>>>(U(), out, n()); });
+        launch(c, -1, 0, n(), [&] { launch_k(k_cast<TV, TO>, gb(), BLK, 0, c.st, U(), out, n()); });
     }
     void body() {
         TO *r = V(h->r), *p = V(h->p), *v = V(h->Ap), *s = V(h->s), *t = V(h->tv), *ph = V(h->ph), *sh = V(h->sh);
-        launch(c, -1, 0, n(), [&] { k_bi_p<TO, TV><<<gb(), BLK, 0, c.st>>>(p, r, v, B(), h->S, n()); });
+        launch(c, -1, 0, n(), [&] { launch_k(k_bi_p<TO, TV>, gb(), BLK, 0, c.st, p, r, v, B(), h->S, n()); });
         precondition(ph);
         apply_outer_T<TO, TC, TW>(h, Co, ph, v, c);
         launch(c, -1, 0, n(), [&] {
-            k_dot<TO, TO, false><<<rb(), BLK, 0, c.st>>>(V(h->rhat), v, n(), make_red(h, rb(), OP_BI_ALPHA));
+            launch_k(k_dot<TO, TO, false>, rb(), BLK, 0, c.st, V(h->rhat), v, n(), make_red(h, rb(), OP_BI_ALPHA));
         });
-        launch(c, -1, 0, n(), [&] { k_bi_s<TO, TV><<<gb(), BLK, 0, c.st>>>(s, r, v, B(), h->S, n()); });
+        launch(c, -1, 0, n(), [&] { launch_k(k_bi_s<TO, TV>, gb(), BLK, 0, c.st, s, r, v, B(), h->S, n()); });
         precondition(sh);
         apply_outer_T<TO, TC, TW>(h, Co, sh, t, c);
-        launch(c, -1, 0, n(), [&] { k_dot2<TO><<<rb(), BLK, 0, c.st>>>(t, s, n(), make_red(h, rb(), OP_BI_OMEGA)); });
+        launch(c, -1, 0, n(), [&] { launch_k(k_dot2<TO>, rb(), BLK, 0, c.st, t, s, n(), make_red(h, rb(), OP_BI_OMEGA)); });
         launch(c, -1, 0, n(), [&] {
-            k_bi_x<TO><<<rb(), BLK, 0, c.st>>>(V(h->x), r, s, t, ph, sh, V(h->rhat), n(),
+            launch_k(k_bi_x<TO>, rb(), BLK, 0, c.st, V(h->x), r, s, t, ph, sh, V(h->rhat), n(),
                                                make_red(h, rb(), OP_BI_RR, cond, set_cond));
         });
         if (ns)
             launch(c, -1, 0, n(), [&] {
-                k_project<TO, TV><<<gb(), BLK, 0, c.st>>>(r, h->t->flags, h->S, (TV*)nullptr, n());
+                launch_k(k_project<TO, TV>, gb(), BLK, 0, c.st, r, h->t->flags, h->S, (TV*)nullptr, n());
             });
         ck_launch("bicg body");
     }
     void finish() {
-        launch(c, -1, 0, n(), [&] { k_cast<TO, double><<<gb(), BLK, 0, c.st>>>(V(h->x), h->xt, n()); });
+        launch(c, -1, 0, n(), [&] { launch_k(k_cast<TO, double>, gb(), BLK, 0, c.st, V(h->x), h->xt, n()); });
         apply_outer_T<double, TC, TW>(h, Co, h->xt, h->yt, c);
         launch(c, -1, 0, n(), [&] {
-            k_resid<double><<<rb(), BLK, 0, c.st>>>(h->bt, h->yt, h->t->flags, n(), make_red(h, rb(), OP_TRUE));
+            launch_k(k_resid<double>, rb(), BLK, 0, c.st, h->bt, h->yt, h->t->flags, n(), make_red(h, rb(), OP_TRUE));
         });
         if (ns) solution_mean(h, c, h->xt);
         ck_launch("bicg finish");
@@ -906,7 +932,7 @@ int krylov_solve(ocg_hier* h, Coefs<TC, TW> Co, int prec, const double* b_user, 
     ck(cudaMemcpyAsync(h->S, h->hS, S_COUNT * sizeof(double), cudaMemcpyHostToDevice, st), "copy scalars");
     ck(cudaMemsetAsync(h->bt, 0, H.ntree * sizeof(double), st), "memset");
     launch(c, -1, 0, H.nleaf, [&] {
-        k_scatter<double, double><<<nblk(H.nleaf), BLK, 0, st>>>(b_user, h->bt, t->leaf_cell, (int)H.nleaf);
+        launch_k(k_scatter<double, double>, nblk(H.nleaf), BLK, 0, st, b_user, h->bt, t->leaf_cell, (int)H.nleaf);
     });
     ck_launch("scatter");
     int64_t kernels = c.count;
@@ -959,10 +985,10 @@ int krylov_solve(ocg_hier* h, Coefs<TC, TW> Co, int prec, const double* b_user, 
     // under the null space
     launch(c, -1, 0, H.nleaf, [&] {
         if (ns)
-            k_gather_shift<double, double><<<nblk(H.nleaf), BLK, 0, st>>>(h->xt, x_user, t->leaf_cell, h->S,
+            launch_k(k_gather_shift<double, double>, nblk(H.nleaf), BLK, 0, st, h->xt, x_user, t->leaf_cell, h->S,
                                                                          (int)H.nleaf);
         else
-            k_gather<double, double><<<nblk(H.nleaf), BLK, 0, st>>>(h->xt, x_user, t->leaf_cell, (int)H.nleaf);
+            launch_k(k_gather<double, double>, nblk(H.nleaf), BLK, 0, st, h->xt, x_user, t->leaf_cell, (int)H.nleaf);
     });
     ck_launch("gather");
     ck(cudaMemcpyAsync(h->hS, h->S, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, st), "copy scalars");
@@ -1140,7 +1166,7 @@ int ocg_setup_hierarchy(const ocg_octree* t, const float* beta, const int32_t bc
         int* derr = dalloc<int>(1);
         ck(cudaMemsetAsync(derr, 0, sizeof(int), st), "memset");
         if (H.nface > 0) {
-            k_face_scatter<<<nblk(H.nface), BLK, 0, st>>>(beta, t->fslot, t->fkind, t->fdepth, dh, (int)H.nface, cm,
+            launch_k(k_face_scatter, nblk(H.nface), BLK, 0, st, beta, t->fslot, t->fkind, t->fdepth, dh, (int)H.nface, cm,
                                                          h->tw64, derr);
             ck_launch("face scatter");
         }
@@ -1150,13 +1176,13 @@ int ocg_setup_hierarchy(const ocg_octree* t, const float* beta, const int32_t bc
             LT.off[m - H.mc] = (int)H.L(m).off;
             LT.h[m - H.mc] = H.L(m).h;
         }
-        k_leaf_gather<<<nblk(H.nleaf), BLK, 0, st>>>(t->leaf_cell, t->level, t->tables(), LT,
+        launch_k(k_leaf_gather, nblk(H.nleaf), BLK, 0, st, t->leaf_cell, t->level, t->tables(), LT,
                                                     make_int4(bc[0], bc[1], bc[2], bc[3]), make_int2(bc[4], bc[5]),
                                                     (int)H.nleaf, (int)H.ncell, h->c64[0], cm, h->tw64);
         ck_launch("leaf gather");
         for (int m = H.D; m > H.mc; --m) {
             const LevelArgs A = t->largs(m);
-            k_coarsen<<<nblk(A.ncell / 8), BLK, 0, st>>>(A, t->tables(), prm->alpha, h->c64[0], cm, (int)H.ncell);
+            launch_k(k_coarsen, nblk(A.ncell / 8), BLK, 0, st, A, t->tables(), prm->alpha, h->c64[0], cm, (int)H.ncell);
             ck_launch("coarsen");
         }
         for (int q = 0; q < 3; ++q) {
@@ -1172,14 +1198,14 @@ int ocg_setup_hierarchy(const ocg_octree* t, const float* beta, const int32_t bc
         if (prm->coef_dtype == OCG_F32) {
             for (int q = 0; q < 4; ++q) {
                 h->c32[q] = dalloc<float>(H.ncell);
-                k_convert<float><<<nblk(H.ncell), BLK, 0, st>>>(h->c64[q], h->c32[q], H.ncell);
+                launch_k(k_convert<float>, nblk(H.ncell), BLK, 0, st, h->c64[q], h->c32[q], H.ncell);
                 if (prm->bf16_coarse) {
                     h->c16[q] = dalloc<__nv_bfloat16>(H.ncell);
-                    k_convert<__nv_bfloat16><<<nblk(H.ncell), BLK, 0, st>>>(h->c64[q], h->c16[q], H.ncell);
+                    launch_k(k_convert<__nv_bfloat16>, nblk(H.ncell), BLK, 0, st, h->c64[q], h->c16[q], H.ncell);
                 }
             }
             h->tw32 = dalloc<float>(ntw);
-            k_convert<float><<<nblk(ntw), BLK, 0, st>>>(h->tw64, h->tw32, ntw);
+            launch_k(k_convert<float>, nblk(ntw), BLK, 0, st, h->tw64, h->tw32, ntw);
             ck_launch("convert");
             ck(cudaStreamSynchronize(st), "setup sync");
             for (int q = 0; q < 4; ++q) { dfree(h->c64[q]); h->c64[q] = nullptr; }
@@ -1268,12 +1294,12 @@ int ocg_apply_A(ocg_hier* h, int32_t dtype, const void* x, void* y, int32_t tran
             TO* Y = (TO*)h->yt;
             ck(cudaMemsetAsync(P, 0, H.ntree * sizeof(TO), st), "memset");
             launch(c, -1, 0, H.nleaf, [&] {
-                k_scatter<TO, TO><<<nblk(H.nleaf), BLK, 0, st>>>((const TO*)x, P, t->leaf_cell, (int)H.nleaf);
+                launch_k(k_scatter<TO, TO>, nblk(H.nleaf), BLK, 0, st, (const TO*)x, P, t->leaf_cell, (int)H.nleaf);
             });
             if (transpose) apply_outer_T<TO, TC, TW>(h, C, P, Y, c);
             else apply_outer<TO, TC, TW>(h, C, P, Y, OP_NONE, c);
             launch(c, -1, 0, H.nleaf, [&] {
-                k_gather<TO, TO><<<nblk(H.nleaf), BLK, 0, st>>>(Y, (TO*)y, t->leaf_cell, (int)H.nleaf);
+                launch_k(k_gather<TO, TO>, nblk(H.nleaf), BLK, 0, st, Y, (TO*)y, t->leaf_cell, (int)H.nleaf);
             });
             ck_launch("apply_A");
         };
@@ -1304,11 +1330,11 @@ int ocg_vcycle(ocg_hier* h, int32_t dtype, const void* r, void* z, void* stream)
             ck(cudaMemsetAsync(U, 0, H.ncell * sizeof(TV), st), "memset");
             ck(cudaMemsetAsync(B, 0, H.ncell * sizeof(TV), st), "memset");
             launch(c, -1, 0, H.nleaf, [&] {
-                k_scatter<TV, TV><<<nblk(H.nleaf), BLK, 0, st>>>((const TV*)r, B, t->leaf_cell, (int)H.nleaf);
+                launch_k(k_scatter<TV, TV>, nblk(H.nleaf), BLK, 0, st, (const TV*)r, B, t->leaf_cell, (int)H.nleaf);
             });
             Cycle<TV>{h, U, B, c}.run();
             launch(c, -1, 0, H.nleaf, [&] {
-                k_gather<TV, TV><<<nblk(H.nleaf), BLK, 0, st>>>(U, (TV*)z, t->leaf_cell, (int)H.nleaf);
+                launch_k(k_gather<TV, TV>, nblk(H.nleaf), BLK, 0, st, U, (TV*)z, t->leaf_cell, (int)H.nleaf);
             });
             ck_launch("vcycle");
         };
@@ -1339,24 +1365,24 @@ int ocg_face_grad(ocg_hier* h, const double* p, const double* lambda, double* db
         ck(cudaMemsetAsync(h->xt, 0, H.ntree * sizeof(double), st), "memset");
         ck(cudaMemsetAsync(h->yt, 0, H.ntree * sizeof(double), st), "memset");
         launch(c, -1, 0, H.nleaf, [&] {
-            k_scatter<double, double><<<nblk(H.nleaf), BLK, 0, st>>>(p, h->xt, t->leaf_cell, (int)H.nleaf);
+            launch_k(k_scatter<double, double>, nblk(H.nleaf), BLK, 0, st, p, h->xt, t->leaf_cell, (int)H.nleaf);
         });
         launch(c, -1, 0, H.nleaf, [&] {
-            k_scatter<double, double><<<nblk(H.nleaf), BLK, 0, st>>>(lambda, h->yt, t->leaf_cell, (int)H.nleaf);
+            launch_k(k_scatter<double, double>, nblk(H.nleaf), BLK, 0, st, lambda, h->yt, t->leaf_cell, (int)H.nleaf);
         });
         for (int m = H.D; m >= 1; --m) {
             const LevelArgs A = t->largs(m);
             launch(c, -1, m, A.ncell, [&] {
                 if (h->c64[0])
-                    k_oavg<double, double><<<nblk(A.ncell / 8, OBLK), OBLK, 0, st>>>(A, t->tables(), h->c64[0], h->xt);
+                    launch_k(k_oavg<double, double>, nblk(A.ncell / 8, OBLK), OBLK, 0, st, A, t->tables(), h->c64[0], h->xt);
                 else
-                    k_oavg<double, float><<<nblk(A.ncell / 8, OBLK), OBLK, 0, st>>>(A, t->tables(), h->c32[0], h->xt);
+                    launch_k(k_oavg<double, float>, nblk(A.ncell / 8, OBLK), OBLK, 0, st, A, t->tables(), h->c32[0], h->xt);
             });
         }
         launch(c, -1, 0, H.nface, [&] {
             FaceHs fh{};
             for (int d = 0; d <= H.D; ++d) fh.h[d] = 1.0 / (double)((int64_t)H.n0 << d);
-            k_face_grad<<<nblk(H.nface), BLK, 0, st>>>((int)H.nface, t->fminus, t->fplus, t->fkind, t->fdepth,
+            launch_k(k_face_grad, nblk(H.nface), BLK, 0, st, (int)H.nface, t->fminus, t->fplus, t->fkind, t->fdepth,
                                                       t->leaf_cell, t->level, t->oct_parent, fh, h->xt, h->yt, dbeta);
         });
         ck_launch("face_grad");
@@ -1477,13 +1503,13 @@ extern "C" int ocg_apply_A_f32_noalloc(ocg_hier* h, const float* x, float* y, vo
         ck(cudaMemsetAsync(P, 0, H.ntree * sizeof(float), st), "memset");
         Ctx c{st, nullptr, 0};
         launch(c, -1, 0, H.nleaf, [&] {
-            k_scatter<float, float><<<nblk(H.nleaf), BLK, 0, st>>>(x, P, t->leaf_cell, (int)H.nleaf);
+            launch_k(k_scatter<float, float>, nblk(H.nleaf), BLK, 0, st, x, P, t->leaf_cell, (int)H.nleaf);
         });
         ck_launch("scatter");
         if (h->c64[0]) apply_outer<float, double, double>(h, h->C64(), P, Y, OP_NONE, c);
         else apply_outer<float, float, float>(h, h->C32(), P, Y, OP_NONE, c);
         launch(c, -1, 0, H.nleaf, [&] {
-            k_gather<float, float><<<nblk(H.nleaf), BLK, 0, st>>>(Y, y, t->leaf_cell, (int)H.nleaf);
+            launch_k(k_gather<float, float>, nblk(H.nleaf), BLK, 0, st, Y, y, t->leaf_cell, (int)H.nleaf);
         });
         ck_launch("gather");
         g_launches += c.count;

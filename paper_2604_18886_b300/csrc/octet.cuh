@@ -287,6 +287,7 @@ __device__ __forceinline__ void osweep_octet(const LevelArgs& A, const Tables& T
 template <class TV, class TC, class TW>
 __global__ void __launch_bounds__(OBLK, sizeof(TV) == 4 ? 16 : 8) k_osweep(LevelArgs A, Tables T, Coefs<TC, TW> C, TV* __restrict__ U,
                                                  TV* __restrict__ B, int colour, int prolong, int fixb) {
+    pdl_enter();
     const int o = blockIdx.x * OBLK + threadIdx.x;
     if (o >= A.ncell / 8) return;
     osweep_octet<TV, TC, TW>(A, T, C, U, B, o, colour, prolong, fixb);
@@ -308,6 +309,7 @@ struct TileSh {
 template <class TV, class TC, class TW>
 __global__ void __launch_bounds__(TBLK) k_tsweep(LevelArgs A, Tables T, Coefs<TC, TW> C, TV* __restrict__ U,
                                                  TV* __restrict__ B, int colour, int prolong) {
+    pdl_enter();
     __shared__ TileSh<TV> sh;
     const int noct = A.ncell >> 3;
     const int o0 = blockIdx.x * TBLK, lo = threadIdx.x;
@@ -500,6 +502,7 @@ __device__ __forceinline__ void csweep_cell(const LevelArgs& A, const Tables& T,
 template <class TV, class TC, class TW>
 __global__ void __launch_bounds__(BLK) k_csweep(LevelArgs A, Tables T, Coefs<TC, TW> C, TV* __restrict__ U,
                                                 TV* __restrict__ B, int colour, int prolong) {
+    pdl_enter();
     csweep_cell<TV, TC, TW>(A, T, C, U, B, blockIdx.x * BLK + threadIdx.x, colour, prolong);
 }
 
@@ -549,6 +552,7 @@ __device__ __forceinline__ void ldc4(const __nv_bfloat16* __restrict__ p, TV (&r
 template <class TV, class TC, class TW>
 __global__ void __launch_bounds__(BLK) k_qsweep(LevelArgs A, Tables T, Coefs<TC, TW> C, TV* __restrict__ U,
                                                 TV* __restrict__ B, int colour, int prolong) {
+    pdl_enter();
     const int tid = blockIdx.x * BLK + threadIdx.x;
     const int noct = A.ncell >> 3;
     const bool valid = (tid >> 1) < noct;
@@ -729,6 +733,7 @@ __device__ __forceinline__ void orestrict_octet(const LevelArgs& A, const Tables
 template <class TV, class TC, class TW>
 __global__ void __launch_bounds__(OBLK) k_orestrict(LevelArgs A, Tables T, Coefs<TC, TW> C, TV* __restrict__ U,
                                                     TV* __restrict__ B, TV scale) {
+    pdl_enter();
     const int o = blockIdx.x * OBLK + threadIdx.x;
     if (o >= A.ncell / 8) return;
     orestrict_octet<TV, TC, TW>(A, T, C, U, B, scale, o);
@@ -738,6 +743,7 @@ __global__ void __launch_bounds__(OBLK) k_orestrict(LevelArgs A, Tables T, Coefs
 template <class TV, class TC>
 __global__ void __launch_bounds__(OBLK) k_oprolong(LevelArgs A, Tables T, const TC* __restrict__ d,
                                                    TV* __restrict__ U) {
+    pdl_enter();
     const int o = blockIdx.x * OBLK + threadIdx.x;
     if (o >= A.ncell / 8) return;
     const int c8 = A.off + 8 * o;
@@ -747,6 +753,7 @@ __global__ void __launch_bounds__(OBLK) k_oprolong(LevelArgs A, Tables T, const 
 // Outer vector: parent value = mean of the active children (composite operator, Sec. 3.1).
 template <class TO, class TC>
 __global__ void __launch_bounds__(OBLK) k_oavg(LevelArgs A, Tables T, const TC* __restrict__ d, TO* __restrict__ P) {
+    pdl_enter();
     const int o = blockIdx.x * OBLK + threadIdx.x;
     if (o >= A.ncell / 8) return;
     const int c8 = A.off + 8 * o;
@@ -776,6 +783,7 @@ struct OMultiLevel {
 template <class TO, class TC, class TW>
 __global__ void __launch_bounds__(OBLK) k_oapply(OMultiLevel ML, Tables T, Coefs<TC, TW> C, const TO* __restrict__ P,
                                                  TO* __restrict__ Y, Red R) {
+    pdl_enter();
     __shared__ double sh[32];
     double dot = 0.0;
     const int nvb = ML.boff[ML.n];
@@ -888,6 +896,7 @@ __device__ __forceinline__ double df_to_double(DF x) {
 template <class TC, class TW>
 __global__ void __launch_bounds__(OBLK) k_oapply_df(OMultiLevel ML, Tables T, Coefs<TC, TW> C,
                                                     const double* __restrict__ P, double* __restrict__ Y, Red R) {
+    pdl_enter();
     __shared__ double sh[32];
     DF dot{0.0f, 0.0f};
     const int nvb = ML.boff[ML.n];
@@ -1018,6 +1027,7 @@ __global__ void __launch_bounds__(OBLK) k_oapply_df(OMultiLevel ML, Tables T, Co
 template <class TO, class TC, class TW>
 __global__ void __launch_bounds__(OBLK) k_tfine(Tables T, Coefs<TC, TW> C, const int32_t* __restrict__ t_oct,
                                                  TO* __restrict__ X, TO* __restrict__ Y, double* __restrict__ tseed) {
+    pdl_enter();
     const int q = blockIdx.x * OBLK + threadIdx.x;
     if (q >= T.nt) return;
     const int og = __ldg(t_oct + q);
@@ -1052,6 +1062,7 @@ __global__ void __launch_bounds__(OBLK) k_tfine(Tables T, Coefs<TC, TW> C, const
 template <class TO, class TC, class TW>
 __global__ void k_tcoarse(Tables T, Coefs<TC, TW> C, OMultiLevel ML, const int8_t* __restrict__ level,
                           const int32_t* __restrict__ tcoarse, int n, const TO* __restrict__ X, TO* __restrict__ Y) {
+    pdl_enter();
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= n) return;
     const int K = __ldg(tcoarse + q);
@@ -1089,6 +1100,7 @@ __global__ void k_tcoarse(Tables T, Coefs<TC, TW> C, OMultiLevel ML, const int8_
 template <class TO>
 __global__ void k_tdesc(Tables T, const int32_t* __restrict__ tdesc, int n, int ntree,
                         const uint8_t* __restrict__ flags, const double* __restrict__ tseed, TO* __restrict__ Y) {
+    pdl_enter();
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= n) return;
     const int og = __ldg(tdesc + q);
@@ -1110,6 +1122,7 @@ __global__ void k_tdesc(Tables T, const int32_t* __restrict__ tdesc, int n, int 
 template <class TV, class TC, class TW>
 __global__ void __launch_bounds__(256) k_ocoarsest(LevelArgs A, Tables T, Coefs<TC, TW> C, TV* __restrict__ U,
                                                     TV* __restrict__ B, int nu, int fas, int prolong) {
+    pdl_enter();
     const int noct = A.ncell / 8;
     auto pass = [&](int colour, bool fixb) {
         for (int o = threadIdx.x; o < noct; o += blockDim.x) {
@@ -1372,6 +1385,7 @@ __device__ __forceinline__ void tail_cycle(const TailArgs& A, int fas, int prolo
 template <class TV, class TC, class TW>
 __global__ void __launch_bounds__(sizeof(TV) == 8 ? 256 : 512)
     k_otail(TailArgs A, Tables T, Coefs<TC, TW> C, TV* __restrict__ U, TV* __restrict__ B, TV scale) {
+    pdl_enter();
     tail_cycle<TV, TC, TW>(A, A.fas, A.prolong, T, C, U, B, scale);
 }
 
