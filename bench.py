@@ -176,6 +176,31 @@ def _hier_bf16(p, tree, dev):
     return S.Hierarchy(tree, torch.from_numpy(beta).to(dev), p.bc, S.mg_params(coef="f32", bf16_coarse=True))
 
 
+def _w_cycle(g, beta, p, b, dev, stream, flush, steps, bf16=False):
+    """The same solve preconditioned by W-cycles (mu = 2; the paper's choice for cut-cell
+    problems) instead of V-cycles: iterations and Mcells/s."""
+    import torch
+    from paper_2604_18886_b300 import solver as S
+    hw = S.Hierarchy(g, beta, p.bc, S.mg_params(mu=2, coef="f32", bf16_coarse=bf16))
+    x = torch.empty_like(b)
+    hw.solve(b, x, tol=1e-6, precision="mixed", stream=stream)
+    t, its = [], set()
+    for s_ in range(steps):
+        flush.fill_(float(s_))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, st = hw.solve(b, x, tol=1e-6, precision="mixed", stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        t.append(e0.elapsed_time(e1))
+        its.add(st.iterations)
+    ms = statistics.mean(t)
+    del hw
+    return {"value": round(g.n_leaves / (ms / 1e3) / 1e6, 3), "unit": UNIT, "ms_per_step": round(ms, 3),
+            "iterations": sorted(its), "true_rel_res": st.true_rel_res, "cycle": "W (mu=2), nu=2/2"}
+
+
 def _cut_cell(dev, stream, flush, args):
     """The cut-cell projection workload: 64^3 root, two levels of refinement within 0.05
     of a solid sphere and box, fluid-fraction beta, Neumann walls, divergence rhs; mixed
@@ -206,7 +231,9 @@ def _cut_cell(dev, stream, flush, args):
         its.add(st.iterations)
         assert st.converged
     ms = statistics.mean(t)
-    return {"workload": "cut-cell projection: 64^3 root, sphere r=0.2 and box, band 0.05, 2 levels "
+    wc = _w_cycle(g, beta, p, b, dev, stream, flush, steps, bf16=True)
+    return {"w_cycle": wc,
+            "workload": "cut-cell projection: 64^3 root, sphere r=0.2 and box, band 0.05, 2 levels "
                         "(%d leaves), fluid-fraction beta, Neumann, divergence rhs" % g.n_leaves,
             "precision": "mixed, BF16 coarse coefficients", "value": round(g.n_leaves / (ms / 1e3) / 1e6, 3),
             "unit": UNIT, "ms_per_step": round(ms, 4), "steps": steps, "iterations": sorted(its),
@@ -280,6 +307,7 @@ def _large(dev, stream, flush, args, peak):
         e1.synchronize()
         t32.append(e0.elapsed_time(e1))
     ms32 = statistics.mean(t32)
+    wc = _w_cycle(g, beta, p, b, dev, stream, flush, steps)
     # finest-level sweep inside an unrolled graph of the same solve
     D = g.D
     L.check(L.lib().ocg_probe_set(h.handle, L.OCG_PROBE_SWEEP, D))
@@ -312,6 +340,7 @@ def _large(dev, stream, flush, args, peak):
             "precision": "mixed (FP32 V-cycle, FP64 PCG)", "value": round(g.n_leaves / (ms / 1e3) / 1e6, 3),
             "unit": UNIT, "ms_per_step": round(ms, 3), "steps": steps, "iterations": sorted(its),
             "true_rel_res": st.true_rel_res, "build_s": round(t_build, 2), "setup_s": round(t_setup, 2),
+            "w_cycle": wc,
             "plain_fp32": {"value": round(g.n_leaves / (ms32 / 1e3) / 1e6, 3), "unit": UNIT,
                            "ms_per_step": round(ms32, 3), "iterations": st32.iterations,
                            "true_rel_res": st32.true_rel_res},

@@ -41,9 +41,20 @@ struct LevelArgs {
     int ni;       // uniform level: octets per axis (lexicographic octets); 0 = adaptive
 };
 
+template <class TC>
+struct DiagOf {
+    using type = TC;
+};
+template <>
+struct DiagOf<__nv_bfloat16> {
+    using type = float;
+};
+
 template <class TC, class TW>
 struct Coefs {
-    const TC* d;
+    // the diagonal is kept in FP32 when the face coefficients are BF16 (conservative
+    // diagonal, see k_diag_conservative)
+    const typename DiagOf<TC>::type* d;
     const TC* cx;
     const TC* cy;
     const TC* cz;

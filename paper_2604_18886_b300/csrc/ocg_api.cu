@@ -247,7 +247,8 @@ struct ocg_hier {
     double* tseed = nullptr;   // adjoint: per tree cell, the a_P weight sums of the T faces
     float* c32[4] = {nullptr, nullptr, nullptr, nullptr};
     float* tw32 = nullptr;
-    __nv_bfloat16* c16[4] = {nullptr, nullptr, nullptr, nullptr};
+    __nv_bfloat16* c16[4] = {nullptr, nullptr, nullptr, nullptr};   // [0] unused: see d16
+    float* d16 = nullptr;         // conservative FP32 diagonal of the BF16 set
     // work space, allocated once at set-up at the widest type so a captured graph keeps
     // valid pointers: x, r, p, Ap, bt (b in cell order), xt, yt over the tree cells;
     // U, B over all cells
@@ -275,7 +276,7 @@ struct ocg_hier {
 
     Coefs<double, double> C64() const { return {c64[0], c64[1], c64[2], c64[3], tw64}; }
     Coefs<float, float> C32() const { return {c32[0], c32[1], c32[2], c32[3], tw32}; }
-    Coefs<__nv_bfloat16, float> C16() const { return {c16[0], c16[1], c16[2], c16[3], tw32}; }
+    Coefs<__nv_bfloat16, float> C16() const { return {d16, c16[1], c16[2], c16[3], tw32}; }
 
     ~ocg_hier() {
         for (auto& tr : graphs)
@@ -289,6 +290,7 @@ struct ocg_hier {
         dfree(tseed);
         if (cap) cudaStreamDestroy(cap);
         for (int i = 0; i < 4; ++i) { dfree(c64[i]); dfree(c32[i]); dfree(c16[i]); }
+        dfree(d16);
         dfree(tw64); dfree(tw32); dfree(S); dfree(part); dfree(cnt); dfree(tail_sched); dfree(tail_sched2);
         if (hS) cudaFreeHost(hS);
         for (double* v : {x, r, p, Ap, bt, xt, yt, U, B}) dfree(v);
@@ -394,7 +396,7 @@ std::vector<int64_t> level_cells_morton(const HostTree& H, int m) {
 // ------------------------------------------------------------------ mu-cycle driver
 template <class CC>
 struct CoefTypes {
-    using TC = std::remove_const_t<std::remove_pointer_t<decltype(CC::d)>>;
+    using TC = std::remove_const_t<std::remove_pointer_t<decltype(CC::cx)>>;
     using TW = std::remove_const_t<std::remove_pointer_t<decltype(CC::tw)>>;
 };
 
@@ -464,7 +466,7 @@ struct Cycle {
             using TC = typename CoefTypes<decltype(C)>::TC;
             const LevelArgs A = h->t->largs(m);
             launch(c, OCG_PROBE_PROLONG, m, A.ncell, [&] {
-                launch_k(k_oprolong<TV, TC>, nblk(A.ncell / 8, OBLK), OBLK, 0, c.st, A, h->t->tables(), C.d, U);
+                launch_k(k_oprolong<TV, std::remove_const_t<std::remove_pointer_t<decltype(C.d)>>>, nblk(A.ncell / 8, OBLK), OBLK, 0, c.st, A, h->t->tables(), C.d, U);
             });
         });
         ck_launch("prolong");
@@ -1199,13 +1201,22 @@ int ocg_setup_hierarchy(const ocg_octree* t, const float* beta, const int32_t bc
             for (int q = 0; q < 4; ++q) {
                 h->c32[q] = dalloc<float>(H.ncell);
                 launch_k(k_convert<float>, nblk(H.ncell), BLK, 0, st, h->c64[q], h->c32[q], H.ncell);
-                if (prm->bf16_coarse) {
+                if (prm->bf16_coarse && q > 0) {
                     h->c16[q] = dalloc<__nv_bfloat16>(H.ncell);
                     launch_k(k_convert<__nv_bfloat16>, nblk(H.ncell), BLK, 0, st, h->c64[q], h->c16[q], H.ncell);
                 }
             }
             h->tw32 = dalloc<float>(ntw);
             launch_k(k_convert<float>, nblk(ntw), BLK, 0, st, h->tw64, h->tw32, ntw);
+            if (prm->bf16_coarse) {
+                h->d16 = dalloc<float>(H.ncell);
+                for (int m = H.mc; m <= H.D; ++m) {
+                    const LevelArgs A = t->largs(m);
+                    launch_k(k_diag_conservative<__nv_bfloat16>, nblk(A.ncell / 8, OBLK), OBLK, 0, st, A, t->tables(),
+                             h->C64(), (const __nv_bfloat16*)h->c16[1], (const __nv_bfloat16*)h->c16[2],
+                             (const __nv_bfloat16*)h->c16[3], (const float*)h->tw32, h->d16);
+                }
+            }
             ck_launch("convert");
             ck(cudaStreamSynchronize(st), "setup sync");
             for (int q = 0; q < 4; ++q) { dfree(h->c64[q]); h->c64[q] = nullptr; }

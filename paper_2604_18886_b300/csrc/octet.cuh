@@ -279,7 +279,7 @@ __device__ __forceinline__ void osweep_octet(const LevelArgs& A, const Tables& T
 #pragma unroll
         for (int s = 0; s < 8; ++s) {
             const int co = __ldg(T.child_oct + c8 + s);
-            if (co >= 0) octet_prolong<TV, TC>(C.d, U, co, un[s]);
+            if (co >= 0) octet_prolong<TV>(C.d, U, co, un[s]);
         }
     }
 }
@@ -412,7 +412,7 @@ __global__ void __launch_bounds__(TBLK) k_tsweep(LevelArgs A, Tables T, Coefs<TC
 #pragma unroll
         for (int s = 0; s < 8; ++s) {
             const int co = __ldg(T.child_oct + c8 + s);
-            if (co >= 0) octet_prolong<TV, TC>(C.d, U, co, un[s]);
+            if (co >= 0) octet_prolong<TV>(C.d, U, co, un[s]);
         }
     }
 }
@@ -495,7 +495,7 @@ __device__ __forceinline__ void csweep_cell(const LevelArgs& A, const Tables& T,
     }
     if (prolong && valid) {
         const int co = __ldg(T.child_oct + g);
-        if (co >= 0) octet_prolong<TV, TC>(C.d, U, co, un);
+        if (co >= 0) octet_prolong<TV>(C.d, U, co, un);
     }
 }
 
@@ -702,7 +702,7 @@ __global__ void __launch_bounds__(BLK) k_qsweep(LevelArgs A, Tables T, Coefs<TC,
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int co = __ldg(T.child_oct + base + q);
-            if (co >= 0) octet_prolong<TV, TC>(C.d, U, co, un[q]);
+            if (co >= 0) octet_prolong<TV>(C.d, U, co, un[q]);
         }
     }
 }
@@ -747,7 +747,7 @@ __global__ void __launch_bounds__(OBLK) k_oprolong(LevelArgs A, Tables T, const 
     const int o = blockIdx.x * OBLK + threadIdx.x;
     if (o >= A.ncell / 8) return;
     const int c8 = A.off + 8 * o;
-    octet_prolong<TV, TC>(d, U, c8 >> 3, U[__ldg(T.oct_parent + (c8 >> 3))]);
+    octet_prolong<TV>(d, U, c8 >> 3, U[__ldg(T.oct_parent + (c8 >> 3))]);
 }
 
 // Outer vector: parent value = mean of the active children (composite operator, Sec. 3.1).
@@ -808,6 +808,73 @@ __global__ void __launch_bounds__(OBLK) k_oapply(OMultiLevel ML, Tables T, Coefs
     }
     }
     if (R.op != OP_NONE) red_finish(R, blockIdx.x, dot, 0.0, sh);
+}
+
+// ------------------------------------------------------------ conservative BF16 diagonal
+// The diagonal of the BF16 coefficient set (kept in FP32): the FP64 remainder
+// d - sum_f w_f over the faces that enter the sweep's stencil (the walls' weights; zero for
+// an interior cell) minus the sum of the stored low-precision coefficients of those faces
+// (BF16 faces, FP32 T-record weights).  A row of the stored operator then sums to the
+// FP32-rounded remainder exactly, so BF16 storage keeps the constant null space of
+// all-Neumann problems; rounding d and the faces independently would leave each row sum
+// off by about 2^-9 d, which W-cycles amplify until PCG stalls.  Inactive cells keep 0.
+template <class TL>
+__global__ void __launch_bounds__(OBLK) k_diag_conservative(LevelArgs A, Tables T, Coefs<double, double> C64,
+                                                            const TL* __restrict__ cxl, const TL* __restrict__ cyl,
+                                                            const TL* __restrict__ czl, const float* __restrict__ twl,
+                                                            float* __restrict__ dout) {
+    pdl_enter();
+    const int o = blockIdx.x * OBLK + threadIdx.x;
+    if (o >= A.ncell / 8) return;
+    const int c8 = A.off + 8 * o, og = c8 >> 3;
+    double rem[8];
+    float sl[8];
+#pragma unroll
+    for (int s = 0; s < 8; ++s) { rem[s] = C64.d[c8 + s]; sl[s] = 0.0f; }
+    int nb[6];
+    octet_neighbours(T, A.ni, o, og, nb);
+    const double* c64[3] = {C64.cx, C64.cy, C64.cz};
+    const TL* cl[3] = {cxl, cyl, czl};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int bit = 1 << a;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int s = clear_slot(a, q), t = s | bit;
+            const double c = c64[a][c8 + t];
+            const float cf = tov(cl[a][c8 + t]);
+            rem[s] += c; rem[t] += c;
+            sl[s] += cf; sl[t] += cf;
+        }
+        const int v = nb[2 * a];
+        if (v != -1) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int s = clear_slot(a, q);
+                rem[s] += c64[a][c8 + s];
+                sl[s] += tov(cl[a][c8 + s]);
+            }
+        }
+        const int w = nb[2 * a + 1];
+        if (w >= 0) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int s = clear_slot(a, q) | bit, n = A.off + 8 * w + clear_slot(a, q);
+                rem[s] += c64[a][n];
+                sl[s] += tov(cl[a][n]);
+            }
+        } else if (w <= -2) {
+            const int t = T.trec[og];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int s = clear_slot(a, q) | bit, idx = ((2 * a + 1) * 4 + q) * T.nt + t;
+                rem[s] += C64.tw[idx];
+                sl[s] += twl[idx];
+            }
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < 8; ++s) dout[c8 + s] = C64.d[c8 + s] == 0.0 ? 0.0f : (float)rem[s] - sl[s];
 }
 
 // ------------------------------------------------------------ double-float outer apply
@@ -1153,7 +1220,7 @@ __global__ void __launch_bounds__(256) k_ocoarsest(LevelArgs A, Tables T, Coefs<
     if (prolong) {
         for (int c = threadIdx.x; c < A.ncell; c += blockDim.x) {
             const int co = T.child_oct[A.off + c];
-            if (co >= 0) octet_prolong<TV, TC>(C.d, U, co, U[A.off + c]);
+            if (co >= 0) octet_prolong<TV>(C.d, U, co, U[A.off + c]);
         }
     }
 }
@@ -1377,7 +1444,7 @@ __device__ __forceinline__ void tail_cycle(const TailArgs& A, int fas, int prolo
         const int no = tail_noct(L);
         for (int c = threadIdx.x; c < 8 * no; c += blockDim.x) {
             const int co = T.child_oct[L.off + c];
-            if (co >= 0) octet_prolong<TV, TC>(C.d, U, co, M.u[L.sbase + (c & 7) * no + (c >> 3)]);
+            if (co >= 0) octet_prolong<TV>(C.d, U, co, M.u[L.sbase + (c & 7) * no + (c >> 3)]);
         }
     }
 }

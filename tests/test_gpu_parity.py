@@ -378,3 +378,23 @@ def test_full_size_cut_cell_properties():
     hh = S.Hierarchy(gh_, bh, ph.bc, S.mg_params(coef="f32", bf16_coarse=True))
     _, sh = hh.solve(cuda(P.rhs(ph, gh_.leaves(), fh, bh)), tol=1e-6, precision="mixed")
     assert abs(sh.iterations - s16.iterations) <= 2, (sh.iterations, s16.iterations)
+
+
+@pytest.mark.parametrize("n0", [16, 24])
+def test_wcycle_with_bf16_coarse_coefficients_converges(n0):
+    # the BF16 coefficient set keeps every row's sum (conservative FP32 diagonal), so the
+    # all-Neumann cut-cell tree keeps its constant null space on the coarse levels and
+    # W-cycles converge as with FP32 coefficients (independent rounding of the diagonal
+    # stalled PCG at 24^3)
+    p = P.c3(n0, 2)
+    g = S.Octree(p.desc)
+    f = g.faces()
+    beta = P.face_beta(p, f)
+    b = cuda(P.rhs(p, g.leaves(), f, beta))
+    its = {}
+    for bf in (False, True):
+        h = S.Hierarchy(g, beta, p.bc, S.mg_params(mu=2, coef="f32", bf16_coarse=bf))
+        x, st = h.solve(b, tol=1e-6, precision="mixed", max_iter=30, raise_on_notconv=False)
+        assert st.converged and st.true_rel_res <= 1.5e-6, (bf, st.iterations, st.rel_res)
+        its[bf] = st.iterations
+    assert its[True] <= its[False] + 1, its
