@@ -346,22 +346,10 @@ __global__ void __launch_bounds__(OBLK) kb_oapply(const BProb* __restrict__ PP, 
     const int o = ((int)blockIdx.x - w.b0) * OBLK + threadIdx.x;
     const double* V = which ? P.xt : P.p;
     double* Y = which ? P.yt : P.Ap;
-    double dot = 0.0;
-    if (!skip && o < A.ncell / 8) {
-        const int c8 = A.off + 8 * o;
-        OctState<double> S;
-        load_octet<double, float, float>(V, P.C, c8, S);
-        octet_mean(S);
-        double Ap[8];
-        octet_Au<double, float, float>(P.T, P.C, V, A, o, c8 >> 3, S, Ap);
-#pragma unroll
-        for (int s = 0; s < 8; ++s) {
-            const bool leaf = __ldg(P.T.child_oct + c8 + s) < 0;
-            Y[c8 + s] = leaf ? Ap[s] : 0.0;
-            if (leaf) dot += S.u[s] * Ap[s];
-        }
-    }
-    if (which == 0) bred_finish<2>(PP, w.prob, (int)blockIdx.x - P.ab0, P.nba, R, dot, 0.0, 0.0, sh);
+    // pair-of-FP32 arithmetic, as the single-problem outer apply (k_oapply_df)
+    DF dot{0.0f, 0.0f};
+    if (!skip && o < A.ncell / 8) octet_apply_df<float, float>(P.T, P.C, V, Y, A.off, A.ni, o, dot);
+    if (which == 0) bred_finish<2>(PP, w.prob, (int)blockIdx.x - P.ab0, P.nba, R, df_to_double(dot), 0.0, 0.0, sh);
 }
 
 }  // namespace ocg

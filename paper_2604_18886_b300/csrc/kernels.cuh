@@ -221,6 +221,95 @@ __device__ __forceinline__ void red_finish(const Red& R, int blk, double va, dou
     red_finish<2>(R, blk, va, vb, 0.0, sh);
 }
 
+// ----------------------------------------------------------------- pair-of-FP32 arithmetic
+// B300 executes FP64 instructions, conversions between FP32 and FP64 included, at 1/64 of
+// the FP32 rate.  These helpers convert exactly with integer operations and evaluate
+// sums and products of binary64 values as pairs of binary32 (hi, lo) with error-free
+// transformations (TwoSum, TwoProd by FMA; T. J. Dekker, "A floating-point technique for
+// extending the available precision", Numer. Math. 18, 1971).
+struct DF {
+    float hi, lo;   // value hi + lo; lo is not kept normalised inside a computation
+};
+// TwoSum (Knuth): s + e = a + b exactly
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+// a += x, the rounding error of the leading parts carried into lo
+__device__ __forceinline__ void df_acc(DF& a, DF x) {
+    float s, e;
+    two_sum(a.hi, x.hi, s, e);
+    a.hi = s;
+    a.lo = a.lo + (e + x.lo);
+}
+// a += c exactly up to the rounding of lo (accumulation of FP32 coefficients)
+__device__ __forceinline__ void df_acc_f(DF& a, float c) {
+    float s, e;
+    two_sum(a.hi, c, s, e);
+    a.hi = s;
+    a.lo = a.lo + e;
+}
+__device__ __forceinline__ DF df_diff(DF x, DF y) {
+    float s, e;
+    two_sum(x.hi, -y.hi, s, e);
+    return {s, e + (x.lo - y.lo)};
+}
+// x * c with the product of the leading parts exact (FMA)
+__device__ __forceinline__ DF df_scale(DF x, float c) {
+    const float p = x.hi * c;
+    return {p, fmaf(x.lo, c, fmaf(x.hi, c, -p))};
+}
+__device__ __forceinline__ DF df_mul(DF x, DF y) {
+    const float p = x.hi * y.hi;
+    return {p, fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, fmaf(x.hi, y.hi, -p)))};
+}
+__device__ __forceinline__ DF df_norm(DF x) {
+    const float s = x.hi + x.lo;
+    return {s, x.lo - (s - x.hi)};
+}
+// binary64 -> (hi, lo): hi = sign, exponent and leading 23 fraction bits (truncated), lo =
+// the remaining 29 fraction bits rounded to 24; integer operations only.  |v| < 2^-126 is
+// flushed to 0, |v| >= 2^128 becomes an infinity or NaN in hi; lo is dropped when |v| <
+// 2^-74 (then the pair keeps 24 bits).
+__device__ __forceinline__ DF df_split(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const unsigned h32 = (unsigned)(b >> 32);
+    const unsigned sign = h32 & 0x80000000u;
+    const int e = (int)((h32 >> 20) & 0x7FFu);   // biased binary64 exponent
+    const unsigned hib = sign | ((unsigned)(e - 896) << 23) | ((unsigned)(b >> 29) & 0x7FFFFFu);
+    const float lo = __uint2float_rn((unsigned)b & 0x1FFFFFFFu) * __uint_as_float((unsigned)(e - 948) << 23);
+    const bool normal = (e >= 897) & (e <= 1150);
+    const unsigned big = sign | 0x7F800000u | ((b & 0xFFFFFFFFFFFFFull) ? 0x400000u : 0u);
+    const float hi = __uint_as_float(normal ? hib : (e < 897 ? sign : big));
+    return {hi, (normal & (e >= 949)) ? __uint_as_float(__float_as_uint(lo) | sign) : 0.0f};
+}
+// binary32 -> binary64 by bits (exact; subnormal floats are flushed to 0)
+__device__ __forceinline__ double f2d_bits(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned ex = (u >> 23) & 0xFFu;
+    const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+    if (ex == 0u) return __longlong_as_double((long long)sign);
+    const unsigned long long e64 = ex == 0xFFu ? 0x7FFull : (unsigned long long)(ex - 127u + 1023u);
+    return __longlong_as_double((long long)(sign | (e64 << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29)));
+}
+__device__ __forceinline__ double df_to_double(DF x) {
+    const DF n = df_norm(x);
+    return f2d_bits(n.hi) + f2d_bits(n.lo);
+}
+
+// FP64 -> FP32 rounded to nearest (through the pair: hi + lo in one FP32 addition)
+__device__ __forceinline__ float d2f_bits(double v) {
+    const DF p = df_split(v);
+    return p.hi + p.lo;
+}
+template <class TO, class TI>
+__device__ __forceinline__ TO cvt(TI v) { return TO(v); }
+template <>
+__device__ __forceinline__ double cvt<double, float>(float v) { return f2d_bits(v); }
+template <>
+__device__ __forceinline__ float cvt<float, double>(double v) { return d2f_bits(v); }
+
 // ----------------------------------------------------------------- PCG vector kernels
 template <class TI, class TO>
 __global__ void k_scatter(const TI* __restrict__ in, TO* __restrict__ out, const int32_t* __restrict__ leaf_cell,
@@ -266,7 +355,7 @@ __global__ void __launch_bounds__(BLK) k_update(TO* __restrict__ x, TO* __restri
             x[i + q * st] = xv[q] + alpha * pv[q];
             const TO rn = rv[q] - alpha * av[q];
             r[i + q * st] = rn;
-            if (b32) b32[i + q * st] = TB(rn);
+            if (b32) b32[i + q * st] = cvt<TB>(rn);
             const double rd = (double)rn;
             rr += rd * rd;
             if (SUM) rs += rd;
@@ -276,7 +365,7 @@ __global__ void __launch_bounds__(BLK) k_update(TO* __restrict__ x, TO* __restri
         x[i] = x[i] + alpha * p[i];
         const TO rn = r[i] - alpha * Ap[i];
         r[i] = rn;
-        if (b32) b32[i] = TB(rn);
+        if (b32) b32[i] = cvt<TB>(rn);
         const double rd = (double)rn;
         rr += rd * rd;
         if (SUM) rs += rd;
@@ -294,7 +383,7 @@ __global__ void k_project(TO* __restrict__ r, const uint8_t* __restrict__ flags,
     TO v = r[i];
     if (flags[i] & 1) v = v - TO(S[S_MEAN]);
     r[i] = v;
-    if (b32) b32[i] = TB(v);
+    if (b32) b32[i] = cvt<TB>(v);
 }
 
 // (a, b) and sum(a) over the first n cells, reduced into R
@@ -313,14 +402,14 @@ __global__ void __launch_bounds__(BLK) k_dot(const TA* __restrict__ a, const TB*
         for (int q = 0; q < 4; ++q) { av[q] = a[i + q * st]; bv[q] = b[i + q * st]; }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const double ai = (double)av[q];
-            v += ai * (double)bv[q];
+            const double ai = cvt<double>(av[q]);
+            v += ai * cvt<double>(bv[q]);
             if (SUM) s += ai;
         }
     }
     for (; i < n; i += st) {
-        const double ai = (double)a[i];
-        v += ai * (double)b[i];
+        const double ai = cvt<double>(a[i]);
+        v += ai * cvt<double>(b[i]);
         if (SUM) s += ai;
     }
     red_finish(R, blockIdx.x, v, s, sh);
@@ -459,7 +548,8 @@ __global__ void k_pupdate(TO* __restrict__ p, const TZ* __restrict__ z, const do
     pdl_enter();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    p[i] = first ? TO(z[i]) : TO(z[i]) + TO(S[S_BETA]) * p[i];
+    const TO zi = cvt<TO>(z[i]);
+    p[i] = first ? zi : zi + TO(S[S_BETA]) * p[i];
 }
 
 // ----------------------------------------------------------------- setup kernels (FP64)

@@ -889,75 +889,112 @@ __global__ void __launch_bounds__(OBLK) k_diag_conservative(LevelArgs A, Tables 
 // computes every face difference before scaling it, so the rounding error is relative to
 // the fluxes, not to d_s u_s; the remainder d_s - sum_f w_f (non-zero at walls and by the
 // FP32 rounding of the stored coefficients) is summed exactly.
-struct DF {
-    float hi, lo;   // value hi + lo; lo is not kept normalised inside a computation
-};
-// TwoSum (Knuth): s + e = a + b exactly
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-    s = a + b;
-    const float bb = s - a;
-    e = (a - (s - bb)) + (b - bb);
-}
-// a += x, the rounding error of the leading parts carried into lo
-__device__ __forceinline__ void df_acc(DF& a, DF x) {
-    float s, e;
-    two_sum(a.hi, x.hi, s, e);
-    a.hi = s;
-    a.lo = a.lo + (e + x.lo);
-}
-// a += c exactly up to the rounding of lo (accumulation of FP32 coefficients)
-__device__ __forceinline__ void df_acc_f(DF& a, float c) {
-    float s, e;
-    two_sum(a.hi, c, s, e);
-    a.hi = s;
-    a.lo = a.lo + e;
-}
-__device__ __forceinline__ DF df_diff(DF x, DF y) {
-    float s, e;
-    two_sum(x.hi, -y.hi, s, e);
-    return {s, e + (x.lo - y.lo)};
-}
-// x * c with the product of the leading parts exact (FMA)
-__device__ __forceinline__ DF df_scale(DF x, float c) {
-    const float p = x.hi * c;
-    return {p, fmaf(x.lo, c, fmaf(x.hi, c, -p))};
-}
-__device__ __forceinline__ DF df_mul(DF x, DF y) {
-    const float p = x.hi * y.hi;
-    return {p, fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, fmaf(x.hi, y.hi, -p)))};
-}
-__device__ __forceinline__ DF df_norm(DF x) {
-    const float s = x.hi + x.lo;
-    return {s, x.lo - (s - x.hi)};
-}
-// binary64 -> (hi, lo): hi = sign, exponent and leading 23 fraction bits (truncated), lo =
-// the remaining 29 fraction bits rounded to 24; integer operations only.  |v| < 2^-126 is
-// flushed to 0, |v| >= 2^128 becomes an infinity or NaN in hi; lo is dropped when |v| <
-// 2^-74 (then the pair keeps 24 bits).
-__device__ __forceinline__ DF df_split(double v) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-    const unsigned h32 = (unsigned)(b >> 32);
-    const unsigned sign = h32 & 0x80000000u;
-    const int e = (int)((h32 >> 20) & 0x7FFu);   // biased binary64 exponent
-    const unsigned hib = sign | ((unsigned)(e - 896) << 23) | ((unsigned)(b >> 29) & 0x7FFFFFu);
-    const float lo = __uint2float_rn((unsigned)b & 0x1FFFFFFFu) * __uint_as_float((unsigned)(e - 948) << 23);
-    const bool normal = (e >= 897) & (e <= 1150);
-    const unsigned big = sign | 0x7F800000u | ((b & 0xFFFFFFFFFFFFFull) ? 0x400000u : 0u);
-    const float hi = __uint_as_float(normal ? hib : (e < 897 ? sign : big));
-    return {hi, (normal & (e >= 949)) ? __uint_as_float(__float_as_uint(lo) | sign) : 0.0f};
-}
-// binary32 -> binary64 by bits (exact; subnormal floats are flushed to 0)
-__device__ __forceinline__ double f2d_bits(float f) {
-    const unsigned u = __float_as_uint(f);
-    const unsigned ex = (u >> 23) & 0xFFu;
-    const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
-    if (ex == 0u) return __longlong_as_double((long long)sign);
-    const unsigned long long e64 = ex == 0xFFu ? 0x7FFull : (unsigned long long)(ex - 127u + 1023u);
-    return __longlong_as_double((long long)(sign | (e64 << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29)));
-}
-__device__ __forceinline__ double df_to_double(DF x) {
-    const DF n = df_norm(x);
-    return f2d_bits(n.hi) + f2d_bits(n.lo);
+// One octet of the pair-of-FP32 outer apply: Y for its 8 cells (0 on inner cells), and
+// (p, Ap) over its leaves added to dot.
+template <class TC, class TW>
+__device__ __forceinline__ void octet_apply_df(const Tables& T, const Coefs<TC, TW>& C, const double* __restrict__ P,
+                                               double* __restrict__ Y, int off, int ni, int o, DF& dot) {
+    const int c8 = off + 8 * o, og = c8 >> 3;
+    int leafbits = 0;
+#pragma unroll
+    for (int s = 0; s < 8; ++s) leafbits |= (__ldg(T.child_oct + c8 + s) < 0 ? 1 : 0) << s;
+    if (!leafbits) {
+        // no leaf in the octet: the composite operator has no row here
+        reinterpret_cast<double4*>(Y + c8)[0] = make_double4(0.0, 0.0, 0.0, 0.0);
+        reinterpret_cast<double4*>(Y + c8)[1] = make_double4(0.0, 0.0, 0.0, 0.0);
+        return;
+    }
+    int nb[6];
+    octet_neighbours(T, ni, o, og, nb);
+    DF u[8];
+    float d[8], cm[3][8];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const double2 v = reinterpret_cast<const double2*>(P + c8)[q];
+        u[2 * q] = df_split(v.x);
+        u[2 * q + 1] = df_split(v.y);
+    }
+    ldc8(C.d + c8, d);
+    ldc8(C.cx + c8, cm[0]);
+    ldc8(C.cy + c8, cm[1]);
+    ldc8(C.cz + c8, cm[2]);
+    // mean of the active cells (the T ghost's ubar)
+    DF us{0.0f, 0.0f};
+    int n = 0;
+#pragma unroll
+    for (int s = 0; s < 8; ++s)
+        if (d[s] != 0.0f) { df_acc(us, u[s]); ++n; }
+    const float ic = inv_count<float>(n);
+    const DF ubar{us.hi * ic, us.lo * ic};   // exact scaling for n = 1, 2, 4, 8
+    DF acc[8], dr[8];
+#pragma unroll
+    for (int s = 0; s < 8; ++s) { acc[s] = DF{0.0f, 0.0f}; dr[s] = DF{d[s], 0.0f}; }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int bit = 1 << a;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int s = clear_slot(a, q), t = s | bit;
+            const float c = cm[a][t];
+            const DF fl = df_scale(df_diff(u[s], u[t]), -c);
+            df_acc(acc[s], fl);
+            df_acc(acc[t], DF{-fl.hi, -fl.lo});
+            df_acc_f(dr[s], c);
+            df_acc_f(dr[t], c);
+        }
+        const int v = nb[2 * a];
+        if (v >= 0) {
+            const double* pn = P + off + 8 * v;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int s = clear_slot(a, q);
+                df_acc(acc[s], df_scale(df_diff(u[s], df_split(pn[s | bit])), -cm[a][s]));
+                df_acc_f(dr[s], cm[a][s]);
+            }
+        } else if (v <= -2) {
+            const DF gk = df_diff(df_split(P[-2 - v]), ubar);   // u_K - ubar
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int s = clear_slot(a, q);
+                df_acc(acc[s], df_scale(gk, 0.5f * cm[a][s]));
+                df_acc_f(dr[s], cm[a][s]);
+            }
+        }
+        const int w = nb[2 * a + 1];
+        if (w >= 0) {
+            const double* pn = P + off + 8 * w;
+            const TC* cc = (a == 0 ? C.cx : (a == 1 ? C.cy : C.cz)) + off + 8 * w;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int s = clear_slot(a, q) | bit;
+                const float c = (float)tov(__ldg(cc + clear_slot(a, q)));
+                df_acc(acc[s], df_scale(df_diff(u[s], df_split(pn[clear_slot(a, q)])), -c));
+                df_acc_f(dr[s], c);
+            }
+        } else if (w <= -2) {
+            const DF gk = df_diff(df_split(P[-2 - w]), ubar);
+            const int t = __ldg(T.trec + og);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int s = clear_slot(a, q) | bit;
+                const float c = (float)tov(__ldg(C.tw + ((2 * a + 1) * 4 + q) * T.nt + t));
+                df_acc(acc[s], df_scale(gk, 0.5f * c));
+                df_acc_f(dr[s], c);
+            }
+        }
+    }
+    double y[8];
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+        const bool leaf = (leafbits >> s) & 1;
+        DF au = acc[s];
+        df_acc(au, df_mul(df_norm(dr[s]), u[s]));
+        au = df_norm(au);
+        y[s] = leaf ? df_to_double(au) : 0.0;
+        if (leaf) df_acc(dot, df_mul(u[s], au));
+    }
+    reinterpret_cast<double4*>(Y + c8)[0] = make_double4(y[0], y[1], y[2], y[3]);
+    reinterpret_cast<double4*>(Y + c8)[1] = make_double4(y[4], y[5], y[6], y[7]);
 }
 
 template <class TC, class TW>
@@ -971,109 +1008,7 @@ __global__ void __launch_bounds__(OBLK) k_oapply_df(OMultiLevel ML, Tables T, Co
     for (int vb = blockIdx.x; vb < nvb; vb += gridDim.x) {
         while (l + 1 < ML.n && vb >= ML.boff[l + 1]) ++l;
         const int o = (vb - ML.boff[l]) * OBLK + threadIdx.x;
-        if (o >= ML.noct[l]) continue;
-        const int off = ML.off[l], ni = ML.ni[l];
-        const int c8 = off + 8 * o, og = c8 >> 3;
-        int leafbits = 0;
-#pragma unroll
-        for (int s = 0; s < 8; ++s) leafbits |= (__ldg(T.child_oct + c8 + s) < 0 ? 1 : 0) << s;
-        if (!leafbits) {
-            // no leaf in the octet: the composite operator has no row here
-            reinterpret_cast<double4*>(Y + c8)[0] = make_double4(0.0, 0.0, 0.0, 0.0);
-            reinterpret_cast<double4*>(Y + c8)[1] = make_double4(0.0, 0.0, 0.0, 0.0);
-            continue;
-        }
-        int nb[6];
-        octet_neighbours(T, ni, o, og, nb);
-        DF u[8];
-        float d[8], cm[3][8];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const double2 v = reinterpret_cast<const double2*>(P + c8)[q];
-            u[2 * q] = df_split(v.x);
-            u[2 * q + 1] = df_split(v.y);
-        }
-        ldc8(C.d + c8, d);
-        ldc8(C.cx + c8, cm[0]);
-        ldc8(C.cy + c8, cm[1]);
-        ldc8(C.cz + c8, cm[2]);
-        // mean of the active cells (the T ghost's ubar)
-        DF us{0.0f, 0.0f};
-        int n = 0;
-#pragma unroll
-        for (int s = 0; s < 8; ++s)
-            if (d[s] != 0.0f) { df_acc(us, u[s]); ++n; }
-        const float ic = inv_count<float>(n);
-        const DF ubar{us.hi * ic, us.lo * ic};   // exact scaling for n = 1, 2, 4, 8
-        DF acc[8], dr[8];
-#pragma unroll
-        for (int s = 0; s < 8; ++s) { acc[s] = DF{0.0f, 0.0f}; dr[s] = DF{d[s], 0.0f}; }
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const int bit = 1 << a;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int s = clear_slot(a, q), t = s | bit;
-                const float c = cm[a][t];
-                const DF fl = df_scale(df_diff(u[s], u[t]), -c);
-                df_acc(acc[s], fl);
-                df_acc(acc[t], DF{-fl.hi, -fl.lo});
-                df_acc_f(dr[s], c);
-                df_acc_f(dr[t], c);
-            }
-            const int v = nb[2 * a];
-            if (v >= 0) {
-                const double* pn = P + off + 8 * v;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int s = clear_slot(a, q);
-                    df_acc(acc[s], df_scale(df_diff(u[s], df_split(pn[s | bit])), -cm[a][s]));
-                    df_acc_f(dr[s], cm[a][s]);
-                }
-            } else if (v <= -2) {
-                const DF gk = df_diff(df_split(P[-2 - v]), ubar);   // u_K - ubar
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int s = clear_slot(a, q);
-                    df_acc(acc[s], df_scale(gk, 0.5f * cm[a][s]));
-                    df_acc_f(dr[s], cm[a][s]);
-                }
-            }
-            const int w = nb[2 * a + 1];
-            if (w >= 0) {
-                const double* pn = P + off + 8 * w;
-                const TC* cc = (a == 0 ? C.cx : (a == 1 ? C.cy : C.cz)) + off + 8 * w;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int s = clear_slot(a, q) | bit;
-                    const float c = (float)tov(__ldg(cc + clear_slot(a, q)));
-                    df_acc(acc[s], df_scale(df_diff(u[s], df_split(pn[clear_slot(a, q)])), -c));
-                    df_acc_f(dr[s], c);
-                }
-            } else if (w <= -2) {
-                const DF gk = df_diff(df_split(P[-2 - w]), ubar);
-                const int t = __ldg(T.trec + og);
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int s = clear_slot(a, q) | bit;
-                    const float c = (float)tov(__ldg(C.tw + ((2 * a + 1) * 4 + q) * T.nt + t));
-                    df_acc(acc[s], df_scale(gk, 0.5f * c));
-                    df_acc_f(dr[s], c);
-                }
-            }
-        }
-        double y[8];
-#pragma unroll
-        for (int s = 0; s < 8; ++s) {
-            const bool leaf = (leafbits >> s) & 1;
-            DF au = acc[s];
-            df_acc(au, df_mul(df_norm(dr[s]), u[s]));
-            au = df_norm(au);
-            y[s] = leaf ? df_to_double(au) : 0.0;
-            if (leaf) df_acc(dot, df_mul(u[s], au));
-        }
-        reinterpret_cast<double4*>(Y + c8)[0] = make_double4(y[0], y[1], y[2], y[3]);
-        reinterpret_cast<double4*>(Y + c8)[1] = make_double4(y[4], y[5], y[6], y[7]);
+        if (o < ML.noct[l]) octet_apply_df<TC, TW>(T, C, P, Y, ML.off[l], ML.ni[l], o, dot);
     }
     if (R.op != OP_NONE) red_finish(R, blockIdx.x, df_to_double(dot), 0.0, sh);
 }
