@@ -53,18 +53,19 @@ def _kernel_hash():
     return h.hexdigest()[:16]
 
 
-def _profiled_traffic():
-    """DRAM bytes per launch of the probed sweep from the committed ncu summary, if it
-    was taken on the current kernel sources."""
-    p = os.path.join(ROOT, "profiles", "sweep_c2_level0_octet.txt")
+def _profiled_traffic(name, cells):
+    """DRAM bytes (read + write) of one launch of a probed kernel on `cells` cells, from the
+    committed ncu summary profiles/<name>.txt (per-cell bytes of the captured launch) when
+    that summary was taken on the current kernel sources; None otherwise."""
+    p = os.path.join(ROOT, "profiles", name + ".txt")
     try:
         kv = {}
         for line in open(p):
-            if ":" in line:
+            if ":" in line and not line.startswith("#"):
                 k, v = line.split(":", 1)
                 kv[k.strip()] = v.strip()
         if kv.get("kernel_hash") == _kernel_hash():
-            return float(kv["dram_bytes_per_launch"])
+            return round(float(kv["dram_bytes_per_cell"]) * cells)
     except Exception:
         pass
     return None
@@ -348,7 +349,10 @@ def _large(dev, stream, flush, args, peak):
             "roofline": {"bound": "hbm", "kernel": "red-black colour sweep (%s form) on level %d" % (form, D),
                          "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "bytes_per_cell": SWEEP_BYTES_PER_CELL,
-                         "cells_per_launch": ce.value, "launches": nl.value, "avg_launch_us": round(sweep_us, 2)},
+                         "cells_per_launch": ce.value, "launches": nl.value, "avg_launch_us": round(sweep_us, 2),
+                         "traffic": _profiled_traffic("sweep_c5_level%d_%s" % (D, form), ce.value),
+                         "traffic_note": "dram bytes per cell of an ncu capture at 64^3 root (same field, "
+                                         "effective 512^3) times the cells of one launch"},
             "adjoint": adj}
 
 
@@ -572,8 +576,8 @@ def run_ours(args):
     peak, peak_kind = _peaks()
     sweep_us = sw_ms * 1e3 / max(sw_n, 1)
     achieved = SWEEP_BYTES_PER_CELL * sw_cells / (sweep_us / 1e6) / 1e9
-    traffic = _profiled_traffic()
     fwd = tuning.get(str(big), {}).get("form", "octet")
+    traffic = _profiled_traffic("sweep_c2_level%d_%s" % (big, fwd), sw_cells)
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
