@@ -325,6 +325,8 @@ void choose_tail(ocg_hier* h, int which, size_t vbytes) {
         sb += (int)H.L(m).ncell;
     }
     A.ncell = sb;
+    A.up_off = (int)H.L(top + 1).off;
+    A.up_ni = H.L(top + 1).ni;
     // expand the sub-cycle (Alg. 4 over the tail levels) into a flat pass schedule
     std::vector<int> sch;
     const ocg_mg_params& P = h->prm;

@@ -35,6 +35,14 @@ __device__ __forceinline__ void ld8(const double* __restrict__ p, double (&r)[8]
         r[2 * q + 1] = a.y;
     }
 }
+__device__ __forceinline__ void st8(float* __restrict__ p, const float (&r)[8]) {
+    reinterpret_cast<float4*>(p)[0] = make_float4(r[0], r[1], r[2], r[3]);
+    reinterpret_cast<float4*>(p)[1] = make_float4(r[4], r[5], r[6], r[7]);
+}
+__device__ __forceinline__ void st8(double* __restrict__ p, const double (&r)[8]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) reinterpret_cast<double2*>(p)[q] = make_double2(r[2 * q], r[2 * q + 1]);
+}
 // read-only coefficient loads, converted to the arithmetic type
 __device__ __forceinline__ void ldc8(const float* __restrict__ p, float (&r)[8]) {
     const float4 a = __ldg(reinterpret_cast<const float4*>(p));
@@ -1179,7 +1187,10 @@ struct TailArgs {
     const int* sched;         // passes of the sub-cycle: 8 * level index + pass kind
     int nsched;
     int fas, prolong;
+    int up_off, up_ni;        // the uniform level above the tail (prolongation target)
 };
+
+constexpr int TAIL_SCHED_SH = 256;   // schedules up to this length are kept in shared memory
 
 template <class TV>
 struct TailMem {
@@ -1340,24 +1351,36 @@ __device__ __forceinline__ void tail_cycle(const TailArgs& A, int fas, int prolo
     TV* base = reinterpret_cast<TV*>(smem);
     M.u = base; M.b = base + N; M.d = base + 2 * N;
     M.cm[0] = base + 3 * N; M.cm[1] = base + 4 * N; M.cm[2] = base + 5 * N;
-    // global cell off + 8 o + s  <->  shared sbase + s * no + o
+    __shared__ int ssched[TAIL_SCHED_SH];
+    const bool sch_sh = A.nsched <= TAIL_SCHED_SH;
+    if (sch_sh)
+        for (int q = threadIdx.x; q < A.nsched; q += blockDim.x) ssched[q] = A.sched[q];
+    // global cell off + 8 o + s  <->  shared sbase + s * no + o; one octet per thread, so
+    // that its vector loads of all six arrays are in flight together
     for (int li = 0; li < A.nlev; ++li) {
         const TailLevel& L = A.L[li];
         const int no = tail_noct(L);
-        for (int c = threadIdx.x; c < 8 * no; c += blockDim.x) {
-            const int g = L.off + c, q = L.sbase + (c & 7) * no + (c >> 3);
-            M.u[q] = U[g];
-            M.b[q] = B[g];
-            M.d[q] = TV(tov(C.d[g]));
-            M.cm[0][q] = TV(tov(C.cx[g]));
-            M.cm[1][q] = TV(tov(C.cy[g]));
-            M.cm[2][q] = TV(tov(C.cz[g]));
+        for (int o = threadIdx.x; o < no; o += blockDim.x) {
+            const int g8 = L.off + 8 * o, q0 = L.sbase + o;
+            TV u[8], b[8], d[8], cx[8], cy[8], cz[8];
+            ld8(U + g8, u);
+            ld8(B + g8, b);
+            ldc8(C.d + g8, d);
+            ldc8(C.cx + g8, cx);
+            ldc8(C.cy + g8, cy);
+            ldc8(C.cz + g8, cz);
+#pragma unroll
+            for (int sl = 0; sl < 8; ++sl) {
+                const int q = q0 + sl * no;
+                M.u[q] = u[sl]; M.b[q] = b[sl]; M.d[q] = d[sl];
+                M.cm[0][q] = cx[sl]; M.cm[1][q] = cy[sl]; M.cm[2][q] = cz[sl];
+            }
         }
     }
     __syncthreads();
     if (fas) tail_pass<TV>(M, A, 0, TP_FIXB, TV(0));
     for (int q = 0; q < A.nsched; ++q) {
-        const int e = __ldg(A.sched + q);
+        const int e = sch_sh ? ssched[q] : __ldg(A.sched + q);
         const int li = e >> 3, kind = e & 7;
         if (kind <= TP_SWEEP1 && 8 * tail_noct(A.L[li]) <= (int)blockDim.x)
             tail_sweep_cells<TV>(M, A.L[li], kind);
@@ -1367,19 +1390,26 @@ __device__ __forceinline__ void tail_cycle(const TailArgs& A, int fas, int prolo
     for (int li = 0; li < A.nlev; ++li) {
         const TailLevel& L = A.L[li];
         const int no = tail_noct(L);
-        for (int c = threadIdx.x; c < 8 * no; c += blockDim.x) {
-            const int q = L.sbase + (c & 7) * no + (c >> 3);
-            U[L.off + c] = M.u[q];
-            B[L.off + c] = M.b[q];
+        for (int o = threadIdx.x; o < no; o += blockDim.x) {
+            TV u[8], b[8];
+#pragma unroll
+            for (int sl = 0; sl < 8; ++sl) { u[sl] = M.u[L.sbase + sl * no + o]; b[sl] = M.b[L.sbase + sl * no + o]; }
+            st8(U + L.off + 8 * o, u);
+            st8(B + L.off + 8 * o, b);
         }
     }
     if (prolong) {
-        // onto the level above the tail: children of the top tail level's cells
+        // onto the level above the tail, one child octet per thread: child octet (I, J, K)
+        // of that uniform level has the parent cell (I, J, K) of the top tail level
         const TailLevel& L = A.L[0];
-        const int no = tail_noct(L);
-        for (int c = threadIdx.x; c < 8 * no; c += blockDim.x) {
-            const int co = T.child_oct[L.off + c];
-            if (co >= 0) octet_prolong<TV>(C.d, U, co, M.u[L.sbase + (c & 7) * no + (c >> 3)]);
+        const int no = tail_noct(L), nu = A.up_ni;
+        const int nco = nu * nu * nu;
+        for (int co = threadIdx.x; co < nco; co += blockDim.x) {
+            int I, J, K;
+            octet_coords(co, nu, I, J, K);
+            const int po = (I >> 1) + L.ni * ((J >> 1) + L.ni * (K >> 1));
+            const int sl = (I & 1) | ((J & 1) << 1) | ((K & 1) << 2);
+            octet_prolong<TV>(C.d, U, A.up_off / 8 + co, M.u[L.sbase + sl * no + po]);
         }
     }
 }
