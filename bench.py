@@ -177,12 +177,16 @@ def _hier_bf16(p, tree, dev):
     return S.Hierarchy(tree, torch.from_numpy(beta).to(dev), p.bc, S.mg_params(coef="f32", bf16_coarse=True))
 
 
-def _w_cycle(g, beta, p, b, dev, stream, flush, steps, bf16=False):
+HYBRID_MIN_CELLS = 1 << 20
+
+
+def _w_cycle(g, beta, p, b, dev, stream, flush, steps, bf16=False, mu_min_cells=0):
     """The same solve preconditioned by W-cycles (mu = 2; the paper's choice for cut-cell
-    problems) instead of V-cycles: iterations and Mcells/s."""
+    problems) instead of V-cycles: iterations and Mcells/s.  mu_min_cells > 0: mu = 2 only
+    into levels with at least that many cells (V below)."""
     import torch
     from paper_2604_18886_b300 import solver as S
-    hw = S.Hierarchy(g, beta, p.bc, S.mg_params(mu=2, coef="f32", bf16_coarse=bf16))
+    hw = S.Hierarchy(g, beta, p.bc, S.mg_params(mu=2, coef="f32", bf16_coarse=bf16, mu_min_cells=mu_min_cells))
     x = torch.empty_like(b)
     hw.solve(b, x, tol=1e-6, precision="mixed", stream=stream)
     t, its = [], set()
@@ -199,7 +203,9 @@ def _w_cycle(g, beta, p, b, dev, stream, flush, steps, bf16=False):
     ms = statistics.mean(t)
     del hw
     return {"value": round(g.n_leaves / (ms / 1e3) / 1e6, 3), "unit": UNIT, "ms_per_step": round(ms, 3),
-            "iterations": sorted(its), "true_rel_res": st.true_rel_res, "cycle": "W (mu=2), nu=2/2"}
+            "iterations": sorted(its), "true_rel_res": st.true_rel_res,
+            "cycle": ("W (mu=2) into levels of >= %d cells, V below, nu=2/2" % mu_min_cells) if mu_min_cells
+            else "W (mu=2), nu=2/2"}
 
 
 def _cut_cell(dev, stream, flush, args):
@@ -233,7 +239,8 @@ def _cut_cell(dev, stream, flush, args):
         assert st.converged
     ms = statistics.mean(t)
     wc = _w_cycle(g, beta, p, b, dev, stream, flush, steps, bf16=True)
-    return {"w_cycle": wc,
+    wh = _w_cycle(g, beta, p, b, dev, stream, flush, steps, bf16=True, mu_min_cells=HYBRID_MIN_CELLS)
+    return {"w_cycle": wc, "w_v_hybrid": wh,
             "workload": "cut-cell projection: 64^3 root, sphere r=0.2 and box, band 0.05, 2 levels "
                         "(%d leaves), fluid-fraction beta, Neumann, divergence rhs" % g.n_leaves,
             "precision": "mixed, BF16 coarse coefficients", "value": round(g.n_leaves / (ms / 1e3) / 1e6, 3),
@@ -309,6 +316,7 @@ def _large(dev, stream, flush, args, peak):
         t32.append(e0.elapsed_time(e1))
     ms32 = statistics.mean(t32)
     wc = _w_cycle(g, beta, p, b, dev, stream, flush, steps)
+    wh = _w_cycle(g, beta, p, b, dev, stream, flush, steps, mu_min_cells=HYBRID_MIN_CELLS)
     # finest-level sweep inside an unrolled graph of the same solve
     D = g.D
     L.check(L.lib().ocg_probe_set(h.handle, L.OCG_PROBE_SWEEP, D))
@@ -341,7 +349,7 @@ def _large(dev, stream, flush, args, peak):
             "precision": "mixed (FP32 V-cycle, FP64 PCG)", "value": round(g.n_leaves / (ms / 1e3) / 1e6, 3),
             "unit": UNIT, "ms_per_step": round(ms, 3), "steps": steps, "iterations": sorted(its),
             "true_rel_res": st.true_rel_res, "build_s": round(t_build, 2), "setup_s": round(t_setup, 2),
-            "w_cycle": wc,
+            "w_cycle": wc, "w_v_hybrid": wh,
             "plain_fp32": {"value": round(g.n_leaves / (ms32 / 1e3) / 1e6, 3), "unit": UNIT,
                            "ms_per_step": round(ms32, 3), "iterations": st32.iterations,
                            "true_rel_res": st32.true_rel_res},

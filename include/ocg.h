@@ -149,7 +149,12 @@ typedef struct {
     int32_t sweep_form;    /* OCG_SWEEP_AUTO (time every form per level at set-up and keep
                               the fastest), OCG_SWEEP_OCTET, OCG_SWEEP_CELL, OCG_SWEEP_QUAD or
                               OCG_SWEEP_TILE */
-    int32_t reserved;
+    int32_t mu_min_cells;  /* 0: mu applies on every level (the paper's cycle).  > 0 (an
+                              extension): the recursion into a coarser level is repeated mu
+                              times only when that level has at least this many cells
+                              (leaves and inner, padding excluded), once otherwise — a
+                              W-cycle on the large levels, a V-cycle on the small ones whose
+                              cost on the GPU is launch latency.  Negative: EINVAL. */
 } ocg_mg_params;
 
 #define OCG_SWEEP_AUTO (-1)

@@ -24,12 +24,18 @@ import numpy as np
 
 
 class CycleParams:
-    def __init__(self, mu=1, nu_pre=2, nu_post=2, nu_coarsest=10, beta=2.0):
+    """mu_min_cells (an extension, not in the paper; 0 = the paper's cycle): the recursion
+    into a coarser level is repeated mu times only when that level has at least this many
+    cells (leaves and inner, padding excluded); smaller levels are visited once per visit of
+    their parent, i.e. a W-cycle on the large levels and a V-cycle below."""
+
+    def __init__(self, mu=1, nu_pre=2, nu_post=2, nu_coarsest=10, beta=2.0, mu_min_cells=0):
         self.mu = mu
         self.nu_pre = nu_pre
         self.nu_post = nu_post
         self.nu_coarsest = nu_coarsest
         self.beta = beta
+        self.mu_min_cells = mu_min_cells
 
 
 def level_residual(H, m, u, b):
@@ -87,7 +93,8 @@ def fas_cycle(H, m, u, b, prm, hook=None):
     Rr = L.R @ r
     b[m - 1][I] = prm.beta * Rr[I] + Av[I]                   # restriction
     u[m - 1][I] = ustar                                      # u^{m-1} <- u*
-    for _ in range(prm.mu):
+    mu = prm.mu if C.n >= getattr(prm, "mu_min_cells", 0) else 1
+    for _ in range(mu):
         fas_cycle(H, m - 1, u, b, prm, hook)                 # recursive solve
     corr = np.zeros(C.n)
     corr[I] = u[m - 1][I] - ustar

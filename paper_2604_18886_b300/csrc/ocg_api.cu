@@ -299,6 +299,16 @@ struct ocg_hier {
 
 namespace {
 
+// Recursions into level m per visit of level m + 1: mu, or 1 when mu_min_cells is set and
+// level m has fewer real cells (padding excluded).
+int mu_at(const ocg_hier* h, int m) {
+    const HostTree& H = h->t->H;
+    if (h->prm.mu <= 1 || h->prm.mu_min_cells <= 0) return h->prm.mu;
+    const LevelMeta& L = H.L(m);
+    const int64_t cells = m >= 0 ? L.ncell : (int64_t)L.N * L.N * L.N;
+    return cells >= h->prm.mu_min_cells ? h->prm.mu : 1;
+}
+
 // The tail is the longest run of the coarsest levels m < 0 whose shared-memory image
 // (u, b and four coefficients per cell) fits in 200 KB.
 void choose_tail(ocg_hier* h, int which, size_t vbytes) {
@@ -341,7 +351,8 @@ void choose_tail(ocg_hier* h, int which, size_t vbytes) {
         }
         for (int it = 0; it < P.nu_pre; ++it) { emit(li, 0); emit(li, 1); }
         emit(li, TP_RESTRICT);
-        for (int k = 0; k < P.mu; ++k) rec(li + 1, k == 0);
+        const int mu = mu_at(h, top - (li + 1));
+        for (int k = 0; k < mu; ++k) rec(li + 1, k == 0);
         emit(li, TP_PROLONG);
         for (int it = 0; it < P.nu_post; ++it) { emit(li, 1); emit(li, 0); }
     };
@@ -516,7 +527,8 @@ struct Cycle {
         if (fas) fixb(m);
         for (int it = 0; it < h->prm.nu_pre; ++it) { sweep(m, 0, 0); sweep(m, 1, 0); }
         restrict_(m);
-        for (int k = 0; k < h->prm.mu; ++k) cycle(m - 1, k == 0, k == h->prm.mu - 1);
+        const int mu = mu_at(h, m - 1);
+        for (int k = 0; k < mu; ++k) cycle(m - 1, k == 0, k == mu - 1);
         const int np = h->prm.nu_post;
         for (int it = 0; it < np; ++it) {
             sweep(m, 1, 0);
@@ -1136,6 +1148,7 @@ int ocg_setup_hierarchy(const ocg_octree* t, const float* beta, const int32_t bc
         if (!t || !beta || !bc || !prm || !out) throw Status(OCG_EINVAL, "null argument");
         *out = nullptr;
         if (prm->mu < 1 || prm->mu > 4 || prm->nu_pre < 0 || prm->nu_post < 0 || prm->nu_coarsest < 0 ||
+            prm->mu_min_cells < 0 ||
             !(prm->alpha > 0) || !std::isfinite(prm->beta_restrict))
             throw Status(OCG_EINVAL, "invalid multigrid parameters");
         if (prm->coef_dtype != OCG_F64 && prm->coef_dtype != OCG_F32) throw Status(OCG_EINVAL, "coef_dtype");

@@ -34,8 +34,8 @@ torch = pytest.importorskip("torch")
 _CACHE = {}
 
 
-def build(p, coef="f64", mu=1, bf16=False, sweep="auto"):
-    key = (p.name, tuple(p.bc), coef, mu, bf16, sweep)
+def build(p, coef="f64", mu=1, bf16=False, sweep="auto", mu_min=0):
+    key = (p.name, tuple(p.bc), coef, mu, bf16, sweep, mu_min)
     if key in _CACHE:
         return _CACHE[key]
     t = O.Octree(p.desc)
@@ -43,7 +43,8 @@ def build(p, coef="f64", mu=1, bf16=False, sweep="auto"):
     beta = P.face_beta(p, f)
     H = OP.Hierarchy(t, beta, p.bc)
     g = S.Octree(p.desc)
-    gh = S.Hierarchy(g, beta, p.bc, S.mg_params(mu=mu, coef=coef, bf16_coarse=bf16, sweep=sweep))
+    gh = S.Hierarchy(g, beta, p.bc, S.mg_params(mu=mu, coef=coef, bf16_coarse=bf16, sweep=sweep,
+                                               mu_min_cells=mu_min))
     _CACHE[key] = (t, H, g, gh, f, beta)
     return _CACHE[key]
 
@@ -398,3 +399,17 @@ def test_wcycle_with_bf16_coarse_coefficients_converges(n0):
         assert st.converged and st.true_rel_res <= 1.5e-6, (bf, st.iterations, st.rel_res)
         its[bf] = st.iterations
     assert its[True] <= its[False] + 1, its
+
+
+@pytest.mark.parametrize("name", ["c2_16", "c3_16_d2", "band_12_d2"])
+def test_hybrid_w_v_cycle_matches_oracle(name):
+    # mu = 2 into the levels with at least 4096 cells, mu = 1 below (host recursion and the
+    # shared-memory tail's schedule follow the same rule as the oracle)
+    t, H, g, gh, f, beta = build(CASES[name](), "f64", mu=2, mu_min=4096)
+    prm = mg.CycleParams(mu=2, mu_min_cells=4096)
+    r = P.random_vector(t.n_leaves, 42)
+    assert rel(gh.vcycle(cuda(r)).cpu().numpy(), mg.vcycle(H, r, prm)) <= 1e-10
+    b = P.rhs(CASES[name](), t.leaves, f, beta)
+    xo, ko, ho = pcg.pcg(H, b, tol=1e-8, prm=prm)
+    x, st = gh.solve(cuda(b), tol=1e-8, precision="fp64")
+    assert st.converged and abs(st.iterations - ko) <= 1

@@ -164,3 +164,26 @@ def test_grid_independent_iterations_and_reduction():
         red = (hist[0] / hist[-1]) ** (1.0 / k)
         assert red > 10
     assert abs(its[0] - its[1]) <= 1 and max(its) <= 8
+
+
+def test_mu_min_cells_runs_w_above_and_v_below():
+    """The minimum level size of the mu-recursion (an extension of Alg. 4): 0 reproduces
+    the W-cycle bit for bit, a threshold above every level the V-cycle bit for bit, and a
+    threshold between the level sizes a cycle that differs from both but converges no
+    slower than V as a preconditioner."""
+    p = P.c2(16)
+    t = O.Octree(p.desc)
+    H = OP.Hierarchy(t, P.face_beta(p, t.faces()), p.bc)
+    r = P.random_vector(t.n_leaves, 41)
+    z_w = mg.vcycle(H, r, mg.CycleParams(mu=2))
+    z_v = mg.vcycle(H, r, mg.CycleParams(mu=1))
+    assert np.array_equal(mg.vcycle(H, r, mg.CycleParams(mu=2, mu_min_cells=0)), z_w)
+    assert np.array_equal(mg.vcycle(H, r, mg.CycleParams(mu=2, mu_min_cells=10 ** 9)), z_v)
+    sizes = sorted(H.levels[m].n for m in H.levels)
+    mid = sizes[len(sizes) // 2]
+    z_m = mg.vcycle(H, r, mg.CycleParams(mu=2, mu_min_cells=mid))
+    assert not np.array_equal(z_m, z_w) and not np.array_equal(z_m, z_v)
+    b = P.rhs(p, t.leaves, t.faces(), P.face_beta(p, t.faces()))
+    _, kv, _ = pcg.pcg(H, b, tol=1e-8, prm=mg.CycleParams(mu=1))
+    _, km, _ = pcg.pcg(H, b, tol=1e-8, prm=mg.CycleParams(mu=2, mu_min_cells=mid))
+    assert km <= kv
