@@ -345,6 +345,19 @@ def _large(dev, stream, flush, args, peak):
     adj = {"ms": round(e0.elapsed_time(e1), 3), "iterations": sa.iterations, "converged": bool(sa.converged),
            "rel_res": sa.rel_res,
            "what": "A^T lambda = p - p_t by BiCGStab (mixed, tol 1e-6) + face gradient"}
+    # the same adjoint preconditioned by the hybrid cycle
+    hh = S.Hierarchy(g, beta, p.bc, S.mg_params(mu=2, coef="f32", mu_min_cells=HYBRID_MIN_CELLS))
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lam, sh_ = hh.solve(gp, tol=1e-6, precision="mixed", stream=stream, transpose=True, max_iter=200,
+                        raise_on_notconv=False)
+    hh.face_grad(x, lam, stream=stream)
+    e1.record(stream)
+    e1.synchronize()
+    adj["hybrid_cycle"] = {"ms": round(e0.elapsed_time(e1), 3), "iterations": sh_.iterations,
+                           "converged": bool(sh_.converged)}
+    del hh
     return {"workload": LARGE_WORKLOAD, "leaves": g.n_leaves, "faces": g.n_faces, "cells_all_levels": g.n_cells,
             "precision": "mixed (FP32 V-cycle, FP64 PCG)", "value": round(g.n_leaves / (ms / 1e3) / 1e6, 3),
             "unit": UNIT, "ms_per_step": round(ms, 3), "steps": steps, "iterations": sorted(its),
