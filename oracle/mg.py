@@ -156,3 +156,96 @@ def plain_vcycle(H, r_leaf, prm=None):
     z = np.zeros(len(r_leaf))
     z[rk] = u[H.D][idx]
     return z
+
+
+# ----------------------------------------------------------------------------------
+# Transposed cycle (for the adjoint system; no counterpart in the paper).  The cycle from
+# zero is a linear map M: r -> z.  Its transpose M^T applies the transposes of the cycle's
+# steps in reverse order to adjoint states (ubar[m], bbar[m]).  Preconditioning A^T by
+# M^T gives A^T M^T = (M A)^T, which has the spectrum of A M, so a Krylov method on the
+# adjoint system converges as the forward one does.
+
+def _avg_matrix(H, m):
+    """(I, G): rows I of level m-1 with children and G (len(I) x n_m) with
+    Avg(u^m)[I] = G @ u^m (mean over active children, 0 rows where none is active)."""
+    import scipy.sparse as sp
+    C, F = H.levels[m - 1], H.levels[m]
+    I = np.nonzero(C.children[:, 0] >= 0)[0]
+    ch = C.children[I]
+    act = F.active[ch]
+    n = act.sum(axis=1)
+    rows = np.repeat(np.arange(len(I)), 8)
+    vals = np.where(act, 1.0 / np.maximum(n, 1)[:, None], 0.0).ravel()
+    G = sp.csr_matrix((vals, (rows, ch.ravel())), shape=(len(I), F.n))
+    return I, G
+
+
+def colour_sweep_T(H, m, ub, bb, colour):
+    """Transpose of colour_sweep: u_C += (b - A u - B u^{m-1})_C / c_C."""
+    L = H.levels[m]
+    sel = (L.colour == colour) & L.active
+    v = np.zeros(L.n)
+    v[sel] = ub[m][sel] / L.c[sel]
+    bb[m] += v
+    ub[m] -= L.A.T @ v
+    if m > H.mc and L.B is not None and L.B.nnz:
+        ub[m - 1] -= L.B.T @ v
+
+
+def smooth_T(H, m, ub, bb, iters, first_colour):
+    """Transpose of smooth(iters, first_colour): the sweeps in reverse order."""
+    for _ in range(iters):
+        colour_sweep_T(H, m, ub, bb, 1 - first_colour)
+        colour_sweep_T(H, m, ub, bb, first_colour)
+
+
+def fas_cycle_T(H, m, ub, bb, prm):
+    """Transpose of fas_cycle at level m on the adjoint state (ub, bb), in place."""
+    if m == H.mc:
+        half = prm.nu_coarsest // 2
+        smooth_T(H, m, ub, bb, prm.nu_coarsest - half, 1)
+        smooth_T(H, m, ub, bb, half, 0)
+        return
+    L, C = H.levels[m], H.levels[m - 1]
+    I, G = _avg_matrix(H, m)
+    smooth_T(H, m, ub, bb, prm.nu_post, 1)                   # post-smoothing
+    corr_b = L.P.T @ np.where(L.active, ub[m], 0.0)          # prolongation u^m += P corr
+    ustar_b = np.zeros(len(I))
+    ub[m - 1][I] += corr_b[I]                                # corr = u^{m-1}[I] - u*
+    ustar_b -= corr_b[I]
+    mu = prm.mu if C.n >= getattr(prm, "mu_min_cells", 0) else 1
+    for _ in range(mu):
+        fas_cycle_T(H, m - 1, ub, bb, prm)                   # recursive solves
+    ustar_b += ub[m - 1][I]                                  # u^{m-1}[I] <- u*
+    ub[m - 1][I] = 0.0
+    g = np.zeros(C.n)                                        # b^{m-1}[I] <- beta R r + A v
+    g[I] = bb[m - 1][I]
+    bb[m - 1][I] = 0.0
+    r_b = prm.beta * (L.R.T @ g)
+    v_b = C.A.T @ g                                          # v = u^{m-1}, v[I] = u*
+    ustar_b += v_b[I]
+    v_b[I] = 0.0
+    ub[m - 1] += v_b
+    ub[m] += G.T @ ustar_b                                   # u* = Avg(u^m)
+    r_b = np.where(L.active, r_b, 0.0)                       # r = b - A u - B u^{m-1}
+    bb[m] += r_b
+    ub[m] -= L.A.T @ r_b
+    if L.B is not None and L.B.nnz:
+        ub[m - 1] -= L.B.T @ r_b
+    smooth_T(H, m, ub, bb, prm.nu_pre, 0)                    # pre-smoothing
+
+
+def vcycle_T(H, z_leaf, prm=None):
+    """M^T z: the transpose of vcycle (one mu-cycle from zero)."""
+    prm = prm or CycleParams()
+    ub = {m: np.zeros(H.levels[m].n) for m in H.levels}
+    bb = {m: np.zeros(H.levels[m].n) for m in H.levels}
+    for m in range(0, H.D + 1):
+        idx, rk = _leaf_slots(H, m)
+        ub[m][idx] = z_leaf[rk]
+    fas_cycle_T(H, H.D, ub, bb, prm)
+    r = np.zeros(len(z_leaf))
+    for m in range(0, H.D + 1):
+        idx, rk = _leaf_slots(H, m)
+        r[rk] = bb[m][idx]
+    return r

@@ -63,7 +63,7 @@ def direct_solve(H, b, transpose=False):
     return np.linalg.solve(A, b)
 
 
-def bicgstab(H, b, tol=1e-6, max_iter=200, prm=None, transpose=False):
+def bicgstab(H, b, tol=1e-6, max_iter=200, prm=None, transpose=False, precond=None):
     """Right-preconditioned BiCGStab (H. A. van der Vorst, SIAM J. Sci. Stat. Comput. 13,
     1992) with one mu-cycle as the preconditioner M; the solver of the adjoint system
     A^T lambda = g.  Alg. 1 with the same cycle stagnates there (M approximates A^{-1},
@@ -81,7 +81,12 @@ def bicgstab(H, b, tol=1e-6, max_iter=200, prm=None, transpose=False):
     hist = [1.0]
     if bn == 0.0:
         return x, 0, hist
-    M = lambda v: mg.vcycle(H, v, prm)
+    # precond: "forward" (the mu-cycle M) or "transposed" (M^T, mg.vcycle_T); default:
+    # the forward cycle
+    if precond == "transposed":
+        M = lambda v: mg.vcycle_T(H, v, prm)
+    else:
+        M = lambda v: mg.vcycle(H, v, prm)
     rho = alpha = omega = 1.0
     v = np.zeros_like(b)
     p = np.zeros_like(b)
