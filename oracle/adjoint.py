@@ -67,12 +67,13 @@ def face_grad(H, p, lam):
 
 def solve(H, rhs, transpose=False, tol=1e-13, method="krylov", prm=None):
     """A x = rhs (or A^T x = rhs): oracle Krylov solve to a tight tolerance (PCG, Alg. 1,
-    for A; preconditioned BiCGStab for A^T), or the dense solve; zero mean under the
-    constant null space."""
+    for A; BiCGStab preconditioned by the transposed cycle M^T for A^T, which converges
+    where the forward cycle diverges at high coefficient contrast), or the dense solve;
+    zero mean under the constant null space."""
     if method == "direct":
         x = pcg.direct_solve(H, rhs, transpose=transpose)
     elif transpose:
-        x, _, _ = pcg.bicgstab(H, rhs, tol=tol, max_iter=500, prm=prm, transpose=True)
+        x, _, _ = pcg.bicgstab(H, rhs, tol=tol, max_iter=500, prm=prm, transpose=True, precond="transposed")
     else:
         x, _, _ = pcg.pcg(H, rhs, tol=tol, max_iter=500, prm=prm)
     return _project(x) if H.nullspace else x
