@@ -553,7 +553,7 @@ def run_ours(args):
     times_b, iters_b, _ = _time_solves(hb, b, x, args.steps, "mixed", flush, stream)
     vb16 = tree.n_leaves / (statistics.mean(times_b) / 1e3) / 1e6
     del hb
-    # ---- adjoint: transpose solve (BiCGStab, same cycle) + face gradient
+    # ---- adjoint: transpose solve (BiCGStab, transposed cycle M^T) + face gradient
     ptgt = torch.from_numpy(np.random.default_rng(2).standard_normal(tree.n_leaves)).to(dev)
     xs, _ = hier.solve(b, tol=1e-6, precision="mixed", stream=stream)
     gp = xs - ptgt

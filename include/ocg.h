@@ -196,6 +196,15 @@ int ocg_apply_A(ocg_hier* h, int32_t dtype, const void* x_dev, void* y_dev, int3
  * (F64 needs coef_dtype OCG_F64; F32 needs OCG_F32); device, canonical leaf order. */
 int ocg_vcycle(ocg_hier* h, int32_t dtype, const void* r_dev, void* z_dev, void* stream);
 
+/* r = M^T z, the transpose of the linear map z = M r of ocg_vcycle (no counterpart in the
+ * paper): the transposes of the cycle's steps (Alg. 4: colour sweeps, FAS restriction with
+ * u* = Avg(u), recursion, prolongation) applied in reverse order to adjoint states.  It is
+ * the preconditioner of the adjoint solve: A^T M^T = (M A)^T has the spectrum of A M.
+ * Every level runs as plain launches (no shared-memory coarse tail).  Same dtype rules and
+ * layout as ocg_vcycle; allocates two scratch vectors over all cells on first use.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+int ocg_vcycle_transpose(ocg_hier* h, int32_t dtype, const void* z_dev, void* r_dev, void* stream);
+
 #define OCG_SOLVE_EAGER 1      /* flags: launch kernel by kernel, test convergence on the host */
 #define OCG_SOLVE_TRANSPOSE 2  /* flags: solve A^T x = b (adjoint system) by BiCGStab */
 #define OCG_SOLVE_UNROLLED 4   /* flags (measurement): run exactly max_iter iterations as one
@@ -230,10 +239,10 @@ typedef struct {
  * at exit.  With the null space on, b is shifted to zero mean and x is returned with
  * zero mean over the leaves.
  * With OCG_SOLVE_TRANSPOSE the call solves A^T x = b (adjoint system; no counterpart in
- * the paper) by right-preconditioned BiCGStab (van der Vorst 1992) with the same
- * mu-cycle: Alg. 1 with that cycle stagnates on A^T, which T-junctions make differ from
- * A.  One iteration there applies the cycle and A^T twice; `iterations` counts
- * iterations.  A hierarchy serves one solve at a time (its work vectors are shared).
+ * the paper) by BiCGStab (van der Vorst 1992) right-preconditioned by the transposed cycle
+ * M^T (ocg_vcycle_transpose): Alg. 1 stagnates on A^T, which T-junctions make differ from
+ * A, and preconditioning A^T by M itself diverges at high coefficient contrast.  One
+ * iteration there applies M^T and A^T twice; `iterations` counts iterations.  A hierarchy serves one solve at a time (its work vectors are shared).
  * Errors: ENOTCONV (stats filled), ENAN, EINVAL (also unknown flags), ECUDA. */
 int ocg_pcg_solve(ocg_hier* h, const double* b_dev, double* x_dev, const ocg_solve_params* prm,
                   ocg_solve_stats* stats, void* stream);

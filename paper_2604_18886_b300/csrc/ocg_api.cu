@@ -207,6 +207,7 @@ struct ocg_octree {
     mutable bool adj_ready = false;
     mutable int n_tcoarse = 0, n_tdesc = 0;
     mutable int32_t *t_oct = nullptr, *tcoarse = nullptr, *tdesc = nullptr, *fminus = nullptr, *fplus = nullptr;
+    mutable std::vector<int> tc_lo, tc_hi;   // per tree level m: the range of tcoarse in level m
     void upload_adjoint() const {
         std::lock_guard<std::mutex> lk(adj_mu);
         if (adj_ready) return;
@@ -214,6 +215,13 @@ struct ocg_octree {
         build_adjoint_topology(H, at);
         n_tcoarse = (int)at.tcoarse.size();
         n_tdesc = (int)at.tdesc.size();
+        tc_lo.assign(H.D + 1, 0);
+        tc_hi.assign(H.D + 1, 0);
+        for (int m = 0; m <= H.D; ++m) {
+            const int64_t a = H.L(m).off, b = a + H.L(m).ncell;
+            tc_lo[m] = (int)(std::lower_bound(at.tcoarse.begin(), at.tcoarse.end(), a) - at.tcoarse.begin());
+            tc_hi[m] = (int)(std::lower_bound(at.tcoarse.begin(), at.tcoarse.end(), b) - at.tcoarse.begin());
+        }
         t_oct = dupload(H.t_oct);
         tcoarse = dupload(at.tcoarse);
         tdesc = dupload(at.tdesc);
@@ -273,6 +281,8 @@ struct ocg_hier {
     float* beta = nullptr;        // copy of the face fractions (transposed operator)
     // BiCGStab vectors over the tree cells (adjoint solves), allocated on first use
     double *rhat = nullptr, *s = nullptr, *tv = nullptr, *ph = nullptr, *sh = nullptr;
+    // transposed cycle scratch over all cells, allocated on first use
+    double *Xc = nullptr, *UST = nullptr;
 
     Coefs<double, double> C64() const { return {c64[0], c64[1], c64[2], c64[3], tw64}; }
     Coefs<float, float> C32() const { return {c32[0], c32[1], c32[2], c32[3], tw32}; }
@@ -285,7 +295,7 @@ struct ocg_hier {
                     if (gs.exec) cudaGraphExecDestroy(gs.exec);
                     if (gs.graph) cudaGraphDestroy(gs.graph);
                 }
-        for (double* v : {rhat, s, tv, ph, sh}) dfree(v);
+        for (double* v : {rhat, s, tv, ph, sh, Xc, UST}) dfree(v);
         dfree(beta);
         dfree(tseed);
         if (cap) cudaStreamDestroy(cap);
@@ -538,6 +548,147 @@ struct Cycle {
     }
     void run() { cycle(H().D, false, false); }
 };
+
+OMultiLevel tree_levels(const HostTree& H);
+
+// ------------------------------------------------------------- transposed mu-cycle
+// M^T for the adjoint system (no counterpart in the paper): the transposes of the steps of
+// Cycle, in reverse order, on the adjoint state (ubar in U, bbar in B).  Input: ubar = z on
+// the leaves, 0 elsewhere, bbar = 0; output: bbar on the leaves.  Every level runs as
+// plain launches (no shared-memory tail); X and UST are scratch over all cells.
+template <class TV>
+struct CycleT {
+    ocg_hier* h;
+    TV* U;
+    TV* B;
+    TV* X;
+    TV* UST;
+    Ctx& c;
+
+    const HostTree& H() const { return h->t->H; }
+    template <class F>
+    void with_coefs(int m, F&& f) { Cycle<TV>{h, U, B, c}.with_coefs(m, f); }
+
+    // ubar_K -= B^m^T X for the coarser leaves K (level m-1) of level m's T faces
+    void coarse(int m) {
+        if (m < 1) return;
+        const ocg_octree* t = h->t;
+        const int k0 = t->tc_lo[m - 1], k1 = t->tc_hi[m - 1];
+        if (k1 <= k0) return;
+        with_coefs(m, [&](auto C) {
+            using TC = typename CoefTypes<decltype(C)>::TC;
+            using TW = typename CoefTypes<decltype(C)>::TW;
+            launch(c, -1, m, k1 - k0, [&] {
+                launch_k(kt_coarse<TV, TC, TW>, nblk(k1 - k0), BLK, 0, c.st, t->tables(), C, tree_levels(H()), t->level,
+                         t->tcoarse, k0, k1, U, (const TV*)X);
+            });
+        });
+    }
+    void apply(int m) {
+        with_coefs(m, [&](auto C) {
+            using TC = typename CoefTypes<decltype(C)>::TC;
+            using TW = typename CoefTypes<decltype(C)>::TW;
+            const LevelArgs A = h->t->largs(m);
+            launch(c, -1, m, A.ncell, [&] {
+                launch_k(kt_apply<TV, TC, TW>, nblk(A.ncell / 8, OBLK), OBLK, 0, c.st, A, h->t->tables(), C, U, (const TV*)X);
+            });
+        });
+        coarse(m);
+    }
+    void sweep(int m, int colour) {
+        with_coefs(m, [&](auto C) {
+            using TC = typename CoefTypes<decltype(C)>::TC;
+            using TW = typename CoefTypes<decltype(C)>::TW;
+            const LevelArgs A = h->t->largs(m);
+            launch(c, OCG_PROBE_SWEEP, m, A.ncell, [&] {
+                launch_k(kt_sweep_v<TV, TC, TW>, nblk(A.ncell / 8, OBLK), OBLK, 0, c.st, A, C, (const TV*)U, B, X, colour);
+            });
+        });
+        apply(m);
+        ck_launch("transposed sweep");
+    }
+    void coarsest(int m) {
+        const int nu = h->prm.nu_coarsest, half = nu / 2;
+        with_coefs(m, [&](auto C) {
+            using TC = typename CoefTypes<decltype(C)>::TC;
+            using TW = typename CoefTypes<decltype(C)>::TW;
+            const LevelArgs A = h->t->largs(m);
+            const int nt = (int)std::min<int64_t>(256, (A.ncell / 8 + 31) / 32 * 32);
+            launch(c, -1, m, A.ncell, [&] {
+                launch_k(kt_coarsest<TV, TC, TW>, 1, nt, 0, c.st, A, h->t->tables(), C, U, B, X, nu - half, nu);
+            });
+        });
+        ck_launch("transposed coarsest");
+    }
+    // transposes of the prolongation (before the recursion) and of the FAS restriction
+    // and residual (after it) between levels m and m-1
+    void prolong(int m) {
+        with_coefs(m, [&](auto C) {
+            using TC = typename CoefTypes<decltype(C)>::TC;
+            using TW = typename CoefTypes<decltype(C)>::TW;
+            const LevelArgs A = h->t->largs(m);
+            launch(c, OCG_PROBE_PROLONG, m, A.ncell, [&] {
+                launch_k(kt_prolong<TV, TC, TW>, nblk(A.ncell / 8, OBLK), OBLK, 0, c.st, A, h->t->tables(), C, U, UST);
+            });
+        });
+        ck_launch("transposed prolong");
+    }
+    void restrict_(int m) {
+        const TV scale = TV(h->prm.beta_restrict / h->prm.alpha);
+        const LevelArgs Ac = h->t->largs(m - 1);
+        launch(c, OCG_PROBE_RESTRICT, m - 1, Ac.ncell, [&] {
+            launch_k(kt_restrict_g<TV>, nblk(Ac.ncell), BLK, 0, c.st, Ac, h->t->tables(), U, B, UST, X);
+        });
+        with_coefs(m - 1, [&](auto C) {
+            using TC = typename CoefTypes<decltype(C)>::TC;
+            using TW = typename CoefTypes<decltype(C)>::TW;
+            launch(c, OCG_PROBE_RESTRICT, m - 1, Ac.ncell, [&] {
+                launch_k(kt_restrict_v<TV, TC, TW>, nblk(Ac.ncell / 8, OBLK), OBLK, 0, c.st, Ac, h->t->tables(), C, U, UST,
+                         (const TV*)X);
+            });
+        });
+        with_coefs(m, [&](auto C) {
+            using TC = typename CoefTypes<decltype(C)>::TC;
+            using TW = typename CoefTypes<decltype(C)>::TW;
+            const LevelArgs A = h->t->largs(m);
+            launch(c, OCG_PROBE_RESTRICT, m, A.ncell, [&] {
+                launch_k(kt_restrict_c<TV, TC, TW>, nblk(A.ncell / 8, OBLK), OBLK, 0, c.st, A, h->t->tables(), C, U, B,
+                         (const TV*)UST, X, scale);
+            });
+        });
+        apply(m);
+        ck_launch("transposed restrict");
+    }
+    void cycle(int m) {
+        if (m == H().mc) { coarsest(m); return; }
+        for (int it = 0; it < h->prm.nu_post; ++it) { sweep(m, 0); sweep(m, 1); }
+        prolong(m);
+        const int mu = mu_at(h, m - 1);
+        for (int k = 0; k < mu; ++k) cycle(m - 1);
+        restrict_(m);
+        for (int it = 0; it < h->prm.nu_pre; ++it) { sweep(m, 1); sweep(m, 0); }
+    }
+    // U, B: the leaf values of Z and zeros over the tree cells, zeros on the coarser levels
+    template <class TZ>
+    void seed(const TZ* Z) {
+        const HostTree& HH = H();
+        const int n = (int)HH.ntree;
+        launch(c, -1, 0, n, [&] { launch_k(kt_seed<TV, TZ>, nblk(n), BLK, 0, c.st, n, h->t->flags, Z, U, B); });
+        const int64_t rest = HH.ncell - HH.ntree;
+        if (rest > 0) {
+            ck(cudaMemsetAsync(U + HH.ntree, 0, rest * sizeof(TV), c.st), "memset");
+            ck(cudaMemsetAsync(B + HH.ntree, 0, rest * sizeof(TV), c.st), "memset");
+        }
+    }
+    void run() { cycle(H().D); }
+};
+
+void ensure_cycle_T(ocg_hier* h) {
+    h->t->upload_adjoint();
+    if (h->Xc) return;
+    h->Xc = dalloc<double>(h->t->H.ncell);
+    h->UST = dalloc<double>(h->t->H.ncell);
+}
 
 // ------------------------------------------------------------------ sweep autotuner
 // For every level the cycle sweeps outside the shared-memory tail, capture 20 colour
@@ -809,10 +960,12 @@ struct BiCG {
         });
         ck_launch("bicg begin");
     }
+    // out = M^T (the value that k_bi_p / k_bi_s left in B)
     void precondition(TO* out) {
-        zero(h->U, H().ntree * sizeof(TV));
-        Cycle<TV>{h, U(), B(), c}.run();
-        launch(c, -1, 0, n(), [&] { launch_k(k_cast<TV, TO>, gb(), BLK, 0, c.st, U(), out, n()); });
+        CycleT<TV> ct{h, U(), B(), (TV*)h->Xc, (TV*)h->UST, c};
+        ct.seed((const TV*)B());
+        ct.run();
+        launch(c, -1, 0, n(), [&] { launch_k(k_cast<TV, TO>, gb(), BLK, 0, c.st, B(), out, n()); });
     }
     void body() {
         TO *r = V(h->r), *p = V(h->p), *v = V(h->Ap), *s = V(h->s), *t = V(h->tv), *ph = V(h->ph), *sh = V(h->sh);
@@ -926,6 +1079,7 @@ void ensure_adjoint(ocg_hier* h) {
 
 void ensure_bicg(ocg_hier* h) {
     ensure_adjoint(h);
+    ensure_cycle_T(h);
     if (h->rhat) return;
     const int64_t n = h->t->H.ntree;
     for (double** v : {&h->rhat, &h->s, &h->tv, &h->ph, &h->sh}) *v = dalloc<double>(n);
@@ -1363,6 +1517,42 @@ int ocg_vcycle(ocg_hier* h, int32_t dtype, const void* r, void* z, void* stream)
                 launch_k(k_gather<TV, TV>, nblk(H.nleaf), BLK, 0, st, U, (TV*)z, t->leaf_cell, (int)H.nleaf);
             });
             ck_launch("vcycle");
+        };
+        if (dtype == OCG_F64) {
+            if (!h->c64[0]) throw Status(OCG_EINVAL, "F64 cycle needs coef_dtype F64");
+            run((double*)nullptr);
+        } else if (dtype == OCG_F32) {
+            if (!h->c32[0]) throw Status(OCG_EINVAL, "F32 cycle needs coef_dtype F32");
+            run((float*)nullptr);
+        } else {
+            throw Status(OCG_EINVAL, "dtype");
+        }
+        g_launches += c.count;
+    });
+}
+
+int ocg_vcycle_transpose(ocg_hier* h, int32_t dtype, const void* z, void* r, void* stream) {
+    return guard([&] {
+        if (!h || !z || !r) throw Status(OCG_EINVAL, "null argument");
+        cudaStream_t st = (cudaStream_t)stream;
+        ensure_cycle_T(h);
+        const ocg_octree* t = h->t;
+        const HostTree& H = t->H;
+        Ctx c{st, &h->probe, 0};
+        auto run = [&](auto* tag) {
+            using TV = std::remove_pointer_t<decltype(tag)>;
+            TV* U = (TV*)h->U;
+            TV* B = (TV*)h->B;
+            ck(cudaMemsetAsync(U, 0, H.ncell * sizeof(TV), st), "memset");
+            ck(cudaMemsetAsync(B, 0, H.ncell * sizeof(TV), st), "memset");
+            launch(c, -1, 0, H.nleaf, [&] {
+                launch_k(k_scatter<TV, TV>, nblk(H.nleaf), BLK, 0, st, (const TV*)z, U, t->leaf_cell, (int)H.nleaf);
+            });
+            CycleT<TV>{h, U, B, (TV*)h->Xc, (TV*)h->UST, c}.run();
+            launch(c, -1, 0, H.nleaf, [&] {
+                launch_k(k_gather<TV, TV>, nblk(H.nleaf), BLK, 0, st, B, (TV*)r, t->leaf_cell, (int)H.nleaf);
+            });
+            ck_launch("vcycle_transpose");
         };
         if (dtype == OCG_F64) {
             if (!h->c64[0]) throw Status(OCG_EINVAL, "F64 cycle needs coef_dtype F64");

@@ -1126,6 +1126,295 @@ __global__ void k_tdesc(Tables T, const int32_t* __restrict__ tdesc, int n, int 
         if (flags[8 * og + s] & 1) Y[8 * og + s] = TO((double)Y[8 * og + s] + acc);
 }
 
+// ------------------------------------------------------------ transposed cycle
+// M^T, the transpose of the mu-cycle (a linear map r -> z from zero), for preconditioning
+// the adjoint system: A^T M^T = (M A)^T has the spectrum of A M.  The transposed steps of
+// Alg. 4 run in reverse order on adjoint states (ubar in U, bbar in B).  The level operator
+// A^m of a fine cell s with T faces (coarser leaf K, octet mean ubar over n active cells)
+// has the row  (d_s + W_s) u_s + c_f/2 u_K - W_s/(2n) sum_active u_j + regular faces,
+// W_s = sum of s's T-face coefficients; so
+//   (A^m^T X)_j = (d_j + W_j) X_j + sum_regular c X_nb - [j active] sum_s W_s X_s / (2n)
+// within the level, and the coarser leaf K receives sum (c_f/2) X_s (B^m^T X).
+
+// Y = A^m^T X for the 8 cells of octet o (see above); X is read, Y returned.
+template <class TV, class TC, class TW>
+__device__ __forceinline__ void octet_AT(const Tables& T, const Coefs<TC, TW>& C, const TV* X, const LevelArgs& A,
+                                         int o, int og, TV (&Y)[8]) {
+    const int c8 = A.off + 8 * o;
+    TV x[8], d[8], cm[3][8], W[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) x[q] = X[c8 + q];
+    ldc8(C.d + c8, d);
+    ldc8(C.cx + c8, cm[0]);
+    ldc8(C.cy + c8, cm[1]);
+    ldc8(C.cz + c8, cm[2]);
+    int nb[6];
+    octet_neighbours(T, A.ni, o, og, nb);
+    int nact = 0;
+#pragma unroll
+    for (int s = 0; s < 8; ++s) { W[s] = TV(0); nact += d[s] != TV(0) ? 1 : 0; }
+    int t = -1;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int bit = 1 << a;
+        if (nb[2 * a] <= -2) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) W[clear_slot(a, q)] += cm[a][clear_slot(a, q)];
+        }
+        if (nb[2 * a + 1] <= -2) {
+            if (t < 0) t = __ldg(T.trec + og);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                W[clear_slot(a, q) | bit] += TV(tov(__ldg(C.tw + ((2 * a + 1) * 4 + q) * T.nt + t)));
+        }
+    }
+    TV tO = TV(0);
+#pragma unroll
+    for (int s = 0; s < 8; ++s) { Y[s] = (d[s] + W[s]) * x[s]; tO += W[s] * x[s]; }
+    tO = tO * TV(0.5) * inv_count<TV>(nact);
+    const int off = A.off;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int bit = 1 << a;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int s = clear_slot(a, q), u = s | bit;
+            const TV c = cm[a][u];
+            Y[s] += c * x[u];
+            Y[u] += c * x[s];
+        }
+        const int v = nb[2 * a];
+        if (v >= 0) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int s = clear_slot(a, q);
+                Y[s] += cm[a][s] * X[off + 8 * v + (s | bit)];
+            }
+        }
+        const int w = nb[2 * a + 1];
+        if (w >= 0) {
+            const TC* cc = a == 0 ? C.cx : (a == 1 ? C.cy : C.cz);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int s = clear_slot(a, q);
+                Y[s | bit] += TV(tov(__ldg(cc + off + 8 * w + s))) * X[off + 8 * w + s];
+            }
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < 8; ++s)
+        if (d[s] != TV(0)) Y[s] -= tO;
+}
+
+// transposed colour sweep, part 1: V = ubar / d on the active cells of the colour (0
+// elsewhere), bbar += V
+template <class TV, class TC, class TW>
+__device__ __forceinline__ void sweep_v_octet(const LevelArgs& A, const Coefs<TC, TW>& C, const TV* U, TV* B, TV* V,
+                                              int colour, int o) {
+    const int c8 = A.off + 8 * o;
+    TV u[8], b[8], d[8], v[8];
+    ld8(U + c8, u);
+    ld8(B + c8, b);
+    ldc8(C.d + c8, d);
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+        v[s] = ((__popc(s) & 1) == colour && d[s] != TV(0)) ? u[s] / d[s] : TV(0);
+        b[s] += v[s];
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) V[c8 + q] = v[q];
+    st8(B + c8, b);
+}
+
+template <class TV, class TC, class TW>
+__global__ void __launch_bounds__(OBLK) kt_sweep_v(LevelArgs A, Coefs<TC, TW> C, const TV* __restrict__ U,
+                                                   TV* __restrict__ B, TV* V, int colour) {
+    pdl_enter();
+    const int o = blockIdx.x * OBLK + threadIdx.x;
+    if (o >= A.ncell / 8) return;
+    sweep_v_octet<TV, TC, TW>(A, C, U, B, V, colour, o);
+}
+
+// ubar -= A^m^T X over the cells of the level (transposed sweep part 2, and the residual
+// part of the transposed restriction)
+template <class TV, class TC, class TW>
+__global__ void __launch_bounds__(OBLK) kt_apply(LevelArgs A, Tables T, Coefs<TC, TW> C, TV* __restrict__ U,
+                                                 const TV* X) {
+    pdl_enter();
+    const int o = blockIdx.x * OBLK + threadIdx.x;
+    if (o >= A.ncell / 8) return;
+    const int c8 = A.off + 8 * o;
+    TV y[8], u[8];
+    octet_AT<TV, TC, TW>(T, C, X, A, o, c8 >> 3, y);
+    ld8(U + c8, u);
+#pragma unroll
+    for (int s = 0; s < 8; ++s) u[s] -= y[s];
+    st8(U + c8, u);
+}
+
+// ubar_K -= sum over the fine T cells s beside K of (c_f / 2) X_s, for the coarser leaves K
+// listed in tcoarse[k0, k1) (those of one level; the fine cells are one level finer)
+template <class TV, class TC, class TW>
+__global__ void kt_coarse(Tables T, Coefs<TC, TW> C, OMultiLevel ML, const int8_t* __restrict__ level,
+                          const int32_t* __restrict__ tcoarse, int k0, int k1, TV* __restrict__ U, const TV* X) {
+    pdl_enter();
+    const int q = k0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= k1) return;
+    const int K = __ldg(tcoarse + q);
+    const int m = level[K];
+    const int off = ML.off[m], sK = K & 7, og = K >> 3, o = (K - off) >> 3;
+    int nb[6];
+    octet_neighbours(T, ML.ni[m], o, og, nb);
+    TV acc = TV(0);
+#pragma unroll
+    for (int dir = 0; dir < 6; ++dir) {
+        const int a = dir >> 1, bit = 1 << a;
+        const bool plus = dir & 1;
+        int Q = -1;
+        if (((sK & bit) != 0) != plus) Q = plus ? K + bit : K - bit;
+        else if (nb[dir] >= 0) Q = off + 8 * nb[dir] + (sK ^ bit);
+        if (Q < 0) continue;
+        const int co = __ldg(T.child_oct + Q);
+        if (co < 0) continue;
+        const TC* cm = a == 0 ? C.cx : (a == 1 ? C.cy : C.cz);
+        const int t = plus ? 0 : __ldg(T.trec + co);
+#pragma unroll
+        for (int qq = 0; qq < 4; ++qq) {
+            const int s = clear_slot(a, qq) | (plus ? 0 : bit);
+            const int i = 8 * co + s;
+            const TV cf = plus ? TV(tov(__ldg(cm + i))) : TV(tov(__ldg(C.tw + ((2 * a + 1) * 4 + qq) * T.nt + t)));
+            acc += TV(0.5) * cf * X[i];
+        }
+    }
+    U[K] -= acc;
+}
+
+// transposed prolongation (u^m += P (u^{m-1} - u*) on active children) and correction:
+// per octet of level m with parent P: corr = sum of ubar over its active cells;
+// ubar_P += corr; UST_P = -corr (the adjoint of u*, completed after the recursion)
+template <class TV, class TC, class TW>
+__global__ void __launch_bounds__(OBLK) kt_prolong(LevelArgs A, Tables T, Coefs<TC, TW> C, TV* __restrict__ U,
+                                                   TV* __restrict__ UST) {
+    pdl_enter();
+    const int o = blockIdx.x * OBLK + threadIdx.x;
+    if (o >= A.ncell / 8) return;
+    const int c8 = A.off + 8 * o;
+    TV u[8], d[8];
+    ld8(U + c8, u);
+    ldc8(C.d + c8, d);
+    TV corr = TV(0);
+#pragma unroll
+    for (int s = 0; s < 8; ++s)
+        if (d[s] != TV(0)) corr += u[s];
+    const int P = __ldg(T.oct_parent + (c8 >> 3));
+    U[P] += corr;
+    UST[P] = -corr;
+}
+
+// transposed FAS restriction, part 1, over the cells of level m-1: for a cell with
+// children, g = bbar (then 0), UST += ubar (then 0: u^{m-1} was overwritten by u*);
+// G = g there and 0 on leaves
+template <class TV>
+__global__ void kt_restrict_g(LevelArgs A, Tables T, TV* __restrict__ U, TV* __restrict__ B, TV* __restrict__ UST,
+                              TV* G) {
+    pdl_enter();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= A.ncell) return;
+    const int c = A.off + i;
+    if (__ldg(T.child_oct + c) >= 0) {
+        G[c] = B[c];
+        B[c] = TV(0);
+        UST[c] += U[c];
+        U[c] = TV(0);
+    } else {
+        G[c] = TV(0);
+    }
+}
+
+// transposed FAS restriction, part 2, over the cells of level m-1: v = A^{m-1}^T G (the
+// rows with children are regular, so no T terms arise); UST += v on cells with children,
+// ubar += v on the others
+template <class TV, class TC, class TW>
+__global__ void __launch_bounds__(OBLK) kt_restrict_v(LevelArgs A, Tables T, Coefs<TC, TW> C, TV* __restrict__ U,
+                                                      TV* __restrict__ UST, const TV* G) {
+    pdl_enter();
+    const int o = blockIdx.x * OBLK + threadIdx.x;
+    if (o >= A.ncell / 8) return;
+    const int c8 = A.off + 8 * o;
+    TV y[8];
+    octet_AT<TV, TC, TW>(T, C, G, A, o, c8 >> 3, y);
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+        if (__ldg(T.child_oct + c8 + s) >= 0) UST[c8 + s] += y[s];
+        else U[c8 + s] += y[s];
+    }
+}
+
+// transposed FAS restriction, part 3, per octet of level m with parent P: on the active
+// cells rbar = (beta/alpha) G_P, bbar += rbar, ubar += UST_P / n (transpose of u* = the
+// mean of the active children).  X holds G on level m-1 and receives rbar on level m
+// (0 on inactive cells) for the residual part.
+template <class TV, class TC, class TW>
+__global__ void __launch_bounds__(OBLK) kt_restrict_c(LevelArgs A, Tables T, Coefs<TC, TW> C, TV* __restrict__ U,
+                                                      TV* __restrict__ B, const TV* __restrict__ UST, TV* X, TV scale) {
+    pdl_enter();
+    const int o = blockIdx.x * OBLK + threadIdx.x;
+    if (o >= A.ncell / 8) return;
+    const int c8 = A.off + 8 * o;
+    const int P = __ldg(T.oct_parent + (c8 >> 3));
+    TV u[8], b[8], d[8], rb[8];
+    ld8(U + c8, u);
+    ld8(B + c8, b);
+    ldc8(C.d + c8, d);
+    int n = 0;
+#pragma unroll
+    for (int s = 0; s < 8; ++s) n += d[s] != TV(0) ? 1 : 0;
+    const TV r = scale * X[P], us = UST[P] * inv_count<TV>(n);
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+        const bool act = d[s] != TV(0);
+        rb[s] = act ? r : TV(0);
+        if (act) { b[s] += r; u[s] += us; }
+    }
+    st8(U + c8, u);
+    st8(B + c8, b);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) X[c8 + q] = rb[q];
+}
+
+// transposed smoothing of the coarsest level in one CTA: 2 nsweep colour sweeps, the first
+// 2 n_a of them in the colour order 0, 1, the rest 1, 0 (the reverse of the forward
+// coarsest smoothing); the level has no coarser leaves
+template <class TV, class TC, class TW>
+__global__ void kt_coarsest(LevelArgs A, Tables T, Coefs<TC, TW> C, TV* U, TV* B, TV* V, int n_a, int nsweep) {
+    pdl_enter();
+    const int noct = A.ncell / 8;
+    for (int k = 0; k < 2 * nsweep; ++k) {
+        const int colour = k < 2 * n_a ? (k & 1) : 1 - (k & 1);
+        for (int o = threadIdx.x; o < noct; o += blockDim.x) sweep_v_octet<TV, TC, TW>(A, C, U, B, V, colour, o);
+        __syncthreads();
+        for (int o = threadIdx.x; o < noct; o += blockDim.x) {
+            const int c8 = A.off + 8 * o;
+            TV y[8];
+            octet_AT<TV, TC, TW>(T, C, V, A, o, c8 >> 3, y);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) U[c8 + q] -= y[q];
+        }
+        __syncthreads();
+    }
+}
+
+// M^T input: U = the leaf values of Z (0 on inner cells), B = 0, over the tree cells
+template <class TV, class TZ>
+__global__ void kt_seed(int n, const uint8_t* __restrict__ flags, const TZ* Z, TV* __restrict__ U, TV* B) {
+    pdl_enter();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const TV z = TV(Z[i]);   // Z may be B itself
+    U[i] = (flags[i] & 1) ? z : TV(0);
+    B[i] = TV(0);
+}
+
 // Coarsest level (Alg. 4, l = 0): one CTA, one thread per octet, nu sweeps (half
 // red->black, half black->red), each a pass separated by __syncthreads; fas completes
 // the FAS right-hand side first; prolong prolongs onto the finer level at the end.

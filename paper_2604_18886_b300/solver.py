@@ -210,10 +210,18 @@ class Hierarchy:
         L.check(L.lib().ocg_vcycle(self._h, dt, L.ptr(r), L.ptr(z), self._stream(stream)))
         return z
 
+    def vcycle_transpose(self, z, stream=None):
+        """r = M^T z, the transpose of vcycle (preconditioner of the adjoint solve)."""
+        import torch
+        r = torch.empty_like(z)
+        dt = L.OCG_F64 if z.dtype == torch.float64 else L.OCG_F32
+        L.check(L.lib().ocg_vcycle_transpose(self._h, dt, L.ptr(z), L.ptr(r), self._stream(stream)))
+        return r
+
     def solve(self, b, x=None, tol=1e-6, max_iter=100, precision="mixed", nullspace=-1,
               stream=None, raise_on_notconv=True, eager=False, transpose=False, unrolled=False):
-        """x with A x = b (PCG, Alg. 1), or A^T x = b with transpose=True (BiCGStab, the
-        adjoint system).  Returns (x, stats)."""
+        """x with A x = b (PCG, Alg. 1), or A^T x = b with transpose=True (the adjoint
+        system: BiCGStab preconditioned by the transposed cycle M^T).  Returns (x, stats)."""
         import torch
         assert b.dtype == torch.float64 and b.is_cuda
         if x is None:

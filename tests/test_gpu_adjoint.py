@@ -3,9 +3,11 @@ gradient, autograd wrapper) against the FP64 oracle, and the gradient against ce
 finite differences at the full two-level workload size.
 
 Tolerances as in test_gpu_parity: FP64 applies 1e-12, FP32 applies 1e-6 relative to the
-vector's max norm; FP64 Krylov iterates 1e-8 (BiCGStab's two-sided recurrences amplify
-rounding-order differences more than CG's).  Finite differences: 1e-4 relative to the
-largest sampled gradient (spec bar).
+vector's max norm; the transposed cycle M^T as the forward cycle (FP64 1e-10, FP32 1e-5);
+FP64 Krylov iterates 1e-8 (BiCGStab's two-sided recurrences amplify rounding-order
+differences more than CG's).  Finite differences: 1e-4 relative to the largest sampled
+gradient.  The adjoint solves are preconditioned by M^T, so the oracle's BiCGStab runs
+with precond="transposed".
 """
 import numpy as np
 import pytest
@@ -40,11 +42,59 @@ def test_transposed_apply_matches_oracle(name):
     assert rel(y32, AT @ x32.astype(np.float64)) <= 1e-6
 
 
-@pytest.mark.parametrize("name", ["c2_16", "c2_16_neumann", "c3_16_d2", "c4_t1"])
+@pytest.mark.parametrize("mu", [1, 2])
+@pytest.mark.parametrize("name", NAMES)
+def test_vcycle_transpose_fp64_matches_oracle(name, mu):
+    from oracle import mg
+    t, H, g, gh, f, beta = build(CASES[name](), "f64", mu=mu)
+    z = P.random_vector(t.n_leaves, 30)
+    r = gh.vcycle_transpose(cuda(z)).cpu().numpy()
+    assert rel(r, mg.vcycle_T(H, z, mg.CycleParams(mu=mu))) <= 1e-10
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_vcycle_transpose_fp32_matches_oracle(name):
+    from oracle import mg
+    t, H, g, gh, f, beta = build(CASES[name](), "f32")
+    z = P.random_vector(t.n_leaves, 31).astype(np.float32)
+    r = gh.vcycle_transpose(cuda(z, torch.float32)).double().cpu().numpy()
+    assert rel(r, mg.vcycle_T(H, z.astype(np.float64))) <= 1e-5
+
+
+@pytest.mark.parametrize("name", ["c3_16_d2", "band_12_d2", "c5_8_d2"])
+def test_vcycle_transpose_hybrid_matches_oracle(name):
+    from oracle import mg
+    t, H, g, gh, f, beta = build(CASES[name](), "f64", mu=2, mu_min=4096)
+    z = P.random_vector(t.n_leaves, 32)
+    r = gh.vcycle_transpose(cuda(z)).cpu().numpy()
+    assert rel(r, mg.vcycle_T(H, z, mg.CycleParams(mu=2, mu_min_cells=4096))) <= 1e-10
+
+
+@pytest.mark.parametrize("bf16", [False, True])
+@pytest.mark.parametrize("name", ["c3_16_d2", "c5_8_d2"])
+def test_vcycle_transpose_is_the_adjoint_of_the_gpu_cycle(name, bf16):
+    # (M^T z, r) = (z, M r) for the library's own M, in FP64 and in FP32 (also with the
+    # BF16 coarse coefficients, where no oracle cycle exists)
+    t, H, g, gh, f, beta = build(CASES[name](), "f64")
+    r = P.random_vector(t.n_leaves, 33)
+    z = P.random_vector(t.n_leaves, 34)
+    lhs = float(np.dot(gh.vcycle_transpose(cuda(z)).cpu().numpy(), r))
+    rhs = float(np.dot(z, gh.vcycle(cuda(r)).cpu().numpy()))
+    assert abs(lhs - rhs) <= 1e-12 * max(abs(lhs), 1e-300) * t.n_leaves ** 0.5
+    t, H, g, gh, f, beta = build(CASES[name](), "f32", bf16=bf16)
+    r32 = cuda(r, torch.float32)
+    z32 = cuda(z, torch.float32)
+    lhs = torch.dot(gh.vcycle_transpose(z32).double(), r32.double()).item()
+    rhs = torch.dot(z32.double(), gh.vcycle(r32).double()).item()
+    scale = gh.vcycle_transpose(z32).double().norm().item() * r32.double().norm().item()
+    assert abs(lhs - rhs) <= 1e-5 * scale
+
+
+@pytest.mark.parametrize("name", ["c2_16", "c2_16_neumann", "c3_16_d2", "c4_t1", "c5_8_d2"])
 def test_bicgstab_fp64_follows_oracle_iterates(name):
     t, H, g, gh, f, beta = build(CASES[name](), "f64")
     rhs = P.random_vector(t.n_leaves, 22)
-    xo, ko, ho = pcg.bicgstab(H, rhs, tol=1e-8, transpose=True)
+    xo, ko, ho = pcg.bicgstab(H, rhs, tol=1e-8, transpose=True, precond="transposed")
     x, st = gh.solve(cuda(rhs), tol=1e-8, precision="fp64", transpose=True)
     assert st.converged and st.iterations == ko
     hist = [st.hist[i] for i in range(st.iterations + 1)]
@@ -55,12 +105,12 @@ def test_bicgstab_fp64_follows_oracle_iterates(name):
 
 
 @pytest.mark.parametrize("precision", ["mixed", "fp32"])
-@pytest.mark.parametrize("name", ["c2_16", "c2_16_neumann", "c3_16_d2", "c4_t1"])
+@pytest.mark.parametrize("name", ["c2_16", "c2_16_neumann", "c3_16_d2", "c4_t1", "c5_8_d2"])
 def test_transpose_solution_within_1e5(name, precision):
     t, H, g, gh, f, beta = build(CASES[name](), "f32")
     rhs = P.random_vector(t.n_leaves, 23)
     ref = ADJ.solve(H, rhs, transpose=True, tol=1e-12)
-    xo, ko, _ = pcg.bicgstab(H, rhs, tol=1e-6, transpose=True)
+    xo, ko, _ = pcg.bicgstab(H, rhs, tol=1e-6, transpose=True, precond="transposed")
     if H.nullspace:
         xo = xo - xo.mean()
     x, st = gh.solve(cuda(rhs), tol=1e-6, precision=precision, transpose=True)
