@@ -210,6 +210,8 @@ int ocg_vcycle_transpose(ocg_hier* h, int32_t dtype, const void* z_dev, void* r_
 #define OCG_SOLVE_UNROLLED 4   /* flags (measurement): run exactly max_iter iterations as one
                                   flat CUDA graph without the WHILE node, so that a probe's
                                   events become graph nodes around the probed kernels */
+#define OCG_SOLVE_BICGSTAB 8   /* flags, with OCG_SOLVE_TRANSPOSE: solve A^T x = b by BiCGStab
+                                  instead of Alg. 1 (both preconditioned by M^T) */
 
 typedef struct {
     double tol;              /* stop when ||r||_2 <= tol ||b||_2 (recursive residual) */
@@ -239,10 +241,14 @@ typedef struct {
  * at exit.  With the null space on, b is shifted to zero mean and x is returned with
  * zero mean over the leaves.
  * With OCG_SOLVE_TRANSPOSE the call solves A^T x = b (adjoint system; no counterpart in
- * the paper) by BiCGStab (van der Vorst 1992) right-preconditioned by the transposed cycle
- * M^T (ocg_vcycle_transpose): Alg. 1 stagnates on A^T, which T-junctions make differ from
- * A, and preconditioning A^T by M itself diverges at high coefficient contrast.  One
- * iteration there applies M^T and A^T twice; `iterations` counts iterations.  A hierarchy serves one solve at a time (its work vectors are shared).
+ * the paper) by Alg. 1 on A^T preconditioned by the transposed cycle M^T
+ * (ocg_vcycle_transpose): its scalars (r, M^T r) = (M r, r) and (p, A^T p) = (A p, p) are
+ * the forward method's quadratic forms.  With OCG_SOLVE_TRANSPOSE | OCG_SOLVE_BICGSTAB it
+ * uses BiCGStab (van der Vorst 1992), right-preconditioned by M^T, whose iteration applies
+ * M^T and A^T twice.  Alg. 1 with the forward cycle M stagnates on A^T, which T-junctions
+ * make differ from A, and BiCGStab with M diverges at high coefficient contrast.
+ * `iterations` counts iterations.  A hierarchy serves one solve at a time (its work
+ * vectors are shared).
  * Errors: ENOTCONV (stats filled), ENAN, EINVAL (also unknown flags), ECUDA. */
 int ocg_pcg_solve(ocg_hier* h, const double* b_dev, double* x_dev, const ocg_solve_params* prm,
                   ocg_solve_stats* stats, void* stream);

@@ -14,6 +14,10 @@ from . import mg
 
 
 def pcg(H, b, tol=1e-6, max_iter=200, prm=None, precond=True, transpose=False):
+    """Alg. 1 on A x = b, or on A^T x = b with transpose=True.  precond: True (the
+    mu-cycle M), False (none) or "transposed" (M^T, mg.vcycle_T: the preconditioner of the
+    adjoint system, whose scalars (r, M^T r) = (M r, r) and (p, A^T p) = (A p, p) are the
+    forward method's quadratic forms)."""
     A = H.A.T.tocsr() if transpose else H.A
     b = np.asarray(b, np.float64).copy()
     ns = H.nullspace
@@ -25,7 +29,12 @@ def pcg(H, b, tol=1e-6, max_iter=200, prm=None, precond=True, transpose=False):
     hist = [1.0]
     if bn == 0.0:
         return x, 0, hist
-    M = (lambda v: mg.vcycle(H, v, prm)) if precond else (lambda v: v.copy())
+    if precond == "transposed":
+        M = lambda v: mg.vcycle_T(H, v, prm)
+    elif precond:
+        M = lambda v: mg.vcycle(H, v, prm)
+    else:
+        M = lambda v: v.copy()
     z = M(r)
     p = z.copy()
     rz = r @ z

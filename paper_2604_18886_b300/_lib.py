@@ -40,6 +40,7 @@ class MGParams(C.Structure):
 OCG_SOLVE_EAGER = 1
 OCG_SOLVE_TRANSPOSE = 2
 OCG_SOLVE_UNROLLED = 4
+OCG_SOLVE_BICGSTAB = 8
 
 
 class SolveParams(C.Structure):

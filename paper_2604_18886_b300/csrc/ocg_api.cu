@@ -277,12 +277,13 @@ struct ocg_hier {
     int* tail_sched = nullptr;    // device copies of the tail pass schedules (float, double)
     int* tail_sched2 = nullptr;
     cudaStream_t cap = nullptr;   // private stream for graph capture
-    GraphSolve graphs[2][3][2];   // [transpose][precision][null space]
+    GraphSolve graphs[3][3][2];   // [A by PCG, A^T by PCG, A^T by BiCGStab][precision][null space]
     float* beta = nullptr;        // copy of the face fractions (transposed operator)
     // BiCGStab vectors over the tree cells (adjoint solves), allocated on first use
     double *rhat = nullptr, *s = nullptr, *tv = nullptr, *ph = nullptr, *sh = nullptr;
     // transposed cycle scratch over all cells, allocated on first use
     double *Xc = nullptr, *UST = nullptr;
+    double* Tacc = nullptr;   // [6][nt]: per T record and face, the coarser leaf's share (zero between uses)
 
     Coefs<double, double> C64() const { return {c64[0], c64[1], c64[2], c64[3], tw64}; }
     Coefs<float, float> C32() const { return {c32[0], c32[1], c32[2], c32[3], tw32}; }
@@ -295,7 +296,7 @@ struct ocg_hier {
                     if (gs.exec) cudaGraphExecDestroy(gs.exec);
                     if (gs.graph) cudaGraphDestroy(gs.graph);
                 }
-        for (double* v : {rhat, s, tv, ph, sh, Xc, UST}) dfree(v);
+        for (double* v : {rhat, s, tv, ph, sh, Xc, UST, Tacc}) dfree(v);
         dfree(beta);
         dfree(tseed);
         if (cap) cudaStreamDestroy(cap);
@@ -555,7 +556,9 @@ OMultiLevel tree_levels(const HostTree& H);
 // M^T for the adjoint system (no counterpart in the paper): the transposes of the steps of
 // Cycle, in reverse order, on the adjoint state (ubar in U, bbar in B).  Input: ubar = z on
 // the leaves, 0 elsewhere, bbar = 0; output: bbar on the leaves.  Every level runs as
-// plain launches (no shared-memory tail); X and UST are scratch over all cells.
+// plain launches (no shared-memory tail).  Scratch over all cells: UST (the adjoint of u*
+// on cells with children) and X, which holds G on level m-1 during a transposed
+// restriction and ubar's other copy during a level's ping-pong sweeps.
 template <class TV>
 struct CycleT {
     ocg_hier* h;
@@ -563,49 +566,49 @@ struct CycleT {
     TV* B;
     TV* X;
     TV* UST;
+    TV* Tacc;
     Ctx& c;
 
     const HostTree& H() const { return h->t->H; }
     template <class F>
     void with_coefs(int m, F&& f) { Cycle<TV>{h, U, B, c}.with_coefs(m, f); }
 
-    // ubar_K -= B^m^T X for the coarser leaves K (level m-1) of level m's T faces
-    void coarse(int m) {
+    // ubar_K -= the accumulated B^m^T contributions (slots Tacc) for the coarser leaves K
+    // (level m-1) of level m's T faces
+    void gather(int m) {
         if (m < 1) return;
         const ocg_octree* t = h->t;
         const int k0 = t->tc_lo[m - 1], k1 = t->tc_hi[m - 1];
         if (k1 <= k0) return;
-        with_coefs(m, [&](auto C) {
-            using TC = typename CoefTypes<decltype(C)>::TC;
-            using TW = typename CoefTypes<decltype(C)>::TW;
-            launch(c, -1, m, k1 - k0, [&] {
-                launch_k(kt_coarse<TV, TC, TW>, nblk(k1 - k0), BLK, 0, c.st, t->tables(), C, tree_levels(H()), t->level,
-                         t->tcoarse, k0, k1, U, (const TV*)X);
-            });
+        launch(c, -1, m, k1 - k0, [&] {
+            launch_k(kt_tgather<TV>, nblk(k1 - k0), BLK, 0, c.st, t->tables(), tree_levels(H()), t->level, t->tcoarse, k0,
+                     k1, U, Tacc);
         });
+        ck_launch("transposed gather");
     }
-    void apply(int m) {
-        with_coefs(m, [&](auto C) {
-            using TC = typename CoefTypes<decltype(C)>::TC;
-            using TW = typename CoefTypes<decltype(C)>::TW;
-            const LevelArgs A = h->t->largs(m);
-            launch(c, -1, m, A.ncell, [&] {
-                launch_k(kt_apply<TV, TC, TW>, nblk(A.ncell / 8, OBLK), OBLK, 0, c.st, A, h->t->tables(), C, U, (const TV*)X);
-            });
-        });
-        coarse(m);
-    }
-    void sweep(int m, int colour) {
+    // one transposed colour sweep from src to dst (U or X over level m); acc: add the
+    // coarser leaves' shares to the slots Tacc
+    void sweep(int m, int colour, TV* src, TV* dst, bool acc) {
         with_coefs(m, [&](auto C) {
             using TC = typename CoefTypes<decltype(C)>::TC;
             using TW = typename CoefTypes<decltype(C)>::TW;
             const LevelArgs A = h->t->largs(m);
             launch(c, OCG_PROBE_SWEEP, m, A.ncell, [&] {
-                launch_k(kt_sweep_v<TV, TC, TW>, nblk(A.ncell / 8, OBLK), OBLK, 0, c.st, A, C, (const TV*)U, B, X, colour);
+                launch_k(kt_fsweep<TV, TC, TW>, nblk(A.ncell / 8, OBLK), OBLK, 0, c.st, A, h->t->tables(), C,
+                         (const TV*)src, dst, B, Tacc, colour, acc ? 1 : 0);
             });
         });
-        apply(m);
         ck_launch("transposed sweep");
+    }
+    // n pairs of transposed sweeps, colours (first, 1 - first) each; ubar ping-pongs
+    // between U and X and ends in U (an even number of sweeps)
+    void smooth(int m, int n, int first, bool acc) {
+        TV* a = U;
+        TV* b = X;
+        for (int it = 0; it < n; ++it) {
+            sweep(m, first, a, b, acc);
+            sweep(m, 1 - first, b, a, acc);
+        }
     }
     void coarsest(int m) {
         const int nu = h->prm.nu_coarsest, half = nu / 2;
@@ -633,7 +636,7 @@ struct CycleT {
         });
         ck_launch("transposed prolong");
     }
-    void restrict_(int m) {
+    void restrict_(int m, bool acc) {
         const TV scale = TV(h->prm.beta_restrict / h->prm.alpha);
         const LevelArgs Ac = h->t->largs(m - 1);
         launch(c, OCG_PROBE_RESTRICT, m - 1, Ac.ncell, [&] {
@@ -653,20 +656,24 @@ struct CycleT {
             const LevelArgs A = h->t->largs(m);
             launch(c, OCG_PROBE_RESTRICT, m, A.ncell, [&] {
                 launch_k(kt_restrict_c<TV, TC, TW>, nblk(A.ncell / 8, OBLK), OBLK, 0, c.st, A, h->t->tables(), C, U, B,
-                         (const TV*)UST, X, scale);
+                         (const TV*)UST, (const TV*)X, Tacc, scale, acc ? 1 : 0);
             });
         });
-        apply(m);
         ck_launch("transposed restrict");
     }
-    void cycle(int m) {
+    // last: no later visit of level m follows in this cycle, so what the steps after the
+    // recursion would add to the coarser leaves (read only by a later visit of level m-1)
+    // is not formed
+    void cycle(int m, bool last) {
         if (m == H().mc) { coarsest(m); return; }
-        for (int it = 0; it < h->prm.nu_post; ++it) { sweep(m, 0); sweep(m, 1); }
+        smooth(m, h->prm.nu_post, 0, true);   // post-smoothing (colours 1, 0 per pair) transposed
+        gather(m);
         prolong(m);
         const int mu = mu_at(h, m - 1);
-        for (int k = 0; k < mu; ++k) cycle(m - 1);
-        restrict_(m);
-        for (int it = 0; it < h->prm.nu_pre; ++it) { sweep(m, 1); sweep(m, 0); }
+        for (int k = 0; k < mu; ++k) cycle(m - 1, last && k == mu - 1);
+        restrict_(m, !last);
+        smooth(m, h->prm.nu_pre, 1, !last);   // pre-smoothing (colours 0, 1 per pair) transposed
+        if (!last) gather(m);
     }
     // U, B: the leaf values of Z and zeros over the tree cells, zeros on the coarser levels
     template <class TZ>
@@ -680,7 +687,7 @@ struct CycleT {
             ck(cudaMemsetAsync(B + HH.ntree, 0, rest * sizeof(TV), c.st), "memset");
         }
     }
-    void run() { cycle(H().D); }
+    void run() { cycle(H().D, true); }
 };
 
 void ensure_cycle_T(ocg_hier* h) {
@@ -688,6 +695,9 @@ void ensure_cycle_T(ocg_hier* h) {
     if (h->Xc) return;
     h->Xc = dalloc<double>(h->t->H.ncell);
     h->UST = dalloc<double>(h->t->H.ncell);
+    const int64_t ns = std::max<int64_t>(6 * h->t->H.nt, 1);
+    h->Tacc = dalloc<double>(ns);
+    ck(cudaMemset(h->Tacc, 0, ns * sizeof(double)), "memset");
 }
 
 // ------------------------------------------------------------------ sweep autotuner
@@ -807,10 +817,11 @@ void apply_outer(ocg_hier* h, Coefs<TC, TW> C, TO* P, TO* Y, int op, Ctx& c) {
 }
 
 // Y = A^T P on the leaves: A P, then the A^T - A rows around the T-junctions.
+// op: the reduction fused into the forward part, over (p, A p) = (p, A^T p).
 template <class TO, class TC, class TW>
-void apply_outer_T(ocg_hier* h, Coefs<TC, TW> C, TO* P, TO* Y, Ctx& c) {
+void apply_outer_T(ocg_hier* h, Coefs<TC, TW> C, TO* P, TO* Y, Ctx& c, int op = OP_NONE) {
     const ocg_octree* t = h->t;
-    apply_outer<TO, TC, TW>(h, C, P, Y, OP_NONE, c);
+    apply_outer<TO, TC, TW>(h, C, P, Y, op, c);
     const HostTree& H = t->H;
     if (H.nt == 0) return;
     const Tables T = t->tables();
@@ -845,8 +856,8 @@ void solution_mean(ocg_hier* h, Ctx& c, const double* xt) {
     });
 }
 
-template <class TO, class TV, class TC, class TW>
-struct Pcg {
+template <class TO, class TV, class TC, class TW, bool TR>
+struct PcgImpl {
     ocg_hier* h;
     Coefs<TC, TW> Co;
     bool ns;
@@ -875,17 +886,26 @@ struct Pcg {
         launch(c, -1, 0, n(), [&] { launch_k(k_project<TO, TV>, gb(), BLK, 0, c.st, r(), h->t->flags, h->S, B(), n()); });
         ck_launch("begin");
         precondition();
-        launch(c, -1, 0, n(), [&] { launch_k(k_dot<TO, TV, false>, rb(), BLK, 0, c.st, r(), U(), n(), make_red(h, rb(), OP_RZ0)); });
-        launch(c, -1, 0, n(), [&] { launch_k(k_pupdate<TO, TV>, gb(), BLK, 0, c.st, p(), U(), h->S, n(), 1); });
+        launch(c, -1, 0, n(), [&] { launch_k(k_dot<TO, TV, false>, rb(), BLK, 0, c.st, r(), Z(), n(), make_red(h, rb(), OP_RZ0)); });
+        launch(c, -1, 0, n(), [&] { launch_k(k_pupdate<TO, TV>, gb(), BLK, 0, c.st, p(), Z(), h->S, n(), 1); });
         ck_launch("begin");
         half_a();
     }
+    // z = M r (forward: r in B, z in U) or z = M^T r (transpose: r in B, z in B)
+    TV* Z() { return TR ? B() : U(); }
     void precondition() {
-        zero(h->U, H().ntree * sizeof(TV));
-        Cycle<TV>{h, U(), B(), c}.run();
+        if constexpr (TR) {
+            CycleT<TV> ct{h, U(), B(), (TV*)h->Xc, (TV*)h->UST, (TV*)h->Tacc, c};
+            ct.seed((const TV*)B());
+            ct.run();
+        } else {
+            zero(h->U, H().ntree * sizeof(TV));
+            Cycle<TV>{h, U(), B(), c}.run();
+        }
     }
     void half_a() {
-        apply_outer<TO, TC, TW>(h, Co, p(), Ap(), OP_ALPHA, c);
+        if constexpr (TR) apply_outer_T<TO, TC, TW>(h, Co, p(), Ap(), c, OP_ALPHA);
+        else apply_outer<TO, TC, TW>(h, Co, p(), Ap(), OP_ALPHA, c);
         launch(c, -1, 0, n(), [&] {
             const Red R = make_red(h, rb(), OP_RR, cond, set_cond);
             if (ns) launch_k(k_update<TO, TV, true>, rb(), BLK, 0, c.st, x(), r(), p(), Ap(), nullptr, n(), R);
@@ -897,8 +917,8 @@ struct Pcg {
     }
     void half_b() {
         precondition();
-        launch(c, -1, 0, n(), [&] { launch_k(k_dot<TO, TV, false>, rb(), BLK, 0, c.st, r(), U(), n(), make_red(h, rb(), OP_BETA)); });
-        launch(c, -1, 0, n(), [&] { launch_k(k_pupdate<TO, TV>, gb(), BLK, 0, c.st, p(), U(), h->S, n(), 0); });
+        launch(c, -1, 0, n(), [&] { launch_k(k_dot<TO, TV, false>, rb(), BLK, 0, c.st, r(), Z(), n(), make_red(h, rb(), OP_BETA)); });
+        launch(c, -1, 0, n(), [&] { launch_k(k_pupdate<TO, TV>, gb(), BLK, 0, c.st, p(), Z(), h->S, n(), 0); });
         ck_launch("half_b");
     }
     void body() {
@@ -907,7 +927,8 @@ struct Pcg {
     }
     void finish() {
         launch(c, -1, 0, n(), [&] { launch_k(k_cast<TO, double>, gb(), BLK, 0, c.st, x(), h->xt, n()); });
-        apply_outer<double, TC, TW>(h, Co, h->xt, h->yt, OP_NONE, c);
+        if constexpr (TR) apply_outer_T<double, TC, TW>(h, Co, h->xt, h->yt, c);
+        else apply_outer<double, TC, TW>(h, Co, h->xt, h->yt, OP_NONE, c);
         launch(c, -1, 0, n(), [&] {
             launch_k(k_resid<double>, rb(), BLK, 0, c.st, h->bt, h->yt, h->t->flags, n(), make_red(h, rb(), OP_TRUE));
         });
@@ -915,6 +936,14 @@ struct Pcg {
         ck_launch("finish");
     }
 };
+
+// Alg. 1 on A x = b, and Alg. 1 on the adjoint system A^T x = b preconditioned by the
+// transposed cycle M^T (no counterpart in the paper): its scalars (r, M^T r) = (M r, r) and
+// (p, A^T p) = (A p, p) are the forward method's quadratic forms.
+template <class TO, class TV, class TC, class TW>
+using Pcg = PcgImpl<TO, TV, TC, TW, false>;
+template <class TO, class TV, class TC, class TW>
+using PcgT = PcgImpl<TO, TV, TC, TW, true>;
 
 // ------------------------------------------------------- BiCGStab (adjoint system)
 // Solves A^T x = b, right-preconditioned by the same mu-cycle (the cycle approximates
@@ -962,7 +991,7 @@ struct BiCG {
     }
     // out = M^T (the value that k_bi_p / k_bi_s left in B)
     void precondition(TO* out) {
-        CycleT<TV> ct{h, U(), B(), (TV*)h->Xc, (TV*)h->UST, c};
+        CycleT<TV> ct{h, U(), B(), (TV*)h->Xc, (TV*)h->UST, (TV*)h->Tacc, c};
         ct.seed((const TV*)B());
         ct.run();
         launch(c, -1, 0, n(), [&] { launch_k(k_cast<TV, TO>, gb(), BLK, 0, c.st, B(), out, n()); });
@@ -1091,6 +1120,7 @@ int krylov_solve(ocg_hier* h, Coefs<TC, TW> Co, int prec, const double* b_user, 
     const ocg_octree* t = h->t;
     const HostTree& H = t->H;
     const bool transpose = (sp->flags & OCG_SOLVE_TRANSPOSE) != 0;
+    const bool bicg = transpose && (sp->flags & OCG_SOLVE_BICGSTAB) != 0;
     const bool ns = sp->nullspace < 0 ? h->ns_auto : sp->nullspace != 0;
     const bool eager = (sp->flags & OCG_SOLVE_EAGER) || h->probe.kind != OCG_PROBE_OFF;
     // scalars: tolerance, iteration cap, null-space flag, counters
@@ -1106,7 +1136,7 @@ int krylov_solve(ocg_hier* h, Coefs<TC, TW> Co, int prec, const double* b_user, 
     });
     ck_launch("scatter");
     int64_t kernels = c.count;
-    GraphSolve& gs = h->graphs[transpose ? 1 : 0][prec][ns ? 1 : 0];
+    GraphSolve& gs = h->graphs[!transpose ? 0 : (bicg ? 2 : 1)][prec][ns ? 1 : 0];
     const bool unrolled = (sp->flags & OCG_SOLVE_UNROLLED) != 0;
     if (unrolled) {
         // measurement form: exactly max_iter iterations captured into one flat graph (no
@@ -1119,7 +1149,7 @@ int krylov_solve(ocg_hier* h, Coefs<TC, TW> Co, int prec, const double* b_user, 
         try {
             Solver<TO, TV, TC, TW> pc{h, Co, ns, cc, 0, 0};
             pc.begin();
-            const int nbody = transpose ? sp->max_iter : sp->max_iter - 1;
+            const int nbody = bicg ? sp->max_iter : sp->max_iter - 1;
             for (int q = 0; q < nbody; ++q) pc.body();
             pc.finish();
         } catch (...) {
@@ -1170,7 +1200,7 @@ int krylov_solve(ocg_hier* h, Coefs<TC, TW> Co, int prec, const double* b_user, 
     } else if (!eager) {
         // PCG's begin ends with the first half iteration, so its WHILE body runs k - 1
         // times; BiCGStab's body runs k times
-        const int64_t body_runs = transpose ? k : std::max(k - 1, 0);
+        const int64_t body_runs = bicg ? k : std::max(k - 1, 0);
         kernels = c.count + gs.outer_kernels + body_runs * gs.body_kernels;
     } else {
         kernels = c.count;
@@ -1548,7 +1578,7 @@ int ocg_vcycle_transpose(ocg_hier* h, int32_t dtype, const void* z, void* r, voi
             launch(c, -1, 0, H.nleaf, [&] {
                 launch_k(k_scatter<TV, TV>, nblk(H.nleaf), BLK, 0, st, (const TV*)z, U, t->leaf_cell, (int)H.nleaf);
             });
-            CycleT<TV>{h, U, B, (TV*)h->Xc, (TV*)h->UST, c}.run();
+            CycleT<TV>{h, U, B, (TV*)h->Xc, (TV*)h->UST, (TV*)h->Tacc, c}.run();
             launch(c, -1, 0, H.nleaf, [&] {
                 launch_k(k_gather<TV, TV>, nblk(H.nleaf), BLK, 0, st, B, (TV*)r, t->leaf_cell, (int)H.nleaf);
             });
@@ -1612,26 +1642,31 @@ int ocg_pcg_solve(ocg_hier* h, const double* b, double* x, const ocg_solve_param
     int g = guard([&] {
         if (!h || !b || !x || !sp || !stats) throw Status(OCG_EINVAL, "null argument");
         if (!(sp->tol > 0) || sp->max_iter < 1) throw Status(OCG_EINVAL, "tol must be > 0 and max_iter >= 1");
-        if (sp->flags & ~(OCG_SOLVE_EAGER | OCG_SOLVE_TRANSPOSE | OCG_SOLVE_UNROLLED))
+        if (sp->flags & ~(OCG_SOLVE_EAGER | OCG_SOLVE_TRANSPOSE | OCG_SOLVE_UNROLLED | OCG_SOLVE_BICGSTAB))
             throw Status(OCG_EINVAL, "unknown solve flags");
         cudaStream_t st = (cudaStream_t)stream;
         const bool tr = (sp->flags & OCG_SOLVE_TRANSPOSE) != 0;
-        if (tr) ensure_bicg(h);
+        const bool bi = tr && (sp->flags & OCG_SOLVE_BICGSTAB) != 0;
+        if (bi) ensure_bicg(h);
+        else if (tr) { ensure_adjoint(h); ensure_cycle_T(h); }
         switch (sp->precision) {
             case OCG_PREC_FP64:
                 if (!h->c64[0]) throw Status(OCG_EINVAL, "FP64 solve needs coef_dtype F64");
-                status = tr ? krylov_solve<BiCG, double, double>(h, h->C64(), 0, b, x, sp, stats, st)
-                            : krylov_solve<Pcg, double, double>(h, h->C64(), 0, b, x, sp, stats, st);
+                status = bi   ? krylov_solve<BiCG, double, double>(h, h->C64(), 0, b, x, sp, stats, st)
+                            : tr ? krylov_solve<PcgT, double, double>(h, h->C64(), 0, b, x, sp, stats, st)
+                                 : krylov_solve<Pcg, double, double>(h, h->C64(), 0, b, x, sp, stats, st);
                 break;
             case OCG_PREC_FP32:
                 if (!h->c32[0]) throw Status(OCG_EINVAL, "FP32 solve needs coef_dtype F32");
-                status = tr ? krylov_solve<BiCG, float, float>(h, h->C32(), 1, b, x, sp, stats, st)
-                            : krylov_solve<Pcg, float, float>(h, h->C32(), 1, b, x, sp, stats, st);
+                status = bi   ? krylov_solve<BiCG, float, float>(h, h->C32(), 1, b, x, sp, stats, st)
+                            : tr ? krylov_solve<PcgT, float, float>(h, h->C32(), 1, b, x, sp, stats, st)
+                                 : krylov_solve<Pcg, float, float>(h, h->C32(), 1, b, x, sp, stats, st);
                 break;
             case OCG_PREC_MIXED:
                 if (!h->c32[0]) throw Status(OCG_EINVAL, "mixed solve needs coef_dtype F32");
-                status = tr ? krylov_solve<BiCG, double, float>(h, h->C32(), 2, b, x, sp, stats, st)
-                            : krylov_solve<Pcg, double, float>(h, h->C32(), 2, b, x, sp, stats, st);
+                status = bi   ? krylov_solve<BiCG, double, float>(h, h->C32(), 2, b, x, sp, stats, st)
+                            : tr ? krylov_solve<PcgT, double, float>(h, h->C32(), 2, b, x, sp, stats, st)
+                                 : krylov_solve<Pcg, double, float>(h, h->C32(), 2, b, x, sp, stats, st);
                 break;
             default:
                 throw Status(OCG_EINVAL, "precision");

@@ -1206,6 +1206,129 @@ __device__ __forceinline__ void octet_AT(const Tables& T, const Coefs<TC, TW>& C
         if (d[s] != TV(0)) Y[s] -= tO;
 }
 
+// T faces of an octet in the transposed kernels: W[s] += the coefficients of cell s's T
+// faces, and (acc) the coarser leaf K's share B^m^T v, the sum of (c_f / 2) v_s over the 4
+// cells of the face, added to the octet's slot Tacc[dir][record] (collected by kt_tgather).
+// Returns the octet's T record (-1 without T faces).
+template <class TV, class TC, class TW>
+__device__ __forceinline__ int t_faces(const Tables& T, const Coefs<TC, TW>& C, const TV (&cm)[3][8], const TV (&v)[8],
+                                       const int (&nb)[6], int og, TV (&W)[8], TV* __restrict__ Tacc, int acc) {
+    bool any = false;
+#pragma unroll
+    for (int dir = 0; dir < 6; ++dir) any |= nb[dir] <= -2;
+    if (!any) return -1;
+    const int t = __ldg(T.trec + og);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int bit = 1 << a;
+        if (nb[2 * a] <= -2) {
+            TV f = TV(0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int s = clear_slot(a, q);
+                W[s] += cm[a][s];
+                f += cm[a][s] * v[s];
+            }
+            if (acc) Tacc[(2 * a) * T.nt + t] += TV(0.5) * f;
+        }
+        if (nb[2 * a + 1] <= -2) {
+            TV f = TV(0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int s = clear_slot(a, q) | bit;
+                const TV cf = TV(tov(__ldg(C.tw + ((2 * a + 1) * 4 + q) * T.nt + t)));
+                W[s] += cf;
+                f += cf * v[s];
+            }
+            if (acc) Tacc[(2 * a + 1) * T.nt + t] += TV(0.5) * f;
+        }
+    }
+    return t;
+}
+
+// Transposed colour sweep in one launch, reading ubar from Uin and writing Uout (ping-pong,
+// so that V = Uin / d on the colour's active cells of a neighbouring octet can be recomputed
+// here instead of being stored): bbar += V, Uout = Uin - A^m^T V.  Only cells of the other
+// colour see V across a face (red-black), so only their neighbour values are fetched.
+template <class TV>
+__device__ __forceinline__ TV colour_v(TV u, TV d, bool on) {
+    return (on && d != TV(0)) ? u / d : TV(0);
+}
+
+template <class TV, class TC, class TW>
+__global__ void __launch_bounds__(OBLK) kt_fsweep(LevelArgs A, Tables T, Coefs<TC, TW> C, const TV* __restrict__ Uin,
+                                                  TV* __restrict__ Uout, TV* __restrict__ B, TV* __restrict__ Tacc,
+                                                  int colour, int acc) {
+    pdl_enter();
+    const int o = blockIdx.x * OBLK + threadIdx.x;
+    if (o >= A.ncell / 8) return;
+    const int c8 = A.off + 8 * o, og = c8 >> 3;
+    TV u[8], d[8], cm[3][8], v[8], W[8], Y[8];
+    ld8(Uin + c8, u);
+    ldc8(C.d + c8, d);
+    ldc8(C.cx + c8, cm[0]);
+    ldc8(C.cy + c8, cm[1]);
+    ldc8(C.cz + c8, cm[2]);
+    int nb[6];
+    octet_neighbours(T, A.ni, o, og, nb);
+    int nact = 0;
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+        nact += d[s] != TV(0) ? 1 : 0;
+        v[s] = colour_v(u[s], d[s], (__popc(s) & 1) == colour);
+        W[s] = TV(0);
+    }
+    t_faces(T, C, cm, v, nb, og, W, Tacc, acc);
+    TV tO = TV(0);
+#pragma unroll
+    for (int s = 0; s < 8; ++s) { Y[s] = (d[s] + W[s]) * v[s]; tO += W[s] * v[s]; }
+    tO = tO * TV(0.5) * inv_count<TV>(nact);
+    const int off = A.off;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int bit = 1 << a;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int s = clear_slot(a, q), w = s | bit;
+            const TV c = cm[a][w];
+            Y[s] += c * v[w];
+            Y[w] += c * v[s];
+        }
+        const int vn = nb[2 * a];
+        if (vn >= 0) {
+            const int n8 = off + 8 * vn;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int s = clear_slot(a, q), ns = s | bit;
+                if ((__popc(ns) & 1) != colour) continue;   // neighbour cell not of the colour
+                const TV dn = TV(tov(__ldg(C.d + n8 + ns)));
+                Y[s] += cm[a][s] * colour_v(Uin[n8 + ns], dn, true);
+            }
+        }
+        const int wn = nb[2 * a + 1];
+        if (wn >= 0) {
+            const int n8 = off + 8 * wn;
+            const TC* cc = a == 0 ? C.cx : (a == 1 ? C.cy : C.cz);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int s = clear_slot(a, q);
+                if ((__popc(s) & 1) != colour) continue;
+                const TV dn = TV(tov(__ldg(C.d + n8 + s)));
+                Y[s | bit] += TV(tov(__ldg(cc + n8 + s))) * colour_v(Uin[n8 + s], dn, true);
+            }
+        }
+    }
+    TV b[8];
+    ld8(B + c8, b);
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+        Y[s] = u[s] - Y[s] + (d[s] != TV(0) ? tO : TV(0));
+        b[s] += v[s];
+    }
+    st8(Uout + c8, Y);
+    st8(B + c8, b);
+}
+
 // transposed colour sweep, part 1: V = ubar / d on the active cells of the colour (0
 // elsewhere), bbar += V
 template <class TV, class TC, class TW>
@@ -1226,37 +1349,13 @@ __device__ __forceinline__ void sweep_v_octet(const LevelArgs& A, const Coefs<TC
     st8(B + c8, b);
 }
 
-template <class TV, class TC, class TW>
-__global__ void __launch_bounds__(OBLK) kt_sweep_v(LevelArgs A, Coefs<TC, TW> C, const TV* __restrict__ U,
-                                                   TV* __restrict__ B, TV* V, int colour) {
-    pdl_enter();
-    const int o = blockIdx.x * OBLK + threadIdx.x;
-    if (o >= A.ncell / 8) return;
-    sweep_v_octet<TV, TC, TW>(A, C, U, B, V, colour, o);
-}
-
-// ubar -= A^m^T X over the cells of the level (transposed sweep part 2, and the residual
-// part of the transposed restriction)
-template <class TV, class TC, class TW>
-__global__ void __launch_bounds__(OBLK) kt_apply(LevelArgs A, Tables T, Coefs<TC, TW> C, TV* __restrict__ U,
-                                                 const TV* X) {
-    pdl_enter();
-    const int o = blockIdx.x * OBLK + threadIdx.x;
-    if (o >= A.ncell / 8) return;
-    const int c8 = A.off + 8 * o;
-    TV y[8], u[8];
-    octet_AT<TV, TC, TW>(T, C, X, A, o, c8 >> 3, y);
-    ld8(U + c8, u);
-#pragma unroll
-    for (int s = 0; s < 8; ++s) u[s] -= y[s];
-    st8(U + c8, u);
-}
-
-// ubar_K -= sum over the fine T cells s beside K of (c_f / 2) X_s, for the coarser leaves K
-// listed in tcoarse[k0, k1) (those of one level; the fine cells are one level finer)
-template <class TV, class TC, class TW>
-__global__ void kt_coarse(Tables T, Coefs<TC, TW> C, OMultiLevel ML, const int8_t* __restrict__ level,
-                          const int32_t* __restrict__ tcoarse, int k0, int k1, TV* __restrict__ U, const TV* X) {
+// ubar_K -= the slots Tacc of the fine T octets beside K, for the coarser leaves K listed in
+// tcoarse[k0, k1) (those of one level; the fine octets are one level finer); the slots
+// are zeroed (each belongs to one K).
+template <class TV>
+__global__ void kt_tgather(Tables T, OMultiLevel ML, const int8_t* __restrict__ level,
+                           const int32_t* __restrict__ tcoarse, int k0, int k1, TV* __restrict__ U,
+                           TV* __restrict__ Tacc) {
     pdl_enter();
     const int q = k0 + blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= k1) return;
@@ -1276,15 +1375,10 @@ __global__ void kt_coarse(Tables T, Coefs<TC, TW> C, OMultiLevel ML, const int8_
         if (Q < 0) continue;
         const int co = __ldg(T.child_oct + Q);
         if (co < 0) continue;
-        const TC* cm = a == 0 ? C.cx : (a == 1 ? C.cy : C.cz);
-        const int t = plus ? 0 : __ldg(T.trec + co);
-#pragma unroll
-        for (int qq = 0; qq < 4; ++qq) {
-            const int s = clear_slot(a, qq) | (plus ? 0 : bit);
-            const int i = 8 * co + s;
-            const TV cf = plus ? TV(tov(__ldg(cm + i))) : TV(tov(__ldg(C.tw + ((2 * a + 1) * 4 + qq) * T.nt + t)));
-            acc += TV(0.5) * cf * X[i];
-        }
+        // K lies on the - side of the fine octet when Q is on K's + side
+        const int slot = (plus ? 2 * a : 2 * a + 1) * T.nt + __ldg(T.trec + co);
+        acc += Tacc[slot];
+        Tacc[slot] = TV(0);
     }
     U[K] -= acc;
 }
@@ -1352,34 +1446,80 @@ __global__ void __launch_bounds__(OBLK) kt_restrict_v(LevelArgs A, Tables T, Coe
 
 // transposed FAS restriction, part 3, per octet of level m with parent P: on the active
 // cells rbar = (beta/alpha) G_P, bbar += rbar, ubar += UST_P / n (transpose of u* = the
-// mean of the active children).  X holds G on level m-1 and receives rbar on level m
-// (0 on inactive cells) for the residual part.
+// mean of the active children), then ubar -= A^m^T rbar (the residual's transpose), with
+// rbar of a neighbouring cell recomputed from its parent's G (G held in X on level m-1).
 template <class TV, class TC, class TW>
 __global__ void __launch_bounds__(OBLK) kt_restrict_c(LevelArgs A, Tables T, Coefs<TC, TW> C, TV* __restrict__ U,
-                                                      TV* __restrict__ B, const TV* __restrict__ UST, TV* X, TV scale) {
+                                                      TV* __restrict__ B, const TV* __restrict__ UST,
+                                                      const TV* __restrict__ G, TV* __restrict__ Tacc, TV scale,
+                                                      int acc) {
     pdl_enter();
     const int o = blockIdx.x * OBLK + threadIdx.x;
     if (o >= A.ncell / 8) return;
-    const int c8 = A.off + 8 * o;
-    const int P = __ldg(T.oct_parent + (c8 >> 3));
-    TV u[8], b[8], d[8], rb[8];
+    const int c8 = A.off + 8 * o, og = c8 >> 3;
+    const int P = __ldg(T.oct_parent + og);
+    TV d[8], cm[3][8], v[8], W[8], Y[8];
+    ldc8(C.d + c8, d);
+    ldc8(C.cx + c8, cm[0]);
+    ldc8(C.cy + c8, cm[1]);
+    ldc8(C.cz + c8, cm[2]);
+    int nb[6];
+    octet_neighbours(T, A.ni, o, og, nb);
+    int nact = 0;
+#pragma unroll
+    for (int s = 0; s < 8; ++s) nact += d[s] != TV(0) ? 1 : 0;
+    const TV r = scale * G[P], us = UST[P] * inv_count<TV>(nact);
+#pragma unroll
+    for (int s = 0; s < 8; ++s) { v[s] = d[s] != TV(0) ? r : TV(0); W[s] = TV(0); }
+    t_faces(T, C, cm, v, nb, og, W, Tacc, acc);
+    TV tO = TV(0);
+#pragma unroll
+    for (int s = 0; s < 8; ++s) { Y[s] = (d[s] + W[s]) * v[s]; tO += W[s] * v[s]; }
+    tO = tO * TV(0.5) * inv_count<TV>(nact);
+    const int off = A.off;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int bit = 1 << a;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int s = clear_slot(a, q), w = s | bit;
+            const TV c = cm[a][w];
+            Y[s] += c * v[w];
+            Y[w] += c * v[s];
+        }
+        const int vn = nb[2 * a];
+        if (vn >= 0) {
+            const int n8 = off + 8 * vn;
+            const TV rn = scale * G[__ldg(T.oct_parent + (n8 >> 3))];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int s = clear_slot(a, q), ns = s | bit;
+                if (TV(tov(__ldg(C.d + n8 + ns))) != TV(0)) Y[s] += cm[a][s] * rn;
+            }
+        }
+        const int wn = nb[2 * a + 1];
+        if (wn >= 0) {
+            const int n8 = off + 8 * wn;
+            const TC* cc = a == 0 ? C.cx : (a == 1 ? C.cy : C.cz);
+            const TV rn = scale * G[__ldg(T.oct_parent + (n8 >> 3))];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int s = clear_slot(a, q);
+                if (TV(tov(__ldg(C.d + n8 + s))) != TV(0)) Y[s | bit] += TV(tov(__ldg(cc + n8 + s))) * rn;
+            }
+        }
+    }
+    TV u[8], b[8];
     ld8(U + c8, u);
     ld8(B + c8, b);
-    ldc8(C.d + c8, d);
-    int n = 0;
-#pragma unroll
-    for (int s = 0; s < 8; ++s) n += d[s] != TV(0) ? 1 : 0;
-    const TV r = scale * X[P], us = UST[P] * inv_count<TV>(n);
 #pragma unroll
     for (int s = 0; s < 8; ++s) {
         const bool act = d[s] != TV(0);
-        rb[s] = act ? r : TV(0);
-        if (act) { b[s] += r; u[s] += us; }
+        b[s] += v[s];
+        u[s] += (act ? us + tO : TV(0)) - Y[s];
     }
     st8(U + c8, u);
     st8(B + c8, b);
-#pragma unroll
-    for (int q = 0; q < 8; ++q) X[c8 + q] = rb[q];
 }
 
 // transposed smoothing of the coarsest level in one CTA: 2 nsweep colour sweeps, the first

@@ -219,17 +219,22 @@ class Hierarchy:
         return r
 
     def solve(self, b, x=None, tol=1e-6, max_iter=100, precision="mixed", nullspace=-1,
-              stream=None, raise_on_notconv=True, eager=False, transpose=False, unrolled=False):
+              stream=None, raise_on_notconv=True, eager=False, transpose=False, unrolled=False,
+              method="pcg"):
         """x with A x = b (PCG, Alg. 1), or A^T x = b with transpose=True (the adjoint
-        system: BiCGStab preconditioned by the transposed cycle M^T).  Returns (x, stats)."""
+        system, preconditioned by the transposed cycle M^T: Alg. 1 with method="pcg",
+        BiCGStab with method="bicgstab").  Returns (x, stats)."""
         import torch
         assert b.dtype == torch.float64 and b.is_cuda
         if x is None:
             x = torch.empty_like(b)
         sp = L.SolveParams()
         sp.tol, sp.max_iter, sp.precision, sp.nullspace = tol, max_iter, PRECISIONS[precision], nullspace
+        if method not in ("pcg", "bicgstab"):
+            raise ValueError("method must be 'pcg' or 'bicgstab'")
         sp.flags = ((L.OCG_SOLVE_EAGER if eager else 0) | (L.OCG_SOLVE_TRANSPOSE if transpose else 0) |
-                    (L.OCG_SOLVE_UNROLLED if unrolled else 0))
+                    (L.OCG_SOLVE_UNROLLED if unrolled else 0) |
+                    (L.OCG_SOLVE_BICGSTAB if transpose and method == "bicgstab" else 0))
         st = L.SolveStats()
         code = L.lib().ocg_pcg_solve(self._h, L.ptr(b), L.ptr(x), C.byref(sp), C.byref(st),
                                      self._stream(stream))

@@ -6,8 +6,8 @@ Tolerances as in test_gpu_parity: FP64 applies 1e-12, FP32 applies 1e-6 relative
 vector's max norm; the transposed cycle M^T as the forward cycle (FP64 1e-10, FP32 1e-5);
 FP64 Krylov iterates 1e-8 (BiCGStab's two-sided recurrences amplify rounding-order
 differences more than CG's).  Finite differences: 1e-4 relative to the largest sampled
-gradient.  The adjoint solves are preconditioned by M^T, so the oracle's BiCGStab runs
-with precond="transposed".
+gradient.  The adjoint solves are preconditioned by M^T (Alg. 1 on A^T by default,
+BiCGStab on request), so the oracle's solvers run with precond="transposed".
 """
 import numpy as np
 import pytest
@@ -91,11 +91,27 @@ def test_vcycle_transpose_is_the_adjoint_of_the_gpu_cycle(name, bf16):
 
 
 @pytest.mark.parametrize("name", ["c2_16", "c2_16_neumann", "c3_16_d2", "c4_t1", "c5_8_d2"])
+def test_alg1_transpose_fp64_follows_oracle_iterates(name):
+    # Alg. 1 on A^T with M^T (the default adjoint method)
+    t, H, g, gh, f, beta = build(CASES[name](), "f64")
+    rhs = P.random_vector(t.n_leaves, 22)
+    xo, ko, ho = pcg.pcg(H, rhs, tol=1e-8, transpose=True, precond="transposed")
+    x, st = gh.solve(cuda(rhs), tol=1e-8, precision="fp64", transpose=True)
+    assert st.converged and st.iterations == ko
+    hist = [st.hist[i] for i in range(st.iterations + 1)]
+    assert np.allclose(hist, ho, rtol=1e-7, atol=0)
+    if H.nullspace:
+        assert abs(x.mean().item()) <= 1e-12 * x.abs().max().item()
+        xo = xo - xo.mean()
+    assert rel(x.cpu().numpy(), xo) <= 1e-9
+
+
+@pytest.mark.parametrize("name", ["c2_16", "c2_16_neumann", "c3_16_d2", "c4_t1", "c5_8_d2"])
 def test_bicgstab_fp64_follows_oracle_iterates(name):
     t, H, g, gh, f, beta = build(CASES[name](), "f64")
     rhs = P.random_vector(t.n_leaves, 22)
     xo, ko, ho = pcg.bicgstab(H, rhs, tol=1e-8, transpose=True, precond="transposed")
-    x, st = gh.solve(cuda(rhs), tol=1e-8, precision="fp64", transpose=True)
+    x, st = gh.solve(cuda(rhs), tol=1e-8, precision="fp64", transpose=True, method="bicgstab")
     assert st.converged and st.iterations == ko
     hist = [st.hist[i] for i in range(st.iterations + 1)]
     assert np.allclose(hist, ho, rtol=1e-6, atol=0)
@@ -104,16 +120,20 @@ def test_bicgstab_fp64_follows_oracle_iterates(name):
     assert rel(x.cpu().numpy(), xo) <= 1e-8
 
 
+@pytest.mark.parametrize("method", ["pcg", "bicgstab"])
 @pytest.mark.parametrize("precision", ["mixed", "fp32"])
 @pytest.mark.parametrize("name", ["c2_16", "c2_16_neumann", "c3_16_d2", "c4_t1", "c5_8_d2"])
-def test_transpose_solution_within_1e5(name, precision):
+def test_transpose_solution_within_1e5(name, precision, method):
     t, H, g, gh, f, beta = build(CASES[name](), "f32")
     rhs = P.random_vector(t.n_leaves, 23)
     ref = ADJ.solve(H, rhs, transpose=True, tol=1e-12)
-    xo, ko, _ = pcg.bicgstab(H, rhs, tol=1e-6, transpose=True, precond="transposed")
+    if method == "pcg":
+        xo, ko, _ = pcg.pcg(H, rhs, tol=1e-6, transpose=True, precond="transposed")
+    else:
+        xo, ko, _ = pcg.bicgstab(H, rhs, tol=1e-6, transpose=True, precond="transposed")
     if H.nullspace:
         xo = xo - xo.mean()
-    x, st = gh.solve(cuda(rhs), tol=1e-6, precision=precision, transpose=True)
+    x, st = gh.solve(cuda(rhs), tol=1e-6, precision=precision, transpose=True, method=method)
     x = x.cpu().numpy()
     assert st.converged and st.rel_res <= 1e-6 and abs(st.iterations - ko) <= 1
     if H.nullspace:
@@ -121,7 +141,7 @@ def test_transpose_solution_within_1e5(name, precision):
     assert rel(x, ref) <= 1.5 * rel(xo, ref) + 1e-5, (rel(x, ref), rel(xo, ref))
     if precision == "mixed":
         assert st.true_rel_res <= 1.5e-6
-        x9, st9 = gh.solve(cuda(rhs), tol=1e-9, precision="mixed", transpose=True)
+        x9, st9 = gh.solve(cuda(rhs), tol=1e-9, precision="mixed", transpose=True, method=method)
         assert st9.converged and st9.true_rel_res <= 2e-9
         assert rel(x9.cpu().numpy(), ref) <= 1e-5
 
@@ -137,11 +157,12 @@ def test_face_grad_matches_oracle(name):
     assert rel(out, ref) <= 1e-12
 
 
-def test_graph_and_eager_transpose_solves_agree():
+@pytest.mark.parametrize("method", ["pcg", "bicgstab"])
+def test_graph_and_eager_transpose_solves_agree(method):
     t, H, g, gh, f, beta = build(CASES["c3_16_d2"](), "f32")
     rhs = cuda(P.random_vector(t.n_leaves, 26))
-    xg, sg = gh.solve(rhs, tol=1e-6, precision="mixed", transpose=True)
-    xe, se = gh.solve(rhs, tol=1e-6, precision="mixed", transpose=True, eager=True)
+    xg, sg = gh.solve(rhs, tol=1e-6, precision="mixed", transpose=True, method=method)
+    xe, se = gh.solve(rhs, tol=1e-6, precision="mixed", transpose=True, eager=True, method=method)
     assert torch.equal(xg, xe) and sg.iterations == se.iterations and sg.kernels == se.kernels
 
 
