@@ -299,10 +299,29 @@ def _large(dev, stream, flush, args, peak):
                       "us_cell": round(v[2], 2), "us_quad": round(v[3], 2), "us_tile": round(v[4], 2)}
              for m, v in tun.items() if m >= 0}
     if args.only_large:
-        return {"workload": LARGE_WORKLOAD, "n0": args.large_n0, "leaves": g.n_leaves,
-                "value": round(g.n_leaves / (ms / 1e3) / 1e6, 3), "unit": UNIT, "ms_per_step": round(ms, 3),
-                "steps": steps, "iterations": sorted(its), "sweep_forms": forms,
-                "note": "--only-large (profiling aid)"}
+        out = {"workload": LARGE_WORKLOAD, "n0": args.large_n0, "leaves": g.n_leaves,
+               "value": round(g.n_leaves / (ms / 1e3) / 1e6, 3), "unit": UNIT, "ms_per_step": round(ms, 3),
+               "steps": steps, "iterations": sorted(its), "sweep_forms": forms,
+               "note": "--only-large (profiling aid)"}
+        if args.adjoint:
+            # one transpose solve (tables built and graph captured by an untimed first call),
+            # then one more inside the NVTX range 'adjoint' (kernel by kernel with --eager)
+            gp = x - torch.from_numpy(np.random.default_rng(8).standard_normal(g.n_leaves)).to(dev)
+            h.solve(gp, tol=1e-6, precision="mixed", stream=stream, transpose=True, max_iter=200)
+            torch.cuda.synchronize()
+            if args.nvtx:
+                torch.cuda.nvtx.range_push("adjoint")
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, sa = h.solve(gp, tol=1e-6, precision="mixed", stream=stream, transpose=True, max_iter=200,
+                            eager=args.eager)
+            e1.record(stream)
+            e1.synchronize()
+            if args.nvtx:
+                torch.cuda.nvtx.range_pop()
+            out["adjoint"] = {"ms": round(e0.elapsed_time(e1), 3), "iterations": sa.iterations}
+        return out
     # plain FP32 beside it (FP32 Krylov vectors, FP64 dot products)
     t32 = []
     for s_ in range(steps):
@@ -727,6 +746,8 @@ def main():
                     help="run the warm-up and the timed mixed solves only (profiling aid)")
     ap.add_argument("--eager", action="store_true",
                     help="launch the timed solves kernel by kernel (profiling aid; not the benchmark path)")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="with --only-large: also one transpose solve, in the NVTX range 'adjoint' (profiling aid)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
