@@ -320,13 +320,13 @@ int mu_at(const ocg_hier* h, int m) {
     return cells >= h->prm.mu_min_cells ? h->prm.mu : 1;
 }
 
-// The tail is the longest run of the coarsest levels m < 0 whose shared-memory image
-// (u, b and four coefficients per cell) fits in 200 KB.
-void choose_tail(ocg_hier* h, int which, size_t vbytes) {
+// The tail is the longest run of the coarsest levels m < 0, up to level max_top, whose
+// shared-memory image (u, b and four coefficients per cell) fits in 200 KB.
+void choose_tail(ocg_hier* h, int which, size_t vbytes, int max_top = -1) {
     const HostTree& H = h->t->H;
     int top = TAIL_NONE;
     int64_t cells = 0;
-    for (int m = H.mc; m < 0; ++m) {
+    for (int m = H.mc; m < 0 && m <= max_top; ++m) {
         const int64_t c = cells + H.L(m).ncell;
         if ((size_t)c * 6 * vbytes > 200 * 1024 || m - H.mc + 1 > MAXLEV) break;
         cells = c;
@@ -373,8 +373,7 @@ void choose_tail(ocg_hier* h, int which, size_t vbytes) {
         dfree(h->tail_sched);
         h->tail_sched = dev;
     } else {
-        // both value types share one hierarchy-owned buffer per type: keep the second in
-        // the args only (freed below through the pool list)
+        dfree(h->tail_sched2);
         h->tail_sched2 = dev;
     }
     A.sched = dev;

@@ -1677,16 +1677,22 @@ __device__ __forceinline__ int tail_parent(const TailLevel& L, const TailLevel& 
 
 enum { TP_SWEEP0 = 0, TP_SWEEP1 = 1, TP_FIXB = 2, TP_RESTRICT = 3, TP_PROLONG = 4 };
 
-// Colour sweep of a small tail level with one thread per cell (short dependency chains
-// when a level has no more cells than the block has threads).  Shared index of cell
-// (o, s) is sbase + s * no + o.
+// Colour sweep of a tail level over the colour's cells only: work item i is the k-th slot of
+// the colour (s = 2k + (parity(k) xor colour): 0, 3, 5, 6 or 1, 2, 4, 7) of octet o, so
+// the threads do no work on the other colour (one thread per octet would evaluate all 8
+// stencils).  The sum runs in the octet form's order (per axis: octet partner, then the
+// neighbouring octet), so both forms give the same bits.  Shared index of cell (o, s) is
+// sbase + s * no + o.
 template <class TV>
 __device__ __forceinline__ void tail_sweep_cells(const TailMem<TV>& M, const TailLevel& L, int colour) {
     const int ni = L.ni, no = ni * ni * ni;
-    for (int c = threadIdx.x; c < 8 * no; c += blockDim.x) {
-        const int s = c / no, o = c - s * no;
-        if ((__popc(s) & 1) != colour) continue;
-        const int q = L.sbase + c;
+    const bool p2 = (no & (no - 1)) == 0;
+    const int sh = p2 ? __ffs(no) - 1 : 0;
+    for (int i = threadIdx.x; i < 4 * no; i += blockDim.x) {
+        const int k = p2 ? (i >> sh) : i / no;
+        const int o = i - k * no;
+        const int s = 2 * k + ((__popc(k) & 1) ^ colour);
+        const int q = L.sbase + s * no + o;
         const TV dd = M.d[q];
         if (dd == TV(0)) continue;
         int crd[3];
@@ -1811,10 +1817,8 @@ __device__ __forceinline__ void tail_cycle(const TailArgs& A, int fas, int prolo
     for (int q = 0; q < A.nsched; ++q) {
         const int e = sch_sh ? ssched[q] : __ldg(A.sched + q);
         const int li = e >> 3, kind = e & 7;
-        if (kind <= TP_SWEEP1 && 8 * tail_noct(A.L[li]) <= (int)blockDim.x)
-            tail_sweep_cells<TV>(M, A.L[li], kind);
-        else
-            tail_pass<TV>(M, A, li, kind, scale);
+        if (kind <= TP_SWEEP1) tail_sweep_cells<TV>(M, A.L[li], kind);
+        else tail_pass<TV>(M, A, li, kind, scale);
     }
     for (int li = 0; li < A.nlev; ++li) {
         const TailLevel& L = A.L[li];
