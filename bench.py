@@ -253,6 +253,78 @@ LARGE_WORKLOAD = ("large differentiable solve: 128^3 root refined 3 times within
                   "divergence rhs")
 
 
+def _accuracy(dev, stream):
+    """The paper's accuracy studies (Sec. 4) at root grids 32/64/128: the Laplacian test
+    (composite operator in FP64 applied to (x^2+y^2+z^2) exp(-xyz); volume-weighted RMS
+    error on the leaves that touch no wall, split into the cells beside a T-junction face
+    and the rest) and the sinusoidal Poisson test (FP64 solve to 1e-10 for the solution
+    error; mixed solve to 1e-6 for iterations and residual reduction per iteration)."""
+    import math
+    import numpy as np
+    import torch
+    from paper_2604_18886_b300 import problems as P
+    from paper_2604_18886_b300 import solver as S
+
+    def rates(e):
+        return [round(math.log2(e[i] / e[i + 1]), 3) for i in range(len(e) - 1)]
+
+    sizes = (32, 64, 128)
+    lap = {}
+    for kind in ("uniform", "ball"):
+        rms, far, tmax = [], [], []
+        for n0 in sizes:
+            p = P.laplacian_problem(kind, n0)
+            g = S.Octree(p.desc)
+            f = g.faces()
+            h_ = S.Hierarchy(g, P.face_beta(p, f), p.bc, S.mg_params(coef="f64"))
+            lv = g.leaves()
+            h, x, y, z = P.leaf_centres(n0, lv)
+            fv = torch.from_numpy(P.laplacian_test_function(x, y, z)).to(dev)
+            e = -h_.apply_A(fv, stream=stream).cpu().numpy() / h ** 3 - P.laplacian_test_exact(x, y, z)
+            inner = P.interior_leaves(n0, lv)
+            tm = P.t_junction_leaves(g.n_leaves, lv, f)
+            rms.append(P.rms_v(h, e, inner))
+            far.append(P.rms_v(h, e, inner & ~tm))
+            tmax.append(float(np.abs(e[inner & tm]).max()) if np.any(inner & tm) else 0.0)
+            del h_
+        lap[kind] = {"n0": list(sizes), "rms": rms, "rms_rates": rates(rms), "rms_away_from_t": far,
+                     "rates_away_from_t": rates(far), "max_beside_t": tmax}
+    sin = {}
+    for kind in ("ball", "band"):
+        errs, its, red, ms, leaves = [], [], [], [], []
+        for n0 in sizes:
+            p = P.sinusoidal(kind, n0)
+            g = S.Octree(p.desc)
+            f = g.faces()
+            beta = P.face_beta(p, f)
+            lv = g.leaves()
+            b = torch.from_numpy(P.rhs(p, lv)).to(dev)
+            h64 = S.Hierarchy(g, beta, p.bc, S.mg_params(coef="f64"))
+            x, st = h64.solve(b, tol=1e-10, precision="fp64", max_iter=60, stream=stream)
+            h, xc, yc, zc = P.leaf_centres(n0, lv)
+            errs.append(P.rms_v(h, x.cpu().numpy() - P.exact_solution(p, xc, yc, zc)))
+            del h64
+            h32 = S.Hierarchy(g, beta, p.bc, S.mg_params(coef="f32"))
+            xm = torch.empty_like(b)
+            h32.solve(b, xm, tol=1e-6, precision="mixed", stream=stream)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, sm = h32.solve(b, xm, tol=1e-6, precision="mixed", stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            its.append(sm.iterations)
+            red.append(round(math.exp(-math.log(sm.hist[sm.iterations]) / sm.iterations), 2))
+            ms.append(round(e0.elapsed_time(e1), 3))
+            leaves.append(g.n_leaves)
+            del h32
+        sin[kind] = {"n0": list(sizes), "leaves": leaves, "rms_error": errs, "rates": rates(errs),
+                     "iterations_1e-6": its, "mean_reduction_per_iteration": red, "ms_mixed_1e-6": ms}
+    return {"laplacian": lap, "sinusoidal": sin,
+            "grids": "uniform n0^3; ball: refined once within 0.25 of the centre; band: refined twice "
+                     "within 0.05 of the sphere r = 0.25"}
+
+
 def _large(dev, stream, flush, args, peak):
     """The sine-band workload at full size: mixed solve to 1e-6 (timed), the red-black sweep
     on its finest level (per-launch events inside an unrolled graph of the same solve),
@@ -598,6 +670,7 @@ def run_ours(args):
     batched = None if args.no_batch else _batched(dev, stream, flush, args)
     # ---- the large sine-band workload (effective 1024^3)
     large = None if args.no_large else _large(dev, stream, flush, args, _peaks()[0])
+    accuracy = None if args.no_accuracy else _accuracy(dev, stream)
     # ---- end to end through the C ABI with host buffers
     bh = b.cpu().pin_memory()
     xh = torch.empty_like(bh).pin_memory()
@@ -654,6 +727,7 @@ def run_ours(args):
         "cut_cell": cut,
         "batched": batched,
         "large": large,
+        "accuracy": accuracy,
         "e2e": {"value": round(e2e, 3), "unit": UNIT, "h2d_bytes_per_step": tree.n_leaves * 8,
                 "d2h_bytes_per_step": tree.n_leaves * 8},
         "clocks": ck,
@@ -736,6 +810,7 @@ def main():
     ap.add_argument("--nvtx", action="store_true", help="NVTX range 'timed' around the timed mixed solves")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 64-tree form")
     ap.add_argument("--no-large", action="store_true", help="skip the large sine-band workload")
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the accuracy studies")
     ap.add_argument("--only-large", action="store_true",
                     help="run only the timed solves of the large sine-band workload (profiling aid)")
     ap.add_argument("--sweep", default="auto", choices=["auto", "octet", "cell", "quad", "tile"],

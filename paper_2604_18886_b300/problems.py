@@ -67,7 +67,7 @@ class Problem:
     desc: OctreeDesc
     bc: tuple                 # 6 wall codes
     beta: str = "one"         # "one" or "cut" (fluid fraction of the solid geometry)
-    rhs: str = "zero"         # "sin_dirichlet", "exp_sin_cos", "divergence", "normal"
+    rhs: str = "zero"         # "sin_dirichlet", "exp_sin_cos", "sinusoidal", "divergence", "normal"
     seed: int = 0
     mode: str = "mixed"       # suggested precision mode
     tol: float = 1e-6
@@ -261,6 +261,9 @@ def exact_solution(p: Problem, x, y, z):
         return np.sin(math.pi * x) * np.sin(math.pi * y) * np.sin(math.pi * z)
     if p.rhs == "exp_sin_cos":
         return np.exp(x) * np.sin(2 * math.pi * y) * np.cos(2 * math.pi * z)
+    if p.rhs == "sinusoidal":
+        # lap p = 4 pi G A sin(2 pi x) sin(2 pi y) sin(2 pi z) on the unit cube, G A = 1
+        return -np.sin(2 * math.pi * x) * np.sin(2 * math.pi * y) * np.sin(2 * math.pi * z) / (3 * math.pi)
     raise ValueError("no closed-form solution for rhs kind %r" % p.rhs)
 
 
@@ -270,7 +273,88 @@ def _source(p: Problem, x, y, z):
         return 3 * math.pi ** 2 * exact_solution(p, x, y, z)
     if p.rhs == "exp_sin_cos":
         return (8 * math.pi ** 2 - 1.0) * exact_solution(p, x, y, z)
+    if p.rhs == "sinusoidal":
+        return 12 * math.pi ** 2 * exact_solution(p, x, y, z)
     raise ValueError(p.rhs)
+
+
+# ----------------------------------------------------------------------------------
+# accuracy studies (Sec. 4: Laplacian accuracy and sinusoidal Poisson tests)
+
+ACCURACY_GRIDS = ("uniform", "ball", "band")
+
+
+def accuracy_desc(kind: str, n0: int) -> OctreeDesc:
+    """Grids of the accuracy studies: uniform n0^3; n0^3 with cells whose centre lies
+    within 0.25 of the cube centre refined once; n0^3 refined twice within 0.05 of the
+    sphere of radius 0.25 about the centre."""
+    if kind == "uniform":
+        return OctreeDesc(n0, 0)
+    if kind == "ball":
+        return OctreeDesc(n0, 1, REFINE_BALL_CENTRE, spheres=[(0.5, 0.5, 0.5, 0.25)])
+    if kind == "band":
+        return OctreeDesc(n0, 2, REFINE_SDF_BAND, band=0.05, spheres=[(0.5, 0.5, 0.5, 0.25)])
+    raise ValueError(kind)
+
+
+def sinusoidal(kind: str, n0: int) -> Problem:
+    """Sinusoidal Poisson test: lap p = 4 pi G A sin(2 pi x) sin(2 pi y) sin(2 pi z)
+    (G A = 1) on an accuracy grid; p vanishes on the walls, which are Dirichlet."""
+    return Problem("sin_%s%d" % (kind, n0), accuracy_desc(kind, n0), (DIRICHLET,) * 6, beta="one",
+                   rhs="sinusoidal", mode="mixed", tol=1e-6)
+
+
+def laplacian_problem(kind: str, n0: int) -> Problem:
+    """Laplacian accuracy test grid: beta = 1, Neumann walls (the outermost cell layer
+    is the boundary; errors are measured on the cells that do not touch a wall)."""
+    return Problem("lap_%s%d" % (kind, n0), accuracy_desc(kind, n0), (NEUMANN,) * 6, beta="one")
+
+
+def laplacian_test_function(x, y, z):
+    """f = (x^2 + y^2 + z^2) exp(-xyz)."""
+    return (x * x + y * y + z * z) * np.exp(-x * y * z)
+
+
+def laplacian_test_exact(x, y, z):
+    """lap f for laplacian_test_function, differentiated from its definition:
+    exp(-xyz) (6 - 12 xyz + (x^2 + y^2 + z^2)(x^2 y^2 + y^2 z^2 + z^2 x^2))."""
+    r2 = x * x + y * y + z * z
+    return np.exp(-x * y * z) * (6.0 - 12.0 * x * y * z + r2 * (x * x * y * y + y * y * z * z + z * z * x * x))
+
+
+def leaf_centres(n0: int, leaves):
+    """(h, x, y, z) of the leaves (canonical order)."""
+    d = np.asarray(leaves["depth"]).astype(np.float64)
+    h = 1.0 / (n0 * 2.0 ** d)
+    return h, (np.asarray(leaves["i"]) + 0.5) * h, (np.asarray(leaves["j"]) + 0.5) * h, \
+        (np.asarray(leaves["k"]) + 0.5) * h
+
+
+def interior_leaves(n0: int, leaves):
+    """Mask of the leaves that touch no domain wall."""
+    nd = n0 * 2 ** np.asarray(leaves["depth"]).astype(np.int64)
+    i, j, k = (np.asarray(leaves[c]) for c in ("i", "j", "k"))
+    return (i > 0) & (j > 0) & (k > 0) & (i < nd - 1) & (j < nd - 1) & (k < nd - 1)
+
+
+def t_junction_leaves(n_leaves: int, leaves, faces):
+    """Mask of the leaves on either side of a T-junction face (the two sides of the face
+    at different depths)."""
+    dm = np.asarray(leaves["depth"])[np.asarray(faces["minus"])]
+    dp = np.asarray(leaves["depth"])[np.asarray(faces["plus"])]
+    t = dm != dp
+    mask = np.zeros(n_leaves, bool)
+    mask[np.asarray(faces["minus"])[t]] = True
+    mask[np.asarray(faces["plus"])[t]] = True
+    return mask
+
+
+def rms_v(h, e, mask=None):
+    """Volume-weighted RMS of e over the masked leaves (cell volume h^3)."""
+    V = h ** 3
+    if mask is not None:
+        V, e = V[mask], e[mask]
+    return math.sqrt(float(np.sum(V * e * e) / np.sum(V)))
 
 
 def rhs(p: Problem, leaves, faces=None, beta=None) -> np.ndarray:
@@ -284,7 +368,7 @@ def rhs(p: Problem, leaves, faces=None, beta=None) -> np.ndarray:
     "normal": N(0,1) per leaf, mean removed when every wall is Neumann.
     """
     n = len(leaves["depth"])
-    if p.rhs in ("sin_dirichlet", "exp_sin_cos"):
+    if p.rhs in ("sin_dirichlet", "exp_sin_cos", "sinusoidal"):
         h, x, y, z = _leaf_geometry(p, leaves)
         b = h ** 3 * _source(p, x, y, z)
         nd = p.desc.n0 * 2 ** leaves["depth"].astype(np.int64)

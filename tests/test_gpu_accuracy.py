@@ -1,0 +1,109 @@
+"""The paper's accuracy studies (Sec. 4) through the library: the Laplacian accuracy test
+(the composite operator applied to f = (x^2 + y^2 + z^2) exp(-xyz)) and the sinusoidal
+Poisson test, at root grids up to 128^3.  Parity with the oracle at a small size (FP64
+apply 1e-12, FP64 solve 1e-8), then the convergence orders the oracle's tests pin at
+small sizes: second order on uniform grids and away from T-junctions, O(1) pointwise
+error beside T-junction faces; second-order solution error and a residual reduction of
+more than 10 per PCG iteration, independent of the resolution.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import octree as O
+from oracle import operator as OP
+from oracle import pcg
+from paper_2604_18886_b300 import problems as P
+from paper_2604_18886_b300 import solver as S
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _cuda(x):
+    return torch.from_numpy(np.ascontiguousarray(x, np.float64)).cuda()
+
+
+def _gpu(p, coef="f64"):
+    g = S.Octree(p.desc)
+    f = g.faces()
+    beta = P.face_beta(p, f)
+    return g, f, S.Hierarchy(g, beta, p.bc, S.mg_params(coef=coef))
+
+
+def _lap_errors(kind, n0):
+    p = P.laplacian_problem(kind, n0)
+    g, f, h_ = _gpu(p)
+    lv = g.leaves()
+    h, x, y, z = P.leaf_centres(n0, lv)
+    Af = h_.apply_A(_cuda(P.laplacian_test_function(x, y, z))).cpu().numpy()
+    e = -Af / h ** 3 - P.laplacian_test_exact(x, y, z)
+    inner = P.interior_leaves(n0, lv)
+    tm = P.t_junction_leaves(g.n_leaves, lv, f)
+    tmax = float(np.abs(e[inner & tm]).max()) if np.any(inner & tm) else 0.0
+    return P.rms_v(h, e, inner), P.rms_v(h, e, inner & ~tm), tmax
+
+
+def _rates(errs):
+    return [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+
+
+def test_laplacian_apply_matches_oracle():
+    p = P.laplacian_problem("ball", 16)
+    t = O.Octree(p.desc)
+    fo = t.faces()
+    H = OP.Hierarchy(t, P.face_beta(p, fo), p.bc)
+    h, x, y, z = P.leaf_centres(16, t.leaves)
+    fv = P.laplacian_test_function(x, y, z)
+    g, f, hg = _gpu(p)
+    y_gpu = hg.apply_A(_cuda(fv)).cpu().numpy()
+    ref = H.A @ fv
+    assert np.abs(y_gpu - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_laplacian_orders_at_large_sizes():
+    uni = [_lap_errors("uniform", n0)[0] for n0 in (32, 64, 128)]
+    assert min(_rates(uni)) > 1.9, uni
+    ball = [_lap_errors("ball", n0) for n0 in (32, 64, 128)]
+    far = [b[1] for b in ball]
+    tmax = [b[2] for b in ball]
+    assert min(_rates(far)) > 1.9, far
+    assert max(tmax) < 10.0 and tmax[-1] < 1.2 * tmax[0], tmax
+
+
+def test_sinusoidal_solve_matches_oracle():
+    p = P.sinusoidal("ball", 16)
+    t = O.Octree(p.desc)
+    fo = t.faces()
+    H = OP.Hierarchy(t, P.face_beta(p, fo), p.bc)
+    b = P.rhs(p, t.leaves)
+    xo, _, _ = pcg.pcg(H, b, tol=1e-12)
+    g, f, hg = _gpu(p)
+    x, st = hg.solve(_cuda(b), tol=1e-10, precision="fp64")
+    assert st.converged
+    assert np.abs(x.cpu().numpy() - xo).max() <= 1e-8 * np.abs(xo).max()
+
+
+@pytest.mark.parametrize("kind", ["ball", "band"])
+def test_sinusoidal_orders_and_residual_decay_at_large_sizes(kind):
+    errs, its = [], []
+    for n0 in (32, 64, 128):
+        p = P.sinusoidal(kind, n0)
+        g, f, h64 = _gpu(p)
+        lv = g.leaves()
+        b = _cuda(P.rhs(p, lv))
+        x, st = h64.solve(b, tol=1e-10, precision="fp64", max_iter=60)
+        assert st.converged
+        h, xc, yc, zc = P.leaf_centres(n0, lv)
+        errs.append(P.rms_v(h, x.cpu().numpy() - P.exact_solution(p, xc, yc, zc)))
+        del h64
+        g2, f2, h32 = _gpu(p, "f32")
+        _, sm = h32.solve(b, tol=1e-6, precision="mixed")
+        assert sm.converged and sm.true_rel_res <= 1.5e-6
+        its.append(sm.iterations)
+        red = math.exp(-math.log(sm.hist[sm.iterations]) / sm.iterations)
+        assert red > 5.0 if kind == "band" else red > 10.0, (n0, red)
+    assert min(_rates(errs)) > 1.9, errs
+    assert max(its) - min(its) <= 2 and max(its) <= 8, its

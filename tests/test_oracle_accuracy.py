@@ -1,0 +1,80 @@
+"""The paper's accuracy studies (Sec. 4) on the oracle: the Laplacian accuracy test and the
+sinusoidal Poisson test, on uniform and refined grids.
+
+Laplacian: the integrated operator A (beta = 1, Neumann walls) applied to
+f = (x^2 + y^2 + z^2) exp(-xyz); the numerical Laplacian of leaf i is -(A f)_i / V_i and
+the error is measured against the exact Laplacian on the leaves that touch no wall.  On
+uniform grids and on the cells away from T-junctions it converges at second order; on the
+cells beside a T-junction face the pointwise error stays O(1) (the ghost value makes the
+T flux first order), while their share of the volume halves with each refinement.
+
+Sinusoidal: lap p = 4 pi sin(2 pi x) sin(2 pi y) sin(2 pi z), Dirichlet walls (p vanishes
+there); Alg. 1 to 1e-10; the solution error is second order and the residual falls by
+more than a factor 10 per iteration (the paper reports about 20, Sec. 4.3).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import octree as O
+from oracle import operator as OP
+from oracle import pcg
+from paper_2604_18886_b300 import problems as P
+
+
+def _setup(p):
+    t = O.Octree(p.desc)
+    f = t.faces()
+    beta = P.face_beta(p, f)
+    return t, f, OP.Hierarchy(t, beta, p.bc)
+
+
+def _laplacian_errors(kind, n0):
+    p = P.laplacian_problem(kind, n0)
+    t, f, H = _setup(p)
+    h, x, y, z = P.leaf_centres(n0, t.leaves)
+    e = -(H.A @ P.laplacian_test_function(x, y, z)) / h ** 3 - P.laplacian_test_exact(x, y, z)
+    inner = P.interior_leaves(n0, t.leaves)
+    tm = P.t_junction_leaves(t.n_leaves, t.leaves, f)
+    far = inner & ~tm
+    tmax = float(np.abs(e[inner & tm]).max()) if np.any(inner & tm) else 0.0
+    return P.rms_v(h, e, inner), P.rms_v(h, e, far), tmax, float(np.sum(h[inner & tm] ** 3) / np.sum(h[inner] ** 3))
+
+
+def _rates(errs):
+    return [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+
+
+def test_laplacian_second_order_on_uniform_grids():
+    errs = [_laplacian_errors("uniform", n0)[0] for n0 in (8, 16, 32)]
+    assert min(_rates(errs)) > 1.8, errs
+
+
+def test_laplacian_on_refined_grids_second_order_away_from_t_junctions():
+    res = [_laplacian_errors("ball", n0) for n0 in (8, 16, 32)]
+    far = [r[1] for r in res]
+    assert min(_rates(far)) > 1.8, far
+    # beside T-junction faces the error is O(1) (bounded, not decaying) on a volume share
+    # that halves with each refinement
+    tmax = [r[2] for r in res]
+    share = [r[3] for r in res]
+    assert 1.0 < tmax[-1] < 1.2 * tmax[-2] and tmax[-1] < 10.0, tmax
+    assert share[2] < 0.6 * share[1] < 0.6 * 0.6 * share[0], share
+
+
+@pytest.mark.parametrize("kind", ["uniform", "ball"])
+def test_sinusoidal_poisson_second_order_and_fast_residual_decay(kind):
+    errs, its = [], []
+    for n0 in (8, 16, 32):
+        p = P.sinusoidal(kind, n0)
+        t, f, H = _setup(p)
+        b = P.rhs(p, t.leaves)
+        x, k, hist = pcg.pcg(H, b, tol=1e-10)
+        h, xc, yc, zc = P.leaf_centres(n0, t.leaves)
+        errs.append(P.rms_v(h, x - P.exact_solution(p, xc, yc, zc)))
+        its.append(next(i for i, v in enumerate(hist) if v <= 1e-6))
+        red = math.exp(-math.log(hist[k]) / k)   # mean reduction per iteration
+        assert red > 10.0, (n0, red, hist)
+    assert min(_rates(errs)) > 1.9, errs
+    assert max(its) <= 7 and max(its) - min(its) <= 2, its
