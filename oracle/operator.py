@@ -73,9 +73,13 @@ class Hierarchy:
     """All levels m = D (finest) .. mc (coarsest) of the octree multigrid.
 
     Parameters: tree (oracle.octree.Octree), beta per canonical face, bc (6 wall codes),
-    alpha (restriction scaling, Sec. 3.3: alpha = 2)."""
+    alpha (restriction scaling, Sec. 3.3: alpha = 2), coarse_beta: None for the
+    algebraically consistent coarsening of Alg. 3 (the paper's method); for the
+    geometric-multigrid ablation of Sec. 3.3, a function (m, axis, i, j, k) -> beta of
+    the - face of cells (i, j, k) of level m along axis, with which every cell that has
+    children is rediscretised at its own resolution (`_rediscretise`)."""
 
-    def __init__(self, tree, beta, bc, alpha=2.0):
+    def __init__(self, tree, beta, bc, alpha=2.0, coarse_beta=None):
         self.tree = tree
         self.D = tree.D
         self.mc = tree.min_level()
@@ -95,6 +99,8 @@ class Hierarchy:
         self._face_lookup()
         self._fill_leaves()
         self._coarsen_all()
+        if coarse_beta is not None:
+            self._rediscretise(coarse_beta)
         self._assemble_all()
         self._composite()
 
@@ -259,6 +265,36 @@ class Hierarchy:
         """Every cell with children gets Alg. 3 of its children, finest first."""
         for m in range(self.D, self.mc, -1):
             self.coarsen_level(m)
+
+    def _rediscretise(self, coarse_beta):
+        """Geometric multigrid (Sec. 3.3): each cell with children takes the coefficients
+        the grid discretisation gives it directly at its size H, without reference to the
+        finer operator: w = beta_face H on each face (beta_face from coarse_beta), the
+        wall weight on a wall face (0 Neumann, 2H Dirichlet, as for leaves), c = the sum
+        of its six face weights (0 kept for a cell without active children).  Leaves keep
+        their coefficients; the - face coefficient of a leaf beside such a cell is the same
+        face's weight, so each face keeps one value."""
+        for m in range(self.D - 1, self.mc - 1, -1):
+            L = self.levels[m]
+            I = np.nonzero(L.children[:, 0] >= 0)[0]
+            if len(I) == 0:
+                continue
+            H = 1.0 / (self.tree.n0 * 2.0 ** m)
+            crd = (L.i[I], L.j[I], L.k[I])
+            total = np.zeros(len(I))
+            for a in range(3):
+                for side in (0, 1):
+                    c = [crd[0].copy(), crd[1].copy(), crd[2].copy()]
+                    if side:
+                        c[a] = c[a] + 1          # the + face is the - face of (i + e_a)
+                    wall = (c[a] - 1 < 0) if side == 0 else (c[a] >= L.N)
+                    wb = 2.0 * H if self.bc[2 * a + side] == 1 else 0.0     # 1: Dirichlet
+                    beta = np.asarray(coarse_beta(m, a, c[0], c[1], c[2]), np.float64)
+                    w = np.where(wall, wb, beta * H)
+                    total += w
+                    if side == 0:
+                        L.cm[a, I] = -w
+            L.c[I] = np.where(L.c[I] != 0.0, total, 0.0)
 
     # ------------------------------------------------------------------ matrices
     def _assemble_all(self):
