@@ -155,7 +155,23 @@ typedef struct {
                               (leaves and inner, padding excluded), once otherwise — a
                               W-cycle on the large levels, a V-cycle on the small ones whose
                               cost on the GPU is launch latency.  Negative: EINVAL. */
+    int32_t coarsening;    /* OCG_COARSEN_ALGEBRAIC (Alg. 3: the paper's algebraically
+                              consistent coarsening) or OCG_COARSEN_GEOMETRIC (the geometric
+                              multigrid of Sec. 3.3, for ablation): every cell with children
+                              on the levels below the finest takes the coefficients the grid
+                              gives it at its own size H: w = beta H per face, beta the fluid
+                              fraction of the face from the SDF of the description's spheres
+                              and boxes (positive in fluid) at its four corners, split into
+                              two triangles along the face's (0,0)-(1,1) diagonal in the
+                              other two axes, phi linear on each, positive area exact,
+                              clamped to [1e-3, 1] and rounded to FP32; a wall face 2H
+                              (Dirichlet) or 0 (Neumann); c = the sum of the six (0 kept
+                              where Alg. 3 gives 0).  For cut-cell problems whose face beta
+                              is that fraction.  Needs OCG_REFINE_SDF_BAND; else EINVAL. */
+    int32_t reserved;      /* must be 0 */
 } ocg_mg_params;
+#define OCG_COARSEN_ALGEBRAIC 0
+#define OCG_COARSEN_GEOMETRIC 1
 
 #define OCG_SWEEP_AUTO (-1)
 #define OCG_SWEEP_OCTET 0      /* one thread per octet (8 cells in registers) */

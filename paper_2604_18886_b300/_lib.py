@@ -34,7 +34,11 @@ class MGParams(C.Structure):
     _fields_ = [("mu", C.c_int32), ("nu_pre", C.c_int32), ("nu_post", C.c_int32),
                 ("nu_coarsest", C.c_int32), ("beta_restrict", C.c_double), ("alpha", C.c_double),
                 ("coef_dtype", C.c_int32), ("bf16_coarse", C.c_int32), ("sweep_form", C.c_int32),
-                ("mu_min_cells", C.c_int32)]
+                ("mu_min_cells", C.c_int32), ("coarsening", C.c_int32), ("reserved", C.c_int32)]
+
+
+OCG_COARSEN_ALGEBRAIC = 0
+OCG_COARSEN_GEOMETRIC = 1
 
 
 OCG_SOLVE_EAGER = 1

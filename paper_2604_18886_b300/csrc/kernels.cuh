@@ -554,6 +554,23 @@ __global__ void k_pupdate(TO* __restrict__ p, const TZ* __restrict__ z, const do
 
 // ----------------------------------------------------------------- setup kernels (FP64)
 
+// Geometric coarsening (ablation): cells idx[q] take d[q] (only where Alg. 3 gave a nonzero
+// diagonal, i.e. the cell has active children) and the - face coefficients cx, cy, cz.
+__global__ void k_set_coefs(int n, const int64_t* __restrict__ idx, const double* __restrict__ d,
+                            const double* __restrict__ cx, const double* __restrict__ cy,
+                            const double* __restrict__ cz, double* __restrict__ D, double* __restrict__ CX,
+                            double* __restrict__ CY, double* __restrict__ CZ) {
+    pdl_enter();
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const int64_t g = idx[q];
+    if (D[g] != 0.0) D[g] = d[q];
+    CX[g] = cx[q];
+    CY[g] = cy[q];
+    CZ[g] = cz[q];
+}
+
+
 // -beta_f h_f into the face's destination: the - face coefficient of its + cell, or the
 // T record weight of a fine leaf's + face.  Flags a negative / non-finite beta.
 __global__ void k_face_scatter(const float* __restrict__ beta, const int64_t* __restrict__ slot,

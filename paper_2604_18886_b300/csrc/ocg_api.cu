@@ -1325,6 +1325,58 @@ int ocg_octree_export_level(const ocg_octree* t, int32_t m, int64_t* n, int32_t*
     });
 }
 
+// Geometric multigrid (ablation of Sec. 3.3): every cell with children on the levels below
+// the finest gets the coefficients of the grid at its own size H (ocg_mg_params.coarsening),
+// computed on the host from the description's solids and written over Alg. 3's FP64 set.
+void rediscretise(ocg_hier* h, cudaStream_t st) {
+    const HostTree& H = h->t->H;
+    std::vector<int64_t> idx;
+    std::vector<double> vd, vc[3];
+    for (int m = H.D - 1; m >= H.mc; --m) {
+        const LevelMeta& l = H.L(m);
+        const double hm = 1.0 / ((double)H.n0 * std::ldexp(1.0, m));
+        const int64_t N = l.N;
+        const size_t base = idx.size();
+        std::vector<int64_t> cells;
+        for (int64_t g = l.off; g < l.off + l.ncell; ++g)
+            if (H.child_oct[g] >= 0 && (H.cell_flags[g] & 2)) cells.push_back(g);
+        idx.resize(base + cells.size());
+        vd.resize(idx.size());
+        for (auto& v : vc) v.resize(idx.size());
+#pragma omp parallel for schedule(static)
+        for (int64_t q = 0; q < (int64_t)cells.size(); ++q) {
+            const int64_t g = cells[q];
+            int64_t c[3];
+            H.cell_coords(m, g, c[0], c[1], c[2]);
+            double total = 0.0;
+            for (int a = 0; a < 3; ++a) {
+                for (int side = 0; side < 2; ++side) {
+                    int64_t p[3] = {c[0], c[1], c[2]};
+                    p[a] += side;                        // the + face is the - face of (c + e_a)
+                    const bool wall = side == 0 ? p[a] - 1 < 0 : p[a] >= N;
+                    const double w = wall ? (h->bc[2 * a + side] == OCG_BC_DIRICHLET ? 2.0 * hm : 0.0)
+                                          : (double)face_beta_geometric(H.desc, m, a, p[0], p[1], p[2]) * hm;
+                    total += w;
+                    if (side == 0) vc[a][base + q] = -w;
+                }
+            }
+            idx[base + q] = g;
+            vd[base + q] = total;
+        }
+    }
+    const int64_t n = (int64_t)idx.size();
+    if (n == 0) return;
+    int64_t* didx = dupload(idx);
+    double* dv[4] = {dupload(vd), dupload(vc[0]), dupload(vc[1]), dupload(vc[2])};
+    launch_k(k_set_coefs, nblk(n), BLK, 0, st, (int)n, (const int64_t*)didx, (const double*)dv[0],
+             (const double*)dv[1], (const double*)dv[2], (const double*)dv[3], h->c64[0], h->c64[1], h->c64[2],
+             h->c64[3]);
+    ck_launch("rediscretise");
+    ck(cudaStreamSynchronize(st), "setup sync");
+    dfree(didx);
+    for (double* v : dv) dfree(v);
+}
+
 int ocg_setup_hierarchy(const ocg_octree* t, const float* beta, const int32_t bc[6], const ocg_mg_params* prm,
                         void* stream, ocg_hier** out) {
     return guard([&] {
@@ -1335,6 +1387,11 @@ int ocg_setup_hierarchy(const ocg_octree* t, const float* beta, const int32_t bc
             !(prm->alpha > 0) || !std::isfinite(prm->beta_restrict))
             throw Status(OCG_EINVAL, "invalid multigrid parameters");
         if (prm->coef_dtype != OCG_F64 && prm->coef_dtype != OCG_F32) throw Status(OCG_EINVAL, "coef_dtype");
+        if (prm->coarsening != OCG_COARSEN_ALGEBRAIC && prm->coarsening != OCG_COARSEN_GEOMETRIC)
+            throw Status(OCG_EINVAL, "coarsening");
+        if (prm->coarsening == OCG_COARSEN_GEOMETRIC && t->H.desc.refine != OCG_REFINE_SDF_BAND)
+            throw Status(OCG_EINVAL, "geometric coarsening needs an OCG_REFINE_SDF_BAND description");
+        if (prm->reserved != 0) throw Status(OCG_EINVAL, "reserved must be 0");
         if (prm->sweep_form < OCG_SWEEP_AUTO || prm->sweep_form > OCG_SWEEP_TILE)
             throw Status(OCG_EINVAL, "sweep_form");
         if (t->H.D - t->H.mc + 1 > 2 * MAXLEV) throw Status(OCG_EINVAL, "too many levels");
@@ -1395,6 +1452,7 @@ int ocg_setup_hierarchy(const ocg_octree* t, const float* beta, const int32_t bc
         ck(cudaStreamSynchronize(st), "setup sync");
         dfree(cm); dfree(dh); dfree(derr);
         if (herr) throw Status(OCG_EINVAL, "face beta must be finite and >= 0");
+        if (prm->coarsening == OCG_COARSEN_GEOMETRIC) rediscretise(h.get(), st);
         if (prm->coef_dtype == OCG_F32) {
             for (int q = 0; q < 4; ++q) {
                 h->c32[q] = dalloc<float>(H.ncell);

@@ -98,6 +98,59 @@ void det_sincos(double a, double& sa, double& ca) {
 }
 }  // namespace
 
+// Signed distance of the fluid region for OCG_REFINE_SDF_BAND (positive in fluid, negative
+// in the solids): min over the spheres |x - c| - r and the boxes' signed distances.
+double solid_sdf(const ocg_octree_desc& d, double x, double y, double z) {
+    double phi = INFINITY;
+    for (int q = 0; q < d.n_spheres; ++q) {
+        const double dx = x - d.spheres[q][0], dy = y - d.spheres[q][1], dz = z - d.spheres[q][2];
+        const double s = dx * dx + dy * dy;
+        const double v = std::sqrt(s + dz * dz) - d.spheres[q][3];
+        phi = std::fmin(phi, v);
+    }
+    for (int q = 0; q < d.n_boxes; ++q) {
+        const double* b = d.boxes[q];
+        const double qx = std::fabs(x - 0.5 * (b[0] + b[3])) - 0.5 * (b[3] - b[0]);
+        const double qy = std::fabs(y - 0.5 * (b[1] + b[4])) - 0.5 * (b[4] - b[1]);
+        const double qz = std::fabs(z - 0.5 * (b[2] + b[5])) - 0.5 * (b[5] - b[2]);
+        const double mx = std::fmax(qx, 0.0), my = std::fmax(qy, 0.0), mz = std::fmax(qz, 0.0);
+        const double s = mx * mx + my * my;
+        const double outside = std::sqrt(s + mz * mz);
+        const double inside = std::fmin(std::fmax(qx, std::fmax(qy, qz)), 0.0);
+        phi = std::fmin(phi, outside + inside);
+    }
+    return phi;
+}
+
+// Area fraction of {phi > 0} on a triangle where phi is linear with vertex values a, b, c.
+static double tri_positive_fraction(double a, double b, double c) {
+    double lo = a, mid = b, hi = c;
+    if (lo > mid) std::swap(lo, mid);
+    if (mid > hi) std::swap(mid, hi);
+    if (lo > mid) std::swap(lo, mid);
+    if (lo > 0.0) return 1.0;
+    if (hi > 0.0 && mid <= 0.0) return hi * hi / ((hi - lo) * (hi - mid));       // one corner positive
+    if (mid > 0.0 && lo <= 0.0) return 1.0 - lo * lo / ((mid - lo) * (hi - lo)); // one corner negative
+    return 0.0;
+}
+
+float face_beta_geometric(const ocg_octree_desc& d, int m, int axis, int64_t i, int64_t j, int64_t k) {
+    const double h = 1.0 / ((double)d.n0 * std::ldexp(1.0, m));
+    const double base[3] = {(double)i * h, (double)j * h, (double)k * h};
+    const int u = axis == 0 ? 1 : 0, v = axis == 2 ? 1 : 2;
+    auto corner = [&](int du, int dv) {
+        double q[3] = {base[0], base[1], base[2]};
+        q[u] = q[u] + (du ? h : 0.0);
+        q[v] = q[v] + (dv ? h : 0.0);
+        return solid_sdf(d, q[0], q[1], q[2]);
+    };
+    const double p00 = corner(0, 0), p10 = corner(1, 0), p11 = corner(1, 1), p01 = corner(0, 1);
+    const double t1 = tri_positive_fraction(p00, p10, p11);
+    const double t2 = tri_positive_fraction(p00, p11, p01);
+    const double f = 0.5 * (t1 + t2);
+    return (float)std::fmin(std::fmax(f, 1e-3), 1.0);
+}
+
 // Refinement predicate (documented in ocg.h); no FMA contraction in this file.
 static bool refine_pred(const ocg_octree_desc& d, int depth, int64_t i, int64_t j, int64_t k) {
     const double nd = (double)((int64_t)d.n0 << depth);
@@ -111,24 +164,7 @@ static bool refine_pred(const ocg_octree_desc& d, int depth, int64_t i, int64_t 
         return (s + dz * dz) < r * r;
     }
     if (d.refine == OCG_REFINE_SDF_BAND) {
-        double phi = INFINITY;
-        for (int q = 0; q < d.n_spheres; ++q) {
-            const double dx = x - d.spheres[q][0], dy = y - d.spheres[q][1], dz = z - d.spheres[q][2];
-            const double s = dx * dx + dy * dy;
-            const double v = std::sqrt(s + dz * dz) - d.spheres[q][3];
-            phi = std::fmin(phi, v);
-        }
-        for (int q = 0; q < d.n_boxes; ++q) {
-            const double* b = d.boxes[q];
-            const double qx = std::fabs(x - 0.5 * (b[0] + b[3])) - 0.5 * (b[3] - b[0]);
-            const double qy = std::fabs(y - 0.5 * (b[1] + b[4])) - 0.5 * (b[4] - b[1]);
-            const double qz = std::fabs(z - 0.5 * (b[2] + b[5])) - 0.5 * (b[5] - b[2]);
-            const double mx = std::fmax(qx, 0.0), my = std::fmax(qy, 0.0), mz = std::fmax(qz, 0.0);
-            const double s = mx * mx + my * my;
-            const double outside = std::sqrt(s + mz * mz);
-            const double inside = std::fmin(std::fmax(qx, std::fmax(qy, qz)), 0.0);
-            phi = std::fmin(phi, outside + inside);
-        }
+        const double phi = solid_sdf(d, x, y, z);
         const double slack = d.band + (0.5 * std::sqrt(3.0)) * (1.0 / nd);
         return std::fabs(phi) < slack;
     }

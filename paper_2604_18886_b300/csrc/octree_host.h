@@ -94,6 +94,14 @@ struct AdjointTopology {
 };
 void build_adjoint_topology(const HostTree& T, AdjointTopology& out);
 
+// Geometry of OCG_REFINE_SDF_BAND descriptions: the solids' signed distance (positive in
+// fluid), and the clamped FP32 fluid fraction of the - face along `axis` of cell (i, j, k)
+// of level m (cell size 1 / (n0 2^m)): the face split into two triangles along its
+// (0,0)-(1,1) diagonal in the two other axes (increasing order), phi linear on each from
+// its corner values, the positive area exact; max(1e-3, min(1, f)) rounded to FP32.
+double solid_sdf(const ocg_octree_desc& d, double x, double y, double z);
+float face_beta_geometric(const ocg_octree_desc& d, int m, int axis, int64_t i, int64_t j, int64_t k);
+
 uint64_t morton3(uint64_t i, uint64_t j, uint64_t k);
 void demorton3(uint64_t key, uint64_t& i, uint64_t& j, uint64_t& k);
 

@@ -116,10 +116,14 @@ SWEEP_FORM_NAMES = {L.OCG_SWEEP_OCTET: "octet", L.OCG_SWEEP_CELL: "cell", L.OCG_
 
 
 def mg_params(mu=1, nu_pre=2, nu_post=2, nu_coarsest=10, beta=2.0, alpha=2.0, coef="f32",
-              bf16_coarse=False, sweep="auto", mu_min_cells=0) -> L.MGParams:
+              bf16_coarse=False, sweep="auto", mu_min_cells=0, coarsening="algebraic") -> L.MGParams:
+    """coarsening: "algebraic" (Alg. 3, the paper's method) or "geometric" (the geometric
+    multigrid of Sec. 3.3, an ablation: cells with children rediscretised from the
+    description's solids at their own resolution)."""
     p = L.MGParams()
     p.mu, p.nu_pre, p.nu_post, p.nu_coarsest = mu, nu_pre, nu_post, nu_coarsest
     p.mu_min_cells = mu_min_cells
+    p.coarsening = {"algebraic": L.OCG_COARSEN_ALGEBRAIC, "geometric": L.OCG_COARSEN_GEOMETRIC}[coarsening]
     p.beta_restrict, p.alpha = beta, alpha
     p.coef_dtype = L.OCG_F64 if coef == "f64" else L.OCG_F32
     p.bf16_coarse = 1 if bf16_coarse else 0
