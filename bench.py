@@ -285,7 +285,7 @@ def _accuracy(dev, stream):
 
     sizes = (32, 64, 128)
     lap = {}
-    for kind in ("uniform", "ball"):
+    for kind in ("uniform", "ball", "star"):
         rms, far, tmax = [], [], []
         for n0 in sizes:
             p = P.laplacian_problem(kind, n0)
@@ -305,7 +305,7 @@ def _accuracy(dev, stream):
         lap[kind] = {"n0": list(sizes), "rms": rms, "rms_rates": rates(rms), "rms_away_from_t": far,
                      "rates_away_from_t": rates(far), "max_beside_t": tmax}
     sin = {}
-    for kind in ("ball", "band"):
+    for kind in ("ball", "band", "star"):
         errs, its, red, ms, leaves = [], [], [], [], []
         for n0 in sizes:
             p = P.sinusoidal(kind, n0)
@@ -337,7 +337,8 @@ def _accuracy(dev, stream):
                      "iterations_1e-6": its, "mean_reduction_per_iteration": red, "ms_mixed_1e-6": ms}
     return {"laplacian": lap, "sinusoidal": sin,
             "grids": "uniform n0^3; ball: refined once within 0.25 of the centre; band: refined twice "
-                     "within 0.05 of the sphere r = 0.25"}
+                     "within 0.05 of the sphere r = 0.25; star: refined twice where cells meet the star "
+                     "surface r = 0.237 + 0.079 cos(6 theta) cos(6 phi)"}
 
 
 def _large(dev, stream, flush, args, peak):

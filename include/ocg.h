@@ -49,6 +49,8 @@ extern "C" {
 #define OCG_REFINE_SDF_BAND 2    /* refine iff |phi(centre)| < band + (sqrt(3)/2) h */
 #define OCG_REFINE_SINE_BAND 3   /* refine iff |phi(c)| < band + |grad phi(c)| (sqrt(3)/2) h,
                                     phi a normalised sum of plane sine waves */
+#define OCG_REFINE_STAR_BAND 4   /* refine iff |phi(c)| < band + L (sqrt(3)/2) h, phi the star
+                                    surface r - (r0 + a cos(k theta) cos(k phi)) (Sec. 4.1) */
 
 #define OCG_F64 0
 #define OCG_F32 1
@@ -69,6 +71,13 @@ typedef struct ocg_hier ocg_hier;
  *                spheres sqrt(dx*dx+dy*dy+dz*dz) - r and boxes (lo, hi):
  *                q = |x - 0.5*(lo+hi)| - 0.5*(hi-lo),
  *                sqrt(mx*mx+my*my+mz*mz) + min(max(qx, max(qy, qz)), 0), m = max(q, 0)
+ *   STAR_BAND:   (cx, cy, cz, r0) = spheres[0], (a, k, L) = spheres[1][0..2] (k an
+ *                integer 0..16): d = x - c, rho2 = dx*dx + dy*dy, r = sqrt(rho2 + dz*dz),
+ *                rho = sqrt(rho2), u = dz / r (1 if r = 0), v = dx / rho (1 if rho = 0),
+ *                T_k by the Chebyshev recurrence t0 = 1, t1 = w, t(n+1) = (2*w)*t(n) - t(n-1)
+ *                (cos(k theta) = T_k(u), cos(k phi) = T_k(v) with theta the polar angle
+ *                from +z and phi the azimuth from +x), phi = r - (r0 + (a * T_k(u)) * T_k(v));
+ *                refined iff |phi| < band + (L * (0.5*sqrt(3))) * (1/(n0 2^d)).
  *   SINE_BAND:   phi = s / n and |grad phi| = sqrt((gx*gx + gy*gy) + gz*gz) / n over the
  *                n = n_sines waves (kappa, dx, dy, dz, theta) = sines[w], accumulated in
  *                w order from 0: w2 = TWO_PI * kappa, a = w2 * ((dx*x + dy*y) + dz*z) + theta,

@@ -64,6 +64,9 @@ def refine_predicate(desc, d, i, j, k):
                     (kappa, dx, dy, dz, theta), accumulated wave by wave from 0:
                     w = 2pi*kappa, a = w*(dx*x + dy*y + dz*z) + theta, s += sin a,
                     g += (w cos a) * (dx, dy, dz); sin and cos from oracle.trig
+      star band   : |phi| < band + (L * (0.5*sqrt(3))) * (1/n_d), phi = r - (r0 +
+                    (a * T_k(dz/r)) * T_k(dx/rho)) about the first sphere's centre, T_k
+                    by the Chebyshev recurrence (Sec. 4.1's star surface)
     Ties count as not refined.
     """
     from paper_2604_18886_b300 import problems as P
@@ -107,6 +110,28 @@ def refine_predicate(desc, d, i, j, k):
         phi = s / n
         grad = np.sqrt(gx * gx + gy * gy + gz * gz) / n
         slack = desc.band + (grad * (0.5 * math.sqrt(3.0))) * (1.0 / nd)
+        return np.abs(phi) < slack
+    if desc.refine == P.REFINE_STAR_BAND:
+        # Sec. 4.1 star surface r = r0 + a cos(k theta) cos(k phi); the cosines of multiple
+        # angles as Chebyshev polynomials of cos(theta) = dz / r and cos(phi) = dx / rho
+        (cx, cy, cz, r0), (a, kk, lip, _) = desc.spheres[0], desc.spheres[1]
+        dx, dy, dz = x - cx, y - cy, z - cz
+        rho2 = dx * dx + dy * dy
+        r = np.sqrt(rho2 + dz * dz)
+        rho = np.sqrt(rho2)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            u = np.where(r > 0.0, dz / r, 1.0)
+            v = np.where(rho > 0.0, dx / rho, 1.0)
+
+        def cheb(w):
+            t0, t1 = np.ones_like(w), w
+            if int(kk) == 0:
+                return t0
+            for _ in range(2, int(kk) + 1):
+                t0, t1 = t1, (2.0 * w) * t1 - t0
+            return t1
+        phi = r - (r0 + (a * cheb(u)) * cheb(v))
+        slack = desc.band + (lip * (0.5 * math.sqrt(3.0))) * (1.0 / nd)
         return np.abs(phi) < slack
     raise NotImplementedError("refine kind %d" % desc.refine)
 

@@ -168,6 +168,26 @@ static bool refine_pred(const ocg_octree_desc& d, int depth, int64_t i, int64_t 
         const double slack = d.band + (0.5 * std::sqrt(3.0)) * (1.0 / nd);
         return std::fabs(phi) < slack;
     }
+    if (d.refine == OCG_REFINE_STAR_BAND) {
+        const double dx = x - d.spheres[0][0], dy = y - d.spheres[0][1], dz = z - d.spheres[0][2];
+        const double rho2 = dx * dx + dy * dy;
+        const double r = std::sqrt(rho2 + dz * dz), rho = std::sqrt(rho2);
+        const double u = r > 0.0 ? dz / r : 1.0, v = rho > 0.0 ? dx / rho : 1.0;
+        const int k = (int)d.spheres[1][1];
+        auto cheb = [k](double w) {
+            double t0 = 1.0, t1 = w;
+            if (k == 0) return t0;
+            for (int n = 2; n <= k; ++n) {
+                const double t = (2.0 * w) * t1 - t0;
+                t0 = t1;
+                t1 = t;
+            }
+            return t1;
+        };
+        const double phi = r - (d.spheres[0][3] + (d.spheres[1][0] * cheb(u)) * cheb(v));
+        const double slack = d.band + (d.spheres[1][2] * (0.5 * std::sqrt(3.0))) * (1.0 / nd);
+        return std::fabs(phi) < slack;
+    }
     if (d.refine == OCG_REFINE_SINE_BAND) {
         double s = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
         for (int w = 0; w < d.n_sines; ++w) {
@@ -295,8 +315,13 @@ void build_host_tree(const ocg_octree_desc& desc, HostTree& T) {
     if (n0 < 2 || (n0 & 1)) throw std::runtime_error("n0 must be even and >= 2");
     if (D < 0 || D > 12) throw std::runtime_error("max_depth out of range [0, 12]");
     if (((int64_t)n0 << D) > (1 << 20)) throw std::runtime_error("n0 * 2^max_depth exceeds 2^20");
-    if (desc.refine < OCG_REFINE_NONE || desc.refine > OCG_REFINE_SINE_BAND)
+    if (desc.refine < OCG_REFINE_NONE || desc.refine > OCG_REFINE_STAR_BAND)
         throw std::runtime_error("unknown refine kind");
+    if (desc.refine == OCG_REFINE_STAR_BAND) {
+        const double k = desc.spheres[1][1];
+        if (desc.n_spheres < 2 || !(k >= 0.0 && k <= 16.0 && k == std::floor(k)) || !(desc.spheres[1][2] >= 0.0))
+            throw std::runtime_error("star refinement needs spheres[0] = (c, r0), spheres[1] = (a, k in 0..16, L >= 0)");
+    }
     if (desc.refine == OCG_REFINE_SINE_BAND) {
         if (desc.n_sines < 1 || desc.n_sines > 8) throw std::runtime_error("n_sines must be in 1..8");
         for (int w = 0; w < desc.n_sines; ++w) {

@@ -34,6 +34,7 @@ REFINE_NONE = 0
 REFINE_BALL_CENTRE = 1
 REFINE_SDF_BAND = 2
 REFINE_SINE_BAND = 3
+REFINE_STAR_BAND = 4
 
 MAX_SPHERES = 4
 MAX_BOXES = 4
@@ -50,6 +51,9 @@ class OctreeDesc:
         phi the minimum of the sphere and box signed distances.
     refine == REFINE_SINE_BAND: refined iff |phi(centre)| < band + |grad phi(centre)|
         (sqrt(3)/2) h_d, phi = (1/n) sum_m sin(2 pi kappa_m (d_m . x) + theta_m).
+    refine == REFINE_STAR_BAND: refined iff |phi(centre)| < band + L (sqrt(3)/2) h_d with
+        phi = r - (r0 + a cos(k theta) cos(k phi)) about spheres[0] = (c, r0) and
+        spheres[1] = (a, k, L, 0) (the star surface of Sec. 4.1).
     """
 
     n0: int
@@ -281,19 +285,26 @@ def _source(p: Problem, x, y, z):
 # ----------------------------------------------------------------------------------
 # accuracy studies (Sec. 4: Laplacian accuracy and sinusoidal Poisson tests)
 
-ACCURACY_GRIDS = ("uniform", "ball", "band")
+ACCURACY_GRIDS = ("uniform", "ball", "band", "star")
+
+# the star surface of Sec. 4.1: r = 0.237 + 0.079 cos(6 theta) cos(6 phi) about the centre;
+# L = 1 + a k / r0 = 3 bounds the field's gradient away from the axis
+STAR = [(0.5, 0.5, 0.5, 0.237), (0.079, 6.0, 3.0, 0.0)]
 
 
 def accuracy_desc(kind: str, n0: int) -> OctreeDesc:
     """Grids of the accuracy studies: uniform n0^3; n0^3 with cells whose centre lies
     within 0.25 of the cube centre refined once; n0^3 refined twice within 0.05 of the
-    sphere of radius 0.25 about the centre."""
+    sphere of radius 0.25 about the centre; n0^3 refined twice where the cells meet the
+    star surface (the paper's sphere and star grids: two levels finer near the surface)."""
     if kind == "uniform":
         return OctreeDesc(n0, 0)
     if kind == "ball":
         return OctreeDesc(n0, 1, REFINE_BALL_CENTRE, spheres=[(0.5, 0.5, 0.5, 0.25)])
     if kind == "band":
         return OctreeDesc(n0, 2, REFINE_SDF_BAND, band=0.05, spheres=[(0.5, 0.5, 0.5, 0.25)])
+    if kind == "star":
+        return OctreeDesc(n0, 2, REFINE_STAR_BAND, band=0.0, spheres=list(STAR))
     raise ValueError(kind)
 
 

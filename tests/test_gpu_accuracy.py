@@ -66,11 +66,12 @@ def test_laplacian_apply_matches_oracle():
 def test_laplacian_orders_at_large_sizes():
     uni = [_lap_errors("uniform", n0)[0] for n0 in (32, 64, 128)]
     assert min(_rates(uni)) > 1.9, uni
-    ball = [_lap_errors("ball", n0) for n0 in (32, 64, 128)]
-    far = [b[1] for b in ball]
-    tmax = [b[2] for b in ball]
-    assert min(_rates(far)) > 1.9, far
-    assert max(tmax) < 10.0 and tmax[-1] < 1.2 * tmax[0], tmax
+    for kind in ("ball", "star"):
+        res = [_lap_errors(kind, n0) for n0 in (32, 64, 128)]
+        far = [b[1] for b in res]
+        tmax = [b[2] for b in res]
+        assert min(_rates(far)) > 1.9, (kind, far)
+        assert max(tmax) < 10.0 and tmax[-1] < 1.2 * tmax[0], (kind, tmax)
 
 
 def test_sinusoidal_solve_matches_oracle():
@@ -86,7 +87,7 @@ def test_sinusoidal_solve_matches_oracle():
     assert np.abs(x.cpu().numpy() - xo).max() <= 1e-8 * np.abs(xo).max()
 
 
-@pytest.mark.parametrize("kind", ["ball", "band"])
+@pytest.mark.parametrize("kind", ["ball", "band", "star"])
 def test_sinusoidal_orders_and_residual_decay_at_large_sizes(kind):
     errs, its = [], []
     for n0 in (32, 64, 128):
@@ -104,6 +105,6 @@ def test_sinusoidal_orders_and_residual_decay_at_large_sizes(kind):
         assert sm.converged and sm.true_rel_res <= 1.5e-6
         its.append(sm.iterations)
         red = math.exp(-math.log(sm.hist[sm.iterations]) / sm.iterations)
-        assert red > 5.0 if kind == "band" else red > 10.0, (n0, red)
+        assert red > 5.0 if kind in ("band", "star") else red > 10.0, (n0, red)
     assert min(_rates(errs)) > 1.9, errs
     assert max(its) - min(its) <= 2 and max(its) <= 8, its

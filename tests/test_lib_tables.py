@@ -37,6 +37,10 @@ def _descs():
     yield P.c5(8, 2).desc           # sine band: deterministic sin/cos in both builders
     yield P.c5(6, 3, band=0.01).desc
     yield P.c5(16, 2).desc
+    yield P.accuracy_desc("star", 8)   # star surface: Chebyshev cosines in both builders
+    yield P.accuracy_desc("star", 16)
+    yield P.OctreeDesc(6, 3, P.REFINE_STAR_BAND, band=0.01,
+                       spheres=[(0.47, 0.52, 0.5, 0.2), (0.05, 4.0, 2.0, 0.0)])
 
 
 @pytest.mark.parametrize("desc", list(_descs()))

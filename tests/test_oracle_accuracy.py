@@ -10,7 +10,8 @@ T flux first order), while their share of the volume halves with each refinement
 
 Sinusoidal: lap p = 4 pi sin(2 pi x) sin(2 pi y) sin(2 pi z), Dirichlet walls (p vanishes
 there); Alg. 1 to 1e-10; the solution error is second order and the residual falls by
-more than a factor 10 per iteration (the paper reports about 20, Sec. 4.3).
+more than a factor 10 per iteration on one-level grids, 5 on the two-level star grid (the
+paper reports about 20, Sec. 4.3).
 """
 import math
 
@@ -51,8 +52,10 @@ def test_laplacian_second_order_on_uniform_grids():
     assert min(_rates(errs)) > 1.8, errs
 
 
-def test_laplacian_on_refined_grids_second_order_away_from_t_junctions():
-    res = [_laplacian_errors("ball", n0) for n0 in (8, 16, 32)]
+@pytest.mark.parametrize("kind, sizes", [("ball", (8, 16, 32)), ("star", (16, 32))])
+def test_laplacian_on_refined_grids_second_order_away_from_t_junctions(kind, sizes):
+    # (the star grid is still pre-asymptotic at an 8^3 root: mostly refined there)
+    res = [_laplacian_errors(kind, n0) for n0 in sizes]
     far = [r[1] for r in res]
     assert min(_rates(far)) > 1.8, far
     # beside T-junction faces the error is O(1) (bounded, not decaying) on a volume share
@@ -60,13 +63,16 @@ def test_laplacian_on_refined_grids_second_order_away_from_t_junctions():
     tmax = [r[2] for r in res]
     share = [r[3] for r in res]
     assert 1.0 < tmax[-1] < 1.2 * tmax[-2] and tmax[-1] < 10.0, tmax
-    assert share[2] < 0.6 * share[1] < 0.6 * 0.6 * share[0], share
+    assert all(share[q + 1] < 0.6 * share[q] for q in range(len(share) - 1)), share
 
 
-@pytest.mark.parametrize("kind", ["uniform", "ball"])
-def test_sinusoidal_poisson_second_order_and_fast_residual_decay(kind):
+@pytest.mark.parametrize("kind, sizes, min_reduction", [("uniform", (8, 16, 32), 10.0), ("ball", (8, 16, 32), 10.0),
+                                                         ("star", (16, 32), 5.0)])
+def test_sinusoidal_poisson_second_order_and_fast_residual_decay(kind, sizes, min_reduction):
+    # (two refinement levels, as on the star grid, reduce a little less per iteration on
+    # small roots: 7 at 8^3, where the star grid is still pre-asymptotic)
     errs, its = [], []
-    for n0 in (8, 16, 32):
+    for n0 in sizes:
         p = P.sinusoidal(kind, n0)
         t, f, H = _setup(p)
         b = P.rhs(p, t.leaves)
@@ -75,6 +81,6 @@ def test_sinusoidal_poisson_second_order_and_fast_residual_decay(kind):
         errs.append(P.rms_v(h, x - P.exact_solution(p, xc, yc, zc)))
         its.append(next(i for i, v in enumerate(hist) if v <= 1e-6))
         red = math.exp(-math.log(hist[k]) / k)   # mean reduction per iteration
-        assert red > 10.0, (n0, red, hist)
+        assert red > min_reduction, (n0, red, hist)
     assert min(_rates(errs)) > 1.9, errs
     assert max(its) <= 7 and max(its) - min(its) <= 2, its
