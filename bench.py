@@ -137,7 +137,7 @@ class Clocks:
                 "power_w": statistics.median(pw) if pw else None, "reasons": reasons, "samples": len(inside)}
 
 
-def _setup(dev):
+def _setup(dev, sweep="auto"):
     import numpy as np
     import torch
     from paper_2604_18886_b300 import problems as P
@@ -146,7 +146,7 @@ def _setup(dev):
     tree = S.Octree(p.desc)
     faces = tree.faces()
     beta = P.face_beta(p, faces)
-    hier = S.Hierarchy(tree, torch.from_numpy(beta).to(dev), p.bc, S.mg_params(coef="f32"))
+    hier = S.Hierarchy(tree, torch.from_numpy(beta).to(dev), p.bc, S.mg_params(coef="f32", sweep=sweep))
     b = P.rhs(p, tree.leaves(), faces, beta)
     return p, tree, hier, torch.from_numpy(b).to(dev), np
 
@@ -594,7 +594,7 @@ def run_ours(args):
         if rank == 0:
             print(json.dumps(out), flush=True)
         return
-    p, tree, hier, b, np = _setup(dev)
+    p, tree, hier, b, np = _setup(dev, args.headline_sweep)
     x = torch.empty_like(b)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
     for _ in range(args.warmup):
@@ -837,6 +837,8 @@ def main():
                     help="run the warm-up and the timed mixed solves only (profiling aid)")
     ap.add_argument("--eager", action="store_true",
                     help="launch the timed solves kernel by kernel (profiling aid; not the benchmark path)")
+    ap.add_argument("--headline-sweep", default="auto", choices=["auto", "octet", "cell", "quad", "tile"],
+                    help="sweep form of the headline hierarchy (auto: timed at set-up; profiling aid)")
     ap.add_argument("--adjoint", action="store_true",
                     help="with --only-large: also one transpose solve, in the NVTX range 'adjoint' (profiling aid)")
     args = ap.parse_args()
