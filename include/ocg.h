@@ -196,6 +196,16 @@ int ocg_setup_hierarchy(const ocg_octree* t, const float* face_beta_dev, const i
                         const ocg_mg_params* prm, void* stream, ocg_hier** out);
 void ocg_hier_destroy(ocg_hier* h);
 
+/* Refresh the hierarchy for new face fractions beta (device, canonical face order, FP32)
+ * on the same octree, walls and parameters (no counterpart in the paper; the per-step
+ * refresh of a moving-boundary simulation whose topology is unchanged): the leaf
+ * coefficients, Alg. 3 (or the geometric rediscretisation) and the FP32 / BF16 copies are
+ * recomputed in place, so solves, graphs captured on the hierarchy and batches built from
+ * it keep working on the new coefficients; sweep and tail choices made at set-up are kept.
+ * Synchronises the stream.  Errors: EINVAL (null argument, negative or non-finite beta:
+ * the coefficients are then undefined until a successful update), ECUDA. */
+int ocg_hier_update_beta(ocg_hier* h, const float* beta_dev, void* stream);
+
 /* Sweep form chosen for level m and, if the set-up timed them, the measured time of one
  * colour sweep in each form (microseconds, captured in a CUDA graph; -1 if not timed).
  * Levels run inside the shared-memory coarse kernel report form -1. */

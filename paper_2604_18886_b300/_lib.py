@@ -79,6 +79,7 @@ _SIGS = [
     ("ocg_setup_hierarchy", C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int32), C.POINTER(MGParams),
                                       C.c_void_p, C.POINTER(C.c_void_p)]),
     ("ocg_hier_destroy", None, [C.c_void_p]),
+    ("ocg_hier_update_beta", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("ocg_hier_export_coefs", C.c_int, [C.c_void_p, C.c_int32] + [C.c_void_p] * 4),
     ("ocg_hier_tuning", C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_double),
                                   C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),

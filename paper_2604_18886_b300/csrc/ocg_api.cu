@@ -1377,6 +1377,88 @@ void rediscretise(ocg_hier* h, cudaStream_t st) {
     for (double* v : dv) dfree(v);
 }
 
+// The coefficient sets of a hierarchy from the face fractions beta (canonical face order):
+// the face scatter and leaf gather (Sec. 3.1), Alg. 3 on every level (or the geometric
+// rediscretisation), the FP32 / BF16 copies.  Arrays are allocated on first use and
+// rewritten in place afterwards, so graphs captured on the hierarchy stay valid.
+void build_coefficients(ocg_hier* h, const float* beta, cudaStream_t st) {
+    const ocg_octree* t = h->t;
+    const HostTree& H = t->H;
+    const int64_t ntw = 24 * std::max<int64_t>(H.nt, 1);
+    if (!h->c64[0]) h->c64[0] = dalloc<double>(H.ncell);
+    if (!h->tw64) h->tw64 = dalloc<double>(ntw);
+    double* cm = dalloc<double>(3 * H.ncell);   // c_x-, c_y-, c_z- as one [3][ncell] block
+    ck(cudaMemsetAsync(h->c64[0], 0, H.ncell * sizeof(double), st), "memset");
+    ck(cudaMemsetAsync(cm, 0, 3 * H.ncell * sizeof(double), st), "memset");
+    ck(cudaMemsetAsync(h->tw64, 0, ntw * sizeof(double), st), "memset");
+    std::vector<double> hd(H.D + 1);
+    for (int d = 0; d <= H.D; ++d) hd[d] = 1.0 / (double)((int64_t)H.n0 << d);
+    double* dh = dupload(hd);
+    int* derr = dalloc<int>(1);
+    ck(cudaMemsetAsync(derr, 0, sizeof(int), st), "memset");
+    if (H.nface > 0) {
+        launch_k(k_face_scatter, nblk(H.nface), BLK, 0, st, beta, t->fslot, t->fkind, t->fdepth, dh, (int)H.nface, cm,
+                                                     h->tw64, derr);
+        ck_launch("face scatter");
+    }
+    LevelTab LT{};
+    LT.mc = H.mc;
+    for (int m = H.mc; m <= H.D; ++m) {
+        LT.off[m - H.mc] = (int)H.L(m).off;
+        LT.h[m - H.mc] = H.L(m).h;
+    }
+    launch_k(k_leaf_gather, nblk(H.nleaf), BLK, 0, st, t->leaf_cell, t->level, t->tables(), LT,
+                                                make_int4(h->bc[0], h->bc[1], h->bc[2], h->bc[3]), make_int2(h->bc[4], h->bc[5]),
+                                                (int)H.nleaf, (int)H.ncell, h->c64[0], cm, h->tw64);
+    ck_launch("leaf gather");
+    for (int m = H.D; m > H.mc; --m) {
+        const LevelArgs A = t->largs(m);
+        launch_k(k_coarsen, nblk(A.ncell / 8), BLK, 0, st, A, t->tables(), h->prm.alpha, h->c64[0], cm, (int)H.ncell);
+        ck_launch("coarsen");
+    }
+    for (int q = 0; q < 3; ++q) {
+        if (!h->c64[q + 1]) h->c64[q + 1] = dalloc<double>(H.ncell);
+        ck(cudaMemcpyAsync(h->c64[q + 1], cm + q * H.ncell, H.ncell * sizeof(double), cudaMemcpyDeviceToDevice, st),
+           "copy");
+    }
+    int herr = 0;
+    ck(cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, st), "copy");
+    ck(cudaStreamSynchronize(st), "setup sync");
+    dfree(cm); dfree(dh); dfree(derr);
+    if (herr) throw Status(OCG_EINVAL, "face beta must be finite and >= 0");
+    if (h->prm.coarsening == OCG_COARSEN_GEOMETRIC) rediscretise(h, st);
+    if (h->prm.coef_dtype == OCG_F32) {
+        for (int q = 0; q < 4; ++q) {
+            if (!h->c32[q]) h->c32[q] = dalloc<float>(H.ncell);
+            launch_k(k_convert<float>, nblk(H.ncell), BLK, 0, st, h->c64[q], h->c32[q], H.ncell);
+            if (h->prm.bf16_coarse && q > 0) {
+                if (!h->c16[q]) h->c16[q] = dalloc<__nv_bfloat16>(H.ncell);
+                launch_k(k_convert<__nv_bfloat16>, nblk(H.ncell), BLK, 0, st, h->c64[q], h->c16[q], H.ncell);
+            }
+        }
+        if (!h->tw32) h->tw32 = dalloc<float>(ntw);
+        launch_k(k_convert<float>, nblk(ntw), BLK, 0, st, h->tw64, h->tw32, ntw);
+        if (h->prm.bf16_coarse) {
+            if (!h->d16) h->d16 = dalloc<float>(H.ncell);
+            for (int m = H.mc; m <= H.D; ++m) {
+                const LevelArgs A = t->largs(m);
+                launch_k(k_diag_conservative<__nv_bfloat16>, nblk(A.ncell / 8, OBLK), OBLK, 0, st, A, t->tables(),
+                         h->C64(), (const __nv_bfloat16*)h->c16[1], (const __nv_bfloat16*)h->c16[2],
+                         (const __nv_bfloat16*)h->c16[3], (const float*)h->tw32, h->d16);
+            }
+        }
+        ck_launch("convert");
+        ck(cudaStreamSynchronize(st), "setup sync");
+        for (int q = 0; q < 4; ++q) { dfree(h->c64[q]); h->c64[q] = nullptr; }
+        dfree(h->tw64);
+        h->tw64 = nullptr;
+    }
+    if (!h->beta) h->beta = dalloc<float>(H.nface);
+    if (H.nface > 0)
+        ck(cudaMemcpyAsync(h->beta, beta, H.nface * sizeof(float), cudaMemcpyDeviceToDevice, st), "copy beta");
+    ck(cudaStreamSynchronize(st), "setup sync");
+}
+
 int ocg_setup_hierarchy(const ocg_octree* t, const float* beta, const int32_t bc[6], const ocg_mg_params* prm,
                         void* stream, ocg_hier** out) {
     return guard([&] {
@@ -1410,79 +1492,8 @@ int ocg_setup_hierarchy(const ocg_octree* t, const float* beta, const int32_t bc
             if (bc[q] == OCG_BC_DIRICHLET) ns = false;
         }
         h->ns_auto = ns;
-        const int64_t ntw = 24 * std::max<int64_t>(H.nt, 1);
-        h->c64[0] = dalloc<double>(H.ncell);
-        h->tw64 = dalloc<double>(ntw);
-        double* cm = dalloc<double>(3 * H.ncell);   // c_x-, c_y-, c_z- as one [3][ncell] block
-        ck(cudaMemsetAsync(h->c64[0], 0, H.ncell * sizeof(double), st), "memset");
-        ck(cudaMemsetAsync(cm, 0, 3 * H.ncell * sizeof(double), st), "memset");
-        ck(cudaMemsetAsync(h->tw64, 0, ntw * sizeof(double), st), "memset");
-        std::vector<double> hd(H.D + 1);
-        for (int d = 0; d <= H.D; ++d) hd[d] = 1.0 / (double)((int64_t)H.n0 << d);
-        double* dh = dupload(hd);
-        int* derr = dalloc<int>(1);
-        ck(cudaMemsetAsync(derr, 0, sizeof(int), st), "memset");
-        if (H.nface > 0) {
-            launch_k(k_face_scatter, nblk(H.nface), BLK, 0, st, beta, t->fslot, t->fkind, t->fdepth, dh, (int)H.nface, cm,
-                                                         h->tw64, derr);
-            ck_launch("face scatter");
-        }
-        LevelTab LT{};
-        LT.mc = H.mc;
-        for (int m = H.mc; m <= H.D; ++m) {
-            LT.off[m - H.mc] = (int)H.L(m).off;
-            LT.h[m - H.mc] = H.L(m).h;
-        }
-        launch_k(k_leaf_gather, nblk(H.nleaf), BLK, 0, st, t->leaf_cell, t->level, t->tables(), LT,
-                                                    make_int4(bc[0], bc[1], bc[2], bc[3]), make_int2(bc[4], bc[5]),
-                                                    (int)H.nleaf, (int)H.ncell, h->c64[0], cm, h->tw64);
-        ck_launch("leaf gather");
-        for (int m = H.D; m > H.mc; --m) {
-            const LevelArgs A = t->largs(m);
-            launch_k(k_coarsen, nblk(A.ncell / 8), BLK, 0, st, A, t->tables(), prm->alpha, h->c64[0], cm, (int)H.ncell);
-            ck_launch("coarsen");
-        }
-        for (int q = 0; q < 3; ++q) {
-            h->c64[q + 1] = dalloc<double>(H.ncell);
-            ck(cudaMemcpyAsync(h->c64[q + 1], cm + q * H.ncell, H.ncell * sizeof(double), cudaMemcpyDeviceToDevice, st),
-               "copy");
-        }
-        int herr = 0;
-        ck(cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, st), "copy");
-        ck(cudaStreamSynchronize(st), "setup sync");
-        dfree(cm); dfree(dh); dfree(derr);
-        if (herr) throw Status(OCG_EINVAL, "face beta must be finite and >= 0");
-        if (prm->coarsening == OCG_COARSEN_GEOMETRIC) rediscretise(h.get(), st);
-        if (prm->coef_dtype == OCG_F32) {
-            for (int q = 0; q < 4; ++q) {
-                h->c32[q] = dalloc<float>(H.ncell);
-                launch_k(k_convert<float>, nblk(H.ncell), BLK, 0, st, h->c64[q], h->c32[q], H.ncell);
-                if (prm->bf16_coarse && q > 0) {
-                    h->c16[q] = dalloc<__nv_bfloat16>(H.ncell);
-                    launch_k(k_convert<__nv_bfloat16>, nblk(H.ncell), BLK, 0, st, h->c64[q], h->c16[q], H.ncell);
-                }
-            }
-            h->tw32 = dalloc<float>(ntw);
-            launch_k(k_convert<float>, nblk(ntw), BLK, 0, st, h->tw64, h->tw32, ntw);
-            if (prm->bf16_coarse) {
-                h->d16 = dalloc<float>(H.ncell);
-                for (int m = H.mc; m <= H.D; ++m) {
-                    const LevelArgs A = t->largs(m);
-                    launch_k(k_diag_conservative<__nv_bfloat16>, nblk(A.ncell / 8, OBLK), OBLK, 0, st, A, t->tables(),
-                             h->C64(), (const __nv_bfloat16*)h->c16[1], (const __nv_bfloat16*)h->c16[2],
-                             (const __nv_bfloat16*)h->c16[3], (const float*)h->tw32, h->d16);
-                }
-            }
-            ck_launch("convert");
-            ck(cudaStreamSynchronize(st), "setup sync");
-            for (int q = 0; q < 4; ++q) { dfree(h->c64[q]); h->c64[q] = nullptr; }
-            dfree(h->tw64);
-            h->tw64 = nullptr;
-        }
+        build_coefficients(h.get(), beta, st);
         ensure_work(h.get());
-        h->beta = dalloc<float>(H.nface);
-        if (H.nface > 0)
-            ck(cudaMemcpyAsync(h->beta, beta, H.nface * sizeof(float), cudaMemcpyDeviceToDevice, st), "copy beta");
         choose_tail(h.get(), 0, sizeof(float));
         choose_tail(h.get(), 1, sizeof(double));
         const int nlev = H.D - H.mc + 1;
@@ -1504,6 +1515,15 @@ int ocg_setup_hierarchy(const ocg_octree* t, const float* beta, const int32_t bc
 }
 
 void ocg_hier_destroy(ocg_hier* h) { delete h; }
+
+int ocg_hier_update_beta(ocg_hier* h, const float* beta, void* stream) {
+    return guard([&] {
+        if (!h || !beta) throw Status(OCG_EINVAL, "null argument");
+        cudaStream_t st = (cudaStream_t)stream;
+        ck(cudaStreamSynchronize(st), "sync");
+        build_coefficients(h, beta, st);
+    });
+}
 
 int ocg_hier_export_coefs(const ocg_hier* h, int32_t m, double* c, double* cx, double* cy, double* cz) {
     return guard([&] {

@@ -169,6 +169,16 @@ class Hierarchy:
         L.check(L.lib().ocg_hier_export_coefs(self._h, m, *[L.ptr(a) for a in out]))
         return out
 
+    def update_beta(self, beta, stream=None):
+        """Recompute the coefficients in place for new face fractions beta on the same tree
+        (ocg_hier_update_beta); captured graphs and batches stay valid."""
+        import torch
+        if isinstance(beta, np.ndarray):
+            beta = torch.from_numpy(np.ascontiguousarray(beta, np.float32)).cuda()
+        assert beta.dtype == torch.float32 and beta.is_cuda and beta.numel() == self.tree.n_faces
+        beta = beta.contiguous()
+        L.check(L.lib().ocg_hier_update_beta(self._h, L.ptr(beta), self._stream(stream)))
+
     def tuning(self):
         """{level: (form, us_octet, us_cell, us_quad, us_tile)} as chosen / measured at set-up."""
         out = {}
