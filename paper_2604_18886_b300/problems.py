@@ -71,7 +71,7 @@ class Problem:
     desc: OctreeDesc
     bc: tuple                 # 6 wall codes
     beta: str = "one"         # "one" or "cut" (fluid fraction of the solid geometry)
-    rhs: str = "zero"         # "sin_dirichlet", "exp_sin_cos", "sinusoidal", "divergence", "normal"
+    rhs: str = "zero"         # "sin_dirichlet", "exp_sin_cos", "sinusoidal", "divergence", "tank", "normal"
     seed: int = 0
     mode: str = "mixed"       # suggested precision mode
     tol: float = 1e-6
@@ -80,6 +80,7 @@ class Problem:
     solid_boxes: list = field(default_factory=list)
     solid_sines: list = field(default_factory=list)
     sine_offset: float = 0.0
+    solid_star: list = field(default_factory=list)   # [(cx, cy, cz, r0), (a, k, ...)]
 
     @property
     def neumann(self) -> bool:
@@ -186,7 +187,22 @@ def solid_sdf(p: Problem, x, y, z):
         for (kap, dx, dy, dz, th) in p.solid_sines:
             s = s + np.sin(2 * math.pi * kap * (dx * x + dy * y + dz * z) + th)
         phi = np.minimum(phi, s / len(p.solid_sines) - p.sine_offset)
+    if p.solid_star:
+        phi = np.minimum(phi, star_field(p.solid_star, x, y, z))
     return phi
+
+
+def star_field(star, x, y, z):
+    """r - (r0 + a cos(k theta) cos(k phi)) about (cx, cy, cz) (the star surface of
+    Sec. 4.1; theta polar from +z, phi azimuth from +x), positive outside the star."""
+    (cx, cy, cz, r0), (a, k) = star[0], star[1][:2]
+    dx, dy, dz = x - cx, y - cy, z - cz
+    r = np.sqrt(dx * dx + dy * dy + dz * dz)
+    rho = np.sqrt(dx * dx + dy * dy)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        th = np.arccos(np.where(r > 0, dz / np.where(r > 0, r, 1.0), 1.0))
+        ph = np.arctan2(dy, dx)
+    return r - (r0 + a * np.cos(k * th) * np.cos(k * ph))
 
 
 def _tri_positive_fraction(a, b, c):
@@ -321,6 +337,27 @@ def laplacian_problem(kind: str, n0: int) -> Problem:
     return Problem("lap_%s%d" % (kind, n0), accuracy_desc(kind, n0), (NEUMANN,) * 6, beta="one")
 
 
+TANK_BC = (NEUMANN, NEUMANN, NEUMANN, DIRICHLET, NEUMANN, NEUMANN)   # open to air at y = 1
+
+
+def tank(obstacle: str, n0: int) -> Problem:
+    """Static tank (Sec. 4.4): liquid filling [0,1]^3, solid bottom and sides (Neumann),
+    open to air at the top (y = 1: zero-pressure Dirichlet), a solid obstacle (sphere of
+    radius 0.25 or the star of Sec. 4.1) at the centre with fluid-fraction beta; the grid
+    is refined two levels where cells meet the obstacle's surface; rhs = the integrated
+    divergence of the uniform velocity (0, -1, 0) (no flux through the solid walls, inflow
+    through the open top)."""
+    if obstacle == "sphere":
+        sph = (0.5, 0.5, 0.5, 0.25)
+        d = OctreeDesc(n0, 2, REFINE_SDF_BAND, band=0.0, spheres=[sph])
+        return Problem("tank_sphere%d" % n0, d, TANK_BC, beta="cut", rhs="tank", mode="mixed",
+                       tol=1e-6, mu=2, solid_spheres=[sph])
+    if obstacle == "star":
+        return Problem("tank_star%d" % n0, accuracy_desc("star", n0), TANK_BC, beta="cut", rhs="tank",
+                       mode="mixed", tol=1e-6, mu=2, solid_star=list(STAR))
+    raise ValueError(obstacle)
+
+
 def laplacian_test_function(x, y, z):
     """f = (x^2 + y^2 + z^2) exp(-xyz)."""
     return (x * x + y * y + z * z) * np.exp(-x * y * z)
@@ -396,6 +433,19 @@ def rhs(p: Problem, leaves, faces=None, beta=None) -> np.ndarray:
                 fc[a] = np.zeros(on.sum()) if side == 0 else np.ones(on.sum())
                 g = exact_solution(p, fc[0], fc[1], fc[2])
                 b[on] += 2.0 * h[on] * g
+        return b
+    if p.rhs == "tank":
+        assert faces is not None and beta is not None
+        b = np.zeros(n)
+        hf = 1.0 / (p.desc.n0 * 2.0 ** np.asarray(faces["depth"], np.float64))
+        u = np.where(np.asarray(faces["axis"]) == 1, -1.0, 0.0)
+        flux = np.asarray(beta, np.float64) * hf * hf * u
+        b += np.bincount(faces["minus"], weights=flux, minlength=n)
+        b -= np.bincount(faces["plus"], weights=flux, minlength=n)
+        # the open top (y = 1): inflow -h^2 through the + y face of the top leaves
+        hl = 1.0 / (p.desc.n0 * 2.0 ** leaves["depth"].astype(np.float64))
+        top = leaves["j"] == p.desc.n0 * 2 ** leaves["depth"].astype(np.int64) - 1
+        b[top] += -hl[top] ** 2
         return b
     rng = np.random.default_rng(p.seed)
     if p.rhs == "divergence":
