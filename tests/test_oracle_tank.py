@@ -7,7 +7,7 @@ reproduces exactly (regular faces, cut-cell faces with any beta, the T-junction 
 value, the Dirichlet face at the open top), so the discrete pressure is p = y - 1 to
 rounding (the field that cancels the motion: the paper's "nearly uniform gradient along
 y"), whatever the obstacle and grid; and Alg. 1 with W-cycles (mu = 2, the paper's choice
-for this test) reduces the residual by more than 5 per iteration.
+for this test) reduces the residual by more than 5 per iteration on these small roots.
 """
 import math
 
