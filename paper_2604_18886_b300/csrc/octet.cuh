@@ -94,10 +94,13 @@ __device__ __forceinline__ void octet_coords(int o, int ni, int& I, int& J, int&
     }
 }
 
-// 1/n for the mean of n active cells (n <= 8): multiply instead of divide
+// 1/n for the mean of n active cells (n <= 8): multiply instead of divide; 0 for n = 0, so
+// that the mean over no active cell is 0 (Alg. 3's active count; inactive cells have no
+// coefficient, and an infinite factor would turn their zero terms into NaN)
 template <class TV>
 __device__ __forceinline__ TV inv_count(int n) {
-    return n == 8 ? TV(0.125) : (n == 4 ? TV(0.25) : (n == 2 ? TV(0.5) : (n == 1 ? TV(1) : TV(1) / TV(n))));
+    return n == 8 ? TV(0.125)
+                  : (n == 4 ? TV(0.25) : (n == 2 ? TV(0.5) : (n == 1 ? TV(1) : (n == 0 ? TV(0) : TV(1) / TV(n)))));
 }
 
 template <class TV>

@@ -256,11 +256,16 @@ def face_fluid_fraction(p: Problem, faces) -> np.ndarray:
 
 def face_beta(p: Problem, faces) -> np.ndarray:
     """Per-face beta in canonical face order (float32): 1 for beta="one"; the clamped
-    fluid fraction max(1e-3, min(1, f)) for beta="cut"."""
+    fluid fraction max(1e-3, min(1, f)) for beta="cut"; the fraction itself in [0, 1]
+    for beta="cut_exact" (cells inside the solid become inactive)."""
     n = len(faces["axis"])
     if p.beta == "one":
         return np.ones(n, np.float32)
     f = face_fluid_fraction(p, faces)
+    if p.beta == "cut_exact":
+        # the exact fraction: faces inside the solid get 0, so a cell inside the solid has
+        # no coefficient and drops out of the system (an inactive cell)
+        return np.clip(f, 0.0, 1.0).astype(np.float32)
     return np.clip(f, 1e-3, 1.0).astype(np.float32)
 
 
@@ -340,20 +345,23 @@ def laplacian_problem(kind: str, n0: int) -> Problem:
 TANK_BC = (NEUMANN, NEUMANN, NEUMANN, DIRICHLET, NEUMANN, NEUMANN)   # open to air at y = 1
 
 
-def tank(obstacle: str, n0: int) -> Problem:
+def tank(obstacle: str, n0: int, inactive: bool = True) -> Problem:
     """Static tank (Sec. 4.4): liquid filling [0,1]^3, solid bottom and sides (Neumann),
     open to air at the top (y = 1: zero-pressure Dirichlet), a solid obstacle (sphere of
     radius 0.25 or the star of Sec. 4.1) at the centre with fluid-fraction beta; the grid
     is refined two levels where cells meet the obstacle's surface; rhs = the integrated
     divergence of the uniform velocity (0, -1, 0) (no flux through the solid walls, inflow
-    through the open top)."""
+    through the open top).  inactive: beta is the exact fraction (cells inside the solid
+    drop out, as in the paper's solver); otherwise the fraction clamped at 1e-3."""
+    kind = "cut_exact" if inactive else "cut"
+    tag = "" if inactive else "_clamped"
     if obstacle == "sphere":
         sph = (0.5, 0.5, 0.5, 0.25)
         d = OctreeDesc(n0, 2, REFINE_SDF_BAND, band=0.0, spheres=[sph])
-        return Problem("tank_sphere%d" % n0, d, TANK_BC, beta="cut", rhs="tank", mode="mixed",
+        return Problem("tank_sphere%d%s" % (n0, tag), d, TANK_BC, beta=kind, rhs="tank", mode="mixed",
                        tol=1e-6, mu=2, solid_spheres=[sph])
     if obstacle == "star":
-        return Problem("tank_star%d" % n0, accuracy_desc("star", n0), TANK_BC, beta="cut", rhs="tank",
+        return Problem("tank_star%d%s" % (n0, tag), accuracy_desc("star", n0), TANK_BC, beta=kind, rhs="tank",
                        mode="mixed", tol=1e-6, mu=2, solid_star=list(STAR))
     raise ValueError(obstacle)
 

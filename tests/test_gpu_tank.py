@@ -1,18 +1,22 @@
-"""Static tank (Sec. 4.4) through the library: the FP64 solve reproduces the hydrostatic
-pressure p = y - 1 that the oracle's tests pin, and at the paper's grid size (64^3 root,
-two levels near the obstacle: 64~256) the mixed W-cycle solve to 1e-6 takes at most 10
-iterations with a fitted residual reduction (least squares on log ||r|| against the
-iteration) above 3 per iteration (the paper fits 5.2-7.2 with inactive solid cells; here
-the solid interior stays a low-conductivity region of unknowns, beta clamped at 1e-3; the
-sphere measures 8.9, the star 3.5), its pressure is within 1e-5 of
-the hydrostatic field, and the divergence of the projected velocity, (b - A p) / V, is
-below 1e-5 of the initial divergence (volume-weighted RMS).
+"""Static tank (Sec. 4.4) through the library: with the solid's interior kept at beta =
+1e-3 the FP64 solve reproduces the exact discrete pressure p = y - 1 that the oracle's
+tests pin; with the interior inactive (exact fractions, the paper's solver) the solve
+matches the oracle's direct solve on the active cells and leaves the inactive ones at 0.
+At the paper's grid size (64^3 root, two levels near the obstacle: 64~256) the mixed
+W-cycle solve to 1e-6 with inactive solid cells converges (sphere: at most 6 iterations,
+fitted residual reduction above 10 per iteration; star: at most 12, above 3; the paper
+fits 7.16 and 5.17; measured 19.9 and 3.2), its pressure stays within 5e-3 of y - 1 on the
+active cells, and the divergence of the projected velocity, (b - A p) / V, is below 1e-5
+of the initial divergence (volume-weighted RMS over the active cells).
 """
 import math
 
 import numpy as np
 import pytest
+import scipy.sparse.linalg as sla
 
+from oracle import octree as O
+from oracle import operator as OP
 from paper_2604_18886_b300 import problems as P
 from paper_2604_18886_b300 import solver as S
 
@@ -21,8 +25,8 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-def _setup(obstacle, n0, coef, mu=1):
-    p = P.tank(obstacle, n0)
+def _setup(obstacle, n0, coef, mu=1, inactive=True):
+    p = P.tank(obstacle, n0, inactive)
     g = S.Octree(p.desc)
     f = g.faces()
     beta = P.face_beta(p, f)
@@ -30,28 +34,47 @@ def _setup(obstacle, n0, coef, mu=1):
     h = S.Hierarchy(g, beta, p.bc, S.mg_params(coef=coef, mu=mu))
     b = torch.from_numpy(P.rhs(p, lv, f, beta)).cuda()
     hc, xc, yc, zc = P.leaf_centres(n0, lv)
-    return h, b, hc, torch.from_numpy(yc - 1.0).cuda()
+    return p, h, b, hc, torch.from_numpy(yc - 1.0).cuda()
 
 
 @pytest.mark.parametrize("obstacle", ["sphere", "star"])
 def test_fp64_tank_solve_is_the_hydrostatic_field(obstacle):
-    h, b, hc, ref = _setup(obstacle, 32, "f64")
+    p, h, b, hc, ref = _setup(obstacle, 32, "f64", inactive=False)
     x, st = h.solve(b, tol=1e-12, precision="fp64", max_iter=100)
     assert st.converged
     assert (x - ref).abs().max().item() <= 1e-9
 
 
 @pytest.mark.parametrize("obstacle", ["sphere", "star"])
-def test_full_size_tank_w_cycle(obstacle):
-    h, b, hc, ref = _setup(obstacle, 64, "f32", mu=2)
+def test_inactive_solid_cells_match_the_oracle(obstacle):
+    p, h, b, hc, ref = _setup(obstacle, 16, "f32", mu=2)
+    t = O.Octree(p.desc)
+    H = OP.Hierarchy(t, P.face_beta(p, t.faces()), p.bc)
+    act = H.A.diagonal() != 0.0
+    assert not np.all(act)
+    bo = b.cpu().numpy()
+    xo = sla.spsolve(H.A.tocsr()[act][:, act].tocsc(), bo[act])
+    x, st = h.solve(b, tol=1e-9, precision="mixed", max_iter=100)
+    assert st.converged
+    x = x.cpu().numpy()
+    assert np.all(x[~act] == 0.0)
+    assert np.abs(x[act] - xo).max() <= 1e-6 * np.abs(xo).max()
+
+
+@pytest.mark.parametrize("obstacle, max_its, min_fitted", [("sphere", 6, 10.0), ("star", 12, 3.0)])
+def test_full_size_tank_w_cycle(obstacle, max_its, min_fitted):
+    p, h, b, hc, ref = _setup(obstacle, 64, "f32", mu=2)
     x, st = h.solve(b, tol=1e-6, precision="mixed", max_iter=100)
-    assert st.converged and st.iterations <= 10, st.iterations
+    assert st.converged and st.iterations <= max_its, st.iterations
     k = st.iterations
     slope = np.polyfit(np.arange(k + 1), np.log([st.hist[i] for i in range(k + 1)]), 1)[0]
-    assert math.exp(-slope) > 3.0, math.exp(-slope)
-    assert (x - ref).abs().max().item() <= 1e-5
+    assert math.exp(-slope) > min_fitted, math.exp(-slope)
+    Ax = h.apply_A(x)
     V = torch.from_numpy(hc ** 3).cuda()
-    div = (b - h.apply_A(x)) / V
-    div0 = b / V
-    rms = lambda e: math.sqrt(float((V * e * e).sum() / V.sum()))
-    assert rms(div) <= 1e-5 * rms(div0), (rms(div), rms(div0))
+    # active cells: a nonzero row (the apply of a unit vector is not needed: inactive
+    # cells have no coefficient, so their rhs and solution are 0 and A x is 0 there)
+    act = (b != 0) | (x != 0)
+    assert (x[~act] == 0).all()
+    assert (x - ref)[act].abs().max().item() <= 5e-3
+    rms = lambda e, m: math.sqrt(float((V[m] * e[m] * e[m]).sum() / V[m].sum()))
+    assert rms((b - Ax) / V, act) <= 1e-5 * rms(b / V, act)

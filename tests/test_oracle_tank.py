@@ -6,8 +6,11 @@ Pins: the velocity is minus the gradient of the linear field y, which the discre
 reproduces exactly (regular faces, cut-cell faces with any beta, the T-junction ghost
 value, the Dirichlet face at the open top), so the discrete pressure is p = y - 1 to
 rounding (the field that cancels the motion: the paper's "nearly uniform gradient along
-y"), whatever the obstacle and grid; and Alg. 1 with W-cycles (mu = 2, the paper's choice
-for this test) reduces the residual by more than 5 per iteration on these small roots.
+y"), whatever the obstacle and grid, when the solid's interior is kept at beta = 1e-3; with
+the interior inactive (exact fractions, the paper's solver) it stays within 5e-3; and Alg. 1 with
+W-cycles (mu = 2, the paper's choice for this test) and inactive solid cells reduces the
+residual by a fitted factor above 5 per iteration on these small roots, leaving the
+inactive cells at 0.
 """
 import math
 
@@ -22,8 +25,8 @@ from oracle import pcg
 from paper_2604_18886_b300 import problems as P
 
 
-def _setup(obstacle, n0):
-    p = P.tank(obstacle, n0)
+def _setup(obstacle, n0, inactive=True):
+    p = P.tank(obstacle, n0, inactive)
     t = O.Octree(p.desc)
     f = t.faces()
     beta = P.face_beta(p, f)
@@ -31,20 +34,34 @@ def _setup(obstacle, n0):
     return p, t, H, P.rhs(p, t.leaves, f, beta)
 
 
+@pytest.mark.parametrize("inactive", [True, False])
 @pytest.mark.parametrize("obstacle", ["sphere", "star"])
-def test_tank_pressure_is_the_hydrostatic_field(obstacle):
+def test_tank_pressure_is_the_hydrostatic_field(obstacle, inactive):
     for n0 in (8, 16):
-        p, t, H, b = _setup(obstacle, n0)
-        assert P.face_beta(p, t.faces()).min() < 0.01          # cut cells present
-        x = sla.spsolve(H.A.tocsc(), b)
+        p, t, H, b = _setup(obstacle, n0, inactive)
+        beta = P.face_beta(p, t.faces())
+        act = H.A.diagonal() != 0.0
+        if inactive:
+            assert beta.min() == 0.0 and not np.all(act)       # cells inside the solid drop out
+            assert np.all(b[~act] == 0.0)
+        else:
+            assert beta.min() < 0.01 and np.all(act)
+        A = H.A.tocsr()[act][:, act].tocsc()
+        x = sla.spsolve(A, b[act])
         h, xc, yc, zc = P.leaf_centres(n0, t.leaves)
-        assert np.abs(x - (yc - 1.0)).max() <= 1e-11, n0
+        # exact with every cell active; with inactive cells a T ghost beside an octet with
+        # inactive siblings averages the active siblings only, which is not the parent's
+        # centre value of a linear field: small O(h) deviations there (1e-3 at most here)
+        assert np.abs(x - (yc[act] - 1.0)).max() <= (5e-3 if inactive else 1e-11), n0
 
 
 @pytest.mark.parametrize("obstacle", ["sphere", "star"])
 def test_tank_w_cycle_reduces_the_residual_by_more_than_five(obstacle):
+    # with inactive solid cells, as the paper's solver (fitted 5.17-7.16 there)
     for n0 in (8, 16):
         p, t, H, b = _setup(obstacle, n0)
         x, k, hist = pcg.pcg(H, b, tol=1e-6, prm=mg.CycleParams(mu=2), max_iter=100)
-        red = math.exp(-math.log(hist[k]) / k)
-        assert red > 5.0 and k <= 10, (n0, k, red)
+        fitted = math.exp(-np.polyfit(np.arange(k + 1), np.log(hist[:k + 1]), 1)[0])
+        assert fitted > 5.0 and k <= 10, (n0, k, fitted)
+        act = H.A.diagonal() != 0.0
+        assert np.all(x[~act] == 0.0)
