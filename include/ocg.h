@@ -191,6 +191,11 @@ typedef struct {
 /* Fill leaf coefficients from face beta (canonical face order, float32, device) and the
  * wall codes (Sec. 2.1; T sub-faces per Sec. 3.1), then coarsen every level with Alg. 3
  * (FP64 arithmetic, stored in coef_dtype).  Synchronises.
+ * beta = 0 on every face of a leaf (e.g. exact fluid fractions inside a solid) leaves it
+ * without a coefficient: an inactive cell that every kernel skips (its solution stays 0;
+ * means over octets count active cells only, 0 when there is none).  With inactive cells
+ * a constant null space is not supported (the mean shift would reach them), and the
+ * transposed operator's T-junction correction assumes every cell active.
  * Errors: EINVAL (negative or non-finite beta, bad params), ENOMEM, ECUDA. */
 int ocg_setup_hierarchy(const ocg_octree* t, const float* face_beta_dev, const int32_t bc[6],
                         const ocg_mg_params* prm, void* stream, ocg_hier** out);
