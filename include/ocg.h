@@ -27,6 +27,7 @@
 #ifndef OCG_H
 #define OCG_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -252,6 +253,9 @@ int ocg_vcycle_transpose(ocg_hier* h, int32_t dtype, const void* z_dev, void* r_
                                   events become graph nodes around the probed kernels */
 #define OCG_SOLVE_BICGSTAB 8   /* flags, with OCG_SOLVE_TRANSPOSE: solve A^T x = b by BiCGStab
                                   instead of Alg. 1 (both preconditioned by M^T) */
+#define OCG_SOLVE_WARM 16      /* flags: x_dev holds the initial guess x0 on input (else
+                                  x0 = 0); r0 = b - A x0 (A^T x0), the stop test stays
+                                  ||r|| <= tol ||b|| */
 
 typedef struct {
     double tol;              /* stop when ||r||_2 <= tol ||b||_2 (recursive residual) */
@@ -368,6 +372,19 @@ int ocg_apply_A_f32_noalloc(ocg_hier* h, const float* x_dev, float* y_dev, void*
 int ocg_probe_set(ocg_hier* h, int32_t kind, int32_t level);
 int ocg_probe_read(ocg_hier* h, void* stream, int64_t* launches, double* total_ms,
                    int64_t* cells_per_launch);
+
+/* Device memory hooks: from now on the library obtains every device buffer (octree
+ * tables, coefficients, work vectors, graphs' scratch) from alloc(bytes, ctx), which must
+ * return memory of the current device aligned to 256 bytes or NULL (ENOMEM), and releases
+ * it with free(ptr, ctx) — e.g. a framework's caching allocator.  Both NULL restores
+ * cudaMalloc / cudaFree.  A block is always released by the hooks that made it, so the
+ * hooks may change while objects live, but they must stay callable until those objects
+ * are destroyed.  Pinned host buffers stay cudaMallocHost.  Thread-safe.
+ * Errors: EINVAL (one hook given without the other). */
+typedef void* (*ocg_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*ocg_free_fn)(void* ptr, void* ctx);
+int ocg_set_allocator(ocg_alloc_fn alloc, ocg_free_fn free_fn, void* ctx);
+
 /* Total kernel launches issued by this library in this process. */
 int ocg_launch_count(int64_t* n);
 

@@ -45,6 +45,7 @@ OCG_SOLVE_EAGER = 1
 OCG_SOLVE_TRANSPOSE = 2
 OCG_SOLVE_UNROLLED = 4
 OCG_SOLVE_BICGSTAB = 8
+OCG_SOLVE_WARM = 16
 
 
 class SolveParams(C.Structure):
@@ -64,6 +65,9 @@ class OcgError(RuntimeError):
 
 
 _lib = None
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 
 # (name, restype, argtypes)
 _SIGS = [
@@ -94,6 +98,7 @@ _SIGS = [
     ("ocg_probe_read", C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_double),
                                  C.POINTER(C.c_int64)]),
     ("ocg_launch_count", C.c_int, [C.POINTER(C.c_int64)]),
+    ("ocg_set_allocator", C.c_int, [ALLOC_FN, FREE_FN, C.c_void_p]),
     ("ocg_batch_create", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.POINTER(C.c_void_p)]),
     ("ocg_batch_destroy", None, [C.c_void_p]),
     ("ocg_batch_info", C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),

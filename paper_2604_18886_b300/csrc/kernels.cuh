@@ -326,6 +326,14 @@ __global__ void k_cast(const TI* __restrict__ in, TO* __restrict__ out, int n) {
     if (i < n) out[i] = TO(in[i]);
 }
 
+// r -= a over the tree cells (the warm start's r = b - A x0)
+template <class T>
+__global__ void k_sub(T* __restrict__ r, const T* __restrict__ a, int n) {
+    pdl_enter();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) r[i] = r[i] - a[i];
+}
+
 template <class TI, class TO>
 __global__ void k_gather(const TI* __restrict__ in, TO* __restrict__ out, const int32_t* __restrict__ leaf_cell,
                          int n) {

@@ -17,6 +17,8 @@
 #include <functional>
 #include <memory>
 #include <mutex>
+#include <unordered_map>
+#include <mutex>
 #include <stdexcept>
 #include <string>
 #include <type_traits>
@@ -49,11 +51,34 @@ void ck(cudaError_t e, const char* what) {
 
 void ck_launch(const char* what) { ck(cudaGetLastError(), what); }
 
+// Device allocations go through cudaMalloc or the caller's hooks (ocg_set_allocator); a
+// block is freed by the allocator that made it, whatever is set at that time.
+struct AllocHooks {
+    ocg_alloc_fn alloc = nullptr;
+    ocg_free_fn free = nullptr;
+    void* ctx = nullptr;
+};
+std::mutex g_alloc_mu;
+AllocHooks g_hooks;
+std::unordered_map<void*, AllocHooks> g_hooked;   // blocks made through the hooks
+
 template <class T>
 T* dalloc(int64_t n) {
     void* p = nullptr;
     if (n <= 0) n = 1;
-    ck(cudaMalloc(&p, (size_t)n * sizeof(T)), "cudaMalloc");
+    const size_t bytes = (size_t)n * sizeof(T);
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    if (g_hooks.alloc) {
+        p = g_hooks.alloc(bytes, g_hooks.ctx);
+        if (!p) throw Status(OCG_ENOMEM, "allocator hook returned NULL");
+        if (reinterpret_cast<uintptr_t>(p) % 256) {
+            g_hooks.free(p, g_hooks.ctx);
+            throw Status(OCG_EINVAL, "allocator hook returned memory not aligned to 256 bytes");
+        }
+        g_hooked[p] = g_hooks;
+        return (T*)p;
+    }
+    ck(cudaMalloc(&p, bytes), "cudaMalloc");
     return (T*)p;
 }
 
@@ -65,7 +90,19 @@ T* dupload(const std::vector<T>& v) {
 }
 
 void dfree(void* p) {
-    if (p) cudaFree(p);
+    if (!p) return;
+    AllocHooks hk;
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        auto it = g_hooked.find(p);
+        if (it == g_hooked.end()) {
+            cudaFree(p);
+            return;
+        }
+        hk = it->second;
+        g_hooked.erase(it);
+    }
+    hk.free(p, hk.ctx);
 }
 
 template <class F>
@@ -277,7 +314,7 @@ struct ocg_hier {
     int* tail_sched = nullptr;    // device copies of the tail pass schedules (float, double)
     int* tail_sched2 = nullptr;
     cudaStream_t cap = nullptr;   // private stream for graph capture
-    GraphSolve graphs[3][3][2];   // [A by PCG, A^T by PCG, A^T by BiCGStab][precision][null space]
+    GraphSolve graphs[3][3][2][2];   // [A by PCG, A^T by PCG, A^T by BiCGStab][precision][null space][warm]
     float* beta = nullptr;        // copy of the face fractions (transposed operator)
     // BiCGStab vectors over the tree cells (adjoint solves), allocated on first use
     double *rhat = nullptr, *s = nullptr, *tv = nullptr, *ph = nullptr, *sh = nullptr;
@@ -292,10 +329,11 @@ struct ocg_hier {
     ~ocg_hier() {
         for (auto& tr : graphs)
             for (auto& row : tr)
-                for (auto& gs : row) {
-                    if (gs.exec) cudaGraphExecDestroy(gs.exec);
-                    if (gs.graph) cudaGraphDestroy(gs.graph);
-                }
+                for (auto& pair : row)
+                    for (auto& gs : pair) {
+                        if (gs.exec) cudaGraphExecDestroy(gs.exec);
+                        if (gs.graph) cudaGraphDestroy(gs.graph);
+                    }
         for (double* v : {rhat, s, tv, ph, sh, Xc, UST, Tacc}) dfree(v);
         dfree(beta);
         dfree(tseed);
@@ -863,6 +901,7 @@ struct PcgImpl {
     Ctx& c;
     cudaGraphConditionalHandle cond;
     int set_cond;
+    bool warm = false;   // x0 from xt (OCG_SOLVE_WARM) instead of 0
 
     const HostTree& H() const { return h->t->H; }
     TO* x() { return (TO*)h->x; }
@@ -877,11 +916,18 @@ struct PcgImpl {
     void zero(void* ptr, size_t bytes) { ck(cudaMemsetAsync(ptr, 0, bytes, c.st), "memset"); }
 
     void begin() {
-        zero(h->x, n() * sizeof(TO));
+        if (warm) launch(c, -1, 0, n(), [&] { launch_k(k_cast<double, TO>, gb(), BLK, 0, c.st, h->xt, x(), n()); });
+        else zero(h->x, n() * sizeof(TO));
         zero(h->p, n() * sizeof(TO));
         zero(h->B, H().ncell * sizeof(TV));
         launch(c, -1, 0, n(), [&] { launch_k(k_cast<double, TO>, gb(), BLK, 0, c.st, h->bt, r(), n()); });
         launch(c, -1, 0, n(), [&] { launch_k(k_dot<TO, TO, true>, rb(), BLK, 0, c.st, r(), r(), n(), make_red(h, rb(), OP_BB)); });
+        if (warm) {
+            // r = b - A x0 (A^T x0); ||b|| above stays the reference of the stop test
+            if constexpr (TR) apply_outer_T<TO, TC, TW>(h, Co, x(), Ap(), c);
+            else apply_outer<TO, TC, TW>(h, Co, x(), Ap(), OP_NONE, c);
+            launch(c, -1, 0, n(), [&] { launch_k(k_sub<TO>, gb(), BLK, 0, c.st, r(), (const TO*)Ap(), n()); });
+        }
         launch(c, -1, 0, n(), [&] { launch_k(k_project<TO, TV>, gb(), BLK, 0, c.st, r(), h->t->flags, h->S, B(), n()); });
         ck_launch("begin");
         precondition();
@@ -960,6 +1006,7 @@ struct BiCG {
     Ctx& c;
     cudaGraphConditionalHandle cond;
     int set_cond;
+    bool warm = false;   // x0 from xt (OCG_SOLVE_WARM) instead of 0
 
     const HostTree& H() const { return h->t->H; }
     TO* V(double* p) { return (TO*)p; }
@@ -971,13 +1018,19 @@ struct BiCG {
     void zero(void* ptr, size_t bytes) { ck(cudaMemsetAsync(ptr, 0, bytes, c.st), "memset"); }
 
     void begin() {
-        zero(h->x, n() * sizeof(TO));
+        if (warm) launch(c, -1, 0, n(), [&] { launch_k(k_cast<double, TO>, gb(), BLK, 0, c.st, h->xt, V(h->x), n()); });
+        else zero(h->x, n() * sizeof(TO));
         zero(h->p, n() * sizeof(TO));
-        zero(h->Ap, n() * sizeof(TO));
         zero(h->B, H().ncell * sizeof(TV));
         TO* r = V(h->r);
         launch(c, -1, 0, n(), [&] { launch_k(k_cast<double, TO>, gb(), BLK, 0, c.st, h->bt, r, n()); });
         launch(c, -1, 0, n(), [&] { launch_k(k_dot<TO, TO, true>, rb(), BLK, 0, c.st, r, r, n(), make_red(h, rb(), OP_BB)); });
+        if (warm) {
+            // r = b - A^T x0; ||b|| above stays the reference of the stop test
+            apply_outer_T<TO, TC, TW>(h, Co, V(h->x), V(h->Ap), c);
+            launch(c, -1, 0, n(), [&] { launch_k(k_sub<TO>, gb(), BLK, 0, c.st, r, (const TO*)V(h->Ap), n()); });
+        }
+        zero(h->Ap, n() * sizeof(TO));
         if (ns)
             launch(c, -1, 0, n(), [&] {
                 launch_k(k_project<TO, TV>, gb(), BLK, 0, c.st, r, h->t->flags, h->S, (TV*)nullptr, n());
@@ -1032,7 +1085,7 @@ struct BiCG {
 // BiCG (both: begin / body / finish, the reduction that ends each of begin and body sets
 // the WHILE condition).
 template <template <class, class, class, class> class Solver, class TO, class TV, class TC, class TW>
-void build_graph(ocg_hier* h, Coefs<TC, TW> Co, bool ns, GraphSolve& gs) {
+void build_graph(ocg_hier* h, Coefs<TC, TW> Co, bool ns, bool warm, GraphSolve& gs) {
     if (!h->cap) ck(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking), "cudaStreamCreate");
     cudaStream_t cs = h->cap;
     Ctx c{cs, nullptr, 0};
@@ -1044,6 +1097,7 @@ void build_graph(ocg_hier* h, Coefs<TC, TW> Co, bool ns, GraphSolve& gs) {
         cudaGraphConditionalHandle cond;
         ck(cudaGraphConditionalHandleCreate(&cond, g, 0, 0), "conditional handle");
         Solver<TO, TV, TC, TW> pc{h, Co, ns, c, cond, 1};
+        pc.warm = warm;
         pc.begin();
         const cudaGraphNode_t* deps = nullptr;
         size_t ndeps = 0;
@@ -1068,6 +1122,7 @@ void build_graph(ocg_hier* h, Coefs<TC, TW> Co, bool ns, GraphSolve& gs) {
         ck(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal),
            "begin body capture");
         Solver<TO, TV, TC, TW> pb{h, Co, ns, cb, cond, 1};
+        pb.warm = warm;
         pb.body();
         cudaGraph_t bg = nullptr;
         ck(cudaStreamEndCapture(cs, &bg), "end body capture");
@@ -1120,6 +1175,7 @@ int krylov_solve(ocg_hier* h, Coefs<TC, TW> Co, int prec, const double* b_user, 
     const HostTree& H = t->H;
     const bool transpose = (sp->flags & OCG_SOLVE_TRANSPOSE) != 0;
     const bool bicg = transpose && (sp->flags & OCG_SOLVE_BICGSTAB) != 0;
+    const bool warm = (sp->flags & OCG_SOLVE_WARM) != 0;
     const bool ns = sp->nullspace < 0 ? h->ns_auto : sp->nullspace != 0;
     const bool eager = (sp->flags & OCG_SOLVE_EAGER) || h->probe.kind != OCG_PROBE_OFF;
     // scalars: tolerance, iteration cap, null-space flag, counters
@@ -1133,9 +1189,17 @@ int krylov_solve(ocg_hier* h, Coefs<TC, TW> Co, int prec, const double* b_user, 
     launch(c, -1, 0, H.nleaf, [&] {
         launch_k(k_scatter<double, double>, nblk(H.nleaf), BLK, 0, st, b_user, h->bt, t->leaf_cell, (int)H.nleaf);
     });
+    if (warm) {
+        // the initial guess, on the leaves of the FP64 tree vector (begin casts it to x)
+        ck(cudaMemsetAsync(h->xt, 0, H.ntree * sizeof(double), st), "memset");
+        launch(c, -1, 0, H.nleaf, [&] {
+            launch_k(k_scatter<double, double>, nblk(H.nleaf), BLK, 0, st, (const double*)x_user, h->xt, t->leaf_cell,
+                     (int)H.nleaf);
+        });
+    }
     ck_launch("scatter");
     int64_t kernels = c.count;
-    GraphSolve& gs = h->graphs[!transpose ? 0 : (bicg ? 2 : 1)][prec][ns ? 1 : 0];
+    GraphSolve& gs = h->graphs[!transpose ? 0 : (bicg ? 2 : 1)][prec][ns ? 1 : 0][warm ? 1 : 0];
     const bool unrolled = (sp->flags & OCG_SOLVE_UNROLLED) != 0;
     if (unrolled) {
         // measurement form: exactly max_iter iterations captured into one flat graph (no
@@ -1147,6 +1211,7 @@ int krylov_solve(ocg_hier* h, Coefs<TC, TW> Co, int prec, const double* b_user, 
         ck(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
         try {
             Solver<TO, TV, TC, TW> pc{h, Co, ns, cc, 0, 0};
+            pc.warm = warm;
             pc.begin();
             const int nbody = bicg ? sp->max_iter : sp->max_iter - 1;
             for (int q = 0; q < nbody; ++q) pc.body();
@@ -1167,6 +1232,7 @@ int krylov_solve(ocg_hier* h, Coefs<TC, TW> Co, int prec, const double* b_user, 
         kernels = cc.count;
     } else if (eager) {
         Solver<TO, TV, TC, TW> pc{h, Co, ns, c, 0, 0};
+        pc.warm = warm;
         pc.begin();
         while (true) {
             ck(cudaMemcpyAsync(h->hS, h->S, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, st), "copy scalars");
@@ -1177,7 +1243,7 @@ int krylov_solve(ocg_hier* h, Coefs<TC, TW> Co, int prec, const double* b_user, 
         pc.finish();
         kernels = c.count;
     } else {
-        if (!gs.exec) build_graph<Solver, TO, TV, TC, TW>(h, Co, ns, gs);
+        if (!gs.exec) build_graph<Solver, TO, TV, TC, TW>(h, Co, ns, warm, gs);
         ck(cudaGraphLaunch(gs.exec, st), "graph launch");
     }
     // the solution is read from xt (FP64 copy of x made by finish), shifted to zero mean
@@ -1719,7 +1785,7 @@ int ocg_pcg_solve(ocg_hier* h, const double* b, double* x, const ocg_solve_param
     int g = guard([&] {
         if (!h || !b || !x || !sp || !stats) throw Status(OCG_EINVAL, "null argument");
         if (!(sp->tol > 0) || sp->max_iter < 1) throw Status(OCG_EINVAL, "tol must be > 0 and max_iter >= 1");
-        if (sp->flags & ~(OCG_SOLVE_EAGER | OCG_SOLVE_TRANSPOSE | OCG_SOLVE_UNROLLED | OCG_SOLVE_BICGSTAB))
+        if (sp->flags & ~(OCG_SOLVE_EAGER | OCG_SOLVE_TRANSPOSE | OCG_SOLVE_UNROLLED | OCG_SOLVE_BICGSTAB | OCG_SOLVE_WARM))
             throw Status(OCG_EINVAL, "unknown solve flags");
         cudaStream_t st = (cudaStream_t)stream;
         const bool tr = (sp->flags & OCG_SOLVE_TRANSPOSE) != 0;
@@ -1776,6 +1842,16 @@ int ocg_probe_read(ocg_hier* h, void* stream, int64_t* launches, double* total_m
         *total_ms = tot;
         *cells = h->probe.cells;
         h->probe.used = 0;
+    });
+}
+
+int ocg_set_allocator(ocg_alloc_fn alloc, ocg_free_fn free_fn, void* ctx) {
+    return guard([&] {
+        if ((alloc == nullptr) != (free_fn == nullptr)) throw Status(OCG_EINVAL, "give both hooks or neither");
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        g_hooks.alloc = alloc;
+        g_hooks.free = free_fn;
+        g_hooks.ctx = alloc ? ctx : nullptr;
     });
 }
 

@@ -115,6 +115,31 @@ SWEEP_FORM_NAMES = {L.OCG_SWEEP_OCTET: "octet", L.OCG_SWEEP_CELL: "cell", L.OCG_
                     L.OCG_SWEEP_TILE: "tile"}
 
 
+_HOOKS = []   # callbacks stay alive: blocks made through them are released through them
+
+
+def use_torch_allocator(enable=True):
+    """Route the library's device allocations through torch's caching allocator
+    (ocg_set_allocator), or back to cudaMalloc with enable=False."""
+    import torch
+    if not enable:
+        L.check(L.lib().ocg_set_allocator(L.ALLOC_FN(), L.FREE_FN(), None))
+        return
+
+    def alloc(nbytes, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes))
+        except RuntimeError:
+            return None
+
+    def free(ptr, ctx):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    hooks = (L.ALLOC_FN(alloc), L.FREE_FN(free))
+    _HOOKS.append(hooks)
+    L.check(L.lib().ocg_set_allocator(hooks[0], hooks[1], None))
+
+
 def mg_params(mu=1, nu_pre=2, nu_post=2, nu_coarsest=10, beta=2.0, alpha=2.0, coef="f32",
               bf16_coarse=False, sweep="auto", mu_min_cells=0, coarsening="algebraic") -> L.MGParams:
     """coarsening: "algebraic" (Alg. 3, the paper's method) or "geometric" (the geometric
@@ -234,13 +259,16 @@ class Hierarchy:
 
     def solve(self, b, x=None, tol=1e-6, max_iter=100, precision="mixed", nullspace=-1,
               stream=None, raise_on_notconv=True, eager=False, transpose=False, unrolled=False,
-              method="pcg"):
+              method="pcg", warm=False):
         """x with A x = b (PCG, Alg. 1), or A^T x = b with transpose=True (the adjoint
         system, preconditioned by the transposed cycle M^T: Alg. 1 with method="pcg",
-        BiCGStab with method="bicgstab").  Returns (x, stats)."""
+        BiCGStab with method="bicgstab").  warm=True starts from the content of x (which
+        must be given) instead of 0.  Returns (x, stats)."""
         import torch
         assert b.dtype == torch.float64 and b.is_cuda
         if x is None:
+            if warm:
+                raise ValueError("warm=True needs the initial guess in x")
             x = torch.empty_like(b)
         sp = L.SolveParams()
         sp.tol, sp.max_iter, sp.precision, sp.nullspace = tol, max_iter, PRECISIONS[precision], nullspace
@@ -248,7 +276,8 @@ class Hierarchy:
             raise ValueError("method must be 'pcg' or 'bicgstab'")
         sp.flags = ((L.OCG_SOLVE_EAGER if eager else 0) | (L.OCG_SOLVE_TRANSPOSE if transpose else 0) |
                     (L.OCG_SOLVE_UNROLLED if unrolled else 0) |
-                    (L.OCG_SOLVE_BICGSTAB if transpose and method == "bicgstab" else 0))
+                    (L.OCG_SOLVE_BICGSTAB if transpose and method == "bicgstab" else 0) |
+                    (L.OCG_SOLVE_WARM if warm else 0))
         st = L.SolveStats()
         code = L.lib().ocg_pcg_solve(self._h, L.ptr(b), L.ptr(x), C.byref(sp), C.byref(st),
                                      self._stream(stream))
