@@ -80,6 +80,57 @@ __device__ __forceinline__ void ldc8(const __nv_bfloat16* __restrict__ p, float 
     }
 }
 
+// The four cells of the octet at p on one side of axis a (the cells whose bit a equals
+// side), in the sub-face order q of clear_slot.  A z layer is four consecutive cells and a
+// y layer two pairs, so both come in vector loads (one request per 16 or 8 bytes instead
+// of one per cell); an x layer is every other cell.  p is the octet's first cell, so 16-byte
+// aligned for 4-byte types.  The values are the ones the per-cell loads would return.
+template <class T>
+__device__ __forceinline__ T ld1(const T* p, bool ro) { return ro ? __ldg(p) : *p; }
+template <class V>
+__device__ __forceinline__ V ldv(const void* p, bool ro) {
+    return ro ? __ldg(reinterpret_cast<const V*>(p)) : *reinterpret_cast<const V*>(p);
+}
+__device__ __forceinline__ void ld_layer(const float* __restrict__ p, int a, int side, bool ro, float (&r)[4]) {
+    if (a == 2) {
+        const float4 v = ldv<float4>(p + 4 * side, ro);
+        r[0] = v.x; r[1] = v.y; r[2] = v.z; r[3] = v.w;
+    } else if (a == 1) {
+        const float2 v0 = ldv<float2>(p + 2 * side, ro), v1 = ldv<float2>(p + 4 + 2 * side, ro);
+        r[0] = v0.x; r[1] = v0.y; r[2] = v1.x; r[3] = v1.y;
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) r[q] = ld1(p + 2 * q + side, ro);
+    }
+}
+__device__ __forceinline__ void ld_layer(const double* __restrict__ p, int a, int side, bool ro, double (&r)[4]) {
+    if (a == 2) {
+        const double2 v0 = ldv<double2>(p + 4 * side, ro), v1 = ldv<double2>(p + 4 * side + 2, ro);
+        r[0] = v0.x; r[1] = v0.y; r[2] = v1.x; r[3] = v1.y;
+    } else if (a == 1) {
+        const double2 v0 = ldv<double2>(p + 2 * side, ro), v1 = ldv<double2>(p + 4 + 2 * side, ro);
+        r[0] = v0.x; r[1] = v0.y; r[2] = v1.x; r[3] = v1.y;
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) r[q] = ld1(p + 2 * q + side, ro);
+    }
+}
+__device__ __forceinline__ void ld_layer(const __nv_bfloat16* __restrict__ p, int a, int side, bool ro,
+                                         __nv_bfloat16 (&r)[4]) {
+    if (a == 2) {
+        const uint2 v = ldv<uint2>(p + 4 * side, ro);
+        const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(&v);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) r[q] = h[q];
+    } else if (a == 1) {
+        const __nv_bfloat162 v0 = ldv<__nv_bfloat162>(p + 2 * side, ro), v1 = ldv<__nv_bfloat162>(p + 4 + 2 * side, ro);
+        r[0] = v0.x; r[1] = v0.y; r[2] = v1.x; r[3] = v1.y;
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) r[q] = ld1(p + 2 * q + side, ro);
+    }
+}
+
 // Coordinates of octet o in a lexicographic ni^3 grid (shifts when ni is a power of two).
 __device__ __forceinline__ void octet_coords(int o, int ni, int& I, int& J, int& K) {
     if ((ni & (ni - 1)) == 0) {
@@ -196,8 +247,7 @@ __device__ __forceinline__ void octet_Au(const Tables& T, const Coefs<TC, TW>& C
         if (v >= 0) {
             const int n8 = off + 8 * v;
             TV nu[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) nu[q] = U[n8 + (clear_slot(a, q) | bit)];
+            ld_layer(U + n8, a, 1, false, nu);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int s = clear_slot(a, q);
@@ -218,11 +268,11 @@ __device__ __forceinline__ void octet_Au(const Tables& T, const Coefs<TC, TW>& C
             const int n8 = off + 8 * w;
             const TC* cc = a == 0 ? C.cx : (a == 1 ? C.cy : C.cz);
             TV nu[4], nc[4];
+            TC ncr[4];
+            ld_layer(U + n8, a, 0, false, nu);
+            ld_layer(cc + n8, a, 0, true, ncr);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                nu[q] = U[n8 + clear_slot(a, q)];
-                nc[q] = TV(tov(__ldg(cc + n8 + clear_slot(a, q))));
-            }
+            for (int q = 0; q < 4; ++q) nc[q] = TV(tov(ncr[q]));
 #pragma unroll
             for (int q = 0; q < 4; ++q) Au[clear_slot(a, q) | bit] += nc[q] * nu[q];
         } else if (w <= -2) {
