@@ -142,7 +142,7 @@ def _setup(dev, sweep="auto"):
     import torch
     from paper_2604_18886_b300 import problems as P
     from paper_2604_18886_b300 import solver as S
-    p = P.c2(64)
+    p = P.two_level_ball(64)
     tree = S.Octree(p.desc)
     faces = tree.faces()
     beta = P.face_beta(p, faces)
@@ -215,7 +215,7 @@ def _cut_cell(dev, stream, flush, args):
     import torch
     from paper_2604_18886_b300 import problems as P
     from paper_2604_18886_b300 import solver as S
-    p = P.c3(64, 2)
+    p = P.cut_cell(64, 2)
     g = S.Octree(p.desc)
     f = g.faces()
     beta = P.face_beta(p, f)
@@ -413,7 +413,7 @@ def _large(dev, stream, flush, args, peak):
     from paper_2604_18886_b300 import problems as P
     from paper_2604_18886_b300 import solver as S
     t0 = time.perf_counter()
-    p = P.c5(args.large_n0, 3)
+    p = P.sine_band(args.large_n0, 3)
     g = S.Octree(p.desc)
     t_build = time.perf_counter() - t0
     beta, bh = P.large_inputs(p, g.n_leaves, g.n_faces, g.faces_range, dev)
@@ -543,7 +543,7 @@ def _large(dev, stream, flush, args, peak):
                          "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "bytes_per_cell": SWEEP_BYTES_PER_CELL,
                          "cells_per_launch": ce.value, "launches": nl.value, "avg_launch_us": round(sweep_us, 2),
-                         "traffic": _profiled_traffic("sweep_c5_level%d_%s" % (D, form), ce.value),
+                         "traffic": _profiled_traffic("sweep_sineband_level%d_%s" % (D, form), ce.value),
                          "traffic_note": "dram bytes per cell of an ncu capture at 64^3 root (same field, "
                                          "effective 512^3) times the cells of one launch"},
             "adjoint": adj}
@@ -562,7 +562,7 @@ def _batched(dev, stream, flush, args):
     from paper_2604_18886_b300 import solver as S
     hs, bs, leaves = [], [], 0
     for k in range(64):
-        p = P.c4_tree(k)
+        p = P.batch_tree(k)
         g = S.Octree(p.desc)
         f = g.faces()
         beta = P.face_beta(p, f)
@@ -772,7 +772,7 @@ def run_ours(args):
     sweep_us = sw_ms * 1e3 / max(sw_n, 1)
     achieved = SWEEP_BYTES_PER_CELL * sw_cells / (sweep_us / 1e6) / 1e9
     fwd = tuning.get(str(big), {}).get("form", "octet")
-    traffic = _profiled_traffic("sweep_c2_level%d_%s" % (big, fwd), sw_cells)
+    traffic = _profiled_traffic("sweep_ball64_level%d_%s" % (big, fwd), sw_cells)
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
@@ -826,7 +826,7 @@ def _oracle_problem():
     from oracle import octree as O
     from oracle import operator as OP
     from paper_2604_18886_b300 import problems as P
-    p = P.c2(64)
+    p = P.two_level_ball(64)
     t = O.Octree(p.desc)
     f = t.faces()
     beta = P.face_beta(p, f)

@@ -90,35 +90,35 @@ class Problem:
 # ----------------------------------------------------------------------------------
 # configurations
 
-C3_SPHERE = (0.5, 0.5, 0.5, 0.2)
-C3_BOX = (0.65, 0.2, 0.3, 0.85, 0.8, 0.7)
+CUT_SPHERE = (0.5, 0.5, 0.5, 0.2)
+CUT_BOX = (0.65, 0.2, 0.3, 0.85, 0.8, 0.7)
 
 
-def c1(n0: int = 32) -> Problem:
+def uniform(n0: int = 32) -> Problem:
     """Uniform n0^3 grid, beta = 1, homogeneous Dirichlet walls, p = sin(pi x)sin(pi y)sin(pi z)."""
-    return Problem("c1_uniform%d" % n0, OctreeDesc(n0, 0), (DIRICHLET,) * 6,
+    return Problem("uniform%d" % n0, OctreeDesc(n0, 0), (DIRICHLET,) * 6,
                    beta="one", rhs="sin_dirichlet", mode="fp64", tol=1e-10)
 
 
-def c2(n0: int = 64, radius: float = 0.25) -> Problem:
+def two_level_ball(n0: int = 64, radius: float = 0.25) -> Problem:
     """n0^3 base, cells with centre within `radius` of the cube centre refined once;
     beta = 1, Dirichlet walls with the manufactured p = exp(x) sin(2 pi y) cos(2 pi z)."""
     d = OctreeDesc(n0, 1, REFINE_BALL_CENTRE, spheres=[(0.5, 0.5, 0.5, radius)])
-    return Problem("c2_ball%d" % n0, d, (DIRICHLET,) * 6, beta="one", rhs="exp_sin_cos",
+    return Problem("ball%d" % n0, d, (DIRICHLET,) * 6, beta="one", rhs="exp_sin_cos",
                    mode="mixed", tol=1e-6)
 
 
-def c3(n0: int = 64, depth: int = 2, band: float = 0.05, seed: int = 4) -> Problem:
+def cut_cell(n0: int = 64, depth: int = 2, band: float = 0.05, seed: int = 4) -> Problem:
     """Cut-cell projection: band refinement around a solid sphere and box; fluid-fraction
     beta clamped to [1e-3, 1]; Neumann everywhere; rhs = divergence of N(0,1) face
     velocities, mean removed."""
-    d = OctreeDesc(n0, depth, REFINE_SDF_BAND, band=band, spheres=[C3_SPHERE], boxes=[C3_BOX])
-    return Problem("c3_cut%d_d%d" % (n0, depth), d, (NEUMANN,) * 6, beta="cut", rhs="divergence",
+    d = OctreeDesc(n0, depth, REFINE_SDF_BAND, band=band, spheres=[CUT_SPHERE], boxes=[CUT_BOX])
+    return Problem("cut%d_d%d" % (n0, depth), d, (NEUMANN,) * 6, beta="cut", rhs="divergence",
                    seed=seed, mode="mixed_bf16", tol=1e-6,
-                   solid_spheres=[C3_SPHERE], solid_boxes=[C3_BOX])
+                   solid_spheres=[CUT_SPHERE], solid_boxes=[CUT_BOX])
 
 
-def c4_tree(k: int) -> Problem:
+def batch_tree(k: int) -> Problem:
     """Tree k of the batched set: effective resolution from {64, 96, 128}, 2-3 levels,
     band refinement within 0.05 of a random sphere; even k Dirichlet beta=1, odd k cut-cell
     Neumann."""
@@ -132,13 +132,13 @@ def c4_tree(k: int) -> Problem:
     sph = (float(c[0]), float(c[1]), float(c[2]), r)
     d = OctreeDesc(n0, depth, REFINE_SDF_BAND, band=0.05, spheres=[sph])
     if k % 2 == 0:
-        return Problem("c4_t%d" % k, d, (DIRICHLET,) * 6, beta="one", rhs="normal",
+        return Problem("batch_t%d" % k, d, (DIRICHLET,) * 6, beta="one", rhs="normal",
                        seed=100 + k, mode="mixed", tol=1e-6)
-    return Problem("c4_t%d" % k, d, (NEUMANN,) * 6, beta="cut", rhs="normal", seed=100 + k,
+    return Problem("batch_t%d" % k, d, (NEUMANN,) * 6, beta="cut", rhs="normal", seed=100 + k,
                    mode="mixed", tol=1e-6, solid_spheres=[sph])
 
 
-def c5_sines(seed: int = 6, n: int = 8):
+def sine_waves(seed: int = 6, n: int = 8):
     """Random smooth field (1/n) sum sin(2 pi kappa (d.x) + theta), kappa in {1..4}."""
     rng = np.random.default_rng(seed)
     out = []
@@ -151,15 +151,15 @@ def c5_sines(seed: int = 6, n: int = 8):
     return out
 
 
-def c5(n0: int = 128, depth: int = 3, band: float = 0.02, seed: int = 7) -> Problem:
-    sines = c5_sines()
+def sine_band(n0: int = 128, depth: int = 3, band: float = 0.02, seed: int = 7) -> Problem:
+    sines = sine_waves()
     d = OctreeDesc(n0, depth, REFINE_SINE_BAND, band=band, sines=sines)
-    return Problem("c5_sine%d_d%d" % (n0, depth), d, (NEUMANN,) * 6, beta="cut",
+    return Problem("sine%d_d%d" % (n0, depth), d, (NEUMANN,) * 6, beta="cut",
                    rhs="divergence", seed=seed, mode="mixed", tol=1e-6, solid_sines=sines)
 
 
 def by_name(name: str) -> Problem:
-    table = {"c1": c1, "c2": c2, "c3": c3, "c5": c5}
+    table = {"uniform": uniform, "two_level_ball": two_level_ball, "cut_cell": cut_cell, "sine_band": sine_band}
     return table[name]()
 
 

@@ -23,7 +23,7 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-NAMES = ["c2_16", "c2_16_neumann", "c3_16_d2", "c4_t1", "band_12_d2", "c5_8_d2"]
+NAMES = ["ball_16", "ball_16_neumann", "cut_16_d2", "batch_t1", "band_12_d2", "sine_8_d2"]
 
 
 @pytest.mark.parametrize("name", NAMES)
@@ -61,7 +61,7 @@ def test_vcycle_transpose_fp32_matches_oracle(name):
     assert rel(r, mg.vcycle_T(H, z.astype(np.float64))) <= 1e-5
 
 
-@pytest.mark.parametrize("name", ["c3_16_d2", "band_12_d2", "c5_8_d2"])
+@pytest.mark.parametrize("name", ["cut_16_d2", "band_12_d2", "sine_8_d2"])
 def test_vcycle_transpose_hybrid_matches_oracle(name):
     from oracle import mg
     t, H, g, gh, f, beta = build(CASES[name](), "f64", mu=2, mu_min=4096)
@@ -71,7 +71,7 @@ def test_vcycle_transpose_hybrid_matches_oracle(name):
 
 
 @pytest.mark.parametrize("bf16", [False, True])
-@pytest.mark.parametrize("name", ["c3_16_d2", "c5_8_d2"])
+@pytest.mark.parametrize("name", ["cut_16_d2", "sine_8_d2"])
 def test_vcycle_transpose_is_the_adjoint_of_the_gpu_cycle(name, bf16):
     # (M^T z, r) = (z, M r) for the library's own M, in FP64 and in FP32 (also with the
     # BF16 coarse coefficients, where no oracle cycle exists)
@@ -90,7 +90,7 @@ def test_vcycle_transpose_is_the_adjoint_of_the_gpu_cycle(name, bf16):
     assert abs(lhs - rhs) <= 1e-5 * scale
 
 
-@pytest.mark.parametrize("name", ["c2_16", "c2_16_neumann", "c3_16_d2", "c4_t1", "c5_8_d2"])
+@pytest.mark.parametrize("name", ["ball_16", "ball_16_neumann", "cut_16_d2", "batch_t1", "sine_8_d2"])
 def test_alg1_transpose_fp64_follows_oracle_iterates(name):
     # Alg. 1 on A^T with M^T (the default adjoint method)
     t, H, g, gh, f, beta = build(CASES[name](), "f64")
@@ -106,7 +106,7 @@ def test_alg1_transpose_fp64_follows_oracle_iterates(name):
     assert rel(x.cpu().numpy(), xo) <= 1e-9
 
 
-@pytest.mark.parametrize("name", ["c2_16", "c2_16_neumann", "c3_16_d2", "c4_t1", "c5_8_d2"])
+@pytest.mark.parametrize("name", ["ball_16", "ball_16_neumann", "cut_16_d2", "batch_t1", "sine_8_d2"])
 def test_bicgstab_fp64_follows_oracle_iterates(name):
     t, H, g, gh, f, beta = build(CASES[name](), "f64")
     rhs = P.random_vector(t.n_leaves, 22)
@@ -122,7 +122,7 @@ def test_bicgstab_fp64_follows_oracle_iterates(name):
 
 @pytest.mark.parametrize("method", ["pcg", "bicgstab"])
 @pytest.mark.parametrize("precision", ["mixed", "fp32"])
-@pytest.mark.parametrize("name", ["c2_16", "c2_16_neumann", "c3_16_d2", "c4_t1", "c5_8_d2"])
+@pytest.mark.parametrize("name", ["ball_16", "ball_16_neumann", "cut_16_d2", "batch_t1", "sine_8_d2"])
 def test_transpose_solution_within_1e5(name, precision, method):
     t, H, g, gh, f, beta = build(CASES[name](), "f32")
     rhs = P.random_vector(t.n_leaves, 23)
@@ -159,14 +159,14 @@ def test_face_grad_matches_oracle(name):
 
 @pytest.mark.parametrize("method", ["pcg", "bicgstab"])
 def test_graph_and_eager_transpose_solves_agree(method):
-    t, H, g, gh, f, beta = build(CASES["c3_16_d2"](), "f32")
+    t, H, g, gh, f, beta = build(CASES["cut_16_d2"](), "f32")
     rhs = cuda(P.random_vector(t.n_leaves, 26))
     xg, sg = gh.solve(rhs, tol=1e-6, precision="mixed", transpose=True, method=method)
     xe, se = gh.solve(rhs, tol=1e-6, precision="mixed", transpose=True, eager=True, method=method)
     assert torch.equal(xg, xe) and sg.iterations == se.iterations and sg.kernels == se.kernels
 
 
-@pytest.mark.parametrize("name", ["c2_16", "c3_16_d2"])
+@pytest.mark.parametrize("name", ["ball_16", "cut_16_d2"])
 def test_autograd_matches_oracle_gradients(name):
     from paper_2604_18886_b300.autograd import poisson_solve
     p = CASES[name]()
@@ -188,7 +188,7 @@ def test_gradient_matches_central_differences_full_size():
     # the two-level workload (64^3 root, ball r = 0.25 refined once): L = 1/2 ||p - p_t||^2,
     # p_t ~ N(0,1) (seed 2); 64 interior faces drawn with seed 3, both regular and T
     # sub-faces; FP64 solves to 1e-12; L+ - L- = 1/2 <p+ - p-, p+ + p- - 2 p_t>
-    p = P.c2(64)
+    p = P.two_level_ball(64)
     g = S.Octree(p.desc)
     fc = g.faces()
     beta = P.face_beta(p, fc)

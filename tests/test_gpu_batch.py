@@ -20,7 +20,7 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-MIX = ["c1_16", "c2_16", "c2_16_neumann", "c3_16_d2", "c4_t1", "band_12_d2"]
+MIX = ["uniform_16", "ball_16", "ball_16_neumann", "cut_16_d2", "batch_t1", "band_12_d2"]
 
 
 def _rhs(name, t, f, beta):
@@ -61,7 +61,7 @@ def test_batched_solutions_match_oracle_and_single_solves():
 
 
 def test_converged_problems_are_frozen():
-    names = ["c2_16", "c3_16_d2"]
+    names = ["ball_16", "cut_16_d2"]
     items, bt = _batch(names)
     b0 = cuda(np.zeros(items[0][0].n_leaves))          # converged before the first iteration
     b1 = cuda(_rhs(names[1], items[1][0], items[1][4], items[1][5]))
@@ -76,7 +76,7 @@ def test_converged_problems_are_frozen():
 
 def test_batch_refuses_incompatible_hierarchies():
     from paper_2604_18886_b300 import _lib
-    p = CASES["c2_16"]()
+    p = CASES["ball_16"]()
     g = S.Octree(p.desc)
     beta = P.face_beta(p, g.faces())
     ok = S.Hierarchy(g, beta, p.bc, S.mg_params(coef="f32"))
@@ -94,7 +94,7 @@ def test_batched_64_trees_full_size():
     # band; even k Dirichlet beta = 1, odd k cut-cell Neumann), rhs N(0,1)
     hs, bs, leaves = [], [], 0
     for k in range(64):
-        p = P.c4_tree(k)
+        p = P.batch_tree(k)
         g = S.Octree(p.desc)
         f = g.faces()
         beta = P.face_beta(p, f)

@@ -12,7 +12,7 @@ torch = pytest.importorskip("torch")
 
 
 def _c3():
-    p = P.c3(16, 2)
+    p = P.cut_cell(16, 2)
     g = S.Octree(p.desc)
     f = g.faces()
     beta = P.face_beta(p, f)

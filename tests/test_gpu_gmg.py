@@ -36,7 +36,7 @@ def _pair(p, coef="f64", mu=1):
     return t, f, beta, Hg, g, hg
 
 
-@pytest.mark.parametrize("make", [lambda: P.c3(16, 2), lambda: P.c4_tree(1), lambda: P.c3(12, 2)])
+@pytest.mark.parametrize("make", [lambda: P.cut_cell(16, 2), lambda: P.batch_tree(1), lambda: P.cut_cell(12, 2)])
 def test_geometric_coefficients_match_oracle(make):
     t, f, beta, Hg, g, hg = _pair(make())
     for m in range(Hg.mc, Hg.D + 1):
@@ -50,7 +50,7 @@ def test_geometric_coefficients_match_oracle(make):
 
 @pytest.mark.parametrize("mu", [1, 2])
 def test_geometric_vcycle_and_pcg_match_oracle(mu):
-    p = P.c3(16, 2)
+    p = P.cut_cell(16, 2)
     t, f, beta, Hg, g, hg = _pair(p, mu=mu)
     r = P.random_vector(t.n_leaves, 70)
     z = hg.vcycle(_cuda(r)).cpu().numpy()
@@ -65,7 +65,7 @@ def test_geometric_vcycle_and_pcg_match_oracle(mu):
 
 
 def test_geometric_coarsening_needs_a_sdf_description():
-    p = P.c2(16)
+    p = P.two_level_ball(16)
     g = S.Octree(p.desc)
     beta = P.face_beta(p, g.faces())
     with pytest.raises(RuntimeError):
@@ -78,7 +78,7 @@ def test_full_size_cut_cell_geometric_needs_several_times_the_iterations():
     # (measured 18 and 14 against 5 and 5)
     its = {}
     for n0 in (32, 64):
-        p = P.c3(n0, 2)
+        p = P.cut_cell(n0, 2)
         g = S.Octree(p.desc)
         f = g.faces()
         beta = P.face_beta(p, f)

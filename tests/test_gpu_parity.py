@@ -3,17 +3,17 @@
 Tolerances:
   FP64 paths  - rounding-order differences only: 1e-12 relative to the vector's max norm
                 (1e-10 for whole cycles and solves, whose ~50 sweeps compound rounding).
-  FP32 apply  - 1e-6 relative (spec bar for operator applies).
+  FP32 apply  - 1e-6 relative (the stated accuracy bar for FP32 operator applies).
   FP32 cycle  - 1e-5 relative: one cycle is ~50 dependent sweeps, each adding about one
                 FP32 rounding (6e-8) per value, amplified at most a few times by the
                 contraction; BF16 coarse coefficients (8-bit mantissa) perturb the
                 preconditioner itself, so that form is checked through the solve only.
   solves      - a relative residual of 1e-6 does not bound the solution error by 1e-5 on
                 cut-cell grids (the oracle's own tol-1e-6 iterate is 8.5e-5 from its
-                1e-12 solution on c3_16_d2).  So: the GPU solution at tol 1e-6 may differ
+                1e-12 solution on cut_16_d2).  So: the GPU solution at tol 1e-6 may differ
                 from the oracle solved to 1e-12 by at most 1.5x the oracle's own tol-1e-6
                 error plus 1e-5, and the mixed solve run to tol 1e-9 must agree with it
-                within 1e-5 relative (spec bar).
+                within 1e-5 relative (the stated bar for solutions).
 """
 import math
 
@@ -63,12 +63,12 @@ def _neumann(p):
 
 
 CASES = {
-    "c1_16": lambda: P.c1(16),
-    "c2_16": lambda: P.c2(16),
-    "c2_16_neumann": lambda: _neumann(P.c2(16)),
-    "c3_16_d2": lambda: P.c3(16, 2),
-    "c4_t1": lambda: P.c4_tree(1),
-    "c5_8_d2": lambda: P.c5(8, 2),
+    "uniform_16": lambda: P.uniform(16),
+    "ball_16": lambda: P.two_level_ball(16),
+    "ball_16_neumann": lambda: _neumann(P.two_level_ball(16)),
+    "cut_16_d2": lambda: P.cut_cell(16, 2),
+    "batch_t1": lambda: P.batch_tree(1),
+    "sine_8_d2": lambda: P.sine_band(8, 2),
     "band_12_d2": lambda: P.Problem("band12", P.OctreeDesc(12, 2, P.REFINE_SDF_BAND, band=0.05,
                                                               spheres=[(0.45, 0.55, 0.5, 0.23)]),
                                     (1, 0, 1, 0, 0, 1), beta="one", rhs="normal", seed=3),
@@ -104,7 +104,7 @@ def test_apply_A_fp64(name):
     assert rel(y, H.A @ x) <= 1e-12
 
 
-@pytest.mark.parametrize("name", ["c2_16", "c2_16_neumann", "c1_16"])
+@pytest.mark.parametrize("name", ["ball_16", "ball_16_neumann", "uniform_16"])
 def test_mixed_outer_apply_is_fp64_accurate(name):
     # FP64 vectors on an FP32-coefficient hierarchy (the mixed solve's outer operator, run
     # in pair-of-FP32 arithmetic): with beta = 1 every stored leaf coefficient is a
@@ -159,7 +159,7 @@ def _ref_solution(H, b):
     return x
 
 
-@pytest.mark.parametrize("name", ["c2_16", "c2_16_neumann", "c3_16_d2", "c4_t1", "band_12_d2"])
+@pytest.mark.parametrize("name", ["ball_16", "ball_16_neumann", "cut_16_d2", "batch_t1", "band_12_d2"])
 def test_pcg_fp64_follows_oracle_iterates(name):
     p = CASES[name]()
     t, H, g, gh, f, beta = build(p, "f64")
@@ -178,7 +178,7 @@ def test_pcg_fp64_follows_oracle_iterates(name):
 
 
 @pytest.mark.parametrize("precision", ["mixed", "fp32"])
-@pytest.mark.parametrize("name", ["c2_16", "c2_16_neumann", "c3_16_d2", "c4_t1", "c5_8_d2"])
+@pytest.mark.parametrize("name", ["ball_16", "ball_16_neumann", "cut_16_d2", "batch_t1", "sine_8_d2"])
 def test_pcg_solution_within_1e5(name, precision):
     p = CASES[name]()
     t, H, g, gh, f, beta = build(p, "f32")
@@ -207,7 +207,7 @@ def test_pcg_solution_within_1e5(name, precision):
 def test_c1_fp64_closed_form():
     # uniform 32^3, Dirichlet, beta = 1: the discrete solution is the sine times
     # 3 pi^2 h^2 / (12 sin^2(pi h / 2)) (exact eigenvector), solved in FP64 to 1e-10
-    p = P.c1(32)
+    p = P.uniform(32)
     g = S.Octree(p.desc)
     f = g.faces()
     beta = P.face_beta(p, f)
@@ -224,7 +224,7 @@ def test_c1_fp64_closed_form():
 
 
 def test_bf16_coarse_solve_converges():
-    p = P.c3(16, 2)
+    p = P.cut_cell(16, 2)
     t, H, g, gh, f, beta = build(p, "f32", bf16=True)
     b = P.rhs(p, t.leaves, f, beta)
     ref = _ref_solution(H, b)
@@ -242,7 +242,7 @@ def test_bf16_coarse_solve_converges():
 
 def test_full_size_c2_apply_and_solve():
     # the bench workload: 64^3 base, ball refined once (382,936 leaves)
-    p = P.c2(64)
+    p = P.two_level_ball(64)
     t, H, g, gh, f, beta = build(p, "f32")
     x = P.random_vector(t.n_leaves, 5)
     y = gh.apply_A(cuda(x)).cpu().numpy()
@@ -256,7 +256,7 @@ def test_full_size_c2_apply_and_solve():
 
 
 def test_errors_are_reported():
-    p = P.c2(8)
+    p = P.two_level_ball(8)
     g = S.Octree(p.desc)
     f = g.faces()
     bad = np.ones(g.n_faces, np.float32)
@@ -276,7 +276,7 @@ def test_errors_are_reported():
 def test_graph_and_eager_solves_agree(precision, mu):
     # the CUDA-graph solve (device-side convergence test under a conditional WHILE node)
     # runs the same kernels in the same order as the kernel-by-kernel solve
-    p = P.c3(16, 2)
+    p = P.cut_cell(16, 2)
     t, H, g, gh, f, beta = build(p, "f32", mu=mu)
     b = cuda(P.rhs(p, t.leaves, f, beta))
     xg, sg = gh.solve(b, tol=1e-7, precision=precision)
@@ -289,7 +289,7 @@ def test_graph_and_eager_solves_agree(precision, mu):
 
 
 def test_wcycle_solve_matches_oracle():
-    p = P.c3(16, 2)
+    p = P.cut_cell(16, 2)
     t, H, g, gh, f, beta = build(p, "f64", mu=2)
     b = P.rhs(p, t.leaves, f, beta)
     xo, ko, ho = pcg.pcg(H, b, tol=1e-8, prm=mg.CycleParams(mu=2))
@@ -299,7 +299,7 @@ def test_wcycle_solve_matches_oracle():
 
 
 @pytest.mark.parametrize("sweep", ["octet", "cell", "quad", "tile"])
-@pytest.mark.parametrize("name", ["c2_16", "c3_16_d2", "band_12_d2", "c4_t1", "c5_8_d2"])
+@pytest.mark.parametrize("name", ["ball_16", "cut_16_d2", "band_12_d2", "batch_t1", "sine_8_d2"])
 def test_every_sweep_form_matches_oracle(name, sweep):
     # the autotuner may pick any form per level; each must reproduce Alg. 4
     p = CASES[name]()
@@ -312,7 +312,7 @@ def test_every_sweep_form_matches_oracle(name, sweep):
 
 
 def test_autotuner_records_every_form():
-    p = P.c2(32)
+    p = P.two_level_ball(32)
     t, H, g, gh, f, beta = build(p, "f32")
     tun = gh.tuning()
     timed = [m for m, v in tun.items() if v[0] >= 0]
@@ -328,7 +328,7 @@ def test_unrolled_measurement_solve_repeats_the_graph_solve():
     # nodes) runs the same kernels as the WHILE-node graph and gives the same result
     from paper_2604_18886_b300 import _lib as L
     import ctypes as C
-    p = P.c3(16, 2)
+    p = P.cut_cell(16, 2)
     t, H, g, gh, f, beta = build(p, "f32")
     b = cuda(P.rhs(p, t.leaves, f, beta))
     xg, sg = gh.solve(b, tol=1e-7, precision="mixed")
@@ -348,7 +348,7 @@ def test_full_size_cut_cell_properties():
     # the cut-cell workload at full size (64^3 root, 2 levels of band refinement around the
     # solid sphere and box, 2,637,132 leaves, Neumann walls, fluid-fraction beta): the
     # oracle cannot assemble this size in a test, so check what holds at any size
-    p = P.c3(64, 2)
+    p = P.cut_cell(64, 2)
     g = S.Octree(p.desc)
     f = g.faces()
     beta = P.face_beta(p, f)
@@ -372,7 +372,7 @@ def test_full_size_cut_cell_properties():
     for x in (x16, x32):
         assert (x - x9).abs().max().item() <= 1e-3 * x9.abs().max().item()
     # grid-independent iteration counts: the same geometry at half the root resolution
-    ph = P.c3(32, 2)
+    ph = P.cut_cell(32, 2)
     gh_ = S.Octree(ph.desc)
     fh = gh_.faces()
     bh = P.face_beta(ph, fh)
@@ -387,7 +387,7 @@ def test_wcycle_with_bf16_coarse_coefficients_converges(n0):
     # all-Neumann cut-cell tree keeps its constant null space on the coarse levels and
     # W-cycles converge as with FP32 coefficients (independent rounding of the diagonal
     # stalled PCG at 24^3)
-    p = P.c3(n0, 2)
+    p = P.cut_cell(n0, 2)
     g = S.Octree(p.desc)
     f = g.faces()
     beta = P.face_beta(p, f)
@@ -401,7 +401,7 @@ def test_wcycle_with_bf16_coarse_coefficients_converges(n0):
     assert its[True] <= its[False] + 1, its
 
 
-@pytest.mark.parametrize("name", ["c2_16", "c3_16_d2", "band_12_d2"])
+@pytest.mark.parametrize("name", ["ball_16", "cut_16_d2", "band_12_d2"])
 def test_hybrid_w_v_cycle_matches_oracle(name):
     # mu = 2 into the levels with at least 4096 cells, mu = 1 below (host recursion and the
     # shared-memory tail's schedule follow the same rule as the oracle)

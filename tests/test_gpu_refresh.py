@@ -23,7 +23,7 @@ def _betas(p, g):
 
 @pytest.mark.parametrize("coarsening", ["algebraic", "geometric"])
 def test_refreshed_coefficients_equal_a_fresh_set_up(coarsening):
-    p = P.c3(16, 2)
+    p = P.cut_cell(16, 2)
     g = S.Octree(p.desc)
     f, b1, b2 = _betas(p, g)
     prm = S.mg_params(coef="f64", sweep="octet", coarsening=coarsening)
@@ -38,7 +38,7 @@ def test_refreshed_coefficients_equal_a_fresh_set_up(coarsening):
 @pytest.mark.parametrize("coef, precision, bf16", [("f64", "fp64", False), ("f32", "mixed", False),
                                                    ("f32", "mixed", True)])
 def test_graph_captured_before_the_refresh_solves_the_new_system(coef, precision, bf16):
-    p = P.c3(16, 2)
+    p = P.cut_cell(16, 2)
     g = S.Octree(p.desc)
     f, b1, b2 = _betas(p, g)
     b = torch.from_numpy(P.rhs(p, g.leaves(), f, b2)).cuda()
@@ -55,7 +55,7 @@ def test_graph_captured_before_the_refresh_solves_the_new_system(coef, precision
 
 
 def test_rejected_refresh_then_a_valid_one():
-    p = P.c3(12, 2)
+    p = P.cut_cell(12, 2)
     g = S.Octree(p.desc)
     f, b1, b2 = _betas(p, g)
     prm = S.mg_params(coef="f64", sweep="octet")
@@ -73,7 +73,7 @@ def test_rejected_refresh_then_a_valid_one():
 
 def test_autograd_with_a_refreshed_hierarchy_matches_fresh_set_ups():
     from paper_2604_18886_b300.autograd import poisson_solve
-    p = P.c3(12, 2)
+    p = P.cut_cell(12, 2)
     g = S.Octree(p.desc)
     f, b1, b2 = _betas(p, g)
     prm = S.mg_params(coef="f32", sweep="octet")

@@ -31,7 +31,7 @@ _STATE = {}
 def _setup(n0=128):
     if n0 in _STATE:
         return _STATE[n0]
-    p = P.c5(n0, 3)
+    p = P.sine_band(n0, 3)
     g = S.Octree(p.desc)
     beta, b = P.large_inputs(p, g.n_leaves, g.n_faces, g.faces_range, "cuda")
     _STATE[n0] = (p, g, beta, torch.from_numpy(b).cuda())

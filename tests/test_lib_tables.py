@@ -25,18 +25,18 @@ def test_library_exports_every_declared_symbol():
 
 
 def _descs():
-    yield P.c1(8).desc
-    yield P.c2(8).desc
-    yield P.c2(16, radius=0.3).desc
-    yield P.c3(8, 2).desc
+    yield P.uniform(8).desc
+    yield P.two_level_ball(8).desc
+    yield P.two_level_ball(16, radius=0.3).desc
+    yield P.cut_cell(8, 2).desc
     yield P.OctreeDesc(4, 3, P.REFINE_SDF_BAND, band=0.02, spheres=[(0.3, 0.4, 0.55, 0.17)])
     yield P.OctreeDesc(6, 3, P.REFINE_SDF_BAND, band=0.01, spheres=[(0.21, 0.8, 0.5, 0.11)],
                        boxes=[(0.5, 0.1, 0.2, 0.9, 0.35, 0.6)])
     yield P.OctreeDesc(12, 2, P.REFINE_SDF_BAND, band=0.05, spheres=[(0.45, 0.55, 0.5, 0.23)])
-    yield P.c4_tree(1).desc
-    yield P.c5(8, 2).desc           # sine band: deterministic sin/cos in both builders
-    yield P.c5(6, 3, band=0.01).desc
-    yield P.c5(16, 2).desc
+    yield P.batch_tree(1).desc
+    yield P.sine_band(8, 2).desc           # sine band: deterministic sin/cos in both builders
+    yield P.sine_band(6, 3, band=0.01).desc
+    yield P.sine_band(16, 2).desc
     yield P.accuracy_desc("star", 8)   # star surface: Chebyshev cosines in both builders
     yield P.accuracy_desc("star", 16)
     yield P.OctreeDesc(6, 3, P.REFINE_STAR_BAND, band=0.01,
@@ -68,8 +68,8 @@ def test_octree_tables_bit_exact(desc):
 
 
 def test_config_leaf_counts():
-    # c2: 64^3 base with the central ball refined once
-    g = S.Octree(P.c2(64).desc)
+    # two-level ball: 64^3 base with the central ball refined once
+    g = S.Octree(P.two_level_ball(64).desc)
     assert g.n_leaves == 382936
     assert g.mc == -4 and g.D == 1
 

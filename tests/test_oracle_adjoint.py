@@ -40,7 +40,7 @@ def _face_classes(H):
 def test_face_grad_equals_assembled_beta_derivative(name):
     # A is affine in beta with a fixed active set, so (A(beta + e_f / 2) - A(beta)) * 2 is
     # dA/dbeta_f up to rounding; -lambda^T (that matrix) p must equal the closed form.
-    p = P.c2(6) if name == "ball_dirichlet" else P.c3(6, 2)
+    p = P.two_level_ball(6) if name == "ball_dirichlet" else P.cut_cell(6, 2)
     t, f, beta = _tree(p)
     if name == "ball_dirichlet":
         beta = np.random.default_rng(11).uniform(0.2, 1.0, len(beta)).astype(np.float32)
@@ -68,9 +68,9 @@ def test_face_grad_equals_assembled_beta_derivative(name):
 
 def _fd_problem(name):
     if name == "dirichlet":
-        p = P.c2(4)
+        p = P.two_level_ball(4)
     else:
-        p = P.c3(4, 1)
+        p = P.cut_cell(4, 1)
     t, f, beta = _tree(p)
     H = OP.Hierarchy(t, beta, p.bc)
     b = P.rhs(p, t.leaves, f, beta)
@@ -130,12 +130,12 @@ def test_adjoint_is_the_transpose_solve():
 @pytest.mark.parametrize("name", ["dirichlet", "neumann", "cut"])
 def test_bicgstab_matches_dense_solve(name):
     if name == "dirichlet":
-        p = P.c2(6)
+        p = P.two_level_ball(6)
     elif name == "neumann":
-        p = P.c2(6)
+        p = P.two_level_ball(6)
         p.bc = (P.NEUMANN,) * 6
     else:
-        p = P.c3(6, 2)
+        p = P.cut_cell(6, 2)
     t, f, beta = _tree(p)
     H = OP.Hierarchy(t, beta, p.bc)
     g = np.random.default_rng(6).normal(size=t.n_leaves)
@@ -159,7 +159,7 @@ def test_neumann_gradients_ignore_constants():
 
 
 @pytest.mark.parametrize("mu", [1, 2])
-@pytest.mark.parametrize("make", [lambda: P.c2(8), lambda: P.c3(8, 2), lambda: P.c5(8, 2)])
+@pytest.mark.parametrize("make", [lambda: P.two_level_ball(8), lambda: P.cut_cell(8, 2), lambda: P.sine_band(8, 2)])
 def test_transposed_cycle_is_the_transpose(make, mu):
     """mg.vcycle_T is the exact transpose of the cycle: <M r1, r2> = <r1, M^T r2>."""
     p = make()
@@ -191,7 +191,7 @@ def test_transposed_cycle_rescues_the_high_contrast_adjoint():
     """On an under-resolved sine-band tree (beta clamped at 1e-3 on a third of the faces)
     BiCGStab on A^T preconditioned by the forward cycle diverges; with the transposed
     cycle it converges to the direct solution."""
-    p = P.c5(8, 2)
+    p = P.sine_band(8, 2)
     t = O.Octree(p.desc)
     H = OP.Hierarchy(t, P.face_beta(p, t.faces()), p.bc)
     g = P.random_vector(t.n_leaves, 23)
@@ -206,7 +206,7 @@ def test_transposed_cycle_rescues_the_high_contrast_adjoint():
     assert np.abs((x - x.mean()) - ref).max() <= 1e-7 * np.abs(ref).max()
 
 
-@pytest.mark.parametrize("make", [lambda: P.c5(8, 2), lambda: P.c3(8, 2), lambda: P.c2(8)])
+@pytest.mark.parametrize("make", [lambda: P.sine_band(8, 2), lambda: P.cut_cell(8, 2), lambda: P.two_level_ball(8)])
 def test_alg1_on_the_transpose_with_the_transposed_cycle(make):
     """Alg. 1 on A^T preconditioned by M^T reaches the direct transpose solution, in about
     as many iterations as BiCGStab with M^T needs preconditioner applications or fewer."""

@@ -50,7 +50,7 @@ def test_fluid_only_geometric_equals_algebraic(kind, bc):
 def test_cut_cell_geometric_coarsening_loses_grid_independence():
     its = {}
     for n0 in (8, 16):
-        p = P.c3(n0, 2)
+        p = P.cut_cell(n0, 2)
         t = O.Octree(p.desc)
         f = t.faces()
         beta = P.face_beta(p, f)

@@ -7,12 +7,12 @@ from paper_2604_18886_b300 import problems as P
 
 
 def _trees():
-    yield P.c2(8).desc
-    yield P.c2(16, radius=0.3).desc
+    yield P.two_level_ball(8).desc
+    yield P.two_level_ball(16, radius=0.3).desc
     yield P.OctreeDesc(4, 3, P.REFINE_SDF_BAND, band=0.02, spheres=[(0.3, 0.4, 0.55, 0.17)])
     yield P.OctreeDesc(6, 3, P.REFINE_SDF_BAND, band=0.01, spheres=[(0.21, 0.8, 0.5, 0.11)],
                        boxes=[(0.5, 0.1, 0.2, 0.9, 0.35, 0.6)])
-    yield P.c3(8, 2).desc
+    yield P.cut_cell(8, 2).desc
 
 
 @pytest.mark.parametrize("desc", list(_trees()))
@@ -75,7 +75,7 @@ def test_counts_and_canonical_order(desc):
 
 
 def test_neighbour_table_consistency():
-    t = O.Octree(P.c2(8).desc)
+    t = O.Octree(P.two_level_ball(8).desc)
     kind, rank = t.neighbour_table()
     L = t.leaves
     for r in range(t.n_leaves):

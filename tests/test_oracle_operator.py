@@ -28,7 +28,7 @@ def _neumann(p):
 
 def test_uniform_fluid_coefficients():
     # Sec. 2.1: fluid cell c_{x-} = -h, c = 6h
-    H, _ = _hier(_neumann(P.c1(8)))
+    H, _ = _hier(_neumann(P.uniform(8)))
     L = H.levels[0]
     h = 1.0 / 8
     interior = (L.i > 0) & (L.i < 7) & (L.j > 0) & (L.j < 7) & (L.k > 0) & (L.k < 7)
@@ -39,7 +39,7 @@ def test_uniform_fluid_coefficients():
 
 def test_galerkin_worked_values_alpha2():
     # Sec. 2.4: coarse off-diagonal -4h/alpha, diagonal 24h/alpha, i.e. -2h and 12h
-    H, _ = _hier(_neumann(P.c1(16)))
+    H, _ = _hier(_neumann(P.uniform(16)))
     g = GOLD["galerkin_alpha2"]
     h = 1.0 / 16
     C = H.levels[-1]
@@ -53,7 +53,7 @@ def test_galerkin_worked_values_alpha2():
 def test_coarse_equals_geometric_alpha2(bc):
     # Sec. 3.3: with alpha = 2 coarsened inner coefficients equal the leaf coefficients
     # the discretisation gives directly at that cell size (including Dirichlet walls)
-    p = P.c2(8)
+    p = P.two_level_ball(8)
     p.bc = (bc,) * 6
     H, _ = _hier(p)
     for m in range(H.mc, H.D):
@@ -77,7 +77,7 @@ def test_coarse_equals_geometric_alpha2(bc):
 def test_alg3_equals_rap_on_uniform_cut_cells():
     # Alg. 3 equals R A P (Eq. galerkin-mat-coarsen) where there are no T-junctions, for
     # arbitrary face beta including zero faces that deactivate cells (active_cnt branch)
-    p = P.c1(8)
+    p = P.uniform(8)
     p.bc = (P.NEUMANN, P.DIRICHLET, P.NEUMANN, P.NEUMANN, P.NEUMANN, P.DIRICHLET)
     t = O.Octree(p.desc)
     f = t.faces()
@@ -106,7 +106,7 @@ def test_alg3_equals_rap_on_uniform_cut_cells():
 
 
 def test_alg3_literal_equals_vectorised():
-    H, _ = _hier(P.c3(8, 2))
+    H, _ = _hier(P.cut_cell(8, 2))
     for m in range(H.D, H.mc, -1):
         C = H.levels[m - 1]
         for I in np.nonzero(C.children[:, 0] >= 0)[0][:200]:
@@ -115,7 +115,7 @@ def test_alg3_literal_equals_vectorised():
 
 
 def test_alg3_equals_rap_away_from_t_junctions():
-    H, _ = _hier(P.c2(8))
+    H, _ = _hier(P.two_level_ball(8))
     m = 1
     inner, rap = H.rap_inner_block(m)
     dense = H.level_dense(0)[np.ix_(inner, inner)]
@@ -135,7 +135,7 @@ def test_t_junction_coefficient_and_ghost_2d_worked_values():
     assert abs(g["c4_xm"] - 0.5 * (g["c6_xm"] + g["c7_xm"])) < 1e-15
     assert abs(g["c6_xm"] - g["S1"] / g["h"]) < 1e-15
     # 3-D: the coarse leaf's face weight is half the sum of its four sub-face weights
-    p = P.c3(8, 1)
+    p = P.cut_cell(8, 1)
     H, f = _hier(p)
     t = H.tree
     kind, rank = t.neighbour_table()
@@ -171,7 +171,7 @@ def _t_free(p):
 def test_constant_nullspace_and_conservation():
     # Sec. 2.2: pure Neumann -> A 1 = 0; flux conservation (f1 + f3 = f4, Eq.
     # flux-conservation) -> every column sums to zero as well
-    for p in (_neumann(P.c2(8)), P.c3(8, 2)):
+    for p in (_neumann(P.two_level_ball(8)), P.cut_cell(8, 2)):
         H, _ = _hier(p)
         one = np.ones(H.A.shape[0])
         assert np.abs(H.A @ one).max() < 1e-14
@@ -180,7 +180,7 @@ def test_constant_nullspace_and_conservation():
 
 def test_symmetric_psd_without_t_junctions():
     # Sec. 2.1: the seven-point system is symmetric and positive semi-definite
-    p = P.c1(6)
+    p = P.uniform(6)
     t = O.Octree(p.desc)
     f = t.faces()
     beta = np.random.default_rng(1).uniform(1e-3, 1.0, len(f["axis"]))
@@ -197,7 +197,7 @@ def test_symmetric_psd_without_t_junctions():
 def test_t_junction_asymmetry_closed_form():
     # Literal T operator: A[i,K] = -w_f/2 per T face of fine leaf i, A[K,i] = -w_KP/8;
     # with full faces w_f = h, w_KP = 2h -> -h/2 vs -h/4; A - A^T vanishes elsewhere
-    p = _neumann(P.c2(8))
+    p = _neumann(P.two_level_ball(8))
     H, _ = _hier(p)
     A = H.A.toarray()
     t = H.tree
@@ -235,7 +235,7 @@ def test_dirichlet_sine_is_exact_eigenvector():
     # face-Dirichlet walls: sin(pi x_i) sin(pi y_j) sin(pi z_k) is an eigenvector of the
     # uniform operator, eigenvalue h^3 * 3 * 4 sin^2(pi h / 2) / h^2
     n = 12
-    p = P.c1(n)
+    p = P.uniform(n)
     H, _ = _hier(p)
     L = H.tree.leaves
     h = 1.0 / n
@@ -253,7 +253,7 @@ def test_laplacian_accuracy_on_octree():
     # shrinks (a wrong ghost weight grows like 1/h there)
     reg_err, t_max = [], []
     for n0 in (8, 16, 32):
-        p = _neumann(P.c2(n0))
+        p = _neumann(P.two_level_ball(n0))
         H, _ = _hier(p)
         t = H.tree
         L = t.leaves

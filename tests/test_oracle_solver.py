@@ -19,7 +19,7 @@ def _hier(p):
 
 
 def _uniform_cut(n=16, bc=P.NEUMANN):
-    p = P.c1(n)
+    p = P.uniform(n)
     p.bc = (bc,) * 6
     t = O.Octree(p.desc)
     f = t.faces()
@@ -42,7 +42,7 @@ def test_fas_equals_plain_cycle_on_uniform_grid(bc, mu):
 
 @pytest.mark.parametrize("mu", [1, 2])
 def test_cycle_is_linear(mu):
-    H, _, _ = _hier(P.c3(8, 2))
+    H, _, _ = _hier(P.cut_cell(8, 2))
     rng = np.random.default_rng(11)
     n = H.A.shape[0]
     r1, r2 = rng.standard_normal(n), rng.standard_normal(n)
@@ -54,7 +54,7 @@ def test_cycle_is_linear(mu):
 
 def test_mean_of_children_equals_parent_after_prolongation():
     # Sec. 3.3, Eq. fas-flux-conservation
-    H, _, _ = _hier(P.c2(8))
+    H, _, _ = _hier(P.two_level_ball(8))
     seen = []
 
     def hook(m, u):
@@ -82,7 +82,7 @@ def test_colour_sweep_zeroes_residual_of_updated_cells():
 
 
 def test_cycle_converges_as_standalone_iteration():
-    H, _, _ = _hier(P.c2(8))
+    H, _, _ = _hier(P.two_level_ball(8))
     rng = np.random.default_rng(9)
     n = H.A.shape[0]
     b = rng.standard_normal(n)
@@ -99,13 +99,13 @@ def test_cycle_converges_as_standalone_iteration():
 @pytest.mark.parametrize("name", ["dirichlet", "neumann", "cut"])
 def test_pcg_matches_dense_solve_on_tiny_octrees(name):
     if name == "dirichlet":
-        p = P.c2(6)
+        p = P.two_level_ball(6)
     elif name == "neumann":
-        p = P.c2(6)
+        p = P.two_level_ball(6)
         p.bc = (P.NEUMANN,) * 6
         p.rhs = "normal"
     else:
-        p = P.c3(6, 2)
+        p = P.cut_cell(6, 2)
     H, f, beta = _hier(p)
     assert H.A.shape[0] < 6000
     b = P.rhs(p, H.tree.leaves, f, beta)
@@ -122,7 +122,7 @@ def test_closed_form_uniform_dirichlet():
     # the discrete solution of the manufactured rhs is that function times
     # 3 pi^2 h^2 / (12 sin^2(pi h / 2))
     n = 16
-    p = P.c1(n)
+    p = P.uniform(n)
     H, f, beta = _hier(p)
     b = P.rhs(p, H.tree.leaves, f, beta)
     x, k, hist = pcg.pcg(H, b, tol=1e-12, max_iter=100)
@@ -138,7 +138,7 @@ def test_second_order_solution_error():
     # Sec. 4.3 (Fig. athena-sin-grid-convergence): close to second order on octrees
     errs = []
     for n0 in (8, 16, 32):
-        p = P.c2(n0)
+        p = P.two_level_ball(n0)
         H, f, beta = _hier(p)
         L = H.tree.leaves
         b = P.rhs(p, L, f, beta)
@@ -156,7 +156,7 @@ def test_grid_independent_iterations_and_reduction():
     # independent of the resolution
     its = []
     for n0 in (16, 32):
-        p = P.c2(n0)
+        p = P.two_level_ball(n0)
         H, f, beta = _hier(p)
         b = P.rhs(p, H.tree.leaves, f, beta)
         x, k, hist = pcg.pcg(H, b, tol=1e-6)
@@ -171,7 +171,7 @@ def test_mu_min_cells_runs_w_above_and_v_below():
     the W-cycle bit for bit, a threshold above every level the V-cycle bit for bit, and a
     threshold between the level sizes a cycle that differs from both but converges no
     slower than V as a preconditioner."""
-    p = P.c2(16)
+    p = P.two_level_ball(16)
     t = O.Octree(p.desc)
     H = OP.Hierarchy(t, P.face_beta(p, t.faces()), p.bc)
     r = P.random_vector(t.n_leaves, 41)

@@ -69,7 +69,7 @@ def test_identities_hold_exactly_or_to_rounding():
 def test_sine_band_predicate_matches_high_precision_evaluation():
     """The predicate's decisions equal those of the same formula in 200-bit arithmetic
     wherever the margin exceeds 1e-12 (brute force on a few thousand cell centres)."""
-    p = P.c5(8, 3)
+    p = P.sine_band(8, 3)
     d = p.desc
     rng = np.random.default_rng(14)
     depth = 2

@@ -30,7 +30,7 @@ def test_face_fraction_of_a_plane():
 
 
 def test_divergence_rhs_sums_to_zero():
-    p = P.c3(8, 2)
+    p = P.cut_cell(8, 2)
     t = O.Octree(p.desc)
     f = t.faces()
     beta = P.face_beta(p, f)

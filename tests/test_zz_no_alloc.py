@@ -33,7 +33,7 @@ def _apply_noalloc(h, x):
 
 @pytest.mark.parametrize("coef", ["f32", "f64"])
 def test_noalloc_apply_matches_regular_apply_twice(coef):
-    p = P.c3(16, 2)
+    p = P.cut_cell(16, 2)
     tree = S.Octree(p.desc)
     beta = P.face_beta(p, tree.faces())
     hier = S.Hierarchy(tree, beta, p.bc, S.mg_params(coef=coef))
@@ -47,7 +47,7 @@ def test_noalloc_apply_matches_regular_apply_twice(coef):
 
 
 def test_noalloc_apply_rejects_trees_above_the_limit():
-    p = P.c1(128)                       # 2,097,152 tree cells > 2^20
+    p = P.uniform(128)                       # 2,097,152 tree cells > 2^20
     tree = S.Octree(p.desc)
     assert tree.n_tree > L.OCG_NOALLOC_MAX_CELLS
     hier = S.Hierarchy(tree, np.ones(tree.n_faces, np.float32), p.bc)
