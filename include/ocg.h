@@ -115,6 +115,24 @@ typedef struct {
  * uploaded to the current device by the first ocg_setup_hierarchy on this octree).
  * Errors: EINVAL (bad desc), ENOMEM. */
 int ocg_octree_build(const ocg_octree_desc* desc, ocg_octree** out);
+
+/* Octree of desc built from a previous octree after a local change of the geometry (a
+ * moved or resized obstacle: the tables are recomputed whenever the grid topology
+ * changes, Sec. 3.4).  box = (lox, loy, loz, hix, hiy, hiz) in the unit cube's
+ * coordinates.  The refinement predicate is evaluated again only for the cells that meet
+ * the box (with one cell of margin per depth) and for the children of cells whose flag
+ * changed; every other cell keeps its flag from prev; the 2:1 closure and all tables are
+ * then formed as by ocg_octree_build.
+ * Contract: the predicate of desc equals that of prev's description on every cell that
+ * does not meet the box (for SDF_BAND: the box holds the moved primitive's old and new
+ * positions grown by band + sqrt(3)/2 / n0).  Under it the result is the octree that
+ * ocg_octree_build(desc) makes, table for table; without it the result is a valid
+ * 2:1-balanced octree but not necessarily that one.  prev is not modified and stays
+ * valid; the new octree is independent of it.
+ * Errors: EINVAL (null argument, bad desc, n0 / max_depth / refine differing from prev's,
+ * box not finite or lo > hi), ENOMEM. */
+int ocg_octree_rebuild(const ocg_octree* prev, const ocg_octree_desc* desc, const double box[6],
+                       ocg_octree** out);
 void ocg_octree_destroy(ocg_octree* t);
 
 /* counts[0] leaves, [1] canonical faces, [2] max depth D, [3] coarsest level mc (<= 0),

@@ -73,6 +73,8 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 _SIGS = [
     ("ocg_last_error", C.c_char_p, []),
     ("ocg_octree_build", C.c_int, [C.POINTER(OctreeDesc), C.POINTER(C.c_void_p)]),
+    ("ocg_octree_rebuild", C.c_int, [C.c_void_p, C.POINTER(OctreeDesc), C.POINTER(C.c_double),
+                                     C.POINTER(C.c_void_p)]),
     ("ocg_octree_destroy", None, [C.c_void_p]),
     ("ocg_octree_counts", C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     ("ocg_octree_export_leaves", C.c_int, [C.c_void_p] + [C.c_void_p] * 4),

@@ -1313,6 +1313,20 @@ int ocg_octree_build(const ocg_octree_desc* desc, ocg_octree** out) {
     });
 }
 
+int ocg_octree_rebuild(const ocg_octree* prev, const ocg_octree_desc* desc, const double box[6], ocg_octree** out) {
+    return guard([&] {
+        if (!prev || !desc || !box || !out) throw Status(OCG_EINVAL, "null argument");
+        *out = nullptr;
+        std::unique_ptr<ocg_octree> t(new ocg_octree());
+        try {
+            rebuild_host_tree(prev->H, *desc, box, t->H);
+        } catch (const std::runtime_error& e) {
+            throw Status(OCG_EINVAL, e.what());
+        }
+        *out = t.release();
+    });
+}
+
 void ocg_octree_destroy(ocg_octree* t) { delete t; }
 
 int ocg_octree_counts(const ocg_octree* t, int64_t c[8]) {

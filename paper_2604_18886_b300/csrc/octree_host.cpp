@@ -309,7 +309,21 @@ static int sub_index(int a, int s) {
     return (s & 1) | (((s >> 1) & 1) << 1);
 }
 
-void build_host_tree(const ocg_octree_desc& desc, HostTree& T) {
+static void build_impl(const ocg_octree_desc& desc, HostTree& T, const HostTree* prev, const double* box);
+
+void build_host_tree(const ocg_octree_desc& desc, HostTree& T) { build_impl(desc, T, nullptr, nullptr); }
+
+void rebuild_host_tree(const HostTree& prev, const ocg_octree_desc& desc, const double box[6], HostTree& T) {
+    if (desc.n0 != prev.desc.n0 || desc.max_depth != prev.desc.max_depth || desc.refine != prev.desc.refine)
+        throw std::runtime_error("rebuild: n0, max_depth and refine must equal the previous octree's");
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(box[a]) || !std::isfinite(box[a + 3]) || box[a] > box[a + 3])
+            throw std::runtime_error("rebuild: the box must be finite with lo <= hi on each axis");
+    if ((int)prev.pred.size() != std::max(prev.D, 0)) throw std::runtime_error("rebuild: previous octree incomplete");
+    build_impl(desc, T, &prev, box);
+}
+
+static void build_impl(const ocg_octree_desc& desc, HostTree& T, const HostTree* prev, const double* box) {
     T.desc = desc;
     const int n0 = desc.n0, D = desc.max_depth;
     if (n0 < 2 || (n0 & 1)) throw std::runtime_error("n0 must be even and >= 2");
@@ -344,22 +358,45 @@ void build_host_tree(const ocg_octree_desc& desc, HostTree& T) {
     const int Nc = N, Ncp = N + (N & 1);
     if ((int64_t)Ncp * Ncp * Ncp > 64 * 64 * 64) throw std::runtime_error("coarsest grid too large");
 
-    // ---- refinement flags per depth (dense, lexicographic)
+    // ---- refinement flags per depth (dense, lexicographic): a cell of depth d is refined
+    // when its parent is and the predicate holds.  A rebuild takes a cell's flag from the
+    // previous octree when the cell lies outside the changed box and its parent's flag is
+    // unchanged (the predicate there is the same by the caller's contract), and evaluates
+    // the predicate for every other cell; the index window has one cell of margin.
     std::vector<std::vector<uint8_t>> ref(D + 1);
     for (int d = 0; d < D; ++d) {
         const int64_t nd = (int64_t)n0 << d;
         ref[d].assign(nd * nd * nd, 0);
         auto& R = ref[d];
         const std::vector<uint8_t>* P = d > 0 ? &ref[d - 1] : nullptr;
+        const std::vector<uint8_t>* Rold = prev ? &prev->pred[d] : nullptr;
+        const std::vector<uint8_t>* Pold = prev && d > 0 ? &prev->pred[d - 1] : nullptr;
+        int64_t lo[3] = {0, 0, 0}, hi[3] = {-1, -1, -1};
+        if (prev)
+            for (int a = 0; a < 3; ++a) {
+                lo[a] = (int64_t)std::floor(std::max(-1.0, std::min(2.0, box[a])) * (double)nd) - 1;
+                hi[a] = (int64_t)std::floor(std::max(-1.0, std::min(2.0, box[a + 3])) * (double)nd) + 1;
+            }
         const int64_t np = nd / 2;
 #pragma omp parallel for schedule(static)
         for (int64_t k = 0; k < nd; ++k)
             for (int64_t j = 0; j < nd; ++j)
                 for (int64_t i = 0; i < nd; ++i) {
-                    if (P && !(*P)[lex(i >> 1, j >> 1, k >> 1, np)]) continue;
-                    if (refine_pred(desc, d, i, j, k)) R[lex(i, j, k, nd)] = 1;
+                    const int64_t pc = lex(i >> 1, j >> 1, k >> 1, np);
+                    if (P && !(*P)[pc]) continue;
+                    const int64_t c = lex(i, j, k, nd);
+                    if (Rold) {
+                        const bool inside = i >= lo[0] && i <= hi[0] && j >= lo[1] && j <= hi[1] &&
+                                            k >= lo[2] && k <= hi[2];
+                        if (!inside && (!Pold || (*Pold)[pc])) {
+                            R[c] = (*Rold)[c];
+                            continue;
+                        }
+                    }
+                    if (refine_pred(desc, d, i, j, k)) R[c] = 1;
                 }
     }
+    T.pred.assign(ref.begin(), ref.begin() + std::max(D, 0));
     // ---- face 2:1 balance, deepest inner cells first (within one depth the order of the
     // marks does not matter: depth e is read, depth e-1 written)
     for (int e = D - 1; e >= 1; --e) {

@@ -43,6 +43,10 @@ struct HostTree {
     // octet parent keys per level (sorted Morton keys of the parent coordinates)
     std::vector<std::vector<uint64_t>> okeys;  // indexed by m - mc
 
+    // refinement predicate flags per depth d < D before the 2:1 closure (dense,
+    // lexicographic), kept for rebuild_host_tree
+    std::vector<std::vector<uint8_t>> pred;
+
     // global tables
     std::vector<int32_t> nbr;        // [6][noct]: level-local octet, -1 wall, -2-K T face
                                      //   (K = global cell of the coarser leaf)
@@ -72,6 +76,12 @@ struct HostTree {
 
 // Builds everything; throws std::runtime_error with a message on invalid input.
 void build_host_tree(const ocg_octree_desc& desc, HostTree& T);
+
+// Builds the octree of desc from prev, evaluating the refinement predicate only for the
+// cells that meet box = (lox, loy, loz, hix, hiy, hiz) or whose parent's flag changed.  When
+// the predicate of desc equals that of prev.desc on every cell that does not meet the box,
+// the result equals build_host_tree(desc) exactly.  n0, max_depth and refine must match.
+void rebuild_host_tree(const HostTree& prev, const ocg_octree_desc& desc, const double box[6], HostTree& T);
 
 // Integer coordinates (at the face's depth) of the cell on the + side of canonical face f;
 // for a T sub-face whose fine leaf is on the - side that cell is virtual.

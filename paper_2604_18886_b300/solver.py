@@ -8,6 +8,7 @@ fails — there is no CPU path here.
 from __future__ import annotations
 
 import ctypes as C
+import math
 
 import numpy as np
 
@@ -38,18 +39,41 @@ def _desc(d: P.OctreeDesc) -> L.OctreeDesc:
     return out
 
 
+def sphere_change_box(old, new, band: float, n0: int):
+    """The box for Octree.rebuild after one sphere of an SDF_BAND or BALL_CENTRE description
+    moved or changed its radius from old = (cx, cy, cz, r) to new: the two spheres' bounding
+    boxes grown by band + sqrt(3)/2 / n0, the farthest a cell centre can be from the sphere's
+    surface and still have the sphere decide its refinement (outside it the signed distance
+    to that sphere exceeds every depth's slack, so the minimum over the primitives, and with
+    it the predicate, is unchanged)."""
+    g = float(band) + 0.5 * math.sqrt(3.0) / n0
+    lo = [min(old[a] - old[3], new[a] - new[3]) - g for a in range(3)]
+    hi = [max(old[a] + old[3], new[a] + new[3]) + g for a in range(3)]
+    return tuple(lo + hi)
+
+
 class Octree:
     """Host-built octree (libocg ocg_octree_build) with its canonical exports."""
 
-    def __init__(self, desc: P.OctreeDesc):
+    def __init__(self, desc: P.OctreeDesc, _prev=None, _box=None):
         lib = L.lib()
         self._h = C.c_void_p()
         self.desc = desc
-        L.check(lib.ocg_octree_build(C.byref(_desc(desc)), C.byref(self._h)))
+        if _prev is None:
+            L.check(lib.ocg_octree_build(C.byref(_desc(desc)), C.byref(self._h)))
+        else:
+            bx = (C.c_double * 6)(*[float(v) for v in _box])
+            L.check(lib.ocg_octree_rebuild(_prev._h, C.byref(_desc(desc)), bx, C.byref(self._h)))
         c = (C.c_int64 * 8)()
         L.check(lib.ocg_octree_counts(self._h, c))
         (self.n_leaves, self.n_faces, self.D, self.mc, self.n_cells, self.n_trec, self.n_tree,
          self.n_oct) = [int(v) for v in c]
+
+    def rebuild(self, desc: P.OctreeDesc, box):
+        """The octree of desc, built from this one after a change of the geometry confined
+        to box = (lox, loy, loz, hix, hiy, hiz) (ocg_octree_rebuild: the refinement
+        predicate is evaluated again only there)."""
+        return Octree(desc, _prev=self, _box=box)
 
     def __del__(self):
         if getattr(self, "_h", None) and self._h.value:
