@@ -490,10 +490,17 @@ static void build_impl(const ocg_octree_desc& desc, HostTree& T, const HostTree*
     if (T.ncell >= (int64_t)1 << 31) throw std::runtime_error("more than 2^31 cells");
 
     // ---- per-cell tables
-    T.child_oct.assign(T.ncell, -1);
-    T.cell_rank.assign(T.ncell, -1);
-    T.cell_flags.assign(T.ncell, 0);
-    T.cell_level.assign(T.ncell, 0);
+#pragma omp parallel sections
+    {
+#pragma omp section
+        T.child_oct.assign(T.ncell, -1);
+#pragma omp section
+        T.cell_rank.assign(T.ncell, -1);
+#pragma omp section
+        T.cell_flags.assign(T.ncell, 0);
+#pragma omp section
+        T.cell_level.assign(T.ncell, 0);
+    }
     for (int m = mc; m <= D; ++m) {
         const LevelMeta& l = T.L(m);
 #pragma omp parallel for schedule(static)
@@ -556,8 +563,17 @@ static void build_impl(const ocg_octree_desc& desc, HostTree& T, const HostTree*
     }
     T.nleaf = (int64_t)T.leaf_cell.size();
     T.leaf_first[D + 1] = T.nleaf;
-    T.leaf_depth.resize(T.nleaf);
-    T.leaf_i.resize(T.nleaf); T.leaf_j.resize(T.nleaf); T.leaf_k.resize(T.nleaf);
+#pragma omp parallel sections
+    {
+#pragma omp section
+        T.leaf_depth.resize(T.nleaf);
+#pragma omp section
+        T.leaf_i.resize(T.nleaf);
+#pragma omp section
+        T.leaf_j.resize(T.nleaf);
+#pragma omp section
+        T.leaf_k.resize(T.nleaf);
+    }
 #pragma omp parallel for schedule(static)
     for (int64_t r = 0; r < T.nleaf; ++r) {
         const int64_t g = T.leaf_cell[r];
@@ -646,29 +662,24 @@ static void build_impl(const ocg_octree_desc& desc, HostTree& T, const HostTree*
     // face of a fine leaf against a coarser leaf (T record) is keyed by the virtual cell
     // beyond it and is merged in.
     std::vector<int64_t> gcount(3 * (D + 1), 0), gbase(3 * (D + 1) + 1, 0);
-    struct Group {
-        std::vector<int32_t> mi, pl;
-        std::vector<int64_t> slot;
-        std::vector<uint64_t> tkey;
-        std::vector<int32_t> tmi, tpl;
-        std::vector<int64_t> tslot;
-    };
+    struct MF { int32_t mi, pl; int64_t slot; };
+    struct TF { uint64_t key; int32_t mi, pl; int64_t slot; };
     auto leaf_key = [&](int64_t r) -> uint64_t {
         const int d = T.leaf_depth[r];
         if (d == 0) return morton3(T.leaf_i[r], T.leaf_j[r], T.leaf_k[r]);
         const int64_t lc = T.leaf_cell[r] - T.L(d).off;
         return (T.okeys[d - mc][lc >> 3] << 3) | (uint64_t)(lc & 7);
     };
-    std::vector<Group> groups(3 * (D + 1));
+    std::vector<std::vector<MF>> gm(3 * (D + 1));
+    std::vector<std::vector<TF>> gt(3 * (D + 1));
     for (int a = 0; a < 3; ++a)
         for (int d = 0; d <= D; ++d) {
-            Group& G = groups[a * (D + 1) + d];
+            const int gi = a * (D + 1) + d;
             const int64_t r0 = T.leaf_first[d], r1 = T.leaf_first[d + 1];
             const int64_t off = T.L(d).off;
             const int bit = 1 << a;
             // - faces
-            struct MF { int32_t mi, pl; int64_t slot; };
-            std::vector<MF> mf = par_compact<MF>(r1 - r0, [&](int64_t q, MF& out) {
+            gm[gi] = par_compact<MF>(r1 - r0, [&](int64_t q, MF& out) {
                 const int64_t r = r0 + q, g = T.leaf_cell[r];
                 const int s = (int)(g & 7);
                 int64_t gn = -1;
@@ -682,11 +693,9 @@ static void build_impl(const ocg_octree_desc& desc, HostTree& T, const HostTree*
                 out = MF{T.cell_rank[gn], (int32_t)r, (int64_t)a * T.ncell + g};
                 return true;
             });
-            G.mi.resize(mf.size()); G.pl.resize(mf.size()); G.slot.resize(mf.size());
-            for (size_t q = 0; q < mf.size(); ++q) { G.mi[q] = mf[q].mi; G.pl[q] = mf[q].pl; G.slot[q] = mf[q].slot; }
             // + faces at T-junctions
-            struct TF { uint64_t key; int32_t mi, pl; int64_t slot; };
-            std::vector<TF> tf = par_compact<TF>(r1 - r0, [&](int64_t q, TF& out) {
+            std::vector<TF>& tf = gt[gi];
+            tf = par_compact<TF>(r1 - r0, [&](int64_t q, TF& out) {
                 const int64_t r = r0 + q, g = T.leaf_cell[r];
                 const int s = (int)(g & 7);
                 if (!(s & bit)) return false;
@@ -700,37 +709,71 @@ static void build_impl(const ocg_octree_desc& desc, HostTree& T, const HostTree*
                 return true;
             });
             std::sort(tf.begin(), tf.end(), [](const TF& x, const TF& y) { return x.key < y.key; });
-            G.tkey.resize(tf.size()); G.tmi.resize(tf.size()); G.tpl.resize(tf.size()); G.tslot.resize(tf.size());
-            for (size_t q = 0; q < tf.size(); ++q) {
-                G.tkey[q] = tf[q].key; G.tmi[q] = tf[q].mi; G.tpl[q] = tf[q].pl; G.tslot[q] = tf[q].slot;
-            }
-            gcount[a * (D + 1) + d] = (int64_t)(mf.size() + tf.size());
+            gcount[gi] = (int64_t)(gm[gi].size() + tf.size());
         }
     for (size_t q = 0; q < gcount.size(); ++q) gbase[q + 1] = gbase[q] + gcount[q];
     T.nface = gbase.back();
-    T.f_axis.resize(T.nface); T.f_depth.resize(T.nface);
-    T.f_minus.resize(T.nface); T.f_plus.resize(T.nface);
-    T.f_slot.resize(T.nface); T.f_kind.resize(T.nface);
+    // (the arrays are sized in parallel: zero-filling ~19 bytes per face on one thread took
+    // longer than the merge itself)
+#pragma omp parallel sections
+    {
+#pragma omp section
+        T.f_axis.resize(T.nface);
+#pragma omp section
+        T.f_depth.resize(T.nface);
+#pragma omp section
+        T.f_minus.resize(T.nface);
+#pragma omp section
+        T.f_plus.resize(T.nface);
+#pragma omp section
+        T.f_slot.resize(T.nface);
+#pragma omp section
+        T.f_kind.resize(T.nface);
+    }
+    // Merge each group's two key-ordered lists (no key is in both: a T face's key is a cell
+    // that is not a leaf of that depth) in chunks of about 2^20 - faces: chunk c takes the
+    // - faces [x_c, x_c+1) and the T faces whose keys fall before the key of - face x_c+1,
+    // and writes from position x_c + y_c of its group, as the one-pass merge would.
+    struct Chunk { int gi; int64_t x0, x1, y0, y1; };
+    std::vector<Chunk> chunks;
+    for (int gi = 0; gi < (int)gm.size(); ++gi) {
+        const std::vector<MF>& mf = gm[gi];
+        const std::vector<TF>& tf = gt[gi];
+        const int64_t nx = (int64_t)mf.size(), nc = std::max<int64_t>(1, nx >> 20);
+        auto ysplit = [&](int64_t x) -> int64_t {
+            const uint64_t key = leaf_key(mf[x].pl);
+            return std::lower_bound(tf.begin(), tf.end(), key,
+                                    [](const TF& t, uint64_t k) { return t.key < k; }) - tf.begin();
+        };
+        int64_t x0 = 0, y0 = 0;
+        for (int64_t c = 1; c <= nc; ++c) {
+            const int64_t x1 = c == nc ? nx : nx * c / nc;
+            const int64_t y1 = c == nc ? (int64_t)tf.size() : ysplit(x1);
+            chunks.push_back(Chunk{gi, x0, x1, y0, y1});
+            x0 = x1;
+            y0 = y1;
+        }
+    }
 #pragma omp parallel for schedule(dynamic, 1)
-    for (int gi = 0; gi < (int)groups.size(); ++gi) {
-        Group& G = groups[gi];
-        const int a = gi / (D + 1), d = gi % (D + 1);
-        int64_t f = gbase[gi];
-        size_t x = 0, y = 0;
-        while (x < G.mi.size() || y < G.tkey.size()) {
-            const bool take_t = y < G.tkey.size() && (x >= G.mi.size() || G.tkey[y] < leaf_key(G.pl[x]));
+    for (int64_t ci = 0; ci < (int64_t)chunks.size(); ++ci) {
+        const Chunk& K = chunks[ci];
+        const std::vector<MF>& mf = gm[K.gi];
+        const std::vector<TF>& tf = gt[K.gi];
+        const int a = K.gi / (D + 1), d = K.gi % (D + 1);
+        int64_t f = gbase[K.gi] + K.x0 + K.y0, x = K.x0, y = K.y0;
+        while (x < K.x1 || y < K.y1) {
+            const bool take_t = y < K.y1 && (x >= K.x1 || tf[y].key < leaf_key(mf[x].pl));
             if (take_t) {
-                T.f_minus[f] = G.tmi[y]; T.f_plus[f] = G.tpl[y]; T.f_slot[f] = G.tslot[y]; T.f_kind[f] = 1;
+                T.f_minus[f] = tf[y].mi; T.f_plus[f] = tf[y].pl; T.f_slot[f] = tf[y].slot; T.f_kind[f] = 1;
                 ++y;
             } else {
-                T.f_minus[f] = G.mi[x]; T.f_plus[f] = G.pl[x]; T.f_slot[f] = G.slot[x]; T.f_kind[f] = 0;
+                T.f_minus[f] = mf[x].mi; T.f_plus[f] = mf[x].pl; T.f_slot[f] = mf[x].slot; T.f_kind[f] = 0;
                 ++x;
             }
             T.f_axis[f] = (int8_t)a;
             T.f_depth[f] = (int8_t)d;
             ++f;
         }
-        G = Group();   // release the group's buffers
     }
 }
 

@@ -67,6 +67,20 @@ def test_octree_tables_bit_exact(desc):
         assert np.array_equal(leafo, leafg)
 
 
+def test_faces_bit_exact_when_a_group_is_merged_in_several_chunks():
+    # the host build merges each (axis, depth) group of faces in chunks of about 2^20 of
+    # its - faces; the cut-cell 64^3 tree has a group large enough for two chunks, with T
+    # faces on both sides of the split
+    desc = P.cut_cell(64, 2).desc
+    g = S.Octree(desc)
+    fg = g.faces()
+    big = max(int(np.sum((fg["axis"] == a) & (fg["depth"] == d))) for a in range(3) for d in range(g.D + 1))
+    assert big >= 2 ** 21
+    fo = O.Octree(desc).faces()
+    for k in ("axis", "depth", "i", "j", "k", "minus", "plus"):
+        assert np.array_equal(fo[k], fg[k]), k
+
+
 def test_config_leaf_counts():
     # two-level ball: 64^3 base with the central ball refined once
     g = S.Octree(P.two_level_ball(64).desc)
