@@ -11,6 +11,7 @@
 #include <cmath>
 #include <numeric>
 #include <stdexcept>
+#include <utility>
 
 #ifdef _OPENMP
 #include <omp.h>
@@ -242,6 +243,28 @@ void HostTree::cell_coords(int m, int64_t g, int64_t& i, int64_t& j, int64_t& k)
     j = 2 * (int64_t)J + ((s >> 1) & 1);
     k = 2 * (int64_t)K + ((s >> 2) & 1);
 }
+
+// Allocator whose element construction without arguments leaves trivially constructible
+// values uninitialised, for large work arrays that a parallel pass fills completely: a
+// value-initialising resize would zero them on one thread first.
+template <class T>
+struct NoInitAlloc : std::allocator<T> {
+    template <class U>
+    struct rebind {
+        using other = NoInitAlloc<U>;
+    };
+    NoInitAlloc() = default;
+    template <class U>
+    NoInitAlloc(const NoInitAlloc<U>&) noexcept {}
+    template <class U>
+    void construct(U* p) noexcept {
+        ::new ((void*)p) U;
+    }
+    template <class U, class... A>
+    void construct(U* p, A&&... a) {
+        ::new ((void*)p) U(std::forward<A>(a)...);
+    }
+};
 
 // Parallel stream compaction: out = [value(c) for c in 0..n-1 if keep(c)], in order.
 // pred(c, value&) returns keep and fills value.
@@ -670,47 +693,92 @@ static void build_impl(const ocg_octree_desc& desc, HostTree& T, const HostTree*
         const int64_t lc = T.leaf_cell[r] - T.L(d).off;
         return (T.okeys[d - mc][lc >> 3] << 3) | (uint64_t)(lc & 7);
     };
-    std::vector<std::vector<MF>> gm(3 * (D + 1));
-    std::vector<std::vector<TF>> gt(3 * (D + 1));
-    for (int a = 0; a < 3; ++a)
-        for (int d = 0; d <= D; ++d) {
-            const int gi = a * (D + 1) + d;
-            const int64_t r0 = T.leaf_first[d], r1 = T.leaf_first[d + 1];
-            const int64_t off = T.L(d).off;
-            const int bit = 1 << a;
-            // - faces
-            gm[gi] = par_compact<MF>(r1 - r0, [&](int64_t q, MF& out) {
-                const int64_t r = r0 + q, g = T.leaf_cell[r];
-                const int s = (int)(g & 7);
-                int64_t gn = -1;
-                if (s & bit) gn = g - bit;
-                else {
-                    const int32_t v = T.nbr[(int64_t)(2 * a) * T.noct + (g >> 3)];
-                    if (v >= 0) gn = off + 8 * (int64_t)v + (s | bit);
-                    else if (v <= -2) gn = -2 - (int64_t)v;
-                }
-                if (gn < 0 || !(T.cell_flags[gn] & 1)) return false;
-                out = MF{T.cell_rank[gn], (int32_t)r, (int64_t)a * T.ncell + g};
-                return true;
-            });
-            // + faces at T-junctions
-            std::vector<TF>& tf = gt[gi];
-            tf = par_compact<TF>(r1 - r0, [&](int64_t q, TF& out) {
-                const int64_t r = r0 + q, g = T.leaf_cell[r];
-                const int s = (int)(g & 7);
-                if (!(s & bit)) return false;
-                const int32_t v = T.nbr[(int64_t)(2 * a + 1) * T.noct + (g >> 3)];
-                if (v > -2) return false;
-                int64_t c[3] = {T.leaf_i[r], T.leaf_j[r], T.leaf_k[r]};
-                c[a] += 1;
-                const int32_t t = T.trec[g >> 3];
-                out = TF{morton3(c[0], c[1], c[2]), (int32_t)r, T.cell_rank[-2 - (int64_t)v],
-                         (int64_t)((2 * a + 1) * 4 + sub_index(a, s)) * T.nt + t};
-                return true;
-            });
-            std::sort(tf.begin(), tf.end(), [](const TF& x, const TF& y) { return x.key < y.key; });
-            gcount[gi] = (int64_t)(gm[gi].size() + tf.size());
+    std::vector<std::vector<MF, NoInitAlloc<MF>>> gm(3 * (D + 1));
+    std::vector<std::vector<TF, NoInitAlloc<TF>>> gt(3 * (D + 1));
+    // The - face of a leaf on each axis (when the cell beyond it is a leaf) and the + face
+    // of a fine leaf against a coarser one, for the three axes in one pass over the leaves
+    // of a depth: a counting pass per chunk of leaves, then a writing pass from each chunk's
+    // offsets (the lists keep leaf order).
+    auto face_of = [&](int64_t r, int a, int64_t off, MF* mf, TF* tf) -> int {
+        const int64_t g = T.leaf_cell[r];
+        const int s = (int)(g & 7), bit = 1 << a;
+        int got = 0;
+        int64_t gn = -1;
+        if (s & bit) gn = g - bit;
+        else {
+            const int32_t v = T.nbr[(int64_t)(2 * a) * T.noct + (g >> 3)];
+            if (v >= 0) gn = off + 8 * (int64_t)v + (s | bit);
+            else if (v <= -2) gn = -2 - (int64_t)v;
         }
+        if (gn >= 0 && (T.cell_flags[gn] & 1)) {
+            if (mf) *mf = MF{T.cell_rank[gn], (int32_t)r, (int64_t)a * T.ncell + g};
+            got |= 1;
+        }
+        if (s & bit) {
+            const int32_t v = T.nbr[(int64_t)(2 * a + 1) * T.noct + (g >> 3)];
+            if (v <= -2) {
+                if (tf) {
+                    int64_t c[3] = {T.leaf_i[r], T.leaf_j[r], T.leaf_k[r]};
+                    c[a] += 1;
+                    const int32_t t = T.trec[g >> 3];
+                    *tf = TF{morton3(c[0], c[1], c[2]), (int32_t)r, T.cell_rank[-2 - (int64_t)v],
+                             (int64_t)((2 * a + 1) * 4 + sub_index(a, s)) * T.nt + t};
+                }
+                got |= 2;
+            }
+        }
+        return got;
+    };
+#ifdef _OPENMP
+    const int nch = std::max(1, omp_get_max_threads() * 8);
+#else
+    const int nch = 1;
+#endif
+    for (int d = 0; d <= D; ++d) {
+        const int64_t r0 = T.leaf_first[d], n = T.leaf_first[d + 1] - r0;
+        const int64_t off = T.L(d).off;
+        std::vector<int64_t> cnt((size_t)(nch + 1) * 6, 0);   // [chunk + 1][axis * 2 + list]
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int c = 0; c < nch; ++c) {
+            const int64_t lo = r0 + n * c / nch, hi = r0 + n * (c + 1) / nch;
+            int64_t k[6] = {0, 0, 0, 0, 0, 0};
+            for (int64_t r = lo; r < hi; ++r)
+                for (int a = 0; a < 3; ++a) {
+                    const int got = face_of(r, a, off, nullptr, nullptr);
+                    k[2 * a] += got & 1;
+                    k[2 * a + 1] += got >> 1;
+                }
+            for (int q = 0; q < 6; ++q) cnt[(size_t)(c + 1) * 6 + q] = k[q];
+        }
+        for (int c = 0; c < nch; ++c)
+            for (int q = 0; q < 6; ++q) cnt[(size_t)(c + 1) * 6 + q] += cnt[(size_t)c * 6 + q];
+#pragma omp parallel for schedule(static, 1)
+        for (int q = 0; q < 6; ++q) {
+            const int gi = (q >> 1) * (D + 1) + d;
+            if (q & 1) gt[gi].resize(cnt[(size_t)nch * 6 + q]);
+            else gm[gi].resize(cnt[(size_t)nch * 6 + q]);
+        }
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int c = 0; c < nch; ++c) {
+            const int64_t lo = r0 + n * c / nch, hi = r0 + n * (c + 1) / nch;
+            int64_t k[6];
+            for (int q = 0; q < 6; ++q) k[q] = cnt[(size_t)c * 6 + q];
+            for (int64_t r = lo; r < hi; ++r)
+                for (int a = 0; a < 3; ++a) {
+                    MF mf;
+                    TF tf;
+                    const int got = face_of(r, a, off, &mf, &tf);
+                    if (got & 1) gm[a * (D + 1) + d][k[2 * a]++] = mf;
+                    if (got & 2) gt[a * (D + 1) + d][k[2 * a + 1]++] = tf;
+                }
+        }
+#pragma omp parallel for schedule(static, 1)
+        for (int a = 0; a < 3; ++a) {
+            auto& tf = gt[a * (D + 1) + d];
+            std::sort(tf.begin(), tf.end(), [](const TF& x, const TF& y) { return x.key < y.key; });
+            gcount[a * (D + 1) + d] = (int64_t)(gm[a * (D + 1) + d].size() + tf.size());
+        }
+    }
     for (size_t q = 0; q < gcount.size(); ++q) gbase[q + 1] = gbase[q] + gcount[q];
     T.nface = gbase.back();
     // (the arrays are sized in parallel: zero-filling ~19 bytes per face on one thread took
@@ -737,8 +805,8 @@ static void build_impl(const ocg_octree_desc& desc, HostTree& T, const HostTree*
     struct Chunk { int gi; int64_t x0, x1, y0, y1; };
     std::vector<Chunk> chunks;
     for (int gi = 0; gi < (int)gm.size(); ++gi) {
-        const std::vector<MF>& mf = gm[gi];
-        const std::vector<TF>& tf = gt[gi];
+        const auto& mf = gm[gi];
+        const auto& tf = gt[gi];
         const int64_t nx = (int64_t)mf.size(), nc = std::max<int64_t>(1, nx >> 20);
         auto ysplit = [&](int64_t x) -> int64_t {
             const uint64_t key = leaf_key(mf[x].pl);
@@ -757,8 +825,8 @@ static void build_impl(const ocg_octree_desc& desc, HostTree& T, const HostTree*
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t ci = 0; ci < (int64_t)chunks.size(); ++ci) {
         const Chunk& K = chunks[ci];
-        const std::vector<MF>& mf = gm[K.gi];
-        const std::vector<TF>& tf = gt[K.gi];
+        const auto& mf = gm[K.gi];
+        const auto& tf = gt[K.gi];
         const int a = K.gi / (D + 1), d = K.gi % (D + 1);
         int64_t f = gbase[K.gi] + K.x0 + K.y0, x = K.x0, y = K.y0;
         while (x < K.x1 || y < K.y1) {
