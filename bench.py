@@ -34,6 +34,7 @@ WORKLOAD = ("octree 64^3 root, ball r=0.25 at the centre refined once (382,936 l
 # algorithmic bytes per cell of one red-black colour sweep: 16 B coefficients (c, c_x-,
 # c_y-, c_z- in FP32) + 4 B u read + 2 B u write (half the cells) + 2 B b (half)
 SWEEP_BYTES_PER_CELL = 24.0
+NOMINAL_HBM_GBS = 7700.0   # B300 HBM3e nominal bandwidth, for a second fraction beside the measured one
 
 
 def _peaks():
@@ -541,7 +542,8 @@ def _large(dev, stream, flush, args, peak):
             "sweep_forms": forms,
             "roofline": {"bound": "hbm", "kernel": "red-black colour sweep (%s form) on level %d" % (form, D),
                          "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                         "frac": round(achieved / peak, 4), "bytes_per_cell": SWEEP_BYTES_PER_CELL,
+                         "frac": round(achieved / peak, 4), "frac_of_nominal": round(achieved / NOMINAL_HBM_GBS, 4),
+                         "bytes_per_cell": SWEEP_BYTES_PER_CELL,
                          "cells_per_launch": ce.value, "launches": nl.value, "avg_launch_us": round(sweep_us, 2),
                          "traffic": _profiled_traffic("sweep_sineband_level%d_%s" % (D, form), ce.value),
                          "traffic_note": "dram bytes per cell of an ncu capture at 64^3 root (same field, "
@@ -797,6 +799,7 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "kernel": "red-black colour sweep (%s form) on level %d" % (fwd, big),
                      "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "peak_source": peak_kind,
+                     "frac_of_nominal": round(achieved / NOMINAL_HBM_GBS, 4),
                      "bytes_per_cell": SWEEP_BYTES_PER_CELL, "cells_per_launch": sw_cells,
                      "launches": sw_n, "avg_launch_us": round(sweep_us, 3),
                      "timing": "CUDA event-record nodes around each launch inside one graph of the solve",
