@@ -140,3 +140,18 @@ def test_grandchildren_of_a_newly_refined_cell_outside_the_box_are_evaluated():
     g1 = S.Octree(d0).rebuild(d1, speck)
     _assert_same(g1, S.Octree(d1))
     assert S.Octree(d1).n_leaves != S.Octree(d0).n_leaves
+
+
+def test_one_of_several_primitives_changes():
+    # the signed distance is the minimum over two spheres and a box; moving one sphere and
+    # shrinking the other, each with its own box, rebuilt one after the other
+    a0, a1 = (0.3, 0.35, 0.5, 0.12), (0.33, 0.37, 0.48, 0.12)
+    b0, b1 = (0.55, 0.7, 0.45, 0.1), (0.55, 0.7, 0.45, 0.07)
+    box = (0.7, 0.15, 0.2, 0.9, 0.5, 0.8)
+    def desc(sa, sb):
+        return P.OctreeDesc(12, 2, P.REFINE_SDF_BAND, band=0.02, spheres=[sa, sb], boxes=[box])
+    g = S.Octree(desc(a0, b0))
+    g = g.rebuild(desc(a1, b0), S.sphere_change_box(a0, a1, 0.02, 12))
+    _assert_same(g, S.Octree(desc(a1, b0)))
+    g = g.rebuild(desc(a1, b1), S.sphere_change_box(b0, b1, 0.02, 12))
+    _assert_same(g, S.Octree(desc(a1, b1)))
