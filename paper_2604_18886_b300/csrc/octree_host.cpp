@@ -560,29 +560,37 @@ static void build_impl(const ocg_octree_desc& desc, HostTree& T, const HostTree*
     }
     // canonical leaves: sorted by (depth, Morton key); level 0 is sorted explicitly, levels
     // m >= 1 are stored in Morton order already
-    T.leaf_cell.clear();
     T.leaf_first.assign(D + 2, 0);
-    {
-        const LevelMeta& l = T.L(0);
-        std::vector<std::pair<uint64_t, int64_t>> lv;
-        for (int64_t lc = 0; lc < l.ncell; ++lc) {
-            const int64_t g = l.off + lc;
-            if (!(T.cell_flags[g] & 1)) continue;
+    std::vector<std::pair<uint64_t, int32_t>> lv0 =
+        par_compact<std::pair<uint64_t, int32_t>>(T.L(0).ncell, [&](int64_t lc, std::pair<uint64_t, int32_t>& out) {
+            const int64_t g = T.L(0).off + lc;
+            if (!(T.cell_flags[g] & 1)) return false;
             int64_t i, j, k;
             T.cell_coords(0, g, i, j, k);
-            lv.push_back({morton3(i, j, k), g});
-        }
-        std::sort(lv.begin(), lv.end());
-        for (const auto& e : lv) T.leaf_cell.push_back((int32_t)e.second);
-    }
-    for (int m = 1; m <= D; ++m) {
-        T.leaf_first[m] = (int64_t)T.leaf_cell.size();
-        const LevelMeta& l = T.L(m);
-        std::vector<int32_t> part = par_compact<int32_t>(l.ncell, [&](int64_t lc, int32_t& out) {
-            out = (int32_t)(l.off + lc);
-            return (T.cell_flags[l.off + lc] & 1) != 0;
+            out = {morton3(i, j, k), (int32_t)g};
+            return true;
         });
-        T.leaf_cell.insert(T.leaf_cell.end(), part.begin(), part.end());
+    std::sort(lv0.begin(), lv0.end());
+    // leaves per level m >= 1 (stored in Morton order already), then each level's leaves
+    // written at their canonical ranks by a parallel scan
+    T.leaf_first[1] = (int64_t)lv0.size();
+    for (int m = 1; m <= D; ++m) {
+        const LevelMeta& l = T.L(m);
+        int64_t nl = 0;
+#pragma omp parallel for schedule(static) reduction(+ : nl)
+        for (int64_t lc = 0; lc < l.ncell; ++lc) nl += T.cell_flags[l.off + lc] & 1;
+        T.leaf_first[m + 1] = T.leaf_first[m] + nl;
+    }
+    T.leaf_cell.resize(T.leaf_first[D + 1]);
+#pragma omp parallel for schedule(static)
+    for (int64_t q = 0; q < (int64_t)lv0.size(); ++q) T.leaf_cell[q] = lv0[q].second;
+    for (int m = 1; m <= D; ++m) {
+        const LevelMeta& l = T.L(m);
+        const int64_t base = T.leaf_first[m];
+        par_scan(l.ncell, [&](int64_t lc) { return (int64_t)(T.cell_flags[l.off + lc] & 1); },
+                 [&](int64_t lc, int64_t rank) {
+                     if (T.cell_flags[l.off + lc] & 1) T.leaf_cell[base + rank] = (int32_t)(l.off + lc);
+                 });
     }
     T.nleaf = (int64_t)T.leaf_cell.size();
     T.leaf_first[D + 1] = T.nleaf;
