@@ -34,9 +34,11 @@ def _project(v):
     return v - v.mean()
 
 
-def face_grad(H, p, lam):
-    """dL/dbeta_f = -lambda^T (dA/dbeta_f) p for every canonical face (order of
-    H.faces), from the per-face closed forms in the module docstring."""
+def face_factors(H, p, lam):
+    """The three factors of dL/dbeta_f = -coef_f * dlam_f * dp_f for every canonical face
+    (order of H.faces), from the per-face closed forms in the module docstring:
+    regular faces coef = h, dlam = lambda_i - lambda_j, dp = p_i - p_j; T sub-faces
+    coef = h/2, dlam = lambda_i - lambda_K, dp = pbar_P - p_K."""
     t = H.tree
     f = H.faces
     L = t.leaves
@@ -46,9 +48,12 @@ def face_grad(H, p, lam):
     d = f["depth"]
     h = 1.0 / (t.n0 * (2.0 ** d))
     dm, dp = L["depth"][mi], L["depth"][pl]
-    out = np.zeros(len(mi))
+    coef = h.astype(np.float64).copy()
+    dlam = np.zeros(len(mi))
+    dpv = np.zeros(len(mi))
     reg = dm == dp
-    out[reg] = -h[reg] * (lam[mi[reg]] - lam[pl[reg]]) * (p[mi[reg]] - p[pl[reg]])
+    dlam[reg] = lam[mi[reg]] - lam[pl[reg]]
+    dpv[reg] = p[mi[reg]] - p[pl[reg]]
     tf = np.nonzero(~reg)[0]
     if len(tf):
         fine = np.where(dm[tf] == d[tf], mi[tf], pl[tf])
@@ -61,8 +66,17 @@ def face_grad(H, p, lam):
             P = lv.index(L["i"][fi] // 2, L["j"][fi] // 2, L["k"][fi] // 2)
             assert np.all(P >= 0)
             pbar[sel] = H.leaves_to_level(dd - 1, p)[P]
-        out[tf] = -(h[tf] / 2.0) * (lam[fine] - lam[coarse]) * (pbar - p[coarse])
-    return out
+        coef[tf] = h[tf] / 2.0
+        dlam[tf] = lam[fine] - lam[coarse]
+        dpv[tf] = pbar - p[coarse]
+    return coef, dlam, dpv
+
+
+def face_grad(H, p, lam):
+    """dL/dbeta_f = -lambda^T (dA/dbeta_f) p for every canonical face (order of
+    H.faces), from the per-face closed forms in the module docstring."""
+    coef, dlam, dpv = face_factors(H, p, lam)
+    return -coef * dlam * dpv
 
 
 def solve(H, rhs, transpose=False, tol=1e-13, method="krylov", prm=None):

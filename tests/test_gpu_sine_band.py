@@ -5,7 +5,8 @@ Neumann walls, divergence right-hand side (seed 7); loss L = 1/2 ||p - p_t||^2 w
 p_t ~ N(0,1) (seed 8).  Too large for the oracle: checked through properties that hold at
 any size (the FP64 residual of the returned solution, agreement of the mixed solve with
 the FP64 solve, grid-independent iteration counts against the same field at half the
-resolution) and the gradient against central finite differences on 32 faces (seed 9).
+resolution) and the gradient against central finite differences on 32 faces (seed 9;
+uniform, T sub-faces, faces at the beta clamp and partly cut faces), face by face.
 
 Finite differences at 1e8 unknowns: the difference of two independently converged solves
 is dominated by their solver errors (each ~1e-12 relative to a solution whose loss is
@@ -20,6 +21,8 @@ import pytest
 
 from paper_2604_18886_b300 import problems as P
 from paper_2604_18886_b300 import solver as S
+
+from test_gpu_adjoint import fd_check
 
 pytestmark = pytest.mark.gpu
 
@@ -36,6 +39,33 @@ def _setup(n0=128):
     beta, b = P.large_inputs(p, g.n_leaves, g.n_faces, g.faces_range, "cuda")
     _STATE[n0] = (p, g, beta, torch.from_numpy(b).cuda())
     return _STATE[n0]
+
+
+def _fd_faces(g, beta):
+    """32 faces (seed 9): 12 uniform over all faces, and from eight random runs of 2^18
+    consecutive canonical faces 8 T sub-faces (leaves of different depths), 6 faces at the
+    beta = 1e-3 clamp and 6 partly cut faces (1e-3 < beta < 1)."""
+    rng = np.random.default_rng(9)
+    uni = np.sort(rng.choice(g.n_faces, 12, replace=False))
+    depth = g.leaf_depths()
+    run = 1 << 18
+    cand = {"T": [], "clamped": [], "cut": []}
+    for first in rng.choice(g.n_faces - run, 8, replace=False):
+        fr = g.faces_range(int(first), run)
+        idx = np.arange(first, first + run)
+        bv = beta[int(first):int(first) + run].cpu().numpy()
+        tmask = depth[fr["minus"]] != depth[fr["plus"]]
+        cand["T"].append(idx[tmask])
+        cand["clamped"].append(idx[(bv == np.float32(1e-3)) & ~tmask])
+        cand["cut"].append(idx[(bv > np.float32(1e-3)) & (bv < 1.0) & ~tmask])
+    del depth
+    picks, kinds = [uni], ["uniform"] * 12
+    for kind, k in (("T", 8), ("clamped", 6), ("cut", 6)):
+        pool = np.setdiff1d(np.concatenate(cand[kind]), uni)
+        assert len(pool) >= k, (kind, len(pool))
+        picks.append(rng.choice(pool, k, replace=False))
+        kinds += [kind] * k
+    return np.concatenate(picks), kinds
 
 
 def test_full_size_c5_counts_and_mixed_solve():
@@ -79,35 +109,13 @@ def test_full_size_c5_gradient_matches_central_differences():
         assert rel(xm) <= 1.5 * rel(x6) + 1e-5, (rel(xm), rel(x6))
         assert rel(x9) <= 1e-5, rel(x9)
     pt = torch.from_numpy(np.random.default_rng(8).standard_normal(g.n_leaves)).cuda()
-    lam, st = h0.solve(x0 - pt, tol=1e-12, precision="fp64", max_iter=300, transpose=True)
-    assert st.converged
-    grad = h0.face_grad(x0, lam)
-    rng = np.random.default_rng(9)
-    faces = np.sort(rng.choice(g.n_faces, 32, replace=False))
-    Ax0 = h0.apply_A(x0)
+    faces, kinds = _fd_faces(g, beta)
+    fd_check(g, beta, p.bc, b, pt, faces, kinds, prm)
     g0 = x0 - pt
-    fd = np.empty(len(faces))
-    for q, fi in enumerate(faces):
-        b0 = float(beta[fi])
-        eps = 1e-3 * b0
-        dps, epss = [], []
-        for sgn in (1.0, -1.0):
-            bb = beta.clone()
-            bb[fi] = float(np.float32(b0 + sgn * eps))
-            epss.append(abs(float(bb[fi]) - b0))
-            hs = S.Hierarchy(g, bb, p.bc, prm)
-            rhs = Ax0 - hs.apply_A(x0)
-            dp, s2 = hs.solve(rhs, tol=1e-12, precision="fp64", max_iter=300)
-            assert s2.converged
-            dps.append(dp)
-            del hs
-        dl = torch.dot(dps[0] - dps[1], g0 + 0.5 * (dps[0] + dps[1])).item()
-        fd[q] = dl / (epss[0] + epss[1])
-    got = grad[torch.from_numpy(faces).cuda()].cpu().numpy()
-    scale = np.abs(got).max()
-    assert scale > 0
-    err = np.abs(fd - got)
-    assert err.max() <= 1e-4 * scale, (err.max(), scale)
+    g0 = g0 - g0.mean()
+    lam, st = h0.solve(g0, tol=1e-12, precision="fp64", max_iter=300, transpose=True)
+    assert st.converged
+    rng = np.random.default_rng(9)
     # dL/db = lambda: central differences in b_k (exact in b, the solve is linear)
     lv = rng.choice(g.n_leaves, 4, replace=False)
     for k in lv:
@@ -116,4 +124,6 @@ def test_full_size_c5_gradient_matches_central_differences():
         d, s3 = h0.solve(e, tol=1e-12, precision="fp64", max_iter=300)
         assert s3.converged
         fdb = torch.dot(d, g0).item()
-        assert abs(fdb - lam[int(k)].item()) <= 1e-6 * lam.abs().max().item()
+        # per leaf: 1e-4 of lambda_k, plus the solve's effect ||res|| ||lambda|| on <d, g0>
+        noise = s3.true_rel_res * lam.norm().item()
+        assert abs(fdb - lam[int(k)].item()) <= 1e-4 * abs(lam[int(k)].item()) + noise, (fdb, lam[int(k)].item())
