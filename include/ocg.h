@@ -20,6 +20,10 @@
  *    sorted by (depth, Morton key of (i,j,k) with x in bit 0).
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  A call
  *    is asynchronous on that stream unless its comment says it synchronises.
+ *  - Device: an octree's tables go to the device that is current at its first
+ *    ocg_setup_hierarchy, and a hierarchy belongs to that device.  Every later call on
+ *    either (set-up of another hierarchy on the octree, applies, cycles, solves, batches)
+ *    must run with that device current, else it returns OCG_EINVAL.
  *  - Boundary codes per wall in the order x-, x+, y-, y+, z-, z+: OCG_BC_NEUMANN (0) or
  *    OCG_BC_DIRICHLET (1, value held at the wall face, weight 2*h, beta = 1 on walls;
  *    a non-zero wall value enters through the right-hand side).
@@ -94,6 +98,10 @@ typedef struct ocg_hier ocg_hier;
  *                r2^j, coefficients formed as 1.0 / n! in double, and the quadrant
  *                q = k mod 4 selecting (sin r, cos r, -sin r, -cos r) for sin(a) and
  *                (cos r, -sin r, -cos r, sin r) for cos(a).  Valid for |a| < 2^20.
+ * With tile_log2 = t > 0 every aligned tile of 2^t x 2^t x 2^t depth-d cells takes one
+ * decision, the predicate above evaluated for the depth-(d - t) cell that covers the tile
+ * (i, j, k replaced by i >> t, j >> t, k >> t and n0 2^d by (n0 2^d) >> t): the paper's
+ * grids refine the 8^3 tiles that meet the surface (Sec. 4.1, t = 3).
  * followed by the minimal refinement that makes face-neighbouring leaves differ by at
  * most one depth (Sec. 3). */
 typedef struct {
@@ -102,7 +110,8 @@ typedef struct {
     int32_t refine;
     int32_t n_spheres;      /* <= 4 */
     int32_t n_boxes;        /* <= 4 */
-    int32_t reserved;
+    int32_t tile_log2;      /* 0..4: the predicate decides per aligned tile of 2^tile_log2
+                               cells per axis (n0 a multiple of 2^tile_log2); 0 = per cell */
     double band;
     double spheres[4][4];   /* cx, cy, cz, r */
     double boxes[4][6];     /* lox, loy, loz, hix, hiy, hiz */
@@ -129,7 +138,7 @@ int ocg_octree_build(const ocg_octree_desc* desc, ocg_octree** out);
  * ocg_octree_build(desc) makes, table for table; without it the result is a valid
  * 2:1-balanced octree but not necessarily that one.  prev is not modified and stays
  * valid; the new octree is independent of it.
- * Errors: EINVAL (null argument, bad desc, n0 / max_depth / refine differing from prev's,
+ * Errors: EINVAL (null argument, bad desc, n0 / max_depth / refine / tile_log2 differing from prev's,
  * box not finite or lo > hi), ENOMEM. */
 int ocg_octree_rebuild(const ocg_octree* prev, const ocg_octree_desc* desc, const double box[6],
                        ocg_octree** out);

@@ -68,10 +68,18 @@ def refine_predicate(desc, d, i, j, k):
                     (a * T_k(dz/r)) * T_k(dx/rho)) about the first sphere's centre, T_k
                     by the Chebyshev recurrence (Sec. 4.1's star surface)
     Ties count as not refined.
+    Tiles (desc.tile_log2 = t > 0; Sec. 4.1 refines the 8^3 tiles that meet the surface):
+    the aligned block of 2^t cells per axis around (i, j, k) decides as one cell of that
+    size, i.e. the rule above for the block (i // 2^t, j // 2^t, k // 2^t) on a grid of
+    n_d / 2^t blocks per axis.
     """
     from paper_2604_18886_b300 import problems as P
 
-    nd = float(desc.n0 * 2 ** d)
+    t = int(getattr(desc, "tile_log2", 0))
+    i = np.asarray(i, np.int64) >> t
+    j = np.asarray(j, np.int64) >> t
+    k = np.asarray(k, np.int64) >> t
+    nd = float((desc.n0 * 2 ** d) >> t)
     x = (np.asarray(i, np.float64) + 0.5) / nd
     y = (np.asarray(j, np.float64) + 0.5) / nd
     z = (np.asarray(k, np.float64) + 0.5) / nd

@@ -21,7 +21,7 @@ OCG_NOALLOC_MAX_CELLS = 1 << 20
 
 class OctreeDesc(C.Structure):
     _fields_ = [("n0", C.c_int32), ("max_depth", C.c_int32), ("refine", C.c_int32),
-                ("n_spheres", C.c_int32), ("n_boxes", C.c_int32), ("reserved", C.c_int32),
+                ("n_spheres", C.c_int32), ("n_boxes", C.c_int32), ("tile_log2", C.c_int32),
                 ("band", C.c_double), ("spheres", (C.c_double * 4) * 4),
                 ("boxes", (C.c_double * 6) * 4), ("n_sines", C.c_int32), ("reserved2", C.c_int32),
                 ("sines", (C.c_double * 5) * 8)]

@@ -26,6 +26,7 @@ struct BProb {
     double* part;         // reduction partials: 3 * max(nbv, nba)
     unsigned* cnt;        // reduction arrival counter
     const uint8_t* flags;
+    const float* rem;     // diagonal remainder of the tree cells (outer apply)
     const int32_t* leaf_cell;
     int ntree, nleaf;
     int vb0, nbv;         // vector kernels: first block, blocks
@@ -335,20 +336,21 @@ __global__ void __launch_bounds__(OBLK) kb_oavg(const BProb* __restrict__ PP, co
 }
 
 // Y = A V over all tree levels of every listed problem; which = 0: V = p, Y = Ap, reduces
-// (p, Ap) -> alpha; which = 1: V = xt, Y = yt (true residual), no reduction
-__global__ void __launch_bounds__(OBLK) kb_oapply(const BProb* __restrict__ PP, const BWork* __restrict__ W,
-                                                  const int* __restrict__ bmap, int which, BRed R) {
+// (p, Ap) -> alpha; which = 1: V = xt, Y = yt (true residual), no reduction.  Blocks of
+// OBLK2 threads, two lanes (z layers) per octet, as the single-problem outer apply.
+__global__ void __launch_bounds__(OBLK2) kb_oapply(const BProb* __restrict__ PP, const BWork* __restrict__ W,
+                                                   const int* __restrict__ bmap, int which, BRed R) {
     __shared__ double sh[32];
     const BWork w = W[bmap[blockIdx.x]];
     const BProb& P = PP[w.prob];
     const bool skip = which == 0 && bdone(P);
     const LevelArgs A = blevel(P, w.m);
-    const int o = ((int)blockIdx.x - w.b0) * OBLK + threadIdx.x;
+    const int o = ((int)blockIdx.x - w.b0) * OBLK + (threadIdx.x >> 1);
     const double* V = which ? P.xt : P.p;
     double* Y = which ? P.yt : P.Ap;
-    // pair-of-FP32 arithmetic, as the single-problem outer apply (k_oapply_df)
     DF dot{0.0f, 0.0f};
-    if (!skip && o < A.ncell / 8) octet_apply_df<float, float>(P.T, P.C, V, Y, A.off, A.ni, o, dot);
+    if (!skip && o < A.ncell / 8)
+        layer_apply_df(P.T, P.C, P.rem, P.flags, V, Y, A.off, A.ni, o, threadIdx.x & 1, 3u << (threadIdx.x & 30), dot);
     if (which == 0) bred_finish<2>(PP, w.prob, (int)blockIdx.x - P.ab0, P.nba, R, df_to_double(dot), 0.0, 0.0, sh);
 }
 

@@ -126,7 +126,7 @@ struct BatchRun {
             if (a.nw > 0) go(0, [&] { kb_oavg<<<a.nb, OBLK, 0, c.st>>>(bt->dP, bt->dW, I(a), which); });
         }
         go(0, [&] {
-            kb_oapply<<<bt->apply.nb, OBLK, 0, c.st>>>(bt->dP, bt->dW, I(bt->apply), which, red(OP_ALPHA));
+            kb_oapply<<<bt->apply.nb, OBLK2, 0, c.st>>>(bt->dP, bt->dW, I(bt->apply), which, red(OP_ALPHA));
         });
     }
     void half_a() {
@@ -263,6 +263,7 @@ int ocg_batch_create(ocg_hier* const* hs, int32_t n, void* stream, ocg_batch** o
         for (int p = 0; p < n; ++p) {
             ocg_hier* h = hs[p];
             if (!h) throw Status(OCG_EINVAL, "null hierarchy");
+            require_device(h);
             for (int q = 0; q < p; ++q)
                 if (hs[q] == h) throw Status(OCG_EINVAL, "a hierarchy appears twice in the batch");
             const ocg_mg_params& m = h->prm;
@@ -283,6 +284,7 @@ int ocg_batch_create(ocg_hier* const* hs, int32_t n, void* stream, ocg_batch** o
             b.B = (float*)h->B;
             b.x = h->x; b.r = h->r; b.p = h->p; b.Ap = h->Ap; b.bt = h->bt; b.xt = h->xt; b.yt = h->yt;
             b.flags = t->flags;
+            b.rem = h->rem32;
             b.leaf_cell = t->leaf_cell;
             b.ntree = (int)Ht.ntree;
             b.nleaf = (int)Ht.nleaf;
@@ -402,6 +404,7 @@ int ocg_pcg_solve_batched(ocg_batch* bt, const double* const* b, double* const* 
         if (!(sp->tol > 0) || sp->max_iter < 1) throw Status(OCG_EINVAL, "tol must be > 0 and max_iter >= 1");
         if (sp->precision != OCG_PREC_MIXED) throw Status(OCG_EINVAL, "batched solves run in mixed precision");
         if (sp->flags != 0) throw Status(OCG_EINVAL, "batched solves take no flags");
+        require_device(bt->hs[0]);
         cudaStream_t st = (cudaStream_t)stream;
         const int n = bt->n;
         for (int p = 0; p < n; ++p) {

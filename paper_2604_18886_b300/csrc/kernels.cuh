@@ -268,6 +268,24 @@ __device__ __forceinline__ DF df_norm(DF x) {
     const float s = x.hi + x.lo;
     return {s, x.lo - (s - x.hi)};
 }
+// s / n for a count 0 <= n <= 8 (the mean of n active cells; 0 for n = 0).  Scaling by
+// 1/n is exact for n = 1, 2, 4, 8; otherwise hi = s.hi (1/n) is within two ulps of the
+// quotient, so the remainder s.hi - n hi is exact in one FMA, and lo = (remainder + s.lo)/n
+// carries the rest to about 2^-47 of the mean.
+__device__ __forceinline__ DF df_div_count(DF s, int n) {
+    if (n == 0) return DF{0.0f, 0.0f};
+    if ((n & (n - 1)) == 0) {
+        const float ic = n == 8 ? 0.125f : (n == 4 ? 0.25f : (n == 2 ? 0.5f : 1.0f));
+        return DF{s.hi * ic, s.lo * ic};
+    }
+    const float ic = 1.0f / (float)n;
+    const float hi = s.hi * ic;
+    const float rem = fmaf(-hi, (float)n, s.hi);
+    const float lo = (rem + s.lo) * ic;
+    const float t = hi + lo;
+    return DF{t, lo - (t - hi)};
+}
+
 // binary64 -> (hi, lo): hi = sign, exponent and leading 23 fraction bits (truncated), lo =
 // the remaining 29 fraction bits rounded to 24; integer operations only.  |v| < 2^-126 is
 // flushed to 0, |v| >= 2^128 becomes an infinity or NaN in hi; lo is dropped when |v| <

@@ -214,6 +214,7 @@ struct ocg_octree {
     HostTree H;
     // device copies of the tables, uploaded by the first hierarchy set-up
     mutable bool on_device = false;
+    mutable int device = -1;   // CUDA device ordinal that holds the tables once uploaded
     mutable int32_t *nbr = nullptr, *oct_parent = nullptr, *child_oct = nullptr, *trec = nullptr,
                     *leaf_cell = nullptr;
     mutable uint8_t* flags = nullptr;
@@ -223,7 +224,15 @@ struct ocg_octree {
     mutable int8_t* fdepth = nullptr;
 
     void upload() const {
-        if (on_device) return;
+        int dev = 0;
+        ck(cudaGetDevice(&dev), "cudaGetDevice");
+        if (on_device) {
+            if (dev != device)
+                throw Status(OCG_EINVAL, "the octree's tables are on device " + std::to_string(device) +
+                                         ", the current device is " + std::to_string(dev));
+            return;
+        }
+        device = dev;
         nbr = dupload(H.nbr);
         oct_parent = dupload(H.oct_parent);
         child_oct = dupload(H.child_oct);
@@ -284,6 +293,7 @@ struct GraphSolve {
 
 struct ocg_hier {
     const ocg_octree* t = nullptr;
+    int device = -1;   // CUDA device ordinal current at set-up; every later call must run there
     ocg_mg_params prm{};
     int bc[6] = {0, 0, 0, 0, 0, 0};
     bool ns_auto = false;
@@ -294,6 +304,7 @@ struct ocg_hier {
     float* tw32 = nullptr;
     __nv_bfloat16* c16[4] = {nullptr, nullptr, nullptr, nullptr};   // [0] unused: see d16
     float* d16 = nullptr;         // conservative FP32 diagonal of the BF16 set
+    float* rem32 = nullptr;       // FP32 sets: diagonal remainder of the tree cells (k_remainder)
     // work space, allocated once at set-up at the widest type so a captured graph keeps
     // valid pointers: x, r, p, Ap, bt (b in cell order), xt, yt over the tree cells;
     // U, B over all cells
@@ -340,6 +351,7 @@ struct ocg_hier {
         if (cap) cudaStreamDestroy(cap);
         for (int i = 0; i < 4; ++i) { dfree(c64[i]); dfree(c32[i]); dfree(c16[i]); }
         dfree(d16);
+        dfree(rem32);
         dfree(tw64); dfree(tw32); dfree(S); dfree(part); dfree(cnt); dfree(tail_sched); dfree(tail_sched2);
         if (hS) cudaFreeHost(hS);
         for (double* v : {x, r, p, Ap, bt, xt, yt, U, B}) dfree(v);
@@ -788,15 +800,26 @@ void autotune_sweeps(ocg_hier* h) {
 }
 
 // ------------------------------------------------------------------ composite operator
+// The device a hierarchy was set up on must be current for every call on it: its tables,
+// coefficients and work vectors live in that device's memory.
+void require_device(const ocg_hier* h) {
+    int dev = 0;
+    ck(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev != h->device)
+        throw Status(OCG_EINVAL, "the hierarchy lives on device " + std::to_string(h->device) +
+                                 ", the current device is " + std::to_string(dev));
+}
+
 int sm_count() {
-    static int n = 0;
-    if (n == 0) {
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-            n <= 0)
-            n = 148;
+    static int n[256] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) dev = 0;
+    if (n[dev] == 0) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 148;
+        n[dev] = v;
     }
-    return n;
+    return n[dev];
 }
 
 OMultiLevel tree_levels(const HostTree& H) {
@@ -845,9 +868,12 @@ void apply_outer(ocg_hier* h, Coefs<TC, TW> C, TO* P, TO* Y, int op, Ctx& c) {
     const int nb = std::min(ML.boff[ML.n], 16 * sm_count());
     const Red R = make_red(h, nb, op);
     launch(c, OCG_PROBE_APPLY, 0, H.ntree, [&] {
-        if constexpr (std::is_same<TO, double>::value && std::is_same<TC, float>::value)
-            launch_k(k_oapply_df<TC, TW>, nb, OBLK, 0, c.st, ML, t->tables(), C, P, Y, R);
-        else
+        if constexpr (std::is_same<TO, double>::value && std::is_same<TC, float>::value) {
+            const int nb2 = std::min(ML.boff[ML.n], 8 * sm_count());
+            const Red R2 = make_red(h, nb2, op);
+            launch_k(k_oapply_df2, nb2, OBLK2, 0, c.st, ML, t->tables(), C, (const float*)h->rem32,
+                     (const uint8_t*)t->flags, P, Y, R2);
+        } else
             launch_k(k_oapply<TO, TC, TW>, nb, OBLK, 0, c.st, ML, t->tables(), C, P, Y, R);
     });
     ck_launch("apply");
@@ -1518,6 +1544,13 @@ void build_coefficients(ocg_hier* h, const float* beta, cudaStream_t st) {
         }
         if (!h->tw32) h->tw32 = dalloc<float>(ntw);
         launch_k(k_convert<float>, nblk(ntw), BLK, 0, st, h->tw64, h->tw32, ntw);
+        // the outer apply's diagonal remainder, from the FP64 diagonal and the stored FP32 faces
+        if (!h->rem32) h->rem32 = dalloc<float>(H.ntree);
+        for (int m = 0; m <= H.D; ++m) {
+            const LevelArgs A = t->largs(m);
+            launch_k(k_remainder, nblk(A.ncell / 8, OBLK), OBLK, 0, st, A, t->tables(), (const double*)h->c64[0],
+                     h->C32(), h->rem32);
+        }
         if (h->prm.bf16_coarse) {
             if (!h->d16) h->d16 = dalloc<float>(H.ncell);
             for (int m = H.mc; m <= H.D; ++m) {
@@ -1565,6 +1598,7 @@ int ocg_setup_hierarchy(const ocg_octree* t, const float* beta, const int32_t bc
         t->upload();
         std::unique_ptr<ocg_hier> h(new ocg_hier());
         h->t = t;
+        h->device = t->device;
         h->prm = *prm;
         bool ns = true;
         for (int q = 0; q < 6; ++q) {
@@ -1599,6 +1633,7 @@ void ocg_hier_destroy(ocg_hier* h) { delete h; }
 int ocg_hier_update_beta(ocg_hier* h, const float* beta, void* stream) {
     return guard([&] {
         if (!h || !beta) throw Status(OCG_EINVAL, "null argument");
+        require_device(h);
         cudaStream_t st = (cudaStream_t)stream;
         ck(cudaStreamSynchronize(st), "sync");
         build_coefficients(h, beta, st);
@@ -1608,6 +1643,7 @@ int ocg_hier_update_beta(ocg_hier* h, const float* beta, void* stream) {
 int ocg_hier_export_coefs(const ocg_hier* h, int32_t m, double* c, double* cx, double* cy, double* cz) {
     return guard([&] {
         if (!h) throw Status(OCG_EINVAL, "null hierarchy");
+        require_device(h);
         const HostTree& H = h->t->H;
         if (m < H.mc || m > H.D) throw Status(OCG_EINVAL, "level out of range");
         const LevelMeta& l = H.L(m);
@@ -1647,6 +1683,7 @@ int ocg_hier_tuning(const ocg_hier* h, int32_t m, int32_t* form, double* us_octe
 int ocg_apply_A(ocg_hier* h, int32_t dtype, const void* x, void* y, int32_t transpose, void* stream) {
     return guard([&] {
         if (!h || !x || !y) throw Status(OCG_EINVAL, "null argument");
+        require_device(h);
         if (transpose != 0 && transpose != 1) throw Status(OCG_EINVAL, "transpose must be 0 or 1");
         if (transpose) ensure_adjoint(h);
         cudaStream_t st = (cudaStream_t)stream;
@@ -1686,6 +1723,7 @@ int ocg_apply_A(ocg_hier* h, int32_t dtype, const void* x, void* y, int32_t tran
 int ocg_vcycle(ocg_hier* h, int32_t dtype, const void* r, void* z, void* stream) {
     return guard([&] {
         if (!h || !r || !z) throw Status(OCG_EINVAL, "null argument");
+        require_device(h);
         cudaStream_t st = (cudaStream_t)stream;
         const ocg_octree* t = h->t;
         const HostTree& H = t->H;
@@ -1721,6 +1759,7 @@ int ocg_vcycle(ocg_hier* h, int32_t dtype, const void* r, void* z, void* stream)
 int ocg_vcycle_transpose(ocg_hier* h, int32_t dtype, const void* z, void* r, void* stream) {
     return guard([&] {
         if (!h || !z || !r) throw Status(OCG_EINVAL, "null argument");
+        require_device(h);
         cudaStream_t st = (cudaStream_t)stream;
         ensure_cycle_T(h);
         const ocg_octree* t = h->t;
@@ -1757,6 +1796,7 @@ int ocg_vcycle_transpose(ocg_hier* h, int32_t dtype, const void* z, void* r, voi
 int ocg_face_grad(ocg_hier* h, const double* p, const double* lambda, double* dbeta, void* stream) {
     return guard([&] {
         if (!h || !p || !lambda || !dbeta) throw Status(OCG_EINVAL, "null argument");
+        require_device(h);
         const ocg_octree* t = h->t;
         const HostTree& H = t->H;
         if (H.nface == 0) return;
@@ -1798,6 +1838,7 @@ int ocg_pcg_solve(ocg_hier* h, const double* b, double* x, const ocg_solve_param
     int status = OCG_OK;
     int g = guard([&] {
         if (!h || !b || !x || !sp || !stats) throw Status(OCG_EINVAL, "null argument");
+        require_device(h);
         if (!(sp->tol > 0) || sp->max_iter < 1) throw Status(OCG_EINVAL, "tol must be > 0 and max_iter >= 1");
         if (sp->flags & ~(OCG_SOLVE_EAGER | OCG_SOLVE_TRANSPOSE | OCG_SOLVE_UNROLLED | OCG_SOLVE_BICGSTAB | OCG_SOLVE_WARM))
             throw Status(OCG_EINVAL, "unknown solve flags");
@@ -1835,6 +1876,7 @@ int ocg_pcg_solve(ocg_hier* h, const double* b, double* x, const ocg_solve_param
 int ocg_probe_set(ocg_hier* h, int32_t kind, int32_t level) {
     return guard([&] {
         if (!h) throw Status(OCG_EINVAL, "null hierarchy");
+        require_device(h);
         if (kind < OCG_PROBE_OFF || kind > OCG_PROBE_TAIL) throw Status(OCG_EINVAL, "probe kind");
         h->probe.kind = kind;
         h->probe.level = level;
@@ -1845,6 +1887,7 @@ int ocg_probe_set(ocg_hier* h, int32_t kind, int32_t level) {
 int ocg_probe_read(ocg_hier* h, void* stream, int64_t* launches, double* total_ms, int64_t* cells) {
     return guard([&] {
         if (!h || !launches || !total_ms || !cells) throw Status(OCG_EINVAL, "null argument");
+        require_device(h);
         ck(cudaStreamSynchronize((cudaStream_t)stream), "stream sync");
         double tot = 0.0;
         for (int64_t q = 0; q + 1 < h->probe.used; q += 2) {
@@ -1906,6 +1949,7 @@ float* noalloc_scratch() {
 extern "C" int ocg_apply_A_f32_noalloc(ocg_hier* h, const float* x, float* y, void* stream) {
     return guard([&] {
         if (!h || !x || !y) throw Status(OCG_EINVAL, "null argument");
+        require_device(h);
         const ocg_octree* t = h->t;
         const HostTree& H = t->H;
         if (!t->on_device) throw Status(OCG_ESTATE, "octree tables are not on the device");

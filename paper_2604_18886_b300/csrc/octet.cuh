@@ -938,7 +938,7 @@ __global__ void __launch_bounds__(OBLK) k_diag_conservative(LevelArgs A, Tables 
     for (int s = 0; s < 8; ++s) dout[c8 + s] = C64.d[c8 + s] == 0.0 ? 0.0f : (float)rem[s] - sl[s];
 }
 
-// ------------------------------------------------------------ double-float outer apply
+// ------------------------------------------------------------ outer apply, two lanes per octet
 // The mixed-precision outer operator (FP64 vectors, FP32 coefficients) without the FP64
 // pipe, which runs at 1/64 of the FP32 rate on this GPU: every binary64 value is split
 // exactly into a pair of binary32 (hi, lo) with integer operations (48 significant bits
@@ -946,130 +946,233 @@ __global__ void __launch_bounds__(OBLK) k_diag_conservative(LevelArgs A, Tables 
 // (TwoSum, TwoProd by FMA; T. J. Dekker, "A floating-point technique for extending the
 // available precision", Numer. Math. 18, 1971), and only the final hi + lo of each output
 // is one binary64 addition.  The flux form
-//   (A u)_s = (d_s - sum_f w_f) u_s + sum_f w_f (u_s - u_f)   (+ T ghosts (w_f/2)(ubar - u_K))
+//   (A u)_s = rem_s u_s + sum_f w_f (u_s - u_f)   (+ T ghosts (w_f/2)(ubar - u_K))
 // computes every face difference before scaling it, so the rounding error is relative to
-// the fluxes, not to d_s u_s; the remainder d_s - sum_f w_f (non-zero at walls and by the
-// FP32 rounding of the stored coefficients) is summed exactly.
-// One octet of the pair-of-FP32 outer apply: Y for its 8 cells (0 on inner cells), and
-// (p, Ap) over its leaves added to dot.
-template <class TC, class TW>
-__device__ __forceinline__ void octet_apply_df(const Tables& T, const Coefs<TC, TW>& C, const double* __restrict__ P,
-                                               double* __restrict__ Y, int off, int ni, int o, DF& dot) {
-    const int c8 = off + 8 * o, og = c8 >> 3;
-    int leafbits = 0;
+// the fluxes, not to d_s u_s.
+// The remainder of a tree cell's diagonal after its stencil faces: rem = d + the sum of
+// the stored FP32 coefficients (each -w_f) of the faces that enter the cell's stencil
+// (internal faces, both neighbour faces, T sub-faces; a wall face enters only here),
+// evaluated in FP64 from the FP64 diagonal and rounded once to FP32: 0 for an interior
+// cell whose face weights are exact in FP32, the wall weight at a Dirichlet wall, a few
+// ulps of w_f beside a rounded T-record weight, 0 for an inactive cell.  The flux form
+// sum_f w_f (u_s - u_f) + rem u_s of the outer apply then carries the FP64 diagonal.
+__global__ void __launch_bounds__(OBLK) k_remainder(LevelArgs A, Tables T, const double* __restrict__ d64,
+                                                    Coefs<float, float> C, float* __restrict__ rem) {
+    pdl_enter();
+    const int o = blockIdx.x * OBLK + threadIdx.x;
+    if (o >= A.ncell / 8) return;
+    const int c8 = A.off + 8 * o, og = c8 >> 3;
+    double r[8];
 #pragma unroll
-    for (int s = 0; s < 8; ++s) leafbits |= (__ldg(T.child_oct + c8 + s) < 0 ? 1 : 0) << s;
-    if (!leafbits) {
-        // no leaf in the octet: the composite operator has no row here
-        reinterpret_cast<double4*>(Y + c8)[0] = make_double4(0.0, 0.0, 0.0, 0.0);
-        reinterpret_cast<double4*>(Y + c8)[1] = make_double4(0.0, 0.0, 0.0, 0.0);
-        return;
-    }
+    for (int s = 0; s < 8; ++s) r[s] = d64[c8 + s];
     int nb[6];
-    octet_neighbours(T, ni, o, og, nb);
-    DF u[8];
-    float d[8], cm[3][8];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const double2 v = reinterpret_cast<const double2*>(P + c8)[q];
-        u[2 * q] = df_split(v.x);
-        u[2 * q + 1] = df_split(v.y);
-    }
-    ldc8(C.d + c8, d);
-    ldc8(C.cx + c8, cm[0]);
-    ldc8(C.cy + c8, cm[1]);
-    ldc8(C.cz + c8, cm[2]);
-    // mean of the active cells (the T ghost's ubar)
-    DF us{0.0f, 0.0f};
-    int n = 0;
-#pragma unroll
-    for (int s = 0; s < 8; ++s)
-        if (d[s] != 0.0f) { df_acc(us, u[s]); ++n; }
-    const float ic = inv_count<float>(n);
-    const DF ubar{us.hi * ic, us.lo * ic};   // exact scaling for n = 1, 2, 4, 8
-    DF acc[8], dr[8];
-#pragma unroll
-    for (int s = 0; s < 8; ++s) { acc[s] = DF{0.0f, 0.0f}; dr[s] = DF{d[s], 0.0f}; }
+    octet_neighbours(T, A.ni, o, og, nb);
+    const float* cm[3] = {C.cx, C.cy, C.cz};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const int bit = 1 << a;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int s = clear_slot(a, q), t = s | bit;
-            const float c = cm[a][t];
-            const DF fl = df_scale(df_diff(u[s], u[t]), -c);
-            df_acc(acc[s], fl);
-            df_acc(acc[t], DF{-fl.hi, -fl.lo});
-            df_acc_f(dr[s], c);
-            df_acc_f(dr[t], c);
+            const double c = cm[a][c8 + t];
+            r[s] += c;
+            r[t] += c;
         }
+        if (nb[2 * a] != -1) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) r[clear_slot(a, q)] += (double)cm[a][c8 + clear_slot(a, q)];
+        }
+        const int w = nb[2 * a + 1];
+        if (w >= 0) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) r[clear_slot(a, q) | bit] += (double)cm[a][A.off + 8 * w + clear_slot(a, q)];
+        } else if (w <= -2) {
+            const int t = T.trec[og];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) r[clear_slot(a, q) | bit] += (double)C.tw[((2 * a + 1) * 4 + q) * T.nt + t];
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < 8; ++s) rem[c8 + s] = (float)r[s];
+}
+
+constexpr int OBLK2 = 128;   // threads per block of the two-lane apply: 64 octets
+
+__device__ __forceinline__ float4 ldg4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ float f4at(const float4& v, int q) {
+    return q == 0 ? v.x : (q == 1 ? v.y : (q == 2 ? v.z : v.w));
+}
+__device__ __forceinline__ DF shfl_df(unsigned m, DF v) {
+    return DF{__shfl_xor_sync(m, v.hi, 1), __shfl_xor_sync(m, v.lo, 1)};
+}
+
+// One z layer (4 cells, slots 4z..4z+3) of the pair-of-FP32 outer apply: the two lanes
+// of a pair (mask pm) hold the two layers of one octet and trade their values for the
+// faces between the layers.  Per face: the exact difference of the two values by TwoSum,
+// its product with the FP32 coefficient by FMA, pair accumulation; the diagonal enters as
+// the remainder from k_remainder, the leaf flags come from the 1-byte cell flags.
+__device__ __forceinline__ void layer_apply_df(const Tables& T, const Coefs<float, float>& C,
+                                               const float* __restrict__ rem, const uint8_t* __restrict__ flags,
+                                               const double* __restrict__ P, double* __restrict__ Y, int off,
+                                               int ni, int o, int z, unsigned pm, DF& dot) {
+    const int c8 = off + 8 * o, og = c8 >> 3, cz0 = c8 + 4 * z;
+    const uint32_t fl = __ldg(reinterpret_cast<const uint32_t*>(flags + cz0));
+    const int leafm = (int)((fl & 1u) | ((fl >> 7) & 2u) | ((fl >> 14) & 4u) | ((fl >> 21) & 8u));
+    const int leafo = __shfl_xor_sync(pm, leafm, 1);
+    if ((leafm | leafo) == 0) {
+        // no leaf in the octet: the composite operator has no row here
+        reinterpret_cast<double4*>(Y + cz0)[0] = make_double4(0.0, 0.0, 0.0, 0.0);
+        return;
+    }
+    int nb[6];
+    octet_neighbours(T, ni, o, og, nb);
+    DF u[4], uo[4], acc[4];
+    {
+        const double2 v0 = reinterpret_cast<const double2*>(P + cz0)[0];
+        const double2 v1 = reinterpret_cast<const double2*>(P + cz0)[1];
+        u[0] = df_split(v0.x); u[1] = df_split(v0.y); u[2] = df_split(v1.x); u[3] = df_split(v1.y);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) { uo[q] = shfl_df(pm, u[q]); acc[q] = DF{0.0f, 0.0f}; }
+    const float4 cx = ldg4(C.cx + cz0), cy = ldg4(C.cy + cz0), czv = ldg4(C.cz + cz0);
+    const float4 rm = ldg4(rem + cz0);
+    // the mean of the octet's active cells, for T ghosts (pair-uniform: both lanes share nb)
+    DF ubar{0.0f, 0.0f};
+    if (nb[0] <= -2 || nb[1] <= -2 || nb[2] <= -2 || nb[3] <= -2 || nb[4] <= -2 || nb[5] <= -2) {
+        const float4 d = ldg4(C.d + cz0);
+        DF sm{0.0f, 0.0f};
+        int n = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (f4at(d, q) != 0.0f) { df_acc(sm, u[q]); ++n; }
+        df_acc(sm, shfl_df(pm, sm));
+        n += __shfl_xor_sync(pm, n, 1);
+        ubar = df_div_count(sm, n);
+    }
+    // faces inside the layer: x between q and q|1, y between q and q|2 (coefficient kept
+    // by the + cell)
+#pragma unroll
+    for (int q = 0; q < 4; q += 2) {
+        const DF f = df_scale(df_diff(u[q], u[q + 1]), -f4at(cx, q + 1));
+        df_acc(acc[q], f);
+        df_acc(acc[q + 1], DF{-f.hi, -f.lo});
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const DF f = df_scale(df_diff(u[q], u[q + 2]), -f4at(cy, q + 2));
+        df_acc(acc[q], f);
+        df_acc(acc[q + 2], DF{-f.hi, -f.lo});
+    }
+    // faces between the layers: the coefficient is the upper layer's c_z-
+    {
+        float czu[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float mine = f4at(czv, q), other = __shfl_xor_sync(pm, mine, 1);
+            czu[q] = z ? mine : other;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) df_acc(acc[q], df_scale(df_diff(u[q], uo[q]), -czu[q]));
+    }
+    // x and y faces of the octet: the - face meets the neighbour's + side, whose cells are
+    // those with the bit set; the + face meets the neighbour's - side, which keeps the
+    // coefficients
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        const int bit = 1 << a;
+        const float4& cown = a == 0 ? cx : cy;
+        const float* cg = a == 0 ? C.cx : C.cy;
         const int v = nb[2 * a];
         if (v >= 0) {
-            const double* pn = P + off + 8 * v;
+            const double* pn = P + off + 8 * v + 4 * z;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int s = clear_slot(a, q);
-                df_acc(acc[s], df_scale(df_diff(u[s], df_split(pn[s | bit])), -cm[a][s]));
-                df_acc_f(dr[s], cm[a][s]);
+            for (int k = 0; k < 2; ++k) {
+                const int q = a == 0 ? 2 * k : k;            // cells with the bit clear
+                df_acc(acc[q], df_scale(df_diff(u[q], df_split(pn[q | bit])), -f4at(cown, q)));
             }
         } else if (v <= -2) {
-            const DF gk = df_diff(df_split(P[-2 - v]), ubar);   // u_K - ubar
+            const DF gk = df_diff(df_split(P[-2 - v]), ubar);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int s = clear_slot(a, q);
-                df_acc(acc[s], df_scale(gk, 0.5f * cm[a][s]));
-                df_acc_f(dr[s], cm[a][s]);
+            for (int k = 0; k < 2; ++k) {
+                const int q = a == 0 ? 2 * k : k;
+                df_acc(acc[q], df_scale(gk, 0.5f * f4at(cown, q)));
             }
         }
         const int w = nb[2 * a + 1];
         if (w >= 0) {
-            const double* pn = P + off + 8 * w;
-            const TC* cc = (a == 0 ? C.cx : (a == 1 ? C.cy : C.cz)) + off + 8 * w;
+            const int n8 = off + 8 * w + 4 * z;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int s = clear_slot(a, q) | bit;
-                const float c = (float)tov(__ldg(cc + clear_slot(a, q)));
-                df_acc(acc[s], df_scale(df_diff(u[s], df_split(pn[clear_slot(a, q)])), -c));
-                df_acc_f(dr[s], c);
+            for (int k = 0; k < 2; ++k) {
+                const int q = a == 0 ? 2 * k + 1 : k + 2;    // cells with the bit set
+                const int qn = q & ~bit;
+                df_acc(acc[q], df_scale(df_diff(u[q], df_split(P[n8 + qn])), -__ldg(cg + n8 + qn)));
             }
         } else if (w <= -2) {
             const DF gk = df_diff(df_split(P[-2 - w]), ubar);
             const int t = __ldg(T.trec + og);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int s = clear_slot(a, q) | bit;
-                const float c = (float)tov(__ldg(C.tw + ((2 * a + 1) * 4 + q) * T.nt + t));
-                df_acc(acc[s], df_scale(gk, 0.5f * c));
-                df_acc_f(dr[s], c);
+            for (int k = 0; k < 2; ++k) {
+                const int q = a == 0 ? 2 * k + 1 : k + 2;
+                const int sub = sub_index(a, 4 * z + q);
+                df_acc(acc[q], df_scale(gk, 0.5f * __ldg(C.tw + ((2 * a + 1) * 4 + sub) * T.nt + t)));
             }
         }
     }
-    double y[8];
+    // z face of this layer: the - face for the lower layer (the neighbour's upper layer,
+    // own coefficients), the + face for the upper one (the neighbour's lower layer and its
+    // coefficients)
+    {
+        const int v = z ? nb[5] : nb[4];
+        if (v >= 0) {
+            const int n8 = off + 8 * v;
+            const double2 w0 = reinterpret_cast<const double2*>(P + n8 + 4 * (1 - z))[0];
+            const double2 w1 = reinterpret_cast<const double2*>(P + n8 + 4 * (1 - z))[1];
+            const float4 cc = z ? ldg4(C.cz + n8) : czv;
+            df_acc(acc[0], df_scale(df_diff(u[0], df_split(w0.x)), -cc.x));
+            df_acc(acc[1], df_scale(df_diff(u[1], df_split(w0.y)), -cc.y));
+            df_acc(acc[2], df_scale(df_diff(u[2], df_split(w1.x)), -cc.z));
+            df_acc(acc[3], df_scale(df_diff(u[3], df_split(w1.y)), -cc.w));
+        } else if (v <= -2) {
+            const DF gk = df_diff(df_split(P[-2 - v]), ubar);
+            const int t = z ? __ldg(T.trec + og) : 0;
 #pragma unroll
-    for (int s = 0; s < 8; ++s) {
-        const bool leaf = (leafbits >> s) & 1;
-        DF au = acc[s];
-        df_acc(au, df_mul(df_norm(dr[s]), u[s]));
-        au = df_norm(au);
-        y[s] = leaf ? df_to_double(au) : 0.0;
-        if (leaf) df_acc(dot, df_mul(u[s], au));
+            for (int q = 0; q < 4; ++q) {
+                const float c = z ? __ldg(C.tw + (5 * 4 + q) * T.nt + t) : f4at(czv, q);
+                df_acc(acc[q], df_scale(gk, 0.5f * c));
+            }
+        }
     }
-    reinterpret_cast<double4*>(Y + c8)[0] = make_double4(y[0], y[1], y[2], y[3]);
-    reinterpret_cast<double4*>(Y + c8)[1] = make_double4(y[4], y[5], y[6], y[7]);
+    double y[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const bool leaf = (leafm >> q) & 1;
+        DF au = acc[q];
+        df_acc(au, df_scale(u[q], f4at(rm, q)));
+        au = df_norm(au);
+        y[q] = leaf ? df_to_double(au) : 0.0;
+        if (leaf) df_acc(dot, df_mul(u[q], au));
+    }
+    reinterpret_cast<double4*>(Y + cz0)[0] = make_double4(y[0], y[1], y[2], y[3]);
 }
 
-template <class TC, class TW>
-__global__ void __launch_bounds__(OBLK) k_oapply_df(OMultiLevel ML, Tables T, Coefs<TC, TW> C,
-                                                    const double* __restrict__ P, double* __restrict__ Y, Red R) {
+// Y = A P over all tree levels (FP64 vectors, FP32 coefficients), two lanes per octet;
+// (P, A P) over the leaves reduced into R.  Blocks of OBLK2 threads take the octet blocks
+// (64 octets) of OMultiLevel and stride over them.
+__global__ void __launch_bounds__(OBLK2, 8) k_oapply_df2(OMultiLevel ML, Tables T, Coefs<float, float> C,
+                                                         const float* __restrict__ rem,
+                                                         const uint8_t* __restrict__ flags,
+                                                         const double* __restrict__ P, double* __restrict__ Y, Red R) {
     pdl_enter();
     __shared__ double sh[32];
     DF dot{0.0f, 0.0f};
     const int nvb = ML.boff[ML.n];
+    const int z = threadIdx.x & 1;
+    const unsigned pm = 3u << (threadIdx.x & 30);
     int l = 0;
     for (int vb = blockIdx.x; vb < nvb; vb += gridDim.x) {
         while (l + 1 < ML.n && vb >= ML.boff[l + 1]) ++l;
-        const int o = (vb - ML.boff[l]) * OBLK + threadIdx.x;
-        if (o < ML.noct[l]) octet_apply_df<TC, TW>(T, C, P, Y, ML.off[l], ML.ni[l], o, dot);
+        const int o = (vb - ML.boff[l]) * OBLK + (threadIdx.x >> 1);
+        if (o < ML.noct[l]) layer_apply_df(T, C, rem, flags, P, Y, ML.off[l], ML.ni[l], o, z, pm, dot);
     }
     if (R.op != OP_NONE) red_finish(R, blockIdx.x, df_to_double(dot), 0.0, sh);
 }
@@ -1347,27 +1450,37 @@ __global__ void __launch_bounds__(OBLK) kt_fsweep(LevelArgs A, Tables T, Coefs<T
             Y[s] += c * v[w];
             Y[w] += c * v[s];
         }
+        // neighbouring octets' faces read as layers (ld_layer: a z layer in one vector
+        // load, a y layer in two), both colours fetched, the colour's cells used
         const int vn = nb[2 * a];
         if (vn >= 0) {
             const int n8 = off + 8 * vn;
+            TV nu[4];
+            typename DiagOf<TC>::type ndr[4];
+            ld_layer(Uin + n8, a, 1, true, nu);
+            ld_layer(C.d + n8, a, 1, true, ndr);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int s = clear_slot(a, q), ns = s | bit;
                 if ((__popc(ns) & 1) != colour) continue;   // neighbour cell not of the colour
-                const TV dn = TV(tov(__ldg(C.d + n8 + ns)));
-                Y[s] += cm[a][s] * colour_v(Uin[n8 + ns], dn, true);
+                Y[s] += cm[a][s] * colour_v(nu[q], TV(tov(ndr[q])), true);
             }
         }
         const int wn = nb[2 * a + 1];
         if (wn >= 0) {
             const int n8 = off + 8 * wn;
             const TC* cc = a == 0 ? C.cx : (a == 1 ? C.cy : C.cz);
+            TV nu[4];
+            typename DiagOf<TC>::type ndr[4];
+            TC ncr[4];
+            ld_layer(Uin + n8, a, 0, true, nu);
+            ld_layer(C.d + n8, a, 0, true, ndr);
+            ld_layer(cc + n8, a, 0, true, ncr);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int s = clear_slot(a, q);
                 if ((__popc(s) & 1) != colour) continue;
-                const TV dn = TV(tov(__ldg(C.d + n8 + s)));
-                Y[s | bit] += TV(tov(__ldg(cc + n8 + s))) * colour_v(Uin[n8 + s], dn, true);
+                Y[s | bit] += TV(tov(ncr[q])) * colour_v(nu[q], TV(tov(ndr[q])), true);
             }
         }
     }

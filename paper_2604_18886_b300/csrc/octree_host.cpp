@@ -154,7 +154,13 @@ float face_beta_geometric(const ocg_octree_desc& d, int m, int axis, int64_t i, 
 
 // Refinement predicate (documented in ocg.h); no FMA contraction in this file.
 static bool refine_pred(const ocg_octree_desc& d, int depth, int64_t i, int64_t j, int64_t k) {
-    const double nd = (double)((int64_t)d.n0 << depth);
+    // tiles of 2^t cells per axis decide together, as the depth-(depth - t) cell that covers
+    // them: its centre and size (nd cells per axis; exact, n0 is a multiple of 2^t)
+    const int t = d.tile_log2;
+    i >>= t;
+    j >>= t;
+    k >>= t;
+    const double nd = (double)(((int64_t)d.n0 << depth) >> t);
     const double x = ((double)i + 0.5) / nd;
     const double y = ((double)j + 0.5) / nd;
     const double z = ((double)k + 0.5) / nd;
@@ -337,8 +343,9 @@ static void build_impl(const ocg_octree_desc& desc, HostTree& T, const HostTree*
 void build_host_tree(const ocg_octree_desc& desc, HostTree& T) { build_impl(desc, T, nullptr, nullptr); }
 
 void rebuild_host_tree(const HostTree& prev, const ocg_octree_desc& desc, const double box[6], HostTree& T) {
-    if (desc.n0 != prev.desc.n0 || desc.max_depth != prev.desc.max_depth || desc.refine != prev.desc.refine)
-        throw std::runtime_error("rebuild: n0, max_depth and refine must equal the previous octree's");
+    if (desc.n0 != prev.desc.n0 || desc.max_depth != prev.desc.max_depth || desc.refine != prev.desc.refine ||
+        desc.tile_log2 != prev.desc.tile_log2)
+        throw std::runtime_error("rebuild: n0, max_depth, refine and tile_log2 must equal the previous octree's");
     for (int a = 0; a < 3; ++a)
         if (!std::isfinite(box[a]) || !std::isfinite(box[a + 3]) || box[a] > box[a + 3])
             throw std::runtime_error("rebuild: the box must be finite with lo <= hi on each axis");
@@ -369,6 +376,8 @@ static void build_impl(const ocg_octree_desc& desc, HostTree& T, const HostTree*
             if (!(amax < 1048576.0)) throw std::runtime_error("sine wave argument out of range (|a| < 2^20)");
         }
     }
+    if (desc.tile_log2 < 0 || desc.tile_log2 > 4 || desc.n0 % (1 << desc.tile_log2) != 0)
+        throw std::runtime_error("tile_log2 must be in 0..4 with n0 a multiple of 2^tile_log2");
     if (desc.n_spheres < 0 || desc.n_spheres > 4 || desc.n_boxes < 0 || desc.n_boxes > 4)
         throw std::runtime_error("too many primitives");
     if (desc.refine == OCG_REFINE_BALL_CENTRE && desc.n_spheres < 1)
@@ -399,6 +408,10 @@ static void build_impl(const ocg_octree_desc& desc, HostTree& T, const HostTree*
             for (int a = 0; a < 3; ++a) {
                 lo[a] = (int64_t)std::floor(std::max(-1.0, std::min(2.0, box[a])) * (double)nd) - 1;
                 hi[a] = (int64_t)std::floor(std::max(-1.0, std::min(2.0, box[a + 3])) * (double)nd) + 1;
+                // whole tiles: a cell's flag is its tile's
+                const int tl = desc.tile_log2;
+                lo[a] = (lo[a] >> tl) << tl;
+                hi[a] = (((hi[a] >> tl) + 1) << tl) - 1;
             }
         const int64_t np = nd / 2;
 #pragma omp parallel for schedule(static)

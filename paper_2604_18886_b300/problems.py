@@ -54,6 +54,8 @@ class OctreeDesc:
     refine == REFINE_STAR_BAND: refined iff |phi(centre)| < band + L (sqrt(3)/2) h_d with
         phi = r - (r0 + a cos(k theta) cos(k phi)) about spheres[0] = (c, r0) and
         spheres[1] = (a, k, L, 0) (the star surface of Sec. 4.1).
+    tile_log2 = t > 0: every aligned tile of 2^t cells per axis takes one decision, the
+        predicate of the depth-(d - t) cell covering it (Sec. 4.1 refines 8^3 tiles, t = 3).
     """
 
     n0: int
@@ -63,6 +65,7 @@ class OctreeDesc:
     spheres: list = field(default_factory=list)   # (cx, cy, cz, r)
     boxes: list = field(default_factory=list)     # (lox, loy, loz, hix, hiy, hiz)
     sines: list = field(default_factory=list)     # (kappa, dx, dy, dz, theta)
+    tile_log2: int = 0    # the predicate decides per aligned tile of 2^tile_log2 cells per axis
 
 
 @dataclass

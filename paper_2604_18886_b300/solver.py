@@ -22,6 +22,7 @@ def _desc(d: P.OctreeDesc) -> L.OctreeDesc:
     out.max_depth = d.max_depth
     out.refine = d.refine
     out.band = d.band
+    out.tile_log2 = d.tile_log2
     if len(d.spheres) > 4 or len(d.boxes) > 4 or len(d.sines) > 8:
         raise ValueError("at most 4 spheres, 4 boxes and 8 sine waves")
     out.n_sines = len(d.sines)
@@ -91,6 +92,12 @@ class Octree:
                                                  L.ptr(a["j"]), L.ptr(a["k"])))
         return {k: v.astype(np.int64) for k, v in a.items()}
 
+    def leaf_depths(self):
+        """Depth of every leaf in canonical order (int32), without the coordinates."""
+        d = np.empty(self.n_leaves, np.int32)
+        L.check(L.lib().ocg_octree_export_leaves(self._h, L.ptr(d), None, None, None))
+        return d
+
     def neighbours(self):
         kind = np.empty((self.n_leaves, 6), np.int8)
         rank = np.empty((self.n_leaves, 6), np.int64)
@@ -121,6 +128,12 @@ class Octree:
         a["minus"] = mi
         a["plus"] = pl
         return a
+
+    def level_size(self, m):
+        """Number of cells of multigrid level m."""
+        n = C.c_int64()
+        L.check(L.lib().ocg_octree_export_level(self._h, m, C.byref(n), None, None, None, None))
+        return int(n.value)
 
     def level(self, m):
         n = C.c_int64()

@@ -122,6 +122,36 @@ def test_mixed_outer_apply_is_fp64_accurate(name):
             np.abs(y - ref).max()
 
 
+def test_mixed_outer_apply_with_partly_active_octets():
+    # the static tank with a staircase sphere (face fractions rounded to 0 or 1, so every
+    # stored coefficient is a multiple of h and exact in FP32): octets beside T faces have
+    # 1, 2, 4, 5, 6 or 7 active cells, whose ghost mean divides by a count that is not a
+    # power of two; the pair-of-FP32 apply must still match the FP64 oracle to FP64
+    # rounding
+    p = P.tank("sphere", 16, True)
+    t = O.Octree(p.desc)
+    f = t.faces()
+    beta = (P.face_beta(p, f) > 0.5).astype(np.float32)
+    H = OP.Hierarchy(t, beta, p.bc)
+    counts = set()
+    for m in range(1, t.D + 1):
+        L, Pl = H.levels[m], H.levels[m - 1]
+        for par in np.unique(L.parent[np.nonzero((L.tK >= 0).any(axis=1))[0]]):
+            ch = Pl.children[par]
+            counts.add(int(L.active[ch[ch >= 0]].sum()))
+    assert counts & {3, 5, 6, 7}, counts
+    g = S.Octree(p.desc)
+    gh = S.Hierarchy(g, beta, p.bc, S.mg_params(coef="f32"))
+    lv = t.leaves
+    h = 1.0 / (t.n0 * 2.0 ** lv["depth"])
+    xs = np.sin(3.1 * (lv["i"] + 0.5) * h) * np.cos(2.3 * (lv["j"] + 0.5) * h) + 0.25
+    for x in (P.random_vector(t.n_leaves, 31), xs, 1e-7 * xs + 1e3):
+        y = gh.apply_A(cuda(x)).cpu().numpy()
+        ref = H.A @ x
+        assert np.abs(y - ref).max() <= 1e-12 * max(np.abs(ref).max(), 1e-300) + 1e-14 * np.abs(x).max() * np.abs(H.A).max(), \
+            np.abs(y - ref).max()
+
+
 @pytest.mark.parametrize("name", list(CASES))
 def test_apply_A_fp32(name):
     t, H, g, gh, f, beta = build(CASES[name](), "f32")

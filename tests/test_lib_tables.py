@@ -41,6 +41,10 @@ def _descs():
     yield P.accuracy_desc("star", 16)
     yield P.OctreeDesc(6, 3, P.REFINE_STAR_BAND, band=0.01,
                        spheres=[(0.47, 0.52, 0.5, 0.2), (0.05, 4.0, 2.0, 0.0)])
+    # tiles (Sec. 4.1 refines the tiles that meet the surface): one decision per block
+    yield P.OctreeDesc(16, 2, P.REFINE_SDF_BAND, band=0.0, spheres=[(0.5, 0.5, 0.5, 0.25)], tile_log2=2)
+    yield P.OctreeDesc(8, 3, P.REFINE_STAR_BAND, band=0.0, spheres=list(P.STAR), tile_log2=1)
+    yield P.OctreeDesc(8, 2, P.REFINE_SINE_BAND, band=0.02, sines=P.sine_waves(), tile_log2=2)
 
 
 @pytest.mark.parametrize("desc", list(_descs()))
@@ -94,3 +98,5 @@ def test_invalid_descriptions_are_rejected():
     assert e.value.code == _lib.OCG_EINVAL
     with pytest.raises(_lib.OcgError):
         S.Octree(P.OctreeDesc(8, 1, P.REFINE_BALL_CENTRE))   # no sphere given
+    with pytest.raises(_lib.OcgError):                         # n0 not a multiple of the tile
+        S.Octree(P.OctreeDesc(12, 1, P.REFINE_BALL_CENTRE, spheres=[(0.5, 0.5, 0.5, 0.25)], tile_log2=3))
