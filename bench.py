@@ -1,15 +1,19 @@
 """Benchmark: full multigrid-preconditioned CG solve to relative residual 1e-6.
 
-One step = one ocg_pcg_solve (Alg. 1 with one FAS-style V-cycle per iteration) of the
-two-level octree workload: 64^3 root grid, cells whose centre lies within 0.25 of the
-cube centre refined once (382,936 leaves), beta = 1, Dirichlet walls, manufactured
-p = exp(x) sin(2 pi y) cos(2 pi z); FP32 cycle inside FP64 PCG ("mixed"), with the plain
-FP32 solve reported beside it.  Inputs are resident in HBM before the timed region; L2
-is flushed (256 MB write) before every timed step.  Under torchrun every rank solves
-its own replica (the path does not shard below one octree): weak scaling, no
-collective in the data path.
+One step = one ocg_pcg_solve (Alg. 1, one FAS-style V-cycle of Alg. 4 per iteration) of
+the large sine-band octree: 128^3 root refined three times within 0.02 (plus the cell's
+reach) of the zero set of a seeded sum of 8 plane sine waves (effective 1024^3,
+106,243,054 leaves), fluid-fraction beta, Neumann walls, divergence right-hand side; FP32
+cycle inside FP64 PCG ("mixed").  Inputs are resident in HBM before the timed region; the
+solve touches about 10 GB per iteration (far beyond the 126 MB L2), and a 256 MB write
+flushes L2 before every timed step anyway.  Beside it, on the same tree: plain FP32 PCG,
+BF16 coarse coefficients, W and hybrid cycles, the adjoint, per-form fractions of the HBM
+roof from the byte model, and every form's error against the library's FP64 solve to
+1e-12; then the two-level ball, the cut-cell and the batched workloads in compact form.
+Under torchrun every rank solves its own replica (the path does not shard below one
+octree): weak scaling, no collective in the data path.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--studies]
 """
 from __future__ import annotations
 
@@ -29,12 +33,32 @@ sys.path.insert(0, ROOT)
 
 METRIC = "solve Mcells/s at rel-res 1e-6 (mixed/batched vs plain FP32), % HBM roof"
 UNIT = "Mcells/s"
-WORKLOAD = ("octree 64^3 root, ball r=0.25 at the centre refined once (382,936 leaves, "
-            "effective 128^3), beta=1, Dirichlet walls, p=exp(x)sin(2pi y)cos(2pi z)")
+LARGE_WORKLOAD = ("large differentiable solve: 128^3 root refined 3 times within 0.02 (+ cell reach) of the "
+                  "zero set of 8 seeded plane sine waves (effective 1024^3), fluid-fraction beta, Neumann, "
+                  "divergence rhs")
+BALL_WORKLOAD = ("octree 64^3 root, ball r=0.25 at the centre refined once (382,936 leaves, effective 128^3), "
+                 "beta=1, Dirichlet walls, p=exp(x)sin(2pi y)cos(2pi z)")
+BATCH_WORKLOAD = ("64 independent octrees, effective 64/96/128 with 2-3 levels refined within 0.05 of a "
+                  "seeded random sphere; even trees beta=1 Dirichlet, odd trees cut-cell beta Neumann; "
+                  "rhs N(0,1)")
+# CPU sample of the large workload: the same sine field, band and refinement rule on a
+# 12^3 root (effective 96^3, 320,984 leaves), small enough for the explicit-matrix oracle
+SAMPLE_N0 = 12
+SAMPLE_WORKLOAD = ("sine-band octree of the large workload's field and rule at a 12^3 root (effective 96^3, "
+                   "320,984 leaves), fluid-fraction beta, Neumann, divergence rhs")
 # algorithmic bytes per cell of one red-black colour sweep: 16 B coefficients (c, c_x-,
 # c_y-, c_z- in FP32) + 4 B u read + 2 B u write (half the cells) + 2 B b (half)
 SWEEP_BYTES_PER_CELL = 24.0
+# outer operator of the mixed solve: 16 B FP32 coefficients + 8 B p + 8 B Ap per tree cell
+APPLY_BYTES_PER_CELL = 32.0
+# byte model of a whole solve: one level visit of the cycle (8 colour sweeps of 24 B,
+# residual/restriction/average/FAS about 28 B, prolongation about 9 B per cell of the
+# level) and the Krylov vectors of one PCG iteration per tree cell (apply + dot, update
+# + norm + cast, (r, z) + p update)
+LEVEL_VISIT_BYTES = 230.0
+OUTER_BYTES = {"mixed": 116.0, "fp32": 72.0}
 NOMINAL_HBM_GBS = 7700.0   # B300 HBM3e nominal bandwidth, for a second fraction beside the measured one
+HYBRID_MIN_CELLS = 1 << 20
 
 
 def _peaks():
@@ -73,17 +97,18 @@ def _profiled_traffic(name, cells):
 
 
 class Clocks:
-    """nvidia-smi samples (every 20 ms) of SM clock, power and throttle reasons; started
-    before the timed region, which is bracketed by line marks."""
+    """nvidia-smi samples (every 20 ms) of SM clock, power and throttle reasons of the GPU
+    with the given UUID (nvidia-smi's own index order ignores CUDA_VISIBLE_DEVICES, the
+    UUID does not); started before the timed region, which is bracketed by line marks."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index):
+    def __init__(self, gpu_id):
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         try:
-            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + self.Q,
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_id), "--query-gpu=" + self.Q,
                                        "--format=csv,noheader,nounits", "-lms", "20"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
@@ -138,18 +163,14 @@ class Clocks:
                 "power_w": statistics.median(pw) if pw else None, "reasons": reasons, "samples": len(inside)}
 
 
-def _setup(dev, sweep="auto"):
-    import numpy as np
+def gpu_uuid(dev):
+    """nvidia-smi's identifier of the torch device (GPU-<uuid>), or its ordinal if unknown."""
     import torch
-    from paper_2604_18886_b300 import problems as P
-    from paper_2604_18886_b300 import solver as S
-    p = P.two_level_ball(64)
-    tree = S.Octree(p.desc)
-    faces = tree.faces()
-    beta = P.face_beta(p, faces)
-    hier = S.Hierarchy(tree, torch.from_numpy(beta).to(dev), p.bc, S.mg_params(coef="f32", sweep=sweep))
-    b = P.rhs(p, tree.leaves(), faces, beta)
-    return p, tree, hier, torch.from_numpy(b).to(dev), np
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return str(dev.index if hasattr(dev, "index") else dev)
 
 
 def max_over_ranks(v, dev):
@@ -170,103 +191,345 @@ def replica_throughput(units_per_rank, steps, world, total_ms):
     return world * units_per_rank * steps / (total_ms / 1e3) / 1e6
 
 
-def _hier_bf16(p, tree, dev):
+def cycle_visits(sizes, mu, mu_min_cells=0):
+    """Visits of every level in one cycle (finest first): the finest once; a coarser
+    level mu times as often as the level above it when it has at least mu_min_cells
+    cells (every level when mu_min_cells is 0), as often otherwise (Alg. 4's recursion
+    with the hybrid rule)."""
+    v, out = 1, []
+    for q, n in enumerate(sizes):
+        if q > 0 and (mu_min_cells == 0 or n >= mu_min_cells):
+            v *= mu
+        out.append(v)
+    return out
+
+
+def model_bytes(sizes, n_tree, iterations, precision="mixed", mu=1, mu_min_cells=0):
+    """Byte model of one solve: per PCG iteration one cycle (LEVEL_VISIT_BYTES per cell per
+    visit of each level) plus the outer Krylov traffic per tree cell."""
+    cyc = sum(LEVEL_VISIT_BYTES * n * v for n, v in zip(sizes, cycle_visits(sizes, mu, mu_min_cells)))
+    return iterations * (cyc + OUTER_BYTES[precision] * n_tree)
+
+
+def _timed(stream, flush, fn, steps):
+    """[(ms, result)] of fn() over `steps` calls, each bracketed by CUDA events on the
+    launching stream after an L2 flush."""
     import torch
-    from paper_2604_18886_b300 import problems as P
-    from paper_2604_18886_b300 import solver as S
-    beta = P.face_beta(p, tree.faces())
-    return S.Hierarchy(tree, torch.from_numpy(beta).to(dev), p.bc, S.mg_params(coef="f32", bf16_coarse=True))
-
-
-HYBRID_MIN_CELLS = 1 << 20
-
-
-def _w_cycle(g, beta, p, b, dev, stream, flush, steps, bf16=False, mu_min_cells=0):
-    """The same solve preconditioned by W-cycles (mu = 2; the paper's choice for cut-cell
-    problems) instead of V-cycles: iterations and Mcells/s.  mu_min_cells > 0: mu = 2 only
-    into levels with at least that many cells (V below)."""
-    import torch
-    from paper_2604_18886_b300 import solver as S
-    hw = S.Hierarchy(g, beta, p.bc, S.mg_params(mu=2, coef="f32", bf16_coarse=bf16, mu_min_cells=mu_min_cells))
-    x = torch.empty_like(b)
-    hw.solve(b, x, tol=1e-6, precision="mixed", stream=stream)
-    t, its = [], set()
+    out = []
     for s_ in range(steps):
         flush.fill_(float(s_))
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        _, st = hw.solve(b, x, tol=1e-6, precision="mixed", stream=stream)
+        r = fn()
         e1.record(stream)
         e1.synchronize()
-        t.append(e0.elapsed_time(e1))
-        its.add(st.iterations)
-    ms = statistics.mean(t)
-    del hw
-    return {"value": round(g.n_leaves / (ms / 1e3) / 1e6, 3), "unit": UNIT, "ms_per_step": round(ms, 3),
-            "iterations": sorted(its), "true_rel_res": st.true_rel_res,
-            "cycle": ("W (mu=2) into levels of >= %d cells, V below, nu=2/2" % mu_min_cells) if mu_min_cells
-            else "W (mu=2), nu=2/2"}
+        out.append((e0.elapsed_time(e1), r))
+    return out
 
 
-def _cut_cell(dev, stream, flush, args):
+def _form(leaves, runs, peak, bytes_fn, x=None, x_ref=None):
+    ms = statistics.mean(t for t, _ in runs)
+    st = runs[-1][1]
+    its = sorted({r.iterations for _, r in runs})
+    d = {"value": round(leaves / (ms / 1e3) / 1e6, 3), "unit": UNIT, "ms_per_step": round(ms, 3),
+         "iterations": its, "true_rel_res": st.true_rel_res}
+    mb = bytes_fn(st.iterations)
+    d["model_gb"] = round(mb / 1e9, 2)
+    d["hbm_roof_frac_model"] = round(mb / (ms / 1e3) / 1e9 / peak, 4)
+    if x is not None and x_ref is not None:
+        d["err_vs_fp64"] = float(((x - x_ref).abs().max() / x_ref.abs().max()).item())
+    return d
+
+
+def _probe(hier, kind, level, b, x, iterations, stream, flush, reps=1):
+    """(launches, total ms, cells per launch) of the probed kernel inside a flat graph of
+    the same solve (OCG_SOLVE_UNROLLED: event-record nodes around each probed launch)."""
+    from paper_2604_18886_b300 import _lib as L
+    L.check(L.lib().ocg_probe_set(hier.handle, kind, level))
+    nl_t, ms_t, cells = 0, 0.0, 0
+    for r in range(reps):
+        flush.fill_(float(r))
+        hier.solve(b, x, tol=1e-6, precision="mixed", stream=stream, max_iter=iterations, unrolled=True,
+                   raise_on_notconv=False)
+        nl, tot, ce = C.c_int64(), C.c_double(), C.c_int64()
+        L.check(L.lib().ocg_probe_read(hier.handle, C.c_void_p(stream.cuda_stream), C.byref(nl), C.byref(tot),
+                                       C.byref(ce)))
+        nl_t += nl.value
+        ms_t += tot.value
+        cells = ce.value
+    L.check(L.lib().ocg_probe_set(hier.handle, L.OCG_PROBE_OFF, 0))
+    return nl_t, ms_t, cells
+
+
+def _roofline(kernel, bytes_per_cell, n, ms, cells, peak, peak_kind, profile=None):
+    us = ms * 1e3 / max(n, 1)
+    achieved = bytes_per_cell * cells / (us / 1e6) / 1e9
+    return {"bound": "hbm", "kernel": kernel, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "peak_source": peak_kind,
+            "frac_of_nominal": round(achieved / NOMINAL_HBM_GBS, 4), "bytes_per_cell": bytes_per_cell,
+            "cells_per_launch": cells, "launches": n, "avg_launch_us": round(us, 2),
+            "timing": "CUDA event-record nodes around each launch inside one graph of the timed solve",
+            "traffic": _profiled_traffic(profile, cells) if profile else None}
+
+
+# ------------------------------------------------------------------ the large workload
+def _large_setup(dev, args):
+    import torch
+    from paper_2604_18886_b300 import problems as P
+    from paper_2604_18886_b300 import solver as S
+    t0 = time.perf_counter()
+    p = P.sine_band(args.large_n0, 3)
+    g = S.Octree(p.desc)
+    t_build = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    beta, bh = P.large_inputs(p, g.n_leaves, g.n_faces, g.faces_range, dev)
+    t_inputs = time.perf_counter() - t1
+    b = torch.from_numpy(bh).to(dev)
+    del bh
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    h = S.Hierarchy(g, beta, p.bc, S.mg_params(coef="f32", sweep=args.sweep))
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t2
+    times = {"octree_build_s": round(t_build, 2), "inputs_s": round(t_inputs, 2),
+             "setup_hierarchy_s": round(t_setup, 2),
+             "what": "host octree build (ocg_octree_build, 8+ threads), input generation (not the library), "
+                     "ocg_setup_hierarchy incl. the sweep-form autotuner"}
+    return p, g, beta, b, h, times
+
+
+def _sweep_forms(h):
+    from paper_2604_18886_b300 import solver as S
+    return {str(m): {"form": S.SWEEP_FORM_NAMES.get(v[0], "shared-memory tail"), "us_octet": round(v[1], 2),
+                     "us_cell": round(v[2], 2), "us_quad": round(v[3], 2), "us_tile": round(v[4], 2)}
+            for m, v in h.tuning().items() if m >= 0}
+
+
+def _large_rest(dev, stream, flush, args, peak, peak_kind, p, g, beta, b, hbox, x, st_mixed):
+    """Everything beside the headline's timed solves on the large tree (hbox: a list holding
+    the timed hierarchy, released here once it is no longer needed)."""
+    h = hbox.pop()
+    import numpy as np
+    import torch
+    from paper_2604_18886_b300 import _lib as L
+    from paper_2604_18886_b300 import solver as S
+    steps = max(3, min(args.steps, 5))
+    sizes = [g.level_size(m) for m in range(g.D, g.mc - 1, -1)]
+    nt = g.n_tree
+    # roofline of the dominant kernel (the finest level's colour sweep, about a third of
+    # the solve) and of the outer operator, inside a graph of the same solve
+    its = st_mixed.iterations
+    tun = h.tuning()
+    form = S.SWEEP_FORM_NAMES.get(tun[g.D][0], "?")
+    sw = _probe(h, L.OCG_PROBE_SWEEP, g.D, b, x, its, stream, flush)
+    ap = _probe(h, L.OCG_PROBE_APPLY, 0, b, x, its, stream, flush)
+    roof = _roofline("red-black colour sweep (%s form) on level %d" % (form, g.D), SWEEP_BYTES_PER_CELL, *sw,
+                     peak, peak_kind, "sweep_sineband_level%d_%s" % (g.D, form))
+    roof_apply = _roofline("outer operator apply in pair-of-FP32 arithmetic (all tree levels)",
+                           APPLY_BYTES_PER_CELL, *ap, peak, peak_kind, "apply_sineband_df")
+    # plain FP32 PCG on the same hierarchy
+    x32 = torch.empty_like(b)
+    r32 = _timed(stream, flush, lambda: h.solve(b, x32, tol=1e-6, precision="fp32", stream=stream)[1], steps)
+    forms = {}
+    forms["plain_fp32"] = (r32, x32, lambda k: model_bytes(sizes, nt, k, "fp32"))
+    # adjoint: A^T lambda = p - p_t by Alg. 1 on A^T with the transposed cycle M^T + face gradient
+    gp = x - torch.from_numpy(np.random.default_rng(8).standard_normal(g.n_leaves)).to(dev)
+
+    def adjoint(hier):
+        res = []
+        for r in range(2):   # the first call builds the adjoint tables and captures the graph
+            flush.fill_(float(r))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            lam, sa = hier.solve(gp, tol=1e-6, precision="mixed", stream=stream, transpose=True, max_iter=200,
+                                 raise_on_notconv=False)
+            hier.face_grad(x, lam, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            res.append((e0.elapsed_time(e1), sa))
+        return {"ms": round(res[-1][0], 3), "iterations": res[-1][1].iterations,
+                "converged": bool(res[-1][1].converged)}
+    adj = adjoint(h)
+    adj["what"] = ("A^T lambda = p - p_t by Alg. 1 on A^T preconditioned by M^T (mixed, tol 1e-6) + face "
+                   "gradient; second call (the first builds the adjoint tables and the graph)")
+    tuning = _sweep_forms(h)
+    del h
+    torch.cuda.empty_cache()
+    # BF16 coarse-level coefficients, W and hybrid cycles: one hierarchy each
+    for name, prm, mu, mmin in (
+            ("mixed_bf16_coarse", S.mg_params(coef="f32", bf16_coarse=True), 1, 0),
+            ("w_cycle", S.mg_params(mu=2, coef="f32"), 2, 0),
+            ("w_v_hybrid", S.mg_params(mu=2, coef="f32", mu_min_cells=HYBRID_MIN_CELLS), 2, HYBRID_MIN_CELLS)):
+        hf = S.Hierarchy(g, beta, p.bc, prm)
+        xf = torch.empty_like(b)
+        hf.solve(b, xf, tol=1e-6, precision="mixed", stream=stream)
+        rf = _timed(stream, flush, lambda: hf.solve(b, xf, tol=1e-6, precision="mixed", stream=stream)[1], steps)
+        forms[name] = (rf, xf, (lambda mu_, mm_: lambda k: model_bytes(sizes, nt, k, "mixed", mu_, mm_))(mu, mmin))
+        if name == "w_v_hybrid":
+            adj["hybrid_cycle"] = adjoint(hf)
+        del hf
+        torch.cuda.empty_cache()
+    # FP64 reference: FP64 coefficients and cycle, FP64 PCG to 1e-12
+    t0 = time.perf_counter()
+    h64 = S.Hierarchy(g, beta, p.bc, S.mg_params(coef="f64", sweep="octet"))
+    x_ref, s64 = h64.solve(b, tol=1e-12, precision="fp64", max_iter=300, stream=stream)
+    torch.cuda.synchronize()
+    t64 = time.perf_counter() - t0
+    del h64
+    torch.cuda.empty_cache()
+    out_forms = {k: _form(g.n_leaves, v[0], peak, v[2], v[1], x_ref) for k, v in forms.items()}
+    out_forms["w_cycle"]["cycle"] = "W (mu=2), nu=2/2"
+    out_forms["w_v_hybrid"]["cycle"] = "W (mu=2) into levels of >= %d cells, V below, nu=2/2" % HYBRID_MIN_CELLS
+    mixed_err = float(((x - x_ref).abs().max() / x_ref.abs().max()).item())
+    return {"roofline": roof, "roofline_apply": roof_apply, "forms": out_forms, "adjoint": adj,
+            "sweep_forms": tuning, "mixed_err_vs_fp64": mixed_err,
+            "fp64_reference": {"iterations": s64.iterations, "true_rel_res": s64.true_rel_res,
+                               "wall_s_incl_setup": round(t64, 2),
+                               "what": "FP64 coefficients, FP64 cycle, FP64 PCG to 1e-12 (the errors' reference)"},
+            "level_cells": sizes}
+
+
+# ------------------------------------------------------------------ smaller workloads
+def _ball(dev, stream, flush, args, peak, peak_kind):
+    """The two-level ball (64^3 root, 382,936 leaves, all in L2): mixed, plain FP32 and
+    BF16-coarse solves, the adjoint and the level-0 sweep roofline."""
+    import numpy as np
+    import torch
+    from paper_2604_18886_b300 import _lib as L
+    from paper_2604_18886_b300 import problems as P
+    from paper_2604_18886_b300 import solver as S
+    p = P.two_level_ball(64)
+    g = S.Octree(p.desc)
+    f = g.faces()
+    beta = torch.from_numpy(P.face_beta(p, f)).to(dev)
+    h = S.Hierarchy(g, beta, p.bc, S.mg_params(coef="f32"))
+    b = torch.from_numpy(P.rhs(p, g.leaves(), f, beta.cpu().numpy())).to(dev)
+    x = torch.empty_like(b)
+    for _ in range(args.warmup):
+        h.solve(b, x, tol=1e-6, precision="mixed", stream=stream)
+    steps = max(3, min(args.steps, 20))
+    sizes = [g.level_size(m) for m in range(g.D, g.mc - 1, -1)]
+    rm = _timed(stream, flush, lambda: h.solve(b, x, tol=1e-6, precision="mixed", stream=stream)[1], steps)
+    r32 = _timed(stream, flush, lambda: h.solve(b, x, tol=1e-6, precision="fp32", stream=stream)[1], steps)
+    out = _form(g.n_leaves, rm, peak, lambda k: model_bytes(sizes, g.n_tree, k, "mixed"))
+    out["plain_fp32"] = _form(g.n_leaves, r32, peak, lambda k: model_bytes(sizes, g.n_tree, k, "fp32"))
+    hb = S.Hierarchy(g, beta, p.bc, S.mg_params(coef="f32", bf16_coarse=True))
+    hb.solve(b, x, tol=1e-6, precision="mixed", stream=stream)
+    rb = _timed(stream, flush, lambda: hb.solve(b, x, tol=1e-6, precision="mixed", stream=stream)[1], steps)
+    out["mixed_bf16_coarse"] = _form(g.n_leaves, rb, peak, lambda k: model_bytes(sizes, g.n_tree, k, "mixed"))
+    del hb
+    its = rm[-1][1].iterations
+    big = int(max(range(g.D + 1), key=lambda q: g.level_size(q)))
+    form = S.SWEEP_FORM_NAMES.get(h.tuning()[big][0], "?")
+    sw = _probe(h, L.OCG_PROBE_SWEEP, big, b, x, its, stream, flush, reps=5)
+    out["roofline_l2_resident"] = _roofline("red-black colour sweep (%s form) on level %d" % (form, big),
+                                            SWEEP_BYTES_PER_CELL, *sw, peak, peak_kind,
+                                            "sweep_ball64_level%d_%s" % (big, form))
+    # adjoint
+    ptgt = torch.from_numpy(np.random.default_rng(2).standard_normal(g.n_leaves)).to(dev)
+    xs, _ = h.solve(b, tol=1e-6, precision="mixed", stream=stream)
+    gp = xs - ptgt
+
+    def adj():
+        lam, sa = h.solve(gp, tol=1e-6, precision="mixed", stream=stream, transpose=True)
+        h.face_grad(xs, lam, stream=stream)
+        return sa
+    adj()
+    ra = _timed(stream, flush, adj, steps)
+    out["adjoint"] = {"ms": round(statistics.mean(t for t, _ in ra), 4), "iterations": ra[-1][1].iterations}
+    # end to end through the C ABI with host buffers
+    bh = b.cpu().pin_memory()
+    xh = torch.empty_like(bh).pin_memory()
+
+    def e2e():
+        b.copy_(bh, non_blocking=True)
+        h.solve(b, x, tol=1e-6, precision="mixed", stream=stream)
+        xh.copy_(x, non_blocking=True)
+    re = _timed(stream, flush, e2e, steps)
+    out["e2e"] = {"value": round(g.n_leaves / (statistics.mean(t for t, _ in re) / 1e3) / 1e6, 3), "unit": UNIT}
+    out["workload"] = BALL_WORKLOAD
+    out["leaves"] = g.n_leaves
+    return out
+
+
+def _cut_cell(dev, stream, flush, args, peak):
     """The cut-cell projection workload: 64^3 root, two levels of refinement within 0.05
     of a solid sphere and box, fluid-fraction beta, Neumann walls, divergence rhs; mixed
-    solve with BF16 coarse coefficients to 1e-6."""
+    solve with BF16 coarse coefficients to 1e-6, W and hybrid cycles, and the geometric
+    coarsening ablation of Sec. 3.3."""
     import torch
     from paper_2604_18886_b300 import problems as P
     from paper_2604_18886_b300 import solver as S
     p = P.cut_cell(64, 2)
     g = S.Octree(p.desc)
     f = g.faces()
-    beta = P.face_beta(p, f)
-    h = S.Hierarchy(g, torch.from_numpy(beta).to(dev), p.bc, S.mg_params(coef="f32", bf16_coarse=True))
-    b = torch.from_numpy(P.rhs(p, g.leaves(), f, beta)).to(dev)
-    x = torch.empty_like(b)
+    beta = torch.from_numpy(P.face_beta(p, f)).to(dev)
+    b = torch.from_numpy(P.rhs(p, g.leaves(), f, beta.cpu().numpy())).to(dev)
+    sizes = [g.level_size(m) for m in range(g.D, g.mc - 1, -1)]
+    steps = max(3, min(args.steps, 10))
+    out = {"workload": "cut-cell projection: 64^3 root, sphere r=0.2 and box, band 0.05, 2 levels "
+                       "(%d leaves), fluid-fraction beta, Neumann, divergence rhs" % g.n_leaves}
+    for name, prm, mu, mmin, maxit in (
+            ("mixed_bf16_coarse", S.mg_params(coef="f32", bf16_coarse=True), 1, 0, 100),
+            ("w_cycle", S.mg_params(mu=2, coef="f32", bf16_coarse=True), 2, 0, 100),
+            ("w_v_hybrid", S.mg_params(mu=2, coef="f32", bf16_coarse=True, mu_min_cells=HYBRID_MIN_CELLS), 2,
+             HYBRID_MIN_CELLS, 100),
+            ("geometric_coarsening", S.mg_params(coef="f32", coarsening="geometric"), 1, 0, 400)):
+        h = S.Hierarchy(g, beta, p.bc, prm)
+        x = torch.empty_like(b)
+        h.solve(b, x, tol=1e-6, precision="mixed", stream=stream, max_iter=maxit)
+        r = _timed(stream, flush, lambda: h.solve(b, x, tol=1e-6, precision="mixed", stream=stream,
+                                                  max_iter=maxit)[1], steps if maxit == 100 else 1)
+        out[name] = _form(g.n_leaves, r, peak, (lambda mu_, mm_: lambda k: model_bytes(
+            sizes, g.n_tree, k, "mixed", mu_, mm_))(mu, mmin))
+        del h
+    return out
+
+
+def _batched(dev, stream, flush, args):
+    """The batched workload solved by ocg_pcg_solve_batched, and the same 64 problems
+    solved one after another by single graph solves, both mixed precision to 1e-6."""
+    import torch
+    from paper_2604_18886_b300 import problems as P
+    from paper_2604_18886_b300 import solver as S
+    hs, bs, leaves = [], [], 0
+    for k in range(64):
+        p = P.batch_tree(k)
+        g = S.Octree(p.desc)
+        f = g.faces()
+        beta = P.face_beta(p, f)
+        hs.append(S.Hierarchy(g, torch.from_numpy(beta).to(dev), p.bc, S.mg_params(coef="f32")))
+        bs.append(torch.from_numpy(P.rhs(p, g.leaves(), f, beta)).to(dev))
+        leaves += g.n_leaves
+    t0 = time.perf_counter()
+    bt = S.Batch(hs, stream=stream)
+    t_create = time.perf_counter() - t0
+    xs = [torch.empty_like(b) for b in bs]
     for _ in range(args.warmup):
-        h.solve(b, x, tol=1e-6, precision="mixed", stream=stream)
+        bt.solve(bs, xs, tol=1e-6, stream=stream)
     steps = max(3, min(args.steps, 20))
-    t, its = [], set()
-    for s_ in range(steps):
-        flush.fill_(float(s_))
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        _, st = h.solve(b, x, tol=1e-6, precision="mixed", stream=stream)
-        e1.record(stream)
-        e1.synchronize()
-        t.append(e0.elapsed_time(e1))
-        its.add(st.iterations)
-        assert st.converged
-    ms = statistics.mean(t)
-    wc = _w_cycle(g, beta, p, b, dev, stream, flush, steps, bf16=True)
-    wh = _w_cycle(g, beta, p, b, dev, stream, flush, steps, bf16=True, mu_min_cells=HYBRID_MIN_CELLS)
-    # ablation (Sec. 3.3): geometric multigrid, coarse cells rediscretised from the solids
-    hg = S.Hierarchy(g, torch.from_numpy(beta).to(dev), p.bc, S.mg_params(coef="f32", coarsening="geometric"))
-    hg.solve(b, x, tol=1e-6, precision="mixed", stream=stream, max_iter=400)
-    flush.fill_(0.0)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    _, sg = hg.solve(b, x, tol=1e-6, precision="mixed", stream=stream, max_iter=400)
-    e1.record(stream)
-    e1.synchronize()
-    msg = e0.elapsed_time(e1)
-    gmg = {"value": round(g.n_leaves / (msg / 1e3) / 1e6, 3), "unit": UNIT, "ms_per_step": round(msg, 3),
-           "iterations": sg.iterations, "converged": bool(sg.converged),
-           "what": "geometric coarsening (Sec. 3.3 ablation), V-cycle, mixed, FP32 coefficients"}
-    del hg
-    return {"w_cycle": wc, "w_v_hybrid": wh, "geometric_coarsening": gmg,
-            "workload": "cut-cell projection: 64^3 root, sphere r=0.2 and box, band 0.05, 2 levels "
-                        "(%d leaves), fluid-fraction beta, Neumann, divergence rhs" % g.n_leaves,
-            "precision": "mixed, BF16 coarse coefficients", "value": round(g.n_leaves / (ms / 1e3) / 1e6, 3),
-            "unit": UNIT, "ms_per_step": round(ms, 4), "steps": steps, "iterations": sorted(its),
-            "true_rel_res": st.true_rel_res}
+    rb = _timed(stream, flush, lambda: bt.solve(bs, xs, tol=1e-6, stream=stream)[1], steps)
+    assert all(s.converged for s in rb[-1][1])
 
-
-LARGE_WORKLOAD = ("large differentiable solve: 128^3 root refined 3 times within 0.02 (+ cell reach) of the "
-                  "zero set of 8 seeded plane sine waves (effective 1024^3), fluid-fraction beta, Neumann, "
-                  "divergence rhs")
+    def seq():
+        for h, b, x in zip(hs, bs, xs):
+            h.solve(b, x, tol=1e-6, precision="mixed", stream=stream)
+    seq()
+    rs = _timed(stream, flush, seq, 3)
+    ms_b = statistics.mean(t for t, _ in rb)
+    ms_s = statistics.mean(t for t, _ in rs)
+    its = sorted({s.iterations for _, st in rb for s in st})
+    forms = {str(h): ["octet", "cell"][f] for h, (f, a, b) in bt.info().items()}
+    kern = rb[-1][1][0].kernels
+    del bt
+    return {"workload": BATCH_WORKLOAD, "problems": 64, "leaves": leaves,
+            "value": round(leaves / (ms_b / 1e3) / 1e6, 3), "unit": UNIT, "ms_per_step": round(ms_b, 4),
+            "steps": steps, "iterations": its, "gpu_launches_per_step": kern,
+            "sweep_forms_by_height": forms, "create_s": round(t_create, 3),
+            "sequential_single_solves": {"value": round(leaves / (ms_s / 1e3) / 1e6, 3), "unit": UNIT,
+                                         "ms_per_step": round(ms_s, 4)}}
 
 
 def _tank(dev, stream, flush, args):
@@ -285,46 +548,38 @@ def _tank(dev, stream, flush, args):
     cases = [(o, n0, True) for o in ("sphere", "star") for n0 in (64, 128)] + \
         [(o, 64, False) for o in ("sphere", "star")]
     for obstacle, n0, inactive in cases:
-        if True:
-            p = P.tank(obstacle, n0, inactive)
-            g = S.Octree(p.desc)
-            f = g.faces()
-            beta = P.face_beta(p, f)
-            lv = g.leaves()
-            b = torch.from_numpy(P.rhs(p, lv, f, beta)).to(dev)
-            hc, xc, yc, zc = P.leaf_centres(n0, lv)
-            ref = torch.from_numpy(yc - 1.0).to(dev)
-            V = torch.from_numpy(hc ** 3).to(dev)
-            row = {"leaves": g.n_leaves}
-            for mu in (2, 1):
-                h = S.Hierarchy(g, beta, p.bc, S.mg_params(coef="f32", mu=mu))
-                x = torch.empty_like(b)
-                h.solve(b, x, tol=1e-6, precision="mixed", stream=stream, max_iter=200, raise_on_notconv=False)
-                flush.fill_(0.0)
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                _, st = h.solve(b, x, tol=1e-6, precision="mixed", stream=stream, max_iter=200,
-                                raise_on_notconv=False)
-                e1.record(stream)
-                e1.synchronize()
-                ms = e0.elapsed_time(e1)
-                act = (b != 0) | (x != 0)              # inactive cells keep b = x = 0
-                rms = lambda e: math.sqrt(float((V[act] * e[act] * e[act]).sum() / V[act].sum()))
-                div = (b - h.apply_A(x, stream=stream)) / V
-                kh = min(st.iterations, 127)                     # the recorded residual history
-                row["mu%d" % mu] = {"iterations": st.iterations, "converged": bool(st.converged),
-                                    "rel_res": st.rel_res, "ms": round(ms, 3),
-                                    "value": round(g.n_leaves / (ms / 1e3) / 1e6, 3), "unit": UNIT,
-                                    "mean_reduction_per_iteration":
-                                        round(math.exp(-math.log(st.hist[kh]) / kh), 2),
-                                    "fitted_reduction_per_iteration": round(math.exp(-np.polyfit(
-                                        np.arange(kh + 1), np.log([st.hist[i] for i in range(kh + 1)]), 1)[0]), 2),
-                                    "max_dev_from_y_minus_1": (x - ref)[act].abs().max().item(),
-                                    "div_rms_ratio": rms(div) / rms(b / V)}
-                del h
-            row["solid_cells"] = "inactive (exact fractions)" if inactive else "beta clamped at 1e-3"
-            out["%s_%d%s" % (obstacle, n0, "" if inactive else "_clamped")] = row
+        p = P.tank(obstacle, n0, inactive)
+        g = S.Octree(p.desc)
+        f = g.faces()
+        beta = P.face_beta(p, f)
+        lv = g.leaves()
+        b = torch.from_numpy(P.rhs(p, lv, f, beta)).to(dev)
+        hc, xc, yc, zc = P.leaf_centres(n0, lv)
+        ref = torch.from_numpy(yc - 1.0).to(dev)
+        V = torch.from_numpy(hc ** 3).to(dev)
+        row = {"leaves": g.n_leaves}
+        for mu in (2, 1):
+            h = S.Hierarchy(g, beta, p.bc, S.mg_params(coef="f32", mu=mu))
+            x = torch.empty_like(b)
+            h.solve(b, x, tol=1e-6, precision="mixed", stream=stream, max_iter=200, raise_on_notconv=False)
+            (ms, st), = _timed(stream, flush, lambda: h.solve(b, x, tol=1e-6, precision="mixed", stream=stream,
+                                                              max_iter=200, raise_on_notconv=False)[1], 1)
+            act = (b != 0) | (x != 0)              # inactive cells keep b = x = 0
+            rms = lambda e: math.sqrt(float((V[act] * e[act] * e[act]).sum() / V[act].sum()))
+            div = (b - h.apply_A(x, stream=stream)) / V
+            kh = min(st.iterations, 127)                     # the recorded residual history
+            row["mu%d" % mu] = {"iterations": st.iterations, "converged": bool(st.converged),
+                                "rel_res": st.rel_res, "ms": round(ms, 3),
+                                "value": round(g.n_leaves / (ms / 1e3) / 1e6, 3), "unit": UNIT,
+                                "mean_reduction_per_iteration":
+                                    round(math.exp(-math.log(st.hist[kh]) / kh), 2),
+                                "fitted_reduction_per_iteration": round(math.exp(-np.polyfit(
+                                    np.arange(kh + 1), np.log([st.hist[i] for i in range(kh + 1)]), 1)[0]), 2),
+                                "max_dev_from_y_minus_1": (x - ref)[act].abs().max().item(),
+                                "div_rms_ratio": rms(div) / rms(b / V)}
+            del h
+        row["solid_cells"] = "inactive (exact fractions)" if inactive else "beta clamped at 1e-3"
+        out["%s_%d%s" % (obstacle, n0, "" if inactive else "_clamped")] = row
     return {"cases": out,
             "what": "static tank, mixed solves to 1e-6; with the solid interior at beta 1e-3 the exact "
                     "discrete pressure is y - 1 (the uniform velocity is minus the gradient of a linear "
@@ -404,32 +659,42 @@ def _accuracy(dev, stream):
                      "surface r = 0.237 + 0.079 cos(6 theta) cos(6 phi)"}
 
 
-def _large(dev, stream, flush, args, peak):
-    """The sine-band workload at full size: mixed solve to 1e-6 (timed), the red-black sweep
-    on its finest level (per-launch events inside an unrolled graph of the same solve),
-    and the adjoint (transpose solve + face gradient)."""
-    import numpy as np
+# ------------------------------------------------------------------ our arm
+def run_ours(args):
     import torch
-    from paper_2604_18886_b300 import _lib as L
-    from paper_2604_18886_b300 import problems as P
-    from paper_2604_18886_b300 import solver as S
-    t0 = time.perf_counter()
-    p = P.sine_band(args.large_n0, 3)
-    g = S.Octree(p.desc)
-    t_build = time.perf_counter() - t0
-    beta, bh = P.large_inputs(p, g.n_leaves, g.n_faces, g.faces_range, dev)
-    b = torch.from_numpy(bh).to(dev)
-    del bh
-    t1 = time.perf_counter()
-    h = S.Hierarchy(g, beta, p.bc, S.mg_params(coef="f32", sweep=args.sweep))
-    torch.cuda.synchronize()
-    t_setup = time.perf_counter() - t1
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    peak, peak_kind = _peaks()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+    flush.fill_(0.0)   # the fill kernel's module loads here, not in the timed region
+    if args.only_ball:
+        out = _ball(dev, stream, flush, args, peak, peak_kind)
+        if rank == 0:
+            print(json.dumps(out), flush=True)
+        return
+    p, g, beta, b, h, setup_times = _large_setup(dev, args)
     x = torch.empty_like(b)
     for _ in range(args.warmup):
         h.solve(b, x, tol=1e-6, precision="mixed", stream=stream)
-    steps = max(1 if args.only_large else 3, min(args.steps, 10))
-    t, its = [], set()
-    for s_ in range(steps):
+    # ---- timed region: mixed solves of the large workload (graph path, one host
+    # synchronisation per solve)
+    clocks = Clocks(gpu_uuid(dev))
+    clocks.wait_first()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    mark0 = clocks.mark()
+    t0 = time.perf_counter()
+    times, iters, kernels = [], [], 0
+    for s_ in range(args.steps):
         flush.fill_(float(s_))
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -441,241 +706,10 @@ def _large(dev, stream, flush, args, peak):
             torch.cuda.nvtx.range_pop()
         e1.record(stream)
         e1.synchronize()
-        t.append(e0.elapsed_time(e1))
-        its.add(st.iterations)
-        assert st.converged
-    ms = statistics.mean(t)
-    tun = h.tuning()
-    forms = {str(m): {"form": S.SWEEP_FORM_NAMES.get(v[0], "shared-memory tail"), "us_octet": round(v[1], 2),
-                      "us_cell": round(v[2], 2), "us_quad": round(v[3], 2), "us_tile": round(v[4], 2)}
-             for m, v in tun.items() if m >= 0}
-    if args.only_large:
-        out = {"workload": LARGE_WORKLOAD, "n0": args.large_n0, "leaves": g.n_leaves,
-               "value": round(g.n_leaves / (ms / 1e3) / 1e6, 3), "unit": UNIT, "ms_per_step": round(ms, 3),
-               "steps": steps, "iterations": sorted(its), "sweep_forms": forms,
-               "note": "--only-large (profiling aid)"}
-        if args.adjoint:
-            # one transpose solve (tables built and graph captured by an untimed first call),
-            # then one more inside the NVTX range 'adjoint' (kernel by kernel with --eager)
-            gp = x - torch.from_numpy(np.random.default_rng(8).standard_normal(g.n_leaves)).to(dev)
-            h.solve(gp, tol=1e-6, precision="mixed", stream=stream, transpose=True, max_iter=200)
-            torch.cuda.synchronize()
-            if args.nvtx:
-                torch.cuda.nvtx.range_push("adjoint")
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            _, sa = h.solve(gp, tol=1e-6, precision="mixed", stream=stream, transpose=True, max_iter=200,
-                            eager=args.eager)
-            e1.record(stream)
-            e1.synchronize()
-            if args.nvtx:
-                torch.cuda.nvtx.range_pop()
-            out["adjoint"] = {"ms": round(e0.elapsed_time(e1), 3), "iterations": sa.iterations}
-        return out
-    # plain FP32 beside it (FP32 Krylov vectors, FP64 dot products)
-    t32 = []
-    for s_ in range(steps):
-        flush.fill_(float(s_))
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        _, st32 = h.solve(b, x, tol=1e-6, precision="fp32", stream=stream)
-        e1.record(stream)
-        e1.synchronize()
-        t32.append(e0.elapsed_time(e1))
-    ms32 = statistics.mean(t32)
-    wc = _w_cycle(g, beta, p, b, dev, stream, flush, steps)
-    wh = _w_cycle(g, beta, p, b, dev, stream, flush, steps, mu_min_cells=HYBRID_MIN_CELLS)
-    # finest-level sweep inside an unrolled graph of the same solve
-    D = g.D
-    L.check(L.lib().ocg_probe_set(h.handle, L.OCG_PROBE_SWEEP, D))
-    h.solve(b, x, tol=1e-6, precision="mixed", stream=stream, max_iter=st.iterations, unrolled=True,
-            raise_on_notconv=False)
-    nl, tot, ce = C.c_int64(), C.c_double(), C.c_int64()
-    L.check(L.lib().ocg_probe_read(h.handle, C.c_void_p(stream.cuda_stream), C.byref(nl), C.byref(tot),
-                                   C.byref(ce)))
-    L.check(L.lib().ocg_probe_set(h.handle, L.OCG_PROBE_OFF, 0))
-    sweep_us = tot.value * 1e3 / max(nl.value, 1)
-    achieved = SWEEP_BYTES_PER_CELL * ce.value / (sweep_us / 1e6) / 1e9
-    form = S.SWEEP_FORM_NAMES.get(tun[D][0], "?")
-    # adjoint: transpose solve of dL/dp = p - p_t and the face gradient
-    ptgt = torch.from_numpy(np.random.default_rng(8).standard_normal(g.n_leaves)).to(dev)
-    gp = x - ptgt
-    del ptgt
-    def adjoint(hier, method="pcg"):
-        # the first call builds the adjoint tables and captures the graph: untimed
-        res = []
-        for r in range(2):
-            flush.fill_(float(r))
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            lam, sa = hier.solve(gp, tol=1e-6, precision="mixed", stream=stream, transpose=True, max_iter=200,
-                                 raise_on_notconv=False, method=method)
-            hier.face_grad(x, lam, stream=stream)
-            e1.record(stream)
-            e1.synchronize()
-            res.append((e0.elapsed_time(e1), sa))
-        return res[-1]
-
-    ms_a, sa = adjoint(h)
-    adj = {"ms": round(ms_a, 3), "iterations": sa.iterations, "converged": bool(sa.converged),
-           "rel_res": sa.rel_res,
-           "what": "A^T lambda = p - p_t by Alg. 1 on A^T preconditioned by M^T (mixed, tol 1e-6) + face "
-                   "gradient; second call (the first builds the adjoint tables and the graph)"}
-    ms_b, sb = adjoint(h, "bicgstab")
-    adj["bicgstab"] = {"ms": round(ms_b, 3), "iterations": sb.iterations, "converged": bool(sb.converged)}
-    # the same adjoint preconditioned by the hybrid cycle
-    hh = S.Hierarchy(g, beta, p.bc, S.mg_params(mu=2, coef="f32", mu_min_cells=HYBRID_MIN_CELLS))
-    ms_h, sh_ = adjoint(hh)
-    adj["hybrid_cycle"] = {"ms": round(ms_h, 3), "iterations": sh_.iterations, "converged": bool(sh_.converged)}
-    del hh
-    return {"workload": LARGE_WORKLOAD, "leaves": g.n_leaves, "faces": g.n_faces, "cells_all_levels": g.n_cells,
-            "precision": "mixed (FP32 V-cycle, FP64 PCG)", "value": round(g.n_leaves / (ms / 1e3) / 1e6, 3),
-            "unit": UNIT, "ms_per_step": round(ms, 3), "steps": steps, "iterations": sorted(its),
-            "true_rel_res": st.true_rel_res, "build_s": round(t_build, 2), "setup_s": round(t_setup, 2),
-            "w_cycle": wc, "w_v_hybrid": wh,
-            "plain_fp32": {"value": round(g.n_leaves / (ms32 / 1e3) / 1e6, 3), "unit": UNIT,
-                           "ms_per_step": round(ms32, 3), "iterations": st32.iterations,
-                           "true_rel_res": st32.true_rel_res},
-            "sweep_forms": forms,
-            "roofline": {"bound": "hbm", "kernel": "red-black colour sweep (%s form) on level %d" % (form, D),
-                         "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                         "frac": round(achieved / peak, 4), "frac_of_nominal": round(achieved / NOMINAL_HBM_GBS, 4),
-                         "bytes_per_cell": SWEEP_BYTES_PER_CELL,
-                         "cells_per_launch": ce.value, "launches": nl.value, "avg_launch_us": round(sweep_us, 2),
-                         "traffic": _profiled_traffic("sweep_sineband_level%d_%s" % (D, form), ce.value),
-                         "traffic_note": "dram bytes per cell of an ncu capture at 64^3 root (same field, "
-                                         "effective 512^3) times the cells of one launch"},
-            "adjoint": adj}
-
-
-BATCH_WORKLOAD = ("64 independent octrees, effective 64/96/128 with 2-3 levels refined within 0.05 of a "
-                  "seeded random sphere; even trees beta=1 Dirichlet, odd trees cut-cell beta Neumann; "
-                  "rhs N(0,1)")
-
-
-def _batched(dev, stream, flush, args):
-    """The batched workload solved by ocg_pcg_solve_batched, and the same 64 problems
-    solved one after another by single graph solves, both mixed precision to 1e-6."""
-    import torch
-    from paper_2604_18886_b300 import problems as P
-    from paper_2604_18886_b300 import solver as S
-    hs, bs, leaves = [], [], 0
-    for k in range(64):
-        p = P.batch_tree(k)
-        g = S.Octree(p.desc)
-        f = g.faces()
-        beta = P.face_beta(p, f)
-        hs.append(S.Hierarchy(g, torch.from_numpy(beta).to(dev), p.bc, S.mg_params(coef="f32")))
-        bs.append(torch.from_numpy(P.rhs(p, g.leaves(), f, beta)).to(dev))
-        leaves += g.n_leaves
-    t0 = time.perf_counter()
-    bt = S.Batch(hs, stream=stream)
-    t_create = time.perf_counter() - t0
-    xs = [torch.empty_like(b) for b in bs]
-    for _ in range(args.warmup):
-        bt.solve(bs, xs, tol=1e-6, stream=stream)
-    steps = max(3, min(args.steps, 20))
-    tb, its, kern = [], set(), 0
-    for s_ in range(steps):
-        flush.fill_(float(s_))
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        _, st = bt.solve(bs, xs, tol=1e-6, stream=stream)
-        e1.record(stream)
-        e1.synchronize()
-        tb.append(e0.elapsed_time(e1))
-        its.update(x.iterations for x in st)
-        kern += st[0].kernels
-        assert all(x.converged for x in st)
-    # the same problems one after another (single graph solves)
-    for h, b, x in zip(hs, bs, xs):
-        h.solve(b, x, tol=1e-6, precision="mixed", stream=stream)
-    ts = []
-    for s_ in range(3):
-        flush.fill_(float(s_))
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for h, b, x in zip(hs, bs, xs):
-            h.solve(b, x, tol=1e-6, precision="mixed", stream=stream)
-        e1.record(stream)
-        e1.synchronize()
-        ts.append(e0.elapsed_time(e1))
-    ms_b = statistics.mean(tb)
-    ms_s = statistics.mean(ts)
-    forms = {str(h): ["octet", "cell"][f] for h, (f, a, b) in bt.info().items()}
-    del bt
-    return {"workload": BATCH_WORKLOAD, "problems": 64, "leaves": leaves,
-            "value": round(leaves / (ms_b / 1e3) / 1e6, 3), "unit": UNIT, "ms_per_step": round(ms_b, 4),
-            "steps": steps, "iterations": sorted(its), "gpu_launches_per_step": kern // steps,
-            "sweep_forms_by_height": forms, "create_s": round(t_create, 3),
-            "sequential_single_solves": {"value": round(leaves / (ms_s / 1e3) / 1e6, 3), "unit": UNIT,
-                                         "ms_per_step": round(ms_s, 4)}}
-
-
-def _time_solves(hier, b, x, steps, precision, flush, stream, nvtx=False, eager=False):
-    import torch
-    times, iters, kernels = [], [], 0
-    for s in range(steps):
-        flush.fill_(float(s))
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        if nvtx:
-            torch.cuda.nvtx.range_push("timed")
-        _, st = hier.solve(b, x, tol=1e-6, precision=precision, stream=stream, eager=eager)
-        if nvtx:
-            torch.cuda.nvtx.range_pop()
-        e1.record(stream)
-        e1.synchronize()
         times.append(e0.elapsed_time(e1))
         iters.append(st.iterations)
         kernels += st.kernels
         assert st.converged
-    return times, iters, kernels
-
-
-def run_ours(args):
-    import torch
-    import torch.distributed as dist
-    from paper_2604_18886_b300 import _lib as L
-
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    stream = torch.cuda.current_stream(dev)
-    if args.only_large:
-        flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
-        out = _large(dev, stream, flush, args, _peaks()[0])
-        if rank == 0:
-            print(json.dumps(out), flush=True)
-        return
-    p, tree, hier, b, np = _setup(dev, args.headline_sweep)
-    x = torch.empty_like(b)
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
-    for _ in range(args.warmup):
-        hier.solve(b, x, tol=1e-6, precision="mixed", stream=stream)
-        hier.solve(b, x, tol=1e-6, precision="fp32", stream=stream)
-    # ---- timed region: mixed solve (graph path, one host synchronisation per solve)
-    levels = [tree.level(m)[0].shape[0] for m in range(0, tree.D + 1)]
-    big = int(max(range(len(levels)), key=lambda q: levels[q]))
-    clocks = Clocks(local)
-    clocks.wait_first()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    mark0 = clocks.mark()
-    t0 = time.perf_counter()
-    times, iters, kernels = _time_solves(hier, b, x, args.steps, "mixed", flush, stream, nvtx=args.nvtx,
-                                         eager=args.eager)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     mark1 = clocks.mark()
@@ -683,141 +717,81 @@ def run_ours(args):
         dist.barrier()
     ck = clocks.stop(mark0, mark1)
     ms = statistics.mean(times)
-    total_ms = sum(times)
-    from paper_2604_18886_b300 import solver as S
-    tuning = {str(m): {"form": S.SWEEP_FORM_NAMES[f] if f >= 0 else "shared-memory tail",
-                       "us_octet": round(a, 2), "us_cell": round(bq, 2), "us_quad": round(qq, 2),
-                       "us_tile": round(tt, 2)}
-              for m, (f, a, bq, qq, tt) in hier.tuning().items()}
-    total_ms = max_over_ranks(total_ms, dev)
-    value = replica_throughput(tree.n_leaves, args.steps, world, total_ms)
+    total_ms = max_over_ranks(sum(times), dev)
+    value = replica_throughput(g.n_leaves, args.steps, world, total_ms)
+    sizes = [g.level_size(m) for m in range(g.D, g.mc - 1, -1)]
+    head = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 cycle + f64 pcg", "data": "synthetic"}
     if args.only_timed:
         if rank == 0:
-            print(json.dumps({"metric": METRIC, "value": round(value, 3), "unit": UNIT, "steps": args.steps,
-                              "ms_per_step": round(ms, 4), "note": "--only-timed (profiling aid)"}), flush=True)
+            head["note"] = "--only-timed (profiling aid)"
+            print(json.dumps(head), flush=True)
         return
-    # ---- per-kernel durations inside a graph: the same solve (same iteration count) as
-    # one flat graph whose probe events are event-record nodes around the probed launches
-    def probe(kind, level, reps=5):
-        L.check(L.lib().ocg_probe_set(hier.handle, kind, level))
-        nl_t, ms_t, cells = 0, 0.0, 0
-        for r in range(reps):
-            flush.fill_(float(r))
-            hier.solve(b, x, tol=1e-6, precision="mixed", stream=stream, max_iter=iters[0], unrolled=True,
-                       raise_on_notconv=False)
-            nl, tot, ce = C.c_int64(), C.c_double(), C.c_int64()
-            L.check(L.lib().ocg_probe_read(hier.handle, C.c_void_p(stream.cuda_stream), C.byref(nl),
-                                           C.byref(tot), C.byref(ce)))
-            nl_t += nl.value
-            ms_t += tot.value
-            cells = ce.value
-        L.check(L.lib().ocg_probe_set(hier.handle, L.OCG_PROBE_OFF, 0))
-        return nl_t, ms_t, cells
-    sw_n, sw_ms, sw_cells = probe(L.OCG_PROBE_SWEEP, big)
-    tail_top = max([m for m, v in hier.tuning().items() if v[0] < 0 and m < 0] or [tree.mc])
-    tl_n, tl_ms, tl_cells = probe(L.OCG_PROBE_TAIL, tail_top)
-    ap_n, ap_ms, ap_cells = probe(L.OCG_PROBE_APPLY, 0)
-    # ---- plain FP32 beside it
-    times32, iters32, _ = _time_solves(hier, b, x, args.steps, "fp32", flush, stream)
-    v32 = tree.n_leaves / (statistics.mean(times32) / 1e3) / 1e6
-    # ---- mixed with BF16 coarse-level coefficients
-    hb = _hier_bf16(p, tree, dev)
-    for _ in range(args.warmup):
-        hb.solve(b, x, tol=1e-6, precision="mixed", stream=stream)
-    times_b, iters_b, _ = _time_solves(hb, b, x, args.steps, "mixed", flush, stream)
-    vb16 = tree.n_leaves / (statistics.mean(times_b) / 1e3) / 1e6
-    del hb
-    # ---- adjoint: transpose solve (Alg. 1 on A^T, transposed cycle M^T) + face gradient
-    ptgt = torch.from_numpy(np.random.default_rng(2).standard_normal(tree.n_leaves)).to(dev)
-    xs, _ = hier.solve(b, tol=1e-6, precision="mixed", stream=stream)
-    gp = xs - ptgt
-    adj_t, adj_it = [], []
-    for r in range(max(3, min(args.steps, 20))):
-        flush.fill_(float(r))
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        lam, sa = hier.solve(gp, tol=1e-6, precision="mixed", stream=stream, transpose=True)
-        hier.face_grad(xs, lam, stream=stream)
-        e1.record(stream)
-        e1.synchronize()
-        if r > 0:
-            adj_t.append(e0.elapsed_time(e1))
-            adj_it.append(sa.iterations)
-    # ---- cut-cell workload (mixed, BF16 coarse coefficients)
-    cut = None if args.no_batch else _cut_cell(dev, stream, flush, args)
-    # ---- batched form: 64 independent trees, one graph, one launch per phase
-    batched = None if args.no_batch else _batched(dev, stream, flush, args)
-    # ---- the large sine-band workload (effective 1024^3)
-    large = None if args.no_large else _large(dev, stream, flush, args, _peaks()[0])
-    accuracy = None if args.no_accuracy else _accuracy(dev, stream)
-    tank = None if args.no_accuracy else _tank(dev, stream, flush, args)
-    # ---- end to end through the C ABI with host buffers
+    # ---- end to end through the C ABI: b from pinned host memory, x back to it
     bh = b.cpu().pin_memory()
     xh = torch.empty_like(bh).pin_memory()
-    e2e_t = []
-    for s_ in range(args.steps):
+    e2e_steps = max(3, min(args.steps, 10))
+    e2e_t, host_t = [], []
+    for s_ in range(e2e_steps):
         flush.fill_(float(s_))
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        th = time.perf_counter()
         e0.record(stream)
         b.copy_(bh, non_blocking=True)
-        hier.solve(b, x, tol=1e-6, precision="mixed", stream=stream)
+        h.solve(b, x, tol=1e-6, precision="mixed", stream=stream)
         xh.copy_(x, non_blocking=True)
         e1.record(stream)
         e1.synchronize()
+        host_t.append((time.perf_counter() - th) * 1e3)
         e2e_t.append(e0.elapsed_time(e1))
-    e2e_total = max_over_ranks(sum(e2e_t), dev)
-    e2e = replica_throughput(tree.n_leaves, args.steps, world, e2e_total)
-    # ---- roofline of the dominant kernel family: the red-black sweep on the largest level
-    peak, peak_kind = _peaks()
-    sweep_us = sw_ms * 1e3 / max(sw_n, 1)
-    achieved = SWEEP_BYTES_PER_CELL * sw_cells / (sweep_us / 1e6) / 1e9
-    fwd = tuning.get(str(big), {}).get("form", "octet")
-    traffic = _profiled_traffic("sweep_ball64_level%d_%s" % (big, fwd), sw_cells)
-    out = {
-        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 cycle + f64 pcg", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "precision": "mixed (FP32 V-cycle, FP64 PCG)", "tol": 1e-6,
-                   "leaves": tree.n_leaves, "iterations": sorted(set(iters)),
-                   "cycle": "V (mu=1), nu=2/2, coarsest 10",
-                   "l2": "flushed before every timed step (256 MB write)",
-                   "parallelism": "replicas" if world > 1 else "single GPU",
-                   "sweep_forms": tuning,
-                   "wall_s_timed": round(wall, 3)},
-        "plain_fp32": {"value": round(v32, 3), "unit": UNIT, "ms_per_step": round(statistics.mean(times32), 4),
-                       "iterations": sorted(set(iters32))},
-        "mixed_bf16_coarse": {"value": round(vb16, 3), "unit": UNIT,
-                              "ms_per_step": round(statistics.mean(times_b), 4),
-                              "iterations": sorted(set(iters_b))},
-        "adjoint": {"ms": round(statistics.mean(adj_t), 4), "iterations": sorted(set(adj_it)),
-                    "what": "A^T lambda = p - p_t by Alg. 1 on A^T preconditioned by M^T (mixed, tol 1e-6) "
-                            "+ face gradient"},
-        "value_mi_cells": round(value / 1.048576, 3),
-        "roofline": {"bound": "hbm", "kernel": "red-black colour sweep (%s form) on level %d" % (fwd, big),
-                     "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "peak_source": peak_kind,
-                     "frac_of_nominal": round(achieved / NOMINAL_HBM_GBS, 4),
-                     "bytes_per_cell": SWEEP_BYTES_PER_CELL, "cells_per_launch": sw_cells,
-                     "launches": sw_n, "avg_launch_us": round(sweep_us, 3),
-                     "timing": "CUDA event-record nodes around each launch inside one graph of the solve",
-                     "traffic": traffic},
-        "kernels_us": {"coarse_tail": round(tl_ms * 1e3 / max(tl_n, 1), 3), "coarse_tail_launches": tl_n,
-                       "operator_apply": round(ap_ms * 1e3 / max(ap_n, 1), 3), "operator_launches": ap_n},
-        "cut_cell": cut,
-        "batched": batched,
-        "large": large,
-        "accuracy": accuracy,
-        "tank": tank,
-        "e2e": {"value": round(e2e, 3), "unit": UNIT, "h2d_bytes_per_step": tree.n_leaves * 8,
-                "d2h_bytes_per_step": tree.n_leaves * 8},
-        "clocks": ck,
-        "gpu_launches": int(kernels),
-    }
+    e2e_total = max_over_ranks(sum(e2e_t), dev) * args.steps / e2e_steps
+    e2e = replica_throughput(g.n_leaves, args.steps, world, e2e_total)
+    hbox = [h]
+    del h
+    rest = _large_rest(dev, stream, flush, args, peak, peak_kind, p, g, beta, b, hbox, x, st)
+    mixed = {"value": round(value, 3), "ms_per_step": round(ms, 3), "iterations": sorted(set(iters)),
+             "true_rel_res": st.true_rel_res, "err_vs_fp64": rest["mixed_err_vs_fp64"]}
+    mb = model_bytes(sizes, g.n_tree, st.iterations, "mixed")
+    mixed["model_gb"] = round(mb / 1e9, 2)
+    mixed["hbm_roof_frac_model"] = round(mb / (ms / 1e3) / 1e9 / peak, 4)
+    out = dict(head)
+    out["config"] = {"workload": LARGE_WORKLOAD, "leaves": g.n_leaves, "faces": g.n_faces,
+                     "tree_cells": g.n_tree, "cells_all_levels": g.n_cells,
+                     "precision": "mixed (FP32 V-cycle, FP64 PCG)", "tol": 1e-6,
+                     "iterations": sorted(set(iters)), "cycle": "V (mu=1), nu=2/2, coarsest 10",
+                     "l2": "inputs larger than L2 (about 10 GB moved per PCG iteration); L2 also flushed "
+                           "before every timed step (256 MB write)",
+                     "parallelism": "replicas" if world > 1 else "single GPU",
+                     "wall_s_timed": round(wall, 3), "host_ms_per_step": round(wall * 1e3 / args.steps, 3)}
+    out["roofline"] = rest["roofline"]
+    out["e2e"] = {"value": round(e2e, 3), "unit": UNIT, "h2d_bytes_per_step": g.n_leaves * 8,
+                  "d2h_bytes_per_step": g.n_leaves * 8, "ms_per_step": round(statistics.mean(e2e_t), 3),
+                  "host_clock_ms_per_step": round(statistics.mean(host_t), 3)}
+    out["clocks"] = ck
+    out["gpu_launches"] = int(kernels)
+    out["value_mi_cells"] = round(value / 1.048576, 3)
+    out["forms"] = dict({"mixed": mixed}, **rest["forms"])
+    out["setup"] = setup_times
+    out["roofline_apply"] = rest["roofline_apply"]
+    out["adjoint"] = rest["adjoint"]
+    out["fp64_reference"] = rest["fp64_reference"]
+    del b, x, beta
+    torch.cuda.empty_cache()
+    # ---- the smaller workloads, compact
+    if not args.no_small:
+        out["two_level_ball"] = _ball(dev, stream, flush, args, peak, peak_kind)
+        out["cut_cell"] = _cut_cell(dev, stream, flush, args, peak)
+        out["batched"] = _batched(dev, stream, flush, args)
+    out["sweep_forms"] = rest["sweep_forms"]
+    out["level_cells"] = rest["level_cells"]
+    if args.studies:
+        out["accuracy"] = _accuracy(dev, stream)
+        out["tank"] = _tank(dev, stream, flush, args)
+    del g
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(budget_s=args.cpu_budget)
+        out["cpu_baseline"] = cpu_baseline(args.cpu_budget)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
@@ -825,33 +799,86 @@ def run_ours(args):
         print(json.dumps(out), flush=True)
 
 
-def _oracle_problem():
+# ------------------------------------------------------------------ the oracle on the host
+def _oracle_worker(n0, warm, steps, budget, barrier, queue):
+    """One host process: the FP64 oracle (explicit CSR, Alg. 4 cycle, Alg. 1) set up on the
+    sine-band sample, then timed solves to 1e-6 after all workers passed the barrier:
+    `warm` untimed and `steps` timed ones, or as many as fit `budget` seconds (at least
+    one) when steps is 0."""
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+    sys.path.insert(0, ROOT)
     from oracle import octree as O
     from oracle import operator as OP
+    from oracle import pcg
     from paper_2604_18886_b300 import problems as P
-    p = P.two_level_ball(64)
+    p = P.sine_band(n0, 3)
     t = O.Octree(p.desc)
     f = t.faces()
     beta = P.face_beta(p, f)
     H = OP.Hierarchy(t, beta, p.bc)
     b = P.rhs(p, t.leaves, f, beta)
-    return t, H, b
-
-
-def cpu_baseline(budget_s=15.0):
-    """The FP64 oracle (explicit CSR, scipy) timed on the host on the same workload."""
-    from oracle import pcg
-    t, H, b = _oracle_problem()
-    times = []
-    t_end = time.perf_counter() + budget_s
-    while not times or (time.perf_counter() < t_end and len(times) < 20):
-        t0 = time.perf_counter()
+    barrier.wait()
+    for _ in range(warm):
         pcg.pcg(H, b, tol=1e-6)
+    times, k = [], 0
+    t_end = time.perf_counter() + budget
+    while (steps and len(times) < steps) or (not steps and (not times or time.perf_counter() < t_end)):
+        t0 = time.perf_counter()
+        _, k, _ = pcg.pcg(H, b, tol=1e-6)
         times.append(time.perf_counter() - t0)
-    v = t.n_leaves / statistics.mean(times) / 1e6
-    return {"value": round(v, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d full solves of the same workload (oracle set-up excluded), %.1f s" %
-                      (len(times), sum(times))}
+    queue.put((t.n_leaves, k, times))
+
+
+def _oracle_on_cores(n_proc, warm=0, steps=0, budget=8.0):
+    """Runs _oracle_worker in n_proc spawned processes (one core each) and returns
+    (leaves, iterations, per-process solve times)."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(n_proc)
+    queue = ctx.Queue()
+    procs = [ctx.Process(target=_oracle_worker, args=(SAMPLE_N0, warm, steps, budget, barrier, queue))
+             for _ in range(n_proc)]
+    for pr in procs:
+        pr.start()
+    res = [queue.get(timeout=1800) for _ in procs]
+    for pr in procs:
+        pr.join(timeout=60)
+    return res[0][0], res[0][1], [r[2] for r in res]
+
+
+def _cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def _host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(budget_s=8.0):
+    """The FP64 oracle timed on the host on the CPU sample of the large workload: one
+    process, then one process per host core (independent solves, aggregate throughput)."""
+    leaves, its, t1 = _oracle_on_cores(1, budget=budget_s)
+    v1 = leaves * len(t1[0]) / sum(t1[0]) / 1e6
+    cores = _host_cores()
+    leaves, its, tn = _oracle_on_cores(cores, budget=budget_s)
+    span = max(sum(t) for t in tn)
+    vn = leaves * sum(len(t) for t in tn) / span / 1e6
+    return {"value": round(vn, 4), "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": _cpu_model(),
+            "one_core": {"value": round(v1, 4), "unit": UNIT, "cores": 1, "solves": len(t1[0])},
+            "iterations": its,
+            "sample": "%s; FP64 oracle (scipy CSR, Alg. 4 cycle, Alg. 1) to 1e-6, set-up excluded; %d solves "
+                      "in %.1f s on %d cores (one independent solve per process), %d solves in %.1f s on one"
+                      % (SAMPLE_WORKLOAD, sum(len(t) for t in tn), span, cores, len(t1[0]), sum(t1[0]))}
 
 
 def run_reference(args):
@@ -859,25 +886,22 @@ def run_reference(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if rank != 0:
         return
-    from oracle import pcg
-    t, H, b = _oracle_problem()
-    for _ in range(args.warmup):
-        pcg.pcg(H, b, tol=1e-6)
-    times = []
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        _, k, _ = pcg.pcg(H, b, tol=1e-6)
-        times.append(time.perf_counter() - t0)
-    ms = statistics.mean(times) * 1e3
-    v = t.n_leaves / (ms / 1e3) / 1e6
+    cores = _host_cores()
+    leaves, k, tn = _oracle_on_cores(cores, warm=args.warmup, steps=args.steps)
+    span = max(sum(t) for t in tn)
+    v = leaves * cores * args.steps / span / 1e6
+    ms = max(statistics.mean(t) for t in tn) * 1e3
+    sample = ("%s; each step one FP64 oracle solve to 1e-6 on each of %d cores (independent processes, set-up "
+              "excluded)" % (SAMPLE_WORKLOAD, cores))
     out = {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic",
-           "config": {"workload": WORKLOAD, "precision": "FP64 oracle (scipy CSR, Alg. 4 cycle, Alg. 1)",
-                      "tol": 1e-6, "leaves": t.n_leaves, "iterations": k},
-           "cpu_baseline": {"value": round(v, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
-                            "sample": "one full solve per step (set-up excluded)"},
+           "config": {"workload": LARGE_WORKLOAD, "sample": SAMPLE_WORKLOAD,
+                      "precision": "FP64 oracle (scipy CSR, Alg. 4 cycle, Alg. 1)", "tol": 1e-6,
+                      "leaves_per_solve": leaves, "iterations": k},
+           "cpu_baseline": {"value": round(v, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "cpu": _cpu_model(), "sample": sample},
            "e2e": {"value": round(v, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -885,29 +909,23 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-budget", type=float, default=15.0)
-    ap.add_argument("--nvtx", action="store_true", help="NVTX range 'timed' around the timed mixed solves")
-    ap.add_argument("--no-batch", action="store_true", help="skip the batched 64-tree form")
-    ap.add_argument("--no-large", action="store_true", help="skip the large sine-band workload")
-    ap.add_argument("--no-accuracy", action="store_true", help="skip the accuracy studies and the static tank")
-    ap.add_argument("--only-large", action="store_true",
-                    help="run only the timed solves of the large sine-band workload (profiling aid)")
+    ap.add_argument("--cpu-budget", type=float, default=8.0, help="seconds of oracle solves per CPU leg")
+    ap.add_argument("--no-small", action="store_true", help="skip the ball, cut-cell and batched workloads")
+    ap.add_argument("--studies", action="store_true", help="also the accuracy studies and the static tank")
+    ap.add_argument("--nvtx", action="store_true", help="NVTX range 'timed' around the timed solves")
+    ap.add_argument("--only-timed", action="store_true",
+                    help="the large workload's warm-up and timed solves only (profiling aid)")
+    ap.add_argument("--only-ball", action="store_true", help="the two-level ball workload only (profiling aid)")
     ap.add_argument("--sweep", default="auto", choices=["auto", "octet", "cell", "quad", "tile"],
                     help="sweep form of the large workload's hierarchy (auto: timed at set-up; profiling aid)")
     ap.add_argument("--large-n0", type=int, default=128,
                     help="root grid of the sine-band workload (128: effective 1024^3; smaller for profiling)")
-    ap.add_argument("--only-timed", action="store_true",
-                    help="run the warm-up and the timed mixed solves only (profiling aid)")
     ap.add_argument("--eager", action="store_true",
                     help="launch the timed solves kernel by kernel (profiling aid; not the benchmark path)")
-    ap.add_argument("--headline-sweep", default="auto", choices=["auto", "octet", "cell", "quad", "tile"],
-                    help="sweep form of the headline hierarchy (auto: timed at set-up; profiling aid)")
-    ap.add_argument("--adjoint", action="store_true",
-                    help="with --only-large: also one transpose solve, in the NVTX range 'adjoint' (profiling aid)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
