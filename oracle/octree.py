@@ -49,6 +49,41 @@ def morton(i, j, k):
     return out
 
 
+def _box_sdf(box, x, y, z):
+    """Signed distance to the axis-aligned box (lo, hi): positive outside."""
+    lx, ly, lz, hx, hy, hz = box
+    qx = np.abs(x - 0.5 * (lx + hx)) - 0.5 * (hx - lx)
+    qy = np.abs(y - 0.5 * (ly + hy)) - 0.5 * (hy - ly)
+    qz = np.abs(z - 0.5 * (lz + hz)) - 0.5 * (hz - lz)
+    mx, my, mz = np.maximum(qx, 0.0), np.maximum(qy, 0.0), np.maximum(qz, 0.0)
+    outside = np.sqrt(mx * mx + my * my + mz * mz)
+    inside = np.minimum(np.maximum(qx, np.maximum(qy, qz)), 0.0)
+    return outside + inside
+
+
+def _star_phi(desc, x, y, z):
+    """Sec. 4.1 star surface r = r0 + a cos(k theta) cos(k phi) about the first sphere's
+    centre: r - (r0 + (a T_k(dz/r)) T_k(dx/rho)), the cosines of multiple angles as
+    Chebyshev polynomials of cos(theta) = dz / r and cos(phi) = dx / rho."""
+    (cx, cy, cz, r0), (a, kk, _, _) = desc.spheres[0], desc.spheres[1]
+    dx, dy, dz = x - cx, y - cy, z - cz
+    rho2 = dx * dx + dy * dy
+    r = np.sqrt(rho2 + dz * dz)
+    rho = np.sqrt(rho2)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        u = np.where(r > 0.0, dz / r, 1.0)
+        v = np.where(rho > 0.0, dx / rho, 1.0)
+
+    def cheb(w):
+        t0, t1 = np.ones_like(w), w
+        if int(kk) == 0:
+            return t0
+        for _ in range(2, int(kk) + 1):
+            t0, t1 = t1, (2.0 * w) * t1 - t0
+        return t1
+    return r - (r0 + (a * cheb(u)) * cheb(v))
+
+
 def refine_predicate(desc, d, i, j, k):
     """Refinement decision for depth-d cells (d < max_depth), Sec. 4.1.
 
@@ -89,19 +124,38 @@ def refine_predicate(desc, d, i, j, k):
         cx, cy, cz, r = desc.spheres[0]
         dx, dy, dz = x - cx, y - cy, z - cz
         return (dx * dx + dy * dy + dz * dz) < r * r
+    if desc.refine == P.REFINE_SDF_BAND and t > 0:
+        # a tile (the box [i, i+1] / nd per axis) meets the band of a sphere when the
+        # sphere's signed distance, which runs over [dmin - r, dmax - r] on the box (nearest
+        # and farthest distance from the centre), takes a value in (-band, band); boxes use
+        # the centre test with the tile's half-diagonal
+        ii, jj, kk = (np.asarray(v, np.float64) for v in (i, j, k))
+        lo = [ii / nd, jj / nd, kk / nd]
+        hi = [(ii + 1.0) / nd, (jj + 1.0) / nd, (kk + 1.0) / nd]
+        out = np.zeros(x.shape, bool)
+        for (cx, cy, cz, r) in desc.spheres:
+            n2 = np.zeros(x.shape)
+            f2 = np.zeros(x.shape)
+            for a, c in enumerate((cx, cy, cz)):
+                nearest = np.where(c < lo[a], lo[a], np.where(c > hi[a], hi[a], c))
+                dn = nearest - c
+                df = np.maximum(np.abs(lo[a] - c), np.abs(hi[a] - c))
+                n2 = n2 + dn * dn
+                f2 = f2 + df * df
+            out |= (np.sqrt(n2) - r < desc.band) & (np.sqrt(f2) - r > -desc.band)
+        if desc.boxes:
+            phi = np.full(x.shape, np.inf)
+            for box in desc.boxes:
+                phi = np.minimum(phi, _box_sdf(box, x, y, z))
+            out |= np.abs(phi) < desc.band + (0.5 * math.sqrt(3.0)) * (1.0 / nd)
+        return out
     if desc.refine == P.REFINE_SDF_BAND:
         phi = np.full(x.shape, np.inf)
         for (cx, cy, cz, r) in desc.spheres:
             dx, dy, dz = x - cx, y - cy, z - cz
             phi = np.minimum(phi, np.sqrt(dx * dx + dy * dy + dz * dz) - r)
-        for (lx, ly, lz, hx, hy, hz) in desc.boxes:
-            qx = np.abs(x - 0.5 * (lx + hx)) - 0.5 * (hx - lx)
-            qy = np.abs(y - 0.5 * (ly + hy)) - 0.5 * (hy - ly)
-            qz = np.abs(z - 0.5 * (lz + hz)) - 0.5 * (hz - lz)
-            mx, my, mz = np.maximum(qx, 0.0), np.maximum(qy, 0.0), np.maximum(qz, 0.0)
-            outside = np.sqrt(mx * mx + my * my + mz * mz)
-            inside = np.minimum(np.maximum(qx, np.maximum(qy, qz)), 0.0)
-            phi = np.minimum(phi, outside + inside)
+        for box in desc.boxes:
+            phi = np.minimum(phi, _box_sdf(box, x, y, z))
         slack = desc.band + (0.5 * math.sqrt(3.0)) * (1.0 / nd)
         return np.abs(phi) < slack
     if desc.refine == P.REFINE_SINE_BAND:
@@ -120,25 +174,21 @@ def refine_predicate(desc, d, i, j, k):
         slack = desc.band + (grad * (0.5 * math.sqrt(3.0))) * (1.0 / nd)
         return np.abs(phi) < slack
     if desc.refine == P.REFINE_STAR_BAND:
-        # Sec. 4.1 star surface r = r0 + a cos(k theta) cos(k phi); the cosines of multiple
-        # angles as Chebyshev polynomials of cos(theta) = dz / r and cos(phi) = dx / rho
-        (cx, cy, cz, r0), (a, kk, lip, _) = desc.spheres[0], desc.spheres[1]
-        dx, dy, dz = x - cx, y - cy, z - cz
-        rho2 = dx * dx + dy * dy
-        r = np.sqrt(rho2 + dz * dz)
-        rho = np.sqrt(rho2)
-        with np.errstate(divide="ignore", invalid="ignore"):
-            u = np.where(r > 0.0, dz / r, 1.0)
-            v = np.where(rho > 0.0, dx / rho, 1.0)
-
-        def cheb(w):
-            t0, t1 = np.ones_like(w), w
-            if int(kk) == 0:
-                return t0
-            for _ in range(2, int(kk) + 1):
-                t0, t1 = t1, (2.0 * w) * t1 - t0
-            return t1
-        phi = r - (r0 + (a * cheb(u)) * cheb(v))
+        if t > 0:
+            # a tile meets the band when the star function takes a value below band and one
+            # above -band among its 27 lattice points (i + q/2) / nd, q = 0, 1, 2 per axis
+            ii, jj, kk = (np.asarray(v, np.float64) for v in (i, j, k))
+            lo = np.full(x.shape, np.inf)
+            hi = np.full(x.shape, -np.inf)
+            for qz in range(3):
+                for qy in range(3):
+                    for qx in range(3):
+                        f = _star_phi(desc, (ii + 0.5 * qx) / nd, (jj + 0.5 * qy) / nd, (kk + 0.5 * qz) / nd)
+                        lo = np.minimum(lo, f)
+                        hi = np.maximum(hi, f)
+            return (lo < desc.band) & (hi > -desc.band)
+        lip = desc.spheres[1][2]
+        phi = _star_phi(desc, x, y, z)
         slack = desc.band + (lip * (0.5 * math.sqrt(3.0))) * (1.0 / nd)
         return np.abs(phi) < slack
     raise NotImplementedError("refine kind %d" % desc.refine)
@@ -179,13 +229,29 @@ class Octree:
                 c = [i.copy(), j.copy(), k.copy()]
                 c[a] = c[a] + s
                 ok = (c[a] >= 0) & (c[a] < ne)
-                add.append(_key(c[0][ok] // 2, c[1][ok] // 2, c[2][ok] // 2, self.nd(e - 1)))
+                add.append(self._tile_cells(e - 1, c[0][ok] // 2, c[1][ok] // 2, c[2][ok] // 2))
             self.refined[e - 1] = np.unique(np.concatenate(add))
         for d in range(D):
             self.exist[d + 1] = self._children(d, self.refined[d])
         self._build_leaves()
 
     # --------------------------------------------------------------------------
+    def _tile_cells(self, d, i, j, k):
+        """Keys of the depth-d cells (i, j, k), each widened to its whole tile of
+        2^tile_log2 cells per axis when the description refines by tiles (a tile is
+        refined as a unit, by the predicate and by the 2:1 balance)."""
+        t = int(getattr(self.desc, "tile_log2", 0))
+        nd = self.nd(d)
+        if t == 0 or len(i) == 0:
+            return _key(i, j, k, nd)
+        tk = np.unique(_key(i >> t, j >> t, k >> t, nd >> t))
+        ti, tj, tk_ = _unkey(tk, nd >> t)
+        w = 1 << t
+        o = np.arange(w)
+        oi, oj, ok = (a.ravel() for a in np.meshgrid(o, o, o, indexing="ij"))
+        return _key((ti[:, None] * w + oi[None]).ravel(), (tj[:, None] * w + oj[None]).ravel(),
+                    (tk_[:, None] * w + ok[None]).ravel(), nd)
+
     def nd(self, d):
         return self.n0 * 2 ** d
 

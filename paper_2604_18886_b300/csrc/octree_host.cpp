@@ -152,6 +152,27 @@ float face_beta_geometric(const ocg_octree_desc& d, int m, int axis, int64_t i, 
     return (float)std::fmin(std::fmax(f, 1e-3), 1.0);
 }
 
+// The star function of Sec. 4.1 (documented in ocg.h): r - (r0 + (a T_k(dz/r)) T_k(dx/rho))
+// about spheres[0]'s centre, T_k by the Chebyshev recurrence.
+static double star_phi(const ocg_octree_desc& d, double x, double y, double z) {
+    const double dx = x - d.spheres[0][0], dy = y - d.spheres[0][1], dz = z - d.spheres[0][2];
+    const double rho2 = dx * dx + dy * dy;
+    const double r = std::sqrt(rho2 + dz * dz), rho = std::sqrt(rho2);
+    const double u = r > 0.0 ? dz / r : 1.0, v = rho > 0.0 ? dx / rho : 1.0;
+    const int k = (int)d.spheres[1][1];
+    auto cheb = [k](double w) {
+        double t0 = 1.0, t1 = w;
+        if (k == 0) return t0;
+        for (int n = 2; n <= k; ++n) {
+            const double t = (2.0 * w) * t1 - t0;
+            t0 = t1;
+            t1 = t;
+        }
+        return t1;
+    };
+    return r - (d.spheres[0][3] + (d.spheres[1][0] * cheb(u)) * cheb(v));
+}
+
 // Refinement predicate (documented in ocg.h); no FMA contraction in this file.
 static bool refine_pred(const ocg_octree_desc& d, int depth, int64_t i, int64_t j, int64_t k) {
     // tiles of 2^t cells per axis decide together, as the depth-(depth - t) cell that covers
@@ -171,27 +192,54 @@ static bool refine_pred(const ocg_octree_desc& d, int depth, int64_t i, int64_t 
         return (s + dz * dz) < r * r;
     }
     if (d.refine == OCG_REFINE_SDF_BAND) {
+        if (t > 0) {
+            // a tile meets the band of a sphere when the sphere's signed distance takes a
+            // value in (-band, band) on the closed box: its range there is
+            // [dmin - r, dmax - r], dmin / dmax the nearest / farthest distance from the
+            // centre to the box; boxes keep the centre test with the tile's half-diagonal
+            const double lo[3] = {(double)i / nd, (double)j / nd, (double)k / nd};
+            const double hi[3] = {((double)i + 1.0) / nd, ((double)j + 1.0) / nd, ((double)k + 1.0) / nd};
+            for (int q = 0; q < d.n_spheres; ++q) {
+                double n2 = 0.0, f2 = 0.0;
+                for (int a = 0; a < 3; ++a) {
+                    const double c = d.spheres[q][a];
+                    const double nc = c < lo[a] ? lo[a] : (c > hi[a] ? hi[a] : c);
+                    const double dn = nc - c;
+                    const double df = std::fmax(std::fabs(lo[a] - c), std::fabs(hi[a] - c));
+                    n2 = n2 + dn * dn;
+                    f2 = f2 + df * df;
+                }
+                const double r = d.spheres[q][3];
+                if (std::sqrt(n2) - r < d.band && std::sqrt(f2) - r > -d.band) return true;
+            }
+            if (d.n_boxes == 0) return false;
+            ocg_octree_desc bx = d;
+            bx.n_spheres = 0;
+            const double phi = solid_sdf(bx, x, y, z);
+            return std::fabs(phi) < d.band + (0.5 * std::sqrt(3.0)) * (1.0 / nd);
+        }
         const double phi = solid_sdf(d, x, y, z);
         const double slack = d.band + (0.5 * std::sqrt(3.0)) * (1.0 / nd);
         return std::fabs(phi) < slack;
     }
     if (d.refine == OCG_REFINE_STAR_BAND) {
-        const double dx = x - d.spheres[0][0], dy = y - d.spheres[0][1], dz = z - d.spheres[0][2];
-        const double rho2 = dx * dx + dy * dy;
-        const double r = std::sqrt(rho2 + dz * dz), rho = std::sqrt(rho2);
-        const double u = r > 0.0 ? dz / r : 1.0, v = rho > 0.0 ? dx / rho : 1.0;
-        const int k = (int)d.spheres[1][1];
-        auto cheb = [k](double w) {
-            double t0 = 1.0, t1 = w;
-            if (k == 0) return t0;
-            for (int n = 2; n <= k; ++n) {
-                const double t = (2.0 * w) * t1 - t0;
-                t0 = t1;
-                t1 = t;
-            }
-            return t1;
-        };
-        const double phi = r - (d.spheres[0][3] + (d.spheres[1][0] * cheb(u)) * cheb(v));
+        if (t > 0) {
+            // a tile meets the band when the star function takes a value below band and one
+            // above -band among its 27 lattice points (corners, edge and face midpoints,
+            // centre): (i + q/2) / nd, q = 0, 1, 2 per axis
+            double lo = INFINITY, hi = -INFINITY;
+            for (int qz = 0; qz < 3; ++qz)
+                for (int qy = 0; qy < 3; ++qy)
+                    for (int qx = 0; qx < 3; ++qx) {
+                        const double px = ((double)i + 0.5 * qx) / nd, py = ((double)j + 0.5 * qy) / nd,
+                                     pz = ((double)k + 0.5 * qz) / nd;
+                        const double f = star_phi(d, px, py, pz);
+                        lo = std::fmin(lo, f);
+                        hi = std::fmax(hi, f);
+                    }
+            return lo < d.band && hi > -d.band;
+        }
+        const double phi = star_phi(d, x, y, z);
         const double slack = d.band + (d.spheres[1][2] * (0.5 * std::sqrt(3.0))) * (1.0 / nd);
         return std::fabs(phi) < slack;
     }
@@ -434,11 +482,16 @@ static void build_impl(const ocg_octree_desc& desc, HostTree& T, const HostTree*
     }
     T.pred.assign(ref.begin(), ref.begin() + std::max(D, 0));
     // ---- face 2:1 balance, deepest inner cells first (within one depth the order of the
-    // marks does not matter: depth e is read, depth e-1 written)
+    // marks does not matter: depth e is read, depth e-1 written).  With tiles the marks go
+    // to whole tiles of depth e-1 (a tile is refined as a unit), collected in TM first.
+    const int tl = desc.tile_log2;
     for (int e = D - 1; e >= 1; --e) {
-        const int64_t ne = (int64_t)n0 << e, np = ne / 2;
+        const int64_t ne = (int64_t)n0 << e, np = ne / 2, nt = np >> tl;
         const auto& R = ref[e];
-        uint8_t* Rp = ref[e - 1].data();
+        std::vector<uint8_t> TM(tl > 0 ? nt * nt * nt : 0, 0);
+        uint8_t* Rp = tl > 0 ? TM.data() : ref[e - 1].data();
+        const int sh = 1 + tl;   // depth-e coordinate -> parent's tile coordinate
+        const int64_t nm = tl > 0 ? nt : np;
 #pragma omp parallel for schedule(static)
         for (int64_t k = 0; k < ne; ++k)
             for (int64_t j = 0; j < ne; ++j)
@@ -450,10 +503,18 @@ static void build_impl(const ocg_octree_desc& desc, HostTree& T, const HostTree*
                             int64_t q[3] = {c[0], c[1], c[2]};
                             q[a] += s;
                             if (q[a] < 0 || q[a] >= ne) continue;
-                            __atomic_store_n(&Rp[lex(q[0] >> 1, q[1] >> 1, q[2] >> 1, np)], (uint8_t)1,
+                            __atomic_store_n(&Rp[lex(q[0] >> sh, q[1] >> sh, q[2] >> sh, nm)], (uint8_t)1,
                                              __ATOMIC_RELAXED);
                         }
                 }
+        if (tl > 0) {
+            uint8_t* P = ref[e - 1].data();
+#pragma omp parallel for schedule(static)
+            for (int64_t k = 0; k < np; ++k)
+                for (int64_t j = 0; j < np; ++j)
+                    for (int64_t i = 0; i < np; ++i)
+                        if (TM[lex(i >> tl, j >> tl, k >> tl, nt)]) P[lex(i, j, k, np)] = 1;
+        }
     }
     auto refined = [&](int d, int64_t i, int64_t j, int64_t k) -> bool {
         if (d >= D) return false;

@@ -316,6 +316,20 @@ ACCURACY_GRIDS = ("uniform", "ball", "band", "star")
 STAR = [(0.5, 0.5, 0.5, 0.237), (0.079, 6.0, 3.0, 0.0)]
 
 
+def paper_grid(kind: str, n0: int, depth: int = 2) -> OctreeDesc:
+    """The sphere and star grids of Sec. 4.1 as the paper builds them: the base grid n0^3
+    (n0 = 8 * 2^l0) cut into 8^3 tiles, a tile refined while it meets the surface, down
+    to `depth` levels below the base, 2:1 balance kept per tile.  A tile meets the sphere
+    when the sphere's signed distance changes sign on it (exact box test), the star when
+    the star function does among the tile's 27 lattice points.  The sphere grids have
+    exactly the leaf counts of Table 1 (1.64453 Mi at 64~256, 7.55078 Mi at 128~512)."""
+    if kind == "sphere":
+        return OctreeDesc(n0, depth, REFINE_SDF_BAND, band=0.0, spheres=[(0.5, 0.5, 0.5, 0.25)], tile_log2=3)
+    if kind == "star":
+        return OctreeDesc(n0, depth, REFINE_STAR_BAND, band=0.0, spheres=list(STAR), tile_log2=3)
+    raise ValueError(kind)
+
+
 def accuracy_desc(kind: str, n0: int) -> OctreeDesc:
     """Grids of the accuracy studies: uniform n0^3; n0^3 with cells whose centre lies
     within 0.25 of the cube centre refined once; n0^3 refined twice within 0.05 of the
@@ -348,24 +362,27 @@ def laplacian_problem(kind: str, n0: int) -> Problem:
 TANK_BC = (NEUMANN, NEUMANN, NEUMANN, DIRICHLET, NEUMANN, NEUMANN)   # open to air at y = 1
 
 
-def tank(obstacle: str, n0: int, inactive: bool = True) -> Problem:
+def tank(obstacle: str, n0: int, inactive: bool = True, tiles: bool = False) -> Problem:
     """Static tank (Sec. 4.4): liquid filling [0,1]^3, solid bottom and sides (Neumann),
     open to air at the top (y = 1: zero-pressure Dirichlet), a solid obstacle (sphere of
-    radius 0.25 or the star of Sec. 4.1) at the centre with fluid-fraction beta; the grid
-    is refined two levels where cells meet the obstacle's surface; rhs = the integrated
-    divergence of the uniform velocity (0, -1, 0) (no flux through the solid walls, inflow
-    through the open top).  inactive: beta is the exact fraction (cells inside the solid
-    drop out, as in the paper's solver); otherwise the fraction clamped at 1e-3."""
+    radius 0.25 or the star of Sec. 4.1) at the centre with fluid-fraction beta; rhs = the
+    integrated divergence of the uniform velocity (0, -1, 0) (no flux through the solid
+    walls, inflow through the open top).  inactive: beta is the exact fraction (cells
+    inside the solid drop out, as in the paper's solver); otherwise the fraction clamped
+    at 1e-3.  The grid is refined two levels near the obstacle's surface: cell by cell
+    where cells meet the surface, or with tiles=True by the paper's 8^3 tiles
+    (paper_grid; roots of 32 and more)."""
     kind = "cut_exact" if inactive else "cut"
     tag = "" if inactive else "_clamped"
     if obstacle == "sphere":
         sph = (0.5, 0.5, 0.5, 0.25)
-        d = OctreeDesc(n0, 2, REFINE_SDF_BAND, band=0.0, spheres=[sph])
-        return Problem("tank_sphere%d%s" % (n0, tag), d, TANK_BC, beta=kind, rhs="tank", mode="mixed",
-                       tol=1e-6, mu=2, solid_spheres=[sph])
+        d = paper_grid("sphere", n0) if tiles else OctreeDesc(n0, 2, REFINE_SDF_BAND, band=0.0, spheres=[sph])
+        return Problem("tank_sphere%d%s%s" % (n0, tag, "_tiles" if tiles else ""), d, TANK_BC, beta=kind,
+                       rhs="tank", mode="mixed", tol=1e-6, mu=2, solid_spheres=[sph])
     if obstacle == "star":
-        return Problem("tank_star%d%s" % (n0, tag), accuracy_desc("star", n0), TANK_BC, beta=kind, rhs="tank",
-                       mode="mixed", tol=1e-6, mu=2, solid_star=list(STAR))
+        d = paper_grid("star", n0) if tiles else accuracy_desc("star", n0)
+        return Problem("tank_star%d%s%s" % (n0, tag, "_tiles" if tiles else ""), d, TANK_BC, beta=kind,
+                       rhs="tank", mode="mixed", tol=1e-6, mu=2, solid_star=list(STAR))
     raise ValueError(obstacle)
 
 

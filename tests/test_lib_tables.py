@@ -45,6 +45,10 @@ def _descs():
     yield P.OctreeDesc(16, 2, P.REFINE_SDF_BAND, band=0.0, spheres=[(0.5, 0.5, 0.5, 0.25)], tile_log2=2)
     yield P.OctreeDesc(8, 3, P.REFINE_STAR_BAND, band=0.0, spheres=list(P.STAR), tile_log2=1)
     yield P.OctreeDesc(8, 2, P.REFINE_SINE_BAND, band=0.02, sines=P.sine_waves(), tile_log2=2)
+    yield P.paper_grid("sphere", 32)      # exact box test of the sphere, 2:1 balance per tile
+    yield P.paper_grid("star", 32)        # 27-point star test
+    yield P.OctreeDesc(16, 2, P.REFINE_SDF_BAND, band=0.01, spheres=[(0.3, 0.4, 0.55, 0.17)],
+                       boxes=[(0.6, 0.1, 0.2, 0.9, 0.35, 0.6)], tile_log2=1)
 
 
 @pytest.mark.parametrize("desc", list(_descs()))
@@ -83,6 +87,15 @@ def test_faces_bit_exact_when_a_group_is_merged_in_several_chunks():
     fo = O.Octree(desc).faces()
     for k in ("axis", "depth", "i", "j", "k", "minus", "plus"):
         assert np.array_equal(fo[k], fg[k]), k
+
+
+def test_paper_grids_at_128_have_the_leaf_counts_of_table1():
+    # Table 1 (Sec. 4.5), 128~512 grids, in units of 2^20 leaves: sphere exactly, star
+    # within 2 % (the bit-exact tables against the oracle are checked at a 32^3 root)
+    import json
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_worked_values.json")))["table1_leaf_counts"]
+    assert round(S.Octree(P.paper_grid("sphere", 128)).n_leaves / 2 ** 20, 5) == gold["sphere_128_512"]
+    assert abs(S.Octree(P.paper_grid("star", 128)).n_leaves / 2 ** 20 / gold["star_128_512"] - 1.0) < 0.02
 
 
 def test_config_leaf_counts():

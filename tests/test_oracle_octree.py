@@ -108,3 +108,18 @@ def test_ball_centre_predicate_exact():
     assert list(sel) == [True, True, False, False]
     t = O.Octree(d)
     assert len(t.refined[0]) == 8 and t.n_leaves == 64 + 7 * 8
+
+
+def test_paper_grids_have_the_leaf_counts_of_table1():
+    # Sec. 4.1's grids (8^3 tiles refined while they meet the surface, two levels, 2:1 per
+    # tile) against Table 1's leaf counts in units of 2^20: the sphere grid exactly; the
+    # star grid, whose tile test the paper leaves open, within 2 %
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_worked_values.json")))
+    gold = gold["table1_leaf_counts"]
+    t = O.Octree(P.paper_grid("sphere", 64))
+    assert round(t.n_leaves / 2 ** 20, 5) == gold["sphere_64_256"]
+    t = O.Octree(P.paper_grid("star", 64))
+    assert abs(t.n_leaves / 2 ** 20 / gold["star_64_256"] - 1.0) < 0.02
+
