@@ -298,28 +298,6 @@ void HostTree::cell_coords(int m, int64_t g, int64_t& i, int64_t& j, int64_t& k)
     k = 2 * (int64_t)K + ((s >> 2) & 1);
 }
 
-// Allocator whose element construction without arguments leaves trivially constructible
-// values uninitialised, for large work arrays that a parallel pass fills completely: a
-// value-initialising resize would zero them on one thread first.
-template <class T>
-struct NoInitAlloc : std::allocator<T> {
-    template <class U>
-    struct rebind {
-        using other = NoInitAlloc<U>;
-    };
-    NoInitAlloc() = default;
-    template <class U>
-    NoInitAlloc(const NoInitAlloc<U>&) noexcept {}
-    template <class U>
-    void construct(U* p) noexcept {
-        ::new ((void*)p) U;
-    }
-    template <class U, class... A>
-    void construct(U* p, A&&... a) {
-        ::new ((void*)p) U(std::forward<A>(a)...);
-    }
-};
-
 // Parallel stream compaction: out = [value(c) for c in 0..n-1 if keep(c)], in order.
 // pred(c, value&) returns keep and fills value.
 template <class V, class F>
@@ -863,8 +841,7 @@ static void build_impl(const ocg_octree_desc& desc, HostTree& T, const HostTree*
     }
     for (size_t q = 0; q < gcount.size(); ++q) gbase[q + 1] = gbase[q] + gcount[q];
     T.nface = gbase.back();
-    // (the arrays are sized in parallel: zero-filling ~19 bytes per face on one thread took
-    // longer than the merge itself)
+    // (sized without initialisation: the merge below writes every entry, in parallel)
 #pragma omp parallel sections
     {
 #pragma omp section

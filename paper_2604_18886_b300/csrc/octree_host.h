@@ -13,12 +13,38 @@
 #pragma once
 
 #include <cstdint>
+#include <memory>
+#include <new>
+#include <utility>
 #include <string>
 #include <vector>
 
 #include "../../include/ocg.h"
 
 namespace ocg {
+
+// Allocator whose element construction without arguments leaves trivially constructible
+// values uninitialised, for large work arrays that a parallel pass fills completely: a
+// value-initialising resize would zero them on one thread first.
+template <class T>
+struct NoInitAlloc : std::allocator<T> {
+    template <class U>
+    struct rebind {
+        using other = NoInitAlloc<U>;
+    };
+    NoInitAlloc() = default;
+    template <class U>
+    NoInitAlloc(const NoInitAlloc<U>&) noexcept {}
+    template <class U>
+    void construct(U* p) noexcept {
+        ::new ((void*)p) U;
+    }
+    template <class U, class... A>
+    void construct(U* p, A&&... a) {
+        ::new ((void*)p) U(std::forward<A>(a)...);
+    }
+};
+
 
 struct LevelMeta {
     int m = 0;        // level index (depth for m >= 0)
@@ -63,10 +89,12 @@ struct HostTree {
     // canonical leaves
     std::vector<int32_t> leaf_depth, leaf_i, leaf_j, leaf_k;
     // canonical faces (the + cell's coordinates follow from the leaves: face_plus_cell)
-    std::vector<int8_t> f_axis, f_depth;
-    std::vector<int32_t> f_minus, f_plus;  // canonical leaf ranks of the two sides
-    std::vector<int64_t> f_slot;     // destination of -beta*h (see setup kernel)
-    std::vector<uint8_t> f_kind;     // 0: c_{a-} of a cell, 1: T record + face weight
+    // (uninitialised on resize: the parallel merge writes every entry, and zero-filling
+    // ~19 bytes per face first cost more than the merge)
+    std::vector<int8_t, NoInitAlloc<int8_t>> f_axis, f_depth;
+    std::vector<int32_t, NoInitAlloc<int32_t>> f_minus, f_plus;  // canonical leaf ranks of the two sides
+    std::vector<int64_t, NoInitAlloc<int64_t>> f_slot;     // destination of -beta*h (see setup kernel)
+    std::vector<uint8_t, NoInitAlloc<uint8_t>> f_kind;     // 0: c_{a-} of a cell, 1: T record + face weight
 
     const LevelMeta& L(int m) const { return lv[m - mc]; }
     LevelMeta& L(int m) { return lv[m - mc]; }
