@@ -411,7 +411,15 @@ def _ball(dev, stream, flush, args, peak, peak_kind):
         h.solve(b, x, tol=1e-6, precision="mixed", stream=stream)
     steps = max(3, min(args.steps, 20))
     sizes = [g.level_size(m) for m in range(g.D, g.mc - 1, -1)]
-    rm = _timed(stream, flush, lambda: h.solve(b, x, tol=1e-6, precision="mixed", stream=stream)[1], steps)
+    if args.nvtx:
+        torch.cuda.nvtx.range_push("timed")
+    rm = _timed(stream, flush, lambda: h.solve(b, x, tol=1e-6, precision="mixed", stream=stream,
+                                               eager=args.eager)[1], steps)
+    if args.nvtx:
+        torch.cuda.nvtx.range_pop()
+    if args.only_ball and args.nvtx:
+        return {"value": round(g.n_leaves / (statistics.mean(t for t, _ in rm) / 1e3) / 1e6, 3),
+                "note": "--only-ball --nvtx (profiling aid)"}
     r32 = _timed(stream, flush, lambda: h.solve(b, x, tol=1e-6, precision="fp32", stream=stream)[1], steps)
     out = _form(g.n_leaves, rm, peak, lambda k: model_bytes(sizes, g.n_tree, k, "mixed"))
     out["plain_fp32"] = _form(g.n_leaves, r32, peak, lambda k: model_bytes(sizes, g.n_tree, k, "fp32"))
@@ -545,10 +553,10 @@ def _tank(dev, stream, flush, args):
     from paper_2604_18886_b300 import problems as P
     from paper_2604_18886_b300 import solver as S
     out = {}
-    cases = [(o, n0, True) for o in ("sphere", "star") for n0 in (64, 128)] + \
-        [(o, 64, False) for o in ("sphere", "star")]
-    for obstacle, n0, inactive in cases:
-        p = P.tank(obstacle, n0, inactive)
+    cases = [(o, n0, True, t) for t in (False, True) for o in ("sphere", "star") for n0 in (64, 128)] + \
+        [(o, 64, False, False) for o in ("sphere", "star")]
+    for obstacle, n0, inactive, tiles in cases:
+        p = P.tank(obstacle, n0, inactive, tiles)
         g = S.Octree(p.desc)
         f = g.faces()
         beta = P.face_beta(p, f)
@@ -579,7 +587,8 @@ def _tank(dev, stream, flush, args):
                                 "div_rms_ratio": rms(div) / rms(b / V)}
             del h
         row["solid_cells"] = "inactive (exact fractions)" if inactive else "beta clamped at 1e-3"
-        out["%s_%d%s" % (obstacle, n0, "" if inactive else "_clamped")] = row
+        row["grid"] = "8^3 tiles (Sec. 4.1)" if tiles else "cells meeting the surface"
+        out["%s_%d%s%s" % (obstacle, n0, "" if inactive else "_clamped", "_tiles" if tiles else "")] = row
     return {"cases": out,
             "what": "static tank, mixed solves to 1e-6; with the solid interior at beta 1e-3 the exact "
                     "discrete pressure is y - 1 (the uniform velocity is minus the gradient of a linear "
@@ -724,6 +733,21 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 cycle + f64 pcg", "data": "synthetic"}
     if args.only_timed:
+        if args.adjoint:
+            # one transpose solve (tables built and graph captured by an untimed first call),
+            # then one more inside the NVTX range 'adjoint' (kernel by kernel with --eager)
+            import numpy as np
+            gp = x - torch.from_numpy(np.random.default_rng(8).standard_normal(g.n_leaves)).to(dev)
+            h.solve(gp, tol=1e-6, precision="mixed", stream=stream, transpose=True, max_iter=200)
+            torch.cuda.synchronize()
+            if args.nvtx:
+                torch.cuda.nvtx.range_push("adjoint")
+            _, sa = h.solve(gp, tol=1e-6, precision="mixed", stream=stream, transpose=True, max_iter=200,
+                            eager=args.eager)
+            torch.cuda.synchronize()
+            if args.nvtx:
+                torch.cuda.nvtx.range_pop()
+            head["adjoint_iterations"] = sa.iterations
         if rank == 0:
             head["note"] = "--only-timed (profiling aid)"
             print(json.dumps(head), flush=True)
@@ -920,6 +944,8 @@ def main():
     ap.add_argument("--only-timed", action="store_true",
                     help="the large workload's warm-up and timed solves only (profiling aid)")
     ap.add_argument("--only-ball", action="store_true", help="the two-level ball workload only (profiling aid)")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="with --only-timed: also one transpose solve in the NVTX range 'adjoint' (profiling aid)")
     ap.add_argument("--sweep", default="auto", choices=["auto", "octet", "cell", "quad", "tile"],
                     help="sweep form of the large workload's hierarchy (auto: timed at set-up; profiling aid)")
     ap.add_argument("--large-n0", type=int, default=128,

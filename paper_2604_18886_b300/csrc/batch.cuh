@@ -350,7 +350,8 @@ __global__ void __launch_bounds__(OBLK2) kb_oapply(const BProb* __restrict__ PP,
     double* Y = which ? P.yt : P.Ap;
     DF dot{0.0f, 0.0f};
     if (!skip && o < A.ncell / 8)
-        layer_apply_df(P.T, P.C, P.rem, P.flags, V, Y, A.off, A.ni, o, threadIdx.x & 1, 3u << (threadIdx.x & 30), dot);
+        layer_apply_df(P.T, P.C, P.rem, P.flags, VecD{V}, OutD{Y}, A.off, A.ni, o, threadIdx.x & 1,
+                       3u << (threadIdx.x & 30), dot);
     if (which == 0) bred_finish<2>(PP, w.prob, (int)blockIdx.x - P.ab0, P.nba, R, df_to_double(dot), 0.0, 0.0, sh);
 }
 

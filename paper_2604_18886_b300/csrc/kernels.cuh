@@ -399,6 +399,69 @@ __global__ void __launch_bounds__(BLK) k_update(TO* __restrict__ x, TO* __restri
     red_finish(R, blockIdx.x, rr, rs, sh);
 }
 
+// The update of k_update for the mixed PCG, whose p is kept as FP32 pairs (hi, lo) that
+// the outer apply reads without conversion: x += alpha p (p = hi + lo exactly in
+// binary64), r -= alpha A p, ||r||^2 (and sum r); four elements per thread and pass.
+template <bool SUM>
+__global__ void __launch_bounds__(BLK) k_update_pp(double* __restrict__ x, double* __restrict__ r,
+                                                   const float* __restrict__ phi, const float* __restrict__ plo,
+                                                   const double* __restrict__ Ap, float* __restrict__ b32, int n,
+                                                   Red R) {
+    pdl_enter();
+    __shared__ double sh[32];
+    const double alpha = R.S[S_ALPHA];
+    double rr = 0.0, rs = 0.0;
+    const int st = gridDim.x * BLK;
+    int i = blockIdx.x * BLK + threadIdx.x;
+    for (; i + 3 * st < n; i += 4 * st) {
+        double xv[4], rv[4], av[4];
+        float hv[4], lv[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            xv[q] = x[i + q * st]; rv[q] = r[i + q * st]; av[q] = Ap[i + q * st];
+            hv[q] = phi[i + q * st]; lv[q] = plo[i + q * st];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            x[i + q * st] = xv[q] + alpha * (f2d_bits(hv[q]) + f2d_bits(lv[q]));
+            const double rn = rv[q] - alpha * av[q];
+            r[i + q * st] = rn;
+            if (b32) b32[i + q * st] = d2f_bits(rn);
+            rr += rn * rn;
+            if (SUM) rs += rn;
+        }
+    }
+    for (; i < n; i += st) {
+        x[i] = x[i] + alpha * (f2d_bits(phi[i]) + f2d_bits(plo[i]));
+        const double rn = r[i] - alpha * Ap[i];
+        r[i] = rn;
+        if (b32) b32[i] = d2f_bits(rn);
+        rr += rn * rn;
+        if (SUM) rs += rn;
+    }
+    red_finish(R, blockIdx.x, rr, rs, sh);
+}
+
+// p = z + beta p (first: p = z) for p kept as FP32 pairs, in pair arithmetic (beta split
+// once, TwoProd by FMA, TwoSum; about 2^-47 relative, no FP64 instruction): the same p
+// then enters both x += alpha p and the apply, so CG's recurrences stay consistent.
+template <class TZ>
+__global__ void k_pupdate_pp(float* __restrict__ hi, float* __restrict__ lo, const TZ* __restrict__ z,
+                             const double* __restrict__ S, int n, int first) {
+    pdl_enter();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float zi = (float)z[i];
+    DF v{zi, 0.0f};
+    if (!first) {
+        v = df_mul(df_split(S[S_BETA]), DF{hi[i], lo[i]});
+        df_acc_f(v, zi);
+        v = df_norm(v);
+    }
+    hi[i] = v.hi;
+    lo[i] = v.lo;
+}
+
 // r -= mean on leaves (null-space shift of Sec. 2.2) and b32 = r.
 template <class TO, class TB>
 __global__ void k_project(TO* __restrict__ r, const uint8_t* __restrict__ flags, const double* __restrict__ S,

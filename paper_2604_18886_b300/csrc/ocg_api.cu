@@ -82,8 +82,8 @@ T* dalloc(int64_t n) {
     return (T*)p;
 }
 
-template <class T>
-T* dupload(const std::vector<T>& v) {
+template <class T, class A>
+T* dupload(const std::vector<T, A>& v) {
     T* p = dalloc<T>((int64_t)v.size());
     if (!v.empty()) ck(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice), "upload");
     return p;
@@ -871,10 +871,32 @@ void apply_outer(ocg_hier* h, Coefs<TC, TW> C, TO* P, TO* Y, int op, Ctx& c) {
         if constexpr (std::is_same<TO, double>::value && std::is_same<TC, float>::value) {
             const int nb2 = std::min(ML.boff[ML.n], 8 * sm_count());
             const Red R2 = make_red(h, nb2, op);
-            launch_k(k_oapply_df2, nb2, OBLK2, 0, c.st, ML, t->tables(), C, (const float*)h->rem32,
-                     (const uint8_t*)t->flags, P, Y, R2);
+            launch_k(k_oapply_df2<VecD, OutD>, nb2, OBLK2, 0, c.st, ML, t->tables(), C, (const float*)h->rem32,
+                     (const uint8_t*)t->flags, VecD{P}, OutD{Y}, R2);
         } else
             launch_k(k_oapply<TO, TC, TW>, nb, OBLK, 0, c.st, ML, t->tables(), C, P, Y, R);
+    });
+    ck_launch("apply");
+}
+
+// The mixed PCG's outer apply on p kept as FP32 pairs P = (ph, pl), the two halves of a
+// tree-cell array (inner cells get the child means in pair form); Y in FP64.
+void apply_outer_pp(ocg_hier* h, Coefs<float, float> C, float* ph, float* pl, double* Y, int op, Ctx& c) {
+    const ocg_octree* t = h->t;
+    const HostTree& H = t->H;
+    for (int m = H.D; m >= 1; --m) {
+        const LevelArgs A = t->largs(m);
+        launch(c, -1, m, A.ncell, [&] {
+            launch_k(k_oavg_pp<float>, nblk(A.ncell / 8, OBLK), OBLK, 0, c.st, A, t->tables(), C.d, ph, pl);
+        });
+    }
+    ck_launch("avg");
+    const OMultiLevel ML = tree_levels(H);
+    const int nb = std::min(ML.boff[ML.n], 8 * sm_count());
+    const Red R = make_red(h, nb, op);
+    launch(c, OCG_PROBE_APPLY, 0, H.ntree, [&] {
+        launch_k(k_oapply_df2<VecP, OutD>, nb, OBLK2, 0, c.st, ML, t->tables(), C, (const float*)h->rem32,
+                 (const uint8_t*)t->flags, VecP{ph, pl}, OutD{Y}, R);
     });
     ck_launch("apply");
 }
@@ -940,6 +962,20 @@ struct PcgImpl {
     unsigned gb() const { return nblk(H().ntree); }
     unsigned rb() const { return std::min<unsigned>(nblk(H().ntree), (unsigned)h->red_blocks); }
     void zero(void* ptr, size_t bytes) { ck(cudaMemsetAsync(ptr, 0, bytes, c.st), "memset"); }
+    // the mixed forward solve keeps p as FP32 pairs: hi in the first n floats of the FP64
+    // array, lo in the next n
+    static constexpr bool PP = !TR && std::is_same<TO, double>::value && std::is_same<TC, float>::value;
+    float* hi(double* v) { return (float*)v; }
+    float* lo(double* v) { return (float*)v + n(); }
+    void pupdate(int first) {
+        launch(c, -1, 0, n(), [&] {
+            if constexpr (PP)
+                launch_k(k_pupdate_pp<TV>, gb(), BLK, 0, c.st, hi(h->p), lo(h->p), (const TV*)Z(), (const double*)h->S,
+                         n(), first);
+            else
+                launch_k(k_pupdate<TO, TV>, gb(), BLK, 0, c.st, p(), Z(), h->S, n(), first);
+        });
+    }
 
     void begin() {
         if (warm) launch(c, -1, 0, n(), [&] { launch_k(k_cast<double, TO>, gb(), BLK, 0, c.st, h->xt, x(), n()); });
@@ -958,7 +994,7 @@ struct PcgImpl {
         ck_launch("begin");
         precondition();
         launch(c, -1, 0, n(), [&] { launch_k(k_dot<TO, TV, false>, rb(), BLK, 0, c.st, r(), Z(), n(), make_red(h, rb(), OP_RZ0)); });
-        launch(c, -1, 0, n(), [&] { launch_k(k_pupdate<TO, TV>, gb(), BLK, 0, c.st, p(), Z(), h->S, n(), 1); });
+        pupdate(1);
         ck_launch("begin");
         half_a();
     }
@@ -976,11 +1012,21 @@ struct PcgImpl {
     }
     void half_a() {
         if constexpr (TR) apply_outer_T<TO, TC, TW>(h, Co, p(), Ap(), c, OP_ALPHA);
+        else if constexpr (PP) apply_outer_pp(h, Co, hi(h->p), lo(h->p), h->Ap, OP_ALPHA, c);
         else apply_outer<TO, TC, TW>(h, Co, p(), Ap(), OP_ALPHA, c);
         launch(c, -1, 0, n(), [&] {
             const Red R = make_red(h, rb(), OP_RR, cond, set_cond);
-            if (ns) launch_k(k_update<TO, TV, true>, rb(), BLK, 0, c.st, x(), r(), p(), Ap(), nullptr, n(), R);
-            else launch_k(k_update<TO, TV, false>, rb(), BLK, 0, c.st, x(), r(), p(), Ap(), B(), n(), R);
+            if constexpr (PP) {
+                if (ns)
+                    launch_k(k_update_pp<true>, rb(), BLK, 0, c.st, h->x, h->r, (const float*)hi(h->p),
+                             (const float*)lo(h->p), (const double*)h->Ap, (float*)nullptr, n(), R);
+                else
+                    launch_k(k_update_pp<false>, rb(), BLK, 0, c.st, h->x, h->r, (const float*)hi(h->p),
+                             (const float*)lo(h->p), (const double*)h->Ap, (float*)B(), n(), R);
+            } else {
+                if (ns) launch_k(k_update<TO, TV, true>, rb(), BLK, 0, c.st, x(), r(), p(), Ap(), nullptr, n(), R);
+                else launch_k(k_update<TO, TV, false>, rb(), BLK, 0, c.st, x(), r(), p(), Ap(), B(), n(), R);
+            }
         });
         if (ns)
             launch(c, -1, 0, n(), [&] { launch_k(k_project<TO, TV>, gb(), BLK, 0, c.st, r(), h->t->flags, h->S, B(), n()); });
@@ -989,7 +1035,7 @@ struct PcgImpl {
     void half_b() {
         precondition();
         launch(c, -1, 0, n(), [&] { launch_k(k_dot<TO, TV, false>, rb(), BLK, 0, c.st, r(), Z(), n(), make_red(h, rb(), OP_BETA)); });
-        launch(c, -1, 0, n(), [&] { launch_k(k_pupdate<TO, TV>, gb(), BLK, 0, c.st, p(), Z(), h->S, n(), 0); });
+        pupdate(0);
         ck_launch("half_b");
     }
     void body() {

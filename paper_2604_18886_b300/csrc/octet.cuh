@@ -829,6 +829,30 @@ __global__ void __launch_bounds__(OBLK) k_oavg(LevelArgs A, Tables T, const TC* 
     P[__ldg(T.oct_parent + (c8 >> 3))] = s * inv_count<TO>(n);
 }
 
+// The same child means for a vector kept as FP32 pairs (hi, lo): sum and division in pair
+// arithmetic, the parent written as a normalised pair.
+template <class TC>
+__global__ void __launch_bounds__(OBLK) k_oavg_pp(LevelArgs A, Tables T, const TC* __restrict__ d,
+                                                  float* __restrict__ hi, float* __restrict__ lo) {
+    pdl_enter();
+    const int o = blockIdx.x * OBLK + threadIdx.x;
+    if (o >= A.ncell / 8) return;
+    const int c8 = A.off + 8 * o;
+    float h[8], l[8], dd[8];
+    ld8(hi + c8, h);
+    ld8(lo + c8, l);
+    ldc8(d + c8, dd);
+    DF s{0.0f, 0.0f};
+    int n = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+        if (dd[q] != 0.0f) { df_acc(s, DF{h[q], l[q]}); ++n; }
+    const DF m = df_norm(df_div_count(s, n));
+    const int par = __ldg(T.oct_parent + (c8 >> 3));
+    hi[par] = m.hi;
+    lo[par] = m.lo;
+}
+
 // Composite leaf operator over all tree levels in one launch (block -> level lookup):
 // Y = A p on leaves, 0 on inner cells; (p, A p) over leaves reduced into R.
 struct OMultiLevel {
@@ -1006,32 +1030,73 @@ __device__ __forceinline__ DF shfl_df(unsigned m, DF v) {
     return DF{__shfl_xor_sync(m, v.hi, 1), __shfl_xor_sync(m, v.lo, 1)};
 }
 
+// Vectors of the outer apply.  VecD: binary64 values, split into pairs on load (48 bits
+// kept).  VecP: the pair itself in two FP32 arrays hi, lo (value hi + lo, exact in
+// binary64), the form in which the mixed PCG keeps its search direction p, so that the
+// apply does not split.  OutD: results rounded back to binary64.
+struct VecD {
+    const double* __restrict__ p;
+    __device__ __forceinline__ DF one(int i) const { return df_split(p[i]); }
+    __device__ __forceinline__ void two(int i, DF& a, DF& b) const {
+        const double2 v = *reinterpret_cast<const double2*>(p + i);
+        a = df_split(v.x);
+        b = df_split(v.y);
+    }
+    __device__ __forceinline__ void four(int i, DF (&v)[4]) const {
+        two(i, v[0], v[1]);
+        two(i + 2, v[2], v[3]);
+    }
+};
+struct VecP {
+    const float* __restrict__ hi;
+    const float* __restrict__ lo;
+    __device__ __forceinline__ DF one(int i) const { return DF{hi[i], lo[i]}; }
+    __device__ __forceinline__ void two(int i, DF& a, DF& b) const {
+        const float2 h = *reinterpret_cast<const float2*>(hi + i), l = *reinterpret_cast<const float2*>(lo + i);
+        a = DF{h.x, l.x};
+        b = DF{h.y, l.y};
+    }
+    __device__ __forceinline__ void four(int i, DF (&v)[4]) const {
+        const float4 h = *reinterpret_cast<const float4*>(hi + i), l = *reinterpret_cast<const float4*>(lo + i);
+        v[0] = DF{h.x, l.x}; v[1] = DF{h.y, l.y}; v[2] = DF{h.z, l.z}; v[3] = DF{h.w, l.w};
+    }
+};
+struct OutD {
+    double* __restrict__ y;
+    __device__ __forceinline__ void zero4(int i) const {
+        reinterpret_cast<double4*>(y + i)[0] = make_double4(0.0, 0.0, 0.0, 0.0);
+    }
+    // a normalised pair per cell, 0 where keep is false
+    __device__ __forceinline__ void put4(int i, const DF (&v)[4], int keep) const {
+        double w[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) w[q] = ((keep >> q) & 1) ? df_to_double(v[q]) : 0.0;
+        reinterpret_cast<double4*>(y + i)[0] = make_double4(w[0], w[1], w[2], w[3]);
+    }
+};
 // One z layer (4 cells, slots 4z..4z+3) of the pair-of-FP32 outer apply: the two lanes
 // of a pair (mask pm) hold the two layers of one octet and trade their values for the
 // faces between the layers.  Per face: the exact difference of the two values by TwoSum,
 // its product with the FP32 coefficient by FMA, pair accumulation; the diagonal enters as
 // the remainder from k_remainder, the leaf flags come from the 1-byte cell flags.
+template <class V, class O>
 __device__ __forceinline__ void layer_apply_df(const Tables& T, const Coefs<float, float>& C,
                                                const float* __restrict__ rem, const uint8_t* __restrict__ flags,
-                                               const double* __restrict__ P, double* __restrict__ Y, int off,
-                                               int ni, int o, int z, unsigned pm, DF& dot) {
+                                               const V& P, const O& Y, int off, int ni, int o, int z, unsigned pm,
+                                               DF& dot) {
     const int c8 = off + 8 * o, og = c8 >> 3, cz0 = c8 + 4 * z;
     const uint32_t fl = __ldg(reinterpret_cast<const uint32_t*>(flags + cz0));
     const int leafm = (int)((fl & 1u) | ((fl >> 7) & 2u) | ((fl >> 14) & 4u) | ((fl >> 21) & 8u));
     const int leafo = __shfl_xor_sync(pm, leafm, 1);
     if ((leafm | leafo) == 0) {
         // no leaf in the octet: the composite operator has no row here
-        reinterpret_cast<double4*>(Y + cz0)[0] = make_double4(0.0, 0.0, 0.0, 0.0);
+        Y.zero4(cz0);
         return;
     }
     int nb[6];
     octet_neighbours(T, ni, o, og, nb);
     DF u[4], uo[4], acc[4];
-    {
-        const double2 v0 = reinterpret_cast<const double2*>(P + cz0)[0];
-        const double2 v1 = reinterpret_cast<const double2*>(P + cz0)[1];
-        u[0] = df_split(v0.x); u[1] = df_split(v0.y); u[2] = df_split(v1.x); u[3] = df_split(v1.y);
-    }
+    P.four(cz0, u);
 #pragma unroll
     for (int q = 0; q < 4; ++q) { uo[q] = shfl_df(pm, u[q]); acc[q] = DF{0.0f, 0.0f}; }
     const float4 cx = ldg4(C.cx + cz0), cy = ldg4(C.cy + cz0), czv = ldg4(C.cz + cz0);
@@ -1084,14 +1149,17 @@ __device__ __forceinline__ void layer_apply_df(const Tables& T, const Coefs<floa
         const float* cg = a == 0 ? C.cx : C.cy;
         const int v = nb[2 * a];
         if (v >= 0) {
-            const double* pn = P + off + 8 * v + 4 * z;
+            const int pn = off + 8 * v + 4 * z;
+            DF nv[2];
+            if (a == 0) { nv[0] = P.one(pn + 1); nv[1] = P.one(pn + 3); }
+            else P.two(pn + 2, nv[0], nv[1]);
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
                 const int q = a == 0 ? 2 * k : k;            // cells with the bit clear
-                df_acc(acc[q], df_scale(df_diff(u[q], df_split(pn[q | bit])), -f4at(cown, q)));
+                df_acc(acc[q], df_scale(df_diff(u[q], nv[k]), -f4at(cown, q)));
             }
         } else if (v <= -2) {
-            const DF gk = df_diff(df_split(P[-2 - v]), ubar);
+            const DF gk = df_diff(P.one(-2 - v), ubar);
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
                 const int q = a == 0 ? 2 * k : k;
@@ -1101,14 +1169,17 @@ __device__ __forceinline__ void layer_apply_df(const Tables& T, const Coefs<floa
         const int w = nb[2 * a + 1];
         if (w >= 0) {
             const int n8 = off + 8 * w + 4 * z;
+            DF nv[2];
+            if (a == 0) { nv[0] = P.one(n8); nv[1] = P.one(n8 + 2); }
+            else P.two(n8, nv[0], nv[1]);
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
                 const int q = a == 0 ? 2 * k + 1 : k + 2;    // cells with the bit set
                 const int qn = q & ~bit;
-                df_acc(acc[q], df_scale(df_diff(u[q], df_split(P[n8 + qn])), -__ldg(cg + n8 + qn)));
+                df_acc(acc[q], df_scale(df_diff(u[q], nv[k]), -__ldg(cg + n8 + qn)));
             }
         } else if (w <= -2) {
-            const DF gk = df_diff(df_split(P[-2 - w]), ubar);
+            const DF gk = df_diff(P.one(-2 - w), ubar);
             const int t = __ldg(T.trec + og);
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
@@ -1125,15 +1196,15 @@ __device__ __forceinline__ void layer_apply_df(const Tables& T, const Coefs<floa
         const int v = z ? nb[5] : nb[4];
         if (v >= 0) {
             const int n8 = off + 8 * v;
-            const double2 w0 = reinterpret_cast<const double2*>(P + n8 + 4 * (1 - z))[0];
-            const double2 w1 = reinterpret_cast<const double2*>(P + n8 + 4 * (1 - z))[1];
+            DF nv[4];
+            P.four(n8 + 4 * (1 - z), nv);
             const float4 cc = z ? ldg4(C.cz + n8) : czv;
-            df_acc(acc[0], df_scale(df_diff(u[0], df_split(w0.x)), -cc.x));
-            df_acc(acc[1], df_scale(df_diff(u[1], df_split(w0.y)), -cc.y));
-            df_acc(acc[2], df_scale(df_diff(u[2], df_split(w1.x)), -cc.z));
-            df_acc(acc[3], df_scale(df_diff(u[3], df_split(w1.y)), -cc.w));
+            df_acc(acc[0], df_scale(df_diff(u[0], nv[0]), -cc.x));
+            df_acc(acc[1], df_scale(df_diff(u[1], nv[1]), -cc.y));
+            df_acc(acc[2], df_scale(df_diff(u[2], nv[2]), -cc.z));
+            df_acc(acc[3], df_scale(df_diff(u[3], nv[3]), -cc.w));
         } else if (v <= -2) {
-            const DF gk = df_diff(df_split(P[-2 - v]), ubar);
+            const DF gk = df_diff(P.one(-2 - v), ubar);
             const int t = z ? __ldg(T.trec + og) : 0;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
@@ -1142,26 +1213,25 @@ __device__ __forceinline__ void layer_apply_df(const Tables& T, const Coefs<floa
             }
         }
     }
-    double y[4];
+    DF out[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const bool leaf = (leafm >> q) & 1;
         DF au = acc[q];
         df_acc(au, df_scale(u[q], f4at(rm, q)));
-        au = df_norm(au);
-        y[q] = leaf ? df_to_double(au) : 0.0;
-        if (leaf) df_acc(dot, df_mul(u[q], au));
+        out[q] = df_norm(au);
+        if (leaf) df_acc(dot, df_mul(u[q], out[q]));
     }
-    reinterpret_cast<double4*>(Y + cz0)[0] = make_double4(y[0], y[1], y[2], y[3]);
+    Y.put4(cz0, out, leafm);
 }
 
 // Y = A P over all tree levels (FP64 vectors, FP32 coefficients), two lanes per octet;
 // (P, A P) over the leaves reduced into R.  Blocks of OBLK2 threads take the octet blocks
 // (64 octets) of OMultiLevel and stride over them.
+template <class V, class O>
 __global__ void __launch_bounds__(OBLK2, 8) k_oapply_df2(OMultiLevel ML, Tables T, Coefs<float, float> C,
                                                          const float* __restrict__ rem,
-                                                         const uint8_t* __restrict__ flags,
-                                                         const double* __restrict__ P, double* __restrict__ Y, Red R) {
+                                                         const uint8_t* __restrict__ flags, V P, O Y, Red R) {
     pdl_enter();
     __shared__ double sh[32];
     DF dot{0.0f, 0.0f};
