@@ -532,12 +532,24 @@ def _batched(dev, stream, flush, args):
     forms = {str(h): ["octet", "cell"][f] for h, (f, a, b) in bt.info().items()}
     kern = rb[-1][1][0].kernels
     del bt
+    # the same batch with W-cycles (mu = 2 for every problem)
+    hw = [S.Hierarchy(h.tree, h._beta, h._bc, S.mg_params(coef="f32", mu=2)) for h in hs]
+    bw = S.Batch(hw, stream=stream)
+    bw.solve(bs, xs, tol=1e-6, stream=stream)
+    rw = _timed(stream, flush, lambda: bw.solve(bs, xs, tol=1e-6, stream=stream)[1], max(3, min(args.steps, 10)))
+    assert all(s.converged for s in rw[-1][1])
+    ms_w = statistics.mean(t for t, _ in rw)
+    w_cycle = {"value": round(leaves / (ms_w / 1e3) / 1e6, 3), "unit": UNIT, "ms_per_step": round(ms_w, 4),
+               "iterations": sorted({s.iterations for _, st in rw for s in st}),
+               "gpu_launches_per_step": rw[-1][1][0].kernels}
+    del bw, hw
     return {"workload": BATCH_WORKLOAD, "problems": 64, "leaves": leaves,
             "value": round(leaves / (ms_b / 1e3) / 1e6, 3), "unit": UNIT, "ms_per_step": round(ms_b, 4),
             "steps": steps, "iterations": its, "gpu_launches_per_step": kern,
             "sweep_forms_by_height": forms, "create_s": round(t_create, 3),
             "sequential_single_solves": {"value": round(leaves / (ms_s / 1e3) / 1e6, 3), "unit": UNIT,
-                                         "ms_per_step": round(ms_s, 4)}}
+                                         "ms_per_step": round(ms_s, 4)},
+            "w_cycle": w_cycle}
 
 
 def _tank(dev, stream, flush, args):

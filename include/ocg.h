@@ -332,12 +332,13 @@ int ocg_pcg_solve(ocg_hier* h, const double* b_dev, double* x_dev, const ocg_sol
 
 /* Batched solves: many independent problems advanced together (no counterpart in the
  * paper).  A batch groups n hierarchies (each set up by ocg_setup_hierarchy with FP32
- * coefficients, no BF16, mu = 1, nu_post >= 1, equal nu / alpha / beta_restrict, and a
- * shared-memory coarse tail, i.e. an even root grid of at least 8 cells per axis).  One
- * launch per phase serves all problems: the V-cycle phases are aligned at the problems'
- * coarse tails (one CTA per problem in a single tail launch); the sweep form of each
- * height above the tails is timed at creation when the first hierarchy's sweep_form is
- * OCG_SWEEP_AUTO.  The batch uses the hierarchies' work vectors: while it exists, do not
+ * coefficients, no BF16, the same mu of 1 or 2 with mu_min_cells 0, nu_post >= 1, equal
+ * nu / alpha / beta_restrict, and a shared-memory coarse tail, i.e. an even root grid of
+ * at least 8 cells per axis).  One launch per phase serves all problems: the cycle's
+ * phases are aligned at the problems' finest levels, so Alg. 4's recursion (mu visits of
+ * the next height per visit) is one schedule for all; the coarse tails that sit at one
+ * height run in one launch (one CTA per problem); the sweep form of each height is
+ * timed at creation when the first hierarchy's sweep_form is OCG_SWEEP_AUTO.  The batch uses the hierarchies' work vectors: while it exists, do not
  * run other solves on those hierarchies concurrently with it, and destroy it before them.
  * Synchronises the stream.  Errors: EINVAL (incompatible hierarchies), ENOMEM, ECUDA. */
 typedef struct ocg_batch ocg_batch;

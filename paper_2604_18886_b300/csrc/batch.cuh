@@ -154,11 +154,14 @@ __global__ void __launch_bounds__(OBLK) kb_orestrict(const BProb* __restrict__ P
 // the coarse tail of every listed problem, one CTA each (dynamic shared memory sized for
 // the largest)
 __global__ void __launch_bounds__(512) kb_otail(const BProb* __restrict__ PP, const BWork* __restrict__ W,
-                                                float scale) {
+                                                float scale, int fas, int prolong) {
     const BWork w = W[blockIdx.x];
     const BProb& P = PP[w.prob];
     if (bdone(P)) return;
-    tail_cycle<float, float, float>(P.tail, w.flags & 1, w.flags & 1, P.T, P.C, P.U, P.B, scale);
+    // a tail that is the problem's finest level (flag 1) is entered from no restriction
+    // and prolongs onto no finer level
+    const int top = w.flags & 1;
+    tail_cycle<float, float, float>(P.tail, top ? 0 : fas, top ? 0 : prolong, P.T, P.C, P.U, P.B, scale);
 }
 
 // ------------------------------------------------------------------ Krylov vectors
@@ -348,10 +351,10 @@ __global__ void __launch_bounds__(OBLK2) kb_oapply(const BProb* __restrict__ PP,
     const int o = ((int)blockIdx.x - w.b0) * OBLK + (threadIdx.x >> 1);
     const double* V = which ? P.xt : P.p;
     double* Y = which ? P.yt : P.Ap;
-    DF dot{0.0f, 0.0f};
+    DF dot{0.0f, 0.0f}, sum{0.0f, 0.0f};
     if (!skip && o < A.ncell / 8)
         layer_apply_df(P.T, P.C, P.rem, P.flags, VecD{V}, OutD{Y}, A.off, A.ni, o, threadIdx.x & 1,
-                       3u << (threadIdx.x & 30), dot);
+                       3u << (threadIdx.x & 30), dot, sum);
     if (which == 0) bred_finish<2>(PP, w.prob, (int)blockIdx.x - P.ab0, P.nba, R, df_to_double(dot), 0.0, 0.0, sh);
 }
 

@@ -1,8 +1,11 @@
 // Host side of the batched form (included by ocg_api.cu after the hierarchy types).
 //
-// The phases of one V-cycle are aligned at the bottom: the coarse tails of all problems
-// run in one launch (one CTA per problem), and the level at height h above a problem's
-// tail is visited together with the levels at height h of the others.  A launch lists
+// The level at height g of a problem is visited together with the levels at height g of
+// the others.  W-cycles align the problems at their finest levels (height H), so that the
+// recursion of Alg. 4 (mu visits of the next height per visit) is one schedule for all,
+// and a problem whose coarse tail sits at height g runs it there (one CTA per problem, one
+// launch per height that holds tails); V-cycles align them at their tails (height 0), and
+// all tails run in one launch.  A launch lists
 // its (problem, level) work items; a block map sends every block to its item.  The sweep
 // form of each height (thread per octet or per cell) is timed at set-up, the faster kept.
 // The whole PCG loop is one CUDA graph with a WHILE node whose condition is "some problem
@@ -23,9 +26,11 @@ struct ocg_batch {
     BProb* dP = nullptr;
     BWork* dW = nullptr;
     int* dI = nullptr;
-    std::vector<Phase> down, up, fixb;   // index h = 1..H
+    std::vector<Phase> down, up, fixb;   // index g = 1..H (height)
+    std::vector<Map> tails;              // index g = 0..H: the coarse tails at height g
     std::vector<Map> avg;                // index m = 1..Dmax
-    Map apply, tail;
+    Map apply;
+    int mu = 1;
     Map vec;                             // vector kernels (items unused)
     int tail_nt = 32;
     size_t tail_smem = 0;
@@ -96,29 +101,37 @@ struct BatchRun {
         else
             go(0, [&] { kb_osweep<<<ph.oct.nb, OBLK, 0, c.st>>>(bt->dP, bt->dW, I(ph.oct), colour, 0); });
     }
-    void cycle() {
+    // Alg. 4 at height g for every problem with a level there; fas: first visit after a
+    // restriction from above, prolong_up: the last visit, whose final operation prolongs
+    // onto height g + 1
+    void cyc(int g, bool fas, bool prolong_up) {
         const ocg_mg_params& P = bt->prm;
         const float scale = (float)(P.beta_restrict / P.alpha);
-        go(0, [&] { kb_zero_u<<<bt->vec.nb, BLK, 0, c.st>>>(bt->dP, I(bt->vec)); });
-        for (int h = bt->H; h >= 1; --h) {
-            const ocg_batch::Phase& f = bt->fixb[h];
-            if (f.oct.nw > 0)
-                go(0, [&] { kb_osweep<<<f.oct.nb, OBLK, 0, c.st>>>(bt->dP, bt->dW, I(f.oct), 0, 1); });
-            for (int it = 0; it < P.nu_pre; ++it) {
-                sweep(h, 0, false, bt->form[h]);
-                sweep(h, 1, false, bt->form[h]);
-            }
-            const ocg_batch::Map& d = bt->down[h].oct;
-            go(0, [&] { kb_orestrict<<<d.nb, OBLK, 0, c.st>>>(bt->dP, bt->dW, I(d), scale); });
+        const ocg_batch::Map& tl = bt->tails[g];
+        if (tl.nw > 0)
+            go(0, [&] {
+                kb_otail<<<tl.nw, bt->tail_nt, bt->tail_smem, c.st>>>(bt->dP, bt->dW + tl.w0, scale, fas ? 1 : 0,
+                                                                         prolong_up ? 1 : 0);
+            });
+        if (g < 1 || bt->down[g].oct.nw == 0) return;
+        const ocg_batch::Phase& f = bt->fixb[g];
+        if (fas && f.oct.nw > 0)
+            go(0, [&] { kb_osweep<<<f.oct.nb, OBLK, 0, c.st>>>(bt->dP, bt->dW, I(f.oct), 0, 1); });
+        for (int it = 0; it < P.nu_pre; ++it) {
+            sweep(g, 0, false, bt->form[g]);
+            sweep(g, 1, false, bt->form[g]);
         }
-        go(0, [&] {
-            kb_otail<<<bt->tail.nw, bt->tail_nt, bt->tail_smem, c.st>>>(bt->dP, bt->dW + bt->tail.w0, scale);
-        });
-        for (int h = 1; h <= bt->H; ++h)
-            for (int it = 0; it < P.nu_post; ++it) {
-                sweep(h, 1, false, bt->form[h]);
-                sweep(h, 0, it == P.nu_post - 1, bt->form[h]);
-            }
+        const ocg_batch::Map& d = bt->down[g].oct;
+        go(0, [&] { kb_orestrict<<<d.nb, OBLK, 0, c.st>>>(bt->dP, bt->dW, I(d), scale); });
+        for (int k = 0; k < bt->mu; ++k) cyc(g - 1, k == 0, k == bt->mu - 1);
+        for (int it = 0; it < P.nu_post; ++it) {
+            sweep(g, 1, false, bt->form[g]);
+            sweep(g, 0, prolong_up && it == P.nu_post - 1, bt->form[g]);
+        }
+    }
+    void cycle() {
+        go(0, [&] { kb_zero_u<<<bt->vec.nb, BLK, 0, c.st>>>(bt->dP, I(bt->vec)); });
+        cyc(bt->H, false, false);
     }
     void apply(int which) {
         for (int m = bt->Dmax; m >= 1; --m) {
@@ -256,7 +269,9 @@ int ocg_batch_create(ocg_hier* const* hs, int32_t n, void* stream, ocg_batch** o
         cudaStream_t st = (cudaStream_t)stream;
         std::unique_ptr<ocg_batch> bt(new ocg_batch());
         bt->n = n;
+        if (!hs[0]) throw Status(OCG_EINVAL, "null hierarchy");
         bt->prm = hs[0]->prm;
+        bt->mu = bt->prm.mu;
         std::vector<BProb> P(n);
         int vb = 0, ab = 0;
         std::vector<int> tops(n);
@@ -268,10 +283,12 @@ int ocg_batch_create(ocg_hier* const* hs, int32_t n, void* stream, ocg_batch** o
                 if (hs[q] == h) throw Status(OCG_EINVAL, "a hierarchy appears twice in the batch");
             const ocg_mg_params& m = h->prm;
             if (!h->c32[0] || m.bf16_coarse) throw Status(OCG_EINVAL, "batched solves need FP32 coefficients");
-            if (m.mu != 1 || m.nu_post < 1 || m.nu_pre != bt->prm.nu_pre || m.nu_post != bt->prm.nu_post ||
+            if (m.mu < 1 || m.mu > 2 || m.mu != bt->prm.mu || m.mu_min_cells != 0 || m.nu_post < 1 ||
+                m.nu_pre != bt->prm.nu_pre || m.nu_post != bt->prm.nu_post ||
                 m.nu_coarsest != bt->prm.nu_coarsest || m.alpha != bt->prm.alpha ||
                 m.beta_restrict != bt->prm.beta_restrict)
-                throw Status(OCG_EINVAL, "batched solves need V-cycles (mu = 1, nu_post >= 1) with equal parameters");
+                throw Status(OCG_EINVAL, "batched solves need V- or W-cycles (mu 1 or 2, mu_min_cells 0, "
+                                         "nu_post >= 1) with equal parameters");
             if (h->tail_top[0] == TAIL_NONE) throw Status(OCG_EINVAL, "every problem needs a shared-memory coarse tail");
             bt->hs.push_back(h);
             const ocg_octree* t = h->t;
@@ -329,23 +346,35 @@ int ocg_batch_create(ocg_hier* const* hs, int32_t n, void* stream, ocg_batch** o
         }
         // work lists
         BatchBuild bb;
+        // heights: for mu = 2 every problem's finest level sits at H (level m of problem p
+        // at height g = H - (D_p - m)), so that the recursion visits each problem's levels
+        // as its own cycle does; for mu = 1 the tails sit at height 0 (m = tops[p] + g), so
+        // that all tails run in one launch.  A tail item's flag marks a tail that is the
+        // problem's finest level (no restriction into it, no prolongation out of it).
         bt->down.resize(bt->H + 1);
         bt->up.resize(bt->H + 1);
         bt->fixb.resize(bt->H + 1);
-        for (int h = 1; h <= bt->H; ++h) {
-            std::vector<std::array<int, 3>> dn, upl, fx;
+        bt->tails.resize(bt->H + 1);
+        for (int g = 0; g <= bt->H; ++g) {
+            std::vector<std::array<int, 3>> dn, upl, fx, tl;
             for (int p = 0; p < n; ++p) {
-                const int m = tops[p] + h;
-                if (m > P[p].D) continue;
+                const int m = bt->mu == 1 ? tops[p] + g : P[p].D - (bt->H - g);
+                if (m < tops[p] || m > P[p].D) continue;
+                if (m == tops[p]) {
+                    tl.push_back({p, m, m == P[p].D ? 1 : 0});
+                    continue;
+                }
                 dn.push_back({p, m, 0});
                 upl.push_back({p, m, m < P[p].D ? 1 : 0});
                 if (m < P[p].D) fx.push_back({p, m, 2});
             }
-            bt->down[h].oct = bb.map(dn, P, 8 * OBLK);
-            bt->down[h].cell = bb.map(dn, P, BLK);
-            bt->up[h].oct = bb.map(upl, P, 8 * OBLK);
-            bt->up[h].cell = bb.map(upl, P, BLK);
-            bt->fixb[h].oct = bb.map(fx, P, 8 * OBLK);
+            bt->tails[g] = bb.map(tl, P, 1 << 30);   // one block per problem
+            if (g == 0) continue;
+            bt->down[g].oct = bb.map(dn, P, 8 * OBLK);
+            bt->down[g].cell = bb.map(dn, P, BLK);
+            bt->up[g].oct = bb.map(upl, P, 8 * OBLK);
+            bt->up[g].cell = bb.map(upl, P, BLK);
+            bt->fixb[g].oct = bb.map(fx, P, 8 * OBLK);
         }
         bt->avg.resize(bt->Dmax + 1);
         for (int m = 1; m <= bt->Dmax; ++m) {
@@ -359,9 +388,6 @@ int ocg_batch_create(ocg_hier* const* hs, int32_t n, void* stream, ocg_batch** o
             for (int p = 0; p < n; ++p)
                 for (int m = 0; m <= P[p].D; ++m) it.push_back({p, m, 0});
             bt->apply = bb.map(it, P, 8 * OBLK);
-            std::vector<std::array<int, 3>> tl;
-            for (int p = 0; p < n; ++p) tl.push_back({p, tops[p], 1});
-            bt->tail = bb.map(tl, P, 1 << 30);   // one block per problem
         }
         bt->vec.i0 = (int)bb.I.size();
         for (int p = 0; p < n; ++p)

@@ -75,7 +75,7 @@ __device__ __forceinline__ int sub_index(int a, int s) {
 // Device scalars of the Krylov loop.
 enum {
     S_PAP = 0, S_ALPHA, S_RZ, S_BETA, S_RR, S_RS, S_MEAN, S_BB, S_NS, S_TOL, S_MAXIT, S_K, S_DONE, S_TRUE,
-    S_RHO, S_RHON, S_OMEGA, S_XMEAN,
+    S_RHO, S_RHON, S_OMEGA, S_XMEAN, S_APMEAN,
     S_HIST = 24, S_COUNT = 24 + 128
 };
 enum {
@@ -133,7 +133,13 @@ __device__ void red_apply(const Red& R, double sa, double sb, double sc) {
     double* S = R.S;
     const bool ns = S[S_NS] != 0.0;
     switch (R.op) {
-        case OP_ALPHA: S[S_PAP] = sa; S[S_ALPHA] = sa != 0.0 ? S[S_RZ] / sa : 0.0; break;
+        // sb = the sum of A p over the leaves (the pair-stored mixed apply), whose mean the
+        // fused update subtracts under the null space
+        case OP_ALPHA:
+            S[S_PAP] = sa;
+            S[S_ALPHA] = sa != 0.0 ? S[S_RZ] / sa : 0.0;
+            S[S_APMEAN] = ns ? sb / R.nleaf : 0.0;
+            break;
         case OP_RZ0: S[S_RZ] = sa; break;
         case OP_BETA: S[S_BETA] = S[S_RZ] != 0.0 ? sa / S[S_RZ] : 0.0; S[S_RZ] = sa; break;
         case OP_BB: {
@@ -401,45 +407,51 @@ __global__ void __launch_bounds__(BLK) k_update(TO* __restrict__ x, TO* __restri
 
 // The update of k_update for the mixed PCG, whose p is kept as FP32 pairs (hi, lo) that
 // the outer apply reads without conversion: x += alpha p (p = hi + lo exactly in
-// binary64), r -= alpha A p, ||r||^2 (and sum r); four elements per thread and pass.
-template <bool SUM>
+// binary64), r -= alpha A p, b32 = r, ||r||^2; four elements per thread and pass.  Under
+// the null space (NS) the zero-mean shift of r (Sec. 2.2) is fused in: r had zero mean, so
+// r - alpha (A p - mean(A p)) on the leaves is the shifted residual, the mean of A p
+// coming from the apply's reduction (S_APMEAN).
+template <bool NS>
 __global__ void __launch_bounds__(BLK) k_update_pp(double* __restrict__ x, double* __restrict__ r,
                                                    const float* __restrict__ phi, const float* __restrict__ plo,
-                                                   const double* __restrict__ Ap, float* __restrict__ b32, int n,
-                                                   Red R) {
+                                                   const double* __restrict__ Ap, const uint8_t* __restrict__ flags,
+                                                   float* __restrict__ b32, int n, Red R) {
     pdl_enter();
     __shared__ double sh[32];
     const double alpha = R.S[S_ALPHA];
-    double rr = 0.0, rs = 0.0;
+    const double shift = NS ? alpha * R.S[S_APMEAN] : 0.0;
+    double rr = 0.0;
     const int st = gridDim.x * BLK;
     int i = blockIdx.x * BLK + threadIdx.x;
     for (; i + 3 * st < n; i += 4 * st) {
         double xv[4], rv[4], av[4];
         float hv[4], lv[4];
+        uint8_t fv[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             xv[q] = x[i + q * st]; rv[q] = r[i + q * st]; av[q] = Ap[i + q * st];
             hv[q] = phi[i + q * st]; lv[q] = plo[i + q * st];
+            fv[q] = NS ? flags[i + q * st] : 0;
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             x[i + q * st] = xv[q] + alpha * (f2d_bits(hv[q]) + f2d_bits(lv[q]));
-            const double rn = rv[q] - alpha * av[q];
+            double rn = rv[q] - alpha * av[q];
+            if (NS && (fv[q] & 1)) rn = rn + shift;
             r[i + q * st] = rn;
-            if (b32) b32[i + q * st] = d2f_bits(rn);
+            b32[i + q * st] = d2f_bits(rn);
             rr += rn * rn;
-            if (SUM) rs += rn;
         }
     }
     for (; i < n; i += st) {
         x[i] = x[i] + alpha * (f2d_bits(phi[i]) + f2d_bits(plo[i]));
-        const double rn = r[i] - alpha * Ap[i];
+        double rn = r[i] - alpha * Ap[i];
+        if (NS && (flags[i] & 1)) rn = rn + shift;
         r[i] = rn;
-        if (b32) b32[i] = d2f_bits(rn);
+        b32[i] = d2f_bits(rn);
         rr += rn * rn;
-        if (SUM) rs += rn;
     }
-    red_finish(R, blockIdx.x, rr, rs, sh);
+    red_finish(R, blockIdx.x, rr, 0.0, sh);
 }
 
 // p = z + beta p (first: p = z) for p kept as FP32 pairs, in pair arithmetic (beta split

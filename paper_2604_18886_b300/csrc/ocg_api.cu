@@ -1019,16 +1019,19 @@ struct PcgImpl {
             if constexpr (PP) {
                 if (ns)
                     launch_k(k_update_pp<true>, rb(), BLK, 0, c.st, h->x, h->r, (const float*)hi(h->p),
-                             (const float*)lo(h->p), (const double*)h->Ap, (float*)nullptr, n(), R);
+                             (const float*)lo(h->p), (const double*)h->Ap, (const uint8_t*)h->t->flags,
+                             (float*)B(), n(), R);
                 else
                     launch_k(k_update_pp<false>, rb(), BLK, 0, c.st, h->x, h->r, (const float*)hi(h->p),
-                             (const float*)lo(h->p), (const double*)h->Ap, (float*)B(), n(), R);
+                             (const float*)lo(h->p), (const double*)h->Ap, (const uint8_t*)nullptr,
+                             (float*)B(), n(), R);
             } else {
                 if (ns) launch_k(k_update<TO, TV, true>, rb(), BLK, 0, c.st, x(), r(), p(), Ap(), nullptr, n(), R);
                 else launch_k(k_update<TO, TV, false>, rb(), BLK, 0, c.st, x(), r(), p(), Ap(), B(), n(), R);
             }
         });
-        if (ns)
+        // the zero-mean shift of r (fused into the update of the pair-stored mixed form)
+        if (ns && !PP)
             launch(c, -1, 0, n(), [&] { launch_k(k_project<TO, TV>, gb(), BLK, 0, c.st, r(), h->t->flags, h->S, B(), n()); });
         ck_launch("half_a");
     }

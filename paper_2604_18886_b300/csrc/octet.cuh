@@ -1083,7 +1083,7 @@ template <class V, class O>
 __device__ __forceinline__ void layer_apply_df(const Tables& T, const Coefs<float, float>& C,
                                                const float* __restrict__ rem, const uint8_t* __restrict__ flags,
                                                const V& P, const O& Y, int off, int ni, int o, int z, unsigned pm,
-                                               DF& dot) {
+                                               DF& dot, DF& sum) {
     const int c8 = off + 8 * o, og = c8 >> 3, cz0 = c8 + 4 * z;
     const uint32_t fl = __ldg(reinterpret_cast<const uint32_t*>(flags + cz0));
     const int leafm = (int)((fl & 1u) | ((fl >> 7) & 2u) | ((fl >> 14) & 4u) | ((fl >> 21) & 8u));
@@ -1220,13 +1220,16 @@ __device__ __forceinline__ void layer_apply_df(const Tables& T, const Coefs<floa
         DF au = acc[q];
         df_acc(au, df_scale(u[q], f4at(rm, q)));
         out[q] = df_norm(au);
-        if (leaf) df_acc(dot, df_mul(u[q], out[q]));
+        if (leaf) {
+            df_acc(dot, df_mul(u[q], out[q]));
+            df_acc(sum, out[q]);
+        }
     }
     Y.put4(cz0, out, leafm);
 }
 
 // Y = A P over all tree levels (FP64 vectors, FP32 coefficients), two lanes per octet;
-// (P, A P) over the leaves reduced into R.  Blocks of OBLK2 threads take the octet blocks
+// (P, A P) and the sum of A P over the leaves reduced into R.  Blocks of OBLK2 threads take the octet blocks
 // (64 octets) of OMultiLevel and stride over them.
 template <class V, class O>
 __global__ void __launch_bounds__(OBLK2, 8) k_oapply_df2(OMultiLevel ML, Tables T, Coefs<float, float> C,
@@ -1234,7 +1237,7 @@ __global__ void __launch_bounds__(OBLK2, 8) k_oapply_df2(OMultiLevel ML, Tables 
                                                          const uint8_t* __restrict__ flags, V P, O Y, Red R) {
     pdl_enter();
     __shared__ double sh[32];
-    DF dot{0.0f, 0.0f};
+    DF dot{0.0f, 0.0f}, sum{0.0f, 0.0f};
     const int nvb = ML.boff[ML.n];
     const int z = threadIdx.x & 1;
     const unsigned pm = 3u << (threadIdx.x & 30);
@@ -1242,9 +1245,9 @@ __global__ void __launch_bounds__(OBLK2, 8) k_oapply_df2(OMultiLevel ML, Tables 
     for (int vb = blockIdx.x; vb < nvb; vb += gridDim.x) {
         while (l + 1 < ML.n && vb >= ML.boff[l + 1]) ++l;
         const int o = (vb - ML.boff[l]) * OBLK + (threadIdx.x >> 1);
-        if (o < ML.noct[l]) layer_apply_df(T, C, rem, flags, P, Y, ML.off[l], ML.ni[l], o, z, pm, dot);
+        if (o < ML.noct[l]) layer_apply_df(T, C, rem, flags, P, Y, ML.off[l], ML.ni[l], o, z, pm, dot, sum);
     }
-    if (R.op != OP_NONE) red_finish(R, blockIdx.x, df_to_double(dot), 0.0, sh);
+    if (R.op != OP_NONE) red_finish(R, blockIdx.x, df_to_double(dot), df_to_double(sum), sh);
 }
 
 // ------------------------------------------------------------ transposed operator

@@ -1,7 +1,7 @@
 """GPU parity of the batched solve (ocg_pcg_solve_batched): every problem of a batch
 against the FP64 oracle (same bar as the single solves) and against its own single
-mixed solve; converged problems are frozen; incompatible hierarchies are refused; the
-64-tree batched workload at full size against single solves.
+mixed solve, with V- and W-cycles; converged problems are frozen; incompatible
+hierarchies are refused; the 64-tree batched workload at full size against single solves.
 
 Tolerances: the batched solve runs the single solve's arithmetic per problem, but its
 reductions sum in another block order and the tail kernel may pick the other sweep form
@@ -74,13 +74,40 @@ def test_converged_problems_are_frozen():
     assert rel(xs[1].cpu().numpy(), x1.cpu().numpy()) <= 1e-6
 
 
+def test_batched_w_cycles_match_oracle_and_single_solves():
+    # mu = 2 for every problem: the batch's schedule, aligned at the finest levels, visits
+    # each problem's coarser levels as its own W-cycle does (Alg. 4)
+    from oracle import mg
+    items = [build(CASES[n](), "f32", mu=2) for n in MIX]
+    bt = S.Batch([it[3] for it in items])
+    bs = [cuda(_rhs(n, it[0], it[4], it[5])) for n, it in zip(MIX, items)]
+    xs, stats = bt.solve(bs, tol=1e-6)
+    for n, it, b, x, st in zip(MIX, items, bs, xs, stats):
+        t, H, g, gh, f, beta = it
+        bn = b.cpu().numpy()
+        ref, _, _ = pcg.pcg(H, bn, tol=1e-12, max_iter=200, prm=mg.CycleParams(mu=2))
+        xo, ko, _ = pcg.pcg(H, bn, tol=1e-6, prm=mg.CycleParams(mu=2))
+        if H.nullspace:
+            ref = ref - ref.mean()
+            xo = xo - xo.mean()
+        assert st.converged and st.true_rel_res <= 1.5e-6, n
+        assert abs(st.iterations - ko) <= 1, (n, st.iterations, ko)
+        assert rel(x.cpu().numpy(), ref) <= 1.5 * rel(xo, ref) + 1e-5, n
+    xs9, st9 = bt.solve(bs, tol=1e-9)
+    for n, it, b, x, st in zip(MIX, items, bs, xs9, st9):
+        x1, s1 = it[3].solve(b, tol=1e-9, precision="mixed")
+        assert st.converged and abs(st.iterations - s1.iterations) <= 1, (n, st.iterations, s1.iterations)
+        assert rel(x.cpu().numpy(), x1.cpu().numpy()) <= 1e-6, n
+
+
 def test_batch_refuses_incompatible_hierarchies():
     from paper_2604_18886_b300 import _lib
     p = CASES["ball_16"]()
     g = S.Octree(p.desc)
     beta = P.face_beta(p, g.faces())
     ok = S.Hierarchy(g, beta, p.bc, S.mg_params(coef="f32"))
-    for bad in (S.mg_params(coef="f32", mu=2), S.mg_params(coef="f32", bf16_coarse=True), S.mg_params(coef="f64")):
+    for bad in (S.mg_params(coef="f32", mu=2), S.mg_params(coef="f32", bf16_coarse=True), S.mg_params(coef="f64"),
+                S.mg_params(coef="f32", mu=2, mu_min_cells=4096)):
         h = S.Hierarchy(g, beta, p.bc, bad)
         with pytest.raises(_lib.OcgError) as e:
             S.Batch([ok, h])

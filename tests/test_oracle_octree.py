@@ -15,7 +15,13 @@ def _trees():
     yield P.cut_cell(8, 2).desc
 
 
-@pytest.mark.parametrize("desc", list(_trees()))
+def _tiled():
+    yield P.OctreeDesc(16, 2, P.REFINE_SDF_BAND, band=0.0, spheres=[(0.5, 0.5, 0.5, 0.25)], tile_log2=2)
+    yield P.OctreeDesc(16, 3, P.REFINE_STAR_BAND, band=0.0, spheres=list(P.STAR), tile_log2=2)
+    yield P.paper_grid("sphere", 32)
+
+
+@pytest.mark.parametrize("desc", list(_trees()) + list(_tiled()))
 def test_face_neighbours_differ_by_at_most_one_depth(desc):
     t = O.Octree(desc)
     L = t.leaves
@@ -59,6 +65,34 @@ def test_balance_is_minimal_and_contains_predicate(desc):
                 if 0 <= c[a] < nd and t.is_refined(d, np.array([O._key(*c, nd)]))[0]:
                     forced = True
             assert forced, "balance refinement at depth %d is not forced" % d
+
+
+@pytest.mark.parametrize("desc", list(_tiled()))
+def test_tile_balance_is_minimal_and_tile_uniform(desc):
+    # with tiles every refinement decision is a whole tile's: refined cells come in full
+    # aligned tiles, and a tile that the predicate did not refine is refined only because a
+    # refined cell one depth below has a face neighbour whose parent lies in it
+    t = O.Octree(desc)
+    w = 1 << desc.tile_log2
+    for d in range(t.D):
+        nd = t.nd(d)
+        i, j, k = O._unkey(t.refined[d], nd)
+        tiles, counts = np.unique(O._key(i // w, j // w, k // w, nd // w), return_counts=True)
+        assert np.all(counts == w ** 3), "refinement at depth %d is not tile-uniform" % d
+        assert np.all(np.isin(t.pred_refined[d], t.refined[d]))
+        pi, pj, pk = O._unkey(t.pred_refined[d], nd)
+        extra = np.setdiff1d(tiles, O._key(pi // w, pj // w, pk // w, nd // w))
+        if len(extra) == 0:
+            continue
+        ci, cj, ck = O._unkey(t.refined[d + 1], 2 * nd) if d + 1 < t.D else (np.zeros(0, np.int64),) * 3
+        forced = []
+        for (a, sg) in O.DIRS:
+            c = [ci.copy(), cj.copy(), ck.copy()]
+            c[a] = c[a] + sg
+            ok = (c[a] >= 0) & (c[a] < 2 * nd)
+            forced.append(O._key(c[0][ok] // 2 // w, c[1][ok] // 2 // w, c[2][ok] // 2 // w, nd // w))
+        forced = np.unique(np.concatenate(forced)) if forced else np.zeros(0, np.int64)
+        assert np.all(np.isin(extra, forced)), "balance tile at depth %d is not forced" % d
 
 
 @pytest.mark.parametrize("desc", list(_trees()))
