@@ -228,7 +228,7 @@ def _timed(stream, flush, fn, steps):
     return out
 
 
-def _form(leaves, runs, peak, bytes_fn, x=None, x_ref=None):
+def _form(leaves, runs, peak, bytes_fn, x=None, x_ref=None, nullspace=False):
     ms = statistics.mean(t for t, _ in runs)
     st = runs[-1][1]
     its = sorted({r.iterations for _, r in runs})
@@ -238,8 +238,28 @@ def _form(leaves, runs, peak, bytes_fn, x=None, x_ref=None):
     d["model_gb"] = round(mb / 1e9, 2)
     d["hbm_roof_frac_model"] = round(mb / (ms / 1e3) / 1e9 / peak, 4)
     if x is not None and x_ref is not None:
-        d["err_vs_fp64"] = float(((x - x_ref).abs().max() / x_ref.abs().max()).item())
+        d["err_vs_fp64"] = _err(x, x_ref, nullspace)
     return d
+
+
+def _fp64_reference(tree, beta, bc, b, stream):
+    """The library's FP64 solve of the same system (FP64 coefficients and cycle, FP64 PCG)
+    to 1e-12: the reference of every form's error."""
+    from paper_2604_18886_b300 import solver as S
+    h64 = S.Hierarchy(tree, beta, bc, S.mg_params(coef="f64", sweep="octet"))
+    x, _ = h64.solve(b, tol=1e-12, precision="fp64", max_iter=300, stream=stream)
+    del h64
+    return x
+
+
+def _err(x, x_ref, nullspace=False):
+    """max |x - x_ref| / max |x_ref|; with a constant null space (all walls Neumann) both are
+    compared modulo constants (means removed)."""
+    d = x - x_ref
+    if nullspace:
+        d = d - d.mean()
+        x_ref = x_ref - x_ref.mean()
+    return float((d.abs().max() / x_ref.abs().max()).item())
 
 
 def _probe(hier, kind, level, b, x, iterations, stream, flush, reps=1):
@@ -421,12 +441,18 @@ def _ball(dev, stream, flush, args, peak, peak_kind):
         return {"value": round(g.n_leaves / (statistics.mean(t for t, _ in rm) / 1e3) / 1e6, 3),
                 "note": "--only-ball --nvtx (profiling aid)"}
     r32 = _timed(stream, flush, lambda: h.solve(b, x, tol=1e-6, precision="fp32", stream=stream)[1], steps)
+    x_ref = _fp64_reference(g, beta, p.bc, b, stream)
     out = _form(g.n_leaves, rm, peak, lambda k: model_bytes(sizes, g.n_tree, k, "mixed"))
+    out["err_vs_fp64"] = _err(h.solve(b, tol=1e-6, precision="mixed", stream=stream)[0], x_ref, h.nullspace)
     out["plain_fp32"] = _form(g.n_leaves, r32, peak, lambda k: model_bytes(sizes, g.n_tree, k, "fp32"))
+    out["plain_fp32"]["err_vs_fp64"] = _err(h.solve(b, tol=1e-6, precision="fp32", stream=stream)[0], x_ref,
+                                            h.nullspace)
     hb = S.Hierarchy(g, beta, p.bc, S.mg_params(coef="f32", bf16_coarse=True))
     hb.solve(b, x, tol=1e-6, precision="mixed", stream=stream)
     rb = _timed(stream, flush, lambda: hb.solve(b, x, tol=1e-6, precision="mixed", stream=stream)[1], steps)
     out["mixed_bf16_coarse"] = _form(g.n_leaves, rb, peak, lambda k: model_bytes(sizes, g.n_tree, k, "mixed"))
+    out["mixed_bf16_coarse"]["err_vs_fp64"] = _err(hb.solve(b, tol=1e-6, precision="mixed", stream=stream)[0],
+                                                   x_ref, hb.nullspace)
     del hb
     its = rm[-1][1].iterations
     big = int(max(range(g.D + 1), key=lambda q: g.level_size(q)))
@@ -479,6 +505,7 @@ def _cut_cell(dev, stream, flush, args, peak):
     steps = max(3, min(args.steps, 10))
     out = {"workload": "cut-cell projection: 64^3 root, sphere r=0.2 and box, band 0.05, 2 levels "
                        "(%d leaves), fluid-fraction beta, Neumann, divergence rhs" % g.n_leaves}
+    x_ref = _fp64_reference(g, beta, p.bc, b, stream)
     for name, prm, mu, mmin, maxit in (
             ("mixed_bf16_coarse", S.mg_params(coef="f32", bf16_coarse=True), 1, 0, 100),
             ("w_cycle", S.mg_params(mu=2, coef="f32", bf16_coarse=True), 2, 0, 100),
@@ -491,7 +518,7 @@ def _cut_cell(dev, stream, flush, args, peak):
         r = _timed(stream, flush, lambda: h.solve(b, x, tol=1e-6, precision="mixed", stream=stream,
                                                   max_iter=maxit)[1], steps if maxit == 100 else 1)
         out[name] = _form(g.n_leaves, r, peak, (lambda mu_, mm_: lambda k: model_bytes(
-            sizes, g.n_tree, k, "mixed", mu_, mm_))(mu, mmin))
+            sizes, g.n_tree, k, "mixed", mu_, mm_))(mu, mmin), x, x_ref, h.nullspace)
         del h
     return out
 
@@ -529,6 +556,10 @@ def _batched(dev, stream, flush, args):
     ms_b = statistics.mean(t for t, _ in rb)
     ms_s = statistics.mean(t for t, _ in rs)
     its = sorted({s.iterations for _, st in rb for s in st})
+    # every problem's batched solution against its own FP64 solve to 1e-12
+    bt.solve(bs, xs, tol=1e-6, stream=stream)
+    err = max(_err(x, _fp64_reference(h.tree, h._beta, h._bc, b, stream), h.nullspace)
+              for h, b, x in zip(hs, bs, xs))
     forms = {str(h): ["octet", "cell"][f] for h, (f, a, b) in bt.info().items()}
     kern = rb[-1][1][0].kernels
     del bt
@@ -538,14 +569,16 @@ def _batched(dev, stream, flush, args):
     bw.solve(bs, xs, tol=1e-6, stream=stream)
     rw = _timed(stream, flush, lambda: bw.solve(bs, xs, tol=1e-6, stream=stream)[1], max(3, min(args.steps, 10)))
     assert all(s.converged for s in rw[-1][1])
+    err_w = max(_err(x, _fp64_reference(h.tree, h._beta, h._bc, b, stream), h.nullspace)
+                for h, b, x in zip(hw, bs, xs))
     ms_w = statistics.mean(t for t, _ in rw)
     w_cycle = {"value": round(leaves / (ms_w / 1e3) / 1e6, 3), "unit": UNIT, "ms_per_step": round(ms_w, 4),
                "iterations": sorted({s.iterations for _, st in rw for s in st}),
-               "gpu_launches_per_step": rw[-1][1][0].kernels}
+               "gpu_launches_per_step": rw[-1][1][0].kernels, "err_vs_fp64_max": err_w}
     del bw, hw
     return {"workload": BATCH_WORKLOAD, "problems": 64, "leaves": leaves,
             "value": round(leaves / (ms_b / 1e3) / 1e6, 3), "unit": UNIT, "ms_per_step": round(ms_b, 4),
-            "steps": steps, "iterations": its, "gpu_launches_per_step": kern,
+            "steps": steps, "iterations": its, "gpu_launches_per_step": kern, "err_vs_fp64_max": err,
             "sweep_forms_by_height": forms, "create_s": round(t_create, 3),
             "sequential_single_solves": {"value": round(leaves / (ms_s / 1e3) / 1e6, 3), "unit": UNIT,
                                          "ms_per_step": round(ms_s, 4)},
