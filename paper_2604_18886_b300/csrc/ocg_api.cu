@@ -558,11 +558,14 @@ struct Cycle {
         ck_launch("coarsest");
     }
     static constexpr int W = std::is_same<TV, double>::value ? 1 : 0;
+    // The shared-memory tail; its prolongation onto the uniform level above runs as a
+    // separate grid-wide launch (k_oprolong, the same arithmetic), which one CTA would take
+    // several memory latencies for.
     void tail(bool fas, bool prolong_up) {
         const int m = h->tail_top[W];
         TailArgs A = h->tail_args[W];
         A.fas = fas ? 1 : 0;
-        A.prolong = prolong_up ? 1 : 0;
+        A.prolong = 0;
         const TV scale = TV(h->prm.beta_restrict / h->prm.alpha);
         const size_t sm = h->tail_smem[W];
         with_coefs(m, [&](auto C) {
@@ -570,13 +573,15 @@ struct Cycle {
             using TW = typename CoefTypes<decltype(C)>::TW;
             ck(cudaFuncSetAttribute(k_otail<TV, TC, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
                "cudaFuncSetAttribute");
+            // the widest pass is a colour sweep of the top level: 4 cells per octet
             const int noct = A.L[0].ni * A.L[0].ni * A.L[0].ni;
-            const int nt = std::min(sizeof(TV) == 8 ? 256 : 512, (noct + 31) / 32 * 32);
+            const int nt = std::min(sizeof(TV) == 8 ? 256 : 1024, (4 * noct + 31) / 32 * 32);
             launch(c, OCG_PROBE_TAIL, m, A.ncell, [&] {
                 launch_k(k_otail<TV, TC, TW>, 1, nt, sm, c.st, A, h->t->tables(), C, U, B, scale);
             });
         });
         ck_launch("tail");
+        if (prolong_up) prolong(m + 1);
     }
     // Alg. 4 at level m.  fas: first visit after a restriction from m+1 (complete the
     // FAS right-hand side); prolong_up: the last visit, whose final operation prolongs

@@ -1920,42 +1920,107 @@ enum { TP_SWEEP0 = 0, TP_SWEEP1 = 1, TP_FIXB = 2, TP_RESTRICT = 3, TP_PROLONG = 
 // the colour (s = 2k + (parity(k) xor colour): 0, 3, 5, 6 or 1, 2, 4, 7) of octet o, so
 // the threads do no work on the other colour (one thread per octet would evaluate all 8
 // stencils).  The sum runs in the octet form's order (per axis: octet partner, then the
-// neighbouring octet), so both forms give the same bits.  Shared index of cell (o, s) is
-// sbase + s * no + o.
+// neighbouring octet).  Shared index of cell (o, s) is sbase + s * no + o.
 template <class TV>
-__device__ __forceinline__ void tail_sweep_cells(const TailMem<TV>& M, const TailLevel& L, int colour) {
+__device__ __forceinline__ void tail_sweep_cell(const TailMem<TV>& M, const TailLevel& L, int colour, int i) {
     const int ni = L.ni, no = ni * ni * ni;
     const bool p2 = (no & (no - 1)) == 0;
     const int sh = p2 ? __ffs(no) - 1 : 0;
-    for (int i = threadIdx.x; i < 4 * no; i += blockDim.x) {
-        const int k = p2 ? (i >> sh) : i / no;
-        const int o = i - k * no;
-        const int s = 2 * k + ((__popc(k) & 1) ^ colour);
-        const int q = L.sbase + s * no + o;
-        const TV dd = M.d[q];
-        if (dd == TV(0)) continue;
-        int crd[3];
-        octet_coords(o, ni, crd[0], crd[1], crd[2]);
-        const int stride[3] = {1, ni, ni * ni};
-        TV Au = dd * M.u[q];
+    const int k = p2 ? (i >> sh) : i / no;
+    const int o = i - k * no;
+    const int s = 2 * k + ((__popc(k) & 1) ^ colour);
+    const int q = L.sbase + s * no + o;
+    const TV dd = M.d[q];
+    if (dd == TV(0)) return;
+    int crd[3];
+    octet_coords(o, ni, crd[0], crd[1], crd[2]);
+    const int stride[3] = {1, ni, ni * ni};
+    TV Au = dd * M.u[q];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const int bit = 1 << a;
-            const int t = s ^ bit;
-            const int qi = L.sbase + t * no + o;                // partner in the octet
-            if (s & bit) {
-                Au += M.cm[a][q] * M.u[qi];
-                if (crd[a] < ni - 1) {
-                    const int qo = qi + stride[a];               // slot t of the + octet
-                    Au += M.cm[a][qo] * M.u[qo];
-                }
-            } else {
-                Au += M.cm[a][qi] * M.u[qi];
-                if (crd[a] > 0) Au += M.cm[a][q] * M.u[qi - stride[a]];   // slot t of the - octet
+    for (int a = 0; a < 3; ++a) {
+        const int bit = 1 << a;
+        const int t = s ^ bit;
+        const int qi = L.sbase + t * no + o;                // partner in the octet
+        if (s & bit) {
+            Au += M.cm[a][q] * M.u[qi];
+            if (crd[a] < ni - 1) {
+                const int qo = qi + stride[a];               // slot t of the + octet
+                Au += M.cm[a][qo] * M.u[qo];
             }
+        } else {
+            Au += M.cm[a][qi] * M.u[qi];
+            if (crd[a] > 0) Au += M.cm[a][q] * M.u[qi - stride[a]];   // slot t of the - octet
         }
-        M.u[q] = M.u[q] + divide(M.b[q] - Au, dd);
     }
+    M.u[q] = M.u[q] + divide(M.b[q] - Au, dd);
+}
+
+// The same update as tail_sweep_cell (the same terms summed in the same order) for a run of
+// sweeps of one small level by one warp: each lane's cell of a colour, its neighbours'
+// shared indices (16 bits each: a shared image of at most 200 KB holds fewer than 2^16
+// cells) and the operands that the sweeps do not change (diagonal, b, face coefficients)
+// are gathered once into shared memory, so that a sweep is seven loads of u, the sum and
+// the store.  (The compiler may pair products and additions into FMAs differently in the
+// two forms, so they agree to FP32 rounding, not bit for bit.)
+template <class TV>
+struct TailCell {
+    int qh;           // shared index | has << 16 (bit a: the neighbouring octet across axis a exists)
+    int nb[3];        // per axis: partner index << 16 | neighbouring octet's cell (q when absent)
+    TV dd, bq, cp[3], co[3];
+};
+
+template <class TV>
+__device__ __forceinline__ void tail_cell_gather(const TailMem<TV>& M, const TailLevel& L, int colour, int i,
+                                                 TailCell<TV>& C) {
+    const int ni = L.ni, no = ni * ni * ni;
+    const bool p2 = (no & (no - 1)) == 0;
+    const int sh = p2 ? __ffs(no) - 1 : 0;
+    const int k = p2 ? (i >> sh) : i / no;
+    const int o = i - k * no;
+    const int s = 2 * k + ((__popc(k) & 1) ^ colour);
+    const int q = L.sbase + s * no + o;
+    int crd[3];
+    octet_coords(o, ni, crd[0], crd[1], crd[2]);
+    const int stride[3] = {1, ni, ni * ni};
+    int has = 0;
+    C.dd = M.d[q];
+    C.bq = M.b[q];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int bit = 1 << a;
+        const int qi = L.sbase + (s ^ bit) * no + o;
+        const bool up = (s & bit) != 0;
+        const bool h = up ? crd[a] < ni - 1 : crd[a] > 0;
+        const int qn = h ? (up ? qi + stride[a] : qi - stride[a]) : q;
+        C.nb[a] = (qi << 16) | qn;
+        C.cp[a] = M.cm[a][up ? q : qi];
+        C.co[a] = M.cm[a][up ? qn : q];
+        has |= h ? bit : 0;
+    }
+    C.qh = q | (has << 16);
+}
+
+template <class TV>
+__device__ __forceinline__ void tail_cell_update(const TailMem<TV>& M, const TailCell<TV>& C) {
+    const int q = C.qh & 0xffff;
+    const TV uq = M.u[q];
+    TV vp[3], vo[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) { vp[a] = M.u[C.nb[a] >> 16]; vo[a] = M.u[C.nb[a] & 0xffff]; }
+    if (C.dd == TV(0)) return;
+    TV Au = C.dd * uq;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        Au += C.cp[a] * vp[a];
+        if ((C.qh >> (16 + a)) & 1) Au += C.co[a] * vo[a];
+    }
+    M.u[q] = uq + divide(C.bq - Au, C.dd);
+}
+
+template <class TV>
+__device__ __forceinline__ void tail_sweep_cells(const TailMem<TV>& M, const TailLevel& L, int colour) {
+    const int no = L.ni * L.ni * L.ni;
+    for (int i = threadIdx.x; i < 4 * no; i += blockDim.x) tail_sweep_cell<TV>(M, L, colour, i);
     __syncthreads();
 }
 
@@ -2026,6 +2091,7 @@ __device__ __forceinline__ void tail_cycle(const TailArgs& A, int fas, int prolo
     M.u = base; M.b = base + N; M.d = base + 2 * N;
     M.cm[0] = base + 3 * N; M.cm[1] = base + 4 * N; M.cm[2] = base + 5 * N;
     __shared__ int ssched[TAIL_SCHED_SH];
+    __shared__ TailCell<TV> wcell[2][32];   // the warp-run sweeps' per-lane records, per colour
     const bool sch_sh = A.nsched <= TAIL_SCHED_SH;
     if (sch_sh)
         for (int q = threadIdx.x; q < A.nsched; q += blockDim.x) ssched[q] = A.sched[q];
@@ -2056,6 +2122,30 @@ __device__ __forceinline__ void tail_cycle(const TailArgs& A, int fas, int prolo
     for (int q = 0; q < A.nsched; ++q) {
         const int e = sch_sh ? ssched[q] : __ldg(A.sched + q);
         const int li = e >> 3, kind = e & 7;
+        if (kind <= TP_SWEEP1 && 4 * tail_noct(A.L[li]) <= 32) {
+            // a run of sweeps of a level whose colour has at most 32 cells (the coarsest):
+            // the first warp does all of them, one cell per lane, ordered by warp barriers
+            int q2 = q + 1;
+            for (; q2 < A.nsched; ++q2) {
+                const int e2 = sch_sh ? ssched[q2] : __ldg(A.sched + q2);
+                if ((e2 >> 3) != li || (e2 & 7) > TP_SWEEP1) break;
+            }
+            if (threadIdx.x < 32) {
+                const bool act = (int)threadIdx.x < 4 * tail_noct(A.L[li]);
+                if (act) {
+                    tail_cell_gather<TV>(M, A.L[li], 0, threadIdx.x, wcell[0][threadIdx.x]);
+                    tail_cell_gather<TV>(M, A.L[li], 1, threadIdx.x, wcell[1][threadIdx.x]);
+                }
+                for (int k = q; k < q2; ++k) {
+                    const int ek = sch_sh ? ssched[k] : __ldg(A.sched + k);
+                    if (act) tail_cell_update<TV>(M, wcell[ek & 1][threadIdx.x]);
+                    __syncwarp();
+                }
+            }
+            __syncthreads();
+            q = q2 - 1;
+            continue;
+        }
         if (kind <= TP_SWEEP1) tail_sweep_cells<TV>(M, A.L[li], kind);
         else tail_pass<TV>(M, A, li, kind, scale);
     }
@@ -2087,7 +2177,7 @@ __device__ __forceinline__ void tail_cycle(const TailArgs& A, int fas, int prolo
 }
 
 template <class TV, class TC, class TW>
-__global__ void __launch_bounds__(sizeof(TV) == 8 ? 256 : 512)
+__global__ void __launch_bounds__(sizeof(TV) == 8 ? 256 : 1024)
     k_otail(TailArgs A, Tables T, Coefs<TC, TW> C, TV* __restrict__ U, TV* __restrict__ B, TV scale) {
     pdl_enter();
     tail_cycle<TV, TC, TW>(A, A.fas, A.prolong, T, C, U, B, scale);
