@@ -19,7 +19,7 @@ struct BLev {
 struct BProb {
     Tables T;
     Coefs<float, float> C;
-    float* U;
+    float* U;             // cycle work vectors, in the cycle layout (cyc)
     float* B;
     double *x, *r, *p, *Ap, *bt, *xt, *yt;
     double* S;            // this problem's Krylov scalars (S_*)
@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(512) kb_otail(const BProb* __restrict__ PP, co
 __global__ void __launch_bounds__(BLK) kb_zero_u(const BProb* __restrict__ PP, const int* __restrict__ bmap) {
     BVEC_PROLOGUE
     if (bdone(P)) return;
-    for (int i = i0; i < P.ntree; i += di) P.U[i] = 0.0f;
+    for (int i = i0; i < P.ntree; i += di) P.U[cyc(i)] = 0.0f;
 }
 
 // Per-call input / output of each problem (canonical leaf order).
@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(BLK) kb_rinit(const BProb* __restrict__ PP, co
         double v = P.bt[i];
         if (P.flags[i] & 1) v -= mean;
         P.r[i] = v;
-        P.B[i] = (float)v;
+        P.B[cyc(i)] = (float)v;
     }
 }
 
@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(BLK) kb_dot_rz(const BProb* __restrict__ PP, c
     BVEC_PROLOGUE
     double v = 0.0;
     if (!bdone(P))
-        for (int i = i0; i < P.ntree; i += di) v += P.r[i] * (double)P.U[i];
+        for (int i = i0; i < P.ntree; i += di) v += P.r[i] * (double)P.U[cyc(i)];
     bred_finish<2>(PP, pid, blk, nb, R, v, 0.0, 0.0, sh);
 }
 
@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(BLK) kb_pupdate(const BProb* __restrict__ PP, 
     BVEC_PROLOGUE
     if (bdone(P)) return;
     const double beta = P.S[S_BETA];
-    for (int i = i0; i < P.ntree; i += di) P.p[i] = first ? (double)P.U[i] : (double)P.U[i] + beta * P.p[i];
+    for (int i = i0; i < P.ntree; i += di) P.p[i] = first ? (double)P.U[cyc(i)] : (double)P.U[cyc(i)] + beta * P.p[i];
 }
 
 // x += alpha p, r -= alpha Ap; ||r||^2, sum(r) -> OP_RR (per-problem stop test)
@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(BLK) kb_update(const BProb* __restrict__ PP, c
             P.x[i] = P.x[i] + alpha * P.p[i];
             const double rn = P.r[i] - alpha * P.Ap[i];
             P.r[i] = rn;
-            if (!ns) P.B[i] = (float)rn;
+            if (!ns) P.B[cyc(i)] = (float)rn;
             rr += rn * rn;
             rs += ns ? rn : 0.0;
         }
@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(BLK) kb_project(const BProb* __restrict__ PP, 
         double v = P.r[i];
         if (P.flags[i] & 1) v -= mean;
         P.r[i] = v;
-        P.B[i] = (float)v;
+        P.B[cyc(i)] = (float)v;
     }
 }
 

@@ -175,8 +175,8 @@ void batch_autotune(ocg_batch* bt) {
     if (!bt->cap) ck(cudaStreamCreateWithFlags(&bt->cap, cudaStreamNonBlocking), "cudaStreamCreate");
     cudaStream_t cs = bt->cap;
     for (ocg_hier* h : bt->hs) {
-        ck(cudaMemsetAsync(h->U, 0, h->t->H.ncell * sizeof(float), cs), "memset");
-        ck(cudaMemsetAsync(h->B, 0, h->t->H.ncell * sizeof(float), cs), "memset");
+        ck(cudaMemsetAsync(h->U, 0, cyc_len(h->t->H.ncell) * sizeof(float), cs), "memset");
+        ck(cudaMemsetAsync(h->B, 0, cyc_len(h->t->H.ncell) * sizeof(float), cs), "memset");
     }
     ck(cudaMemsetAsync(bt->S, 0, (size_t)bt->n * S_COUNT * sizeof(double), cs), "memset");
     cudaEvent_t e0, e1;

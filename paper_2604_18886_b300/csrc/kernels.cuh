@@ -26,6 +26,27 @@ __device__ __forceinline__ void pdl_enter() {
 }
 constexpr int MAXLEV = 16;
 
+// Storage of the forward cycle's work vectors (u and b of every level).  The cells of an
+// octet split into two colours of the red-black sweep, colour(s) = parity of the slot s
+// (the octet's first cell has even coordinates): slots 0, 3, 5, 6 and 1, 2, 4, 7, the
+// k-th slot of a colour being s = 2k + (parity(k) xor colour), so k = s >> 1.  Each
+// aligned group of 8 octets (64 cells) stores the colour-0 cells of its octets first
+// (4 per octet, 16 bytes in FP32) and then the colour-1 cells: a colour sweep reads b and
+// writes u in whole 32-byte sectors, and reads one 16-byte chunk per neighbouring octet
+// (the face neighbours of a colour's cells are all of the other colour).  The map keeps
+// every cell inside its group, so it needs only an allocation rounded up to 64 cells
+// (cyc_len) starting at cell 0.  The Krylov vectors and the transposed cycle keep the
+// plain cell order.
+__host__ __device__ __forceinline__ int cyc_colour(int s) { return (0x96 >> s) & 1; }
+__host__ __device__ __forceinline__ int cyc(int g) {
+    return (g & ~63) | (cyc_colour(g & 7) << 5) | (((g >> 3) & 7) << 2) | ((g & 7) >> 1);
+}
+// position of the colour-0 chunk of the octet whose first cell is c8 (colour 1: + 32)
+__host__ __device__ __forceinline__ int cyc8(int c8) { return (c8 & ~63) | (((c8 >> 3) & 7) << 2); }
+__host__ __device__ __forceinline__ int64_t cyc_len(int64_t n) { return (n + 63) & ~(int64_t)63; }
+template <bool CY>
+__device__ __forceinline__ int vidx(int g) { return CY ? cyc(g) : g; }
+
 struct Tables {
     const int32_t* nbr;        // [6][noct] level-local octet / -1 wall / -2-K T face
     const int32_t* oct_parent; // [noct] global parent cell
@@ -335,12 +356,13 @@ template <>
 __device__ __forceinline__ float cvt<float, double>(double v) { return d2f_bits(v); }
 
 // ----------------------------------------------------------------- PCG vector kernels
-template <class TI, class TO>
+// CY: out in the cycle layout (cyc)
+template <class TI, class TO, bool CY = false>
 __global__ void k_scatter(const TI* __restrict__ in, TO* __restrict__ out, const int32_t* __restrict__ leaf_cell,
                           int n) {
     pdl_enter();
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r < n) out[leaf_cell[r]] = TO(in[r]);
+    if (r < n) out[vidx<CY>(leaf_cell[r])] = TO(in[r]);
 }
 
 template <class TI, class TO>
@@ -358,17 +380,19 @@ __global__ void k_sub(T* __restrict__ r, const T* __restrict__ a, int n) {
     if (i < n) r[i] = r[i] - a[i];
 }
 
-template <class TI, class TO>
+// CY: in in the cycle layout (cyc)
+template <class TI, class TO, bool CY = false>
 __global__ void k_gather(const TI* __restrict__ in, TO* __restrict__ out, const int32_t* __restrict__ leaf_cell,
                          int n) {
     pdl_enter();
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r < n) out[r] = TO(in[leaf_cell[r]]);
+    if (r < n) out[r] = TO(in[vidx<CY>(leaf_cell[r])]);
 }
 
 // x += alpha p, r -= alpha Ap over the tree cells (inner cells keep r = 0 since Ap = 0
-// there); reduces r.r and sum(r) (OP_RR: convergence test of Alg. 1); optionally b32 = r.
-template <class TO, class TB, bool SUM>
+// there); reduces r.r and sum(r) (OP_RR: convergence test of Alg. 1); optionally b32 = r
+// (b32 in the cycle layout when CY).
+template <class TO, class TB, bool SUM, bool CY = false>
 __global__ void __launch_bounds__(BLK) k_update(TO* __restrict__ x, TO* __restrict__ r, const TO* __restrict__ p,
                                                 const TO* __restrict__ Ap, TB* __restrict__ b32, int n, Red R) {
     pdl_enter();
@@ -387,7 +411,7 @@ __global__ void __launch_bounds__(BLK) k_update(TO* __restrict__ x, TO* __restri
             x[i + q * st] = xv[q] + alpha * pv[q];
             const TO rn = rv[q] - alpha * av[q];
             r[i + q * st] = rn;
-            if (b32) b32[i + q * st] = cvt<TB>(rn);
+            if (b32) b32[vidx<CY>(i + q * st)] = cvt<TB>(rn);
             const double rd = (double)rn;
             rr += rd * rd;
             if (SUM) rs += rd;
@@ -397,7 +421,7 @@ __global__ void __launch_bounds__(BLK) k_update(TO* __restrict__ x, TO* __restri
         x[i] = x[i] + alpha * p[i];
         const TO rn = r[i] - alpha * Ap[i];
         r[i] = rn;
-        if (b32) b32[i] = cvt<TB>(rn);
+        if (b32) b32[vidx<CY>(i)] = cvt<TB>(rn);
         const double rd = (double)rn;
         rr += rd * rd;
         if (SUM) rs += rd;
@@ -410,7 +434,8 @@ __global__ void __launch_bounds__(BLK) k_update(TO* __restrict__ x, TO* __restri
 // binary64), r -= alpha A p, b32 = r, ||r||^2; four elements per thread and pass.  Under
 // the null space (NS) the zero-mean shift of r (Sec. 2.2) is fused in: r had zero mean, so
 // r - alpha (A p - mean(A p)) on the leaves is the shifted residual, the mean of A p
-// coming from the apply's reduction (S_APMEAN).
+// coming from the apply's reduction (S_APMEAN).  b32 is the forward cycle's b (cycle
+// layout).
 template <bool NS>
 __global__ void __launch_bounds__(BLK) k_update_pp(double* __restrict__ x, double* __restrict__ r,
                                                    const float* __restrict__ phi, const float* __restrict__ plo,
@@ -439,7 +464,7 @@ __global__ void __launch_bounds__(BLK) k_update_pp(double* __restrict__ x, doubl
             double rn = rv[q] - alpha * av[q];
             if (NS && (fv[q] & 1)) rn = rn + shift;
             r[i + q * st] = rn;
-            b32[i + q * st] = d2f_bits(rn);
+            b32[cyc(i + q * st)] = d2f_bits(rn);
             rr += rn * rn;
         }
     }
@@ -448,7 +473,7 @@ __global__ void __launch_bounds__(BLK) k_update_pp(double* __restrict__ x, doubl
         double rn = r[i] - alpha * Ap[i];
         if (NS && (flags[i] & 1)) rn = rn + shift;
         r[i] = rn;
-        b32[i] = d2f_bits(rn);
+        b32[cyc(i)] = d2f_bits(rn);
         rr += rn * rn;
     }
     red_finish(R, blockIdx.x, rr, 0.0, sh);
@@ -456,14 +481,15 @@ __global__ void __launch_bounds__(BLK) k_update_pp(double* __restrict__ x, doubl
 
 // p = z + beta p (first: p = z) for p kept as FP32 pairs, in pair arithmetic (beta split
 // once, TwoProd by FMA, TwoSum; about 2^-47 relative, no FP64 instruction): the same p
-// then enters both x += alpha p and the apply, so CG's recurrences stay consistent.
+// then enters both x += alpha p and the apply, so CG's recurrences stay consistent.  z is
+// the forward cycle's u (cycle layout).
 template <class TZ>
 __global__ void k_pupdate_pp(float* __restrict__ hi, float* __restrict__ lo, const TZ* __restrict__ z,
                              const double* __restrict__ S, int n, int first) {
     pdl_enter();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const float zi = (float)z[i];
+    const float zi = (float)z[cyc(i)];
     DF v{zi, 0.0f};
     if (!first) {
         v = df_mul(df_split(S[S_BETA]), DF{hi[i], lo[i]});
@@ -474,8 +500,8 @@ __global__ void k_pupdate_pp(float* __restrict__ hi, float* __restrict__ lo, con
     lo[i] = v.lo;
 }
 
-// r -= mean on leaves (null-space shift of Sec. 2.2) and b32 = r.
-template <class TO, class TB>
+// r -= mean on leaves (null-space shift of Sec. 2.2) and b32 = r (cycle layout when CY).
+template <class TO, class TB, bool CY = false>
 __global__ void k_project(TO* __restrict__ r, const uint8_t* __restrict__ flags, const double* __restrict__ S,
                           TB* __restrict__ b32, int n) {
     pdl_enter();
@@ -484,12 +510,13 @@ __global__ void k_project(TO* __restrict__ r, const uint8_t* __restrict__ flags,
     TO v = r[i];
     if (flags[i] & 1) v = v - TO(S[S_MEAN]);
     r[i] = v;
-    if (b32) b32[i] = cvt<TB>(v);
+    if (b32) b32[vidx<CY>(i)] = cvt<TB>(v);
 }
 
 // (a, b) and sum(a) over the first n cells, reduced into R
-// (a, b) over the first n cells; with SUM also sum(a) (the null-space mean of Sec. 2.2)
-template <class TA, class TB, bool SUM>
+// (a, b) over the first n cells; with SUM also sum(a) (the null-space mean of Sec. 2.2);
+// CY: b in the cycle layout
+template <class TA, class TB, bool SUM, bool CY = false>
 __global__ void __launch_bounds__(BLK) k_dot(const TA* __restrict__ a, const TB* __restrict__ b, int n, Red R) {
     pdl_enter();
     __shared__ double sh[32];
@@ -500,7 +527,7 @@ __global__ void __launch_bounds__(BLK) k_dot(const TA* __restrict__ a, const TB*
         TA av[4];
         TB bv[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) { av[q] = a[i + q * st]; bv[q] = b[i + q * st]; }
+        for (int q = 0; q < 4; ++q) { av[q] = a[i + q * st]; bv[q] = b[vidx<CY>(i + q * st)]; }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const double ai = cvt<double>(av[q]);
@@ -510,7 +537,7 @@ __global__ void __launch_bounds__(BLK) k_dot(const TA* __restrict__ a, const TB*
     }
     for (; i < n; i += st) {
         const double ai = cvt<double>(a[i]);
-        v += ai * cvt<double>(b[i]);
+        v += ai * cvt<double>(b[vidx<CY>(i)]);
         if (SUM) s += ai;
     }
     red_finish(R, blockIdx.x, v, s, sh);
@@ -643,13 +670,14 @@ __global__ void __launch_bounds__(BLK) k_leafsum(const double* __restrict__ x, c
     red_finish(R, blockIdx.x, 0.0, v, sh);
 }
 
-template <class TO, class TZ>
+// p = z (first) or z + beta p; CY: z in the cycle layout
+template <class TO, class TZ, bool CY = false>
 __global__ void k_pupdate(TO* __restrict__ p, const TZ* __restrict__ z, const double* __restrict__ S, int n,
                           int first) {
     pdl_enter();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const TO zi = cvt<TO>(z[i]);
+    const TO zi = cvt<TO>(z[vidx<CY>(i)]);
     p[i] = first ? zi : zi + TO(S[S_BETA]) * p[i];
 }
 

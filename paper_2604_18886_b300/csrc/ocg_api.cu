@@ -497,7 +497,7 @@ struct Cycle {
             using TW = typename CoefTypes<decltype(C)>::TW;
             const LevelArgs A = h->t->largs(m);
             launch(c, -1, m, A.ncell, [&] {
-                launch_k(k_osweep<TV, TC, TW>, nblk(A.ncell / 8, OBLK), OBLK, 0, c.st, A, h->t->tables(), C, U, B, 0, 0, 1);
+                launch_k(k_osweep<TV, TC, TW, 2>, nblk(A.ncell / 8, OBLK), OBLK, 0, c.st, A, h->t->tables(), C, U, B, 0);
             });
         });
         ck_launch("fixb");
@@ -516,8 +516,10 @@ struct Cycle {
                 else if (form == OCG_SWEEP_TILE)
                     launch_k(k_tsweep<TV, TC, TW>, nblk(A.ncell / 8, TBLK), TBLK, 0, c.st, A, h->t->tables(), C, U, B, colour,
                                                                                   prolong);
+                else if (colour)
+                    launch_k(k_osweep<TV, TC, TW, 1>, nblk(A.ncell / 8, OBLK), OBLK, 0, c.st, A, h->t->tables(), C, U, B, prolong);
                 else
-                    launch_k(k_osweep<TV, TC, TW>, nblk(A.ncell / 8, OBLK), OBLK, 0, c.st, A, h->t->tables(), C, U, B, colour, prolong, 0);
+                    launch_k(k_osweep<TV, TC, TW, 0>, nblk(A.ncell / 8, OBLK), OBLK, 0, c.st, A, h->t->tables(), C, U, B, prolong);
             });
         });
         ck_launch("sweep");
@@ -764,8 +766,8 @@ void autotune_sweeps(ocg_hier* h) {
     const HostTree& H = h->t->H;
     if (!h->cap) ck(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking), "cudaStreamCreate");
     cudaStream_t cs = h->cap;
-    ck(cudaMemsetAsync(h->U, 0, H.ncell * sizeof(double), cs), "memset");
-    ck(cudaMemsetAsync(h->B, 0, H.ncell * sizeof(double), cs), "memset");
+    ck(cudaMemsetAsync(h->U, 0, cyc_len(H.ncell) * sizeof(double), cs), "memset");
+    ck(cudaMemsetAsync(h->B, 0, cyc_len(H.ncell) * sizeof(double), cs), "memset");
     cudaEvent_t e0, e1;
     ck(cudaEventCreate(&e0), "cudaEventCreate");
     ck(cudaEventCreate(&e1), "cudaEventCreate");
@@ -970,6 +972,8 @@ struct PcgImpl {
     // the mixed forward solve keeps p as FP32 pairs: hi in the first n floats of the FP64
     // array, lo in the next n
     static constexpr bool PP = !TR && std::is_same<TO, double>::value && std::is_same<TC, float>::value;
+    // the forward cycle keeps u and b in the cycle layout (cyc); the transposed one does not
+    static constexpr bool CY = !TR;
     float* hi(double* v) { return (float*)v; }
     float* lo(double* v) { return (float*)v + n(); }
     void pupdate(int first) {
@@ -978,7 +982,7 @@ struct PcgImpl {
                 launch_k(k_pupdate_pp<TV>, gb(), BLK, 0, c.st, hi(h->p), lo(h->p), (const TV*)Z(), (const double*)h->S,
                          n(), first);
             else
-                launch_k(k_pupdate<TO, TV>, gb(), BLK, 0, c.st, p(), Z(), h->S, n(), first);
+                launch_k(k_pupdate<TO, TV, CY>, gb(), BLK, 0, c.st, p(), Z(), h->S, n(), first);
         });
     }
 
@@ -986,7 +990,7 @@ struct PcgImpl {
         if (warm) launch(c, -1, 0, n(), [&] { launch_k(k_cast<double, TO>, gb(), BLK, 0, c.st, h->xt, x(), n()); });
         else zero(h->x, n() * sizeof(TO));
         zero(h->p, n() * sizeof(TO));
-        zero(h->B, H().ncell * sizeof(TV));
+        zero(h->B, cyc_len(H().ncell) * sizeof(TV));
         launch(c, -1, 0, n(), [&] { launch_k(k_cast<double, TO>, gb(), BLK, 0, c.st, h->bt, r(), n()); });
         launch(c, -1, 0, n(), [&] { launch_k(k_dot<TO, TO, true>, rb(), BLK, 0, c.st, r(), r(), n(), make_red(h, rb(), OP_BB)); });
         if (warm) {
@@ -995,10 +999,10 @@ struct PcgImpl {
             else apply_outer<TO, TC, TW>(h, Co, x(), Ap(), OP_NONE, c);
             launch(c, -1, 0, n(), [&] { launch_k(k_sub<TO>, gb(), BLK, 0, c.st, r(), (const TO*)Ap(), n()); });
         }
-        launch(c, -1, 0, n(), [&] { launch_k(k_project<TO, TV>, gb(), BLK, 0, c.st, r(), h->t->flags, h->S, B(), n()); });
+        launch(c, -1, 0, n(), [&] { launch_k(k_project<TO, TV, CY>, gb(), BLK, 0, c.st, r(), h->t->flags, h->S, B(), n()); });
         ck_launch("begin");
         precondition();
-        launch(c, -1, 0, n(), [&] { launch_k(k_dot<TO, TV, false>, rb(), BLK, 0, c.st, r(), Z(), n(), make_red(h, rb(), OP_RZ0)); });
+        launch(c, -1, 0, n(), [&] { launch_k(k_dot<TO, TV, false, CY>, rb(), BLK, 0, c.st, r(), Z(), n(), make_red(h, rb(), OP_RZ0)); });
         pupdate(1);
         ck_launch("begin");
         half_a();
@@ -1011,7 +1015,7 @@ struct PcgImpl {
             ct.seed((const TV*)B());
             ct.run();
         } else {
-            zero(h->U, H().ntree * sizeof(TV));
+            zero(h->U, cyc_len(H().ntree) * sizeof(TV));   // the tree cells' positions and a few coarse cells
             Cycle<TV>{h, U(), B(), c}.run();
         }
     }
@@ -1031,18 +1035,18 @@ struct PcgImpl {
                              (const float*)lo(h->p), (const double*)h->Ap, (const uint8_t*)nullptr,
                              (float*)B(), n(), R);
             } else {
-                if (ns) launch_k(k_update<TO, TV, true>, rb(), BLK, 0, c.st, x(), r(), p(), Ap(), nullptr, n(), R);
-                else launch_k(k_update<TO, TV, false>, rb(), BLK, 0, c.st, x(), r(), p(), Ap(), B(), n(), R);
+                if (ns) launch_k(k_update<TO, TV, true, CY>, rb(), BLK, 0, c.st, x(), r(), p(), Ap(), nullptr, n(), R);
+                else launch_k(k_update<TO, TV, false, CY>, rb(), BLK, 0, c.st, x(), r(), p(), Ap(), B(), n(), R);
             }
         });
         // the zero-mean shift of r (fused into the update of the pair-stored mixed form)
         if (ns && !PP)
-            launch(c, -1, 0, n(), [&] { launch_k(k_project<TO, TV>, gb(), BLK, 0, c.st, r(), h->t->flags, h->S, B(), n()); });
+            launch(c, -1, 0, n(), [&] { launch_k(k_project<TO, TV, CY>, gb(), BLK, 0, c.st, r(), h->t->flags, h->S, B(), n()); });
         ck_launch("half_a");
     }
     void half_b() {
         precondition();
-        launch(c, -1, 0, n(), [&] { launch_k(k_dot<TO, TV, false>, rb(), BLK, 0, c.st, r(), Z(), n(), make_red(h, rb(), OP_BETA)); });
+        launch(c, -1, 0, n(), [&] { launch_k(k_dot<TO, TV, false, CY>, rb(), BLK, 0, c.st, r(), Z(), n(), make_red(h, rb(), OP_BETA)); });
         pupdate(0);
         ck_launch("half_b");
     }
@@ -1223,8 +1227,9 @@ void ensure_work(ocg_hier* h) {
     const HostTree& H = h->t->H;
     const int64_t n = H.ntree;
     for (double** v : {&h->x, &h->r, &h->p, &h->Ap, &h->bt, &h->xt, &h->yt}) *v = dalloc<double>(n);
-    h->U = dalloc<double>(H.ncell);
-    h->B = dalloc<double>(H.ncell);
+    // the cycle's u and b: FP64 or FP32, in the cycle layout (whole 64-cell groups)
+    h->U = dalloc<double>(cyc_len(H.ncell));
+    h->B = dalloc<double>(cyc_len(H.ncell));
     h->S = dalloc<double>(S_COUNT);
     ck(cudaMallocHost((void**)&h->hS, S_COUNT * sizeof(double)), "cudaMallocHost");
     h->part = dalloc<double>(3 * ((int64_t)nblk(n) + H.D + 8));
@@ -1786,14 +1791,14 @@ int ocg_vcycle(ocg_hier* h, int32_t dtype, const void* r, void* z, void* stream)
             using TV = std::remove_pointer_t<decltype(tag)>;
             TV* U = (TV*)h->U;
             TV* B = (TV*)h->B;
-            ck(cudaMemsetAsync(U, 0, H.ncell * sizeof(TV), st), "memset");
-            ck(cudaMemsetAsync(B, 0, H.ncell * sizeof(TV), st), "memset");
+            ck(cudaMemsetAsync(U, 0, cyc_len(H.ncell) * sizeof(TV), st), "memset");
+            ck(cudaMemsetAsync(B, 0, cyc_len(H.ncell) * sizeof(TV), st), "memset");
             launch(c, -1, 0, H.nleaf, [&] {
-                launch_k(k_scatter<TV, TV>, nblk(H.nleaf), BLK, 0, st, (const TV*)r, B, t->leaf_cell, (int)H.nleaf);
+                launch_k(k_scatter<TV, TV, true>, nblk(H.nleaf), BLK, 0, st, (const TV*)r, B, t->leaf_cell, (int)H.nleaf);
             });
             Cycle<TV>{h, U, B, c}.run();
             launch(c, -1, 0, H.nleaf, [&] {
-                launch_k(k_gather<TV, TV>, nblk(H.nleaf), BLK, 0, st, U, (TV*)z, t->leaf_cell, (int)H.nleaf);
+                launch_k(k_gather<TV, TV, true>, nblk(H.nleaf), BLK, 0, st, U, (TV*)z, t->leaf_cell, (int)H.nleaf);
             });
             ck_launch("vcycle");
         };

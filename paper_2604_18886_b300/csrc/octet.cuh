@@ -131,6 +131,69 @@ __device__ __forceinline__ void ld_layer(const __nv_bfloat16* __restrict__ p, in
     }
 }
 
+// ------------------------------------------------ vectors in either layout (CY: cycle)
+// One colour chunk (the 4 cells of colour col of the octet at c8, in the colour's slot
+// order k = s >> 1) of a vector in the cycle layout.
+__device__ __forceinline__ void ldk4(const float* __restrict__ U, int c8, int col, float (&r)[4]) {
+    const float4 a = *reinterpret_cast<const float4*>(U + cyc8(c8) + 32 * col);
+    r[0] = a.x; r[1] = a.y; r[2] = a.z; r[3] = a.w;
+}
+__device__ __forceinline__ void ldk4(const double* __restrict__ U, int c8, int col, double (&r)[4]) {
+    const double2* p = reinterpret_cast<const double2*>(U + cyc8(c8) + 32 * col);
+    const double2 a = p[0], b = p[1];
+    r[0] = a.x; r[1] = a.y; r[2] = b.x; r[3] = b.y;
+}
+__device__ __forceinline__ void stk4(float* __restrict__ U, int c8, int col, const float (&r)[4]) {
+    *reinterpret_cast<float4*>(U + cyc8(c8) + 32 * col) = make_float4(r[0], r[1], r[2], r[3]);
+}
+__device__ __forceinline__ void stk4(double* __restrict__ U, int c8, int col, const double (&r)[4]) {
+    double2* p = reinterpret_cast<double2*>(U + cyc8(c8) + 32 * col);
+    p[0] = make_double2(r[0], r[1]);
+    p[1] = make_double2(r[2], r[3]);
+}
+// slot of the k-th cell of colour col
+__host__ __device__ __forceinline__ constexpr int colour_slot(int col, int k) {
+    return 2 * k + (((k ^ (k >> 1)) & 1) ^ col);
+}
+// the 8 values of the octet at c8 in slot order, from either layout
+template <bool CY, class TV>
+__device__ __forceinline__ void ldv8(const TV* __restrict__ U, int c8, TV (&r)[8]) {
+    if (CY) {
+        TV k0[4], k1[4];
+        ldk4(U, c8, 0, k0);
+        ldk4(U, c8, 1, k1);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) { r[colour_slot(0, k)] = k0[k]; r[colour_slot(1, k)] = k1[k]; }
+    } else {
+        ld8(U + c8, r);
+    }
+}
+template <bool CY, class TV>
+__device__ __forceinline__ void stv8(TV* __restrict__ U, int c8, const TV (&r)[8]) {
+    if (CY) {
+        TV k0[4], k1[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) { k0[k] = r[colour_slot(0, k)]; k1[k] = r[colour_slot(1, k)]; }
+        stk4(U, c8, 0, k0);
+        stk4(U, c8, 1, k1);
+    } else {
+        st8(U + c8, r);
+    }
+}
+// the four cells of the octet at n8 with bit a equal to side, in sub-face order q (as
+// ld_layer), from either layout
+template <bool CY, class TV>
+__device__ __forceinline__ void ldv_layer(const TV* __restrict__ U, int n8, int a, int side, TV (&r)[4]) {
+    if (CY) {
+        TV v[8];
+        ldv8<true>(U, n8, v);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) r[q] = v[clear_slot(a, q) | (side << a)];
+    } else {
+        ld_layer(U + n8, a, side, false, r);
+    }
+}
+
 // Coordinates of octet o in a lexicographic ni^3 grid (shifts when ni is a power of two).
 __device__ __forceinline__ void octet_coords(int o, int ni, int& I, int& J, int& K) {
     if ((ni & (ni - 1)) == 0) {
@@ -161,11 +224,12 @@ struct OctState {
     int nact;
 };
 
-// Loads u and the coefficients of the octet whose first cell is c8.
-template <class TV, class TC, class TW>
+// Loads u (plain or cycle layout, CY) and the coefficients of the octet whose first cell
+// is c8.
+template <class TV, class TC, class TW, bool CY = false>
 __device__ __forceinline__ void load_octet(const TV* __restrict__ U, const Coefs<TC, TW>& C, int c8,
                                            OctState<TV>& S) {
-    ld8(U + c8, S.u);
+    ldv8<CY>(U, c8, S.u);
     ldc8(C.d + c8, S.d);
     ldc8(C.cx + c8, S.cm[0]);
     ldc8(C.cy + c8, S.cm[1]);
@@ -221,9 +285,9 @@ __device__ __forceinline__ T divide(T a, T b) { return a / b; }
 template <>
 __device__ __forceinline__ float divide<float>(float a, float b) { return __fdividef(a, b); }
 
-// Au[s] = (A^m u) for the 8 cells of local octet o (global og) of the level A; U is read
-// for the neighbouring octets and the coarser leaves K of T faces.
-template <class TV, class TC, class TW>
+// Au[s] = (A^m u) for the 8 cells of local octet o (global og) of the level A; U (plain or
+// cycle layout, CY) is read for the neighbouring octets and the coarser leaves K of T faces.
+template <class TV, class TC, class TW, bool CY = false>
 __device__ __forceinline__ void octet_Au(const Tables& T, const Coefs<TC, TW>& C, const TV* __restrict__ U,
                                          const LevelArgs& A, int o, int og, const OctState<TV>& S, TV (&Au)[8]) {
 #pragma unroll
@@ -247,14 +311,14 @@ __device__ __forceinline__ void octet_Au(const Tables& T, const Coefs<TC, TW>& C
         if (v >= 0) {
             const int n8 = off + 8 * v;
             TV nu[4];
-            ld_layer(U + n8, a, 1, false, nu);
+            ldv_layer<CY>(U, n8, a, 1, nu);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int s = clear_slot(a, q);
                 Au[s] += S.cm[a][s] * nu[q];
             }
         } else if (v <= -2) {
-            const TV uK = U[-2 - v];
+            const TV uK = U[vidx<CY>(-2 - v)];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int s = clear_slot(a, q);
@@ -269,14 +333,14 @@ __device__ __forceinline__ void octet_Au(const Tables& T, const Coefs<TC, TW>& C
             const TC* cc = a == 0 ? C.cx : (a == 1 ? C.cy : C.cz);
             TV nu[4], nc[4];
             TC ncr[4];
-            ld_layer(U + n8, a, 0, false, nu);
+            ldv_layer<CY>(U, n8, a, 0, nu);
             ld_layer(cc + n8, a, 0, true, ncr);
 #pragma unroll
             for (int q = 0; q < 4; ++q) nc[q] = TV(tov(ncr[q]));
 #pragma unroll
             for (int q = 0; q < 4; ++q) Au[clear_slot(a, q) | bit] += nc[q] * nu[q];
         } else if (w <= -2) {
-            const TV uK = U[-2 - w];
+            const TV uK = U[vidx<CY>(-2 - w)];
             const int t = __ldg(T.trec + og);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
@@ -288,11 +352,13 @@ __device__ __forceinline__ void octet_Au(const Tables& T, const Coefs<TC, TW>& C
     }
 }
 
+// u of the children octet co += uP - (mean of its active cells); U in the cycle layout
+// (both colour chunks rewritten, the inactive cells unchanged: one thread owns the octet)
 template <class TV, class TC>
 __device__ __forceinline__ void octet_prolong(const TC* __restrict__ d, TV* __restrict__ U, int co, TV uP) {
     const int c8 = 8 * co;
     TV v[8], dd[8];
-    ld8(U + c8, v);
+    ldv8<true>(U, c8, v);
     ldc8(d + c8, dd);
     TV s = TV(0);
     int n = 0;
@@ -303,55 +369,119 @@ __device__ __forceinline__ void octet_prolong(const TC* __restrict__ d, TV* __re
     const TV delta = uP - s * inv_count<TV>(n);
 #pragma unroll
     for (int q = 0; q < 8; ++q)
-        if (dd[q] != TV(0)) U[c8 + q] = v[q] + delta;
+        if (dd[q] != TV(0)) v[q] = v[q] + delta;
+    stv8<true>(U, c8, v);
 }
 
-// Red-black colour sweep (Sec. 2.3) of a level, or (fixb) completion of the FAS
-// right-hand side b += A^m u* on cells with children (Alg. 4).  prolong: after the
-// update, every cell with children prolongs its final value onto them.
+// Completion of the FAS right-hand side b += A^m u* on the cells with children of a level
+// (Alg. 4); u and b in the cycle layout.
 template <class TV, class TC, class TW>
-__device__ __forceinline__ void osweep_octet(const LevelArgs& A, const Tables& T, const Coefs<TC, TW>& C,
-                                             TV* __restrict__ U, TV* __restrict__ B, int o, int colour,
-                                             int prolong, int fixb) {
+__device__ __forceinline__ void ofixb_octet(const LevelArgs& A, const Tables& T, const Coefs<TC, TW>& C,
+                                            const TV* __restrict__ U, TV* __restrict__ B, int o) {
     const int c8 = A.off + 8 * o;
     const int og = c8 >> 3;
     OctState<TV> S;
-    load_octet<TV, TC, TW>(U, C, c8, S);
+    load_octet<TV, TC, TW, true>(U, C, c8, S);
     octet_mean(S);
     TV b[8], Au[8];
-    ld8(B + c8, b);
-    octet_Au<TV, TC, TW>(T, C, U, A, o, og, S, Au);
-    if (fixb) {
+    ldv8<true>(B, c8, b);
+    octet_Au<TV, TC, TW, true>(T, C, U, A, o, og, S, Au);
 #pragma unroll
-        for (int s = 0; s < 8; ++s)
-            if (__ldg(T.child_oct + c8 + s) >= 0) B[c8 + s] = b[s] + Au[s];
-        return;
+    for (int s = 0; s < 8; ++s)
+        if (__ldg(T.child_oct + c8 + s) >= 0) b[s] = b[s] + Au[s];
+    stv8<true>(B, c8, b);
+}
+
+// Red-black colour sweep (Sec. 2.3) of a level, colour COL: u += (b - A^m u) / c on the
+// 4 cells of colour COL of octet o, every read from the state at launch.  Only the rows
+// of the colour are formed (the terms of each row summed in the order of octet_Au); from
+// each neighbouring octet only its other-colour chunk is read, which holds the 2 cells
+// facing this octet's cells of colour COL; b is read and u written as one chunk each.
+// prolong: after the update, every cell with children prolongs its final value onto them.
+template <class TV, class TC, class TW, int COL>
+__device__ __forceinline__ void osweep_colour(const LevelArgs& A, const Tables& T, const Coefs<TC, TW>& C,
+                                              TV* __restrict__ U, const TV* __restrict__ B, int o, int prolong) {
+    const int c8 = A.off + 8 * o;
+    const int og = c8 >> 3;
+    int nb[6];
+    octet_neighbours(T, A.ni, o, og, nb);
+    OctState<TV> S;
+    load_octet<TV, TC, TW, true>(U, C, c8, S);
+    TV b[4];
+    ldk4(B, c8, COL, b);
+    octet_mean(S);
+    const int off = A.off;
+    TV Au[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int s = colour_slot(COL, k);
+        Au[k] = S.d[s] * S.u[s];
     }
-    TV un[8];
 #pragma unroll
-    for (int s = 0; s < 8; ++s) {
-        un[s] = S.u[s];
-        if (((__popc(s) & 1) == colour) && S.d[s] != TV(0)) {
-            un[s] = S.u[s] + divide(b[s] - Au[s], S.d[s]);
-            U[c8 + s] = un[s];
+    for (int a = 0; a < 3; ++a) {
+        const int bit = 1 << a;
+        const int v = nb[2 * a], w = nb[2 * a + 1];
+        TV vu[4], wu[4];
+        if (v >= 0) ldk4(U, off + 8 * v, 1 - COL, vu);
+        if (w >= 0) ldk4(U, off + 8 * w, 1 - COL, wu);
+        const TV uKv = v <= -2 ? U[cyc(-2 - v)] : TV(0);
+        const TV uKw = w <= -2 ? U[cyc(-2 - w)] : TV(0);
+        const TC* cc = a == 0 ? C.cx : (a == 1 ? C.cy : C.cz);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int s = colour_slot(COL, k), t = s ^ bit;
+            // internal face (s, t), coefficient kept by the + cell
+            Au[k] += ((s & bit) ? S.cm[a][s] : S.cm[a][t]) * S.u[t];
+            if (!(s & bit)) {
+                // - face: the - neighbour's cell s | bit (other colour, chunk slot t >> 1)
+                if (v >= 0) Au[k] += S.cm[a][s] * vu[t >> 1];
+                else if (v <= -2) Au[k] += S.cm[a][s] * (S.u[s] + (uKv - S.ubar) * TV(0.5));
+            } else {
+                // + face: the + neighbour's cell t = s & ~bit keeps the face coefficient; at a
+                // T face the fine weight is in the T record
+                if (w >= 0) Au[k] += TV(tov(__ldg(cc + off + 8 * w + t))) * wu[t >> 1];
+                else if (w <= -2) {
+                    const TV cf = TV(tov(__ldg(C.tw + ((2 * a + 1) * 4 + sub_index(a, t)) * T.nt + __ldg(T.trec + og))));
+                    Au[k] += cf * (S.u[s] + (uKw - S.ubar) * TV(0.5));
+                }
+            }
         }
     }
+    TV un[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int s = colour_slot(COL, k);
+        un[k] = S.d[s] != TV(0) ? S.u[s] + divide(b[k] - Au[k], S.d[s]) : S.u[s];
+    }
+    stk4(U, c8, COL, un);
     if (prolong) {
 #pragma unroll
         for (int s = 0; s < 8; ++s) {
             const int co = __ldg(T.child_oct + c8 + s);
-            if (co >= 0) octet_prolong<TV>(C.d, U, co, un[s]);
+            if (co >= 0) octet_prolong<TV>(C.d, U, co, cyc_colour(s) == COL ? un[s >> 1] : S.u[s]);
         }
     }
 }
 
+// Either colour sweep (colour at run time) or, with fixb, the FAS right-hand-side pass.
 template <class TV, class TC, class TW>
+__device__ __forceinline__ void osweep_octet(const LevelArgs& A, const Tables& T, const Coefs<TC, TW>& C,
+                                             TV* __restrict__ U, TV* __restrict__ B, int o, int colour,
+                                             int prolong, int fixb) {
+    if (fixb) ofixb_octet<TV, TC, TW>(A, T, C, U, B, o);
+    else if (colour) osweep_colour<TV, TC, TW, 1>(A, T, C, U, B, o, prolong);
+    else osweep_colour<TV, TC, TW, 0>(A, T, C, U, B, o, prolong);
+}
+
+// MODE 0 / 1: colour sweep of that colour; 2: the FAS right-hand-side pass
+template <class TV, class TC, class TW, int MODE>
 __global__ void __launch_bounds__(OBLK, sizeof(TV) == 4 ? 16 : 8) k_osweep(LevelArgs A, Tables T, Coefs<TC, TW> C, TV* __restrict__ U,
-                                                 TV* __restrict__ B, int colour, int prolong, int fixb) {
+                                                 TV* __restrict__ B, int prolong) {
     pdl_enter();
     const int o = blockIdx.x * OBLK + threadIdx.x;
     if (o >= A.ncell / 8) return;
-    osweep_octet<TV, TC, TW>(A, T, C, U, B, o, colour, prolong, fixb);
+    if (MODE == 2) ofixb_octet<TV, TC, TW>(A, T, C, U, B, o);
+    else osweep_colour<TV, TC, TW, MODE>(A, T, C, U, B, o, prolong);
 }
 
 // ------------------------------------------------------------ shared-block sweep
@@ -381,7 +511,7 @@ __global__ void __launch_bounds__(TBLK) k_tsweep(LevelArgs A, Tables T, Coefs<TC
     int nb[6];
     octet_neighbours(T, A.ni, valid ? o : noct - 1, og, nb);
     OctState<TV> S;
-    load_octet<TV, TC, TW>(U, C, c8, S);
+    load_octet<TV, TC, TW, true>(U, C, c8, S);
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
         sh.u[q * TBLK + lo] = S.u[q];
@@ -393,7 +523,7 @@ __global__ void __launch_bounds__(TBLK) k_tsweep(LevelArgs A, Tables T, Coefs<TC
     if (!valid) return;
     octet_mean(S);
     TV b[8], Au[8];
-    ld8(B + c8, b);
+    ldv8<true>(B, c8, b);
 #pragma unroll
     for (int q = 0; q < 8; ++q) Au[q] = S.d[q] * S.u[q];
     const int off = A.off;
@@ -417,12 +547,12 @@ __global__ void __launch_bounds__(TBLK) k_tsweep(LevelArgs A, Tables T, Coefs<TC
                 for (int q = 0; q < 4; ++q) nu[q] = sh.u[(clear_slot(a, q) | bit) * TBLK + lv];
             } else {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) nu[q] = U[off + 8 * v + (clear_slot(a, q) | bit)];
+                for (int q = 0; q < 4; ++q) nu[q] = U[cyc(off + 8 * v + (clear_slot(a, q) | bit))];
             }
 #pragma unroll
             for (int q = 0; q < 4; ++q) Au[clear_slot(a, q)] += S.cm[a][clear_slot(a, q)] * nu[q];
         } else if (v <= -2) {
-            const TV uK = U[-2 - v];
+            const TV uK = U[cyc(-2 - v)];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int s = clear_slot(a, q);
@@ -443,14 +573,14 @@ __global__ void __launch_bounds__(TBLK) k_tsweep(LevelArgs A, Tables T, Coefs<TC
                 const TC* cc = a == 0 ? C.cx : (a == 1 ? C.cy : C.cz);
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    nu[q] = U[off + 8 * w + clear_slot(a, q)];
+                    nu[q] = U[cyc(off + 8 * w + clear_slot(a, q))];
                     nc[q] = TV(tov(__ldg(cc + off + 8 * w + clear_slot(a, q))));
                 }
             }
 #pragma unroll
             for (int q = 0; q < 4; ++q) Au[clear_slot(a, q) | bit] += nc[q] * nu[q];
         } else if (w <= -2) {
-            const TV uK = U[-2 - w];
+            const TV uK = U[cyc(-2 - w)];
             const int t = __ldg(T.trec + og);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
@@ -466,7 +596,7 @@ __global__ void __launch_bounds__(TBLK) k_tsweep(LevelArgs A, Tables T, Coefs<TC
         un[s] = S.u[s];
         if (((__popc(s) & 1) == colour) && S.d[s] != TV(0)) {
             un[s] = S.u[s] + divide(b[s] - Au[s], S.d[s]);
-            U[c8 + s] = un[s];
+            U[cyc(c8 + s)] = un[s];
         }
     }
     if (prolong) {
@@ -503,8 +633,8 @@ __device__ __forceinline__ void csweep_cell(const LevelArgs& A, const Tables& T,
     const int lc = valid ? tid : (A.ncell - 8 + (tid & 7));
     const int g = A.off + lc;
     const int s = lc & 7, o = lc >> 3, og = g >> 3;
-    const TV u = U[g];
-    const TV b = B[g];
+    const TV u = U[cyc(g)];
+    const TV b = B[cyc(g)];
     const TV dd = TV(tov(__ldg(C.d + g)));
     const TV cm[3] = {TV(tov(__ldg(C.cx + g))), TV(tov(__ldg(C.cy + g))), TV(tov(__ldg(C.cz + g)))};
     const bool act = dd != TV(0);
@@ -537,22 +667,22 @@ __device__ __forceinline__ void csweep_cell(const LevelArgs& A, const Tables& T,
             if (v >= 0) {
                 const int ng = A.off + 8 * v + (s ^ bit);
                 const TC* cc = a == 0 ? C.cx : (a == 1 ? C.cy : C.cz);
-                Au += TV(tov(__ldg(cc + ng))) * U[ng];
+                Au += TV(tov(__ldg(cc + ng))) * U[cyc(ng)];
             } else if (v <= -2) {
                 const int t = __ldg(T.trec + og);
                 const TV cf = TV(tov(__ldg(C.tw + ((2 * a + 1) * 4 + sub_index(a, s)) * T.nt + t)));
-                Au += cf * (u + (U[-2 - v] - ubar) * TV(0.5));
+                Au += cf * (u + (U[cyc(-2 - v)] - ubar) * TV(0.5));
             }
         } else {
             Au += c_in * u_in;
-            if (v >= 0) Au += cm[a] * U[A.off + 8 * v + (s ^ bit)];
-            else if (v <= -2) Au += cm[a] * (u + (U[-2 - v] - ubar) * TV(0.5));
+            if (v >= 0) Au += cm[a] * U[cyc(A.off + 8 * v + (s ^ bit))];
+            else if (v <= -2) Au += cm[a] * (u + (U[cyc(-2 - v)] - ubar) * TV(0.5));
         }
     }
     TV un = u;
     if (valid && act && ((__popc(s) & 1) == colour)) {
         un = u + divide(b - Au, dd);
-        U[g] = un;
+        U[cyc(g)] = un;
     }
     if (prolong && valid) {
         const int co = __ldg(T.child_oct + g);
@@ -610,6 +740,28 @@ __device__ __forceinline__ void ldc4(const __nv_bfloat16* __restrict__ p, TV (&r
     r[0] = TV(f0.x); r[1] = TV(f0.y); r[2] = TV(f1.x); r[3] = TV(f1.y);
 }
 
+// z layer hz (slots 4 hz .. 4 hz + 3, in that order) of the octet at c8 of a vector in the
+// cycle layout: two pairs, ranks 2 hz and 2 hz + 1 of each colour chunk (layer 0: slots 0, 3
+// of colour 0 and 1, 2 of colour 1; layer 1: slots 5, 6 and 4, 7).
+__device__ __forceinline__ void ldh4(const float* __restrict__ U, int c8, int hz, float (&r)[4]) {
+    const float2 v0 = *reinterpret_cast<const float2*>(U + cyc8(c8) + 2 * hz);
+    const float2 v1 = *reinterpret_cast<const float2*>(U + cyc8(c8) + 32 + 2 * hz);
+    r[0] = hz ? v1.x : v0.x; r[1] = hz ? v0.x : v1.x; r[2] = hz ? v0.y : v1.y; r[3] = hz ? v1.y : v0.y;
+}
+__device__ __forceinline__ void ldh4(const double* __restrict__ U, int c8, int hz, double (&r)[4]) {
+    const double2 v0 = *reinterpret_cast<const double2*>(U + cyc8(c8) + 2 * hz);
+    const double2 v1 = *reinterpret_cast<const double2*>(U + cyc8(c8) + 32 + 2 * hz);
+    r[0] = hz ? v1.x : v0.x; r[1] = hz ? v0.x : v1.x; r[2] = hz ? v0.y : v1.y; r[3] = hz ? v1.y : v0.y;
+}
+__device__ __forceinline__ void sth4(float* __restrict__ U, int c8, int hz, const float (&r)[4]) {
+    *reinterpret_cast<float2*>(U + cyc8(c8) + 2 * hz) = hz ? make_float2(r[1], r[2]) : make_float2(r[0], r[3]);
+    *reinterpret_cast<float2*>(U + cyc8(c8) + 32 + 2 * hz) = hz ? make_float2(r[0], r[3]) : make_float2(r[1], r[2]);
+}
+__device__ __forceinline__ void sth4(double* __restrict__ U, int c8, int hz, const double (&r)[4]) {
+    *reinterpret_cast<double2*>(U + cyc8(c8) + 2 * hz) = hz ? make_double2(r[1], r[2]) : make_double2(r[0], r[3]);
+    *reinterpret_cast<double2*>(U + cyc8(c8) + 32 + 2 * hz) = hz ? make_double2(r[0], r[3]) : make_double2(r[1], r[2]);
+}
+
 template <class TV, class TC, class TW>
 __global__ void __launch_bounds__(BLK) k_qsweep(LevelArgs A, Tables T, Coefs<TC, TW> C, TV* __restrict__ U,
                                                 TV* __restrict__ B, int colour, int prolong) {
@@ -621,8 +773,8 @@ __global__ void __launch_bounds__(BLK) k_qsweep(LevelArgs A, Tables T, Coefs<TC,
     const int hz = tid & 1;
     const int c8 = A.off + 8 * o, og = c8 >> 3, base = c8 + 4 * hz;
     TV u[4], b[4], d[4], cx[4], cy[4], cz[4];
-    ld4(U + base, u);
-    ld4(B + base, b);
+    ldh4(U, c8, hz, u);
+    ldh4(B, c8, hz, b);
     ldc4<TV>(C.d + base, d);
     ldc4<TV>(C.cx + base, cx);
     ldc4<TV>(C.cy + base, cy);
@@ -657,11 +809,11 @@ __global__ void __launch_bounds__(BLK) k_qsweep(LevelArgs A, Tables T, Coefs<TC,
         const int v = octet_neighbour(T, A.ni, o, og, 0);
         if (v >= 0) {
             TV nu[4];
-            ld4(U + off + 8 * v + 4 * hz, nu);
+            ldh4(U, off + 8 * v, hz, nu);
             Au[0] += cx[0] * nu[1];
             Au[2] += cx[2] * nu[3];
         } else if (v <= -2) {
-            const TV uK = U[-2 - v];
+            const TV uK = U[cyc(-2 - v)];
             Au[0] += cx[0] * (u[0] + (uK - ubar) * half);
             Au[2] += cx[2] * (u[2] + (uK - ubar) * half);
         }
@@ -671,11 +823,11 @@ __global__ void __launch_bounds__(BLK) k_qsweep(LevelArgs A, Tables T, Coefs<TC,
         const int v = octet_neighbour(T, A.ni, o, og, 2);
         if (v >= 0) {
             TV nu[4];
-            ld4(U + off + 8 * v + 4 * hz, nu);
+            ldh4(U, off + 8 * v, hz, nu);
             Au[0] += cy[0] * nu[2];
             Au[1] += cy[1] * nu[3];
         } else if (v <= -2) {
-            const TV uK = U[-2 - v];
+            const TV uK = U[cyc(-2 - v)];
             Au[0] += cy[0] * (u[0] + (uK - ubar) * half);
             Au[1] += cy[1] * (u[1] + (uK - ubar) * half);
         }
@@ -685,12 +837,12 @@ __global__ void __launch_bounds__(BLK) k_qsweep(LevelArgs A, Tables T, Coefs<TC,
         const int w = octet_neighbour(T, A.ni, o, og, 1);
         if (w >= 0) {
             TV nu[4], nc[4];
-            ld4(U + off + 8 * w + 4 * hz, nu);
+            ldh4(U, off + 8 * w, hz, nu);
             ldc4<TV>(C.cx + off + 8 * w + 4 * hz, nc);
             Au[1] += nc[0] * nu[0];
             Au[3] += nc[2] * nu[2];
         } else if (w <= -2) {
-            const TV uK = U[-2 - w];
+            const TV uK = U[cyc(-2 - w)];
             const int t = __ldg(T.trec + og);
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
@@ -705,12 +857,12 @@ __global__ void __launch_bounds__(BLK) k_qsweep(LevelArgs A, Tables T, Coefs<TC,
         const int w = octet_neighbour(T, A.ni, o, og, 3);
         if (w >= 0) {
             TV nu[4], nc[4];
-            ld4(U + off + 8 * w + 4 * hz, nu);
+            ldh4(U, off + 8 * w, hz, nu);
             ldc4<TV>(C.cy + off + 8 * w + 4 * hz, nc);
             Au[2] += nc[0] * nu[0];
             Au[3] += nc[1] * nu[1];
         } else if (w <= -2) {
-            const TV uK = U[-2 - w];
+            const TV uK = U[cyc(-2 - w)];
             const int t = __ldg(T.trec + og);
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
@@ -725,11 +877,11 @@ __global__ void __launch_bounds__(BLK) k_qsweep(LevelArgs A, Tables T, Coefs<TC,
         const int v = octet_neighbour(T, A.ni, o, og, 4);
         if (v >= 0) {
             TV nu[4];
-            ld4(U + off + 8 * v + 4, nu);
+            ldh4(U, off + 8 * v, 1, nu);
 #pragma unroll
             for (int q = 0; q < 4; ++q) Au[q] += cz[q] * nu[q];
         } else if (v <= -2) {
-            const TV uK = U[-2 - v];
+            const TV uK = U[cyc(-2 - v)];
 #pragma unroll
             for (int q = 0; q < 4; ++q) Au[q] += cz[q] * (u[q] + (uK - ubar) * half);
         }
@@ -737,12 +889,12 @@ __global__ void __launch_bounds__(BLK) k_qsweep(LevelArgs A, Tables T, Coefs<TC,
         const int w = octet_neighbour(T, A.ni, o, og, 5);
         if (w >= 0) {
             TV nu[4], nc[4];
-            ld4(U + off + 8 * w, nu);
+            ldh4(U, off + 8 * w, 0, nu);
             ldc4<TV>(C.cz + off + 8 * w, nc);
 #pragma unroll
             for (int q = 0; q < 4; ++q) Au[q] += nc[q] * nu[q];
         } else if (w <= -2) {
-            const TV uK = U[-2 - w];
+            const TV uK = U[cyc(-2 - w)];
             const int t = __ldg(T.trec + og);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
@@ -758,7 +910,7 @@ __global__ void __launch_bounds__(BLK) k_qsweep(LevelArgs A, Tables T, Coefs<TC,
         un[q] = ((__popc(s) & 1) == colour && d[q] != TV(0)) ? u[q] + divide(b[q] - Au[q], d[q]) : u[q];
     }
     if (!valid) return;
-    st4(U + base, un);   // the other colour's values are rewritten unchanged
+    sth4(U, c8, hz, un);   // the other colour's values are rewritten unchanged
     if (prolong) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -777,18 +929,18 @@ __device__ __forceinline__ void orestrict_octet(const LevelArgs& A, const Tables
     const int c8 = A.off + 8 * o;
     const int og = c8 >> 3;
     OctState<TV> S;
-    load_octet<TV, TC, TW>(U, C, c8, S);
+    load_octet<TV, TC, TW, true>(U, C, c8, S);
     octet_mean(S);
     TV b[8], Au[8];
-    ld8(B + c8, b);
-    octet_Au<TV, TC, TW>(T, C, U, A, o, og, S, Au);
+    ldv8<true>(B, c8, b);
+    octet_Au<TV, TC, TW, true>(T, C, U, A, o, og, S, Au);
     TV rs = TV(0);
 #pragma unroll
     for (int s = 0; s < 8; ++s)
         if (S.d[s] != TV(0)) rs += b[s] - Au[s];
     const int P = __ldg(T.oct_parent + og);
-    B[P] = scale * rs;
-    U[P] = S.ubar;
+    B[cyc(P)] = scale * rs;
+    U[cyc(P)] = S.ubar;
 }
 
 template <class TV, class TC, class TW>
@@ -808,7 +960,7 @@ __global__ void __launch_bounds__(OBLK) k_oprolong(LevelArgs A, Tables T, const 
     const int o = blockIdx.x * OBLK + threadIdx.x;
     if (o >= A.ncell / 8) return;
     const int c8 = A.off + 8 * o;
-    octet_prolong<TV>(d, U, c8 >> 3, U[__ldg(T.oct_parent + (c8 >> 3))]);
+    octet_prolong<TV>(d, U, c8 >> 3, U[cyc(__ldg(T.oct_parent + (c8 >> 3)))]);
 }
 
 // Outer vector: parent value = mean of the active children (composite operator, Sec. 3.1).
@@ -1806,20 +1958,20 @@ __global__ void __launch_bounds__(256) k_ocoarsest(LevelArgs A, Tables T, Coefs<
         for (int o = threadIdx.x; o < noct; o += blockDim.x) {
             const int c8 = A.off + 8 * o;
             OctState<TV> S;
-            load_octet<TV, TC, TW>(U, C, c8, S);
+            load_octet<TV, TC, TW, true>(U, C, c8, S);
             octet_mean(S);
             TV b[8], Au[8];
-            ld8(B + c8, b);
-            octet_Au<TV, TC, TW>(T, C, U, A, o, c8 >> 3, S, Au);
+            ldv8<true>(B, c8, b);
+            octet_Au<TV, TC, TW, true>(T, C, U, A, o, c8 >> 3, S, Au);
             if (fixb) {
 #pragma unroll
                 for (int s = 0; s < 8; ++s)
-                    if (T.child_oct[c8 + s] >= 0) B[c8 + s] = b[s] + Au[s];
+                    if (T.child_oct[c8 + s] >= 0) B[cyc(c8 + s)] = b[s] + Au[s];
             } else {
 #pragma unroll
                 for (int s = 0; s < 8; ++s)
                     if (((__popc(s) & 1) == colour) && S.d[s] != TV(0))
-                        U[c8 + s] = S.u[s] + divide(b[s] - Au[s], S.d[s]);
+                        U[cyc(c8 + s)] = S.u[s] + divide(b[s] - Au[s], S.d[s]);
             }
         }
         __syncthreads();
@@ -1831,7 +1983,7 @@ __global__ void __launch_bounds__(256) k_ocoarsest(LevelArgs A, Tables T, Coefs<
     if (prolong) {
         for (int c = threadIdx.x; c < A.ncell; c += blockDim.x) {
             const int co = T.child_oct[A.off + c];
-            if (co >= 0) octet_prolong<TV>(C.d, U, co, U[A.off + c]);
+            if (co >= 0) octet_prolong<TV>(C.d, U, co, U[cyc(A.off + c)]);
         }
     }
 }
@@ -2103,8 +2255,8 @@ __device__ __forceinline__ void tail_cycle(const TailArgs& A, int fas, int prolo
         for (int o = threadIdx.x; o < no; o += blockDim.x) {
             const int g8 = L.off + 8 * o, q0 = L.sbase + o;
             TV u[8], b[8], d[8], cx[8], cy[8], cz[8];
-            ld8(U + g8, u);
-            ld8(B + g8, b);
+            ldv8<true>(U, g8, u);
+            ldv8<true>(B, g8, b);
             ldc8(C.d + g8, d);
             ldc8(C.cx + g8, cx);
             ldc8(C.cy + g8, cy);
@@ -2156,8 +2308,8 @@ __device__ __forceinline__ void tail_cycle(const TailArgs& A, int fas, int prolo
             TV u[8], b[8];
 #pragma unroll
             for (int sl = 0; sl < 8; ++sl) { u[sl] = M.u[L.sbase + sl * no + o]; b[sl] = M.b[L.sbase + sl * no + o]; }
-            st8(U + L.off + 8 * o, u);
-            st8(B + L.off + 8 * o, b);
+            stv8<true>(U, L.off + 8 * o, u);
+            stv8<true>(B, L.off + 8 * o, b);
         }
     }
     if (prolong) {
