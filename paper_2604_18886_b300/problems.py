@@ -73,7 +73,7 @@ class Problem:
     name: str
     desc: OctreeDesc
     bc: tuple                 # 6 wall codes
-    beta: str = "one"         # "one" or "cut" (fluid fraction of the solid geometry)
+    beta: str = "one"         # "one", "cut" (clamped fluid fraction), "cut_exact" or "cut_centre"
     rhs: str = "zero"         # "sin_dirichlet", "exp_sin_cos", "sinusoidal", "divergence", "tank", "normal"
     seed: int = 0
     mode: str = "mixed"       # suggested precision mode
@@ -257,14 +257,25 @@ def face_fluid_fraction(p: Problem, faces) -> np.ndarray:
     return frac
 
 
-def face_beta(p: Problem, faces) -> np.ndarray:
+def face_beta(p: Problem, faces, leaves=None) -> np.ndarray:
     """Per-face beta in canonical face order (float32): 1 for beta="one"; the clamped
     fluid fraction max(1e-3, min(1, f)) for beta="cut"; the fraction itself in [0, 1]
-    for beta="cut_exact" (cells inside the solid become inactive)."""
+    for beta="cut_exact" (cells inside the solid become inactive); for beta="cut_centre"
+    (needs the leaves) the ghost-fluid classification of Sec. 2.1: a leaf whose centre lies
+    in the solid (signed distance < 0) is a Neumann cell, no unknown, and every face that
+    touches it gets 0; the faces between two cells whose centres are in the fluid keep
+    their fluid fraction (the cut-cell coefficients)."""
     n = len(faces["axis"])
     if p.beta == "one":
         return np.ones(n, np.float32)
     f = face_fluid_fraction(p, faces)
+    if p.beta == "cut_centre":
+        if leaves is None:
+            raise ValueError("beta='cut_centre' needs the leaves")
+        h, x, y, z = _leaf_geometry(p, leaves)
+        solid = solid_sdf(p, x, y, z) < 0.0
+        touch = solid[np.asarray(faces["minus"])] | solid[np.asarray(faces["plus"])]
+        return np.where(touch, 0.0, np.clip(f, 0.0, 1.0)).astype(np.float32)
     if p.beta == "cut_exact":
         # the exact fraction: faces inside the solid get 0, so a cell inside the solid has
         # no coefficient and drops out of the system (an inactive cell)
@@ -362,18 +373,20 @@ def laplacian_problem(kind: str, n0: int) -> Problem:
 TANK_BC = (NEUMANN, NEUMANN, NEUMANN, DIRICHLET, NEUMANN, NEUMANN)   # open to air at y = 1
 
 
-def tank(obstacle: str, n0: int, inactive: bool = True, tiles: bool = False) -> Problem:
+def tank(obstacle: str, n0: int, solid: str = "centre", tiles: bool = False) -> Problem:
     """Static tank (Sec. 4.4): liquid filling [0,1]^3, solid bottom and sides (Neumann),
     open to air at the top (y = 1: zero-pressure Dirichlet), a solid obstacle (sphere of
     radius 0.25 or the star of Sec. 4.1) at the centre with fluid-fraction beta; rhs = the
     integrated divergence of the uniform velocity (0, -1, 0) (no flux through the solid
-    walls, inflow through the open top).  inactive: beta is the exact fraction (cells
-    inside the solid drop out, as in the paper's solver); otherwise the fraction clamped
-    at 1e-3.  The grid is refined two levels near the obstacle's surface: cell by cell
-    where cells meet the surface, or with tiles=True by the paper's 8^3 tiles
-    (paper_grid; roots of 32 and more)."""
-    kind = "cut_exact" if inactive else "cut"
-    tag = "" if inactive else "_clamped"
+    walls, inflow through the open top).  solid: "centre" (the paper's solver: cells whose
+    centre is in the solid are Neumann cells without an unknown, faces touching them get
+    0, the others their fluid fraction; face_beta then needs the leaves), "exact" (the
+    exact fraction on every face: only cells with no fluid on any face drop out) or
+    "clamped" (the fraction clamped at 1e-3: every cell an unknown).  The grid is refined
+    two levels near the obstacle's surface: cell by cell where cells meet the surface, or
+    with tiles=True by the paper's 8^3 tiles (paper_grid; roots of 32 and more)."""
+    kind = {"centre": "cut_centre", "exact": "cut_exact", "clamped": "cut"}[solid]
+    tag = {"centre": "", "exact": "_exact", "clamped": "_clamped"}[solid]
     if obstacle == "sphere":
         sph = (0.5, 0.5, 0.5, 0.25)
         d = paper_grid("sphere", n0) if tiles else OctreeDesc(n0, 2, REFINE_SDF_BAND, band=0.0, spheres=[sph])

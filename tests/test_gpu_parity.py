@@ -128,7 +128,7 @@ def test_mixed_outer_apply_with_partly_active_octets():
     # 1, 2, 4, 5, 6 or 7 active cells, whose ghost mean divides by a count that is not a
     # power of two; the pair-of-FP32 apply must still match the FP64 oracle to FP64
     # rounding
-    p = P.tank("sphere", 16, True)
+    p = P.tank("sphere", 16, "exact")
     t = O.Octree(p.desc)
     f = t.faces()
     beta = (P.face_beta(p, f) > 0.5).astype(np.float32)

@@ -1,13 +1,16 @@
 """Static tank (Sec. 4.4) through the library: with the solid's interior kept at beta =
 1e-3 the FP64 solve reproduces the exact discrete pressure p = y - 1 that the oracle's
-tests pin; with the interior inactive (exact fractions, the paper's solver) the solve
-matches the oracle's direct solve on the active cells and leaves the inactive ones at 0.
-At the paper's grid size (64^3 root, two levels near the obstacle: 64~256) the mixed
-W-cycle solve to 1e-6 with inactive solid cells converges (sphere: at most 6 iterations,
-fitted residual reduction above 10 per iteration; star: at most 12, above 3; the paper
-fits 7.16 and 5.17; measured 19.9 and 3.2), its pressure stays within 5e-3 of y - 1 on the
-active cells, and the divergence of the projected velocity, (b - A p) / V, is below 1e-5
-of the initial divergence (volume-weighted RMS over the active cells).
+tests pin; with the solid cells out of the system (the paper's classification of Sec. 2.1:
+a cell whose centre is in the solid is a Neumann cell without an unknown, the faces
+touching it carry no coefficient; or exact fractions on every face) the solve matches the
+oracle's direct solve on the active cells and leaves the inactive ones at 0.  At the
+paper's grid size (64^3 root, two levels near the obstacle: 64~256), on the cell-by-cell
+band grids and on the paper's tile grids up to the 128^3 root, the mixed W-cycle solve to
+1e-6 with the paper's classification converges with a fitted residual reduction above 5
+per iteration (the paper fits 7.16 for the sphere, 5.17 and 5.88 for the star), its
+pressure stays within 6e-3 of y - 1 on the active cells (the T ghosts beside partly active
+octets; the oracle's pins measure 0.5e-3 to 5e-3), and the divergence of the projected velocity, (b - A p) / V,
+is below 1e-5 of the initial divergence (volume-weighted RMS over the active cells).
 """
 import math
 
@@ -25,12 +28,12 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-def _setup(obstacle, n0, coef, mu=1, inactive=True, tiles=False):
-    p = P.tank(obstacle, n0, inactive, tiles)
+def _setup(obstacle, n0, coef, mu=1, solid="centre", tiles=False):
+    p = P.tank(obstacle, n0, solid, tiles)
     g = S.Octree(p.desc)
     f = g.faces()
-    beta = P.face_beta(p, f)
     lv = g.leaves()
+    beta = P.face_beta(p, f, lv)
     h = S.Hierarchy(g, beta, p.bc, S.mg_params(coef=coef, mu=mu))
     b = torch.from_numpy(P.rhs(p, lv, f, beta)).cuda()
     hc, xc, yc, zc = P.leaf_centres(n0, lv)
@@ -39,17 +42,18 @@ def _setup(obstacle, n0, coef, mu=1, inactive=True, tiles=False):
 
 @pytest.mark.parametrize("obstacle", ["sphere", "star"])
 def test_fp64_tank_solve_is_the_hydrostatic_field(obstacle):
-    p, h, b, hc, ref = _setup(obstacle, 32, "f64", inactive=False)
+    p, h, b, hc, ref = _setup(obstacle, 32, "f64", solid="clamped")
     x, st = h.solve(b, tol=1e-12, precision="fp64", max_iter=100)
     assert st.converged
     assert (x - ref).abs().max().item() <= 1e-9
 
 
+@pytest.mark.parametrize("solid", ["centre", "exact"])
 @pytest.mark.parametrize("obstacle", ["sphere", "star"])
-def test_inactive_solid_cells_match_the_oracle(obstacle):
-    p, h, b, hc, ref = _setup(obstacle, 16, "f32", mu=2)
+def test_inactive_solid_cells_match_the_oracle(obstacle, solid):
+    p, h, b, hc, ref = _setup(obstacle, 16, "f32", mu=2, solid=solid)
     t = O.Octree(p.desc)
-    H = OP.Hierarchy(t, P.face_beta(p, t.faces()), p.bc)
+    H = OP.Hierarchy(t, P.face_beta(p, t.faces(), t.leaves), p.bc)
     act = H.A.diagonal() != 0.0
     assert not np.all(act)
     bo = b.cpu().numpy()
@@ -61,7 +65,7 @@ def test_inactive_solid_cells_match_the_oracle(obstacle):
     assert np.abs(x[act] - xo).max() <= 1e-6 * np.abs(xo).max()
 
 
-@pytest.mark.parametrize("obstacle, max_its, min_fitted", [("sphere", 6, 10.0), ("star", 12, 3.0)])
+@pytest.mark.parametrize("obstacle, max_its, min_fitted", [("sphere", 6, 10.0), ("star", 9, 5.0)])
 def test_full_size_tank_w_cycle(obstacle, max_its, min_fitted):
     p, h, b, hc, ref = _setup(obstacle, 64, "f32", mu=2)
     x, st = h.solve(b, tol=1e-6, precision="mixed", max_iter=100)
@@ -75,20 +79,37 @@ def test_full_size_tank_w_cycle(obstacle, max_its, min_fitted):
     # cells have no coefficient, so their rhs and solution are 0 and A x is 0 there)
     act = (b != 0) | (x != 0)
     assert (x[~act] == 0).all()
-    assert (x - ref)[act].abs().max().item() <= 5e-3
+    assert (x - ref)[act].abs().max().item() <= 6e-3
     rms = lambda e, m: math.sqrt(float((V[m] * e[m] * e[m]).sum() / V[m].sum()))
     assert rms((b - Ax) / V, act) <= 1e-5 * rms(b / V, act)
 
 
-@pytest.mark.parametrize("obstacle, n0, max_its", [("star", 128, 24), ("sphere", 128, 18), ("star", 64, 20),
-                                                   ("sphere", 64, 14)])
-def test_tank_on_the_paper_tile_grids_converges(obstacle, n0, max_its):
+@pytest.mark.parametrize("obstacle, n0, max_its, min_fitted", [("star", 128, 10, 4.0), ("sphere", 128, 7, 10.0),
+                                                               ("star", 64, 9, 5.0), ("sphere", 64, 6, 10.0)])
+def test_tank_on_the_paper_tile_grids_converges(obstacle, n0, max_its, min_fitted):
     # Sec. 4.1's grids (8^3 tiles that meet the obstacle refined two levels; the sphere
-    # grids have Table 1's leaf counts), inactive solid cells, W-cycles: the 128^3-root
-    # star, which stagnates on the cell-by-cell band grid, converges here
+    # grids have Table 1's leaf counts), the paper's classification of the solid cells,
+    # W-cycles: fitted reductions of the paper's order (it reports 5.17 for star 64~256 and
+    # 7.16 / 5.88 at the 256^3 root; measured here 6.2 and 19.0 at the 64^3 root, 4.5 and
+    # 19.1 at the 128^3 root; with exact fractions on every face 2.0-3.5)
     p, h, b, hc, ref = _setup(obstacle, n0, "f32", mu=2, tiles=True)
     x, st = h.solve(b, tol=1e-6, precision="mixed", max_iter=100)
     assert st.converged and st.iterations <= max_its, st.iterations
+    k = st.iterations
+    slope = np.polyfit(np.arange(k + 1), np.log([st.hist[i] for i in range(k + 1)]), 1)[0]
+    assert math.exp(-slope) > min_fitted, math.exp(-slope)
     act = (b != 0) | (x != 0)
-    assert (x - ref)[act].abs().max().item() <= 5e-3
+    assert (x - ref)[act].abs().max().item() <= 6e-3
+
+
+def test_star_tank_on_the_band_grid_at_the_128_root_converges():
+    # the cell-by-cell band grid at the 128^3 root, whose T-junctions sit one cell from the
+    # star's surface: with exact fractions on every face the iteration stagnates near 1e-2
+    # (in the FP64 oracle too); with the paper's classification it converges
+    p, h, b, hc, ref = _setup("star", 128, "f32", mu=2)
+    x, st = h.solve(b, tol=1e-6, precision="mixed", max_iter=100)
+    assert st.converged and st.iterations <= 12, st.iterations
+    pe, he, be, hce, refe = _setup("star", 128, "f32", mu=2, solid="exact")
+    xe, se = he.solve(be, tol=1e-6, precision="mixed", max_iter=40, raise_on_notconv=False)
+    assert not se.converged
 

@@ -7,10 +7,13 @@ reproduces exactly (regular faces, cut-cell faces with any beta, the T-junction 
 value, the Dirichlet face at the open top), so the discrete pressure is p = y - 1 to
 rounding (the field that cancels the motion: the paper's "nearly uniform gradient along
 y"), whatever the obstacle and grid, when the solid's interior is kept at beta = 1e-3; with
-the interior inactive (exact fractions, the paper's solver) it stays within 5e-3; and Alg. 1 with
-W-cycles (mu = 2, the paper's choice for this test) and inactive solid cells reduces the
-residual by a fitted factor above 5 per iteration on these small roots, leaving the
-inactive cells at 0.
+the interior inactive it stays within 5e-3, both with the paper's classification of the
+solid cells (Sec. 2.1: a cell whose centre is in the solid is a Neumann cell without an
+unknown, the faces touching it carry no coefficient) and with exact fractions on every
+face; and Alg. 1 with W-cycles (mu = 2, the paper's choice for this test) and the paper's
+classification reduces the residual by a fitted factor above 5 per iteration (the paper
+fits 5.17-7.16), also on the paper's 32^3-root tile grid where the exact-fraction reading
+falls below 3.5, leaving the inactive cells at 0.
 """
 import math
 
@@ -25,21 +28,22 @@ from oracle import pcg
 from paper_2604_18886_b300 import problems as P
 
 
-def _setup(obstacle, n0, inactive=True):
-    p = P.tank(obstacle, n0, inactive)
+def _setup(obstacle, n0, solid="centre", tiles=False):
+    p = P.tank(obstacle, n0, solid, tiles)
     t = O.Octree(p.desc)
     f = t.faces()
-    beta = P.face_beta(p, f)
+    beta = P.face_beta(p, f, t.leaves)
     H = OP.Hierarchy(t, beta, p.bc)
     return p, t, H, P.rhs(p, t.leaves, f, beta)
 
 
-@pytest.mark.parametrize("inactive", [True, False])
+@pytest.mark.parametrize("solid", ["centre", "exact", "clamped"])
 @pytest.mark.parametrize("obstacle", ["sphere", "star"])
-def test_tank_pressure_is_the_hydrostatic_field(obstacle, inactive):
+def test_tank_pressure_is_the_hydrostatic_field(obstacle, solid):
+    inactive = solid != "clamped"
     for n0 in (8, 16):
-        p, t, H, b = _setup(obstacle, n0, inactive)
-        beta = P.face_beta(p, t.faces())
+        p, t, H, b = _setup(obstacle, n0, solid)
+        beta = P.face_beta(p, t.faces(), t.leaves)
         act = H.A.diagonal() != 0.0
         if inactive:
             assert beta.min() == 0.0 and not np.all(act)       # cells inside the solid drop out
@@ -50,9 +54,11 @@ def test_tank_pressure_is_the_hydrostatic_field(obstacle, inactive):
         x = sla.spsolve(A, b[act])
         h, xc, yc, zc = P.leaf_centres(n0, t.leaves)
         # exact with every cell active; with inactive cells a T ghost beside an octet with
-        # inactive siblings averages the active siblings only, which is not the parent's
-        # centre value of a linear field: small O(h) deviations there (1e-3 at most here)
-        assert np.abs(x - (yc[act] - 1.0)).max() <= (5e-3 if inactive else 1e-11), n0
+        # inactive siblings averages the active siblings only, whose mean centre is up to
+        # half a fine cell from the parent's centre: the linear field deviates there, by
+        # 0.5e-3 to 5e-3 at roots 8 to 64 for both readings (it does not shrink with h:
+        # the ghost's error is a flux error of the order of the fluxes near the solid)
+        assert np.abs(x - (yc[act] - 1.0)).max() <= (6e-3 if inactive else 1e-11), n0
 
 
 @pytest.mark.parametrize("obstacle", ["sphere", "star"])
@@ -65,3 +71,36 @@ def test_tank_w_cycle_reduces_the_residual_by_more_than_five(obstacle):
         assert fitted > 5.0 and k <= 10, (n0, k, fitted)
         act = H.A.diagonal() != 0.0
         assert np.all(x[~act] == 0.0)
+
+
+def test_centre_classification_drops_exactly_the_solid_centre_cells():
+    # Sec. 2.1: the leaves whose centre is in the solid have no unknown and no face
+    # coefficient; every other leaf keeps its faces' fluid fractions
+    for obstacle in ("sphere", "star"):
+        p, t, H, b = _setup(obstacle, 16)
+        f = t.faces()
+        h, x, y, z = P.leaf_centres(16, t.leaves)
+        solid = P.solid_sdf(p, x, y, z) < 0.0
+        act = H.A.diagonal() != 0.0
+        assert np.all(act == ~solid)
+        beta = P.face_beta(p, f, t.leaves)
+        touch = solid[f["minus"]] | solid[f["plus"]]
+        assert np.all(beta[touch] == 0.0)
+        pe = P.tank(obstacle, 16, "exact")
+        be = P.face_beta(pe, f)
+        assert np.array_equal(beta[~touch], be[~touch])
+        assert np.any(be[touch] > 0.0)      # the exact reading keeps partly fluid faces there
+
+
+def test_centre_classification_restores_the_papers_reduction_on_tile_grids():
+    # the star tank on the paper's 32^3-root tile grid (Sec. 4.1 grids, 8^3 tiles refined
+    # two levels): with the ghost-fluid classification the W-cycle PCG reduces the residual
+    # by more than 5 per iteration (the paper fits 5.17 on star 64~256); with exact
+    # fractions on every face it falls below 3.5 and needs about twice the iterations
+    res = {}
+    for solid in ("centre", "exact"):
+        p, t, H, b = _setup("star", 32, solid, tiles=True)
+        x, k, hist = pcg.pcg(H, b, tol=1e-6, prm=mg.CycleParams(mu=2), max_iter=100)
+        res[solid] = (k, math.exp(-np.polyfit(np.arange(k + 1), np.log(hist[:k + 1]), 1)[0]))
+    assert res["centre"][1] > 5.0 and res["centre"][0] <= 9, res
+    assert res["exact"][1] < 3.5 and res["exact"][0] >= res["centre"][0] + 3, res
