@@ -320,12 +320,13 @@ typedef struct {
  * make differ from A, and BiCGStab with M diverges at high coefficient contrast.
  * `iterations` counts iterations.  A hierarchy serves one solve at a time (its work
  * vectors are shared).
- * Known limit: inactive cells (zero face fractions) in an octet beside a T-junction give
- * the T ghost a mean over few active cells; where many such octets sit on the obstacle
- * (cell-by-cell refinement with the T-junctions one cell from a thin solid, e.g. the
- * star tank on a 128^3 root) the iteration can stagnate (ENOTCONV).  Refining by tiles
- * (ocg_octree_desc.tile_log2 = 3, the paper's grids) keeps the T-junctions off the
- * surface and those solves converge.
+ * Known limit: partly solid cells kept as unknowns (exact fractions on every face, so a
+ * cell with tiny fluid faces stays active) beside T-junctions give rows whose T ghost
+ * outweighs the diagonal; where many sit on a thin obstacle (e.g. the star tank on the
+ * 128^3-root cell-by-cell band grid) the iteration can stagnate (ENOTCONV).  Classifying
+ * the solid cells as the ghost-fluid method of Sec. 2.1 does (a cell whose centre is in
+ * the solid is no unknown: give every face touching it beta = 0) removes those rows, and
+ * the tank solves then converge at the paper's rates on band and tile grids.
  * Errors: ENOTCONV (stats filled), ENAN, EINVAL (also unknown flags), ECUDA. */
 int ocg_pcg_solve(ocg_hier* h, const double* b_dev, double* x_dev, const ocg_solve_params* prm,
                   ocg_solve_stats* stats, void* stream);
