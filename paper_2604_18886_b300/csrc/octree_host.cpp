@@ -610,19 +610,22 @@ static void build_impl(const ocg_octree_desc& desc, HostTree& T, const HostTree*
                      });
         }
     }
-    // canonical leaves: sorted by (depth, Morton key); level 0 is sorted explicitly, levels
-    // m >= 1 are stored in Morton order already
+    // canonical leaves: sorted by (depth, Morton key); level 0 by enumerating the Morton
+    // keys of the smallest power-of-two cube that holds the root grid in order (a parallel
+    // compaction, no sort), levels m >= 1 are stored in Morton order already
     T.leaf_first.assign(D + 2, 0);
+    int64_t side = 1;
+    while (side < n0) side <<= 1;
     std::vector<std::pair<uint64_t, int32_t>> lv0 =
-        par_compact<std::pair<uint64_t, int32_t>>(T.L(0).ncell, [&](int64_t lc, std::pair<uint64_t, int32_t>& out) {
-            const int64_t g = T.L(0).off + lc;
+        par_compact<std::pair<uint64_t, int32_t>>(side * side * side, [&](int64_t key, std::pair<uint64_t, int32_t>& out) {
+            uint64_t i, j, k;
+            demorton3((uint64_t)key, i, j, k);
+            if (i >= (uint64_t)n0 || j >= (uint64_t)n0 || k >= (uint64_t)n0) return false;
+            const int64_t g = T.cell_index(0, (int64_t)i, (int64_t)j, (int64_t)k);
             if (!(T.cell_flags[g] & 1)) return false;
-            int64_t i, j, k;
-            T.cell_coords(0, g, i, j, k);
-            out = {morton3(i, j, k), (int32_t)g};
+            out = {(uint64_t)key, (int32_t)g};
             return true;
         });
-    std::sort(lv0.begin(), lv0.end());
     // leaves per level m >= 1 (stored in Morton order already), then each level's leaves
     // written at their canonical ranks by a parallel scan
     T.leaf_first[1] = (int64_t)lv0.size();
