@@ -436,11 +436,29 @@ __global__ void __launch_bounds__(BLK) k_update(TO* __restrict__ x, TO* __restri
 // r - alpha (A p - mean(A p)) on the leaves is the shifted residual, the mean of A p
 // coming from the apply's reduction (S_APMEAN).  b32 is the forward cycle's b (cycle
 // layout).
+//
+// The first step of the next preconditioner application can be fused in (F.u32 set): the
+// cycle starts from u = 0, so its first step, the colour-0 sweep of the finest level, sets
+// u = b / c on that level's active colour-0 cells (every neighbour and T ghost is 0) and
+// leaves the other cells at 0.  This kernel then writes that u over the tree cells (cycle
+// layout) beside b32, in the sweep's arithmetic (b rounded to FP32, then the same FP32
+// division), and the cycle skips both the zeroing of u and that sweep.  [d0, d1) are the
+// finest level's cells, d its FP32 diagonal in cell order.
+struct FirstSweep {
+    float* u32;
+    const float* d;
+    int d0, d1;
+};
+__device__ __forceinline__ float first_sweep_u(const FirstSweep& F, int i, float b) {
+    if (i < F.d0 || i >= F.d1 || cyc_colour(i & 7) != 0) return 0.0f;
+    const float c = F.d[i];
+    return c != 0.0f ? __fdividef(b, c) : 0.0f;
+}
 template <bool NS>
 __global__ void __launch_bounds__(BLK) k_update_pp(double* __restrict__ x, double* __restrict__ r,
                                                    const float* __restrict__ phi, const float* __restrict__ plo,
                                                    const double* __restrict__ Ap, const uint8_t* __restrict__ flags,
-                                                   float* __restrict__ b32, int n, Red R) {
+                                                   float* __restrict__ b32, int n, Red R, FirstSweep F) {
     pdl_enter();
     __shared__ double sh[32];
     const double alpha = R.S[S_ALPHA];
@@ -464,7 +482,9 @@ __global__ void __launch_bounds__(BLK) k_update_pp(double* __restrict__ x, doubl
             double rn = rv[q] - alpha * av[q];
             if (NS && (fv[q] & 1)) rn = rn + shift;
             r[i + q * st] = rn;
-            b32[cyc(i + q * st)] = d2f_bits(rn);
+            const float bf = d2f_bits(rn);
+            b32[cyc(i + q * st)] = bf;
+            if (F.u32) F.u32[cyc(i + q * st)] = first_sweep_u(F, i + q * st, bf);
             rr += rn * rn;
         }
     }
@@ -473,7 +493,9 @@ __global__ void __launch_bounds__(BLK) k_update_pp(double* __restrict__ x, doubl
         double rn = r[i] - alpha * Ap[i];
         if (NS && (flags[i] & 1)) rn = rn + shift;
         r[i] = rn;
-        b32[cyc(i)] = d2f_bits(rn);
+        const float bf = d2f_bits(rn);
+        b32[cyc(i)] = bf;
+        if (F.u32) F.u32[cyc(i)] = first_sweep_u(F, i, bf);
         rr += rn * rn;
     }
     red_finish(R, blockIdx.x, rr, 0.0, sh);

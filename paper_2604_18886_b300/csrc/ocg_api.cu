@@ -479,6 +479,8 @@ struct Cycle {
     TV* U;
     TV* B;
     Ctx& c;
+    bool skip_first = false;   // the first colour-0 sweep of the finest level was fused into
+                               // the Krylov update (FirstSweep), which also zeroed u
 
     const HostTree& H() const { return h->t->H; }
 
@@ -503,6 +505,10 @@ struct Cycle {
         ck_launch("fixb");
     }
     void sweep(int m, int colour, int prolong, int form = -2) {
+        if (skip_first && m == H().D && colour == 0) {
+            skip_first = false;
+            return;
+        }
         if (form == -2) form = h->sweep_form[m - H().mc];
         with_coefs(m, [&](auto C) {
             using TC = typename CoefTypes<decltype(C)>::TC;
@@ -605,6 +611,14 @@ struct Cycle {
     }
     void run() { cycle(H().D, false, false); }
 };
+
+// The Krylov update can take over the first step of the next cycle (FirstSweep) when that
+// step is a colour-0 sweep of the finest level: an FP32 cycle whose finest level is swept
+// by launches (not the coarsest level, not inside the shared-memory tail), nu_pre >= 1.
+inline bool first_sweep_fusable(const ocg_hier* h) {
+    const HostTree& H = h->t->H;
+    return h->c32[0] && h->prm.nu_pre >= 1 && H.D != H.mc && H.D != h->tail_top[0];
+}
 
 OMultiLevel tree_levels(const HostTree& H);
 
@@ -1009,14 +1023,24 @@ struct PcgImpl {
     }
     // z = M r (forward: r in B, z in U) or z = M^T r (transpose: r in B, z in B)
     TV* Z() { return TR ? B() : U(); }
+    // the Krylov update forms the next cycle's first sweep (FirstSweep); first_done: the
+    // preceding half iteration did (a loop body always follows one)
+    bool fuse_first() const {
+        if constexpr (PP) return first_sweep_fusable(h);
+        else return false;
+    }
+    bool first_done = false;
     void precondition() {
         if constexpr (TR) {
             CycleT<TV> ct{h, U(), B(), (TV*)h->Xc, (TV*)h->UST, (TV*)h->Tacc, c};
             ct.seed((const TV*)B());
             ct.run();
         } else {
-            zero(h->U, cyc_len(H().ntree) * sizeof(TV));   // the tree cells' positions and a few coarse cells
-            Cycle<TV>{h, U(), B(), c}.run();
+            Cycle<TV> cy{h, U(), B(), c};
+            if (first_done) cy.skip_first = true;
+            else zero(h->U, cyc_len(H().ntree) * sizeof(TV));   // the tree cells' positions and a few coarse cells
+            first_done = false;
+            cy.run();
         }
     }
     void half_a() {
@@ -1026,14 +1050,19 @@ struct PcgImpl {
         launch(c, -1, 0, n(), [&] {
             const Red R = make_red(h, rb(), OP_RR, cond, set_cond);
             if constexpr (PP) {
+                FirstSweep F{nullptr, nullptr, 0, 0};
+                if (fuse_first()) {
+                    const LevelArgs AD = h->t->largs(H().D);
+                    F = FirstSweep{(float*)U(), h->c32[0], AD.off, AD.off + AD.ncell};
+                }
                 if (ns)
                     launch_k(k_update_pp<true>, rb(), BLK, 0, c.st, h->x, h->r, (const float*)hi(h->p),
                              (const float*)lo(h->p), (const double*)h->Ap, (const uint8_t*)h->t->flags,
-                             (float*)B(), n(), R);
+                             (float*)B(), n(), R, F);
                 else
                     launch_k(k_update_pp<false>, rb(), BLK, 0, c.st, h->x, h->r, (const float*)hi(h->p),
                              (const float*)lo(h->p), (const double*)h->Ap, (const uint8_t*)nullptr,
-                             (float*)B(), n(), R);
+                             (float*)B(), n(), R, F);
             } else {
                 if (ns) launch_k(k_update<TO, TV, true, CY>, rb(), BLK, 0, c.st, x(), r(), p(), Ap(), nullptr, n(), R);
                 else launch_k(k_update<TO, TV, false, CY>, rb(), BLK, 0, c.st, x(), r(), p(), Ap(), B(), n(), R);
@@ -1051,6 +1080,7 @@ struct PcgImpl {
         ck_launch("half_b");
     }
     void body() {
+        first_done = fuse_first();
         half_b();
         half_a();
     }

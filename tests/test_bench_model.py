@@ -14,7 +14,10 @@ def test_cycle_visits_follow_the_recursion():
 def test_model_bytes_per_solve():
     sizes = [1000, 125]
     n_tree = 1125
-    v = bench.model_bytes(sizes, n_tree, 3, "mixed")
+    v = bench.model_bytes(sizes, n_tree, 3, "mixed", fused_first=False)
     assert v == 3 * (bench.LEVEL_VISIT_BYTES * (1000 + 125) + bench.OUTER_BYTES["mixed"] * n_tree)
+    # the mixed solve's cycles after the first take their first sweep from the update
+    vf = bench.model_bytes(sizes, n_tree, 3, "mixed")
+    assert vf == v - 2 * bench.FIRST_SWEEP_SAVED_BYTES * 1000
     w = bench.model_bytes(sizes, n_tree, 3, "fp32", mu=2)
     assert w == 3 * (bench.LEVEL_VISIT_BYTES * (1000 + 2 * 125) + bench.OUTER_BYTES["fp32"] * n_tree)
