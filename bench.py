@@ -57,9 +57,10 @@ APPLY_BYTES_PER_CELL = 32.0
 # + norm + cast, (r, z) + p update)
 LEVEL_VISIT_BYTES = 230.0
 OUTER_BYTES = {"mixed": 116.0, "fp32": 72.0}
-# the mixed solve forms the first colour sweep of each cycle after the first (from u = 0 on
-# the finest level: u = b / c on the colour's cells) in the Krylov update, which reads the
-# diagonal and writes u (8 B per cell of the finest level) instead of a 24 B sweep
+# the mixed solve forms the first colour sweep of each cycle (from u = 0 on the finest
+# level: u = b / c on the colour's cells) in the Krylov update or the initial projection,
+# which read the diagonal and write u (8 B per cell of the finest level) instead of a 24 B
+# sweep
 FIRST_SWEEP_SAVED_BYTES = SWEEP_BYTES_PER_CELL - 8.0
 NOMINAL_HBM_GBS = 7700.0   # B300 HBM3e nominal bandwidth, for a second fraction beside the measured one
 HYBRID_MIN_CELLS = 1 << 20
@@ -211,12 +212,12 @@ def cycle_visits(sizes, mu, mu_min_cells=0):
 def model_bytes(sizes, n_tree, iterations, precision="mixed", mu=1, mu_min_cells=0, fused_first=None):
     """Byte model of one solve: per PCG iteration one cycle (LEVEL_VISIT_BYTES per cell per
     visit of each level) plus the outer Krylov traffic per tree cell; with fused_first
-    (default: the mixed solve) the cycles after the first save FIRST_SWEEP_SAVED_BYTES per
-    cell of the finest level."""
+    (default: the mixed solve) every cycle saves FIRST_SWEEP_SAVED_BYTES per cell of the
+    finest level."""
     if fused_first is None:
         fused_first = precision == "mixed"
     cyc = sum(LEVEL_VISIT_BYTES * n * v for n, v in zip(sizes, cycle_visits(sizes, mu, mu_min_cells)))
-    saved = FIRST_SWEEP_SAVED_BYTES * sizes[0] * max(iterations - 1, 0) if fused_first else 0.0
+    saved = FIRST_SWEEP_SAVED_BYTES * sizes[0] * iterations if fused_first else 0.0
     return iterations * (cyc + OUTER_BYTES[precision] * n_tree) - saved
 
 

@@ -523,16 +523,25 @@ __global__ void k_pupdate_pp(float* __restrict__ hi, float* __restrict__ lo, con
 }
 
 // r -= mean on leaves (null-space shift of Sec. 2.2) and b32 = r (cycle layout when CY).
+// With F.u32 set (an FP32 cycle), the first sweep of the next cycle as in k_update_pp.
+__device__ __forceinline__ void first_sweep_store(const FirstSweep& F, int i, float b) {
+    if (F.u32) F.u32[cyc(i)] = first_sweep_u(F, i, b);
+}
+__device__ __forceinline__ void first_sweep_store(const FirstSweep&, int, double) {}
 template <class TO, class TB, bool CY = false>
 __global__ void k_project(TO* __restrict__ r, const uint8_t* __restrict__ flags, const double* __restrict__ S,
-                          TB* __restrict__ b32, int n) {
+                          TB* __restrict__ b32, int n, FirstSweep F) {
     pdl_enter();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     TO v = r[i];
     if (flags[i] & 1) v = v - TO(S[S_MEAN]);
     r[i] = v;
-    if (b32) b32[vidx<CY>(i)] = cvt<TB>(v);
+    if (b32) {
+        const TB bv = cvt<TB>(v);
+        b32[vidx<CY>(i)] = bv;
+        first_sweep_store(F, i, bv);
+    }
 }
 
 // (a, b) and sum(a) over the first n cells, reduced into R

@@ -1013,8 +1013,11 @@ struct PcgImpl {
             else apply_outer<TO, TC, TW>(h, Co, x(), Ap(), OP_NONE, c);
             launch(c, -1, 0, n(), [&] { launch_k(k_sub<TO>, gb(), BLK, 0, c.st, r(), (const TO*)Ap(), n()); });
         }
-        launch(c, -1, 0, n(), [&] { launch_k(k_project<TO, TV, CY>, gb(), BLK, 0, c.st, r(), h->t->flags, h->S, B(), n()); });
+        // (the mixed solve forms the first cycle's first sweep here, as in the Krylov update)
+        const FirstSweep F = first_sweep_args();
+        launch(c, -1, 0, n(), [&] { launch_k(k_project<TO, TV, CY>, gb(), BLK, 0, c.st, r(), h->t->flags, h->S, B(), n(), F); });
         ck_launch("begin");
+        first_done = F.u32 != nullptr;
         precondition();
         launch(c, -1, 0, n(), [&] { launch_k(k_dot<TO, TV, false, CY>, rb(), BLK, 0, c.st, r(), Z(), n(), make_red(h, rb(), OP_RZ0)); });
         pupdate(1);
@@ -1030,6 +1033,11 @@ struct PcgImpl {
         else return false;
     }
     bool first_done = false;
+    FirstSweep first_sweep_args() const {
+        if (!fuse_first()) return FirstSweep{nullptr, nullptr, 0, 0};
+        const LevelArgs AD = h->t->largs(H().D);
+        return FirstSweep{(float*)h->U, h->c32[0], AD.off, AD.off + AD.ncell};
+    }
     void precondition() {
         if constexpr (TR) {
             CycleT<TV> ct{h, U(), B(), (TV*)h->Xc, (TV*)h->UST, (TV*)h->Tacc, c};
@@ -1050,11 +1058,7 @@ struct PcgImpl {
         launch(c, -1, 0, n(), [&] {
             const Red R = make_red(h, rb(), OP_RR, cond, set_cond);
             if constexpr (PP) {
-                FirstSweep F{nullptr, nullptr, 0, 0};
-                if (fuse_first()) {
-                    const LevelArgs AD = h->t->largs(H().D);
-                    F = FirstSweep{(float*)U(), h->c32[0], AD.off, AD.off + AD.ncell};
-                }
+                const FirstSweep F = first_sweep_args();
                 if (ns)
                     launch_k(k_update_pp<true>, rb(), BLK, 0, c.st, h->x, h->r, (const float*)hi(h->p),
                              (const float*)lo(h->p), (const double*)h->Ap, (const uint8_t*)h->t->flags,
@@ -1070,7 +1074,9 @@ struct PcgImpl {
         });
         // the zero-mean shift of r (fused into the update of the pair-stored mixed form)
         if (ns && !PP)
-            launch(c, -1, 0, n(), [&] { launch_k(k_project<TO, TV, CY>, gb(), BLK, 0, c.st, r(), h->t->flags, h->S, B(), n()); });
+            launch(c, -1, 0, n(), [&] {
+                launch_k(k_project<TO, TV, CY>, gb(), BLK, 0, c.st, r(), h->t->flags, h->S, B(), n(), FirstSweep{});
+            });
         ck_launch("half_a");
     }
     void half_b() {
@@ -1147,7 +1153,7 @@ struct BiCG {
         zero(h->Ap, n() * sizeof(TO));
         if (ns)
             launch(c, -1, 0, n(), [&] {
-                launch_k(k_project<TO, TV>, gb(), BLK, 0, c.st, r, h->t->flags, h->S, (TV*)nullptr, n());
+                launch_k(k_project<TO, TV>, gb(), BLK, 0, c.st, r, h->t->flags, h->S, (TV*)nullptr, n(), FirstSweep{});
             });
         launch(c, -1, 0, n(), [&] { launch_k(k_cast<TO, TO>, gb(), BLK, 0, c.st, r, V(h->rhat), n()); });
         launch(c, -1, 0, n(), [&] {
@@ -1180,7 +1186,7 @@ struct BiCG {
         });
         if (ns)
             launch(c, -1, 0, n(), [&] {
-                launch_k(k_project<TO, TV>, gb(), BLK, 0, c.st, r, h->t->flags, h->S, (TV*)nullptr, n());
+                launch_k(k_project<TO, TV>, gb(), BLK, 0, c.st, r, h->t->flags, h->S, (TV*)nullptr, n(), FirstSweep{});
             });
         ck_launch("bicg body");
     }
