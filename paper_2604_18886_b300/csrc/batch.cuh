@@ -32,6 +32,8 @@ struct BProb {
     int vb0, nbv;         // vector kernels: first block, blocks
     int ab0, nba;         // composite operator: first block, blocks
     int D, mc;
+    int fuse_first;       // the vector kernels that write B form the cycle's first sweep (finest
+                          // level swept by launches, not inside the tail): FirstSweep
     BLev L[2 * MAXLEV];   // index m - mc
     TailArgs tail;        // float cycle
 };
@@ -114,11 +116,13 @@ __device__ __forceinline__ LevelArgs blevel(const BProb& P, int m) {
 // ------------------------------------------------------------------ cycle phases
 // colour sweep / FAS right-hand-side pass of one level of every listed problem, one
 // thread per octet
+// skip_first: the first colour-0 sweep of a cycle, which the vector kernels already formed
+// on the finest level of the problems with fuse_first
 __global__ void __launch_bounds__(OBLK) kb_osweep(const BProb* __restrict__ PP, const BWork* __restrict__ W,
-                                                  const int* __restrict__ bmap, int colour, int fixb) {
+                                                  const int* __restrict__ bmap, int colour, int fixb, int skip_first) {
     const BWork w = W[bmap[blockIdx.x]];
     const BProb& P = PP[w.prob];
-    if (bdone(P)) return;
+    if (bdone(P) || (skip_first && P.fuse_first && w.m == P.D)) return;
     const LevelArgs A = blevel(P, w.m);
     const int o = ((int)blockIdx.x - w.b0) * OBLK + threadIdx.x;
     if (o >= A.ncell / 8) return;
@@ -131,10 +135,10 @@ __global__ void __launch_bounds__(OBLK) kb_osweep(const BProb* __restrict__ PP, 
 
 // the same colour sweep, one thread per cell
 __global__ void __launch_bounds__(BLK) kb_csweep(const BProb* __restrict__ PP, const BWork* __restrict__ W,
-                                                 const int* __restrict__ bmap, int colour) {
+                                                 const int* __restrict__ bmap, int colour, int skip_first) {
     const BWork w = W[bmap[blockIdx.x]];
     const BProb& P = PP[w.prob];
-    if (bdone(P)) return;
+    if (bdone(P) || (skip_first && P.fuse_first && w.m == P.D)) return;
     const LevelArgs A = blevel(P, w.m);
     csweep_cell<float, float, float>(A, P.T, P.C, P.U, P.B, ((int)blockIdx.x - w.b0) * BLK + threadIdx.x, colour,
                                      w.flags & 1);
@@ -173,11 +177,22 @@ __global__ void __launch_bounds__(512) kb_otail(const BProb* __restrict__ PP, co
     const int blk = (int)blockIdx.x - P.vb0, nb = P.nbv;           \
     const int i0 = blk * BLK + threadIdx.x, di = nb * BLK;
 
-// U = 0 on the tree cells (the cycle's initial guess)
+// U = 0 on the tree cells (the cycle's initial guess) of the problems whose vector kernels
+// do not form the first sweep
 __global__ void __launch_bounds__(BLK) kb_zero_u(const BProb* __restrict__ PP, const int* __restrict__ bmap) {
     BVEC_PROLOGUE
-    if (bdone(P)) return;
+    if (bdone(P) || P.fuse_first) return;
     for (int i = i0; i < P.ntree; i += di) P.U[cyc(i)] = 0.0f;
+}
+
+// B = b on tree cell i and, with fuse_first, the cycle's first sweep in U (FirstSweep)
+__device__ __forceinline__ void bput(const BProb& P, int i, float b) {
+    P.B[cyc(i)] = b;
+    if (P.fuse_first) {
+        const BLev& l = P.L[P.D - P.mc];
+        const FirstSweep F{P.U, P.C.d, l.off, l.off + l.ncell};
+        P.U[cyc(i)] = first_sweep_u(F, i, b);
+    }
 }
 
 // Per-call input / output of each problem (canonical leaf order).
@@ -215,7 +230,7 @@ __global__ void __launch_bounds__(BLK) kb_rinit(const BProb* __restrict__ PP, co
         double v = P.bt[i];
         if (P.flags[i] & 1) v -= mean;
         P.r[i] = v;
-        P.B[cyc(i)] = (float)v;
+        bput(P, i, (float)v);
     }
 }
 
@@ -252,7 +267,7 @@ __global__ void __launch_bounds__(BLK) kb_update(const BProb* __restrict__ PP, c
             P.x[i] = P.x[i] + alpha * P.p[i];
             const double rn = P.r[i] - alpha * P.Ap[i];
             P.r[i] = rn;
-            if (!ns) P.B[cyc(i)] = (float)rn;
+            if (!ns) bput(P, i, (float)rn);
             rr += rn * rn;
             rs += ns ? rn : 0.0;
         }
@@ -269,7 +284,7 @@ __global__ void __launch_bounds__(BLK) kb_project(const BProb* __restrict__ PP, 
         double v = P.r[i];
         if (P.flags[i] & 1) v -= mean;
         P.r[i] = v;
-        P.B[cyc(i)] = (float)v;
+        bput(P, i, (float)v);
     }
 }
 

@@ -94,12 +94,12 @@ struct BatchRun {
         launch(c, -1, 0, cells, f);
         ck_launch("batched launch");
     }
-    void sweep(int h, int colour, bool last_post, int form) {
+    void sweep(int h, int colour, bool last_post, int form, int skip_first = 0) {
         const ocg_batch::Phase& ph = last_post ? bt->up[h] : bt->down[h];
         if (form == OCG_SWEEP_CELL)
-            go(0, [&] { kb_csweep<<<ph.cell.nb, BLK, 0, c.st>>>(bt->dP, bt->dW, I(ph.cell), colour); });
+            go(0, [&] { kb_csweep<<<ph.cell.nb, BLK, 0, c.st>>>(bt->dP, bt->dW, I(ph.cell), colour, skip_first); });
         else
-            go(0, [&] { kb_osweep<<<ph.oct.nb, OBLK, 0, c.st>>>(bt->dP, bt->dW, I(ph.oct), colour, 0); });
+            go(0, [&] { kb_osweep<<<ph.oct.nb, OBLK, 0, c.st>>>(bt->dP, bt->dW, I(ph.oct), colour, 0, skip_first); });
     }
     // Alg. 4 at height g for every problem with a level there; fas: first visit after a
     // restriction from above, prolong_up: the last visit, whose final operation prolongs
@@ -116,9 +116,11 @@ struct BatchRun {
         if (g < 1 || bt->down[g].oct.nw == 0) return;
         const ocg_batch::Phase& f = bt->fixb[g];
         if (fas && f.oct.nw > 0)
-            go(0, [&] { kb_osweep<<<f.oct.nb, OBLK, 0, c.st>>>(bt->dP, bt->dW, I(f.oct), 0, 1); });
+            go(0, [&] { kb_osweep<<<f.oct.nb, OBLK, 0, c.st>>>(bt->dP, bt->dW, I(f.oct), 0, 1, 0); });
         for (int it = 0; it < P.nu_pre; ++it) {
-            sweep(g, 0, false, bt->form[g]);
+            // a problem's finest level is visited once per cycle, and its first sweep there
+            // was formed by the vector kernels (fuse_first)
+            sweep(g, 0, false, bt->form[g], it == 0 ? 1 : 0);
             sweep(g, 1, false, bt->form[g]);
         }
         const ocg_batch::Map& d = bt->down[g].oct;
@@ -307,6 +309,7 @@ int ocg_batch_create(ocg_hier* const* hs, int32_t n, void* stream, ocg_batch** o
             b.nleaf = (int)Ht.nleaf;
             b.D = Ht.D;
             b.mc = Ht.mc;
+            b.fuse_first = first_sweep_fusable(h) ? 1 : 0;
             for (int m2 = Ht.mc; m2 <= Ht.D; ++m2)
                 b.L[m2 - Ht.mc] = BLev{(int)Ht.L(m2).off, (int)Ht.L(m2).ncell, Ht.L(m2).ni};
             b.tail = h->tail_args[0];

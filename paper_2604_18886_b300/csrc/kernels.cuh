@@ -389,12 +389,35 @@ __global__ void k_gather(const TI* __restrict__ in, TO* __restrict__ out, const 
     if (r < n) out[r] = TO(in[vidx<CY>(leaf_cell[r])]);
 }
 
+// The first step of the next preconditioner application, fused into the kernel that writes
+// the cycle's right-hand side b32 (F.u32 set, FP32 cycles): the cycle starts from u = 0, so
+// its first step, the colour-0 sweep of the finest level, sets u = b / c on that level's
+// active colour-0 cells (every neighbour and T ghost is 0) and leaves the other cells at 0.
+// The kernel then writes that u over the tree cells (cycle layout) beside b32, in the
+// sweep's arithmetic (b rounded to FP32, then the same FP32 division), and the cycle skips
+// both the zeroing of u and that sweep.  [d0, d1) are the finest level's cells, d its FP32
+// diagonal in cell order.
+struct FirstSweep {
+    float* u32;
+    const float* d;
+    int d0, d1;
+};
+__device__ __forceinline__ float first_sweep_u(const FirstSweep& F, int i, float b) {
+    if (i < F.d0 || i >= F.d1 || cyc_colour(i & 7) != 0) return 0.0f;
+    const float c = F.d[i];
+    return c != 0.0f ? __fdividef(b, c) : 0.0f;
+}
+__device__ __forceinline__ void first_sweep_store(const FirstSweep& F, int i, float b) {
+    if (F.u32) F.u32[cyc(i)] = first_sweep_u(F, i, b);
+}
+__device__ __forceinline__ void first_sweep_store(const FirstSweep&, int, double) {}
 // x += alpha p, r -= alpha Ap over the tree cells (inner cells keep r = 0 since Ap = 0
 // there); reduces r.r and sum(r) (OP_RR: convergence test of Alg. 1); optionally b32 = r
 // (b32 in the cycle layout when CY).
 template <class TO, class TB, bool SUM, bool CY = false>
 __global__ void __launch_bounds__(BLK) k_update(TO* __restrict__ x, TO* __restrict__ r, const TO* __restrict__ p,
-                                                const TO* __restrict__ Ap, TB* __restrict__ b32, int n, Red R) {
+                                                const TO* __restrict__ Ap, TB* __restrict__ b32, int n, Red R,
+                                                FirstSweep F) {
     pdl_enter();
     __shared__ double sh[32];
     const TO alpha = TO(R.S[S_ALPHA]);
@@ -411,7 +434,11 @@ __global__ void __launch_bounds__(BLK) k_update(TO* __restrict__ x, TO* __restri
             x[i + q * st] = xv[q] + alpha * pv[q];
             const TO rn = rv[q] - alpha * av[q];
             r[i + q * st] = rn;
-            if (b32) b32[vidx<CY>(i + q * st)] = cvt<TB>(rn);
+            if (b32) {
+                const TB bv = cvt<TB>(rn);
+                b32[vidx<CY>(i + q * st)] = bv;
+                first_sweep_store(F, i + q * st, bv);
+            }
             const double rd = (double)rn;
             rr += rd * rd;
             if (SUM) rs += rd;
@@ -421,7 +448,11 @@ __global__ void __launch_bounds__(BLK) k_update(TO* __restrict__ x, TO* __restri
         x[i] = x[i] + alpha * p[i];
         const TO rn = r[i] - alpha * Ap[i];
         r[i] = rn;
-        if (b32) b32[vidx<CY>(i)] = cvt<TB>(rn);
+        if (b32) {
+            const TB bv = cvt<TB>(rn);
+            b32[vidx<CY>(i)] = bv;
+            first_sweep_store(F, i, bv);
+        }
         const double rd = (double)rn;
         rr += rd * rd;
         if (SUM) rs += rd;
@@ -436,24 +467,6 @@ __global__ void __launch_bounds__(BLK) k_update(TO* __restrict__ x, TO* __restri
 // r - alpha (A p - mean(A p)) on the leaves is the shifted residual, the mean of A p
 // coming from the apply's reduction (S_APMEAN).  b32 is the forward cycle's b (cycle
 // layout).
-//
-// The first step of the next preconditioner application can be fused in (F.u32 set): the
-// cycle starts from u = 0, so its first step, the colour-0 sweep of the finest level, sets
-// u = b / c on that level's active colour-0 cells (every neighbour and T ghost is 0) and
-// leaves the other cells at 0.  This kernel then writes that u over the tree cells (cycle
-// layout) beside b32, in the sweep's arithmetic (b rounded to FP32, then the same FP32
-// division), and the cycle skips both the zeroing of u and that sweep.  [d0, d1) are the
-// finest level's cells, d its FP32 diagonal in cell order.
-struct FirstSweep {
-    float* u32;
-    const float* d;
-    int d0, d1;
-};
-__device__ __forceinline__ float first_sweep_u(const FirstSweep& F, int i, float b) {
-    if (i < F.d0 || i >= F.d1 || cyc_colour(i & 7) != 0) return 0.0f;
-    const float c = F.d[i];
-    return c != 0.0f ? __fdividef(b, c) : 0.0f;
-}
 template <bool NS>
 __global__ void __launch_bounds__(BLK) k_update_pp(double* __restrict__ x, double* __restrict__ r,
                                                    const float* __restrict__ phi, const float* __restrict__ plo,
@@ -523,11 +536,6 @@ __global__ void k_pupdate_pp(float* __restrict__ hi, float* __restrict__ lo, con
 }
 
 // r -= mean on leaves (null-space shift of Sec. 2.2) and b32 = r (cycle layout when CY).
-// With F.u32 set (an FP32 cycle), the first sweep of the next cycle as in k_update_pp.
-__device__ __forceinline__ void first_sweep_store(const FirstSweep& F, int i, float b) {
-    if (F.u32) F.u32[cyc(i)] = first_sweep_u(F, i, b);
-}
-__device__ __forceinline__ void first_sweep_store(const FirstSweep&, int, double) {}
 template <class TO, class TB, bool CY = false>
 __global__ void k_project(TO* __restrict__ r, const uint8_t* __restrict__ flags, const double* __restrict__ S,
                           TB* __restrict__ b32, int n, FirstSweep F) {

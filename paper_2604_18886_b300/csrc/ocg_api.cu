@@ -1029,7 +1029,7 @@ struct PcgImpl {
     // the Krylov update forms the next cycle's first sweep (FirstSweep); first_done: the
     // preceding half iteration did (a loop body always follows one)
     bool fuse_first() const {
-        if constexpr (PP) return first_sweep_fusable(h);
+        if constexpr (!TR && std::is_same<TV, float>::value) return first_sweep_fusable(h);
         else return false;
     }
     bool first_done = false;
@@ -1068,14 +1068,17 @@ struct PcgImpl {
                              (const float*)lo(h->p), (const double*)h->Ap, (const uint8_t*)nullptr,
                              (float*)B(), n(), R, F);
             } else {
-                if (ns) launch_k(k_update<TO, TV, true, CY>, rb(), BLK, 0, c.st, x(), r(), p(), Ap(), nullptr, n(), R);
-                else launch_k(k_update<TO, TV, false, CY>, rb(), BLK, 0, c.st, x(), r(), p(), Ap(), B(), n(), R);
+                // under the null space k_project below writes b (and the first sweep)
+                if (ns) launch_k(k_update<TO, TV, true, CY>, rb(), BLK, 0, c.st, x(), r(), p(), Ap(), nullptr, n(), R,
+                                 FirstSweep{});
+                else launch_k(k_update<TO, TV, false, CY>, rb(), BLK, 0, c.st, x(), r(), p(), Ap(), B(), n(), R,
+                              first_sweep_args());
             }
         });
         // the zero-mean shift of r (fused into the update of the pair-stored mixed form)
         if (ns && !PP)
             launch(c, -1, 0, n(), [&] {
-                launch_k(k_project<TO, TV, CY>, gb(), BLK, 0, c.st, r(), h->t->flags, h->S, B(), n(), FirstSweep{});
+                launch_k(k_project<TO, TV, CY>, gb(), BLK, 0, c.st, r(), h->t->flags, h->S, B(), n(), first_sweep_args());
             });
         ck_launch("half_a");
     }
