@@ -207,9 +207,10 @@ def test_autograd_matches_oracle_gradients(name):
     # dL/dbeta comes back in beta's dtype (float32): one rounding to 24 bits on top
     bound = grad_bound(coef, dlam, dp, e_p, e_l)
     bound = bound + 2.0 ** -24 * (np.abs(gbeta_o) + bound)
-    worst = np.argsort(err / np.maximum(np.abs(gbeta_o), 1e-300))[-5:]
+    gmag = np.maximum(np.abs(gbeta_o), 1e-300)  # faces with no gradient at all divide by a tiny floor
+    worst = np.argsort(err / gmag)[-5:]
     print("faces %d, e_p %.2e, e_lambda %.2e; largest per-face relative errors:" % (len(got), e_p, e_l),
-          ["%.2e (bound %.2e, |g| %.2e)" % (err[q] / abs(gbeta_o[q]), bound[q] / abs(gbeta_o[q]), abs(gbeta_o[q]))
+          ["%.2e (bound %.2e, |g| %.2e)" % (err[q] / gmag[q], bound[q] / gmag[q], abs(gbeta_o[q]))
            for q in worst])
     assert np.all(err <= bound), (err - bound).max()
     # the bound is tight enough to mean something: 1e-4 of the face's gradient or better on
