@@ -670,8 +670,8 @@ def _tank(dev, stream, flush, args):
     cut-cell sphere or star obstacle; the 64^3 root with two levels near the obstacle is
     the paper's 64~256 grid.  Mixed solves to 1e-6 with W-cycles (the paper's choice here)
     and V-cycles: iterations, mean residual reduction per iteration, time, the largest
-    deviation from the exact discrete pressure y - 1 and the divergence of the projected
-    velocity relative to the initial one (volume-weighted RMS)."""
+    deviation from the exact discrete pressure y - 1 and the divergence left after the
+    projection relative to the initial one (volume-weighted RMS)."""
     import math
     import numpy as np
     import torch

@@ -1,7 +1,7 @@
 """Oracle octree: refinement, face 2:1 balance and canonical tables (TEST INFRASTRUCTURE).
 
-Follows Sec. 3 of the paper: leaf cells carry the unknowns, an inner cell is the
-parent of 8 cells one depth finer, and two face-neighbouring leaves differ by at
+Follows Sec. 3 of the paper: leaf cells carry the unknowns, an inner cell has 8
+children one depth finer, and two face-neighbouring leaves differ by at
 most one depth.  Refinement is top-down from the root grid by the predicate of the
 problem description (Sec. 4.1 grids); the 2:1 rule is then enforced by the minimal
 extra refinement, processed from the deepest inner cells upward: every inner cell at

@@ -375,7 +375,7 @@ TANK_BC = (NEUMANN, NEUMANN, NEUMANN, DIRICHLET, NEUMANN, NEUMANN)   # open to a
 
 def tank(obstacle: str, n0: int, solid: str = "centre", tiles: bool = False) -> Problem:
     """Static tank (Sec. 4.4): liquid filling [0,1]^3, solid bottom and sides (Neumann),
-    open to air at the top (y = 1: zero-pressure Dirichlet), a solid obstacle (sphere of
+    a free surface at y = 1 (zero-pressure Dirichlet), a solid obstacle (sphere of
     radius 0.25 or the star of Sec. 4.1) at the centre with fluid-fraction beta; rhs = the
     integrated divergence of the uniform velocity (0, -1, 0) (no flux through the solid
     walls, inflow through the open top).  solid: "centre" (the paper's solver: cells whose

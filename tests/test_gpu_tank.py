@@ -9,7 +9,7 @@ band grids and on the paper's tile grids up to the 128^3 root, the mixed W-cycle
 1e-6 with the paper's classification converges with a fitted residual reduction above 5
 per iteration (the paper fits 7.16 for the sphere, 5.17 and 5.88 for the star), its
 pressure stays within 6e-3 of y - 1 on the active cells (the T ghosts beside partly active
-octets; the oracle's pins measure 0.5e-3 to 5e-3), and the divergence of the projected velocity, (b - A p) / V,
+octets; the oracle's pins measure 0.5e-3 to 5e-3), and the divergence left after the projection, (b - A p) / V,
 is below 1e-5 of the initial divergence (volume-weighted RMS over the active cells).
 """
 import math

@@ -5,8 +5,8 @@ of the uniform velocity (0, -1, 0) as rhs.
 Pins: the velocity is minus the gradient of the linear field y, which the discretisation
 reproduces exactly (regular faces, cut-cell faces with any beta, the T-junction ghost
 value, the Dirichlet face at the open top), so the discrete pressure is p = y - 1 to
-rounding (the field that cancels the motion: the paper's "nearly uniform gradient along
-y"), whatever the obstacle and grid, when the solid's interior is kept at beta = 1e-3; with
+rounding (the field that cancels the motion, whose gradient points along y as the
+paper's figure shows), whatever the obstacle and grid, when the solid's interior is kept at beta = 1e-3; with
 the interior inactive it stays within 5e-3, both with the paper's classification of the
 solid cells (Sec. 2.1: a cell whose centre is in the solid is a Neumann cell without an
 unknown, the faces touching it carry no coefficient) and with exact fractions on every
